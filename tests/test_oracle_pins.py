@@ -1,0 +1,338 @@
+"""Pins of the CPU oracle to what the paper and the mathematics fix (no GPU needed).
+
+Each test checks the oracle against something other than itself: the subtract-with-
+borrow recurrence run step by step (the definition of RANLUX), closed forms derived by
+hand, algebraic invariants, and values the paper prints.  A plausible mistake in the
+oracle (a wrong lag, a dropped borrow, a wrong shift in the conversion, a wrong
+exponent in seeding, a transposed word pair in the 48-bit draw) fails one of them.
+"""
+import os
+import random
+
+import numpy as np
+import pytest
+
+from oracle import ranluxpp as R
+from oracle import swb_lib as S
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _paper_constants():
+    out = {}
+    with open(os.path.join(GOLDEN, "paper_constants.txt")) as fh:
+        for line in fh:
+            line = line.split("#")[0].strip()
+            if line:
+                k, v = (t.strip() for t in line.split("="))
+                out[k] = v
+    return out
+
+
+def _random_swb_state(rng, warmup=48):
+    """A state reached by running the recurrence (canonical for the LCG map)."""
+    w = [rng.randrange(R.BASE) for _ in range(24)]
+    c = rng.randrange(2)
+    return R.swb_steps(w, c, warmup)
+
+
+# --- constants the paper prints ---------------------------------------------------
+def test_modulus_is_the_papers():
+    pc = _paper_constants()
+    assert pc["modulus_formula"] == "2^576 - 2^240 + 1"
+    assert R.M == 2 ** 576 - 2 ** 240 + 1           # Sec. 2.2
+    assert R.M == R.BASE ** 24 - R.BASE ** 10 + 1   # b^r - b^s + 1
+    assert R.STATE_BITS == int(pc["state_bits"]) == 64 * int(pc["state_limbs_u64"])
+    assert int(pc["double_bits"]) == 48
+    assert R.SEED_SHIFT == int(pc["seed_skip_exponent"])
+
+
+def test_one_step_multiplier_closed_form():
+    # a = m - (m - 1) / 2^24, (m - 1) / 2^24 = 2^552 - 2^216, derived by hand.
+    a = R.one_step_multiplier()
+    assert a == 2 ** 576 - 2 ** 552 - 2 ** 240 + 2 ** 216 + 1
+    assert (a * R.BASE - 1) % R.M == 0
+    # sparse form a = 2^216 - 2^552 (mod m)
+    assert (a - (2 ** 216 - 2 ** 552)) % R.M == 0
+
+
+def test_luxury_multiplier_small_powers():
+    a = R.one_step_multiplier()
+    assert R.luxury_multiplier(1) == a
+    assert R.luxury_multiplier(2) == a * a % R.M
+    assert R.luxury_multiplier(0) == 1
+    # a^24 = b^-24 = 2^-576 = (2^240 - 1)^-1 mod m
+    assert R.luxury_multiplier(24) * (2 ** 240 - 1) % R.M == 1
+
+
+# --- the LCG equals the recurrence --------------------------------------------------
+def test_lcg_equals_swb_p24_ten_thousand():
+    """10,000 single LCG advances at p = 24, each against 24 recurrence steps."""
+    p = 24
+    A = R.luxury_multiplier(p)
+    w, c = R.to_ranlux(R.seed_lcg(1, p))
+    w = R.unpack_words(w)
+    X = R.to_lcg(R.pack_words(w), c)
+    for _ in range(10_000):
+        w, c = R.swb_steps(w, c, p)
+        X = R.advance(X, A)
+        D, cx = R.to_ranlux(X)
+        assert R.unpack_words(D) == w and cx == c
+        assert R.to_lcg(R.pack_words(w), c) == X
+
+
+@pytest.mark.parametrize("p", [1, 2, 7, 23, 24, 25, 223, 389, 2048])
+def test_lcg_equals_swb_various_p(p):
+    rng = random.Random(1000 + p)
+    A = R.luxury_multiplier(p)
+    for _ in range(20):
+        w, c = _random_swb_state(rng)
+        X = R.to_lcg(R.pack_words(w), c)
+        w2, c2 = S.block(w, c, p)           # C recurrence
+        if p <= 400:
+            assert (w2, c2) == tuple(R.swb_steps(w, c, p))  # Python recurrence
+        D, cx = R.to_ranlux(R.advance(X, A))
+        assert R.unpack_words(D) == w2 and cx == c2
+
+
+def test_c_and_python_recurrence_agree():
+    rng = random.Random(7)
+    for _ in range(50):
+        w = [rng.randrange(R.BASE) for _ in range(24)]
+        c = rng.randrange(2)
+        n = rng.randrange(1, 100)
+        assert S.block(w, c, n) == tuple(R.swb_steps(w, c, n))
+
+
+def test_recurrence_hand_values():
+    """One step on hand-made windows: x_n = x_{n-10} - x_{n-24} - c mod 2^24."""
+    w = list(range(24))            # w[0] = 0 is x_{n-24}, w[14] = 14 is x_{n-10}
+    w2, c2 = R.swb_step(w, 0)
+    assert w2[-1] == 14 and c2 == 0 and w2[:-1] == w[1:]
+    w = [5] + [0] * 23             # 0 - 5 - 1 = -6 -> 2^24 - 6, borrow 1
+    w2, c2 = R.swb_step(w, 1)
+    assert w2[-1] == 2 ** 24 - 6 and c2 == 1
+    assert S.block([5] + [0] * 23, 1, 1) == ([0] * 23 + [2 ** 24 - 6], 1)
+
+
+# --- conversions ----------------------------------------------------------------------
+def test_conversion_round_trip_and_range():
+    rng = random.Random(3)
+    xs = [1, 2, 3, R.M - 1, R.M - 2, 2 ** 575, 2 ** 576 - 2 ** 240, 2 ** 336, 2 ** 336 - 1,
+          2 ** 240, 2 ** 240 - 1] + [rng.randrange(1, R.M) for _ in range(2000)]
+    for X in xs:
+        D, c = R.to_ranlux(X)
+        assert c in (0, 1)
+        assert 0 <= D < 2 ** 576
+        assert R.to_lcg(D, c) == X
+        # D / 2^576 approximates X / m from below within 2^-576
+        assert D * R.M <= X * 2 ** 576 < (D + 1) * R.M
+
+
+def test_conversion_inverts_recurrence_states():
+    rng = random.Random(5)
+    for _ in range(500):
+        w, c = _random_swb_state(rng)
+        X = R.to_lcg(R.pack_words(w), c)
+        assert 0 < X < R.M
+        D, c2 = R.to_ranlux(X)
+        assert R.unpack_words(D) == w and c2 == c
+
+
+# --- modulo ---------------------------------------------------------------------------
+def test_mod_m_closed_forms():
+    M = R.M
+    assert R.mod_m(0) == 0
+    assert R.mod_m(1) == 1
+    assert R.mod_m(M - 1) == M - 1
+    assert R.mod_m(M) == 0
+    assert R.mod_m(M + 1) == 1
+    assert R.mod_m(2 * M - 1) == M - 1
+    assert R.mod_m(2 * M) == 0
+    assert R.mod_m(2 ** 576 - 1) == 2 ** 240 - 2            # 2^576 = m + 2^240 - 1
+    assert R.mod_m(2 ** 576) == 2 ** 240 - 1
+    assert R.mod_m((M - 1) ** 2) == 1                         # (-1)^2
+    # 2^1152 = (2^240 - 1)^2 = 2^480 - 2^241 + 1 < m
+    assert R.mod_m(2 ** 1152 - 1) == 2 ** 480 - 2 ** 241
+    assert R.mod_m(2 ** 1152) == 2 ** 480 - 2 ** 241 + 1
+
+
+def test_multiply9x9_limbs():
+    """Sec. 2.1: 18 output limbs; each 64-bit column sums its pair products."""
+    rng = random.Random(11)
+    for _ in range(100):
+        x, y = rng.randrange(2 ** 576), rng.randrange(2 ** 576)
+        xs = [(x >> (64 * i)) & (2 ** 64 - 1) for i in range(9)]
+        ys = [(y >> (64 * i)) & (2 ** 64 - 1) for i in range(9)]
+        cols = [0] * 19
+        for i in range(9):
+            for j in range(9):
+                cols[i + j] += xs[i] * ys[j]
+        acc, carry = 0, 0
+        for k in range(18):
+            t = cols[k] + carry
+            acc |= (t & (2 ** 64 - 1)) << (64 * k)
+            carry = t >> 64
+        assert carry == 0
+        assert R.multiply9x9(x, y) == acc
+
+
+# --- seeding and skipping -------------------------------------------------------------
+def test_skip_equals_single_advances():
+    for p in (24, 2048):
+        s = R.Stream(p, seed=3)
+        t = R.Stream(p, seed=3)
+        A = R.luxury_multiplier(p)
+        X = t.X
+        for n in range(1, 40):
+            X = R.advance(X, A)
+            s2 = R.Stream(p, X=s.X)
+            s2.skip(n)
+            assert s2.X == X
+
+
+def test_skip_composes():
+    rng = random.Random(17)
+    for _ in range(10):
+        n1, n2 = rng.randrange(2 ** 128), rng.randrange(2 ** 128)
+        a = R.Stream(2048, seed=5)
+        b = R.Stream(2048, seed=5)
+        a.skip(n1)
+        a.skip(n2)
+        b.skip(n1 + n2)
+        assert a.X == b.X
+
+
+def test_seed_spacing_is_2_96_advances():
+    p = 2048
+    s1 = R.Stream(p, seed=1)
+    s2 = R.Stream(p, seed=2)
+    s1.skip(2 ** 96)
+    assert s1.X == s2.X
+    # seed 1 from the state 1 by square-and-multiply written out by hand
+    A = R.luxury_multiplier(p)
+    y = A
+    for _ in range(96):
+        y = y * y % R.M
+    assert R.seed_lcg(1, p) == y
+
+
+def test_skip_keeps_position_and_matches_recurrence_blocks():
+    p = 223
+    s = R.Stream(p, seed=9)
+    s.draw_u24(5)
+    w, c = s.words(), s.c
+    s.skip(3)
+    assert s.pos == 5
+    for _ in range(3):
+        w, c = S.block(w, c, p)
+    assert s.words() == w and s.c == c
+
+
+# --- draw rule ---------------------------------------------------------------------------
+def _blocks_from_recurrence(w, c, p, n_blocks):
+    out = [list(w)]
+    for _ in range(n_blocks - 1):
+        w, c = S.block(w, c, p)
+        out.append(list(w))
+    return out
+
+
+@pytest.mark.parametrize("p", [24, 389, 2048])
+def test_u24_draws_are_recurrence_blocks(p):
+    s = R.Stream(p, seed=4)
+    blocks = _blocks_from_recurrence(s.words(), s.c, p, 5)
+    got = s.draw_u24(24 * 5)
+    assert got == [x for b in blocks for x in b]
+
+
+@pytest.mark.parametrize("p", [24, 2048])
+def test_f64_draws_pair_words_low_first(p):
+    s = R.Stream(p, seed=6)
+    blocks = _blocks_from_recurrence(s.words(), s.c, p, 4)
+    got = s.draw_f64(12 * 4)
+    want = [(b[2 * k] + (b[2 * k + 1] << 24)) * 2.0 ** -48 for b in blocks for k in range(12)]
+    assert got == want
+    for v in got:
+        assert 0.0 <= v < 1.0 and (v * 2 ** 48).is_integer()
+
+
+def test_f64_discards_odd_leftover_word():
+    s = R.Stream(24, seed=8)
+    blocks = _blocks_from_recurrence(s.words(), s.c, 24, 2)
+    assert s.draw_u24(23) == blocks[0][:23]     # one word left in block 0
+    v = s.draw_bits48(1)[0]                       # needs two: comes from block 1
+    assert v == blocks[1][0] + (blocks[1][1] << 24)
+    assert s.pos == 2
+
+
+def test_double_conversion_closed_forms():
+    assert R.f64_from_bits48(0) == 0.0
+    assert R.f64_from_bits48(1) == 2.0 ** -48
+    assert R.f64_from_bits48(2 ** 47) == 0.5
+    assert R.f64_from_bits48(2 ** 48 - 1) == 1.0 - 2.0 ** -48
+    assert R.f64_bits(R.f64_from_bits48(2 ** 48 - 1)) == 0x3FEFFFFFFFFFFFE0  # mantissa 2^52 - 2^5
+    assert R.f64_bits(0.5) == 0x3FE0000000000000
+
+
+def test_sum_hist_brute_force():
+    vals = [0, 1, 2 ** 40 - 1, 2 ** 40, 2 ** 48 - 1, 5 * 2 ** 40 + 7]
+    s, h = R.sum_hist48(vals)
+    assert s == sum(vals)
+    assert h[0] == 3 and h[1] == 1 and h[255] == 1 and h[5] == 1 and sum(h) == 6
+
+
+# --- the C oracle's draw rule against the Python one -----------------------------------
+@pytest.mark.parametrize("kind", [S.KIND_U24, S.KIND_F64, S.KIND_BITS48])
+def test_c_draws_match_python(kind):
+    p = 389
+    streams = [R.Stream(p, seed=s) for s in range(1, 9)]
+    for k, st in enumerate(streams):     # assorted start positions
+        st.draw_u24(k * 3)
+    words = np.array([st.words() for st in streams], dtype=np.uint32)
+    carry = np.array([st.c for st in streams], dtype=np.uint32)
+    pos = np.array([st.pos for st in streams], dtype=np.int32)
+    n = 61
+    got = S.draw_many(words, carry, pos, p, n, kind, threads=3)
+    for k, st in enumerate(streams):
+        if kind == S.KIND_U24:
+            want = st.draw_u24(n)
+        elif kind == S.KIND_F64:
+            want = st.draw_f64(n)
+        else:
+            want = st.draw_bits48(n)
+        assert list(got[k]) == want
+        assert list(words[k]) == st.words() and carry[k] == st.c and pos[k] == st.pos
+
+
+def test_c_sum_hist_matches_python():
+    p = 2048
+    streams = [R.Stream(p, seed=s) for s in range(1, 6)]
+    words = np.array([st.words() for st in streams], dtype=np.uint32)
+    carry = np.array([st.c for st in streams], dtype=np.uint32)
+    pos = np.zeros(5, dtype=np.int32)
+    sums, hist = S.sum_hist_many(words, carry, pos, p, 100, threads=2)
+    all_vals = []
+    for k, st in enumerate(streams):
+        vals = st.draw_bits48(100)
+        all_vals += vals
+        assert int(sums[k]) == sum(vals)
+    assert [int(h) for h in hist] == R.sum_hist48(all_vals)[1]
+
+
+# --- golden regression vectors ------------------------------------------------------------
+def test_golden_seed_vectors():
+    rows = []
+    with open(os.path.join(GOLDEN, "seed_vectors.txt")) as fh:
+        for line in fh:
+            if line.startswith("#") or not line.strip():
+                continue
+            p, s, kind, k, v = line.split()
+            rows.append((int(p), int(s), kind, int(k), int(v, 16)))
+    cache = {}
+    for p, s, kind, k, v in rows:
+        key = (p, s, kind)
+        if key not in cache:
+            st = R.Stream(p, seed=s)
+            cache[key] = st.draw_u24(30) if kind == "u24" else [R.f64_bits(x) for x in st.draw_f64(15)]
+        assert cache[key][k] == v, (p, s, kind, k)
