@@ -1,0 +1,370 @@
+#!/usr/bin/env python3
+"""Benchmark of the RANLUX++ hot path on GB300: the 2^20-stream workload.
+
+One step = the whole hot path over 2^20 independent streams at luxury p = 2048:
+  1. rlxpp_seed: stream i restarts at the seed-1 state skipped by i 2^96 advances
+     (exponentiation by squaring over the power table, Sec. 2.4);
+  2. rlxpp_draw_f64: 1024 doubles per stream written to HBM (8 GiB);
+  3. rlxpp_draw_f64_sum_hist: 4096 more doubles per stream consumed in the kernel by an
+     exact sum and a 256-bin histogram (no output traffic; the consumer of the paper's
+     GPU benchmark, Sec. 4.2).
+That is 5120 doubles and 426 LCG advances per stream per step.  Every step writes 8 GiB,
+more than the 129 MB L2, so no explicit flush is needed between steps.
+
+Prints one JSON line (rank 0).  `--impl reference` times the CPU oracle instead (the
+plain recurrence in C on the host cores, over a bounded sample of the same workload).
+Under torchrun each rank runs its own disjoint range of streams (weak scaling, no
+collective on the data path).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "LCG advances/s and random doubles/s on 1 GB300 (bit-exact), % of INT/IMMA roofline"
+UNIT = "doubles/s"
+N_STREAMS = 1 << 20
+LUXURY = 2048
+HBM_COUNT = 1024
+FUSED_COUNT = 4096
+# Per stream and step: 1024 doubles from a freshly seeded block take 85 refills and stop
+# at read position 8; the 4096 fused doubles take the 8 left in that block and then
+# 341 refills (advances_for below); 426 LCG advances in all.
+IMAD_PER_ADVANCE = 648        # 18 x 18 products of 32 x 32 -> 64 bits = 324 lo + 324 hi
+SMS = 152
+IMAD_PER_SM_CLK = 64
+SM_MAX_MHZ = 2070.0
+CPU_SAMPLE_STREAMS = 16384
+
+
+def advances_for(count, pos_words, need=2):
+    """Refills needed to draw `count` values of `need` words from read position pos."""
+    room = max(0, (24 - pos_words) // need)
+    head = min(count, room)
+    rest = count - head
+    per = 24 // need
+    adv = -(-rest // per)
+    last = rest - (adv - 1) * per if adv else 0
+    new_pos = pos_words + head * need if adv == 0 else last * need
+    return adv, new_pos
+
+
+ADV_HBM, POS_AFTER_HBM = advances_for(HBM_COUNT, 0)
+ADV_FUSED, _ = advances_for(FUSED_COUNT, POS_AFTER_HBM)
+ADV_PER_STREAM = ADV_HBM + ADV_FUSED
+
+
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return json.load(fh)
+    except OSError:
+        return {}
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms in the background."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = str(gpu_index)
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits", "-lms", "200",
+                 "-i", self.gpu], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        with open(self.path) as fh:
+            for line in fh:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons, "samples": len(rows)}
+
+
+def cpu_oracle_sample(n_sample, first_seed, threads=None):
+    """The oracle as it stands on the host cores: seed n_sample streams (Python big
+    integers), then 1024 doubles and 4096 fused doubles per stream (C recurrence,
+    one thread per stream range).  Returns (seconds, doubles, threads)."""
+    import numpy as np
+
+    from oracle import swb_lib as S
+    from tests.oracle_side import StreamSet
+    S.build()
+    threads = threads or S.default_threads()
+    seeds = np.arange(first_seed, first_seed + n_sample, dtype=np.uint64)
+    t0 = time.perf_counter()
+    ss = StreamSet.from_seeds(seeds, LUXURY)
+    S.draw_many(ss.words, ss.carry, ss.pos, LUXURY, HBM_COUNT, S.KIND_F64, threads=threads)
+    S.sum_hist_many(ss.words, ss.carry, ss.pos, LUXURY, FUSED_COUNT, threads=threads)
+    dt = time.perf_counter() - t0
+    return dt, n_sample * (HBM_COUNT + FUSED_COUNT), threads
+
+
+def workload_config(n_streams, world):
+    return {"workload": f"{n_streams} streams x {world} ranks, p={LUXURY}: seed (stream i = seed-1 state "
+                        f"skipped by i*2^96 advances) + {HBM_COUNT} f64/stream to HBM + {FUSED_COUNT} "
+                        f"f64/stream fused exact sum + 256-bin histogram",
+            "streams_per_gpu": n_streams, "luxury": LUXURY, "doubles_per_stream_per_step": HBM_COUNT + FUSED_COUNT,
+            "advances_per_stream_per_step": ADV_PER_STREAM, "hbm_bytes_per_step": n_streams * HBM_COUNT * 8,
+            "l2": "each step writes 8 GiB (> 129 MB L2); no explicit flush", "parallelism": f"streams x{world}"}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return 0
+    n_sample = args.cpu_sample
+    for _ in range(args.warmup):
+        cpu_oracle_sample(min(n_sample, 1024), 1)
+    times = []
+    threads = None
+    doubles = 0
+    for _ in range(args.steps):
+        dt, doubles, threads = cpu_oracle_sample(n_sample, 1)
+        times.append(dt)
+    tot = sum(times)
+    value = doubles * args.steps / tot
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
+            "data": "synthetic", "config": workload_config(args.streams, world),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
+                             "sample": f"first {n_sample} of the {args.streams} streams per step: seed + "
+                                       f"{HBM_COUNT} f64 + {FUSED_COUNT} fused f64 each (C recurrence oracle, "
+                                       f"{threads} threads)"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_native(args, rank, world, local_rank):
+    import numpy as np
+    import torch
+
+    import paper_2106_02504_gb300 as P
+    nat = P.native
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+    n = args.streams
+    first_seed = 1 + rank * n
+    seeds_h = np.arange(first_seed, first_seed + n, dtype=np.uint64)
+    seeds = torch.from_numpy(seeds_h.view(np.int64)).to(dev)
+    g = nat.Generator(n, [LUXURY], seeds)
+    out = torch.empty((n, HBM_COUNT), dtype=torch.float64, device=dev)
+    sums = torch.zeros(n, dtype=torch.int64, device=dev)
+    hist = torch.zeros(256, dtype=torch.int64, device=dev)
+    stream = torch.cuda.current_stream()
+    sp = stream.cuda_stream
+
+    def step(ev=None):
+        if ev:
+            ev[0].record(stream)
+        nat.rlxpp_seed(g.handle, seeds, sp)
+        if ev:
+            ev[1].record(stream)
+        nat.rlxpp_draw_f64(g.handle, out, HBM_COUNT, None, None, sp)
+        if ev:
+            ev[2].record(stream)
+        nat.rlxpp_draw_f64_sum_hist(g.handle, FUSED_COUNT, sums, hist, sp)
+        if ev:
+            ev[3].record(stream)
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    for _ in range(args.warmup):
+        step()
+    g.sync(sp)
+    launches_per_step = 3
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(args.steps)]
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    clk = ClockSampler(local_rank)
+    barrier()
+    torch.cuda.synchronize()
+    clk.start()
+    t0.record(stream)
+    for k in range(args.steps):
+        step(evs[k])
+    t1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    clocks = clk.stop()
+    g.sync(sp)
+    ms = t0.elapsed_time(t1)
+    if dist is not None:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    ms_step = ms / args.steps
+    per_kernel = {
+        "seed": statistics.mean(e[0].elapsed_time(e[1]) for e in evs),
+        "draw_f64_hbm": statistics.mean(e[1].elapsed_time(e[2]) for e in evs),
+        "draw_f64_sum_hist": statistics.mean(e[2].elapsed_time(e[3]) for e in evs),
+    }
+    doubles_step = n * (HBM_COUNT + FUSED_COUNT) * world
+    advances_step = n * ADV_PER_STREAM * world
+    value = doubles_step / (ms_step * 1e-3)
+    peaks = load_peaks()
+    imad_peak = SMS * IMAD_PER_SM_CLK * SM_MAX_MHZ * 1e6  # IMAD ops/s, derived
+    hbm_peak = peaks.get("hbm_gbs", 6800.0)
+    kern = {}
+    for name, kms in per_kernel.items():
+        entry = {"ms": kms, "share": kms / sum(per_kernel.values())}
+        if name == "draw_f64_hbm":
+            adv = n * ADV_HBM
+            entry["advances_per_s"] = adv / (kms * 1e-3)
+            entry["imad_frac"] = adv * IMAD_PER_ADVANCE / (kms * 1e-3) / imad_peak
+            entry["hbm_gbs"] = n * HBM_COUNT * 8 / (kms * 1e-3) / 1e9
+            entry["hbm_frac"] = entry["hbm_gbs"] / hbm_peak
+        elif name == "draw_f64_sum_hist":
+            adv = n * ADV_FUSED
+            entry["advances_per_s"] = adv / (kms * 1e-3)
+            entry["imad_frac"] = adv * IMAD_PER_ADVANCE / (kms * 1e-3) / imad_peak
+        kern[name] = entry
+    dom = max(per_kernel, key=per_kernel.get)
+    if dom == "draw_f64_sum_hist":
+        adv = n * ADV_FUSED
+    elif dom == "draw_f64_hbm":
+        adv = n * ADV_HBM
+    else:
+        adv = 0
+    achieved = adv * IMAD_PER_ADVANCE / (per_kernel[dom] * 1e-3) / 1e12
+    roofline = {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": imad_peak / 1e12,
+                "unit": "Top/s (32-bit IMAD, 648 per advance)", "frac": achieved / (imad_peak / 1e12),
+                "peak_source": "derived: 152 SMs x 64 IMAD/clk x 2070 MHz", "traffic": None}
+
+    result = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+              "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+              "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+              "config": workload_config(n, world),
+              "advances_per_s": advances_step / (ms_step * 1e-3),
+              "gpu_launches": launches_per_step * args.steps, "kernels": kern, "roofline": roofline,
+              "clocks": clocks}
+
+    # end to end through the C ABI with host buffers
+    if not args.no_e2e:
+        result["e2e"] = run_e2e(args, nat, g, seeds_h, n, world, dev, dist)
+    g.close()
+    del out
+    if rank == 0 and not args.no_cpu_baseline:
+        dt, doubles, threads = cpu_oracle_sample(args.cpu_sample, 1)
+        result["cpu_baseline"] = {
+            "value": doubles / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": f"first {args.cpu_sample} of the {n} streams: seed + {HBM_COUNT} f64 + {FUSED_COUNT} "
+                      f"fused f64 each (C recurrence oracle, {threads} threads), {dt:.1f} s"}
+    if rank == 0:
+        print(json.dumps(result), flush=True)
+    return 0
+
+
+def run_e2e(args, nat, g, seeds_h, n, world, dev, dist):
+    import numpy as np
+    import torch
+    seeds_pin = torch.from_numpy(seeds_h.view(np.int64)).pin_memory()
+    out_pin = torch.empty((n, HBM_COUNT), dtype=torch.float64).pin_memory()
+    sums = torch.zeros(n, dtype=torch.int64, device=dev)
+    hist = torch.zeros(256, dtype=torch.int64, device=dev)
+    sums_h = torch.empty(n, dtype=torch.int64).pin_memory()
+    hist_h = torch.empty(256, dtype=torch.int64).pin_memory()
+    sp = torch.cuda.current_stream().cuda_stream
+
+    def step():
+        nat.rlxpp_seed(g.handle, seeds_pin, sp)                       # host seeds
+        nat.rlxpp_draw_f64(g.handle, out_pin, HBM_COUNT, None, None, sp)  # host output
+        nat.rlxpp_draw_f64_sum_hist(g.handle, FUSED_COUNT, sums, hist, sp)
+        sums_h.copy_(sums, non_blocking=True)
+        hist_h.copy_(hist, non_blocking=True)
+        torch.cuda.current_stream().synchronize()
+
+    steps = max(1, min(args.steps, 3))
+    step()
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        step()
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    if dist is not None:
+        t = torch.tensor([dt], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dt = float(t.item())
+    doubles = n * (HBM_COUNT + FUSED_COUNT) * world * steps
+    return {"value": doubles / dt, "unit": UNIT, "h2d_bytes_per_step": n * 8,
+            "d2h_bytes_per_step": n * HBM_COUNT * 8 + n * 8 + 256 * 8, "steps": steps,
+            "how": "rlxpp_seed from pinned host seeds, rlxpp_draw_f64 into pinned host memory (library-staged, "
+                   "double-buffered), fused sum/hist with sums+hist read back; wall clock"}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["native", "reference"], default="native")
+    ap.add_argument("--streams", type=int, default=N_STREAMS)
+    ap.add_argument("--cpu-sample", type=int, default=CPU_SAMPLE_STREAMS)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local_rank)
+        dist.init_process_group("nccl")
+    try:
+        return run_native(args, rank, world, local_rank)
+    finally:
+        if world > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    sys.exit(main())

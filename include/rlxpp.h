@@ -1,0 +1,176 @@
+/*
+ * rlxpp — RANLUX++ random number streams on one NVIDIA GB300 (sm_103a).
+ *
+ * C ABI of librlxpp.so.  The method is the one of Hahnfeld & Moneta, "A Portable
+ * Implementation of RANLUX++" (arXiv 2106.02504): the RANLUX subtract-with-borrow
+ * generator (base 2^24, lags 24 and 10, with a borrow bit) run as a linear
+ * congruential generator X <- A X mod m with m = 2^576 - 2^240 + 1 (Sec. 1, Sec. 2.2)
+ * and A = a^p, a = 2^-24 mod m, for luxury level p.  Each stream keeps the paper's
+ * state (Sec. 2): 24 RANLUX numbers packed in 576 bits, the borrow bit, the read
+ * position.  A refill converts the numbers to the LCG state, multiplies by A
+ * (multiply9x9, Sec. 2.1), reduces mod m (mod_m, Sec. 2.2) and converts back
+ * (Sec. 2.3).
+ *
+ * Conventions shared by every entry point
+ *  - Calls are asynchronous on the CUDA stream passed as `cuda_stream` (a
+ *    cudaStream_t; NULL = the legacy default stream).  Argument errors are detected on
+ *    the host and returned at once; errors found by kernels are sticky and reported by
+ *    rlxpp_sync().
+ *  - Pointers to per-stream arrays and outputs may point to device memory or to host
+ *    memory (pinned or pageable).  Host arrays are staged through device buffers that
+ *    the library owns; the call then returns only after the host data has been read
+ *    (inputs) or written (outputs).
+ *  - The caller owns every buffer it passes; the library owns the generator state.
+ *  - A handle is not thread-safe: calls on one handle must not overlap in time.
+ *  - Every call returns RLXPP_OK or an error code; rlxpp_last_error() gives a message
+ *    for the calling thread's last failure.
+ *  - Draw order (a reading; the paper does not fix it): the 24 numbers of a block are
+ *    delivered oldest first.  A u24 draw returns the next number; a double takes the
+ *    next two numbers w_k, w_{k+1} (both from the current block; otherwise the stream
+ *    refills first and a lone leftover number is skipped) and returns
+ *    (w_k + 2^24 w_{k+1}) * 2^-48, exactly (Sec. 2.3: 48 bits per double).
+ *  - Seeding (Sec. 2.4, exponentiation by squaring; the 2^96 spacing is the one in
+ *    Sec. 2.5): seed s starts at the LCG state A^(2^96 s), read position 0.
+ */
+#ifndef RLXPP_H
+#define RLXPP_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct rlxpp_gen rlxpp_gen;
+
+typedef enum rlxpp_status {
+  RLXPP_OK = 0,
+  RLXPP_ERR_INVALID = 1,     /* bad argument or state record                        */
+  RLXPP_ERR_NOMEM = 2,       /* device or pinned host allocation failed             */
+  RLXPP_ERR_CUDA = 3,        /* a CUDA runtime call failed                          */
+  RLXPP_ERR_TIMEOUT = 4,     /* a bounded device-side wait gave up                  */
+  RLXPP_ERR_UNSUPPORTED = 5  /* valid request the library does not implement        */
+} rlxpp_status;
+
+/* Exported state of one stream (88 bytes), the paper's generator state (Sec. 2):
+ *  d[9]   the 24 RANLUX numbers, number k at bits 24k..24k+23 of the little-endian
+ *         576-bit value (k = 0 the oldest);
+ *  carry  the borrow bit, 0 or 1;
+ *  pos    numbers already read from the current block, 0..24;
+ *  p      luxury level (must be one of the handle's levels on import);
+ *  reserved must be 0. */
+typedef struct rlxpp_state {
+  uint64_t d[9];
+  uint32_t carry;
+  uint32_t pos;
+  uint32_t p;
+  uint32_t reserved;
+} rlxpp_state;
+
+/* Largest number of distinct luxury levels one handle can hold. */
+#define RLXPP_MAX_LEVELS 16
+
+/* Create a handle for n_streams streams and seed them.
+ *  levels[n_levels]   host array of luxury levels p >= 1 (Sec. 4.2 uses p = 2048);
+ *                     1 <= n_levels <= RLXPP_MAX_LEVELS.  For each level the library
+ *                     computes A = a^p and a table of A^(j 16^w) (w < 40, j < 16) on
+ *                     the device (Sec. 2.4).
+ *  level_of_stream    NULL (every stream uses levels[0]) or n_streams bytes, each
+ *                     < n_levels, host or device.
+ *  seeds              n_streams uint64 seeds, host or device; stream i starts at
+ *                     A^(2^96 seeds[i]).
+ *  out                receives the handle; *out is NULL on failure.
+ * n_streams may be 0.  Fails with RLXPP_ERR_INVALID on a bad level or level index
+ * (level indices are checked on the device and reported by rlxpp_sync()). */
+rlxpp_status rlxpp_create(uint64_t n_streams, const uint32_t* levels, uint32_t n_levels,
+                          const uint8_t* level_of_stream, const uint64_t* seeds,
+                          void* cuda_stream, rlxpp_gen** out);
+
+/* Re-seed every stream in place (levels unchanged): stream i restarts at
+ * A^(2^96 seeds[i]) with read position 0.  seeds: n_streams uint64, host or device. */
+rlxpp_status rlxpp_seed(rlxpp_gen* gen, const uint64_t* seeds, void* cuda_stream);
+
+/* Skip ahead (Sec. 2.4): stream i applies n_i LCG advances, X <- A^(n_i) X, without
+ * producing output; its read position is unchanged.  n128: n_streams pairs of uint64
+ * (low word first), host or device; n_i < 2^128.  Computed by square-and-multiply over
+ * the 4-bit-window power table (at most 32 modular products per stream). */
+rlxpp_status rlxpp_skip(rlxpp_gen* gen, const uint64_t* n128, void* cuda_stream);
+
+/* Draw 24-bit integers (Sec. 2.4, IntRndm) into uint32 out.
+ *  counts == NULL: every stream draws count_each values; stream i writes
+ *                  out[i * count_each + k], k < count_each (offsets ignored).
+ *  counts != NULL: stream i draws counts[i] >= 0 values to out[offsets[i] + k];
+ *                  counts and offsets are n_streams int64 each, host or device, and
+ *                  the output ranges must not overlap.
+ * out: host or device. */
+rlxpp_status rlxpp_draw_u24(rlxpp_gen* gen, const int64_t* counts, const int64_t* offsets,
+                            int64_t count_each, uint32_t* out, void* cuda_stream);
+
+/* Draw doubles in [0, 1) with 48 random bits each (Sec. 2.3, Rndm); same layout rules
+ * as rlxpp_draw_u24. */
+rlxpp_status rlxpp_draw_f64(rlxpp_gen* gen, const int64_t* counts, const int64_t* offsets,
+                            int64_t count_each, double* out, void* cuda_stream);
+
+/* Fused consumer (the GPU benchmark of Sec. 4.2 sums every number a thread draws):
+ * every stream draws count_each doubles without storing them.  sums (NULL or
+ * n_streams uint64, device) receives, per stream, the exact sum of the 48-bit
+ * integers v behind its doubles (double = v 2^-48); hist (device, 256 uint64) is
+ * incremented at bin v >> 40 for every value.  hist is accumulated, not cleared. */
+rlxpp_status rlxpp_draw_f64_sum_hist(rlxpp_gen* gen, int64_t count_each, uint64_t* sums,
+                                     uint64_t* hist, void* cuda_stream);
+
+/* Export / import the state of every stream (Sec. 4.2: the state is plain memory that
+ * can move between host and device and continue the same sequence).  dst/src:
+ * n_streams records, host or device.  Import checks each record on the device:
+ * carry <= 1, pos <= 24, p one of the handle's levels, reserved == 0, and (d, carry)
+ * must be the RANLUX form of an LCG state X with 0 < X < m, i.e. converting
+ * X = d - floor(d / 2^336) + carry back gives the same record (every state the
+ * recurrence reaches after 24 steps, and every exported state, has this form).  A bad
+ * record leaves its stream unchanged and sets a sticky RLXPP_ERR_INVALID reported by
+ * rlxpp_sync(). */
+rlxpp_status rlxpp_get_state(const rlxpp_gen* gen, rlxpp_state* dst, void* cuda_stream);
+rlxpp_status rlxpp_set_state(rlxpp_gen* gen, const rlxpp_state* src, void* cuda_stream);
+
+/* Wait for the handle's work on cuda_stream and return (and clear) the sticky device
+ * status: RLXPP_OK, RLXPP_ERR_INVALID or RLXPP_ERR_TIMEOUT. */
+rlxpp_status rlxpp_sync(rlxpp_gen* gen, void* cuda_stream);
+
+/* Number of streams of the handle. */
+uint64_t rlxpp_num_streams(const rlxpp_gen* gen);
+
+/* Message for the calling thread's last failed call ("" if none). */
+const char* rlxpp_last_error(void);
+
+/* Release the handle and its device memory (synchronises the device first). */
+void rlxpp_destroy(rlxpp_gen* gen);
+
+/* ---- unit-test entry points (device arithmetic on n independent items) ----------
+ * Numbers are little-endian arrays of uint64 limbs, item-major; all pointers are
+ * device pointers and n may be 0.
+ *  rlxpp_test_multiply9x9  x[9], y[9] -> out[18] = x * y              (Sec. 2.1)
+ *  rlxpp_test_mod_m        in[18]     -> out[9]  = in mod m, in [0, m) (Sec. 2.2)
+ *  rlxpp_test_mul_mod      x[9], y[9] -> out[9]  = x y mod m; x, y < 2^576
+ *  rlxpp_test_to_ranlux    x[9] (< m) -> d[9] = floor(2^576 x / m), carry[1] (Sec. 2.3)
+ *  rlxpp_test_to_lcg       d[9], carry[1] -> x[9] = d - floor(d / 2^336) + carry
+ *  rlxpp_test_f64_from48   v[1] (< 2^48) -> out[1] = bit pattern of v 2^-48 */
+rlxpp_status rlxpp_test_multiply9x9(const uint64_t* x, const uint64_t* y, uint64_t* out,
+                                    uint64_t n, void* cuda_stream);
+rlxpp_status rlxpp_test_mod_m(const uint64_t* in, uint64_t* out, uint64_t n, void* cuda_stream);
+rlxpp_status rlxpp_test_mul_mod(const uint64_t* x, const uint64_t* y, uint64_t* out,
+                                uint64_t n, void* cuda_stream);
+rlxpp_status rlxpp_test_to_ranlux(const uint64_t* x, uint64_t* d, uint32_t* carry,
+                                  uint64_t n, void* cuda_stream);
+rlxpp_status rlxpp_test_to_lcg(const uint64_t* d, const uint32_t* carry, uint64_t* x,
+                               uint64_t n, void* cuda_stream);
+rlxpp_status rlxpp_test_f64_from48(const uint64_t* v, uint64_t* out, uint64_t n,
+                                   void* cuda_stream);
+
+/* Luxury multiplier A = a^p mod m as 9 uint64 limbs written to host memory out9,
+ * computed on the device (Sec. 1: RANLUX as an LCG with a large multiplier). */
+rlxpp_status rlxpp_luxury_multiplier(uint32_t p, uint64_t* out9);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* RLXPP_H */

@@ -1,0 +1,248 @@
+"""ctypes binding of librlxpp.so, one Python function per C entry point of
+include/rlxpp.h, with the same names.  Only argument marshalling happens here: integers
+and pointers are passed through, torch tensors are passed by ``data_ptr()``, CUDA
+streams by their handle.  Every non-OK status raises ``RlxppError``.
+
+There is no fallback: if the CUDA library is missing, importing this module fails.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+from . import build as _build
+
+_vp = ctypes.c_void_p
+_u64 = ctypes.c_uint64
+_i64 = ctypes.c_int64
+_u32 = ctypes.c_uint32
+
+
+class RlxppState(ctypes.Structure):
+    """struct rlxpp_state (88 bytes)."""
+    _fields_ = [("d", ctypes.c_uint64 * 9), ("carry", ctypes.c_uint32), ("pos", ctypes.c_uint32),
+                ("p", ctypes.c_uint32), ("reserved", ctypes.c_uint32)]
+
+
+STATE_BYTES = ctypes.sizeof(RlxppState)
+assert STATE_BYTES == 88
+
+RLXPP_OK, RLXPP_ERR_INVALID, RLXPP_ERR_NOMEM, RLXPP_ERR_CUDA, RLXPP_ERR_TIMEOUT, \
+    RLXPP_ERR_UNSUPPORTED = range(6)
+RLXPP_MAX_LEVELS = 16
+
+
+class RlxppError(RuntimeError):
+    def __init__(self, status, message):
+        super().__init__(f"rlxpp status {status}: {message}")
+        self.status = status
+
+
+def _load():
+    path = _build.LIB_PATH
+    if not os.path.exists(path):
+        raise ImportError(
+            f"librlxpp.so not built ({path}); run paper_2106_02504_gb300.build.build() first")
+    L = ctypes.CDLL(path)
+    sigs = {
+        "rlxpp_create": [_u64, _vp, _u32, _vp, _vp, _vp, ctypes.POINTER(_vp)],
+        "rlxpp_seed": [_vp, _vp, _vp],
+        "rlxpp_skip": [_vp, _vp, _vp],
+        "rlxpp_draw_u24": [_vp, _vp, _vp, _i64, _vp, _vp],
+        "rlxpp_draw_f64": [_vp, _vp, _vp, _i64, _vp, _vp],
+        "rlxpp_draw_f64_sum_hist": [_vp, _i64, _vp, _vp, _vp],
+        "rlxpp_get_state": [_vp, _vp, _vp],
+        "rlxpp_set_state": [_vp, _vp, _vp],
+        "rlxpp_sync": [_vp, _vp],
+        "rlxpp_test_multiply9x9": [_vp, _vp, _vp, _u64, _vp],
+        "rlxpp_test_mod_m": [_vp, _vp, _u64, _vp],
+        "rlxpp_test_mul_mod": [_vp, _vp, _vp, _u64, _vp],
+        "rlxpp_test_to_ranlux": [_vp, _vp, _vp, _u64, _vp],
+        "rlxpp_test_to_lcg": [_vp, _vp, _vp, _u64, _vp],
+        "rlxpp_test_f64_from48": [_vp, _vp, _u64, _vp],
+        "rlxpp_luxury_multiplier": [_u32, _vp],
+    }
+    for name, args in sigs.items():
+        fn = getattr(L, name)
+        fn.argtypes = args
+        fn.restype = ctypes.c_int
+    L.rlxpp_num_streams.argtypes = [_vp]
+    L.rlxpp_num_streams.restype = _u64
+    L.rlxpp_last_error.argtypes = []
+    L.rlxpp_last_error.restype = ctypes.c_char_p
+    L.rlxpp_destroy.argtypes = [_vp]
+    L.rlxpp_destroy.restype = None
+    return L
+
+
+_lib = _load()
+LIB_PATH = _build.LIB_PATH
+
+
+def _ptr(x):
+    """None -> NULL, int -> address, torch tensor / numpy array -> its data pointer."""
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if hasattr(x, "data_ptr"):
+        return x.data_ptr()
+    if hasattr(x, "ctypes"):
+        return x.ctypes.data
+    if isinstance(x, ctypes.Array) or isinstance(x, ctypes.Structure):
+        return ctypes.addressof(x)
+    raise TypeError(f"cannot pass {type(x)} as a pointer")
+
+
+def _stream(s):
+    if s is None:
+        try:
+            import torch
+            if torch.cuda.is_available():
+                return torch.cuda.current_stream().cuda_stream
+        except ImportError:  # pragma: no cover
+            pass
+        return None
+    if isinstance(s, int):
+        return s
+    return s.cuda_stream
+
+
+def _check(status):
+    if status != RLXPP_OK:
+        raise RlxppError(status, _lib.rlxpp_last_error().decode(errors="replace"))
+
+
+# ---- one function per C entry point ------------------------------------------------
+def rlxpp_create(n_streams, levels, seeds, level_of_stream=None, stream=None):
+    """Returns the handle (an int).  levels: sequence of luxury levels p (host)."""
+    arr = (_u32 * len(levels))(*levels)
+    h = _vp()
+    _check(_lib.rlxpp_create(n_streams, arr, len(levels), _ptr(level_of_stream), _ptr(seeds),
+                             _stream(stream), ctypes.byref(h)))
+    return h.value
+
+
+def rlxpp_seed(gen, seeds, stream=None):
+    _check(_lib.rlxpp_seed(gen, _ptr(seeds), _stream(stream)))
+
+
+def rlxpp_skip(gen, n128, stream=None):
+    _check(_lib.rlxpp_skip(gen, _ptr(n128), _stream(stream)))
+
+
+def rlxpp_draw_u24(gen, out, count_each=0, counts=None, offsets=None, stream=None):
+    _check(_lib.rlxpp_draw_u24(gen, _ptr(counts), _ptr(offsets), count_each, _ptr(out), _stream(stream)))
+
+
+def rlxpp_draw_f64(gen, out, count_each=0, counts=None, offsets=None, stream=None):
+    _check(_lib.rlxpp_draw_f64(gen, _ptr(counts), _ptr(offsets), count_each, _ptr(out), _stream(stream)))
+
+
+def rlxpp_draw_f64_sum_hist(gen, count_each, sums, hist, stream=None):
+    _check(_lib.rlxpp_draw_f64_sum_hist(gen, count_each, _ptr(sums), _ptr(hist), _stream(stream)))
+
+
+def rlxpp_get_state(gen, dst, stream=None):
+    _check(_lib.rlxpp_get_state(gen, _ptr(dst), _stream(stream)))
+
+
+def rlxpp_set_state(gen, src, stream=None):
+    _check(_lib.rlxpp_set_state(gen, _ptr(src), _stream(stream)))
+
+
+def rlxpp_sync(gen, stream=None):
+    _check(_lib.rlxpp_sync(gen, _stream(stream)))
+
+
+def rlxpp_num_streams(gen):
+    return int(_lib.rlxpp_num_streams(gen))
+
+
+def rlxpp_last_error():
+    return _lib.rlxpp_last_error().decode(errors="replace")
+
+
+def rlxpp_destroy(gen):
+    _lib.rlxpp_destroy(gen)
+
+
+def rlxpp_test_multiply9x9(x, y, out, n, stream=None):
+    _check(_lib.rlxpp_test_multiply9x9(_ptr(x), _ptr(y), _ptr(out), n, _stream(stream)))
+
+
+def rlxpp_test_mod_m(inp, out, n, stream=None):
+    _check(_lib.rlxpp_test_mod_m(_ptr(inp), _ptr(out), n, _stream(stream)))
+
+
+def rlxpp_test_mul_mod(x, y, out, n, stream=None):
+    _check(_lib.rlxpp_test_mul_mod(_ptr(x), _ptr(y), _ptr(out), n, _stream(stream)))
+
+
+def rlxpp_test_to_ranlux(x, d, carry, n, stream=None):
+    _check(_lib.rlxpp_test_to_ranlux(_ptr(x), _ptr(d), _ptr(carry), n, _stream(stream)))
+
+
+def rlxpp_test_to_lcg(d, carry, x, n, stream=None):
+    _check(_lib.rlxpp_test_to_lcg(_ptr(d), _ptr(carry), _ptr(x), n, _stream(stream)))
+
+
+def rlxpp_test_f64_from48(v, out, n, stream=None):
+    _check(_lib.rlxpp_test_f64_from48(_ptr(v), _ptr(out), n, _stream(stream)))
+
+
+def rlxpp_luxury_multiplier(p):
+    """A = a^p mod m as a Python int (computed on the device)."""
+    out = (ctypes.c_uint64 * 9)()
+    _check(_lib.rlxpp_luxury_multiplier(p, out))
+    return sum(int(out[k]) << (64 * k) for k in range(9))
+
+
+class Generator:
+    """Owns one handle; methods forward to the functions above."""
+
+    def __init__(self, n_streams, levels, seeds, level_of_stream=None, stream=None):
+        self.n = n_streams
+        self.levels = list(levels)
+        self.handle = rlxpp_create(n_streams, self.levels, seeds, level_of_stream, stream)
+
+    def seed(self, seeds, stream=None):
+        rlxpp_seed(self.handle, seeds, stream)
+
+    def skip(self, n128, stream=None):
+        rlxpp_skip(self.handle, n128, stream)
+
+    def draw_u24(self, out, count_each=0, counts=None, offsets=None, stream=None):
+        rlxpp_draw_u24(self.handle, out, count_each, counts, offsets, stream)
+
+    def draw_f64(self, out, count_each=0, counts=None, offsets=None, stream=None):
+        rlxpp_draw_f64(self.handle, out, count_each, counts, offsets, stream)
+
+    def draw_f64_sum_hist(self, count_each, sums, hist, stream=None):
+        rlxpp_draw_f64_sum_hist(self.handle, count_each, sums, hist, stream)
+
+    def get_state(self, dst, stream=None):
+        rlxpp_get_state(self.handle, dst, stream)
+
+    def set_state(self, src, stream=None):
+        rlxpp_set_state(self.handle, src, stream)
+
+    def sync(self, stream=None):
+        rlxpp_sync(self.handle, stream)
+
+    def close(self):
+        if self.handle:
+            rlxpp_destroy(self.handle)
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,441 @@
+// Host side of the C ABI declared in include/rlxpp.h: argument checks, device memory
+// of the generator state, staging of host buffers, and the launches.
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "rlxpp_internal.h"
+
+using namespace rlxpp;
+
+struct rlxpp_gen {
+  int device = 0;
+  uint64_t n = 0;
+  uint32_t n_levels = 0;
+  uint32_t levels[RLXPP_MAX_LEVELS] = {};
+  Lux lux_host[RLXPP_MAX_LEVELS] = {};
+  uint64_t* D = nullptr;        // [9][n]
+  uint32_t* meta = nullptr;     // [n]
+  uint32_t* lux = nullptr;      // [n_levels][18]
+  uint32_t* table = nullptr;    // [n_levels][kTableLimbs]
+  uint32_t* level_p = nullptr;  // [n_levels]
+  int* status = nullptr;        // sticky device status
+  cudaStream_t copy_stream = nullptr;  // device-to-host copies of chunked host output
+  cudaEvent_t ev[4] = {};
+  StateView view() const { return StateView{D, meta, n, n, lux, table, status}; }
+};
+
+namespace {
+
+thread_local std::string g_last_error;
+
+rlxpp_status fail(rlxpp_status code, const std::string& msg) {
+  g_last_error = msg;
+  return code;
+}
+
+#define RLX_CUDA(expr)                                                                  \
+  do {                                                                                  \
+    cudaError_t e_ = (expr);                                                            \
+    if (e_ != cudaSuccess) {                                                            \
+      return fail(e_ == cudaErrorMemoryAllocation ? RLXPP_ERR_NOMEM : RLXPP_ERR_CUDA,   \
+                  std::string(#expr) + ": " + cudaGetErrorString(e_));                  \
+    }                                                                                   \
+  } while (0)
+
+cudaStream_t as_stream(void* s) { return reinterpret_cast<cudaStream_t>(s); }
+
+// true when the device can dereference p directly (device or managed memory)
+bool on_device(const void* p) {
+  cudaPointerAttributes attr;
+  if (cudaPointerGetAttributes(&attr, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return attr.type == cudaMemoryTypeDevice || attr.type == cudaMemoryTypeManaged;
+}
+
+// A device copy of a host input array, or the pointer itself if already on the device.
+// The copy completes before this returns, so the caller's host buffer may be reused.
+struct Staged {
+  void* dev = nullptr;
+  bool owned = false;
+  cudaStream_t st = nullptr;
+  ~Staged() {
+    if (owned && dev) cudaFreeAsync(dev, st);
+  }
+};
+
+rlxpp_status stage_in(const void* src, size_t bytes, cudaStream_t st, Staged& out) {
+  out.st = st;
+  if (src == nullptr || bytes == 0 || on_device(src)) {
+    out.dev = const_cast<void*>(src);
+    return RLXPP_OK;
+  }
+  RLX_CUDA(cudaMallocAsync(&out.dev, bytes, st));
+  out.owned = true;
+  RLX_CUDA(cudaMemcpyAsync(out.dev, src, bytes, cudaMemcpyHostToDevice, st));
+  RLX_CUDA(cudaStreamSynchronize(st));
+  return RLXPP_OK;
+}
+
+rlxpp_status check_gen(const rlxpp_gen* g) {
+  if (!g) return fail(RLXPP_ERR_INVALID, "null generator handle");
+  RLX_CUDA(cudaSetDevice(g->device));
+  return RLXPP_OK;
+}
+
+rlxpp_status setup_levels(rlxpp_gen* g, cudaStream_t st) {
+  for (uint32_t l = 0; l < g->n_levels; ++l) {
+    cudaError_t e = launch_level_setup(g->levels[l], g->lux + (size_t)l * 18,
+                                       g->table + (size_t)l * kTableLimbs, st);
+    if (e != cudaSuccess) return fail(RLXPP_ERR_CUDA, std::string("level setup: ") + cudaGetErrorString(e));
+  }
+  RLX_CUDA(cudaMemcpyAsync(g->lux_host, g->lux, sizeof(uint32_t) * 18 * g->n_levels,
+                           cudaMemcpyDeviceToHost, st));
+  RLX_CUDA(cudaStreamSynchronize(st));
+  return RLXPP_OK;
+}
+
+void free_gen(rlxpp_gen* g) {
+  if (!g) return;
+  cudaSetDevice(g->device);
+  cudaDeviceSynchronize();
+  cudaFree(g->D);
+  cudaFree(g->meta);
+  cudaFree(g->lux);
+  cudaFree(g->table);
+  cudaFree(g->level_p);
+  cudaFree(g->status);
+  for (auto& e : g->ev)
+    if (e) cudaEventDestroy(e);
+  if (g->copy_stream) cudaStreamDestroy(g->copy_stream);
+  delete g;
+}
+
+DrawArgs make_args(const rlxpp_gen* g) {
+  DrawArgs a{};
+  a.s = g->view();
+  a.uniform = g->n_levels == 1;
+  a.A = g->lux_host[0];
+  return a;
+}
+
+constexpr size_t kChunkBytes = size_t(256) << 20;  // device staging per chunk of host output
+
+// Draw of kind (u24 / f64) into out; host outputs go through device chunks that are
+// copied back on a second stream while the next chunk computes.
+rlxpp_status draw_common(rlxpp_gen* g, int kind, const int64_t* counts, const int64_t* offsets,
+                         int64_t count_each, void* out, size_t elem, cudaStream_t st) {
+  if (rlxpp_status s = check_gen(g)) return s;
+  if (g->n == 0) return RLXPP_OK;
+  if (!counts && count_each < 0) return fail(RLXPP_ERR_INVALID, "count_each must be >= 0");
+  if (counts && !offsets) return fail(RLXPP_ERR_INVALID, "offsets required with counts");
+  if (!out) {
+    if (!counts && count_each == 0) return RLXPP_OK;
+    return fail(RLXPP_ERR_INVALID, "null output");
+  }
+  Staged sc, so;
+  if (rlxpp_status s = stage_in(counts, sizeof(int64_t) * g->n, st, sc)) return s;
+  if (rlxpp_status s = stage_in(offsets, sizeof(int64_t) * g->n, st, so)) return s;
+  DrawArgs a = make_args(g);
+  a.counts = static_cast<const int64_t*>(sc.dev);
+  a.offsets = static_cast<const int64_t*>(so.dev);
+  a.count_each = count_each;
+  if (on_device(out)) {
+    a.out = out;
+    cudaError_t e = launch_draw(kind, a, st);
+    if (e != cudaSuccess) return fail(RLXPP_ERR_CUDA, std::string("draw: ") + cudaGetErrorString(e));
+    return RLXPP_OK;
+  }
+  if (counts) {
+    // host output with per-stream ranges: one device image of the whole output
+    std::vector<int64_t> hc(g->n), ho(g->n);
+    RLX_CUDA(cudaMemcpyAsync(hc.data(), a.counts, sizeof(int64_t) * g->n, cudaMemcpyDeviceToHost, st));
+    RLX_CUDA(cudaMemcpyAsync(ho.data(), a.offsets, sizeof(int64_t) * g->n, cudaMemcpyDeviceToHost, st));
+    RLX_CUDA(cudaStreamSynchronize(st));
+    int64_t total = 0;
+    for (uint64_t i = 0; i < g->n; ++i) {
+      if (hc[i] < 0 || ho[i] < 0) return fail(RLXPP_ERR_INVALID, "negative count or offset");
+      if (hc[i] > 0) total = std::max(total, ho[i] + hc[i]);
+    }
+    if (total == 0) return RLXPP_OK;
+    void* dev = nullptr;
+    RLX_CUDA(cudaMallocAsync(&dev, (size_t)total * elem, st));
+    // keep untouched elements of the caller's buffer: start from its contents
+    cudaError_t e = cudaMemcpyAsync(dev, out, (size_t)total * elem, cudaMemcpyHostToDevice, st);
+    a.out = dev;
+    if (e == cudaSuccess) e = launch_draw(kind, a, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(out, dev, (size_t)total * elem, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    cudaFreeAsync(dev, st);
+    if (e != cudaSuccess) return fail(RLXPP_ERR_CUDA, std::string("draw to host: ") + cudaGetErrorString(e));
+    return RLXPP_OK;
+  }
+  if (count_each == 0) return RLXPP_OK;
+  // uniform counts: chunks of whole streams, double-buffered
+  const size_t per_stream = (size_t)count_each * elem;
+  uint64_t chunk = std::max<uint64_t>(1, kChunkBytes / per_stream);
+  chunk = std::min<uint64_t>(chunk, g->n);
+  void* buf[2] = {nullptr, nullptr};
+  RLX_CUDA(cudaMallocAsync(&buf[0], chunk * per_stream, st));
+  cudaError_t e = cudaMallocAsync(&buf[1], chunk * per_stream, st);
+  int k = 0;
+  for (uint64_t s0 = 0; e == cudaSuccess && s0 < g->n; s0 += chunk, ++k) {
+    const uint64_t s1 = std::min<uint64_t>(g->n, s0 + chunk);
+    const int b = k & 1;
+    if (k >= 2) e = cudaStreamWaitEvent(st, g->ev[2 + b], 0);  // buffer b copied out
+    if (e != cudaSuccess) break;
+    DrawArgs c = a;
+    c.s.D = g->D + s0;  // a view of streams s0..s1-1 (plane stride stays n)
+    c.s.meta = g->meta + s0;
+    c.s.n = s1 - s0;
+    c.out = buf[b];
+    e = launch_draw(kind, c, st);
+    if (e == cudaSuccess) e = cudaEventRecord(g->ev[b], st);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(g->copy_stream, g->ev[b], 0);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(static_cast<char*>(out) + s0 * per_stream, buf[b], (s1 - s0) * per_stream,
+                          cudaMemcpyDeviceToHost, g->copy_stream);
+    if (e == cudaSuccess) e = cudaEventRecord(g->ev[2 + b], g->copy_stream);
+  }
+  cudaError_t e2 = cudaStreamSynchronize(g->copy_stream);
+  if (e == cudaSuccess) e = e2;
+  cudaStreamWaitEvent(st, g->ev[2], 0);
+  cudaStreamWaitEvent(st, g->ev[3], 0);
+  cudaFreeAsync(buf[0], st);
+  if (buf[1]) cudaFreeAsync(buf[1], st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return fail(RLXPP_ERR_CUDA, std::string("draw to host: ") + cudaGetErrorString(e));
+  return RLXPP_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+rlxpp_status rlxpp_create(uint64_t n_streams, const uint32_t* levels, uint32_t n_levels,
+                          const uint8_t* level_of_stream, const uint64_t* seeds,
+                          void* cuda_stream, rlxpp_gen** out) {
+  if (!out) return fail(RLXPP_ERR_INVALID, "null output handle pointer");
+  *out = nullptr;
+  if (!levels || n_levels == 0 || n_levels > RLXPP_MAX_LEVELS)
+    return fail(RLXPP_ERR_INVALID, "need 1..RLXPP_MAX_LEVELS luxury levels");
+  for (uint32_t l = 0; l < n_levels; ++l)
+    if (levels[l] == 0) return fail(RLXPP_ERR_INVALID, "luxury level must be >= 1");
+  if (n_streams > 0 && !seeds) return fail(RLXPP_ERR_INVALID, "null seeds");
+  if (n_streams > (uint64_t(1) << 40)) return fail(RLXPP_ERR_INVALID, "too many streams");
+  cudaStream_t st = as_stream(cuda_stream);
+  rlxpp_gen* g = new rlxpp_gen();
+  auto bail = [&](rlxpp_status s) {
+    free_gen(g);
+    return s;
+  };
+  if (cudaGetDevice(&g->device) != cudaSuccess) return bail(fail(RLXPP_ERR_CUDA, "no CUDA device"));
+  g->n = n_streams;
+  g->n_levels = n_levels;
+  std::memcpy(g->levels, levels, sizeof(uint32_t) * n_levels);
+  const size_t nn = std::max<uint64_t>(n_streams, 1);
+  cudaError_t e = cudaMalloc(&g->D, sizeof(uint64_t) * 9 * nn);
+  if (e == cudaSuccess) e = cudaMalloc(&g->meta, sizeof(uint32_t) * nn);
+  if (e == cudaSuccess) e = cudaMalloc(&g->lux, sizeof(uint32_t) * 18 * n_levels);
+  if (e == cudaSuccess) e = cudaMalloc(&g->table, sizeof(uint32_t) * kTableLimbs * n_levels);
+  if (e == cudaSuccess) e = cudaMalloc(&g->level_p, sizeof(uint32_t) * n_levels);
+  if (e == cudaSuccess) e = cudaMalloc(&g->status, sizeof(int));
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&g->copy_stream, cudaStreamNonBlocking);
+  for (auto& ev : g->ev)
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+  if (e != cudaSuccess)
+    return bail(fail(e == cudaErrorMemoryAllocation ? RLXPP_ERR_NOMEM : RLXPP_ERR_CUDA,
+                     std::string("create: ") + cudaGetErrorString(e)));
+  e = cudaMemsetAsync(g->status, 0, sizeof(int), st);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(g->level_p, g->levels, sizeof(uint32_t) * n_levels, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(g->D, 0, sizeof(uint64_t) * 9 * nn, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(g->meta, 0, sizeof(uint32_t) * nn, st);
+  if (e != cudaSuccess) return bail(fail(RLXPP_ERR_CUDA, std::string("create: ") + cudaGetErrorString(e)));
+  if (rlxpp_status s = setup_levels(g, st)) return bail(s);
+  if (n_streams > 0) {
+    Staged ss, sl;
+    if (rlxpp_status s = stage_in(seeds, sizeof(uint64_t) * n_streams, st, ss)) return bail(s);
+    if (rlxpp_status s = stage_in(level_of_stream, n_streams, st, sl)) return bail(s);
+    e = launch_seed(g->view(), static_cast<const uint64_t*>(ss.dev), static_cast<const uint8_t*>(sl.dev),
+                    n_levels, false, st);
+    if (e != cudaSuccess) return bail(fail(RLXPP_ERR_CUDA, std::string("seed: ") + cudaGetErrorString(e)));
+  }
+  *out = g;
+  return RLXPP_OK;
+}
+
+rlxpp_status rlxpp_seed(rlxpp_gen* g, const uint64_t* seeds, void* cuda_stream) {
+  if (rlxpp_status s = check_gen(g)) return s;
+  if (g->n == 0) return RLXPP_OK;
+  if (!seeds) return fail(RLXPP_ERR_INVALID, "null seeds");
+  cudaStream_t st = as_stream(cuda_stream);
+  Staged ss;
+  if (rlxpp_status s = stage_in(seeds, sizeof(uint64_t) * g->n, st, ss)) return s;
+  cudaError_t e = launch_seed(g->view(), static_cast<const uint64_t*>(ss.dev), nullptr, g->n_levels,
+                              true, st);
+  if (e != cudaSuccess) return fail(RLXPP_ERR_CUDA, std::string("seed: ") + cudaGetErrorString(e));
+  return RLXPP_OK;
+}
+
+rlxpp_status rlxpp_skip(rlxpp_gen* g, const uint64_t* n128, void* cuda_stream) {
+  if (rlxpp_status s = check_gen(g)) return s;
+  if (g->n == 0) return RLXPP_OK;
+  if (!n128) return fail(RLXPP_ERR_INVALID, "null skip distances");
+  cudaStream_t st = as_stream(cuda_stream);
+  Staged sn;
+  if (rlxpp_status s = stage_in(n128, sizeof(uint64_t) * 2 * g->n, st, sn)) return s;
+  cudaError_t e = launch_skip(g->view(), static_cast<const uint64_t*>(sn.dev), st);
+  if (e != cudaSuccess) return fail(RLXPP_ERR_CUDA, std::string("skip: ") + cudaGetErrorString(e));
+  return RLXPP_OK;
+}
+
+rlxpp_status rlxpp_draw_u24(rlxpp_gen* g, const int64_t* counts, const int64_t* offsets,
+                            int64_t count_each, uint32_t* out, void* cuda_stream) {
+  return draw_common(g, kDrawU24, counts, offsets, count_each, out, sizeof(uint32_t),
+                     as_stream(cuda_stream));
+}
+
+rlxpp_status rlxpp_draw_f64(rlxpp_gen* g, const int64_t* counts, const int64_t* offsets,
+                            int64_t count_each, double* out, void* cuda_stream) {
+  return draw_common(g, kDrawF64, counts, offsets, count_each, out, sizeof(double),
+                     as_stream(cuda_stream));
+}
+
+rlxpp_status rlxpp_draw_f64_sum_hist(rlxpp_gen* g, int64_t count_each, uint64_t* sums,
+                                     uint64_t* hist, void* cuda_stream) {
+  if (rlxpp_status s = check_gen(g)) return s;
+  if (count_each < 0) return fail(RLXPP_ERR_INVALID, "count_each must be >= 0");
+  if (!hist) return fail(RLXPP_ERR_INVALID, "null histogram");
+  if (!on_device(hist) || (sums && !on_device(sums)))
+    return fail(RLXPP_ERR_INVALID, "sums and hist must be device memory");
+  if (g->n == 0) return RLXPP_OK;
+  cudaStream_t st = as_stream(cuda_stream);
+  DrawArgs a = make_args(g);
+  a.out = sums;
+  a.hist = reinterpret_cast<unsigned long long*>(hist);
+  // per-warp 32-bit shared-memory bins: at most 2^26 values per lane and launch
+  const int64_t kMaxPerLaunch = int64_t(1) << 26;
+  int64_t done = 0;
+  do {
+    a.count_each = std::min(count_each - done, kMaxPerLaunch);
+    a.accumulate_sums = done > 0;
+    cudaError_t e = launch_draw(kDrawSumHist, a, st);
+    if (e != cudaSuccess) return fail(RLXPP_ERR_CUDA, std::string("sum/hist: ") + cudaGetErrorString(e));
+    done += a.count_each;
+  } while (done < count_each);
+  return RLXPP_OK;
+}
+
+rlxpp_status rlxpp_get_state(const rlxpp_gen* g, rlxpp_state* dst, void* cuda_stream) {
+  if (rlxpp_status s = check_gen(g)) return s;
+  if (g->n == 0) return RLXPP_OK;
+  if (!dst) return fail(RLXPP_ERR_INVALID, "null destination");
+  cudaStream_t st = as_stream(cuda_stream);
+  const size_t bytes = sizeof(rlxpp_state) * g->n;
+  if (on_device(dst)) {
+    cudaError_t e = launch_export(g->view(), g->level_p, dst, st);
+    if (e != cudaSuccess) return fail(RLXPP_ERR_CUDA, std::string("export: ") + cudaGetErrorString(e));
+    return RLXPP_OK;
+  }
+  void* dev = nullptr;
+  RLX_CUDA(cudaMallocAsync(&dev, bytes, st));
+  cudaError_t e = launch_export(g->view(), g->level_p, static_cast<rlxpp_state*>(dev), st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(dst, dev, bytes, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  cudaFreeAsync(dev, st);
+  if (e != cudaSuccess) return fail(RLXPP_ERR_CUDA, std::string("export: ") + cudaGetErrorString(e));
+  return RLXPP_OK;
+}
+
+rlxpp_status rlxpp_set_state(rlxpp_gen* g, const rlxpp_state* src, void* cuda_stream) {
+  if (rlxpp_status s = check_gen(g)) return s;
+  if (g->n == 0) return RLXPP_OK;
+  if (!src) return fail(RLXPP_ERR_INVALID, "null source");
+  cudaStream_t st = as_stream(cuda_stream);
+  Staged ss;
+  if (rlxpp_status s = stage_in(src, sizeof(rlxpp_state) * g->n, st, ss)) return s;
+  cudaError_t e = launch_import(g->view(), g->level_p, g->n_levels,
+                                static_cast<const rlxpp_state*>(ss.dev), st);
+  if (e != cudaSuccess) return fail(RLXPP_ERR_CUDA, std::string("import: ") + cudaGetErrorString(e));
+  return RLXPP_OK;
+}
+
+rlxpp_status rlxpp_sync(rlxpp_gen* g, void* cuda_stream) {
+  if (rlxpp_status s = check_gen(g)) return s;
+  cudaStream_t st = as_stream(cuda_stream);
+  int h = 0;
+  RLX_CUDA(cudaMemcpyAsync(&h, g->status, sizeof(int), cudaMemcpyDeviceToHost, st));
+  RLX_CUDA(cudaMemsetAsync(g->status, 0, sizeof(int), st));
+  RLX_CUDA(cudaStreamSynchronize(st));
+  if (h == RLXPP_ERR_INVALID) return fail(RLXPP_ERR_INVALID, "a kernel rejected its input");
+  if (h == RLXPP_ERR_TIMEOUT) return fail(RLXPP_ERR_TIMEOUT, "a bounded device wait gave up");
+  if (h != 0) return fail(RLXPP_ERR_CUDA, "unknown device status");
+  return RLXPP_OK;
+}
+
+uint64_t rlxpp_num_streams(const rlxpp_gen* g) { return g ? g->n : 0; }
+
+const char* rlxpp_last_error(void) { return g_last_error.c_str(); }
+
+void rlxpp_destroy(rlxpp_gen* g) { free_gen(g); }
+
+// ---- unit-test entry points --------------------------------------------------------
+static rlxpp_status run_test(int op, const void* x, const void* y, void* out, void* carry,
+                             uint64_t n, void* cuda_stream) {
+  if (n == 0) return RLXPP_OK;
+  if (!x || !out) return fail(RLXPP_ERR_INVALID, "null test buffer");
+  cudaError_t e = launch_test(op, static_cast<const uint64_t*>(x), static_cast<const uint64_t*>(y),
+                              static_cast<uint64_t*>(out), static_cast<uint32_t*>(carry), n,
+                              as_stream(cuda_stream));
+  if (e != cudaSuccess) return fail(RLXPP_ERR_CUDA, std::string("test kernel: ") + cudaGetErrorString(e));
+  return RLXPP_OK;
+}
+
+rlxpp_status rlxpp_test_multiply9x9(const uint64_t* x, const uint64_t* y, uint64_t* out, uint64_t n,
+                                    void* cuda_stream) {
+  if (n && !y) return fail(RLXPP_ERR_INVALID, "null y");
+  return run_test(kTestMultiply, x, y, out, nullptr, n, cuda_stream);
+}
+rlxpp_status rlxpp_test_mod_m(const uint64_t* in, uint64_t* out, uint64_t n, void* cuda_stream) {
+  return run_test(kTestModM, in, nullptr, out, nullptr, n, cuda_stream);
+}
+rlxpp_status rlxpp_test_mul_mod(const uint64_t* x, const uint64_t* y, uint64_t* out, uint64_t n,
+                                void* cuda_stream) {
+  if (n && !y) return fail(RLXPP_ERR_INVALID, "null y");
+  return run_test(kTestMulMod, x, y, out, nullptr, n, cuda_stream);
+}
+rlxpp_status rlxpp_test_to_ranlux(const uint64_t* x, uint64_t* d, uint32_t* carry, uint64_t n,
+                                  void* cuda_stream) {
+  if (n && !carry) return fail(RLXPP_ERR_INVALID, "null carry");
+  return run_test(kTestToRanlux, x, nullptr, d, carry, n, cuda_stream);
+}
+rlxpp_status rlxpp_test_to_lcg(const uint64_t* d, const uint32_t* carry, uint64_t* x, uint64_t n,
+                               void* cuda_stream) {
+  if (n && !carry) return fail(RLXPP_ERR_INVALID, "null carry");
+  return run_test(kTestToLcg, d, nullptr, x, const_cast<uint32_t*>(carry), n, cuda_stream);
+}
+rlxpp_status rlxpp_test_f64_from48(const uint64_t* v, uint64_t* out, uint64_t n, void* cuda_stream) {
+  return run_test(kTestF64, v, nullptr, out, nullptr, n, cuda_stream);
+}
+
+rlxpp_status rlxpp_luxury_multiplier(uint32_t p, uint64_t* out9) {
+  if (p == 0 || !out9) return fail(RLXPP_ERR_INVALID, "need p >= 1 and an output");
+  uint32_t *lux = nullptr, *table = nullptr;
+  RLX_CUDA(cudaMalloc(&lux, sizeof(uint32_t) * 18));
+  cudaError_t e = cudaMalloc(&table, sizeof(uint32_t) * kTableLimbs);
+  if (e == cudaSuccess) e = launch_level_setup(p, lux, table, nullptr);
+  uint32_t h[18] = {};
+  if (e == cudaSuccess) e = cudaMemcpy(h, lux, sizeof h, cudaMemcpyDeviceToHost);
+  cudaFree(lux);
+  cudaFree(table);
+  if (e != cudaSuccess) return fail(RLXPP_ERR_CUDA, std::string("luxury multiplier: ") + cudaGetErrorString(e));
+  for (int k = 0; k < 9; ++k) out9[k] = ((uint64_t)h[2 * k + 1] << 32) | h[2 * k];
+  return RLXPP_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,295 @@
+// 576-bit modular arithmetic for RANLUX++ on sm_103a: the LCG advance X <- A X mod m
+// with m = 2^576 - 2^240 + 1 (Sec. 2.2 of Hahnfeld & Moneta, arXiv 2106.02504), the
+// 576 x 576 -> 1152-bit product (Sec. 2.1), the reduction mod m (Sec. 2.2) and the
+// conversion between the LCG state and the 24 RANLUX numbers (Sec. 2.3).
+//
+// Numbers are little-endian arrays of 32-bit limbs held in registers: 18 limbs for a
+// 576-bit value, 36 for a product.  Carry chains are written with PTX add.cc/addc
+// (the GPU counterpart of the branch-free carry propagation of Sec. 3.4) and the limb
+// products with mad.wide.u32 (32 x 32 -> 64 bits, the device has no 128-bit integer
+// type; Sec. 4.2).  Every loop has a compile-time trip count and is fully unrolled
+// (Sec. 3.1).
+#pragma once
+#include <cstdint>
+
+namespace rlxpp {
+
+constexpr int kLimbs = 18;        // 576 / 32
+constexpr int kWords = 24;        // RANLUX numbers per block
+constexpr int kDoubles = 12;      // 48-bit doubles per block
+
+// ---------------------------------------------------------------------------------
+// carry-chain primitives (PTX condition-code chains; kept in program order by volatile)
+// ---------------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t add_cc(uint32_t a, uint32_t b) {
+  uint32_t r;
+  asm volatile("add.cc.u32 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(b));
+  return r;
+}
+__device__ __forceinline__ uint32_t addc_cc(uint32_t a, uint32_t b) {
+  uint32_t r;
+  asm volatile("addc.cc.u32 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(b));
+  return r;
+}
+__device__ __forceinline__ uint32_t addc(uint32_t a, uint32_t b) {
+  uint32_t r;
+  asm volatile("addc.u32 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(b));
+  return r;
+}
+__device__ __forceinline__ uint32_t sub_cc(uint32_t a, uint32_t b) {
+  uint32_t r;
+  asm volatile("sub.cc.u32 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(b));
+  return r;
+}
+__device__ __forceinline__ uint32_t subc_cc(uint32_t a, uint32_t b) {
+  uint32_t r;
+  asm volatile("subc.cc.u32 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(b));
+  return r;
+}
+__device__ __forceinline__ uint32_t subc(uint32_t a, uint32_t b) {
+  uint32_t r;
+  asm volatile("subc.u32 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(b));
+  return r;
+}
+__device__ __forceinline__ uint64_t mad_wide(uint32_t a, uint32_t b, uint64_t c) {
+  uint64_t r;
+  asm("mad.wide.u32 %0, %1, %2, %3;" : "=l"(r) : "r"(a), "r"(b), "l"(c));
+  return r;
+}
+__device__ __forceinline__ uint32_t lo32(uint64_t v) { return (uint32_t)v; }
+__device__ __forceinline__ uint32_t hi32(uint64_t v) { return (uint32_t)(v >> 32); }
+// (hi:lo) >> s for 0 < s < 32
+__device__ __forceinline__ uint32_t shr_pair(uint32_t lo, uint32_t hi, int s) {
+  return __funnelshift_r(lo, hi, s);
+}
+
+// ---------------------------------------------------------------------------------
+// Sec. 2.1: p = a * b (576 x 576 -> 1152 bits), operand scanning.
+// Row i adds a_i * b shifted by i limbs: the 18 products a_i b_j + p_{i+j} fit in 64
+// bits each ((2^32-1)^2 + 2^32-1 < 2^64) and are independent; one carry chain then adds
+// the high half of product j-1 to the low half of product j.  After row i the partial
+// product (a mod 2^(32(i+1))) b fits in limbs 0..i+18, so no carry leaves limb i+18.
+// A is passed through an accessor so that a constant multiplier can stay in the
+// constant bank (kernel parameters) instead of registers.
+// ---------------------------------------------------------------------------------
+template <class AFn>
+__device__ __forceinline__ void multiply9x9(AFn a, const uint32_t b[kLimbs], uint32_t p[2 * kLimbs]) {
+#pragma unroll
+  for (int k = 0; k < 2 * kLimbs; ++k) p[k] = 0;
+#pragma unroll
+  for (int i = 0; i < kLimbs; ++i) {
+    const uint32_t ai = a(i);
+    uint64_t t[kLimbs];
+#pragma unroll
+    for (int j = 0; j < kLimbs; ++j) t[j] = mad_wide(ai, b[j], (uint64_t)p[i + j]);
+    p[i] = lo32(t[0]);
+    p[i + 1] = add_cc(lo32(t[1]), hi32(t[0]));
+#pragma unroll
+    for (int j = 2; j < kLimbs; ++j) p[i + j] = addc_cc(lo32(t[j]), hi32(t[j - 1]));
+    p[i + kLimbs] = addc(hi32(t[kLimbs - 1]), 0u);
+  }
+}
+
+// ---------------------------------------------------------------------------------
+// Sec. 2.2: r = p mod m, m = 2^576 - 2^240 + 1, using only additions, subtractions and
+// shifts, with the final correction that puts the result in [0, m).
+//
+// With 2^576 = 2^240 - 1 (mod m), write p = H 2^576 + L and H = H1 2^336 + H0:
+//   p = L + H 2^240 - H = L + H0 2^240 + H1 2^576 - H = L + (H0 + H1) 2^240 - H - H1.
+// Adding 2m keeps every intermediate non-negative:
+//   R = L + S 2^240 + (2m - V),  S = H0 + H1 < 2^337,  V = H + H1 < 2m,
+// so 0 <= R < 5 2^576.  Folding the top limb t (0..4) with 2^576 = 2^240 - 1 leaves at
+// most one more 2^576 overflow c, and when c = 1 the low part is below 2^243, so the
+// second fold only touches limbs 0..7.  The result is then below 2^576 and at most one
+// subtraction of m puts it in [0, m): r >= m exactly when r + (2^240 - 1) >= 2^576.
+// ---------------------------------------------------------------------------------
+__device__ __forceinline__ void mod_m(const uint32_t p[2 * kLimbs], uint32_t r[kLimbs]) {
+  const uint32_t* L = p;
+  const uint32_t* H = p + kLimbs;
+  // H1 = H >> 336 (240 bits, limbs 0..7; limb 7 holds 16 bits)
+  uint32_t H1[8];
+#pragma unroll
+  for (int k = 0; k < 7; ++k) H1[k] = shr_pair(H[10 + k], H[11 + k], 16);
+  H1[7] = H[17] >> 16;
+  // S = H0 + H1, H0 = H mod 2^336 (limbs 0..9 and the low 16 bits of limb 10)
+  uint32_t S[11];
+  S[0] = add_cc(H[0], H1[0]);
+#pragma unroll
+  for (int k = 1; k < 8; ++k) S[k] = addc_cc(H[k], H1[k]);
+  S[8] = addc_cc(H[8], 0u);
+  S[9] = addc_cc(H[9], 0u);
+  S[10] = addc(H[10] & 0xFFFFu, 0u);
+  // V = H + H1 (19 limbs, top limb 0 or 1)
+  uint32_t V[kLimbs + 1];
+  V[0] = add_cc(H[0], H1[0]);
+#pragma unroll
+  for (int k = 1; k < 8; ++k) V[k] = addc_cc(H[k], H1[k]);
+#pragma unroll
+  for (int k = 8; k < kLimbs; ++k) V[k] = addc_cc(H[k], 0u);
+  V[kLimbs] = addc(0u, 0u);
+  // W = 2m - V; 2m = 2^577 - 2^241 + 2: limb 0 = 2, limb 7 = 0xFFFE0000,
+  // limbs 8..17 = 0xFFFFFFFF, limb 18 = 1, other limbs 0.
+  uint32_t W[kLimbs + 1];
+  W[0] = sub_cc(2u, V[0]);
+#pragma unroll
+  for (int k = 1; k < 7; ++k) W[k] = subc_cc(0u, V[k]);
+  W[7] = subc_cc(0xFFFE0000u, V[7]);
+#pragma unroll
+  for (int k = 8; k < kLimbs; ++k) W[k] = subc_cc(0xFFFFFFFFu, V[k]);
+  W[kLimbs] = subc(1u, V[kLimbs]);
+  // U = L + (S << 240); 240 = 7 limbs + 16 bits, S << 240 covers limbs 7..18
+  uint32_t Sh[12];
+  Sh[0] = S[0] << 16;
+#pragma unroll
+  for (int k = 1; k < 11; ++k) Sh[k] = __funnelshift_l(S[k - 1], S[k], 16);
+  Sh[11] = S[10] >> 16;
+  uint32_t R[kLimbs + 1];
+  // R = L + W first (limbs 0..6 of the shifted S are zero), then add the shifted S.
+  R[0] = add_cc(L[0], W[0]);
+#pragma unroll
+  for (int k = 1; k < kLimbs; ++k) R[k] = addc_cc(L[k], W[k]);
+  R[kLimbs] = addc(W[kLimbs], 0u);
+  R[7] = add_cc(R[7], Sh[0]);
+#pragma unroll
+  for (int k = 8; k < kLimbs; ++k) R[k] = addc_cc(R[k], Sh[k - 7]);
+  R[kLimbs] = addc(R[kLimbs], Sh[11]);
+  // fold 1: R = R[0..17] + t (2^240 - 1), t = R[18] in 0..4.
+  // t (2^240 - 1) = t 2^240 - t: limbs 0..6 of (2^240 - t) and limb 7 = (t - 1) 2^16 + 0xFFFF
+  // for t >= 1; all zero for t = 0.
+  const uint32_t t = R[kLimbs];
+  const uint32_t nz = t ? 0xFFFFFFFFu : 0u;
+  uint32_t c;
+  r[0] = add_cc(R[0], (0u - t));
+#pragma unroll
+  for (int k = 1; k < 7; ++k) r[k] = addc_cc(R[k], nz);
+  r[7] = addc_cc(R[7], ((t - 1u) << 16 | 0xFFFFu) & nz);
+#pragma unroll
+  for (int k = 8; k < kLimbs; ++k) r[k] = addc_cc(R[k], 0u);
+  c = addc(0u, 0u);
+  // fold 2: c (2^240 - 1), c in {0, 1}; when c = 1 the value is below 2^243.
+  const uint32_t cm = 0u - c;
+  r[0] = add_cc(r[0], cm);
+#pragma unroll
+  for (int k = 1; k < 7; ++k) r[k] = addc_cc(r[k], cm);
+  r[7] = addc(r[7], cm & 0xFFFFu);
+  // final correction: r >= m  <=>  r + (2^240 - 1) >= 2^576; then r - m = that sum mod 2^576
+  uint32_t e[kLimbs];
+  e[0] = add_cc(r[0], 0xFFFFFFFFu);
+#pragma unroll
+  for (int k = 1; k < 7; ++k) e[k] = addc_cc(r[k], 0xFFFFFFFFu);
+  e[7] = addc_cc(r[7], 0xFFFFu);
+#pragma unroll
+  for (int k = 8; k < kLimbs; ++k) e[k] = addc_cc(r[k], 0u);
+  const uint32_t ge = addc(0u, 0u);
+#pragma unroll
+  for (int k = 0; k < kLimbs; ++k) r[k] = ge ? e[k] : r[k];
+}
+
+// ---------------------------------------------------------------------------------
+// Sec. 2.3: LCG state X (in [0, m)) -> the 24 RANLUX numbers D = floor(2^576 X / m).
+// 2^576 = m + 2^240 - 1 gives D = X + q with q = floor(T / m), T = X (2^240 - 1) < 2^816.
+// Since m < 2^576 and T / m - T / 2^576 < 2^-96, q is q0 = floor(T / 2^576) or q0 + 1,
+// and q = q0 + 1 exactly when (q0 + 1) m <= T, i.e. when
+//   T_lo + (q0 + 1)(2^240 - 1) >= 2^576,  T_lo = T mod 2^576,
+// using (q0 + 1) m = (q0 + 1) 2^576 - (q0 + 1)(2^240 - 1).
+// ---------------------------------------------------------------------------------
+__device__ __forceinline__ void to_ranlux(const uint32_t X[kLimbs], uint32_t D[kLimbs]) {
+  // T = (X << 240) - X, 26 limbs
+  uint32_t T[26];
+  T[0] = sub_cc(0u, X[0]);
+#pragma unroll
+  for (int k = 1; k < 7; ++k) T[k] = subc_cc(0u, X[k]);
+  T[7] = subc_cc(X[0] << 16, X[7]);
+#pragma unroll
+  for (int k = 8; k < kLimbs; ++k) T[k] = subc_cc(__funnelshift_l(X[k - 8], X[k - 7], 16), X[k]);
+#pragma unroll
+  for (int k = kLimbs; k < 25; ++k) T[k] = subc_cc(__funnelshift_l(X[k - 8], X[k - 7], 16), 0u);
+  T[25] = subc(X[17] >> 16, 0u);
+  // q1 = q0 + 1 (q0 = T >> 576, limbs 18..25, below 2^240)
+  uint32_t q1[8];
+  q1[0] = add_cc(T[18], 1u);
+#pragma unroll
+  for (int k = 1; k < 8; ++k) q1[k] = addc_cc(T[18 + k], 0u);
+  // F = T_lo - q1 + (q1 << 240): compare against 2^576 through the net carry
+  uint32_t F[kLimbs];
+  F[0] = sub_cc(T[0], q1[0]);
+#pragma unroll
+  for (int k = 1; k < 8; ++k) F[k] = subc_cc(T[k], q1[k]);
+#pragma unroll
+  for (int k = 8; k < kLimbs; ++k) F[k] = subc_cc(T[k], 0u);
+  const uint32_t borrow = subc(0u, 0u);  // 0 or 0xFFFFFFFF
+  // q1 << 240 occupies limbs 7..15 (q1 <= 2^240): limb 7 + k holds the top 16 bits of
+  // q1[k-1] and the low 16 bits of q1[k], limb 15 the top 16 bits of q1[7].
+  uint32_t dummy = add_cc(F[7], q1[0] << 16);
+  (void)dummy;
+#pragma unroll
+  for (int k = 8; k < 15; ++k) dummy = addc_cc(F[k], __funnelshift_l(q1[k - 8], q1[k - 7], 16));
+  dummy = addc_cc(F[15], q1[7] >> 16);
+  dummy = addc_cc(F[16], 0u);
+  dummy = addc_cc(F[17], 0u);
+  const uint32_t carry = addc(0u, 0u);
+  // overflow of F past 2^576 = carry - borrow_bit; q = q0 + 1 iff it is +1
+  const bool up = (carry == 1u) && (borrow == 0u);
+  D[0] = add_cc(X[0], up ? q1[0] : T[18]);
+#pragma unroll
+  for (int k = 1; k < 8; ++k) D[k] = addc_cc(X[k], up ? q1[k] : T[18 + k]);
+#pragma unroll
+  for (int k = 8; k < kLimbs - 1; ++k) D[k] = addc_cc(X[k], 0u);
+  D[kLimbs - 1] = addc(X[kLimbs - 1], 0u);
+}
+
+// (D, c) -> X = D - floor(D / 2^336) + c, 336 = 24 (r - s) bits (inverse of to_ranlux).
+__device__ __forceinline__ void to_lcg(const uint32_t D[kLimbs], uint32_t c, uint32_t X[kLimbs]) {
+  uint32_t Q[8];  // D >> 336: 240 bits
+#pragma unroll
+  for (int k = 0; k < 7; ++k) Q[k] = shr_pair(D[10 + k], D[11 + k], 16);
+  Q[7] = D[17] >> 16;
+  X[0] = sub_cc(D[0], Q[0]);
+#pragma unroll
+  for (int k = 1; k < 8; ++k) X[k] = subc_cc(D[k], Q[k]);
+#pragma unroll
+  for (int k = 8; k < kLimbs - 1; ++k) X[k] = subc_cc(D[k], 0u);
+  X[kLimbs - 1] = subc(D[kLimbs - 1], 0u);
+  X[0] = add_cc(X[0], c);
+#pragma unroll
+  for (int k = 1; k < kLimbs - 1; ++k) X[k] = addc_cc(X[k], 0u);
+  X[kLimbs - 1] = addc(X[kLimbs - 1], 0u);
+}
+
+// Borrow bit of the RANLUX state: c = X - D + floor(D / 2^336), known to be 0 or 1, so
+// the low 32 bits of each term suffice.
+__device__ __forceinline__ uint32_t carry_of(const uint32_t X[kLimbs], const uint32_t D[kLimbs]) {
+  return X[0] - D[0] + shr_pair(D[10], D[11], 16);
+}
+
+// ---------------------------------------------------------------------------------
+// Sec. 2.3 outputs.  Word k of the block (k = 0 the oldest) is bits 24k..24k+23 of D;
+// the 48-bit value j is bits 48j..48j+47 = word 2j + 2^24 word 2j+1.
+// ---------------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t word24(const uint32_t D[kLimbs], int k) {
+  const int bit = 24 * k;
+  const int limb = bit >> 5, off = bit & 31;
+  uint32_t v = D[limb] >> off;
+  if (off > 8) v |= D[limb + 1] << (32 - off);
+  return v & 0xFFFFFFu;
+}
+
+__device__ __forceinline__ uint64_t bits48(const uint32_t D[kLimbs], int j) {
+  const int limb = (3 * j) >> 1;  // 48 j / 32
+  if ((j & 1) == 0) return ((uint64_t)(D[limb + 1] & 0xFFFFu) << 32) | D[limb];
+  return ((uint64_t)(D[limb + 1]) << 16) | (D[limb] >> 16);
+}
+
+// 48-bit integer v -> the double v 2^-48 in [0, 1), built with integer operations only
+// (the GPU's FP64 pipe is narrow; the conversion is exact because v < 2^53).  The
+// leading one of v is moved to bit 52, the exponent field is set so that the value
+// reads v 2^-48, and v = 0 maps to +0.0.
+__device__ __forceinline__ uint64_t f64_bits_from48(uint64_t v) {
+  const int lz = __clzll((long long)v);          // 16..64
+  const int s = lz - 11;                         // shift that puts the leading 1 at bit 52
+  const uint64_t mant = v << (s & 63);
+  const uint64_t bits = mant + ((uint64_t)(1026 - s) << 52);
+  return v ? bits : 0ull;
+}
+
+}  // namespace rlxpp

@@ -1,0 +1,83 @@
+// Internal declarations shared by the translation units of librlxpp.so.
+#pragma once
+#include <cstddef>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "../../include/rlxpp.h"
+
+namespace rlxpp {
+
+// Power table for skips and seeds (Sec. 2.4): entry (w, j) = A^(j 16^w) mod m for
+// windows w < kWindows (exponents below 2^160 = 2^96 * 2^64 seeds) and digits j < 16
+// (j = 0 unused), each 18 limbs of 32 bits.
+constexpr int kWindows = 40;
+constexpr int kDigits = 16;
+constexpr size_t kTableLimbs = (size_t)kWindows * kDigits * 18;
+constexpr int kSeedWindow0 = 24;  // 2^96 = 16^24
+
+// Resident per-stream state, structure of arrays:
+//   D      9 planes of n uint64 (plane k holds bits 64k..64k+63 of every stream's D);
+//   meta   n uint32: bits 0..7 read position (0..24), bit 8 borrow, bits 16..23 level.
+__host__ __device__ inline uint32_t meta_pack(uint32_t pos, uint32_t carry, uint32_t level) {
+  return pos | (carry << 8) | (level << 16);
+}
+__host__ __device__ inline uint32_t meta_pos(uint32_t m) { return m & 0xFFu; }
+__host__ __device__ inline uint32_t meta_carry(uint32_t m) { return (m >> 8) & 1u; }
+__host__ __device__ inline uint32_t meta_level(uint32_t m) { return (m >> 16) & 0xFFu; }
+
+struct Lux {  // a luxury multiplier in kernel-parameter (constant bank) form
+  uint32_t a[18];
+};
+
+struct StateView {
+  uint64_t* D;       // [9][stride], this view's streams first
+  uint32_t* meta;    // [n]
+  uint64_t n;        // streams in this view
+  uint64_t stride;   // distance between the planes of D (streams of the handle)
+  const uint32_t* lux;    // [n_levels][18] multipliers A
+  const uint32_t* table;  // [n_levels][kTableLimbs]
+  int* status;       // sticky device status (rlxpp_status value, 0 = ok)
+};
+
+enum DrawKind { kDrawU24 = 0, kDrawF64 = 1, kDrawSumHist = 2 };
+
+struct DrawArgs {
+  StateView s;
+  Lux A;                 // used when `uniform` (every stream at level 0)
+  int uniform;
+  const int64_t* counts;   // NULL: count_each for all, out offset i * count_each
+  const int64_t* offsets;
+  int64_t count_each;
+  void* out;             // uint32 / double output, or per-stream sums (sum/hist)
+  unsigned long long* hist;  // 256 bins (sum/hist)
+  int accumulate_sums;   // sum/hist: add to sums[i] instead of overwriting
+};
+
+constexpr int kDrawBlock = 128;  // threads per block of the draw kernels
+
+// ---- kernels launchers (defined in the .cu files) --------------------------------
+cudaError_t launch_level_setup(uint32_t p, uint32_t* lux_out18, uint32_t* table_out,
+                               cudaStream_t st);
+// keep_levels: take each stream's level from its current meta word (re-seeding)
+cudaError_t launch_seed(const StateView& s, const uint64_t* seeds, const uint8_t* level_of_stream,
+                        uint32_t n_levels, bool keep_levels, cudaStream_t st);
+cudaError_t launch_skip(const StateView& s, const uint64_t* n128, cudaStream_t st);
+cudaError_t launch_draw(int kind, const DrawArgs& a, cudaStream_t st);
+cudaError_t launch_export(const StateView& s, const uint32_t* level_p, rlxpp_state* dst,
+                          cudaStream_t st);
+cudaError_t launch_import(const StateView& s, const uint32_t* level_p, uint32_t n_levels,
+                          const rlxpp_state* src, cudaStream_t st);
+cudaError_t launch_test(int which, const uint64_t* x, const uint64_t* y, uint64_t* out,
+                        uint32_t* carry, uint64_t n, cudaStream_t st);
+
+enum TestOp {
+  kTestMultiply = 0,
+  kTestModM = 1,
+  kTestMulMod = 2,
+  kTestToRanlux = 3,
+  kTestToLcg = 4,
+  kTestF64 = 5
+};
+
+}  // namespace rlxpp

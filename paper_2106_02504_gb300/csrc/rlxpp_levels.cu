@@ -1,0 +1,337 @@
+// Luxury-level setup, seeding, skipping, state import/export and the arithmetic test
+// kernels.
+//
+// Seeding and skipping follow Sec. 2.4: exponentiation by squaring, here with a
+// 4-bit fixed window whose powers A^(j 16^w) are tabulated once per luxury level, so
+// that a stream needs one modular product per non-zero exponent digit.
+#include "rlxpp_arith.cuh"
+#include "rlxpp_internal.h"
+
+namespace rlxpp {
+namespace {
+
+// a = 2^-24 mod m = 2^576 - 2^552 - 2^240 + 2^216 + 1 (one recurrence step, Sec. 1),
+// as 32-bit limbs, least significant first.
+__constant__ uint32_t kOneStep[18] = {
+    0x00000001u, 0x00000000u, 0x00000000u, 0x00000000u, 0x00000000u, 0x00000000u,
+    0x01000000u, 0xFFFF0000u, 0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu,
+    0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFEFFu};
+
+__device__ __forceinline__ void mul_mod(const uint32_t x[kLimbs], const uint32_t y[kLimbs],
+                                        uint32_t r[kLimbs]) {
+  uint32_t p[2 * kLimbs];
+  multiply9x9([&](int i) { return y[i]; }, x, p);
+  mod_m(p, r);
+}
+
+__device__ __forceinline__ void load18(const uint32_t* __restrict__ src, uint32_t v[kLimbs]) {
+  const uint2* s2 = reinterpret_cast<const uint2*>(src);  // entries are 8-byte aligned
+#pragma unroll
+  for (int k = 0; k < 9; ++k) {
+    const uint2 t = __ldg(s2 + k);
+    v[2 * k] = t.x;
+    v[2 * k + 1] = t.y;
+  }
+}
+__device__ __forceinline__ void store18(uint32_t* dst, const uint32_t v[kLimbs]) {
+#pragma unroll
+  for (int k = 0; k < kLimbs; ++k) dst[k] = v[k];
+}
+
+__device__ __forceinline__ void load_state_D(const StateView& s, uint64_t i, uint32_t D[kLimbs]) {
+#pragma unroll
+  for (int k = 0; k < 9; ++k) {
+    const uint64_t v = s.D[(uint64_t)k * s.stride + i];
+    D[2 * k] = (uint32_t)v;
+    D[2 * k + 1] = (uint32_t)(v >> 32);
+  }
+}
+__device__ __forceinline__ void store_state_D(const StateView& s, uint64_t i, const uint32_t D[kLimbs]) {
+#pragma unroll
+  for (int k = 0; k < 9; ++k)
+    s.D[(uint64_t)k * s.stride + i] = ((uint64_t)D[2 * k + 1] << 32) | D[2 * k];
+}
+
+__device__ __forceinline__ void set_status(int* status, int code) {
+  atomicCAS(status, 0, code);
+}
+
+// ---- per-level setup: A = a^p, then A^(16^w) by repeated squaring ----------------
+__global__ void k_level_powers(uint32_t p, uint32_t* __restrict__ lux, uint32_t* __restrict__ table) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  uint32_t a[kLimbs], r[kLimbs], t[kLimbs];
+#pragma unroll
+  for (int k = 0; k < kLimbs; ++k) a[k] = kOneStep[k];
+  // left-to-right square-and-multiply over the bits of p (p >= 1)
+  int top = 31 - __clz(p);
+#pragma unroll
+  for (int k = 0; k < kLimbs; ++k) r[k] = a[k];
+#pragma unroll 1
+  for (int b = top - 1; b >= 0; --b) {
+    mul_mod(r, r, t);
+    if ((p >> b) & 1u) {
+      mul_mod(t, a, r);
+    } else {
+#pragma unroll
+      for (int k = 0; k < kLimbs; ++k) r[k] = t[k];
+    }
+  }
+  store18(lux, r);
+  // window w, digit 1: A^(16^w)
+#pragma unroll 1
+  for (int w = 0; w < kWindows; ++w) {
+    store18(table + ((size_t)w * kDigits + 1) * kLimbs, r);
+    if (w + 1 < kWindows) {
+#pragma unroll 1
+      for (int s = 0; s < 4; ++s) {
+        mul_mod(r, r, t);
+#pragma unroll
+        for (int k = 0; k < kLimbs; ++k) r[k] = t[k];
+      }
+    }
+  }
+}
+
+// digits 0 and 2..15 of every window: A^(j 16^w) = A^((j-1) 16^w) A^(16^w)
+__global__ void k_level_digits(uint32_t* __restrict__ table) {
+  const int w = blockIdx.x * blockDim.x + threadIdx.x;
+  if (w >= kWindows) return;
+  uint32_t* row = table + (size_t)w * kDigits * kLimbs;
+  uint32_t base[kLimbs], cur[kLimbs], t[kLimbs];
+#pragma unroll
+  for (int k = 0; k < kLimbs; ++k) {
+    base[k] = row[kLimbs + k];
+    cur[k] = base[k];
+    row[k] = k == 0 ? 1u : 0u;
+  }
+#pragma unroll 1
+  for (int j = 2; j < kDigits; ++j) {
+    mul_mod(cur, base, t);
+#pragma unroll
+    for (int k = 0; k < kLimbs; ++k) cur[k] = t[k];
+    store18(row + (size_t)j * kLimbs, cur);
+  }
+}
+
+// X <- X * prod_w T[w0 + w][digit_w(e)], digits of a 64-bit exponent chunk e; `have`
+// tracks whether X holds a value yet (X = 1 otherwise, which is never materialised).
+__device__ __forceinline__ void apply_digits(const uint32_t* __restrict__ T, int w0, uint64_t e,
+                                             uint32_t X[kLimbs], bool& have) {
+#pragma unroll 1
+  for (int w = 0; w < 16; ++w) {
+    const uint32_t d = (uint32_t)(e >> (4 * w)) & 15u;
+    if (d == 0) continue;
+    const uint32_t* entry = T + ((size_t)(w0 + w) * kDigits + d) * kLimbs;
+    if (!have) {
+      load18(entry, X);
+      have = true;
+    } else {
+      uint32_t Y[kLimbs], R[kLimbs];
+      load18(entry, Y);
+      mul_mod(X, Y, R);
+#pragma unroll
+      for (int k = 0; k < kLimbs; ++k) X[k] = R[k];
+    }
+  }
+}
+
+__global__ void k_seed(StateView s, const uint64_t* __restrict__ seeds,
+                       const uint8_t* __restrict__ level_of, uint32_t n_levels, bool keep_levels) {
+  const uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= s.n) return;
+  uint32_t lvl = keep_levels ? meta_level(s.meta[i]) : level_of ? level_of[i] : 0u;
+  if (lvl >= n_levels) {
+    set_status(s.status, RLXPP_ERR_INVALID);
+    lvl = 0;
+  }
+  const uint32_t* T = s.table + (size_t)lvl * kTableLimbs;
+  uint32_t X[kLimbs];
+  bool have = false;
+  apply_digits(T, kSeedWindow0, seeds[i], X, have);
+  if (!have) {
+#pragma unroll
+    for (int k = 0; k < kLimbs; ++k) X[k] = k == 0 ? 1u : 0u;
+  }
+  uint32_t D[kLimbs];
+  to_ranlux(X, D);
+  store_state_D(s, i, D);
+  s.meta[i] = meta_pack(0u, carry_of(X, D), lvl);
+}
+
+__global__ void k_skip(StateView s, const uint64_t* __restrict__ n128) {
+  const uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= s.n) return;
+  const uint64_t lo = n128[2 * i], hi = n128[2 * i + 1];
+  if ((lo | hi) == 0) return;
+  const uint32_t meta = s.meta[i];
+  const uint32_t lvl = meta_level(meta);
+  const uint32_t* T = s.table + (size_t)lvl * kTableLimbs;
+  uint32_t D[kLimbs], X[kLimbs];
+  load_state_D(s, i, D);
+  to_lcg(D, meta_carry(meta), X);
+  bool have = true;  // X already holds the state: multiply by every digit's power
+  apply_digits(T, 0, lo, X, have);
+  apply_digits(T, 16, hi, X, have);
+  to_ranlux(X, D);
+  store_state_D(s, i, D);
+  s.meta[i] = meta_pack(meta_pos(meta), carry_of(X, D), lvl);
+}
+
+__global__ void k_export(StateView s, const uint32_t* __restrict__ level_p, rlxpp_state* dst) {
+  const uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= s.n) return;
+  const uint32_t meta = s.meta[i];
+  uint64_t* rec = reinterpret_cast<uint64_t*>(dst + i);
+#pragma unroll
+  for (int k = 0; k < 9; ++k) rec[k] = s.D[(uint64_t)k * s.stride + i];
+  rec[9] = (uint64_t)meta_carry(meta) | ((uint64_t)meta_pos(meta) << 32);
+  rec[10] = (uint64_t)level_p[meta_level(meta)];
+}
+
+__global__ void k_import(StateView s, const uint32_t* __restrict__ level_p, uint32_t n_levels,
+                         const rlxpp_state* __restrict__ src) {
+  const uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= s.n) return;
+  const uint64_t* rec = reinterpret_cast<const uint64_t*>(src + i);
+  uint32_t D[kLimbs];
+#pragma unroll
+  for (int k = 0; k < 9; ++k) {
+    const uint64_t v = rec[k];
+    D[2 * k] = (uint32_t)v;
+    D[2 * k + 1] = (uint32_t)(v >> 32);
+  }
+  const uint32_t carry = (uint32_t)rec[9], pos = (uint32_t)(rec[9] >> 32);
+  const uint32_t p = (uint32_t)rec[10], reserved = (uint32_t)(rec[10] >> 32);
+  uint32_t lvl = n_levels;
+  for (uint32_t l = 0; l < n_levels; ++l)
+    if (level_p[l] == p) { lvl = l; break; }
+  bool ok = carry <= 1u && pos <= (uint32_t)kWords && reserved == 0u && lvl < n_levels;
+  if (ok) {
+    uint32_t X[kLimbs], D2[kLimbs];
+    to_lcg(D, carry, X);
+    uint32_t nz = 0;
+#pragma unroll
+    for (int k = 0; k < kLimbs; ++k) nz |= X[k];
+    // X < m  <=>  X + (2^240 - 1) < 2^576
+    uint32_t e = add_cc(X[0], 0xFFFFFFFFu);
+#pragma unroll
+    for (int k = 1; k < 7; ++k) e = addc_cc(X[k], 0xFFFFFFFFu);
+    e = addc_cc(X[7], 0xFFFFu);
+#pragma unroll
+    for (int k = 8; k < kLimbs; ++k) e = addc_cc(X[k], 0u);
+    const uint32_t ge = addc(0u, 0u);
+    (void)e;
+    ok = nz != 0 && ge == 0;
+    if (ok) {
+      to_ranlux(X, D2);
+      uint32_t diff = carry_of(X, D2) ^ carry;
+#pragma unroll
+      for (int k = 0; k < kLimbs; ++k) diff |= D2[k] ^ D[k];
+      ok = diff == 0;
+    }
+  }
+  if (!ok) {
+    set_status(s.status, RLXPP_ERR_INVALID);
+    return;
+  }
+  store_state_D(s, i, D);
+  s.meta[i] = meta_pack(pos, carry, lvl);
+}
+
+// ---- arithmetic unit tests --------------------------------------------------------
+__device__ __forceinline__ void load_u64_limbs(const uint64_t* src, int n64, uint32_t* v) {
+  for (int k = 0; k < n64; ++k) {
+    v[2 * k] = (uint32_t)src[k];
+    v[2 * k + 1] = (uint32_t)(src[k] >> 32);
+  }
+}
+__device__ __forceinline__ void store_u64_limbs(uint64_t* dst, int n64, const uint32_t* v) {
+  for (int k = 0; k < n64; ++k) dst[k] = ((uint64_t)v[2 * k + 1] << 32) | v[2 * k];
+}
+
+__global__ void k_test(int op, const uint64_t* __restrict__ x, const uint64_t* __restrict__ y,
+                       uint64_t* __restrict__ out, uint32_t* __restrict__ carry, uint64_t n) {
+  const uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  uint32_t a[kLimbs], b[kLimbs], r[kLimbs], p[2 * kLimbs];
+  switch (op) {
+    case kTestMultiply:
+      load_u64_limbs(x + 9 * i, 9, a);
+      load_u64_limbs(y + 9 * i, 9, b);
+      multiply9x9([&](int k) { return a[k]; }, b, p);
+      store_u64_limbs(out + 18 * i, 18, p);
+      break;
+    case kTestModM:
+      load_u64_limbs(x + 18 * i, 18, p);
+      mod_m(p, r);
+      store_u64_limbs(out + 9 * i, 9, r);
+      break;
+    case kTestMulMod:
+      load_u64_limbs(x + 9 * i, 9, a);
+      load_u64_limbs(y + 9 * i, 9, b);
+      mul_mod(a, b, r);
+      store_u64_limbs(out + 9 * i, 9, r);
+      break;
+    case kTestToRanlux:
+      load_u64_limbs(x + 9 * i, 9, a);
+      to_ranlux(a, r);
+      store_u64_limbs(out + 9 * i, 9, r);
+      carry[i] = carry_of(a, r);
+      break;
+    case kTestToLcg:
+      load_u64_limbs(x + 9 * i, 9, a);
+      to_lcg(a, carry[i], r);
+      store_u64_limbs(out + 9 * i, 9, r);
+      break;
+    case kTestF64:
+      out[i] = f64_bits_from48(x[i]);
+      break;
+  }
+}
+
+inline unsigned grid_for(uint64_t n, unsigned block) {
+  return (unsigned)((n + block - 1) / block);
+}
+
+}  // namespace
+
+cudaError_t launch_level_setup(uint32_t p, uint32_t* lux_out18, uint32_t* table_out, cudaStream_t st) {
+  k_level_powers<<<1, 32, 0, st>>>(p, lux_out18, table_out);
+  k_level_digits<<<1, 64, 0, st>>>(table_out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_seed(const StateView& s, const uint64_t* seeds, const uint8_t* level_of_stream,
+                        uint32_t n_levels, bool keep_levels, cudaStream_t st) {
+  if (s.n == 0) return cudaSuccess;
+  k_seed<<<grid_for(s.n, 128), 128, 0, st>>>(s, seeds, level_of_stream, n_levels, keep_levels);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_skip(const StateView& s, const uint64_t* n128, cudaStream_t st) {
+  if (s.n == 0) return cudaSuccess;
+  k_skip<<<grid_for(s.n, 128), 128, 0, st>>>(s, n128);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_export(const StateView& s, const uint32_t* level_p, rlxpp_state* dst, cudaStream_t st) {
+  if (s.n == 0) return cudaSuccess;
+  k_export<<<grid_for(s.n, 256), 256, 0, st>>>(s, level_p, dst);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_import(const StateView& s, const uint32_t* level_p, uint32_t n_levels,
+                          const rlxpp_state* src, cudaStream_t st) {
+  if (s.n == 0) return cudaSuccess;
+  k_import<<<grid_for(s.n, 128), 128, 0, st>>>(s, level_p, n_levels, src);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_test(int which, const uint64_t* x, const uint64_t* y, uint64_t* out,
+                        uint32_t* carry, uint64_t n, cudaStream_t st) {
+  if (n == 0) return cudaSuccess;
+  k_test<<<grid_for(n, 128), 128, 0, st>>>(which, x, y, out, carry, n);
+  return cudaGetLastError();
+}
+
+}  // namespace rlxpp

@@ -1,0 +1,73 @@
+"""Oracle-side helpers for the parity tests: expected states and outputs computed only
+with ``oracle/`` (Python big integers for the LCG form, the C recurrence for volume)."""
+from __future__ import annotations
+
+import numpy as np
+
+from oracle import ranluxpp as R
+from oracle import swb_lib as S
+
+MASK64 = (1 << 64) - 1
+
+
+def limbs64(v, n):
+    return [(v >> (64 * k)) & MASK64 for k in range(n)]
+
+
+def from_limbs64(arr):
+    return sum(int(x) << (64 * k) for k, x in enumerate(arr))
+
+
+def seeded_X(seeds, p):
+    """LCG states of the given seeds (dict seed -> X); consecutive runs share work."""
+    A = R.luxury_multiplier(p)
+    B = pow(A, 1 << R.SEED_SHIFT, R.M)
+    out = {}
+    prev_seed, prev_X = None, None
+    for s in sorted(set(int(x) for x in seeds)):
+        if prev_seed is not None and s == prev_seed + 1:
+            X = prev_X * B % R.M
+        else:
+            X = pow(B, s, R.M)
+        out[s] = X
+        prev_seed, prev_X = s, X
+    return out
+
+
+class StreamSet:
+    """Oracle copies of many streams as recurrence windows (for the C oracle)."""
+
+    def __init__(self, Xs, p, pos=None):
+        n = len(Xs)
+        self.p = p
+        self.words = np.zeros((n, 24), dtype=np.uint32)
+        self.carry = np.zeros(n, dtype=np.uint32)
+        self.pos = np.zeros(n, dtype=np.int32) if pos is None else np.array(pos, dtype=np.int32)
+        for i, X in enumerate(Xs):
+            D, c = R.to_ranlux(X)
+            self.words[i] = R.unpack_words(D)
+            self.carry[i] = c
+
+    @classmethod
+    def from_seeds(cls, seeds, p):
+        xs = seeded_X(seeds, p)
+        return cls([xs[int(s)] for s in seeds], p)
+
+    def draw(self, count, kind):
+        return S.draw_many(self.words, self.carry, self.pos, self.p, count, kind)
+
+    def sum_hist(self, count):
+        return S.sum_hist_many(self.words, self.carry, self.pos, self.p, count)
+
+    def D(self, i):
+        return R.pack_words(int(w) for w in self.words[i])
+
+    def state_records(self):
+        """(n, 11) uint64 rows laid out like struct rlxpp_state."""
+        n = self.words.shape[0]
+        rec = np.zeros((n, 11), dtype=np.uint64)
+        for i in range(n):
+            rec[i, :9] = limbs64(self.D(i), 9)
+            rec[i, 9] = int(self.carry[i]) | (int(self.pos[i]) << 32)
+            rec[i, 10] = self.p
+        return rec

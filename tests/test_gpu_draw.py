@@ -1,0 +1,344 @@
+"""Generator entry points against the oracle, element by element, bit-exact (GPU).
+
+Seeding, skipping, u24/f64 draws (uniform and ragged per-stream counts, odd read
+positions, host and device outputs), the fused sum/histogram consumer, state export /
+import and its validation, mixed luxury levels, and the single-stream workload
+(2^20 doubles and 2^20 integers from seed 1 at p = 2048; 10,000 advances at p = 24)."""
+import numpy as np
+import pytest
+
+from oracle import ranluxpp as R
+from oracle import swb_lib as S
+from paper_2106_02504_gb300 import workloads as W
+from tests.oracle_side import StreamSet, from_limbs64, seeded_X
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def native():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2106_02504_gb300 as P
+    return P.native
+
+
+def dev_u64(a):
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.uint64).view(np.int64)).cuda()
+
+
+def states(native, g, n):
+    buf = torch.zeros((n, 11), dtype=torch.int64, device="cuda")
+    native.rlxpp_get_state(g.handle, buf)
+    return buf.cpu().numpy().view(np.uint64)
+
+
+def assert_states(native, g, ref: StreamSet):
+    n = ref.words.shape[0]
+    got = states(native, g, n)
+    want = ref.state_records()
+    bad = np.nonzero((got != want).any(axis=1))[0]
+    assert bad.size == 0, f"{bad.size} streams differ, first {bad[:5]}"
+
+
+def f64_bits(t):
+    return t.cpu().numpy().view(np.uint64)
+
+
+N = 300  # three blocks of 128 threads and a ragged tail
+
+
+def make(native, seeds, levels=(2048,), level_of=None):
+    lo = None if level_of is None else torch.from_numpy(np.asarray(level_of, dtype=np.uint8)).cuda()
+    return native.Generator(len(seeds), list(levels), dev_u64(seeds), lo)
+
+
+def test_seed_states(native):
+    seeds = W.consecutive_seeds(N)
+    g = make(native, seeds)
+    assert_states(native, g, StreamSet.from_seeds(seeds, 2048))
+    # extreme seeds, including 0 and 2^64 - 1
+    seeds2 = np.array([0, 1, 2 ** 63, 2 ** 64 - 1, 2718, 123456789012345], dtype=np.uint64)
+    g2 = make(native, seeds2, levels=(389,))
+    assert_states(native, g2, StreamSet.from_seeds(seeds2, 389))
+    g.close()
+    g2.close()
+
+
+@pytest.mark.parametrize("p,count", [(2048, 1000), (24, 1001), (223, 12), (389, 1)])
+def test_draw_f64_uniform(native, p, count):
+    seeds = W.random_seeds(N, 31 + p)
+    g = make(native, seeds, levels=(p,))
+    out = torch.zeros((N, count), dtype=torch.float64, device="cuda")
+    g.draw_f64(out, count)
+    ref = StreamSet.from_seeds(seeds, p)
+    want = ref.draw(count, S.KIND_F64)
+    assert np.array_equal(f64_bits(out), want.view(np.uint64))
+    assert_states(native, g, ref)
+
+
+@pytest.mark.parametrize("p,count", [(2048, 1000), (24, 24), (389, 23)])
+def test_draw_u24_uniform(native, p, count):
+    seeds = W.random_seeds(N, 41 + p)
+    g = make(native, seeds, levels=(p,))
+    out = torch.zeros((N, count), dtype=torch.int32, device="cuda")
+    g.draw_u24(out, count)
+    ref = StreamSet.from_seeds(seeds, p)
+    assert np.array_equal(out.cpu().numpy().view(np.uint32), ref.draw(count, S.KIND_U24))
+    assert_states(native, g, ref)
+
+
+def test_mixed_types_odd_positions(native):
+    """u24 draws leave odd read positions; doubles then skip a lone leftover word."""
+    seeds = W.consecutive_seeds(N, first=77)
+    g = make(native, seeds, levels=(223,))
+    ref = StreamSet.from_seeds(seeds, 223)
+    for kind, count in [(S.KIND_U24, 5), (S.KIND_F64, 7), (S.KIND_U24, 23), (S.KIND_F64, 30),
+                        (S.KIND_U24, 1), (S.KIND_F64, 11), (S.KIND_F64, 0), (S.KIND_U24, 48)]:
+        if kind == S.KIND_U24:
+            out = torch.zeros((N, max(count, 1)), dtype=torch.int32, device="cuda")
+            g.draw_u24(out, count)
+            got = out.cpu().numpy().view(np.uint32)[:, :count]
+        else:
+            out = torch.zeros((N, max(count, 1)), dtype=torch.float64, device="cuda")
+            g.draw_f64(out, count)
+            got = f64_bits(out)[:, :count]
+        want = ref.draw(count, kind)
+        if kind == S.KIND_F64:
+            want = want.view(np.uint64)
+        assert np.array_equal(got, want), (kind, count)
+    assert_states(native, g, ref)
+
+
+@pytest.mark.parametrize("kind", [S.KIND_U24, S.KIND_F64])
+def test_ragged_counts_offsets(native, kind):
+    seeds = W.random_seeds(N, 51)
+    counts, offsets = W.ragged_counts(N, 200, seed=52)
+    total = int(counts.sum())
+    g = make(native, seeds, levels=(2048,))
+    dt = torch.int32 if kind == S.KIND_U24 else torch.float64
+    out = torch.full((total + 1,), -1, dtype=dt, device="cuda")
+    c_d = torch.from_numpy(counts).cuda()
+    o_d = torch.from_numpy(offsets).cuda()
+    (g.draw_u24 if kind == S.KIND_U24 else g.draw_f64)(out, 0, c_d, o_d)
+    got = out.cpu().numpy()
+    ref = StreamSet.from_seeds(seeds, 2048)
+    for i in range(N):
+        one = StreamSet.__new__(StreamSet)
+        one.p, one.words, one.carry, one.pos = 2048, ref.words[i:i + 1], ref.carry[i:i + 1], ref.pos[i:i + 1]
+        w = one.draw(int(counts[i]), kind)[0]
+        seg = got[offsets[i]:offsets[i] + counts[i]]
+        if kind == S.KIND_F64:
+            assert np.array_equal(seg.view(np.uint64), w.view(np.uint64)), i
+        else:
+            assert np.array_equal(seg.view(np.uint32), w), i
+    assert got[total] == -1  # nothing written past the packed output
+    assert_states(native, g, ref)
+
+
+def test_sum_hist(native):
+    seeds = W.consecutive_seeds(N, first=1000)
+    g = make(native, seeds, levels=(2048,))
+    sums = torch.zeros(N, dtype=torch.int64, device="cuda")
+    hist = torch.zeros(256, dtype=torch.int64, device="cuda")
+    g.draw_f64_sum_hist(4096, sums, hist)
+    ref = StreamSet.from_seeds(seeds, 2048)
+    wsums, whist = ref.sum_hist(4096)
+    assert np.array_equal(sums.cpu().numpy().view(np.uint64), wsums)
+    assert np.array_equal(hist.cpu().numpy().view(np.uint64), whist)
+    assert int(hist.sum()) == N * 4096
+    # accumulation across calls, with a ragged count
+    g.draw_f64_sum_hist(13, sums, hist)
+    wsums2, whist2 = ref.sum_hist(13)
+    assert np.array_equal(sums.cpu().numpy().view(np.uint64), wsums2)  # sums are overwritten
+    assert np.array_equal(hist.cpu().numpy().view(np.uint64), whist + whist2)
+    assert_states(native, g, ref)
+
+
+def test_skip(native):
+    seeds = W.consecutive_seeds(N)
+    p = 2048
+    g = make(native, seeds, levels=(p,))
+    # move some streams off position 0 first
+    out = torch.zeros((N, 5), dtype=torch.int32, device="cuda")
+    g.draw_u24(out, 5)
+    dist = W.skip_distances(N, seed=4)
+    dist[0] = [0, 0]
+    dist[1] = [1, 0]
+    dist[2] = [2 ** 64 - 1, 2 ** 64 - 1]
+    g.skip(dev_u64(dist))
+    xs = seeded_X(seeds, p)
+    A = R.luxury_multiplier(p)
+    got = states(native, g, N)
+    for i in range(N):
+        n = int(dist[i, 0]) | (int(dist[i, 1]) << 64)
+        X = pow(A, n, R.M) * xs[int(seeds[i])] % R.M
+        D, c = R.to_ranlux(X)
+        assert from_limbs64(got[i, :9]) == D, i
+        assert int(got[i, 9]) == c | (5 << 32), i
+
+
+def test_state_round_trip_and_validation(native):
+    seeds = W.random_seeds(N, 61)
+    g = make(native, seeds, levels=(24, 2048), level_of=np.arange(N) % 2)
+    out1 = torch.zeros((N, 50), dtype=torch.float64, device="cuda")
+    g.draw_f64(out1, 50)
+    saved = states(native, g, N).copy()
+    out2 = torch.zeros((N, 77), dtype=torch.float64, device="cuda")
+    g.draw_f64(out2, 77)
+    # restore from host memory and draw again: same numbers
+    g.set_state(saved.view(np.int64).copy())
+    g.sync()
+    out3 = torch.zeros((N, 77), dtype=torch.float64, device="cuda")
+    g.draw_f64(out3, 77)
+    assert torch.equal(out2, out3)
+    # a host copy of the state continues the same sequence (Sec. 4.2)
+    assert np.array_equal(states(native, g, N)[:, 10], np.where(np.arange(N) % 2, 2048, 24))
+    # invalid records: bad carry, bad pos, unknown p, non-canonical numbers, zero state
+    bad = states(native, g, N).copy()
+    keep = bad.copy()
+    bad[0, 9] = 2                                   # carry 2
+    bad[1, 9] = 25 << 32                            # pos 25
+    bad[2, 10] = 7                                  # p not a level of the handle
+    bad[3, :9] = 0
+    bad[3, 9] = 0                                   # X = 0
+    bad[4, :9] = [2 ** 64 - 1] * 9
+    bad[4, 9] = 1                                   # X = m
+    g.set_state(bad.view(np.int64).copy())
+    with pytest.raises(native.RlxppError) as e:
+        g.sync()
+    assert e.value.status == native.RLXPP_ERR_INVALID
+    got = states(native, g, N)
+    assert np.array_equal(got[:5], keep[:5])        # rejected streams unchanged
+    assert np.array_equal(got[5:], bad[5:])
+    g.sync()                                        # status was cleared
+
+
+def test_noncanonical_record_rejected(native):
+    # find a non-canonical (D, c): to_ranlux(to_lcg(D, c)) != (D, c)
+    rng = np.random.Generator(np.random.PCG64(71))
+    for _ in range(100):
+        w = [int(x) for x in rng.integers(0, 2 ** 24, size=24)]
+        c = int(rng.integers(0, 2))
+        X = R.to_lcg(R.pack_words(w), c)
+        if 0 < X < R.M and R.to_ranlux(X) != (R.pack_words(w), c):
+            break
+    g = make(native, np.array([5], dtype=np.uint64), levels=(2048,))
+    rec = states(native, g, 1).copy()
+    D = R.pack_words(w)
+    rec[0, :9] = [(D >> (64 * k)) & (2 ** 64 - 1) for k in range(9)]
+    rec[0, 9] = c
+    g.set_state(rec.view(np.int64).copy())
+    with pytest.raises(native.RlxppError):
+        g.sync()
+
+
+def test_mixed_levels(native):
+    levels, lvl_idx, _, _ = W.batch_mix(N, seed=81)
+    seeds = W.random_seeds(N, 82)
+    g = make(native, seeds, levels=levels, level_of=lvl_idx)
+    out = torch.zeros((N, 40), dtype=torch.float64, device="cuda")
+    g.draw_f64(out, 40)
+    got = f64_bits(out)
+    for li, p in enumerate(levels):
+        idx = np.nonzero(lvl_idx == li)[0]
+        ref = StreamSet.from_seeds(seeds[idx], p)
+        assert np.array_equal(got[idx], ref.draw(40, S.KIND_F64).view(np.uint64)), p
+
+
+def test_reseed(native):
+    g = make(native, W.consecutive_seeds(N), levels=(24, 389), level_of=np.arange(N) % 2)
+    out = torch.zeros((N, 9), dtype=torch.float64, device="cuda")
+    g.draw_f64(out, 9)
+    seeds = W.random_seeds(N, 91)
+    g.seed(dev_u64(seeds))
+    g.draw_f64(out, 9)
+    got = f64_bits(out)
+    for li, p in enumerate((24, 389)):
+        idx = np.nonzero(np.arange(N) % 2 == li)[0]
+        assert np.array_equal(got[idx], StreamSet.from_seeds(seeds[idx], p).draw(9, S.KIND_F64).view(np.uint64))
+
+
+def test_host_buffers(native):
+    """Pageable and pinned host outputs and host inputs (seeds, counts, offsets)."""
+    seeds = W.random_seeds(N, 101)
+    g = native.Generator(N, [2048], seeds)            # seeds from pageable host memory
+    h = np.zeros((N, 100), dtype=np.float64)
+    g.draw_f64(h, 100)                                # pageable host output
+    ref = StreamSet.from_seeds(seeds, 2048)
+    assert np.array_equal(h.view(np.uint64), ref.draw(100, S.KIND_F64).view(np.uint64))
+    pinned = torch.zeros((N, 64), dtype=torch.int32).pin_memory()
+    g.draw_u24(pinned, 64)
+    assert np.array_equal(pinned.numpy().view(np.uint32), ref.draw(64, S.KIND_U24))
+    counts, offsets = W.ragged_counts(N, 30, seed=102)
+    hc = np.zeros(int(counts.sum()), dtype=np.float64)
+    g.draw_f64(hc, 0, counts, offsets)                # host counts/offsets/output
+    for i in range(0, N, 37):
+        one = StreamSet.__new__(StreamSet)
+        one.p, one.words, one.carry, one.pos = 2048, ref.words[i:i + 1], ref.carry[i:i + 1], ref.pos[i:i + 1]
+        want = one.draw(int(counts[i]), S.KIND_F64)[0]
+        assert np.array_equal(hc[offsets[i]:offsets[i] + counts[i]].view(np.uint64), want.view(np.uint64))
+
+
+def test_host_output_chunked(native):
+    """Host output larger than one device staging chunk (256 MiB): 2^16 streams x 1024."""
+    n, count = 1 << 16, 1024
+    seeds = W.consecutive_seeds(n)
+    g = make(native, seeds)
+    h = torch.zeros((n, count), dtype=torch.float64).pin_memory()
+    g.draw_f64(h, count)
+    d = torch.zeros((n, count), dtype=torch.float64, device="cuda")
+    g2 = make(native, seeds)
+    g2.draw_f64(d, count)
+    assert torch.equal(h, d.cpu())
+    idx = [0, 1, 4095, 4096, n - 1]
+    ref = StreamSet.from_seeds(seeds[idx], 2048)
+    assert np.array_equal(h.numpy()[idx].view(np.uint64), ref.draw(count, S.KIND_F64).view(np.uint64))
+
+
+def test_empty_and_zero(native):
+    g = native.Generator(0, [2048], None)
+    assert native.rlxpp_num_streams(g.handle) == 0
+    g.draw_f64(None, 0)
+    g.sync()
+    g1 = make(native, W.consecutive_seeds(3))
+    out = torch.zeros(1, dtype=torch.float64, device="cuda")
+    g1.draw_f64(out, 0)
+    with pytest.raises(native.RlxppError):
+        native.rlxpp_draw_f64(g1.handle, out, -1)
+    with pytest.raises(native.RlxppError):
+        native.rlxpp_create(1, [0], np.array([1], dtype=np.uint64))
+
+
+def test_single_stream_workload(native):
+    """Seed 1, p = 2048: 2^20 doubles, and 2^20 integers from a fresh seed-1 state."""
+    n = 1 << 20
+    for kind in (S.KIND_F64, S.KIND_U24):
+        g = make(native, np.array([1], dtype=np.uint64))
+        dt = torch.float64 if kind == S.KIND_F64 else torch.int32
+        out = torch.zeros((1, n), dtype=dt, device="cuda")
+        (g.draw_f64 if kind == S.KIND_F64 else g.draw_u24)(out, n)
+        ref = StreamSet.from_seeds([1], 2048)
+        want = ref.draw(n, kind)
+        got = out.cpu().numpy()
+        if kind == S.KIND_F64:
+            assert np.array_equal(got.view(np.uint64), want.view(np.uint64))
+        else:
+            assert np.array_equal(got.view(np.uint32), want)
+        assert_states(native, g, ref)
+
+
+def test_p24_ten_thousand_advances(native):
+    """10,000 refills at p = 24 on one stream, each block equal to 24 recurrence steps."""
+    g = make(native, np.array([1], dtype=np.uint64), levels=(24,))
+    n = 24 * 10_001
+    out = torch.zeros((1, n), dtype=torch.int32, device="cuda")
+    g.draw_u24(out, n)
+    got = out.cpu().numpy().view(np.uint32)[0]
+    w, c = R.to_ranlux(R.seed_lcg(1, 24))
+    w = R.unpack_words(w)
+    for b in range(10_001):
+        assert list(got[24 * b:24 * (b + 1)]) == w, b
+        w, c = S.block(w, c, 24)
