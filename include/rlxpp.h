@@ -144,6 +144,42 @@ const char* rlxpp_last_error(void);
 /* Release the handle and its device memory (synchronises the device first). */
 void rlxpp_destroy(rlxpp_gen* gen);
 
+/* ---- seeding without device allocation --------------------------------------------
+ * The paper has no counterpart of this entry point.  It serves callers that must not
+ * allocate device memory themselves or through this library: code that runs inside a
+ * host application which owns the whole device-memory budget (a fixed pool carved out
+ * at start-up), code on a latency-critical path where cudaMalloc/cudaFree would stall
+ * on an implicit device synchronisation, and code that may not create a handle
+ * (rlxpp_create allocates the resident state and the tables).
+ *
+ * It writes the seeded state of n_streams streams — exactly the records rlxpp_create
+ * followed by rlxpp_get_state would give — into caller-owned records, which the caller
+ * can keep, copy or import with rlxpp_set_state.
+ *  levels[n_levels]  host array of luxury levels p >= 1, 1 <= n_levels <=
+ *                    RLXPP_NOALLOC_MAX_LEVELS; more levels are rejected with
+ *                    RLXPP_ERR_INVALID.
+ *  level_of_stream   NULL (all streams at levels[0]) or n_streams bytes, device memory;
+ *                    a stream whose index is >= n_levels gets an all-zero record
+ *                    (p = 0 marks it invalid).
+ *  seeds             n_streams uint64, device memory.
+ *  out               n_streams records, device memory.
+ * Host pointers are rejected (staging them would allocate).
+ *
+ * Scratch: the multiplier and the power table of each level are computed on the
+ * device, at every call, into one fixed array of the library (184,608 bytes, room for
+ * RLXPP_NOALLOC_MAX_LEVELS levels) that every GPU loading the library holds until the
+ * process exits.  The call allocates nothing (no cudaMalloc, cudaFree or allocating
+ * library routine).  The first call on a device looks up the array's device address
+ * with that device current (cudaGetSymbolAddress); make that first call before any
+ * stream capture.  All calls share the array and it keeps the last call's contents:
+ * calls that overlap on the GPU (on different streams or from different threads) race
+ * and must be serialised by the caller.  Each call costs the table set-up of its
+ * levels (a few short kernels per level) plus one seeding kernel. */
+#define RLXPP_NOALLOC_MAX_LEVELS 4
+rlxpp_status rlxpp_seed_states_noalloc(const uint32_t* levels, uint32_t n_levels,
+                                       const uint8_t* level_of_stream, const uint64_t* seeds,
+                                       uint64_t n_streams, rlxpp_state* out, void* cuda_stream);
+
 /* ---- unit-test entry points (device arithmetic on n independent items) ----------
  * Numbers are little-endian arrays of uint64 limbs, item-major; all pointers are
  * device pointers and n may be 0.

@@ -30,6 +30,7 @@ assert STATE_BYTES == 88
 RLXPP_OK, RLXPP_ERR_INVALID, RLXPP_ERR_NOMEM, RLXPP_ERR_CUDA, RLXPP_ERR_TIMEOUT, \
     RLXPP_ERR_UNSUPPORTED = range(6)
 RLXPP_MAX_LEVELS = 16
+RLXPP_NOALLOC_MAX_LEVELS = 4
 
 
 class RlxppError(RuntimeError):
@@ -61,6 +62,7 @@ def _load():
         "rlxpp_test_to_lcg": [_vp, _vp, _vp, _u64, _vp],
         "rlxpp_test_f64_from48": [_vp, _vp, _u64, _vp],
         "rlxpp_luxury_multiplier": [_u32, _vp],
+        "rlxpp_seed_states_noalloc": [_vp, _u32, _vp, _vp, _u64, _vp, _vp],
     }
     for name, args in sigs.items():
         fn = getattr(L, name)
@@ -189,6 +191,14 @@ def rlxpp_test_to_lcg(d, carry, x, n, stream=None):
 
 def rlxpp_test_f64_from48(v, out, n, stream=None):
     _check(_lib.rlxpp_test_f64_from48(_ptr(v), _ptr(out), n, _stream(stream)))
+
+
+def rlxpp_seed_states_noalloc(levels, seeds, n_streams, out, level_of_stream=None, stream=None):
+    """Seeded state records written to caller-owned device memory, without any device
+    allocation (the library's fixed scratch array holds the level tables)."""
+    arr = (_u32 * max(1, len(levels)))(*levels)
+    _check(_lib.rlxpp_seed_states_noalloc(arr if len(levels) else None, len(levels), _ptr(level_of_stream),
+                                          _ptr(seeds), n_streams, _ptr(out), _stream(stream)))
 
 
 def rlxpp_luxury_multiplier(p):

@@ -214,6 +214,10 @@ rlxpp_status draw_common(rlxpp_gen* g, int kind, const int64_t* counts, const in
 
 }  // namespace
 
+rlxpp_status rlxpp::set_last_error(rlxpp_status code, const char* msg) {
+  return fail(code, msg);
+}
+
 extern "C" {
 
 rlxpp_status rlxpp_create(uint64_t n_streams, const uint32_t* levels, uint32_t n_levels,

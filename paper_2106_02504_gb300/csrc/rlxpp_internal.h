@@ -80,4 +80,7 @@ enum TestOp {
   kTestF64 = 5
 };
 
+// Records msg as the calling thread's rlxpp_last_error() text and returns code.
+rlxpp_status set_last_error(rlxpp_status code, const char* msg);
+
 }  // namespace rlxpp

@@ -4,6 +4,8 @@
 // Seeding and skipping follow Sec. 2.4: exponentiation by squaring, here with a
 // 4-bit fixed window whose powers A^(j 16^w) are tabulated once per luxury level, so
 // that a stream needs one modular product per non-zero exponent digit.
+#include <mutex>
+
 #include "rlxpp_arith.cuh"
 #include "rlxpp_internal.h"
 
@@ -335,3 +337,128 @@ cudaError_t launch_test(int which, const uint64_t* x, const uint64_t* y, uint64_
 }
 
 }  // namespace rlxpp
+
+// ---- seeding without allocation ---------------------------------------------------
+// A handle-free variant of k_seed for callers that must not allocate device memory.
+// Its scratch (the multiplier and the power table of each requested luxury level) lives
+// in one file-scope device array instead of memory from cudaMalloc.  The array exists
+// on every GPU that loads the library, for the life of the process, and is shared by
+// all calls: every call rewrites the tables it uses before reading them, and calls that
+// overlap on the GPU (different streams, different threads) race on it.
+
+namespace rlxpp {
+namespace {
+
+constexpr uint32_t kNoAllocMaxLevels = RLXPP_NOALLOC_MAX_LEVELS;
+constexpr size_t kNoAllocLevelLimbs = 18 + kTableLimbs;  // A, then the power table
+
+// 4 levels x (72 B + 46,080 B) = 184,608 bytes of device memory per GPU.
+static __device__ __align__(256) uint32_t g_noalloc_scratch[kNoAllocMaxLevels * kNoAllocLevelLimbs];
+
+struct LevelList {
+  uint32_t p[kNoAllocMaxLevels];
+  uint32_t n;
+};
+
+// Seeds n streams straight into caller-owned state records (pos 0).  A stream whose
+// level index is out of range gets an all-zero record (p = 0 marks it invalid).
+__global__ void k_seed_records(const uint32_t* __restrict__ scratch, LevelList lv,
+                               const uint64_t* __restrict__ seeds, const uint8_t* __restrict__ level_of,
+                               uint64_t n, rlxpp_state* __restrict__ out) {
+  const uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  uint64_t* rec = reinterpret_cast<uint64_t*>(out + i);
+  const uint32_t lvl = level_of ? level_of[i] : 0u;
+  if (lvl >= lv.n) {
+#pragma unroll
+    for (int k = 0; k < 11; ++k) rec[k] = 0;
+    return;
+  }
+  const uint32_t* T = scratch + (size_t)lvl * kNoAllocLevelLimbs + 18;
+  uint32_t X[kLimbs];
+  bool have = false;
+  apply_digits(T, kSeedWindow0, seeds[i], X, have);
+  if (!have) {
+#pragma unroll
+    for (int k = 0; k < kLimbs; ++k) X[k] = k == 0 ? 1u : 0u;
+  }
+  uint32_t D[kLimbs];
+  to_ranlux(X, D);
+#pragma unroll
+  for (int k = 0; k < 9; ++k) rec[k] = ((uint64_t)D[2 * k + 1] << 32) | D[2 * k];
+  rec[9] = carry_of(X, D);          // pos 0
+  rec[10] = lv.p[lvl];              // reserved 0
+}
+
+// Device address of g_noalloc_scratch, looked up once per device (with that device
+// current) the first time the entry point runs on it.
+constexpr int kMaxDevices = 64;
+std::mutex g_noalloc_mutex;
+uint32_t* g_noalloc_ptr[kMaxDevices] = {};
+
+rlxpp_status noalloc_scratch(uint32_t** out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return set_last_error(RLXPP_ERR_CUDA, cudaGetErrorString(e));
+  if (dev < 0 || dev >= kMaxDevices) return set_last_error(RLXPP_ERR_UNSUPPORTED, "device ordinal >= 64");
+  std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+  if (!g_noalloc_ptr[dev]) {
+    void* p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess || p == nullptr)
+      return set_last_error(RLXPP_ERR_CUDA, e != cudaSuccess ? cudaGetErrorString(e)
+                                                            : "no device address for the scratch array");
+    g_noalloc_ptr[dev] = static_cast<uint32_t*>(p);
+  }
+  *out = g_noalloc_ptr[dev];
+  return RLXPP_OK;
+}
+
+bool device_pointer(const void* p) {
+  cudaPointerAttributes attr;
+  if (cudaPointerGetAttributes(&attr, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return attr.type == cudaMemoryTypeDevice || attr.type == cudaMemoryTypeManaged;
+}
+
+}  // namespace
+}  // namespace rlxpp
+
+extern "C" rlxpp_status rlxpp_seed_states_noalloc(const uint32_t* levels, uint32_t n_levels,
+                                                   const uint8_t* level_of_stream, const uint64_t* seeds,
+                                                   uint64_t n_streams, rlxpp_state* out,
+                                                   void* cuda_stream) {
+  using namespace rlxpp;
+  if (!levels || n_levels == 0)
+    return set_last_error(RLXPP_ERR_INVALID, "need at least one luxury level");
+  if (n_levels > kNoAllocMaxLevels)
+    return set_last_error(RLXPP_ERR_INVALID,
+                          "rlxpp_seed_states_noalloc: more luxury levels than its fixed scratch holds "
+                          "(RLXPP_NOALLOC_MAX_LEVELS = 4)");
+  LevelList lv{};
+  lv.n = n_levels;
+  for (uint32_t l = 0; l < n_levels; ++l) {
+    if (levels[l] == 0) return set_last_error(RLXPP_ERR_INVALID, "luxury level must be >= 1");
+    lv.p[l] = levels[l];
+  }
+  if (n_streams == 0) return RLXPP_OK;
+  if (!seeds || !out) return set_last_error(RLXPP_ERR_INVALID, "null seeds or output");
+  if (!device_pointer(seeds) || !device_pointer(out) ||
+      (level_of_stream && !device_pointer(level_of_stream)))
+    return set_last_error(RLXPP_ERR_INVALID, "seeds, level indices and output must be device memory");
+  uint32_t* scratch = nullptr;
+  if (rlxpp_status s = noalloc_scratch(&scratch)) return s;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(cuda_stream);
+  for (uint32_t l = 0; l < n_levels; ++l) {
+    uint32_t* base = scratch + (size_t)l * kNoAllocLevelLimbs;
+    cudaError_t e = launch_level_setup(lv.p[l], base, base + 18, st);
+    if (e != cudaSuccess) return set_last_error(RLXPP_ERR_CUDA, cudaGetErrorString(e));
+  }
+  k_seed_records<<<grid_for(n_streams, 128), 128, 0, st>>>(scratch, lv, seeds, level_of_stream, n_streams,
+                                                           out);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return set_last_error(RLXPP_ERR_CUDA, cudaGetErrorString(e));
+  return RLXPP_OK;
+}

@@ -1,0 +1,63 @@
+"""rlxpp_seed_states_noalloc: seeding for callers that cannot allocate device memory
+(an application that owns the whole memory budget, or a path where the implicit
+synchronisation of cudaMalloc/cudaFree is not acceptable).  It must give exactly the
+records of the allocating path (rlxpp_create followed by rlxpp_get_state), on two calls
+in a row that reuse its fixed scratch array with different luxury levels.
+
+This file is named so that pytest collects it last."""
+import numpy as np
+import pytest
+
+from paper_2106_02504_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def native():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2106_02504_gb300 as P
+    return P.native
+
+
+def _records_allocating_path(native, levels, seeds_d, level_of_d, n):
+    g = native.Generator(n, levels, seeds_d, level_of_d)
+    ref = torch.zeros((n, 11), dtype=torch.int64, device="cuda")
+    g.get_state(ref)
+    g.sync()
+    g.close()
+    return ref
+
+
+def test_noalloc_seeding_matches_allocating_path(native):
+    n = 1000  # several 128-thread blocks and a ragged tail
+    calls = [([2048], 11, None),
+             ([24, 223, 389, 2048], 12, W.batch_mix(n, seed=13)[1])]
+    for levels, seed, level_of in calls:   # two calls in a row share the scratch array
+        seeds = W.random_seeds(n, seed)
+        seeds[:3] = [0, 1, 2 ** 64 - 1]
+        seeds_d = torch.from_numpy(seeds.view(np.int64)).cuda()
+        level_of_d = None if level_of is None else torch.from_numpy(level_of).cuda()
+        out = torch.full((n, 11), -1, dtype=torch.int64, device="cuda")
+        native.rlxpp_seed_states_noalloc(levels, seeds_d, n, out, level_of_d)
+        torch.cuda.synchronize()
+        ref = _records_allocating_path(native, levels, seeds_d, level_of_d, n)
+        assert torch.equal(out, ref), levels
+
+
+def test_noalloc_limits(native):
+    seeds = torch.ones(4, dtype=torch.int64, device="cuda")
+    out = torch.zeros((4, 11), dtype=torch.int64, device="cuda")
+    with pytest.raises(native.RlxppError) as e:
+        native.rlxpp_seed_states_noalloc([24, 48, 97, 223, 389], seeds, 4, out)   # 5 > 4 levels
+    assert e.value.status == native.RLXPP_ERR_INVALID
+    with pytest.raises(native.RlxppError):
+        native.rlxpp_seed_states_noalloc([2048], seeds.cpu(), 4, out)             # host seeds
+    # a level index beyond the list gives an all-zero (invalid, p = 0) record
+    lvl = torch.tensor([0, 1, 0, 0], dtype=torch.uint8, device="cuda")
+    native.rlxpp_seed_states_noalloc([2048], seeds, 4, out, lvl)
+    torch.cuda.synchronize()
+    assert int(out[1].abs().sum()) == 0 and int(out[0, 10]) == 2048
