@@ -47,7 +47,11 @@ def up_to_date():
 
 
 def build(force=False, verbose=False):
-    """Compile and link; returns the library path.  Raises on any compiler error."""
+    """Compile and link; returns the library path.  Raises on any compiler error.
+    Extra nvcc flags (e.g. -DRLXPP_DRAW_MIN_BLOCKS=8) can be given in RLXPP_NVCC_FLAGS;
+    a build with such flags is always redone."""
+    if os.environ.get("RLXPP_NVCC_FLAGS"):
+        force = True
     if not force and up_to_date():
         return LIB_PATH
     os.makedirs(OUT_DIR, exist_ok=True)
@@ -57,7 +61,8 @@ def build(force=False, verbose=False):
     for src in _sources():
         obj = os.path.join(OUT_DIR, os.path.basename(src).replace(".cu", ".o"))
         objs.append(obj)
-        cmd = [nvcc, *ARCH, *CFLAGS, "-c", src, "-o", obj]
+        extra = os.environ.get("RLXPP_NVCC_FLAGS", "").split()
+        cmd = [nvcc, *ARCH, *CFLAGS, *extra, "-c", src, "-o", obj]
         if verbose:
             cmd.insert(1, "-Xptxas=-v")
         procs.append((cmd, subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.STDOUT)))

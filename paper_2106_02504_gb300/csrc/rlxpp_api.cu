@@ -93,9 +93,20 @@ rlxpp_status setup_levels(rlxpp_gen* g, cudaStream_t st) {
                                        g->table + (size_t)l * kTableLimbs, st);
     if (e != cudaSuccess) return fail(RLXPP_ERR_CUDA, std::string("level setup: ") + cudaGetErrorString(e));
   }
-  RLX_CUDA(cudaMemcpyAsync(g->lux_host, g->lux, sizeof(uint32_t) * 18 * g->n_levels,
-                           cudaMemcpyDeviceToHost, st));
+  std::vector<uint32_t> limbs(18 * g->n_levels);
+  RLX_CUDA(cudaMemcpyAsync(limbs.data(), g->lux, sizeof(uint32_t) * limbs.size(), cudaMemcpyDeviceToHost, st));
   RLX_CUDA(cudaStreamSynchronize(st));
+  for (uint32_t l = 0; l < g->n_levels; ++l) {  // kernel-parameter form of each multiplier
+    Lux& x = g->lux_host[l];
+    std::memcpy(x.a, limbs.data() + 18 * l, sizeof x.a);
+    uint64_t carry = 0;
+    for (int k = 0; k < 9; ++k) {
+      const uint64_t t = (uint64_t)x.a[k] + x.a[9 + k] + carry;
+      x.as[k] = (uint32_t)t;
+      carry = t >> 32;
+    }
+    x.ca = (uint32_t)carry;
+  }
   return RLXPP_OK;
 }
 

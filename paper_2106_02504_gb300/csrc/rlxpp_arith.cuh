@@ -64,30 +64,100 @@ __device__ __forceinline__ uint32_t shr_pair(uint32_t lo, uint32_t hi, int s) {
 }
 
 // ---------------------------------------------------------------------------------
-// Sec. 2.1: p = a * b (576 x 576 -> 1152 bits), operand scanning.
-// Row i adds a_i * b shifted by i limbs: the 18 products a_i b_j + p_{i+j} fit in 64
-// bits each ((2^32-1)^2 + 2^32-1 < 2^64) and are independent; one carry chain then adds
-// the high half of product j-1 to the low half of product j.  After row i the partial
-// product (a mod 2^(32(i+1))) b fits in limbs 0..i+18, so no carry leaves limb i+18.
-// A is passed through an accessor so that a constant multiplier can stay in the
-// constant bank (kernel parameters) instead of registers.
+// Sec. 2.1: the 576 x 576 -> 1152-bit product.
+//
+// mul_9x9 multiplies two 9-limb (288-bit) numbers by operand scanning: row i adds
+// a_i * b shifted by i limbs; the 9 products a_i b_j + p_{i+j} fit in 64 bits each
+// ((2^32-1)^2 + 2^32-1 < 2^64) and are independent, and one carry chain adds the high
+// half of product j-1 to the low half of product j.  After row i the partial product
+// (a mod 2^(32(i+1))) b fits in limbs 0..i+9, so no carry leaves limb i+9.
+// The multiplier comes through an accessor so that a constant can stay in the constant
+// bank (kernel parameters) instead of registers.
 // ---------------------------------------------------------------------------------
 template <class AFn>
-__device__ __forceinline__ void multiply9x9(AFn a, const uint32_t b[kLimbs], uint32_t p[2 * kLimbs]) {
+__device__ __forceinline__ void mul_9x9(AFn a, const uint32_t* b, uint32_t* p) {
 #pragma unroll
-  for (int k = 0; k < 2 * kLimbs; ++k) p[k] = 0;
+  for (int k = 0; k < 18; ++k) p[k] = 0;
 #pragma unroll
-  for (int i = 0; i < kLimbs; ++i) {
+  for (int i = 0; i < 9; ++i) {
     const uint32_t ai = a(i);
-    uint64_t t[kLimbs];
+    uint64_t t[9];
 #pragma unroll
-    for (int j = 0; j < kLimbs; ++j) t[j] = mad_wide(ai, b[j], (uint64_t)p[i + j]);
+    for (int j = 0; j < 9; ++j) t[j] = mad_wide(ai, b[j], (uint64_t)p[i + j]);
     p[i] = lo32(t[0]);
     p[i + 1] = add_cc(lo32(t[1]), hi32(t[0]));
 #pragma unroll
-    for (int j = 2; j < kLimbs; ++j) p[i + j] = addc_cc(lo32(t[j]), hi32(t[j - 1]));
-    p[i + kLimbs] = addc(hi32(t[kLimbs - 1]), 0u);
+    for (int j = 2; j < 9; ++j) p[i + j] = addc_cc(lo32(t[j]), hi32(t[j - 1]));
+    p[i + 9] = addc(hi32(t[8]), 0u);
   }
+}
+
+// multiply9x9 with one level of Karatsuba (243 limb products instead of 324).  With
+// A = A1 2^288 + A0 and X = X1 2^288 + X0,
+//   A X = A1 X1 2^576 + ((A0 + A1)(X0 + X1) - A0 X0 - A1 X1) 2^288 + A0 X0.
+// The half sums carry one extra bit each: A0 + A1 = As + ca 2^288, X0 + X1 = Xs + cx 2^288,
+// so (A0 + A1)(X0 + X1) = As Xs + 2^288 (cx As + ca Xs) + ca cx 2^576 (below 2^578).
+// a(i), i < 18: limbs of A; as(i), i < 9: limbs of As; ca: its carry.
+template <class AFn, class ASFn>
+__device__ __forceinline__ void multiply9x9_split(AFn a, ASFn as, uint32_t ca, const uint32_t X[kLimbs],
+                                                  uint32_t P[2 * kLimbs]) {
+  uint32_t Xs[9];
+  Xs[0] = add_cc(X[0], X[9]);
+#pragma unroll
+  for (int k = 1; k < 9; ++k) Xs[k] = addc_cc(X[k], X[9 + k]);
+  const uint32_t cx = addc(0u, 0u);
+  uint32_t P0[18], P2[18], M[20];
+  mul_9x9([&](int i) { return a(i); }, X, P0);
+  mul_9x9([&](int i) { return a(9 + i); }, X + 9, P2);
+  mul_9x9(as, Xs, M);
+  // M += 2^288 (cx As + ca Xs) + ca cx 2^576
+  const uint32_t mx = 0u - cx;
+  M[9] = add_cc(M[9], as(0) & mx);
+#pragma unroll
+  for (int k = 1; k < 9; ++k) M[9 + k] = addc_cc(M[9 + k], as(k) & mx);
+  M[18] = addc(0u, 0u);
+  M[19] = 0u;
+  if (ca) {
+    M[9] = add_cc(M[9], Xs[0]);
+#pragma unroll
+    for (int k = 1; k < 9; ++k) M[9 + k] = addc_cc(M[9 + k], Xs[k]);
+    M[18] = addc_cc(M[18], cx);
+    M[19] = addc(0u, 0u);
+  }
+  // middle term M - A0 X0 - A1 X1 (non-negative, 20 limbs)
+  M[0] = sub_cc(M[0], P0[0]);
+#pragma unroll
+  for (int k = 1; k < 18; ++k) M[k] = subc_cc(M[k], P0[k]);
+  M[18] = subc_cc(M[18], 0u);
+  M[19] = subc(M[19], 0u);
+  M[0] = sub_cc(M[0], P2[0]);
+#pragma unroll
+  for (int k = 1; k < 18; ++k) M[k] = subc_cc(M[k], P2[k]);
+  M[18] = subc_cc(M[18], 0u);
+  M[19] = subc(M[19], 0u);
+  // P = A0 X0 + A1 X1 2^576 + middle 2^288
+#pragma unroll
+  for (int k = 0; k < 18; ++k) {
+    P[k] = P0[k];
+    P[18 + k] = P2[k];
+  }
+  P[9] = add_cc(P[9], M[0]);
+#pragma unroll
+  for (int k = 1; k < 20; ++k) P[9 + k] = addc_cc(P[9 + k], M[k]);
+#pragma unroll
+  for (int k = 29; k < 35; ++k) P[k] = addc_cc(P[k], 0u);
+  P[35] = addc(P[35], 0u);
+}
+
+// Both operands variable: the half sum of A is formed here.
+template <class AFn>
+__device__ __forceinline__ void multiply9x9(AFn a, const uint32_t X[kLimbs], uint32_t P[2 * kLimbs]) {
+  uint32_t As[9];
+  As[0] = add_cc(a(0), a(9));
+#pragma unroll
+  for (int k = 1; k < 9; ++k) As[k] = addc_cc(a(k), a(9 + k));
+  const uint32_t ca = addc(0u, 0u);
+  multiply9x9_split(a, [&](int i) { return As[i]; }, ca, X, P);
 }
 
 // ---------------------------------------------------------------------------------
@@ -166,23 +236,29 @@ __device__ __forceinline__ void mod_m(const uint32_t p[2 * kLimbs], uint32_t r[k
 #pragma unroll
   for (int k = 8; k < kLimbs; ++k) r[k] = addc_cc(R[k], 0u);
   c = addc(0u, 0u);
-  // fold 2: c (2^240 - 1), c in {0, 1}; when c = 1 the value is below 2^243.
-  const uint32_t cm = 0u - c;
-  r[0] = add_cc(r[0], cm);
+  // fold 2: c (2^240 - 1), c in {0, 1}; when c = 1 the value is below 2^243.  c = 1 needs
+  // the low part of R within t (2^240 - 1) of 2^576, so this branch is almost never taken.
+  if (c) {
+    r[0] = add_cc(r[0], 0xFFFFFFFFu);
 #pragma unroll
-  for (int k = 1; k < 7; ++k) r[k] = addc_cc(r[k], cm);
-  r[7] = addc(r[7], cm & 0xFFFFu);
-  // final correction: r >= m  <=>  r + (2^240 - 1) >= 2^576; then r - m = that sum mod 2^576
-  uint32_t e[kLimbs];
-  e[0] = add_cc(r[0], 0xFFFFFFFFu);
+    for (int k = 1; k < 7; ++k) r[k] = addc_cc(r[k], 0xFFFFFFFFu);
+    r[7] = addc(r[7], 0xFFFFu);
+  }
+  // final correction: r >= m  <=>  r + (2^240 - 1) >= 2^576; then r - m = that sum mod
+  // 2^576.  r >= m needs bits 240..575 of r all set, which is checked first.
+  uint32_t top = r[8] & r[9] & r[10] & r[11] & r[12] & r[13] & r[14] & r[15] & r[16] & r[17];
+  if (top == 0xFFFFFFFFu && r[7] >= 0xFFFF0000u) {
+    uint32_t e[kLimbs];
+    e[0] = add_cc(r[0], 0xFFFFFFFFu);
 #pragma unroll
-  for (int k = 1; k < 7; ++k) e[k] = addc_cc(r[k], 0xFFFFFFFFu);
-  e[7] = addc_cc(r[7], 0xFFFFu);
+    for (int k = 1; k < 7; ++k) e[k] = addc_cc(r[k], 0xFFFFFFFFu);
+    e[7] = addc_cc(r[7], 0xFFFFu);
 #pragma unroll
-  for (int k = 8; k < kLimbs; ++k) e[k] = addc_cc(r[k], 0u);
-  const uint32_t ge = addc(0u, 0u);
+    for (int k = 8; k < kLimbs; ++k) e[k] = addc_cc(r[k], 0u);
+    const uint32_t ge = addc(0u, 0u);
 #pragma unroll
-  for (int k = 0; k < kLimbs; ++k) r[k] = ge ? e[k] : r[k];
+    for (int k = 0; k < kLimbs; ++k) r[k] = ge ? e[k] : r[k];
+  }
 }
 
 // ---------------------------------------------------------------------------------
@@ -205,34 +281,41 @@ __device__ __forceinline__ void to_ranlux(const uint32_t X[kLimbs], uint32_t D[k
 #pragma unroll
   for (int k = kLimbs; k < 25; ++k) T[k] = subc_cc(__funnelshift_l(X[k - 8], X[k - 7], 16), 0u);
   T[25] = subc(X[17] >> 16, 0u);
-  // q1 = q0 + 1 (q0 = T >> 576, limbs 18..25, below 2^240)
-  uint32_t q1[8];
-  q1[0] = add_cc(T[18], 1u);
+  // q = q0 + 1 needs T_lo + (q0 + 1)(2^240 - 1) >= 2^576 with (q0 + 1)(2^240 - 1) < 2^480,
+  // so T_lo must have bits 480..575 all set (limbs 15..17 all ones); only then is the
+  // exact test run (probability about 2^-96 for a random state).
+  if ((T[15] & T[16] & T[17]) == 0xFFFFFFFFu) {
+    uint32_t q1[8];  // q0 + 1 (q0 = T >> 576, limbs 18..25, below 2^240)
+    q1[0] = add_cc(T[18], 1u);
 #pragma unroll
-  for (int k = 1; k < 8; ++k) q1[k] = addc_cc(T[18 + k], 0u);
-  // F = T_lo - q1 + (q1 << 240): compare against 2^576 through the net carry
-  uint32_t F[kLimbs];
-  F[0] = sub_cc(T[0], q1[0]);
+    for (int k = 1; k < 8; ++k) q1[k] = addc_cc(T[18 + k], 0u);
+    // F = T_lo - q1 + (q1 << 240): compare against 2^576 through the net carry
+    uint32_t F[kLimbs];
+    F[0] = sub_cc(T[0], q1[0]);
 #pragma unroll
-  for (int k = 1; k < 8; ++k) F[k] = subc_cc(T[k], q1[k]);
+    for (int k = 1; k < 8; ++k) F[k] = subc_cc(T[k], q1[k]);
 #pragma unroll
-  for (int k = 8; k < kLimbs; ++k) F[k] = subc_cc(T[k], 0u);
-  const uint32_t borrow = subc(0u, 0u);  // 0 or 0xFFFFFFFF
-  // q1 << 240 occupies limbs 7..15 (q1 <= 2^240): limb 7 + k holds the top 16 bits of
-  // q1[k-1] and the low 16 bits of q1[k], limb 15 the top 16 bits of q1[7].
-  uint32_t dummy = add_cc(F[7], q1[0] << 16);
-  (void)dummy;
+    for (int k = 8; k < kLimbs; ++k) F[k] = subc_cc(T[k], 0u);
+    const uint32_t borrow = subc(0u, 0u);  // 0 or 0xFFFFFFFF
+    // q1 << 240 occupies limbs 7..15 (q1 <= 2^240): limb 7 + k holds the top 16 bits of
+    // q1[k-1] and the low 16 bits of q1[k], limb 15 the top 16 bits of q1[7].
+    uint32_t dummy = add_cc(F[7], q1[0] << 16);
 #pragma unroll
-  for (int k = 8; k < 15; ++k) dummy = addc_cc(F[k], __funnelshift_l(q1[k - 8], q1[k - 7], 16));
-  dummy = addc_cc(F[15], q1[7] >> 16);
-  dummy = addc_cc(F[16], 0u);
-  dummy = addc_cc(F[17], 0u);
-  const uint32_t carry = addc(0u, 0u);
-  // overflow of F past 2^576 = carry - borrow_bit; q = q0 + 1 iff it is +1
-  const bool up = (carry == 1u) && (borrow == 0u);
-  D[0] = add_cc(X[0], up ? q1[0] : T[18]);
+    for (int k = 8; k < 15; ++k) dummy = addc_cc(F[k], __funnelshift_l(q1[k - 8], q1[k - 7], 16));
+    dummy = addc_cc(F[15], q1[7] >> 16);
+    dummy = addc_cc(F[16], 0u);
+    dummy = addc_cc(F[17], 0u);
+    (void)dummy;
+    const uint32_t carry = addc(0u, 0u);
+    // overflow of F past 2^576 = carry - borrow bit; q = q0 + 1 iff it is +1
+    if (carry == 1u && borrow == 0u) {
 #pragma unroll
-  for (int k = 1; k < 8; ++k) D[k] = addc_cc(X[k], up ? q1[k] : T[18 + k]);
+      for (int k = 0; k < 8; ++k) T[18 + k] = q1[k];
+    }
+  }
+  D[0] = add_cc(X[0], T[18]);
+#pragma unroll
+  for (int k = 1; k < 8; ++k) D[k] = addc_cc(X[k], T[18 + k]);
 #pragma unroll
   for (int k = 8; k < kLimbs - 1; ++k) D[k] = addc_cc(X[k], 0u);
   D[kLimbs - 1] = addc(X[kLimbs - 1], 0u);
@@ -282,11 +365,21 @@ __device__ __forceinline__ uint64_t bits48(const uint32_t D[kLimbs], int j) {
 
 // 48-bit integer v -> the double v 2^-48 in [0, 1), built with integer operations only
 // (the GPU's FP64 pipe is narrow; the conversion is exact because v < 2^53).  The
-// leading one of v is moved to bit 52, the exponent field is set so that the value
-// reads v 2^-48, and v = 0 maps to +0.0.
+// leading one of v is moved to bit 52 and the exponent field is set so that the value
+// reads v 2^-48: with lz leading zeros in the 64-bit v, the shift is s = lz - 11 and
+// the biased exponent 1038 - lz (the leading one itself adds 1 to the field when
+// (1026 - s) << 52 is added).  v = 0 maps to +0.0.
 __device__ __forceinline__ uint64_t f64_bits_from48(uint64_t v) {
-  const int lz = __clzll((long long)v);          // 16..64
-  const int s = lz - 11;                         // shift that puts the leading 1 at bit 52
+  const uint32_t hi = (uint32_t)(v >> 32), lo = (uint32_t)v;
+  if (hi != 0u) {  // 2^32 <= v < 2^48 (all but a 2^-16 share of the values)
+    const uint32_t lz = __clz(hi);  // 16..31, the leading zeros of v as a 64-bit word
+    const uint32_t s = lz - 11u;    // 5..20
+    const uint32_t mh = __funnelshift_l(lo, hi, s);
+    const uint32_t ml = lo << s;
+    return ((uint64_t)(mh + ((1037u - lz) << 20)) << 32) | ml;
+  }
+  const int lz = __clzll((long long)v);  // 32..64
+  const int s = lz - 11;
   const uint64_t mant = v << (s & 63);
   const uint64_t bits = mant + ((uint64_t)(1026 - s) << 52);
   return v ? bits : 0ull;

@@ -11,6 +11,12 @@
 #include "rlxpp_arith.cuh"
 #include "rlxpp_internal.h"
 
+// Resident 128-thread blocks per SM the single-level draw kernels are compiled for
+// (caps their registers at 65536 / (128 * blocks)).
+#ifndef RLXPP_DRAW_MIN_BLOCKS
+#define RLXPP_DRAW_MIN_BLOCKS 6
+#endif
+
 namespace rlxpp {
 namespace {
 
@@ -132,7 +138,7 @@ struct Consumer<kDrawSumHist> {
 };
 
 template <int Kind, bool Uniform>
-__global__ void __launch_bounds__(kDrawBlock) k_draw(const DrawArgs a) {
+__global__ void __launch_bounds__(kDrawBlock, Uniform ? RLXPP_DRAW_MIN_BLOCKS : 4) k_draw(const DrawArgs a) {
   constexpr int kWarps = kDrawBlock / 32;
   __shared__ unsigned int hist_s[Kind == kDrawSumHist ? kWarps * 256 : 1];
   if (Kind == kDrawSumHist) {
@@ -170,7 +176,16 @@ __global__ void __launch_bounds__(kDrawBlock) k_draw(const DrawArgs a) {
         Areg[2 * k + 1] = t.y;
       }
     }
+    uint32_t ASreg[9], careg = 0;
+    if (!Uniform) {  // half sum of A for the Karatsuba product
+      ASreg[0] = add_cc(Areg[0], Areg[9]);
+#pragma unroll
+      for (int k = 1; k < 9; ++k) ASreg[k] = addc_cc(Areg[k], Areg[9 + k]);
+      careg = addc(0u, 0u);
+    }
     auto A = [&](int k) { return Uniform ? a.A.a[k] : Areg[k]; };
+    auto AS = [&](int k) { return Uniform ? a.A.as[k] : ASreg[k]; };
+    const uint32_t ca = Uniform ? a.A.ca : careg;
 
     Consumer<Kind> out;
     if constexpr (Kind == kDrawU24) out.out = static_cast<uint32_t*>(a.out);
@@ -201,7 +216,7 @@ __global__ void __launch_bounds__(kDrawBlock) k_draw(const DrawArgs a) {
 #pragma unroll 1
       while (true) {
         uint32_t P[2 * kLimbs];
-        multiply9x9(A, X, P);
+        multiply9x9_split(A, AS, ca, X, P);
         mod_m(P, X);
         to_ranlux(X, D);
         const int64_t rem = cnt - k;

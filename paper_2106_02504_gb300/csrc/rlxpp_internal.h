@@ -27,7 +27,9 @@ __host__ __device__ inline uint32_t meta_carry(uint32_t m) { return (m >> 8) & 1
 __host__ __device__ inline uint32_t meta_level(uint32_t m) { return (m >> 16) & 0xFFu; }
 
 struct Lux {  // a luxury multiplier in kernel-parameter (constant bank) form
-  uint32_t a[18];
+  uint32_t a[18];   // A, 32-bit limbs
+  uint32_t as[9];   // A0 + A1 mod 2^288 (A = A1 2^288 + A0), for the Karatsuba product
+  uint32_t ca;      // carry of A0 + A1
 };
 
 struct StateView {
