@@ -119,6 +119,76 @@ rlxpp_status rlxpp_draw_f64(rlxpp_gen* gen, const int64_t* counts, const int64_t
 rlxpp_status rlxpp_draw_f64_sum_hist(rlxpp_gen* gen, int64_t count_each, uint64_t* sums,
                                      uint64_t* hist, void* cuda_stream);
 
+/* ---- batched requests (uneven counts, mixed levels and kinds, sequence splitting) ----
+ * A request draws `count` values of one kind from one stream, starting `skip` LCG
+ * advances after the stream's current state, at read position `pos` of that block
+ * (pos = the stream's own position with skip = 0 continues it exactly; rlxpp_get_state
+ * reports positions).  Requests are independent: several may name the same stream
+ * (each reads its own part of the sequence) and none needs another to finish first.
+ *
+ * The library splits every request into chunks of at most L refills and starts each
+ * chunk from its own block by jump-ahead (X <- A^b X over the power table, Sec. 2.4),
+ * so a long request runs on many threads; chunks are ordered longest first and taken
+ * from a device work queue by a persistent kernel.  L and the grid are chosen by the
+ * handle's tuner (rlxpp_autotune_requests) or by defaults. */
+#define RLXPP_KIND_U24 0u
+#define RLXPP_KIND_F64 1u
+#define RLXPP_REQ_ADVANCE 1u /* flag: move each stream to the end of its request (at most
+                                one request per stream); otherwise states are unchanged */
+
+typedef struct rlxpp_request {
+  uint64_t stream; /* stream index < n_streams                                       */
+  uint64_t skip;   /* LCG advances (blocks) between the current state and the start  */
+  uint32_t pos;    /* numbers of the start block already consumed, 0..24             */
+  uint32_t kind;   /* RLXPP_KIND_U24 (uint32 out) or RLXPP_KIND_F64 (double out)       */
+  int64_t count;   /* values to draw, >= 0                                           */
+  uint64_t offset; /* index of the first value in out_u24 or out_f64 (by kind)       */
+} rlxpp_request;   /* 40 bytes */
+
+typedef struct rlxpp_tuning {
+  uint32_t chunk_blocks;  /* L: refills per chunk, >= 2                                  */
+  uint32_t blocks_per_sm; /* persistent grid = blocks_per_sm x SMs blocks of 128 threads */
+} rlxpp_tuning;
+
+typedef struct rlxpp_plan rlxpp_plan;
+
+/* Plan requests (host array reqs[n_reqs]): validates them (stream < n_streams,
+ * pos <= 24, kind, count >= 0, skip + refills < 2^64, no stream twice with
+ * RLXPP_REQ_ADVANCE), splits them into chunks and uploads the work list to device
+ * memory owned by the plan.  tuning: NULL = the handle's tuned choice for requests of
+ * this shape, else the defaults.  Synchronous; the plan belongs to `gen`. */
+rlxpp_status rlxpp_plan_requests(rlxpp_gen* gen, const rlxpp_request* reqs, uint64_t n_reqs,
+                                 uint32_t flags, const rlxpp_tuning* tuning, rlxpp_plan** out);
+
+/* Run a plan: out_u24 / out_f64 are device arrays large enough for every request's
+ * offset + count of its kind (NULL allowed when no request has that kind).  Issues
+ * only kernel launches and one memset on cuda_stream (no allocation, no host
+ * synchronisation), so it can be captured in a CUDA graph and replayed; every run
+ * recomputes the same values unless RLXPP_REQ_ADVANCE moved the streams. */
+rlxpp_status rlxpp_run_plan(rlxpp_gen* gen, const rlxpp_plan* plan, uint32_t* out_u24,
+                            double* out_f64, void* cuda_stream);
+
+/* Work items (chunks) of a plan, and its tuning. */
+uint64_t rlxpp_plan_items(const rlxpp_plan* plan);
+rlxpp_tuning rlxpp_plan_tuning(const rlxpp_plan* plan);
+
+void rlxpp_destroy_plan(rlxpp_plan* plan);
+
+/* plan + run + destroy in one call. */
+rlxpp_status rlxpp_draw_requests(rlxpp_gen* gen, const rlxpp_request* reqs, uint64_t n_reqs,
+                                 uint32_t* out_u24, double* out_f64, uint32_t flags,
+                                 void* cuda_stream);
+
+/* Tuner: times candidate (chunk length, grid) pairs on these requests (without
+ * RLXPP_REQ_ADVANCE, so the streams do not move; the outputs are overwritten) and
+ * keeps the fastest for requests of the same shape (log2 buckets of the request count
+ * and of the total refills).  The choice is kept in the handle and, when the
+ * environment variable RLXPP_TUNE_CACHE names a file, appended there and read back
+ * by later handles on the same device model.  best may be NULL. */
+rlxpp_status rlxpp_autotune_requests(rlxpp_gen* gen, const rlxpp_request* reqs, uint64_t n_reqs,
+                                     uint32_t* out_u24, double* out_f64, void* cuda_stream,
+                                     rlxpp_tuning* best);
+
 /* Export / import the state of every stream (Sec. 4.2: the state is plain memory that
  * can move between host and device and continue the same sequence).  dst/src:
  * n_streams records, host or device.  Import checks each record on the device:

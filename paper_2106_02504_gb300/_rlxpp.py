@@ -27,6 +27,22 @@ class RlxppState(ctypes.Structure):
 STATE_BYTES = ctypes.sizeof(RlxppState)
 assert STATE_BYTES == 88
 
+
+class RlxppTuning(ctypes.Structure):
+    """struct rlxpp_tuning."""
+    _fields_ = [("chunk_blocks", ctypes.c_uint32), ("blocks_per_sm", ctypes.c_uint32)]
+
+
+RLXPP_KIND_U24, RLXPP_KIND_F64 = 0, 1
+RLXPP_REQ_ADVANCE = 1
+
+
+def request_dtype():
+    """numpy dtype laid out like struct rlxpp_request (40 bytes)."""
+    import numpy as np
+    return np.dtype([("stream", "<u8"), ("skip", "<u8"), ("pos", "<u4"), ("kind", "<u4"),
+                     ("count", "<i8"), ("offset", "<u8")])
+
 RLXPP_OK, RLXPP_ERR_INVALID, RLXPP_ERR_NOMEM, RLXPP_ERR_CUDA, RLXPP_ERR_TIMEOUT, \
     RLXPP_ERR_UNSUPPORTED = range(6)
 RLXPP_MAX_LEVELS = 16
@@ -63,6 +79,10 @@ def _load():
         "rlxpp_test_f64_from48": [_vp, _vp, _u64, _vp],
         "rlxpp_luxury_multiplier": [_u32, _vp],
         "rlxpp_seed_states_noalloc": [_vp, _u32, _vp, _vp, _u64, _vp, _vp],
+        "rlxpp_plan_requests": [_vp, _vp, _u64, _u32, _vp, ctypes.POINTER(_vp)],
+        "rlxpp_run_plan": [_vp, _vp, _vp, _vp, _vp],
+        "rlxpp_draw_requests": [_vp, _vp, _u64, _vp, _vp, _u32, _vp],
+        "rlxpp_autotune_requests": [_vp, _vp, _u64, _vp, _vp, _vp, _vp],
     }
     for name, args in sigs.items():
         fn = getattr(L, name)
@@ -74,6 +94,12 @@ def _load():
     L.rlxpp_last_error.restype = ctypes.c_char_p
     L.rlxpp_destroy.argtypes = [_vp]
     L.rlxpp_destroy.restype = None
+    L.rlxpp_plan_items.argtypes = [_vp]
+    L.rlxpp_plan_items.restype = _u64
+    L.rlxpp_plan_tuning.argtypes = [_vp]
+    L.rlxpp_plan_tuning.restype = RlxppTuning
+    L.rlxpp_destroy_plan.argtypes = [_vp]
+    L.rlxpp_destroy_plan.restype = None
     return L
 
 
@@ -201,6 +227,63 @@ def rlxpp_seed_states_noalloc(levels, seeds, n_streams, out, level_of_stream=Non
                                           _ptr(seeds), n_streams, _ptr(out), _stream(stream)))
 
 
+def _requests(reqs):
+    import numpy as np
+    a = np.ascontiguousarray(reqs)
+    if a.dtype != request_dtype():
+        raise TypeError("requests must use request_dtype()")
+    return a, len(a)
+
+
+def _tuning(t):
+    if t is None:
+        return None
+    if isinstance(t, RlxppTuning):
+        return ctypes.byref(t)
+    return ctypes.byref(RlxppTuning(*t))
+
+
+def rlxpp_plan_requests(gen, reqs, flags=0, tuning=None):
+    """Returns a plan handle (int).  reqs: numpy array of request_dtype() (host)."""
+    a, n = _requests(reqs)
+    h = _vp()
+    _check(_lib.rlxpp_plan_requests(gen, a.ctypes.data if n else None, n, flags, _tuning(tuning),
+                                    ctypes.byref(h)))
+    return h.value
+
+
+def rlxpp_run_plan(gen, plan, out_u24=None, out_f64=None, stream=None):
+    _check(_lib.rlxpp_run_plan(gen, plan, _ptr(out_u24), _ptr(out_f64), _stream(stream)))
+
+
+def rlxpp_plan_items(plan):
+    return int(_lib.rlxpp_plan_items(plan))
+
+
+def rlxpp_plan_tuning(plan):
+    t = _lib.rlxpp_plan_tuning(plan)
+    return (t.chunk_blocks, t.blocks_per_sm)
+
+
+def rlxpp_destroy_plan(plan):
+    _lib.rlxpp_destroy_plan(plan)
+
+
+def rlxpp_draw_requests(gen, reqs, out_u24=None, out_f64=None, flags=0, stream=None):
+    a, n = _requests(reqs)
+    _check(_lib.rlxpp_draw_requests(gen, a.ctypes.data if n else None, n, _ptr(out_u24), _ptr(out_f64),
+                                    flags, _stream(stream)))
+
+
+def rlxpp_autotune_requests(gen, reqs, out_u24=None, out_f64=None, stream=None):
+    """Returns the chosen (chunk_blocks, blocks_per_sm)."""
+    a, n = _requests(reqs)
+    t = RlxppTuning()
+    _check(_lib.rlxpp_autotune_requests(gen, a.ctypes.data if n else None, n, _ptr(out_u24), _ptr(out_f64),
+                                        _stream(stream), ctypes.byref(t)))
+    return (t.chunk_blocks, t.blocks_per_sm)
+
+
 def rlxpp_luxury_multiplier(p):
     """A = a^p mod m as a Python int (computed on the device)."""
     out = (ctypes.c_uint64 * 9)()
@@ -227,6 +310,9 @@ class Generator:
 
     def draw_f64(self, out, count_each=0, counts=None, offsets=None, stream=None):
         rlxpp_draw_f64(self.handle, out, count_each, counts, offsets, stream)
+
+    def draw_requests(self, reqs, out_u24=None, out_f64=None, flags=0, stream=None):
+        rlxpp_draw_requests(self.handle, reqs, out_u24, out_f64, flags, stream)
 
     def draw_f64_sum_hist(self, count_each, sums, hist, stream=None):
         rlxpp_draw_f64_sum_hist(self.handle, count_each, sums, hist, stream)

@@ -10,23 +10,6 @@
 
 using namespace rlxpp;
 
-struct rlxpp_gen {
-  int device = 0;
-  uint64_t n = 0;
-  uint32_t n_levels = 0;
-  uint32_t levels[RLXPP_MAX_LEVELS] = {};
-  Lux lux_host[RLXPP_MAX_LEVELS] = {};
-  uint64_t* D = nullptr;        // [9][n]
-  uint32_t* meta = nullptr;     // [n]
-  uint32_t* lux = nullptr;      // [n_levels][18]
-  uint32_t* table = nullptr;    // [n_levels][kTableLimbs]
-  uint32_t* level_p = nullptr;  // [n_levels]
-  int* status = nullptr;        // sticky device status
-  cudaStream_t copy_stream = nullptr;  // device-to-host copies of chunked host output
-  cudaEvent_t ev[4] = {};
-  StateView view() const { return StateView{D, meta, n, n, lux, table, status}; }
-};
-
 namespace {
 
 thread_local std::string g_last_error;
@@ -249,6 +232,9 @@ rlxpp_status rlxpp_create(uint64_t n_streams, const uint32_t* levels, uint32_t n
     return s;
   };
   if (cudaGetDevice(&g->device) != cudaSuccess) return bail(fail(RLXPP_ERR_CUDA, "no CUDA device"));
+  if (cudaDeviceGetAttribute(&g->sms, cudaDevAttrMultiProcessorCount, g->device) != cudaSuccess)
+    return bail(fail(RLXPP_ERR_CUDA, "cannot read the multiprocessor count"));
+  load_tune_cache(g);
   g->n = n_streams;
   g->n_levels = n_levels;
   std::memcpy(g->levels, levels, sizeof(uint32_t) * n_levels);

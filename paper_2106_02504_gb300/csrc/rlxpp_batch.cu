@@ -1,0 +1,440 @@
+// Batched requests: many streams, uneven counts, mixed luxury levels and output kinds,
+// and long requests split into chunks that start by jump-ahead.
+//
+// A request (stream, skip, pos, kind, count, offset) reads a contiguous part of one
+// stream's sequence.  The host planner cuts it into chunks of at most L refills; chunk
+// j starts from block b_j of that stream, whose LCG state is A^(b_j) X (fixed-window
+// exponentiation over the power table, Sec. 2.4: one product per non-zero 4-bit digit
+// of b_j), so every chunk is independent.  Chunks are sorted longest first and taken
+// 32 at a time by the warps of a persistent kernel from a device counter; each thread
+// then runs the same refill loop as the plain draw kernels.  Reading the stream states
+// through a snapshot taken at the start of the run keeps chunks independent of the
+// write-back of the final states.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <fstream>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "rlxpp_arith.cuh"
+#include "rlxpp_drawloop.cuh"
+#include "rlxpp_internal.h"
+#include "rlxpp_state.cuh"
+
+namespace rlxpp {
+namespace {
+
+constexpr int kReqBlock = 128;
+
+struct Item {       // one chunk (32 bytes)
+  uint64_t jump;    // LCG advances from the request's start state to this chunk's block
+  int64_t count;    // values
+  uint64_t out;     // index of the first value in the output array of its kind
+  uint32_t req;     // request index
+  uint32_t info;    // bit 0: kind (1 = f64); bits 8..15: read position; bit 16: last chunk
+};
+
+struct BatchArgs {
+  const Item* items;
+  uint64_t n_items;
+  const uint64_t* req_stream;  // [n_reqs]
+  uint64_t* snap_D;            // [9][n_reqs]
+  uint32_t* snap_meta;         // [n_reqs]
+  uint64_t n_reqs;
+  StateView s;                 // resident states (final states are written back here)
+  uint32_t* out_u24;
+  uint64_t* out_f64;
+  unsigned long long* counter;
+  int advance;
+};
+
+// Copy the state of each request's stream (before any chunk runs).
+__global__ void k_snapshot(BatchArgs b) {
+  const uint64_t r = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= b.n_reqs) return;
+  const uint64_t st = b.req_stream[r];
+#pragma unroll
+  for (int k = 0; k < 9; ++k) b.snap_D[(uint64_t)k * b.n_reqs + r] = b.s.D[(uint64_t)k * b.s.stride + st];
+  b.snap_meta[r] = b.s.meta[st];
+}
+
+__device__ __forceinline__ void run_item(const BatchArgs& b, const Item& it) {
+  const uint32_t r = it.req;
+  const uint32_t meta = b.snap_meta[r];
+  const uint32_t lvl = meta_level(meta);
+  uint32_t D[kLimbs];
+#pragma unroll
+  for (int k = 0; k < 9; ++k) {
+    const uint64_t v = b.snap_D[(uint64_t)k * b.n_reqs + r];
+    D[2 * k] = (uint32_t)v;
+    D[2 * k + 1] = (uint32_t)(v >> 32);
+  }
+  uint32_t c = meta_carry(meta);
+  if (it.jump) {  // X <- A^jump X
+    uint32_t X[kLimbs];
+    to_lcg(D, c, X);
+    bool have = true;
+    apply_digits(b.s.table + (size_t)lvl * kTableLimbs, 0, it.jump, X, have);
+    to_ranlux(X, D);
+    c = carry_of(X, D);
+  }
+  uint32_t Areg[kLimbs], ASreg[9];
+  load18(b.s.lux + (size_t)lvl * kLimbs, Areg);
+  ASreg[0] = add_cc(Areg[0], Areg[9]);
+#pragma unroll
+  for (int k = 1; k < 9; ++k) ASreg[k] = addc_cc(Areg[k], Areg[9 + k]);
+  const uint32_t ca = addc(0u, 0u);
+  auto A = [&](int k) { return Areg[k]; };
+  auto AS = [&](int k) { return ASreg[k]; };
+  uint32_t pos = (it.info >> 8) & 0xFFu;
+  if (it.info & 1u) {
+    Consumer<kDrawF64> o;
+    o.out = b.out_f64;
+    draw_stream<kDrawF64>(o, D, c, pos, A, AS, ca, it.count, (int64_t)it.out);
+  } else {
+    Consumer<kDrawU24> o;
+    o.out = b.out_u24;
+    draw_stream<kDrawU24>(o, D, c, pos, A, AS, ca, it.count, (int64_t)it.out);
+  }
+  if (b.advance && ((it.info >> 16) & 1u)) {
+    const uint64_t st = b.req_stream[r];
+#pragma unroll
+    for (int q = 0; q < 9; ++q) b.s.D[(uint64_t)q * b.s.stride + st] = ((uint64_t)D[2 * q + 1] << 32) | D[2 * q];
+    b.s.meta[st] = meta_pack(pos, c, lvl);
+  }
+}
+
+// Persistent: each warp takes the next 32 chunks of the (longest-first) list.
+__global__ void __launch_bounds__(kReqBlock, 4) k_requests(BatchArgs b) {
+  const int lane = threadIdx.x & 31;
+  while (true) {
+    unsigned long long base = 0;
+    if (lane == 0) base = atomicAdd(b.counter, 32ull);
+    base = __shfl_sync(0xFFFFFFFFu, base, 0);
+    if (base >= b.n_items) break;
+    const uint64_t idx = base + (uint64_t)lane;
+    if (idx < b.n_items) run_item(b, b.items[idx]);
+  }
+}
+
+uint32_t log2_floor(uint64_t v) {
+  uint32_t r = 0;
+  while (v > 1) {
+    v >>= 1;
+    ++r;
+  }
+  return r;
+}
+
+// Request-shape signature: log2 buckets of the request count and of the total refills.
+uint32_t shape_signature(uint64_t n_reqs, uint64_t refills) {
+  return (log2_floor(n_reqs + 1) << 8) | log2_floor(refills + 1);
+}
+
+std::mutex g_cache_mutex;
+
+std::string device_key(const rlxpp_gen* g) {
+  cudaDeviceProp prop;
+  if (cudaGetDeviceProperties(&prop, g->device) != cudaSuccess) return "unknown";
+  return std::string(prop.name) + "/" + std::to_string(prop.multiProcessorCount);
+}
+
+void append_cache_line(const rlxpp_gen* g, uint32_t sig, const rlxpp_tuning& t) {
+  const char* path = std::getenv("RLXPP_TUNE_CACHE");
+  if (!path || !*path) return;
+  std::lock_guard<std::mutex> lock(g_cache_mutex);
+  std::ofstream f(path, std::ios::app);
+  if (f) f << device_key(g) << "|" << sig << "|" << t.chunk_blocks << "|" << t.blocks_per_sm << "\n";
+}
+
+// Refills a request needs after its start block.
+uint64_t request_refills(const rlxpp_request& q) {
+  const uint32_t need = q.kind == RLXPP_KIND_F64 ? 2 : 1;
+  const uint32_t per = kWords / need;
+  const uint64_t room = q.pos + need <= (uint32_t)kWords ? (kWords - q.pos) / need : 0;
+  const uint64_t count = (uint64_t)q.count;
+  const uint64_t head = std::min<uint64_t>(count, room);
+  return (count - head + per - 1) / per;
+}
+
+}  // namespace
+
+void load_tune_cache(rlxpp_gen* g) {
+  const char* path = std::getenv("RLXPP_TUNE_CACHE");
+  if (!path || !*path) return;
+  std::lock_guard<std::mutex> lock(g_cache_mutex);
+  std::ifstream f(path);
+  if (!f) return;
+  const std::string key = device_key(g);
+  std::string line;
+  while (std::getline(f, line)) {
+    // <device>/<sms>|<signature>|<chunk_blocks>|<blocks_per_sm>
+    const size_t a = line.find('|');
+    if (a == std::string::npos || line.compare(0, a, key) != 0) continue;
+    unsigned sig = 0, L = 0, bps = 0;
+    if (std::sscanf(line.c_str() + a + 1, "%u|%u|%u", &sig, &L, &bps) == 3 && L >= 2 && bps >= 1 && bps <= 8)
+      g->tuned[sig] = rlxpp_tuning{L, bps};  // later lines win
+  }
+}
+
+}  // namespace rlxpp
+
+using namespace rlxpp;
+
+struct rlxpp_plan {
+  rlxpp_gen* gen = nullptr;
+  uint64_t n_items = 0, n_reqs = 0;
+  uint32_t flags = 0;
+  rlxpp_tuning tuning{};
+  bool has_u24 = false, has_f64 = false;
+  Item* items = nullptr;
+  uint64_t* req_stream = nullptr;  // [n_reqs] stream of each request
+  uint64_t* snap_D = nullptr;
+  uint32_t* snap_meta = nullptr;
+  unsigned long long* counter = nullptr;
+};
+
+namespace {
+
+void free_plan(rlxpp_plan* p, cudaStream_t st, bool async) {
+  if (!p) return;
+  void* ptrs[] = {p->items, p->req_stream, p->snap_D, p->snap_meta, p->counter};
+  for (void* q : ptrs)
+    if (q) async ? cudaFreeAsync(q, st) : cudaFree(q);
+  delete p;
+}
+
+rlxpp_status plan_impl(rlxpp_gen* g, const rlxpp_request* reqs, uint64_t n_reqs, uint32_t flags,
+                       const rlxpp_tuning* tuning, rlxpp_plan** out) {
+  if (!out) return set_last_error(RLXPP_ERR_INVALID, "null plan output");
+  *out = nullptr;
+  if (!g) return set_last_error(RLXPP_ERR_INVALID, "null generator handle");
+  if (n_reqs && !reqs) return set_last_error(RLXPP_ERR_INVALID, "null requests");
+  if (flags & ~RLXPP_REQ_ADVANCE) return set_last_error(RLXPP_ERR_INVALID, "unknown flags");
+  if (cudaSetDevice(g->device) != cudaSuccess) return set_last_error(RLXPP_ERR_CUDA, "cudaSetDevice failed");
+  uint64_t total_refills = 0;
+  std::vector<uint8_t> seen((flags & RLXPP_REQ_ADVANCE) ? g->n : 0, 0);
+  for (uint64_t r = 0; r < n_reqs; ++r) {
+    const rlxpp_request& q = reqs[r];
+    if (q.stream >= g->n || q.pos > (uint32_t)kWords || q.count < 0 ||
+        (q.kind != RLXPP_KIND_U24 && q.kind != RLXPP_KIND_F64))
+      return set_last_error(RLXPP_ERR_INVALID, ("bad request " + std::to_string(r)).c_str());
+    const uint64_t nr = request_refills(q);
+    if (q.skip > ~uint64_t(0) - nr - 1)
+      return set_last_error(RLXPP_ERR_INVALID, "request reaches past 2^64 blocks");
+    if (flags & RLXPP_REQ_ADVANCE) {
+      if (seen[q.stream]) return set_last_error(RLXPP_ERR_INVALID, "stream requested twice with RLXPP_REQ_ADVANCE");
+      seen[q.stream] = 1;
+    }
+    total_refills += nr;
+  }
+  rlxpp_tuning t{};
+  if (tuning) {
+    t = *tuning;
+  } else {
+    auto it = g->tuned.find(shape_signature(n_reqs, total_refills));
+    if (it != g->tuned.end()) {
+      t = it->second;
+    } else {  // default: enough chunks to fill the GPU, at most 256 refills each
+      const uint64_t threads = (uint64_t)std::max(1, g->sms) * 4 * kReqBlock;
+      uint64_t L = total_refills / std::max<uint64_t>(threads, 1);
+      uint32_t p2 = 4;
+      while (p2 < L && p2 < 256) p2 <<= 1;
+      t = rlxpp_tuning{p2, 4};
+    }
+  }
+  if (t.chunk_blocks < 2 || t.blocks_per_sm < 1 || t.blocks_per_sm > 8)
+    return set_last_error(RLXPP_ERR_INVALID, "tuning needs chunk_blocks >= 2 and 1..8 blocks per SM");
+  const uint64_t L = t.chunk_blocks;
+  // chunks
+  std::vector<Item> items;
+  items.reserve((size_t)(total_refills / L + n_reqs + 1));
+  bool has_u24 = false, has_f64 = false;
+  for (uint64_t r = 0; r < n_reqs; ++r) {
+    const rlxpp_request& q = reqs[r];
+    const uint32_t kind = q.kind == RLXPP_KIND_F64 ? 1u : 0u;
+    const uint32_t need = kind ? 2 : 1;
+    const uint64_t per = kWords / need;
+    const uint64_t room = q.pos + need <= (uint32_t)kWords ? (kWords - q.pos) / need : 0;
+    const uint64_t count = (uint64_t)q.count;
+    const uint64_t head = std::min<uint64_t>(count, room);
+    uint64_t refills_left = request_refills(q);
+    if (count > 0) (kind ? has_f64 : has_u24) = true;
+    if (count == 0) {
+      if (flags & RLXPP_REQ_ADVANCE)  // no values, the state still moves by the skip
+        items.push_back(Item{q.skip, 0, q.offset, (uint32_t)r, kind | (q.pos << 8) | (1u << 16)});
+      continue;
+    }
+    // chunk 0: the head of the start block and up to L - 1 refills
+    uint64_t r0 = std::min<uint64_t>(refills_left, L - 1);
+    uint64_t n0 = std::min<uint64_t>(count, head + r0 * per);
+    uint64_t block = q.skip + r0, emitted = n0;
+    refills_left -= r0;
+    items.push_back(Item{q.skip, (int64_t)n0, q.offset, (uint32_t)r, kind | (q.pos << 8)});
+    // chunk j: from the last block of the previous chunk, position 24 (refill first)
+    while (refills_left > 0) {
+      const uint64_t rj = std::min<uint64_t>(refills_left, L);
+      const uint64_t nj = std::min<uint64_t>(count - emitted, rj * per);
+      items.push_back(Item{block, (int64_t)nj, q.offset + emitted, (uint32_t)r, kind | ((uint32_t)kWords << 8)});
+      block += rj;
+      emitted += nj;
+      refills_left -= rj;
+    }
+    items.back().info |= 1u << 16;
+  }
+  if (n_reqs >= (uint64_t(1) << 32)) return set_last_error(RLXPP_ERR_INVALID, "too many requests");
+  // longest first; equal lengths grouped by kind and then by request
+  std::sort(items.begin(), items.end(), [](const Item& a, const Item& b) {
+    if (a.count != b.count) return a.count > b.count;
+    if ((a.info & 1u) != (b.info & 1u)) return (a.info & 1u) > (b.info & 1u);
+    return a.req < b.req;
+  });
+  rlxpp_plan* p = new rlxpp_plan();
+  p->gen = g;
+  p->n_items = items.size();
+  p->n_reqs = n_reqs;
+  p->flags = flags;
+  p->tuning = t;
+  p->has_u24 = has_u24;
+  p->has_f64 = has_f64;
+  const size_t nr = std::max<uint64_t>(n_reqs, 1);
+  cudaError_t e = cudaMalloc(&p->items, sizeof(Item) * std::max<size_t>(items.size(), 1));
+  if (e == cudaSuccess) e = cudaMalloc(&p->req_stream, sizeof(uint64_t) * nr);
+  if (e == cudaSuccess) e = cudaMalloc(&p->snap_D, sizeof(uint64_t) * 9 * nr);
+  if (e == cudaSuccess) e = cudaMalloc(&p->snap_meta, sizeof(uint32_t) * nr);
+  if (e == cudaSuccess) e = cudaMalloc(&p->counter, sizeof(unsigned long long));
+  std::vector<uint64_t> rs(nr, 0);
+  for (uint64_t r = 0; r < n_reqs; ++r) rs[r] = reqs[r].stream;
+  if (e == cudaSuccess && !items.empty())
+    e = cudaMemcpy(p->items, items.data(), sizeof(Item) * items.size(), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(p->req_stream, rs.data(), sizeof(uint64_t) * rs.size(), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) {
+    free_plan(p, nullptr, false);
+    return set_last_error(e == cudaErrorMemoryAllocation ? RLXPP_ERR_NOMEM : RLXPP_ERR_CUDA,
+                          (std::string("plan: ") + cudaGetErrorString(e)).c_str());
+  }
+  *out = p;
+  return RLXPP_OK;
+}
+
+rlxpp_status run_impl(rlxpp_gen* g, const rlxpp_plan* p, uint32_t* out_u24, double* out_f64, cudaStream_t st) {
+  if (!g || !p || p->gen != g) return set_last_error(RLXPP_ERR_INVALID, "plan does not belong to this handle");
+  if ((p->has_u24 && !out_u24) || (p->has_f64 && !out_f64))
+    return set_last_error(RLXPP_ERR_INVALID, "missing output array for a requested kind");
+  if (cudaSetDevice(g->device) != cudaSuccess) return set_last_error(RLXPP_ERR_CUDA, "cudaSetDevice failed");
+  if (p->n_items == 0) return RLXPP_OK;
+  BatchArgs b{};
+  b.items = p->items;
+  b.n_items = p->n_items;
+  b.req_stream = p->req_stream;
+  b.snap_D = p->snap_D;
+  b.snap_meta = p->snap_meta;
+  b.n_reqs = p->n_reqs;
+  b.s = g->view();
+  b.out_u24 = out_u24;
+  b.out_f64 = reinterpret_cast<uint64_t*>(out_f64);
+  b.counter = p->counter;
+  b.advance = (p->flags & RLXPP_REQ_ADVANCE) ? 1 : 0;
+  cudaError_t e = cudaMemsetAsync(p->counter, 0, sizeof(unsigned long long), st);
+  if (e == cudaSuccess) {
+    k_snapshot<<<(unsigned)((p->n_reqs + 255) / 256), 256, 0, st>>>(b);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) {
+    const unsigned grid = (unsigned)std::max(1, g->sms) * p->tuning.blocks_per_sm;
+    k_requests<<<grid, kReqBlock, 0, st>>>(b);
+    e = cudaGetLastError();
+  }
+  if (e != cudaSuccess) return set_last_error(RLXPP_ERR_CUDA, (std::string("run plan: ") + cudaGetErrorString(e)).c_str());
+  return RLXPP_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+rlxpp_status rlxpp_plan_requests(rlxpp_gen* gen, const rlxpp_request* reqs, uint64_t n_reqs, uint32_t flags,
+                                 const rlxpp_tuning* tuning, rlxpp_plan** out) {
+  return plan_impl(gen, reqs, n_reqs, flags, tuning, out);
+}
+
+rlxpp_status rlxpp_run_plan(rlxpp_gen* gen, const rlxpp_plan* plan, uint32_t* out_u24, double* out_f64,
+                            void* cuda_stream) {
+  return run_impl(gen, plan, out_u24, out_f64, reinterpret_cast<cudaStream_t>(cuda_stream));
+}
+
+uint64_t rlxpp_plan_items(const rlxpp_plan* plan) { return plan ? plan->n_items : 0; }
+
+rlxpp_tuning rlxpp_plan_tuning(const rlxpp_plan* plan) { return plan ? plan->tuning : rlxpp_tuning{0, 0}; }
+
+void rlxpp_destroy_plan(rlxpp_plan* plan) {
+  if (plan) cudaSetDevice(plan->gen->device);
+  free_plan(plan, nullptr, false);
+}
+
+rlxpp_status rlxpp_draw_requests(rlxpp_gen* gen, const rlxpp_request* reqs, uint64_t n_reqs, uint32_t* out_u24,
+                                 double* out_f64, uint32_t flags, void* cuda_stream) {
+  rlxpp_plan* p = nullptr;
+  if (rlxpp_status s = plan_impl(gen, reqs, n_reqs, flags, nullptr, &p)) return s;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(cuda_stream);
+  rlxpp_status s = run_impl(gen, p, out_u24, out_f64, st);
+  free_plan(p, st, true);  // stream-ordered: freed after the run
+  return s;
+}
+
+rlxpp_status rlxpp_autotune_requests(rlxpp_gen* gen, const rlxpp_request* reqs, uint64_t n_reqs, uint32_t* out_u24,
+                                     double* out_f64, void* cuda_stream, rlxpp_tuning* best) {
+  if (!gen) return set_last_error(RLXPP_ERR_INVALID, "null generator handle");
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(cuda_stream);
+  uint64_t total = 0, longest = 0;
+  for (uint64_t r = 0; r < n_reqs; ++r) {
+    if (!reqs || reqs[r].count < 0 || reqs[r].pos > (uint32_t)kWords) return set_last_error(RLXPP_ERR_INVALID, "bad request");
+    const uint64_t nr = request_refills(reqs[r]);
+    total += nr;
+    longest = std::max(longest, nr);
+  }
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
+    return set_last_error(RLXPP_ERR_CUDA, "cudaEventCreate failed");
+  rlxpp_tuning bestt{0, 0};
+  float best_ms = 1e30f;
+  rlxpp_status status = RLXPP_OK;
+  for (uint32_t L = 4; L <= 1024 && status == RLXPP_OK; L <<= 1) {
+    if (L > 4 && L / 2 >= std::max<uint64_t>(longest, 4)) break;  // longer chunks change nothing
+    for (uint32_t bps = 2; bps <= 4 && status == RLXPP_OK; ++bps) {
+      rlxpp_tuning t{L, bps};
+      rlxpp_plan* p = nullptr;
+      status = plan_impl(gen, reqs, n_reqs, 0, &t, &p);
+      if (status != RLXPP_OK) break;
+      float ms = 1e30f;
+      for (int rep = 0; rep < 3 && status == RLXPP_OK; ++rep) {  // first run warms up
+        cudaEventRecord(e0, st);
+        status = run_impl(gen, p, out_u24, out_f64, st);
+        cudaEventRecord(e1, st);
+        if (cudaEventSynchronize(e1) != cudaSuccess) status = set_last_error(RLXPP_ERR_CUDA, "tuning run failed");
+        float m = 0;
+        cudaEventElapsedTime(&m, e0, e1);
+        if (rep > 0) ms = std::min(ms, m);
+      }
+      free_plan(p, nullptr, false);
+      if (status == RLXPP_OK && ms < best_ms) {
+        best_ms = ms;
+        bestt = t;
+      }
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (status != RLXPP_OK) return status;
+  const uint32_t sig = shape_signature(n_reqs, total);
+  gen->tuned[sig] = bestt;
+  append_cache_line(gen, sig, bestt);
+  if (best) *best = bestt;
+  return RLXPP_OK;
+}
+
+}  // extern "C"

@@ -2,6 +2,7 @@
 #pragma once
 #include <cstddef>
 #include <cstdint>
+#include <map>
 #include <cuda_runtime.h>
 
 #include "../../include/rlxpp.h"
@@ -85,4 +86,28 @@ enum TestOp {
 // Records msg as the calling thread's rlxpp_last_error() text and returns code.
 rlxpp_status set_last_error(rlxpp_status code, const char* msg);
 
+// Reads the request tuner's saved choices for this device model (RLXPP_TUNE_CACHE).
+void load_tune_cache(rlxpp_gen* g);
+
 }  // namespace rlxpp
+
+// The handle behind rlxpp_gen* (opaque in the public header).
+struct rlxpp_gen {
+  int device = 0;
+  uint64_t n = 0;
+  uint32_t n_levels = 0;
+  uint32_t levels[RLXPP_MAX_LEVELS] = {};
+  rlxpp::Lux lux_host[RLXPP_MAX_LEVELS] = {};
+  uint64_t* D = nullptr;        // [9][n]
+  uint32_t* meta = nullptr;     // [n]
+  uint32_t* lux = nullptr;      // [n_levels][18]
+  uint32_t* table = nullptr;    // [n_levels][kTableLimbs]
+  uint32_t* level_p = nullptr;  // [n_levels]
+  int* status = nullptr;        // sticky device status
+  cudaStream_t copy_stream = nullptr;  // device-to-host copies of chunked host output
+  cudaEvent_t ev[4] = {};
+  int sms = 0;                         // multiprocessors of the device
+  std::map<uint32_t, rlxpp_tuning> tuned;  // request-shape signature -> tuner choice
+  rlxpp::StateView view() const { return rlxpp::StateView{D, meta, n, n, lux, table, status}; }
+};
+
