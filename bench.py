@@ -286,6 +286,14 @@ def run_native(args, rank, world, local_rank):
         result["e2e"] = run_e2e(args, nat, g, seeds_h, n, world, dev, dist)
     g.close()
     del out
+    if not args.only_main:
+        torch.cuda.empty_cache()
+        result["other_workloads"] = {
+            "single_stream": bench_single_stream(nat, dev),
+            "mixed_batch": bench_mixed_batch(nat, dev, args),
+            "skip": bench_skip(nat, dev),
+            "serving": bench_serving(args),
+        }
     if rank == 0 and not args.no_cpu_baseline:
         dt, doubles, threads = cpu_oracle_sample(args.cpu_sample, 1)
         result["cpu_baseline"] = {
@@ -295,6 +303,147 @@ def run_native(args, rank, world, local_rank):
     if rank == 0:
         print(json.dumps(result), flush=True)
     return 0
+
+
+def _time_events(fn, reps, stream):
+    import torch
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    fn()
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(reps):
+        fn()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / reps
+
+
+def bench_single_stream(nat, dev):
+    """Seed 1, p = 2048, 2^20 doubles from one stream: one thread (serial refills) and
+    the same segment split by jump-ahead over many threads (batched requests)."""
+    import numpy as np
+    import torch
+    n = 1 << 20
+    st = torch.cuda.current_stream()
+    g = nat.Generator(1, [LUXURY], torch.ones(1, dtype=torch.int64, device=dev))
+    out = torch.empty(n, dtype=torch.float64, device=dev)
+    ms_serial = _time_events(lambda: nat.rlxpp_draw_f64(g.handle, out, n, None, None, st.cuda_stream), 2, st)
+    adv = advances_for(n, 0)[0]
+    req = np.zeros(1, dtype=nat.request_dtype())
+    req[0] = (0, 0, 0, nat.RLXPP_KIND_F64, n, 0)
+    tuning = nat.rlxpp_autotune_requests(g.handle, req, None, out)
+    plan = nat.rlxpp_plan_requests(g.handle, req, 0, tuning)
+    ms_split = _time_events(lambda: nat.rlxpp_run_plan(g.handle, plan, None, out, st.cuda_stream), 5, st)
+    items = nat.rlxpp_plan_items(plan)
+    nat.rlxpp_destroy_plan(plan)
+    g.close()
+    return {"doubles": n, "advances": adv,
+            "serial": {"ms": ms_serial, "doubles_per_s": n / (ms_serial * 1e-3),
+                       "ns_per_advance": ms_serial * 1e6 / adv},
+            "split": {"ms": ms_split, "doubles_per_s": n / (ms_split * 1e-3), "chunks": items,
+                      "tuning": {"chunk_blocks": tuning[0], "blocks_per_sm": tuning[1]}}}
+
+
+def bench_mixed_batch(nat, dev, args):
+    """65,536 streams, luxury uniform over {24, 223, 389, 2048}, counts log-uniform in
+    [1, 10^6], u24/f64 50/50: one tuned plan captured in a CUDA graph and replayed,
+    against the plain per-stream kernels (one thread per stream) on the same work."""
+    import numpy as np
+    import torch
+
+    from paper_2106_02504_gb300 import workloads as W
+    n = args.batch_streams
+    levels, lvl, counts, is_f64 = W.batch_mix(n, seed=3)
+    seeds = torch.from_numpy(np.arange(1, n + 1, dtype=np.uint64).view(np.int64)).to(dev)
+    g = nat.Generator(n, levels, seeds, torch.from_numpy(lvl).to(dev))
+    kind = is_f64.astype(np.uint32)
+    offs = np.zeros(n, dtype=np.int64)
+    for k in (0, 1):
+        idx = np.nonzero(kind == k)[0]
+        offs[idx] = np.concatenate([[0], np.cumsum(counts[idx])[:-1]])
+    n_u, n_f = int(counts[kind == 0].sum()), int(counts[kind == 1].sum())
+    reqs = np.zeros(n, dtype=nat.request_dtype())
+    reqs["stream"] = np.arange(n)
+    reqs["kind"] = kind
+    reqs["count"] = counts
+    reqs["offset"] = offs
+    out_u = torch.empty(max(n_u, 1), dtype=torch.int32, device=dev)
+    out_f = torch.empty(max(n_f, 1), dtype=torch.float64, device=dev)
+    refills = sum(advances_for(int(c), 0, 2 if f else 1)[0] for c, f in zip(counts, is_f64))
+    st = torch.cuda.current_stream()
+    t = time.perf_counter()
+    tuning = nat.rlxpp_autotune_requests(g.handle, reqs, out_u, out_f)
+    tune_s = time.perf_counter() - t
+    t = time.perf_counter()
+    plan = nat.rlxpp_plan_requests(g.handle, reqs, 0, tuning)
+    plan_s = time.perf_counter() - t
+    graph = torch.cuda.CUDAGraph()
+    side = torch.cuda.Stream()
+    side.wait_stream(st)
+    with torch.cuda.stream(side):
+        nat.rlxpp_run_plan(g.handle, plan, out_u, out_f, side.cuda_stream)
+    st.wait_stream(side)
+    with torch.cuda.graph(graph):
+        nat.rlxpp_run_plan(g.handle, plan, out_u, out_f)
+    ms_graph = _time_events(graph.replay, 3, st)
+    items = nat.rlxpp_plan_items(plan)
+    nat.rlxpp_destroy_plan(plan)
+    # plain per-stream kernels: u24 streams, then f64 streams (the other kind draws 0)
+    cu = torch.from_numpy(np.where(kind == 0, counts, 0)).to(dev)
+    cf = torch.from_numpy(np.where(kind == 1, counts, 0)).to(dev)
+    o = torch.from_numpy(offs).to(dev)
+
+    def plain():
+        nat.rlxpp_draw_u24(g.handle, out_u, 0, cu, o, st.cuda_stream)
+        nat.rlxpp_draw_f64(g.handle, out_f, 0, cf, o, st.cuda_stream)
+    ms_plain = _time_events(plain, 1, st)
+    g.close()
+    values = int(counts.sum())
+    return {"streams": n, "values": values, "doubles": n_f, "u24": n_u, "advances": int(refills),
+            "output_bytes": n_u * 4 + n_f * 8,
+            "batched_graph": {"ms": ms_graph, "values_per_s": values / (ms_graph * 1e-3),
+                              "advances_per_s": refills / (ms_graph * 1e-3), "chunks": items,
+                              "tuning": {"chunk_blocks": tuning[0], "blocks_per_sm": tuning[1]},
+                              "tune_s": tune_s, "plan_s": plan_s},
+            "plain_per_stream": {"ms": ms_plain, "values_per_s": values / (ms_plain * 1e-3),
+                                 "advances_per_s": refills / (ms_plain * 1e-3)},
+            "speedup_vs_plain": ms_plain / ms_graph}
+
+
+def bench_skip(nat, dev):
+    """2^18 streams (seeds i + 1, p = 2048) skipped by uniform 128-bit distances, then
+    48 doubles each."""
+    import numpy as np
+    import torch
+
+    from paper_2106_02504_gb300 import workloads as W
+    n = 1 << 18
+    seeds = torch.from_numpy(np.arange(1, n + 1, dtype=np.uint64).view(np.int64)).to(dev)
+    g = nat.Generator(n, [LUXURY], seeds)
+    dist = torch.from_numpy(W.skip_distances(n, seed=4).view(np.int64)).to(dev)
+    out = torch.empty((n, 48), dtype=torch.float64, device=dev)
+    st = torch.cuda.current_stream()
+    ms_skip = _time_events(lambda: nat.rlxpp_skip(g.handle, dist, st.cuda_stream), 3, st)
+    ms_draw = _time_events(lambda: nat.rlxpp_draw_f64(g.handle, out, 48, None, None, st.cuda_stream), 3, st)
+    g.close()
+    return {"streams": n, "skip_ms": ms_skip, "skips_per_s": n / (ms_skip * 1e-3),
+            "products_per_stream_max": 32, "draw48_ms": ms_draw}
+
+
+def bench_serving(args):
+    """10^5 resident streams, Poisson arrivals at 2 10^4 requests/s, counts log-uniform in
+    [10^2, 10^7], u24/f64 50/50, outputs copied to pinned host memory."""
+    from paper_2106_02504_gb300 import workloads as W
+    from paper_2106_02504_gb300.serve import Server
+    n_res, rate = 100_000, 20_000
+    n_req = int(rate * args.serve_seconds)
+    arr, stream, counts, is_f64 = W.serving_trace(n_req, rate, n_res, seed=5)
+    srv = Server(n_res, pool_bytes=args.serve_pool_gib << 30, n_cuda_streams=4, max_batch=512)
+    stats = srv.run_trace(arr, stream, counts, is_f64)
+    srv.close()
+    stats.update({"resident_streams": n_res, "arrival_rate_hz": rate, "trace_seconds": args.serve_seconds,
+                  "pool_bytes": args.serve_pool_gib << 30})
+    return stats
 
 
 def run_e2e(args, nat, g, seeds_h, n, world, dev, dist):
@@ -347,6 +496,10 @@ def main():
     ap.add_argument("--cpu-sample", type=int, default=CPU_SAMPLE_STREAMS)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--only-main", action="store_true", help="skip the other workloads")
+    ap.add_argument("--batch-streams", type=int, default=65536)
+    ap.add_argument("--serve-seconds", type=float, default=5.0)
+    ap.add_argument("--serve-pool-gib", type=int, default=8)
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))

@@ -174,7 +174,9 @@ rlxpp_tuning rlxpp_plan_tuning(const rlxpp_plan* plan);
 
 void rlxpp_destroy_plan(rlxpp_plan* plan);
 
-/* plan + run + destroy in one call. */
+/* plan + run + destroy in one call; the work list is allocated, uploaded and freed in
+ * order on cuda_stream (no device-wide synchronisation), and the host request array may
+ * be reused when the call returns. */
 rlxpp_status rlxpp_draw_requests(rlxpp_gen* gen, const rlxpp_request* reqs, uint64_t n_reqs,
                                  uint32_t* out_u24, double* out_f64, uint32_t flags,
                                  void* cuda_stream);

@@ -208,8 +208,11 @@ void free_plan(rlxpp_plan* p, cudaStream_t st, bool async) {
   delete p;
 }
 
+// stream_ordered: allocate and upload on `st` (cudaMallocAsync / cudaMemcpyAsync), so
+// that planning does not synchronise the device; otherwise plain cudaMalloc/cudaMemcpy.
 rlxpp_status plan_impl(rlxpp_gen* g, const rlxpp_request* reqs, uint64_t n_reqs, uint32_t flags,
-                       const rlxpp_tuning* tuning, rlxpp_plan** out) {
+                       const rlxpp_tuning* tuning, rlxpp_plan** out, cudaStream_t st = nullptr,
+                       bool stream_ordered = false) {
   if (!out) return set_last_error(RLXPP_ERR_INVALID, "null plan output");
   *out = nullptr;
   if (!g) return set_last_error(RLXPP_ERR_INVALID, "null generator handle");
@@ -302,18 +305,25 @@ rlxpp_status plan_impl(rlxpp_gen* g, const rlxpp_request* reqs, uint64_t n_reqs,
   p->has_u24 = has_u24;
   p->has_f64 = has_f64;
   const size_t nr = std::max<uint64_t>(n_reqs, 1);
-  cudaError_t e = cudaMalloc(&p->items, sizeof(Item) * std::max<size_t>(items.size(), 1));
-  if (e == cudaSuccess) e = cudaMalloc(&p->req_stream, sizeof(uint64_t) * nr);
-  if (e == cudaSuccess) e = cudaMalloc(&p->snap_D, sizeof(uint64_t) * 9 * nr);
-  if (e == cudaSuccess) e = cudaMalloc(&p->snap_meta, sizeof(uint32_t) * nr);
-  if (e == cudaSuccess) e = cudaMalloc(&p->counter, sizeof(unsigned long long));
+  auto alloc = [&](void** ptr, size_t bytes) {
+    return stream_ordered ? cudaMallocAsync(ptr, bytes, st) : cudaMalloc(ptr, bytes);
+  };
+  auto upload = [&](void* dst, const void* src, size_t bytes) {
+    // pageable source: the call returns once the data is staged, so the vectors may go
+    return stream_ordered ? cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, st)
+                          : cudaMemcpy(dst, src, bytes, cudaMemcpyHostToDevice);
+  };
+  cudaError_t e = alloc((void**)&p->items, sizeof(Item) * std::max<size_t>(items.size(), 1));
+  if (e == cudaSuccess) e = alloc((void**)&p->req_stream, sizeof(uint64_t) * nr);
+  if (e == cudaSuccess) e = alloc((void**)&p->snap_D, sizeof(uint64_t) * 9 * nr);
+  if (e == cudaSuccess) e = alloc((void**)&p->snap_meta, sizeof(uint32_t) * nr);
+  if (e == cudaSuccess) e = alloc((void**)&p->counter, sizeof(unsigned long long));
   std::vector<uint64_t> rs(nr, 0);
   for (uint64_t r = 0; r < n_reqs; ++r) rs[r] = reqs[r].stream;
-  if (e == cudaSuccess && !items.empty())
-    e = cudaMemcpy(p->items, items.data(), sizeof(Item) * items.size(), cudaMemcpyHostToDevice);
-  if (e == cudaSuccess) e = cudaMemcpy(p->req_stream, rs.data(), sizeof(uint64_t) * rs.size(), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess && !items.empty()) e = upload(p->items, items.data(), sizeof(Item) * items.size());
+  if (e == cudaSuccess) e = upload(p->req_stream, rs.data(), sizeof(uint64_t) * rs.size());
   if (e != cudaSuccess) {
-    free_plan(p, nullptr, false);
+    free_plan(p, st, stream_ordered);
     return set_last_error(e == cudaErrorMemoryAllocation ? RLXPP_ERR_NOMEM : RLXPP_ERR_CUDA,
                           (std::string("plan: ") + cudaGetErrorString(e)).c_str());
   }
@@ -379,8 +389,8 @@ void rlxpp_destroy_plan(rlxpp_plan* plan) {
 rlxpp_status rlxpp_draw_requests(rlxpp_gen* gen, const rlxpp_request* reqs, uint64_t n_reqs, uint32_t* out_u24,
                                  double* out_f64, uint32_t flags, void* cuda_stream) {
   rlxpp_plan* p = nullptr;
-  if (rlxpp_status s = plan_impl(gen, reqs, n_reqs, flags, nullptr, &p)) return s;
   cudaStream_t st = reinterpret_cast<cudaStream_t>(cuda_stream);
+  if (rlxpp_status s = plan_impl(gen, reqs, n_reqs, flags, nullptr, &p, st, true)) return s;
   rlxpp_status s = run_impl(gen, p, out_u24, out_f64, st);
   free_plan(p, st, true);  // stream-ordered: freed after the run
   return s;

@@ -1,0 +1,242 @@
+"""Continuous-batching request loop over resident RANLUX++ streams.
+
+Every resident stream keeps its state on the device (created once, never rewritten by
+the loop).  A request asks for `count` u24 integers or doubles from one stream; at
+arrival it is given the next segment of that stream — its start block and read
+position follow from the stream's host-side cursor by position arithmetic (24 numbers
+per block, 2 per double, a lone leftover number skipped) — so it can run before,
+after or beside any other request: the device starts it by jump-ahead
+(rlxpp_draw_requests with skip = start block).  A request is admitted when its output
+fits in a fixed device-memory arena, launched with whatever else is admitted as one
+batch on one of several CUDA streams while earlier batches still run, copied to a
+pinned host mirror of the arena, and completed when the batch's event has fired.
+"""
+from __future__ import annotations
+
+import collections
+import time
+from dataclasses import dataclass, field
+
+import numpy as np
+
+from . import _rlxpp as B
+
+KIND_U24, KIND_F64 = B.RLXPP_KIND_U24, B.RLXPP_KIND_F64
+_ALIGN = 256
+
+
+def advance_cursor(block, pos, kind, count):
+    """Stream position after `count` values of `kind` starting at (block, pos)."""
+    need = 2 if kind == KIND_F64 else 1
+    per = 24 // need
+    room = (24 - pos) // need if pos + need <= 24 else 0
+    head = min(count, room)
+    rest = count - head
+    if rest == 0:
+        return block, pos + head * need
+    refills = -(-rest // per)
+    last = rest - (refills - 1) * per
+    return block + refills, last * need
+
+
+class Arena:
+    """First-fit allocator over [0, size) bytes with coalescing free list."""
+
+    def __init__(self, size):
+        self.size = size
+        self.free = [(0, size)]     # sorted (offset, length)
+        self.used = 0
+
+    def alloc(self, nbytes):
+        n = -(-nbytes // _ALIGN) * _ALIGN
+        for k, (off, ln) in enumerate(self.free):
+            if ln >= n:
+                if ln == n:
+                    self.free.pop(k)
+                else:
+                    self.free[k] = (off + n, ln - n)
+                self.used += n
+                return off, n
+        return None
+
+    def release(self, off, n):
+        self.used -= n
+        lo, hi = 0, len(self.free)
+        while lo < hi:
+            mid = (lo + hi) // 2
+            if self.free[mid][0] < off:
+                lo = mid + 1
+            else:
+                hi = mid
+        self.free.insert(lo, (off, n))
+        if lo + 1 < len(self.free) and self.free[lo][0] + self.free[lo][1] == self.free[lo + 1][0]:
+            self.free[lo] = (off, self.free[lo][1] + self.free[lo + 1][1])
+            self.free.pop(lo + 1)
+        if lo > 0 and self.free[lo - 1][0] + self.free[lo - 1][1] == self.free[lo][0]:
+            self.free[lo - 1] = (self.free[lo - 1][0], self.free[lo - 1][1] + self.free[lo][1])
+            self.free.pop(lo)
+
+
+@dataclass
+class Request:
+    rid: int
+    stream: int
+    kind: int
+    count: int
+    arrival: float
+    skip: int = 0
+    pos: int = 0
+    offset: int = -1          # byte offset in the arena
+    nbytes: int = 0
+    reserved: int = 0
+    launch: float = 0.0
+    done: float = 0.0
+    result: np.ndarray | None = field(default=None, repr=False)
+
+
+class Server:
+    def __init__(self, n_resident, luxury=2048, seeds=None, pool_bytes=1 << 30, n_cuda_streams=4,
+                 max_batch=512, keep_results=False, copy_to_host=True):
+        import torch
+        self.torch = torch
+        if seeds is None:
+            seeds = np.arange(1, n_resident + 1, dtype=np.uint64)
+        self.gen = B.Generator(n_resident, [luxury], torch.from_numpy(np.asarray(seeds, np.uint64).view(np.int64)).cuda())
+        self.n = n_resident
+        self.cur_block = [0] * n_resident
+        self.cur_pos = [0] * n_resident
+        self.dev = torch.empty(pool_bytes, dtype=torch.uint8, device="cuda")
+        self.host = torch.empty(pool_bytes, dtype=torch.uint8).pin_memory() if copy_to_host else None
+        self.arena = Arena(pool_bytes)
+        self.streams = [torch.cuda.Stream() for _ in range(n_cuda_streams)]
+        self.free_streams = collections.deque(range(n_cuda_streams))
+        self.waiting = collections.deque()     # arrived, not admitted (FIFO)
+        self.admitted = collections.deque()    # admitted, not launched
+        self.inflight = collections.deque()    # (event, stream index, [requests])
+        self.max_batch = max_batch
+        self.keep_results = keep_results
+        self.finished = []
+        self.t0 = time.perf_counter()
+
+    def now(self):
+        return time.perf_counter() - self.t0
+
+    # -- request life cycle -----------------------------------------------------------
+    def submit(self, rid, stream, kind, count, arrival=None):
+        r = Request(rid, int(stream), int(kind), int(count), self.now() if arrival is None else arrival)
+        b, p = self.cur_block[r.stream], self.cur_pos[r.stream]
+        r.skip, r.pos = b, p
+        self.cur_block[r.stream], self.cur_pos[r.stream] = advance_cursor(b, p, r.kind, r.count)
+        r.nbytes = r.count * (8 if r.kind == KIND_F64 else 4)
+        if r.nbytes > self.arena.size:
+            raise ValueError(f"request {rid} needs {r.nbytes} bytes, more than the whole arena")
+        self.waiting.append(r)
+        return r
+
+    def _admit(self):
+        while self.waiting:
+            r = self.waiting[0]
+            got = self.arena.alloc(max(r.nbytes, 1))
+            if got is None:
+                return
+            r.offset, r.reserved = got
+            self.waiting.popleft()
+            self.admitted.append(r)
+
+    def _dispatch(self):
+        torch = self.torch
+        while self.admitted and self.free_streams:
+            batch = [self.admitted.popleft() for _ in range(min(self.max_batch, len(self.admitted)))]
+            si = self.free_streams.popleft()
+            st = self.streams[si]
+            reqs = np.zeros(len(batch), dtype=B.request_dtype())
+            for k, r in enumerate(batch):
+                elem = 8 if r.kind == KIND_F64 else 4
+                reqs[k] = (r.stream, r.skip, r.pos, r.kind, r.count, r.offset // elem)
+            base = self.dev.data_ptr()
+            with torch.cuda.stream(st):
+                B.rlxpp_draw_requests(self.gen.handle, reqs, base, base, 0, st)
+                if self.host is not None:
+                    for r in batch:
+                        if r.nbytes:
+                            self.host[r.offset:r.offset + r.nbytes].copy_(self.dev[r.offset:r.offset + r.nbytes],
+                                                                          non_blocking=True)
+                ev = torch.cuda.Event()
+                ev.record(st)
+            t = self.now()
+            for r in batch:
+                r.launch = t
+            self.inflight.append((ev, si, batch))
+
+    def _complete(self, wait_first=False):
+        """Retire every finished batch (any order); optionally wait for the oldest first."""
+        if wait_first and self.inflight:
+            self.inflight[0][0].synchronize()
+        keep = collections.deque()
+        while self.inflight:
+            ev, si, batch = self.inflight.popleft()
+            if not ev.query():
+                keep.append((ev, si, batch))
+                continue
+            t = self.now()
+            for r in batch:
+                r.done = t
+                if self.keep_results and self.host is not None and r.nbytes:
+                    raw = self.host[r.offset:r.offset + r.nbytes].numpy()
+                    r.result = raw.view(np.uint64 if r.kind == KIND_F64 else np.uint32).copy()
+                self.arena.release(r.offset, r.reserved)
+                self.finished.append(r)
+            self.free_streams.append(si)
+        self.inflight = keep
+
+    def pump(self):
+        """One round: complete finished batches, admit, launch."""
+        self._complete()
+        self._admit()
+        self._dispatch()
+
+    def drain(self):
+        """Run everything submitted so far to completion."""
+        while self.waiting or self.admitted or self.inflight:
+            self.pump()
+            if self.inflight and (not self.free_streams or not self.admitted):
+                self._complete(wait_first=True)
+
+    def close(self):
+        self.torch.cuda.synchronize()
+        self.gen.close()
+
+    # -- trace replay ---------------------------------------------------------------------
+    def run_trace(self, arrival_s, stream, count, is_f64, duration=None):
+        """Release requests at their (wall-clock) arrival times; returns stats."""
+        n = len(arrival_s)
+        if duration is not None:
+            n = int(np.searchsorted(arrival_s, duration))
+        self.t0 = time.perf_counter()
+        i = 0
+        while i < n or self.waiting or self.admitted or self.inflight:
+            t = self.now()
+            while i < n and arrival_s[i] <= t:
+                self.submit(i, stream[i], KIND_F64 if is_f64[i] else KIND_U24, count[i], arrival=float(arrival_s[i]))
+                i += 1
+            self.pump()
+            if i < n and not self.admitted and not self.waiting:
+                gap = arrival_s[i] - self.now()
+                if gap > 2e-4 and not self.inflight:
+                    time.sleep(min(gap, 1e-3))
+        self.torch.cuda.synchronize()
+        return self.stats()
+
+    def stats(self):
+        if not self.finished:
+            return {}
+        lat = np.array([r.done - r.arrival for r in self.finished])
+        first = min(r.arrival for r in self.finished)
+        last = max(r.done for r in self.finished)
+        values = sum(r.count for r in self.finished)
+        doubles = sum(r.count for r in self.finished if r.kind == KIND_F64)
+        return {"requests": len(self.finished), "values": values, "doubles": doubles,
+                "seconds": last - first, "values_per_s": values / (last - first),
+                "doubles_per_s": doubles / (last - first),
+                "p50_ms": float(np.percentile(lat, 50) * 1e3), "p99_ms": float(np.percentile(lat, 99) * 1e3),
+                "max_ms": float(lat.max() * 1e3)}
