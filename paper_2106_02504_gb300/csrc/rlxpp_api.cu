@@ -105,6 +105,10 @@ void free_gen(rlxpp_gen* g) {
   cudaFree(g->status);
   for (auto& e : g->ev)
     if (e) cudaEventDestroy(e);
+  for (auto& e : g->level_event)
+    if (e) cudaEventDestroy(e);
+  for (auto& s : g->level_stream)
+    if (s) cudaStreamDestroy(s);
   if (g->copy_stream) cudaStreamDestroy(g->copy_stream);
   delete g;
 }
@@ -248,6 +252,12 @@ rlxpp_status rlxpp_create(uint64_t n_streams, const uint32_t* levels, uint32_t n
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&g->copy_stream, cudaStreamNonBlocking);
   for (auto& ev : g->ev)
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+  if (n_levels > 1) {  // concurrent per-level launches of the request kernel
+    for (uint32_t l = 0; l < n_levels && e == cudaSuccess; ++l)
+      e = cudaStreamCreateWithFlags(&g->level_stream[l], cudaStreamNonBlocking);
+    for (uint32_t l = 0; l <= n_levels && e == cudaSuccess; ++l)
+      e = cudaEventCreateWithFlags(&g->level_event[l], cudaEventDisableTiming);
+  }
   if (e != cudaSuccess)
     return bail(fail(e == cudaErrorMemoryAllocation ? RLXPP_ERR_NOMEM : RLXPP_ERR_CUDA,
                      std::string("create: ") + cudaGetErrorString(e)));
@@ -265,6 +275,14 @@ rlxpp_status rlxpp_create(uint64_t n_streams, const uint32_t* levels, uint32_t n
     e = launch_seed(g->view(), static_cast<const uint64_t*>(ss.dev), static_cast<const uint8_t*>(sl.dev),
                     n_levels, false, st);
     if (e != cudaSuccess) return bail(fail(RLXPP_ERR_CUDA, std::string("seed: ") + cudaGetErrorString(e)));
+    g->level_host.assign(n_streams, 0);
+    if (sl.dev) {  // host copy of the level indices (out-of-range ones were seeded at level 0)
+      e = cudaMemcpyAsync(g->level_host.data(), sl.dev, n_streams, cudaMemcpyDeviceToHost, st);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+      if (e != cudaSuccess) return bail(fail(RLXPP_ERR_CUDA, std::string("levels: ") + cudaGetErrorString(e)));
+      for (auto& l : g->level_host)
+        if (l >= n_levels) l = 0;
+    }
   }
   *out = g;
   return RLXPP_OK;
@@ -363,6 +381,7 @@ rlxpp_status rlxpp_set_state(rlxpp_gen* g, const rlxpp_state* src, void* cuda_st
   cudaError_t e = launch_import(g->view(), g->level_p, g->n_levels,
                                 static_cast<const rlxpp_state*>(ss.dev), st);
   if (e != cudaSuccess) return fail(RLXPP_ERR_CUDA, std::string("import: ") + cudaGetErrorString(e));
+  g->level_host_stale = true;  // levels may have changed; the next request plan re-reads them
   return RLXPP_OK;
 }
 

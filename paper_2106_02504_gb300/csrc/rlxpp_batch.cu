@@ -25,6 +25,11 @@
 #include "rlxpp_internal.h"
 #include "rlxpp_state.cuh"
 
+// Resident 128-thread blocks per SM the request kernel is compiled for.
+#ifndef RLXPP_REQ_MIN_BLOCKS
+#define RLXPP_REQ_MIN_BLOCKS 5
+#endif
+
 namespace rlxpp {
 namespace {
 
@@ -39,8 +44,6 @@ struct Item {       // one chunk (32 bytes)
 };
 
 struct BatchArgs {
-  const Item* items;
-  uint64_t n_items;
   const uint64_t* req_stream;  // [n_reqs]
   uint64_t* snap_D;            // [9][n_reqs]
   uint32_t* snap_meta;         // [n_reqs]
@@ -48,7 +51,6 @@ struct BatchArgs {
   StateView s;                 // resident states (final states are written back here)
   uint32_t* out_u24;
   uint64_t* out_f64;
-  unsigned long long* counter;
   int advance;
 };
 
@@ -62,7 +64,7 @@ __global__ void k_snapshot(BatchArgs b) {
   b.snap_meta[r] = b.s.meta[st];
 }
 
-__device__ __forceinline__ void run_item(const BatchArgs& b, const Item& it) {
+__device__ __forceinline__ void run_item(const BatchArgs& b, const Lux& L, const Item& it) {
   const uint32_t r = it.req;
   const uint32_t meta = b.snap_meta[r];
   const uint32_t lvl = meta_level(meta);
@@ -82,23 +84,18 @@ __device__ __forceinline__ void run_item(const BatchArgs& b, const Item& it) {
     to_ranlux(X, D);
     c = carry_of(X, D);
   }
-  uint32_t Areg[kLimbs], ASreg[9];
-  load18(b.s.lux + (size_t)lvl * kLimbs, Areg);
-  ASreg[0] = add_cc(Areg[0], Areg[9]);
-#pragma unroll
-  for (int k = 1; k < 9; ++k) ASreg[k] = addc_cc(Areg[k], Areg[9 + k]);
-  const uint32_t ca = addc(0u, 0u);
-  auto A = [&](int k) { return Areg[k]; };
-  auto AS = [&](int k) { return ASreg[k]; };
+  // every chunk of this launch belongs to one luxury level: A stays in the constant bank
+  auto A = [&](int k) { return L.a[k]; };
+  auto AS = [&](int k) { return L.as[k]; };
   uint32_t pos = (it.info >> 8) & 0xFFu;
   if (it.info & 1u) {
     Consumer<kDrawF64> o;
     o.out = b.out_f64;
-    draw_stream<kDrawF64>(o, D, c, pos, A, AS, ca, it.count, (int64_t)it.out);
+    draw_stream<kDrawF64>(o, D, c, pos, A, AS, L.ca, it.count, (int64_t)it.out);
   } else {
     Consumer<kDrawU24> o;
     o.out = b.out_u24;
-    draw_stream<kDrawU24>(o, D, c, pos, A, AS, ca, it.count, (int64_t)it.out);
+    draw_stream<kDrawU24>(o, D, c, pos, A, AS, L.ca, it.count, (int64_t)it.out);
   }
   if (b.advance && ((it.info >> 16) & 1u)) {
     const uint64_t st = b.req_stream[r];
@@ -108,16 +105,18 @@ __device__ __forceinline__ void run_item(const BatchArgs& b, const Item& it) {
   }
 }
 
-// Persistent: each warp takes the next 32 chunks of the (longest-first) list.
-__global__ void __launch_bounds__(kReqBlock, 4) k_requests(BatchArgs b) {
+// Persistent, one luxury level per launch (items[0..n_items) of that level): each warp
+// takes the next 32 chunks of the longest-first list from the level's counter.
+__global__ void __launch_bounds__(kReqBlock, RLXPP_REQ_MIN_BLOCKS) k_requests(BatchArgs b, const Lux L, const Item* __restrict__ items,
+                                                           uint64_t n_items, unsigned long long* counter) {
   const int lane = threadIdx.x & 31;
   while (true) {
     unsigned long long base = 0;
-    if (lane == 0) base = atomicAdd(b.counter, 32ull);
+    if (lane == 0) base = atomicAdd(counter, 32ull);
     base = __shfl_sync(0xFFFFFFFFu, base, 0);
-    if (base >= b.n_items) break;
+    if (base >= n_items) break;
     const uint64_t idx = base + (uint64_t)lane;
-    if (idx < b.n_items) run_item(b, b.items[idx]);
+    if (idx < n_items) run_item(b, L, items[idx]);
   }
 }
 
@@ -192,6 +191,7 @@ struct rlxpp_plan {
   rlxpp_tuning tuning{};
   bool has_u24 = false, has_f64 = false;
   Item* items = nullptr;
+  uint64_t level_begin[RLXPP_MAX_LEVELS + 1] = {};  // items of level l: [begin[l], begin[l+1])
   uint64_t* req_stream = nullptr;  // [n_reqs] stream of each request
   uint64_t* snap_D = nullptr;
   uint32_t* snap_meta = nullptr;
@@ -219,6 +219,14 @@ rlxpp_status plan_impl(rlxpp_gen* g, const rlxpp_request* reqs, uint64_t n_reqs,
   if (n_reqs && !reqs) return set_last_error(RLXPP_ERR_INVALID, "null requests");
   if (flags & ~RLXPP_REQ_ADVANCE) return set_last_error(RLXPP_ERR_INVALID, "unknown flags");
   if (cudaSetDevice(g->device) != cudaSuccess) return set_last_error(RLXPP_ERR_CUDA, "cudaSetDevice failed");
+  if (g->level_host.size() != g->n || g->level_host_stale) {  // re-read the stream levels
+    std::vector<uint32_t> meta(g->n);
+    if (g->n && cudaMemcpy(meta.data(), g->meta, sizeof(uint32_t) * g->n, cudaMemcpyDeviceToHost) != cudaSuccess)
+      return set_last_error(RLXPP_ERR_CUDA, "reading stream levels failed");
+    g->level_host.resize(g->n);
+    for (uint64_t i = 0; i < g->n; ++i) g->level_host[i] = (uint8_t)meta_level(meta[i]);
+    g->level_host_stale = false;
+  }
   uint64_t total_refills = 0;
   std::vector<uint8_t> seen((flags & RLXPP_REQ_ADVANCE) ? g->n : 0, 0);
   for (uint64_t r = 0; r < n_reqs; ++r) {
@@ -290,13 +298,26 @@ rlxpp_status plan_impl(rlxpp_gen* g, const rlxpp_request* reqs, uint64_t n_reqs,
     items.back().info |= 1u << 16;
   }
   if (n_reqs >= (uint64_t(1) << 32)) return set_last_error(RLXPP_ERR_INVALID, "too many requests");
-  // longest first; equal lengths grouped by kind and then by request
-  std::sort(items.begin(), items.end(), [](const Item& a, const Item& b) {
+  // by luxury level (one launch each), then longest first; equal lengths grouped by kind
+  // and then by request
+  const uint8_t* lev = g->level_host.data();
+  auto level_of = [&](const Item& a) { return lev[reqs[a.req].stream]; };
+  std::sort(items.begin(), items.end(), [&](const Item& a, const Item& b) {
+    const uint8_t la = level_of(a), lb = level_of(b);
+    if (la != lb) return la < lb;
     if (a.count != b.count) return a.count > b.count;
     if ((a.info & 1u) != (b.info & 1u)) return (a.info & 1u) > (b.info & 1u);
     return a.req < b.req;
   });
   rlxpp_plan* p = new rlxpp_plan();
+  {
+    uint64_t k = 0;
+    for (uint32_t l = 0; l <= g->n_levels; ++l) {
+      while (k < items.size() && level_of(items[k]) < l) ++k;
+      p->level_begin[l] = k;
+    }
+    p->level_begin[g->n_levels] = items.size();
+  }
   p->gen = g;
   p->n_items = items.size();
   p->n_reqs = n_reqs;
@@ -317,7 +338,7 @@ rlxpp_status plan_impl(rlxpp_gen* g, const rlxpp_request* reqs, uint64_t n_reqs,
   if (e == cudaSuccess) e = alloc((void**)&p->req_stream, sizeof(uint64_t) * nr);
   if (e == cudaSuccess) e = alloc((void**)&p->snap_D, sizeof(uint64_t) * 9 * nr);
   if (e == cudaSuccess) e = alloc((void**)&p->snap_meta, sizeof(uint32_t) * nr);
-  if (e == cudaSuccess) e = alloc((void**)&p->counter, sizeof(unsigned long long));
+  if (e == cudaSuccess) e = alloc((void**)&p->counter, sizeof(unsigned long long) * RLXPP_MAX_LEVELS);
   std::vector<uint64_t> rs(nr, 0);
   for (uint64_t r = 0; r < n_reqs; ++r) rs[r] = reqs[r].stream;
   if (e == cudaSuccess && !items.empty()) e = upload(p->items, items.data(), sizeof(Item) * items.size());
@@ -338,8 +359,6 @@ rlxpp_status run_impl(rlxpp_gen* g, const rlxpp_plan* p, uint32_t* out_u24, doub
   if (cudaSetDevice(g->device) != cudaSuccess) return set_last_error(RLXPP_ERR_CUDA, "cudaSetDevice failed");
   if (p->n_items == 0) return RLXPP_OK;
   BatchArgs b{};
-  b.items = p->items;
-  b.n_items = p->n_items;
   b.req_stream = p->req_stream;
   b.snap_D = p->snap_D;
   b.snap_meta = p->snap_meta;
@@ -347,17 +366,38 @@ rlxpp_status run_impl(rlxpp_gen* g, const rlxpp_plan* p, uint32_t* out_u24, doub
   b.s = g->view();
   b.out_u24 = out_u24;
   b.out_f64 = reinterpret_cast<uint64_t*>(out_f64);
-  b.counter = p->counter;
   b.advance = (p->flags & RLXPP_REQ_ADVANCE) ? 1 : 0;
-  cudaError_t e = cudaMemsetAsync(p->counter, 0, sizeof(unsigned long long), st);
+  cudaError_t e = cudaMemsetAsync(p->counter, 0, sizeof(unsigned long long) * RLXPP_MAX_LEVELS, st);
   if (e == cudaSuccess) {
     k_snapshot<<<(unsigned)((p->n_reqs + 255) / 256), 256, 0, st>>>(b);
     e = cudaGetLastError();
   }
-  if (e == cudaSuccess) {
-    const unsigned grid = (unsigned)std::max(1, g->sms) * p->tuning.blocks_per_sm;
-    k_requests<<<grid, kReqBlock, 0, st>>>(b);
-    e = cudaGetLastError();
+  const unsigned grid = (unsigned)std::max(1, g->sms) * p->tuning.blocks_per_sm;
+  uint32_t busy = 0;
+  for (uint32_t l = 0; l < g->n_levels; ++l) busy += p->level_begin[l + 1] > p->level_begin[l];
+  if (busy <= 1) {
+    for (uint32_t l = 0; e == cudaSuccess && l < g->n_levels; ++l) {
+      const uint64_t n = p->level_begin[l + 1] - p->level_begin[l];
+      if (n == 0) continue;
+      k_requests<<<grid, kReqBlock, 0, st>>>(b, g->lux_host[l], p->items + p->level_begin[l], n, p->counter + l);
+      e = cudaGetLastError();
+    }
+  } else {
+    // one launch per level, concurrently on the handle's side streams (fork / join with
+    // events, which stream capture records as graph dependencies)
+    cudaEvent_t fork = g->level_event[g->n_levels];
+    e = cudaEventRecord(fork, st);
+    for (uint32_t l = 0; e == cudaSuccess && l < g->n_levels; ++l) {
+      const uint64_t n = p->level_begin[l + 1] - p->level_begin[l];
+      if (n == 0) continue;
+      cudaStream_t ls = g->level_stream[l];
+      e = cudaStreamWaitEvent(ls, fork, 0);
+      if (e != cudaSuccess) break;
+      k_requests<<<grid, kReqBlock, 0, ls>>>(b, g->lux_host[l], p->items + p->level_begin[l], n, p->counter + l);
+      e = cudaGetLastError();
+      if (e == cudaSuccess) e = cudaEventRecord(g->level_event[l], ls);
+      if (e == cudaSuccess) e = cudaStreamWaitEvent(st, g->level_event[l], 0);
+    }
   }
   if (e != cudaSuccess) return set_last_error(RLXPP_ERR_CUDA, (std::string("run plan: ") + cudaGetErrorString(e)).c_str());
   return RLXPP_OK;
@@ -413,13 +453,19 @@ rlxpp_status rlxpp_autotune_requests(rlxpp_gen* gen, const rlxpp_request* reqs, 
   rlxpp_tuning bestt{0, 0};
   float best_ms = 1e30f;
   rlxpp_status status = RLXPP_OK;
-  for (uint32_t L = 4; L <= 1024 && status == RLXPP_OK; L <<= 1) {
-    if (L > 4 && L / 2 >= std::max<uint64_t>(longest, 4)) break;  // longer chunks change nothing
+  // chunk lengths from the one giving ~64 chunks per resident thread (shorter ones only
+  // add jump-ahead work) up to 1024, and not beyond the longest request
+  const uint64_t threads = (uint64_t)std::max(1, gen->sms) * 4 * kReqBlock;
+  uint32_t L0 = 4;
+  while (L0 < 1024 && (uint64_t)L0 * threads * 64 < total) L0 <<= 1;
+  for (uint32_t L = L0; L <= 1024 && status == RLXPP_OK; L <<= 1) {
+    if (L > L0 && L / 2 >= std::max<uint64_t>(longest, 4)) break;  // longer chunks change nothing
+    rlxpp_tuning t{L, 4};
+    rlxpp_plan* p = nullptr;
+    status = plan_impl(gen, reqs, n_reqs, 0, &t, &p);
+    if (status != RLXPP_OK) break;
     for (uint32_t bps = 2; bps <= 4 && status == RLXPP_OK; ++bps) {
-      rlxpp_tuning t{L, bps};
-      rlxpp_plan* p = nullptr;
-      status = plan_impl(gen, reqs, n_reqs, 0, &t, &p);
-      if (status != RLXPP_OK) break;
+      p->tuning.blocks_per_sm = bps;  // the grid is chosen at run time
       float ms = 1e30f;
       for (int rep = 0; rep < 3 && status == RLXPP_OK; ++rep) {  // first run warms up
         cudaEventRecord(e0, st);
@@ -430,12 +476,12 @@ rlxpp_status rlxpp_autotune_requests(rlxpp_gen* gen, const rlxpp_request* reqs, 
         cudaEventElapsedTime(&m, e0, e1);
         if (rep > 0) ms = std::min(ms, m);
       }
-      free_plan(p, nullptr, false);
       if (status == RLXPP_OK && ms < best_ms) {
         best_ms = ms;
-        bestt = t;
+        bestt = rlxpp_tuning{L, bps};
       }
     }
+    free_plan(p, nullptr, false);
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);

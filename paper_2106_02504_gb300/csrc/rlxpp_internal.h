@@ -3,6 +3,7 @@
 #include <cstddef>
 #include <cstdint>
 #include <map>
+#include <vector>
 #include <cuda_runtime.h>
 
 #include "../../include/rlxpp.h"
@@ -108,6 +109,10 @@ struct rlxpp_gen {
   cudaEvent_t ev[4] = {};
   int sms = 0;                         // multiprocessors of the device
   std::map<uint32_t, rlxpp_tuning> tuned;  // request-shape signature -> tuner choice
+  std::vector<uint8_t> level_host;         // host copy of every stream's level index
+  cudaStream_t level_stream[RLXPP_MAX_LEVELS] = {};  // side streams: one per luxury level
+  cudaEvent_t level_event[RLXPP_MAX_LEVELS + 1] = {};  // fork (last) and per-level joins
+  bool level_host_stale = false;           // set_state may have changed levels
   rlxpp::StateView view() const { return rlxpp::StateView{D, meta, n, n, lux, table, status}; }
 };
 

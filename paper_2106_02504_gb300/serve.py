@@ -150,17 +150,26 @@ class Server:
             si = self.free_streams.popleft()
             st = self.streams[si]
             reqs = np.zeros(len(batch), dtype=B.request_dtype())
-            for k, r in enumerate(batch):
-                elem = 8 if r.kind == KIND_F64 else 4
-                reqs[k] = (r.stream, r.skip, r.pos, r.kind, r.count, r.offset // elem)
+            reqs["stream"] = [r.stream for r in batch]
+            reqs["skip"] = [r.skip for r in batch]
+            reqs["pos"] = [r.pos for r in batch]
+            reqs["kind"] = [r.kind for r in batch]
+            reqs["count"] = [r.count for r in batch]
+            reqs["offset"] = [r.offset // (8 if r.kind == KIND_F64 else 4) for r in batch]
             base = self.dev.data_ptr()
             with torch.cuda.stream(st):
                 B.rlxpp_draw_requests(self.gen.handle, reqs, base, base, 0, st)
                 if self.host is not None:
-                    for r in batch:
-                        if r.nbytes:
-                            self.host[r.offset:r.offset + r.nbytes].copy_(self.dev[r.offset:r.offset + r.nbytes],
-                                                                          non_blocking=True)
+                    # one copy per run of adjacent arena blocks of this batch
+                    spans = sorted((r.offset, r.reserved) for r in batch if r.nbytes)
+                    k = 0
+                    while k < len(spans):
+                        a, ln = spans[k]
+                        while k + 1 < len(spans) and spans[k + 1][0] == a + ln:
+                            ln += spans[k + 1][1]
+                            k += 1
+                        self.host[a:a + ln].copy_(self.dev[a:a + ln], non_blocking=True)
+                        k += 1
                 ev = torch.cuda.Event()
                 ev.record(st)
             t = self.now()
