@@ -43,6 +43,9 @@ IMAD_PER_ADVANCE = 648        # 18 x 18 products of 32 x 32 -> 64 bits = 324 lo 
 SMS = 152
 IMAD_PER_SM_CLK = 64
 SM_MAX_MHZ = 2070.0
+ALU_PER_SM_CLK = 64
+TC_FLOP_PER_ADVANCE = 2 * 80 * 80      # padded 128 x 80 x 80 fp16 product per 128 streams
+ALU_INSTR_PER_ADVANCE_TC = 299         # integer-pipe instructions per refill of k_draw_tc (ncu, fused kernel)
 CPU_SAMPLE_STREAMS = 16384
 
 
@@ -212,74 +215,94 @@ def run_native(args, rank, world, local_rank):
         if dist is not None:
             dist.barrier()
 
-    for _ in range(args.warmup):
-        step()
-    g.sync(sp)
+    def time_path(path):
+        g.set_path(path)
+        for _ in range(args.warmup):
+            step()
+        g.sync(sp)
+        evs = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(args.steps)]
+        t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        clk = ClockSampler(local_rank)
+        barrier()
+        torch.cuda.synchronize()
+        clk.start()
+        t0.record(stream)
+        for k in range(args.steps):
+            step(evs[k])
+        t1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+        clocks = clk.stop()
+        g.sync(sp)
+        ms = t0.elapsed_time(t1)
+        if dist is not None:
+            t = torch.tensor([ms], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms = float(t.item())
+        per_kernel = {
+            "seed": statistics.mean(e[0].elapsed_time(e[1]) for e in evs),
+            "draw_f64_hbm": statistics.mean(e[1].elapsed_time(e[2]) for e in evs),
+            "draw_f64_sum_hist": statistics.mean(e[2].elapsed_time(e[3]) for e in evs),
+        }
+        return ms / args.steps, per_kernel, clocks
+
     launches_per_step = 3
-    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(args.steps)]
-    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    clk = ClockSampler(local_rank)
-    barrier()
-    torch.cuda.synchronize()
-    clk.start()
-    t0.record(stream)
-    for k in range(args.steps):
-        step(evs[k])
-    t1.record(stream)
-    torch.cuda.synchronize()
-    barrier()
-    clocks = clk.stop()
-    g.sync(sp)
-    ms = t0.elapsed_time(t1)
-    if dist is not None:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    ms_step = ms / args.steps
-    per_kernel = {
-        "seed": statistics.mean(e[0].elapsed_time(e[1]) for e in evs),
-        "draw_f64_hbm": statistics.mean(e[1].elapsed_time(e[2]) for e in evs),
-        "draw_f64_sum_hist": statistics.mean(e[2].elapsed_time(e[3]) for e in evs),
-    }
-    doubles_step = n * (HBM_COUNT + FUSED_COUNT) * world
-    advances_step = n * ADV_PER_STREAM * world
-    value = doubles_step / (ms_step * 1e-3)
     peaks = load_peaks()
     imad_peak = SMS * IMAD_PER_SM_CLK * SM_MAX_MHZ * 1e6  # IMAD ops/s, derived
     hbm_peak = peaks.get("hbm_gbs", 6800.0)
-    kern = {}
-    for name, kms in per_kernel.items():
-        entry = {"ms": kms, "share": kms / sum(per_kernel.values())}
-        if name == "draw_f64_hbm":
-            adv = n * ADV_HBM
-            entry["advances_per_s"] = adv / (kms * 1e-3)
-            entry["imad_frac"] = adv * IMAD_PER_ADVANCE / (kms * 1e-3) / imad_peak
-            entry["hbm_gbs"] = n * HBM_COUNT * 8 / (kms * 1e-3) / 1e9
-            entry["hbm_frac"] = entry["hbm_gbs"] / hbm_peak
-        elif name == "draw_f64_sum_hist":
-            adv = n * ADV_FUSED
-            entry["advances_per_s"] = adv / (kms * 1e-3)
-            entry["imad_frac"] = adv * IMAD_PER_ADVANCE / (kms * 1e-3) / imad_peak
-        kern[name] = entry
+    f16_peak = peaks.get("bf16_tflops", 1900.0)  # dense f16 and bf16 run at the same rate
+    path_ids = {"imad": nat.RLXPP_PATH_IMAD, "tensor": nat.RLXPP_PATH_TENSOR}
+    paths = {}
+    for name in args.path.split(","):
+        ms_step, per_kernel, clocks = time_path(path_ids[name])
+        kern = {}
+        for kname, kms in per_kernel.items():
+            entry = {"ms": kms, "share": kms / sum(per_kernel.values())}
+            adv = {"draw_f64_hbm": n * ADV_HBM, "draw_f64_sum_hist": n * ADV_FUSED}.get(kname)
+            if adv:
+                entry["advances_per_s"] = adv / (kms * 1e-3)
+                entry["imad_equiv_frac"] = adv * IMAD_PER_ADVANCE / (kms * 1e-3) / imad_peak
+                if name == "tensor":  # 128 x 80 x 80 fp16 MMA per 128-stream tile and refill
+                    entry["tensor_tflops"] = adv * TC_FLOP_PER_ADVANCE / (kms * 1e-3) / 1e12
+                    entry["tensor_frac"] = entry["tensor_tflops"] / f16_peak
+            if kname == "draw_f64_hbm":
+                entry["hbm_gbs"] = n * HBM_COUNT * 8 / (kms * 1e-3) / 1e9
+                entry["hbm_frac"] = entry["hbm_gbs"] / hbm_peak
+            kern[kname] = entry
+        paths[name] = {"ms_per_step": ms_step, "value": n * (HBM_COUNT + FUSED_COUNT) * world / (ms_step * 1e-3),
+                       "kernels": kern, "per_kernel_ms": per_kernel, "clocks": clocks}
+    best = max(paths, key=lambda k: paths[k]["value"])
+    ms_step, per_kernel, clocks = paths[best]["ms_per_step"], paths[best]["per_kernel_ms"], paths[best]["clocks"]
+    doubles_step = n * (HBM_COUNT + FUSED_COUNT) * world
+    advances_step = n * ADV_PER_STREAM * world
+    value = doubles_step / (ms_step * 1e-3)
     dom = max(per_kernel, key=per_kernel.get)
-    if dom == "draw_f64_sum_hist":
-        adv = n * ADV_FUSED
-    elif dom == "draw_f64_hbm":
-        adv = n * ADV_HBM
+    adv = {"draw_f64_sum_hist": n * ADV_FUSED, "draw_f64_hbm": n * ADV_HBM}.get(dom, 0)
+    if best == "imad":
+        achieved = adv * IMAD_PER_ADVANCE / (per_kernel[dom] * 1e-3) / 1e12
+        roofline = {"bound": "alu", "kernel": dom + " (k_draw, integer pipe)", "achieved": achieved,
+                    "peak": imad_peak / 1e12, "unit": "Top/s (32-bit IMAD, 648 per advance)",
+                    "frac": achieved / (imad_peak / 1e12),
+                    "peak_source": "derived: 152 SMs x 64 IMAD/clk x 2070 MHz", "traffic": None}
     else:
-        adv = 0
-    achieved = adv * IMAD_PER_ADVANCE / (per_kernel[dom] * 1e-3) / 1e12
-    roofline = {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": imad_peak / 1e12,
-                "unit": "Top/s (32-bit IMAD, 648 per advance)", "frac": achieved / (imad_peak / 1e12),
-                "peak_source": "derived: 152 SMs x 64 IMAD/clk x 2070 MHz", "traffic": None}
-
+        achieved = adv * ALU_INSTR_PER_ADVANCE_TC / (per_kernel[dom] * 1e-3) / 1e12
+        roofline = {"bound": "alu", "kernel": dom + " (k_draw_tc, tensor path)", "achieved": achieved,
+                    "peak": SMS * ALU_PER_SM_CLK * SM_MAX_MHZ * 1e6 / 1e12,
+                    "unit": f"Top/s (integer-pipe instructions of the epilogue, {ALU_INSTR_PER_ADVANCE_TC} per advance)",
+                    "frac": achieved / (SMS * ALU_PER_SM_CLK * SM_MAX_MHZ * 1e6 / 1e12),
+                    "peak_source": "derived: 152 SMs x 64 ALU lanes/clk x 2070 MHz", "traffic": None,
+                    "tensor_pipe": {"achieved_tflops": adv * TC_FLOP_PER_ADVANCE / (per_kernel[dom] * 1e-3) / 1e12,
+                                    "peak_tflops": f16_peak, "peak_source": "MEASURED_PEAKS bf16_tflops (burst)"}}
+    for name in paths:
+        paths[name].pop("per_kernel_ms")
     result = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
               "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
               "vs_baseline": None, "dtype": "u32", "data": "synthetic",
-              "config": workload_config(n, world),
+              "config": dict(workload_config(n, world), path=best),
               "advances_per_s": advances_step / (ms_step * 1e-3),
-              "gpu_launches": launches_per_step * args.steps, "kernels": kern, "roofline": roofline,
-              "clocks": clocks}
+              "gpu_launches": launches_per_step * args.steps, "kernels": paths[best]["kernels"],
+              "roofline": roofline, "clocks": clocks, "paths": paths}
+    g.set_path(path_ids[best])
 
     # end to end through the C ABI with host buffers
     if not args.no_e2e:
@@ -497,6 +520,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--only-main", action="store_true", help="skip the other workloads")
+    ap.add_argument("--path", default="imad,tensor", help="refill paths to time; the faster one is reported")
     ap.add_argument("--batch-streams", type=int, default=65536)
     ap.add_argument("--serve-seconds", type=float, default=5.0)
     ap.add_argument("--serve-pool-gib", type=int, default=8)

@@ -207,6 +207,21 @@ rlxpp_status rlxpp_set_state(rlxpp_gen* gen, const rlxpp_state* src, void* cuda_
  * status: RLXPP_OK, RLXPP_ERR_INVALID or RLXPP_ERR_TIMEOUT. */
 rlxpp_status rlxpp_sync(rlxpp_gen* gen, void* cuda_stream);
 
+/* ---- refill path -------------------------------------------------------------------
+ * RLXPP_PATH_IMAD (default): the product on the integer pipe, one thread per stream.
+ * RLXPP_PATH_TENSOR: the product A X mod m as an exact-integer fp16 matrix product on
+ * the tensor cores (tcgen05.mma, fp32 accumulation in tensor memory): with
+ * R_j = A 2^(8j) mod m, A X = sum_j x_j R_j = sum_k S_k 2^(8k) (mod m) where x_j are
+ * the 72 bytes of X and S_k = sum_j x_j byte_k(R_j) < 2^23, so a tile of 128 streams is
+ * one 128 x 80 x 80 product per refill (Sec. 2.1-2.2 computed differently, same
+ * result).  Only for handles with one luxury level (else RLXPP_ERR_UNSUPPORTED); used
+ * by rlxpp_draw_u24/f64/f64_sum_hist, not by batched requests.  Synchronises the
+ * device.  Both paths give bit-identical results. */
+#define RLXPP_PATH_IMAD 0u
+#define RLXPP_PATH_TENSOR 1u
+rlxpp_status rlxpp_set_path(rlxpp_gen* gen, uint32_t path);
+uint32_t rlxpp_get_path(const rlxpp_gen* gen);
+
 /* Number of streams of the handle. */
 uint64_t rlxpp_num_streams(const rlxpp_gen* gen);
 
@@ -272,6 +287,11 @@ rlxpp_status rlxpp_test_to_lcg(const uint64_t* d, const uint32_t* carry, uint64_
                                uint64_t n, void* cuda_stream);
 rlxpp_status rlxpp_test_f64_from48(const uint64_t* v, uint64_t* out, uint64_t n,
                                    void* cuda_stream);
+
+/* One tensor-path product per item: out[9] = A x mod m for luxury p (x < m, device
+ * arrays of 9 uint64 limbs per item); synchronous. */
+rlxpp_status rlxpp_test_tc_mulmod(uint32_t p, const uint64_t* x, uint64_t* out, uint64_t n,
+                                  void* cuda_stream);
 
 /* Luxury multiplier A = a^p mod m as 9 uint64 limbs written to host memory out9,
  * computed on the device (Sec. 1: RANLUX as an LCG with a large multiplier). */

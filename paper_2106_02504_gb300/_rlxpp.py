@@ -34,6 +34,7 @@ class RlxppTuning(ctypes.Structure):
 
 
 RLXPP_KIND_U24, RLXPP_KIND_F64 = 0, 1
+RLXPP_PATH_IMAD, RLXPP_PATH_TENSOR = 0, 1
 RLXPP_REQ_ADVANCE = 1
 
 
@@ -83,6 +84,8 @@ def _load():
         "rlxpp_run_plan": [_vp, _vp, _vp, _vp, _vp],
         "rlxpp_draw_requests": [_vp, _vp, _u64, _vp, _vp, _u32, _vp],
         "rlxpp_autotune_requests": [_vp, _vp, _u64, _vp, _vp, _vp, _vp],
+        "rlxpp_set_path": [_vp, _u32],
+        "rlxpp_test_tc_mulmod": [_u32, _vp, _vp, _u64, _vp],
     }
     for name, args in sigs.items():
         fn = getattr(L, name)
@@ -98,6 +101,8 @@ def _load():
     L.rlxpp_plan_items.restype = _u64
     L.rlxpp_plan_tuning.argtypes = [_vp]
     L.rlxpp_plan_tuning.restype = RlxppTuning
+    L.rlxpp_get_path.argtypes = [_vp]
+    L.rlxpp_get_path.restype = _u32
     L.rlxpp_destroy_plan.argtypes = [_vp]
     L.rlxpp_destroy_plan.restype = None
     return L
@@ -284,6 +289,18 @@ def rlxpp_autotune_requests(gen, reqs, out_u24=None, out_f64=None, stream=None):
     return (t.chunk_blocks, t.blocks_per_sm)
 
 
+def rlxpp_set_path(gen, path):
+    _check(_lib.rlxpp_set_path(gen, path))
+
+
+def rlxpp_get_path(gen):
+    return int(_lib.rlxpp_get_path(gen))
+
+
+def rlxpp_test_tc_mulmod(p, x, out, n, stream=None):
+    _check(_lib.rlxpp_test_tc_mulmod(p, _ptr(x), _ptr(out), n, _stream(stream)))
+
+
 def rlxpp_luxury_multiplier(p):
     """A = a^p mod m as a Python int (computed on the device)."""
     out = (ctypes.c_uint64 * 9)()
@@ -310,6 +327,9 @@ class Generator:
 
     def draw_f64(self, out, count_each=0, counts=None, offsets=None, stream=None):
         rlxpp_draw_f64(self.handle, out, count_each, counts, offsets, stream)
+
+    def set_path(self, path):
+        rlxpp_set_path(self.handle, path)
 
     def draw_requests(self, reqs, out_u24=None, out_f64=None, flags=0, stream=None):
         rlxpp_draw_requests(self.handle, reqs, out_u24, out_f64, flags, stream)

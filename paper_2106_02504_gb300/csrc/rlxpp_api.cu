@@ -103,6 +103,7 @@ void free_gen(rlxpp_gen* g) {
   cudaFree(g->table);
   cudaFree(g->level_p);
   cudaFree(g->status);
+  cudaFree(g->tc_matrix);
   for (auto& e : g->ev)
     if (e) cudaEventDestroy(e);
   for (auto& e : g->level_event)
@@ -122,6 +123,12 @@ DrawArgs make_args(const rlxpp_gen* g) {
 }
 
 constexpr size_t kChunkBytes = size_t(256) << 20;  // device staging per chunk of host output
+
+// The draw kernels of the handle's path: integer pipe, or tensor cores (single level).
+cudaError_t launch_path(const rlxpp_gen* g, int kind, const DrawArgs& a, cudaStream_t st) {
+  if (g->path == RLXPP_PATH_TENSOR) return launch_draw_tc(kind, a, g->tc_matrix, st);
+  return launch_draw(kind, a, st);
+}
 
 // Draw of kind (u24 / f64) into out; host outputs go through device chunks that are
 // copied back on a second stream while the next chunk computes.
@@ -144,7 +151,7 @@ rlxpp_status draw_common(rlxpp_gen* g, int kind, const int64_t* counts, const in
   a.count_each = count_each;
   if (on_device(out)) {
     a.out = out;
-    cudaError_t e = launch_draw(kind, a, st);
+    cudaError_t e = launch_path(g, kind, a, st);
     if (e != cudaSuccess) return fail(RLXPP_ERR_CUDA, std::string("draw: ") + cudaGetErrorString(e));
     return RLXPP_OK;
   }
@@ -165,7 +172,7 @@ rlxpp_status draw_common(rlxpp_gen* g, int kind, const int64_t* counts, const in
     // keep untouched elements of the caller's buffer: start from its contents
     cudaError_t e = cudaMemcpyAsync(dev, out, (size_t)total * elem, cudaMemcpyHostToDevice, st);
     a.out = dev;
-    if (e == cudaSuccess) e = launch_draw(kind, a, st);
+    if (e == cudaSuccess) e = launch_path(g, kind, a, st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(out, dev, (size_t)total * elem, cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     cudaFreeAsync(dev, st);
@@ -191,7 +198,7 @@ rlxpp_status draw_common(rlxpp_gen* g, int kind, const int64_t* counts, const in
     c.s.meta = g->meta + s0;
     c.s.n = s1 - s0;
     c.out = buf[b];
-    e = launch_draw(kind, c, st);
+    e = launch_path(g, kind, c, st);
     if (e == cudaSuccess) e = cudaEventRecord(g->ev[b], st);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(g->copy_stream, g->ev[b], 0);
     if (e == cudaSuccess)
@@ -343,7 +350,7 @@ rlxpp_status rlxpp_draw_f64_sum_hist(rlxpp_gen* g, int64_t count_each, uint64_t*
   do {
     a.count_each = std::min(count_each - done, kMaxPerLaunch);
     a.accumulate_sums = done > 0;
-    cudaError_t e = launch_draw(kDrawSumHist, a, st);
+    cudaError_t e = launch_path(g, kDrawSumHist, a, st);
     if (e != cudaSuccess) return fail(RLXPP_ERR_CUDA, std::string("sum/hist: ") + cudaGetErrorString(e));
     done += a.count_each;
   } while (done < count_each);
@@ -398,6 +405,24 @@ rlxpp_status rlxpp_sync(rlxpp_gen* g, void* cuda_stream) {
   return RLXPP_OK;
 }
 
+rlxpp_status rlxpp_set_path(rlxpp_gen* g, uint32_t path) {
+  if (rlxpp_status s = check_gen(g)) return s;
+  if (path != RLXPP_PATH_IMAD && path != RLXPP_PATH_TENSOR) return fail(RLXPP_ERR_INVALID, "unknown path");
+  if (path == RLXPP_PATH_TENSOR) {
+    if (g->n_levels != 1) return fail(RLXPP_ERR_UNSUPPORTED, "the tensor path serves single-level handles");
+    if (!g->tc_matrix) {
+      RLX_CUDA(cudaMalloc(&g->tc_matrix, tc_matrix_bytes()));
+      RLX_CUDA(launch_tc_matrix(g->lux, g->tc_matrix, nullptr));
+      RLX_CUDA(cudaStreamSynchronize(nullptr));
+    }
+  }
+  RLX_CUDA(cudaDeviceSynchronize());  // no draw of the old path may still run
+  g->path = path;
+  return RLXPP_OK;
+}
+
+uint32_t rlxpp_get_path(const rlxpp_gen* g) { return g ? g->path : 0u; }
+
 uint64_t rlxpp_num_streams(const rlxpp_gen* g) { return g ? g->n : 0; }
 
 const char* rlxpp_last_error(void) { return g_last_error.c_str(); }
@@ -441,6 +466,34 @@ rlxpp_status rlxpp_test_to_lcg(const uint64_t* d, const uint32_t* carry, uint64_
 }
 rlxpp_status rlxpp_test_f64_from48(const uint64_t* v, uint64_t* out, uint64_t n, void* cuda_stream) {
   return run_test(kTestF64, v, nullptr, out, nullptr, n, cuda_stream);
+}
+
+rlxpp_status rlxpp_test_tc_mulmod(uint32_t p, const uint64_t* x, uint64_t* out, uint64_t n, void* cuda_stream) {
+  if (p == 0) return fail(RLXPP_ERR_INVALID, "need p >= 1");
+  if (n == 0) return RLXPP_OK;
+  if (!x || !out) return fail(RLXPP_ERR_INVALID, "null test buffer");
+  cudaStream_t st = as_stream(cuda_stream);
+  uint32_t *lux = nullptr, *table = nullptr;
+  void* mat = nullptr;
+  int* status = nullptr;
+  cudaError_t e = cudaMalloc(&lux, sizeof(uint32_t) * 18);
+  if (e == cudaSuccess) e = cudaMalloc(&table, sizeof(uint32_t) * kTableLimbs);
+  if (e == cudaSuccess) e = cudaMalloc(&mat, tc_matrix_bytes());
+  if (e == cudaSuccess) e = cudaMalloc(&status, sizeof(int));
+  if (e == cudaSuccess) e = cudaMemsetAsync(status, 0, sizeof(int), st);
+  if (e == cudaSuccess) e = launch_level_setup(p, lux, table, st);
+  if (e == cudaSuccess) e = launch_tc_matrix(lux, mat, st);
+  if (e == cudaSuccess) e = launch_tc_mulmod(mat, x, out, n, status, st);
+  int h = 0;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&h, status, sizeof(int), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  cudaFree(lux);
+  cudaFree(table);
+  cudaFree(mat);
+  cudaFree(status);
+  if (e != cudaSuccess) return fail(RLXPP_ERR_CUDA, std::string("tensor test: ") + cudaGetErrorString(e));
+  if (h) return fail((rlxpp_status)h, "tensor test: a bounded wait gave up");
+  return RLXPP_OK;
 }
 
 rlxpp_status rlxpp_luxury_multiplier(uint32_t p, uint64_t* out9) {

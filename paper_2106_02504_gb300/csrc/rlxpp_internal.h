@@ -72,6 +72,12 @@ cudaError_t launch_export(const StateView& s, const uint32_t* level_p, rlxpp_sta
                           cudaStream_t st);
 cudaError_t launch_import(const StateView& s, const uint32_t* level_p, uint32_t n_levels,
                           const rlxpp_state* src, cudaStream_t st);
+// tensor-core refill (rlxpp_tensor.cu)
+size_t tc_matrix_bytes();
+cudaError_t launch_tc_matrix(const uint32_t* lux18, void* bimg, cudaStream_t st);
+cudaError_t launch_draw_tc(int kind, const DrawArgs& a, const void* bimg, cudaStream_t st);
+cudaError_t launch_tc_mulmod(const void* bimg, const uint64_t* x, uint64_t* out, uint64_t n, int* status,
+                             cudaStream_t st);
 cudaError_t launch_test(int which, const uint64_t* x, const uint64_t* y, uint64_t* out,
                         uint32_t* carry, uint64_t n, cudaStream_t st);
 
@@ -113,6 +119,8 @@ struct rlxpp_gen {
   cudaStream_t level_stream[RLXPP_MAX_LEVELS] = {};  // side streams: one per luxury level
   cudaEvent_t level_event[RLXPP_MAX_LEVELS + 1] = {};  // fork (last) and per-level joins
   bool level_host_stale = false;           // set_state may have changed levels
+  uint32_t path = 0;                       // RLXPP_PATH_IMAD or RLXPP_PATH_TENSOR
+  void* tc_matrix = nullptr;               // [n_levels] tensor-path matrices (on first use)
   rlxpp::StateView view() const { return rlxpp::StateView{D, meta, n, n, lux, table, status}; }
 };
 

@@ -1,0 +1,486 @@
+// The refill on the tensor cores (tcgen05, sm_103a): the product A X mod m of Sec. 2.1-2.2
+// as an exact-integer fp16 matrix product.
+//
+// With X = sum_j x_j 2^(8j) (72 bytes) and R_j = A 2^(8j) mod m (72 bytes each),
+//   A X = sum_j x_j R_j = sum_k S_k 2^(8k) (mod m),   S_k = sum_j x_j byte_k(R_j),
+// so one refill of a tile of 128 streams is the product of a 128 x 72 byte matrix (the
+// streams' X) with the 72 x 72 byte matrix of the level.  Bytes are exact in fp16, each
+// product is below 2^16 and every partial sum below 72 * 255^2 < 2^23, so fp32
+// accumulation is exact.  An extra K row (x_72 = 2048 against 4096) adds 2^23 to every
+// column: the fp32 bit pattern of 2^23 + S is then 0x4B000000 + S, which gives S with
+// one logical AND.  K = 80 and N = 80 after padding (five K = 16 instructions).
+//
+// One CTA owns one tile (128 threads, one stream per thread = one TMEM lane).  Per
+// refill: each thread writes its X as fp16 into the shared A tile, one thread issues
+// the five MMAs and commits them to an mbarrier, every thread waits (bounded) and loads
+// its row of the fp32 accumulator from TMEM, forms the 590-bit sum of S_k 2^(8k), folds
+// it below m (2^576 = 2^240 - 1 mod m) and continues with the conversion to RANLUX
+// numbers (Sec. 2.3) and the output, as the integer-pipe kernels do.
+//
+// Shared operand layout (both operands K-major, no swizzle): core matrices of 8 rows x
+// 16 bytes; element (row, k) of a 80-wide K tile sits at
+//   (row / 8) * 1280 + (k / 8) * 128 + (row % 8) * 16 + (k % 8) * 2 bytes,
+// i.e. leading-dimension byte offset (between K-adjacent core matrices) 128 and stride
+// byte offset (between 8-row groups) 1280.
+#include <cuda_fp16.h>
+
+#include "rlxpp_arith.cuh"
+#include "rlxpp_drawloop.cuh"
+#include "rlxpp_internal.h"
+#include "rlxpp_state.cuh"
+
+namespace rlxpp {
+namespace {
+
+constexpr int kTcRows = 128;                 // streams per tile = TMEM lanes = M
+constexpr int kTcK = 80;                     // 72 bytes + bias + padding
+constexpr int kTcN = 80;                     // 72 output columns + padding
+constexpr int kTcCols = 128;                 // TMEM columns allocated (power of two >= N)
+constexpr int kTileBytes = kTcRows * kTcK * 2;   // 20480
+constexpr int kBBytes = kTcN * kTcK * 2;         // 12800
+constexpr int kLBO = 128, kSBO = 1280;
+constexpr uint64_t kWaitLimit = 1ull << 22;  // mbarrier polls (about 0.3 s) before giving up
+
+// fp16 element offset of (row, k) in a K-major 80-wide tile
+__host__ __device__ constexpr int tc_off(int row, int k) {
+  return (row >> 3) * (kSBO / 2) + (k >> 3) * (kLBO / 2) + (row & 7) * 8 + (k & 7);
+}
+
+// ---- PTX wrappers ----------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+      : "=r"(ok)
+      : "r"(smem_addr(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
+  for (uint64_t i = 0; i < kWaitLimit; ++i) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if (i > 64) __nanosleep(64);
+  }
+  return false;
+}
+__device__ __forceinline__ void fence_barrier_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void fence_proxy_async_smem() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_before() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+// whole warp: allocate ncols TMEM columns, address written to *dst (shared)
+__device__ __forceinline__ void tmem_alloc(uint32_t* dst, uint32_t ncols) {
+  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(dst)),
+               "r"(ncols)
+               : "memory");
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr) {
+  // start address, LBO and SBO in 16-byte units; version 1 (bits 46-47); no swizzle
+  return (uint64_t)((saddr >> 4) & 0x3FFFu) | ((uint64_t)(kLBO >> 4) << 16) | ((uint64_t)(kSBO >> 4) << 32) |
+         (1ull << 46);
+}
+// kind::f16 instruction descriptor: D f32, A and B f16, both K-major, N = 80, M = 128
+constexpr uint32_t kIdesc = (1u << 4) | ((uint32_t)(kTcN >> 3) << 17) | ((uint32_t)(kTcRows >> 4) << 24);
+
+__device__ __forceinline__ void tc_mma(uint32_t d_tmem, uint64_t a_desc, uint64_t b_desc, uint32_t accumulate) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(d_tmem),
+      "l"(a_desc), "l"(b_desc), "r"(kIdesc), "r"(accumulate)
+      : "memory");
+}
+__device__ __forceinline__ void tc_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                   smem_addr(bar))
+               : "memory");
+}
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t* v) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+        "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+      : "r"(taddr));
+}
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t* v) {
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+               : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7])
+               : "r"(taddr));
+}
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
+// ---- per-thread pieces -------------------------------------------------------------
+// X (18 limbs) -> 72 fp16 values (one per byte) in this thread's row of the A tile
+// (chunks 0..8 of the row, 16 bytes each).  (0x6400 | b) is the fp16 1024 + b, exact.
+__device__ __forceinline__ void write_x_row(__half* tile, int row, const uint32_t X[kLimbs]) {
+  const __half2 k1024 = __floats2half2_rn(1024.f, 1024.f);
+  uint4* base = reinterpret_cast<uint4*>(tile + tc_off(row, 0));
+#pragma unroll
+  for (int c = 0; c < 9; ++c) {  // chunk c = bytes 8c .. 8c+7 = limbs 2c, 2c+1
+    uint32_t w[4];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const uint32_t L = X[2 * c + h];
+      const uint32_t lo = __byte_perm(L, 0x64646464u, 0x4140u);  // (1024+b0, 1024+b1)
+      const uint32_t hi = __byte_perm(L, 0x64646464u, 0x4342u);  // (1024+b2, 1024+b3)
+      __half2 a = __hsub2(*reinterpret_cast<const __half2*>(&lo), k1024);
+      __half2 b = __hsub2(*reinterpret_cast<const __half2*>(&hi), k1024);
+      w[2 * h] = *reinterpret_cast<uint32_t*>(&a);
+      w[2 * h + 1] = *reinterpret_cast<uint32_t*>(&b);
+    }
+    base[c * (kLBO / 16)] = make_uint4(w[0], w[1], w[2], w[3]);
+  }
+}
+
+// Column sums S_0..S_71 (fp32 bits with the 2^23 bias) -> X = sum_k S_k 2^(8k) mod m.
+__device__ __forceinline__ void columns_to_x(const uint32_t col[72], uint32_t X[kLimbs]) {
+  // limb t gathers S_4t + S_4t+1 2^8 + S_4t+2 2^16 + S_4t+3 2^24 (below 2^48) as lo + hi 2^32
+  uint32_t lo[kLimbs], hi[kLimbs];
+#pragma unroll
+  for (int t = 0; t < kLimbs; ++t) {
+    const uint32_t s0 = col[4 * t] & 0x7FFFFFu, s1 = col[4 * t + 1] & 0x7FFFFFu;
+    const uint32_t s2 = col[4 * t + 2] & 0x7FFFFFu, s3 = col[4 * t + 3] & 0x7FFFFFu;
+    const uint32_t u = s0 + (s1 << 8);  // < 2^31
+    const uint32_t v = s2 + (s3 << 8);  // < 2^31
+    lo[t] = add_cc(u, v << 16);
+    hi[t] = addc(v >> 16, 0u);
+  }
+  // value = sum_t lo_t 2^(32t) + hi_t 2^(32(t+1)): one carry chain, top limb T < 2^15
+  X[0] = lo[0];
+  X[1] = add_cc(lo[1], hi[0]);
+#pragma unroll
+  for (int t = 2; t < kLimbs; ++t) X[t] = addc_cc(lo[t], hi[t - 1]);
+  const uint32_t T = addc(hi[kLimbs - 1], 0u);
+  // fold: X + T (2^240 - 1).  T (2^240 - 1) = (T - 1) 2^240 + (2^240 - T) for T >= 1:
+  // limb 0 = 2^32 - T, limbs 1..6 all ones, limb 7 = ((T - 1) << 16) | 0xFFFF.
+  const uint32_t nz = T ? 0xFFFFFFFFu : 0u;
+  X[0] = add_cc(X[0], 0u - T);
+#pragma unroll
+  for (int k = 1; k < 7; ++k) X[k] = addc_cc(X[k], nz);
+  X[7] = addc_cc(X[7], ((T - 1u) << 16 | 0xFFFFu) & nz);
+#pragma unroll
+  for (int k = 8; k < kLimbs; ++k) X[k] = addc_cc(X[k], 0u);
+  const uint32_t c = addc(0u, 0u);
+  if (c) {  // another 2^576: the low part is below 2^256, add 2^240 - 1 again (rare)
+    X[0] = add_cc(X[0], 0xFFFFFFFFu);
+#pragma unroll
+    for (int k = 1; k < 7; ++k) X[k] = addc_cc(X[k], 0xFFFFFFFFu);
+    X[7] = addc(X[7], 0xFFFFu);
+  }
+  // X >= m needs bits 240..575 all set (rare): then X - m = X + 2^240 - 1 mod 2^576
+  const uint32_t top = X[8] & X[9] & X[10] & X[11] & X[12] & X[13] & X[14] & X[15] & X[16] & X[17];
+  if (top == 0xFFFFFFFFu && X[7] >= 0xFFFF0000u) {
+    uint32_t e[kLimbs];
+    e[0] = add_cc(X[0], 0xFFFFFFFFu);
+#pragma unroll
+    for (int k = 1; k < 7; ++k) e[k] = addc_cc(X[k], 0xFFFFFFFFu);
+    e[7] = addc_cc(X[7], 0xFFFFu);
+#pragma unroll
+    for (int k = 8; k < kLimbs; ++k) e[k] = addc_cc(X[k], 0u);
+    const uint32_t ge = addc(0u, 0u);
+#pragma unroll
+    for (int k = 0; k < kLimbs; ++k) X[k] = ge ? e[k] : X[k];
+  }
+}
+
+struct TcShared {
+  uint64_t bar;      // MMA completion
+  uint32_t taddr;    // TMEM base
+  int any;           // tile still refilling
+};
+
+// Setup per tile: the level's matrix into shared memory, the constant chunk 9 of every
+// row (bias 2048 at k = 72, zeros after it), the mbarrier and the TMEM columns.
+__device__ __forceinline__ void tc_setup(__half* tile, __half* bmat, const __half* __restrict__ bimg, TcShared* sh) {
+  const int tid = threadIdx.x;
+  const uint4* src = reinterpret_cast<const uint4*>(bimg);
+  uint4* dst = reinterpret_cast<uint4*>(bmat);
+  for (int i = tid; i < kBBytes / 16; i += kTcRows) dst[i] = src[i];
+  {
+    __half* row9 = tile + tc_off(tid, 72);
+    row9[0] = __float2half(2048.f);
+#pragma unroll
+    for (int k = 1; k < 8; ++k) row9[k] = __float2half(0.f);
+  }
+  if (tid == 0) {
+    mbar_init(&sh->bar, 1);
+    fence_barrier_init();
+  }
+  if (tid < 32) tmem_alloc(&sh->taddr, kTcCols);
+  fence_proxy_async_smem();
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+}
+
+// One refill of the whole tile: rows already written; returns false on a wait timeout.
+__device__ __forceinline__ bool tc_refill(__half* tile, __half* bmat, TcShared* sh, uint32_t& phase,
+                                          uint32_t col[72]) {
+  const int tid = threadIdx.x;
+  fence_proxy_async_smem();  // this thread's row writes -> visible to the tensor core
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t taddr = sh->taddr;
+  if (tid == 0) {
+    const uint32_t a0 = smem_addr(tile), b0 = smem_addr(bmat);
+#pragma unroll
+    for (int s = 0; s < kTcK / 16; ++s)  // K = 16 per instruction: two core matrices
+      tc_mma(taddr, smem_desc(a0 + s * 2 * kLBO), smem_desc(b0 + s * 2 * kLBO), s > 0 ? 1u : 0u);
+    tc_commit(&sh->bar);
+  }
+  const bool ok = mbar_wait_bounded(&sh->bar, phase);
+  if (__syncthreads_and(ok) == 0) return false;  // phase stays: the teardown waits on it
+  phase ^= 1u;
+  tc_fence_after();
+  const uint32_t lane_addr = taddr + ((uint32_t)((tid / 32) * 32) << 16);
+#pragma unroll
+  for (int q = 0; q < 4; ++q) tmem_ld16(lane_addr + 16 * q, col + 16 * q);
+  tmem_ld8(lane_addr + 64, col + 64);
+  tmem_wait_ld();
+  return true;
+}
+
+// Release the TMEM columns.  After a timed-out wait (pending), first wait once more,
+// again with a limit, for the MMA that may still be writing them.
+__device__ __forceinline__ void tc_teardown(TcShared* sh, bool pending, uint32_t phase) {
+  if (pending) (void)mbar_wait_bounded(&sh->bar, phase);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (threadIdx.x < 32) tmem_dealloc(sh->taddr, kTcCols);
+}
+
+// Draw kernel on the tensor path (single-level handles).  Same semantics as k_draw.
+template <int Kind>
+__global__ void __launch_bounds__(kTcRows, 4) k_draw_tc(const DrawArgs a, const __half* __restrict__ bimg) {
+  extern __shared__ __align__(1024) unsigned char smem[];
+  __half* tile = reinterpret_cast<__half*>(smem);
+  __half* bmat = reinterpret_cast<__half*>(smem + kTileBytes);
+  TcShared* sh = reinterpret_cast<TcShared*>(smem + kTileBytes + kBBytes);
+  __shared__ unsigned int hist_s[Kind == kDrawSumHist ? 4 * 256 : 1];
+  const int tid = threadIdx.x;
+  if (Kind == kDrawSumHist)
+    for (int t = tid; t < 4 * 256; t += kTcRows) hist_s[t] = 0;
+  tc_setup(tile, bmat, bimg, sh);
+
+  const StateView& s = a.s;
+  const uint64_t i = (uint64_t)blockIdx.x * kTcRows + tid;
+  const bool live = i < s.n;
+  int64_t cnt = 0, base = 0;
+  uint32_t pos = kWords, c = 0, lvl = 0;
+  uint32_t D[kLimbs];
+#pragma unroll
+  for (int k = 0; k < kLimbs; ++k) D[k] = 0;
+  if (live) {
+    if (a.counts) {
+      cnt = a.counts[i];
+      base = a.offsets[i];
+    } else {
+      cnt = a.count_each;
+      base = (int64_t)i * a.count_each;
+    }
+    const uint32_t meta = s.meta[i];
+    pos = meta_pos(meta);
+    c = meta_carry(meta);
+    lvl = meta_level(meta);
+    load_state_D(s, i, D);
+  }
+  Consumer<Kind> out;
+  if constexpr (Kind == kDrawU24) out.out = static_cast<uint32_t*>(a.out);
+  if constexpr (Kind == kDrawF64) out.out = static_cast<uint64_t*>(a.out);
+  if constexpr (Kind == kDrawSumHist) {
+    out.sum = 0;
+    out.hist = hist_s + (tid / 32) * 256;
+  }
+  constexpr int need = Kind == kDrawU24 ? 1 : 2;
+  constexpr int per_block = kWords / need;
+  int64_t k = 0;
+  if (live && cnt > 0 && pos + need <= (uint32_t)kWords) {  // head of the current block
+    const int64_t room = (kWords - pos) / need;
+    const int64_t h = cnt < room ? cnt : room;
+#pragma unroll
+    for (int w = 0; w + need <= kWords; ++w) {
+      const int d = w - (int)pos;
+      if (d >= 0 && d % need == 0 && d / need < h) out.value_at_word(D, w, base + d / need);
+    }
+    k = h;
+    pos += (uint32_t)(h * need);
+  }
+  bool mine = live && k < cnt;
+  bool refilled = false;
+  uint32_t X[kLimbs];
+  to_lcg(D, c, X);
+  uint32_t phase = 0;
+  bool ok = true;
+  while (__syncthreads_or(mine)) {
+    write_x_row(tile, tid, X);
+    uint32_t col[72];
+    if (!tc_refill(tile, bmat, sh, phase, col)) {
+      ok = false;
+      break;
+    }
+    uint32_t Xn[kLimbs];
+    columns_to_x(col, Xn);
+    if (mine) {
+#pragma unroll
+      for (int q = 0; q < kLimbs; ++q) X[q] = Xn[q];
+      to_ranlux(X, D);
+      refilled = true;
+      const int64_t rem = cnt - k;
+      if (rem >= per_block) {
+        out.block(D, base + k);
+        k += per_block;
+        pos = kWords;
+      } else {
+        out.partial(D, base + k, rem);
+        k = cnt;
+        pos = (uint32_t)(rem * need);
+      }
+      mine = k < cnt;
+    }
+  }
+  if (!ok) {
+    if (tid == 0) atomicCAS(s.status, 0, (int)RLXPP_ERR_TIMEOUT);
+  } else if (live) {
+    if (refilled) {
+      c = carry_of(X, D);
+      store_state_D(s, i, D);
+    }
+    s.meta[i] = meta_pack(pos, c, lvl);
+    if constexpr (Kind == kDrawSumHist) {
+      uint64_t* sums = static_cast<uint64_t*>(a.out);
+      if (sums) sums[i] = a.accumulate_sums ? sums[i] + out.sum : out.sum;
+    }
+  }
+  tc_teardown(sh, !ok, phase);
+  if (Kind == kDrawSumHist && ok) {
+    __syncthreads();
+    for (int t = tid; t < 256; t += kTcRows) {
+      unsigned long long tot = 0;
+#pragma unroll
+      for (int w = 0; w < 4; ++w) tot += hist_s[w * 256 + t];
+      if (tot) atomicAdd(a.hist + t, tot);
+    }
+  }
+}
+
+// One tensor-path product per item: out = A x mod m (x < m), for testing.
+__global__ void __launch_bounds__(kTcRows, 4) k_tc_mulmod(const __half* __restrict__ bimg, const uint64_t* x,
+                                                          uint64_t* out, uint64_t n, int* status) {
+  extern __shared__ __align__(1024) unsigned char smem[];
+  __half* tile = reinterpret_cast<__half*>(smem);
+  __half* bmat = reinterpret_cast<__half*>(smem + kTileBytes);
+  TcShared* sh = reinterpret_cast<TcShared*>(smem + kTileBytes + kBBytes);
+  tc_setup(tile, bmat, bimg, sh);
+  const uint64_t i = (uint64_t)blockIdx.x * kTcRows + threadIdx.x;
+  uint32_t X[kLimbs];
+#pragma unroll
+  for (int k = 0; k < 9; ++k) {
+    const uint64_t v = i < n ? x[9 * i + k] : 0;
+    X[2 * k] = (uint32_t)v;
+    X[2 * k + 1] = (uint32_t)(v >> 32);
+  }
+  write_x_row(tile, threadIdx.x, X);
+  uint32_t col[72], phase = 0;
+  const bool ok = tc_refill(tile, bmat, sh, phase, col);
+  if (ok) {
+    columns_to_x(col, X);
+    if (i < n)
+#pragma unroll
+      for (int k = 0; k < 9; ++k) out[9 * i + k] = ((uint64_t)X[2 * k + 1] << 32) | X[2 * k];
+  } else if (threadIdx.x == 0) {
+    atomicCAS(status, 0, (int)RLXPP_ERR_TIMEOUT);
+  }
+  tc_teardown(sh, !ok, phase);
+}
+
+// The level's matrix in the shared-memory image layout: column j (K index) holds the
+// bytes of R_j = A 2^(8j) mod m for j < 72, the bias 4096 for j = 72, zeros after.
+__global__ void k_tc_matrix(const uint32_t* __restrict__ lux, __half* __restrict__ bimg) {
+  const int j = threadIdx.x;  // 0..79
+  if (j >= kTcK) return;
+  uint8_t bytes[kTcN];
+  if (j < 72) {
+    uint32_t P[2 * kLimbs];
+#pragma unroll 1
+    for (int q = 0; q < 2 * kLimbs; ++q) P[q] = 0;
+    const int sh_limb = (8 * j) >> 5, sh_bit = (8 * j) & 31;
+#pragma unroll 1
+    for (int q = 0; q < kLimbs; ++q) {
+      const uint32_t a = lux[q];
+      P[q + sh_limb] |= a << sh_bit;
+      if (sh_bit) P[q + sh_limb + 1] |= a >> (32 - sh_bit);
+    }
+    uint32_t R[kLimbs];
+    mod_m(P, R);
+#pragma unroll 1
+    for (int n = 0; n < kTcN; ++n) bytes[n] = n < 72 ? (uint8_t)(R[n >> 2] >> (8 * (n & 3))) : 0;
+  }
+#pragma unroll 1
+  for (int n = 0; n < kTcN; ++n) {
+    float v = j < 72 ? (float)bytes[n] : (j == 72 ? 4096.f : 0.f);
+    bimg[tc_off(n, j)] = __float2half(v);
+  }
+}
+
+// Dynamic shared memory per CTA: the two operand tiles and the barrier (33.3 KB) rounded
+// up so that at most 4 CTAs share an SM, whose 512 TMEM columns then always suffice.
+constexpr size_t kTcSmem = 48 * 1024;
+
+template <int Kind>
+cudaError_t launch_tc_kind(const DrawArgs& a, const __half* bimg, cudaStream_t st) {
+  cudaError_t e = cudaFuncSetAttribute(k_draw_tc<Kind>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTcSmem);
+  if (e != cudaSuccess) return e;
+  const unsigned grid = (unsigned)((a.s.n + kTcRows - 1) / kTcRows);
+  k_draw_tc<Kind><<<grid, kTcRows, kTcSmem, st>>>(a, bimg);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+size_t tc_matrix_bytes() { return kBBytes; }
+
+cudaError_t launch_tc_matrix(const uint32_t* lux18, void* bimg, cudaStream_t st) {
+  k_tc_matrix<<<1, kTcK, 0, st>>>(lux18, static_cast<__half*>(bimg));
+  return cudaGetLastError();
+}
+
+cudaError_t launch_draw_tc(int kind, const DrawArgs& a, const void* bimg, cudaStream_t st) {
+  if (a.s.n == 0) return cudaSuccess;
+  const __half* b = static_cast<const __half*>(bimg);
+  switch (kind) {
+    case kDrawU24: return launch_tc_kind<kDrawU24>(a, b, st);
+    case kDrawF64: return launch_tc_kind<kDrawF64>(a, b, st);
+    case kDrawSumHist: return launch_tc_kind<kDrawSumHist>(a, b, st);
+  }
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_tc_mulmod(const void* bimg, const uint64_t* x, uint64_t* out, uint64_t n, int* status,
+                             cudaStream_t st) {
+  if (n == 0) return cudaSuccess;
+  cudaError_t e = cudaFuncSetAttribute(k_tc_mulmod, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTcSmem);
+  if (e != cudaSuccess) return e;
+  k_tc_mulmod<<<(unsigned)((n + kTcRows - 1) / kTcRows), kTcRows, kTcSmem, st>>>(static_cast<const __half*>(bimg),
+                                                                                 x, out, n, status);
+  return cudaGetLastError();
+}
+
+}  // namespace rlxpp

@@ -1,0 +1,128 @@
+"""The tensor-core refill (RLXPP_PATH_TENSOR) against the oracle and against the
+integer-pipe path, bit-exact (GPU).  The exact-integer fp16 product is checked on
+crafted operands, including all-ones X (the largest column sums), at several luxury
+levels; the draw kernels on the tensor path must give the same values and states as
+the integer path for uniform and ragged counts, odd read positions and the fused
+consumer."""
+import random
+
+import numpy as np
+import pytest
+
+from oracle import ranluxpp as R
+from oracle import swb_lib as S
+from paper_2106_02504_gb300 import workloads as W
+from tests.oracle_side import StreamSet, from_limbs64, limbs64
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def native():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2106_02504_gb300 as P
+    return P.native
+
+
+def to_dev(rows):
+    return torch.from_numpy(np.array(rows, dtype=np.uint64).view(np.int64)).cuda()
+
+
+@pytest.mark.parametrize("p", [1, 24, 389, 2048])
+def test_tc_product(native, p):
+    rng = random.Random(300 + p)
+    M = R.M
+    xs = [0, 1, 2, M - 1, M - 2, 2 ** 576 - 1, 2 ** 575, 2 ** 240 - 1, (2 ** 576 - 1) // 255 * 254] + \
+        [rng.randrange(M) for _ in range(1000)]
+    n = len(xs)
+    out = torch.zeros((n, 9), dtype=torch.int64, device="cuda")
+    native.rlxpp_test_tc_mulmod(p, to_dev([limbs64(x, 9) for x in xs]), out, n)
+    got = out.cpu().numpy().view(np.uint64)
+    A = R.luxury_multiplier(p)
+    for k in range(n):
+        assert from_limbs64(got[k]) == A * xs[k] % M, (p, k)
+
+
+def pair(native, seeds, levels=(2048,)):
+    d = torch.from_numpy(np.asarray(seeds, np.uint64).view(np.int64)).cuda()
+    a = native.Generator(len(seeds), list(levels), d)
+    b = native.Generator(len(seeds), list(levels), d)
+    b.set_path(native.RLXPP_PATH_TENSOR)
+    return a, b
+
+
+def states(native, g, n):
+    buf = torch.zeros((n, 11), dtype=torch.int64, device="cuda")
+    g.get_state(buf)
+    return buf.cpu()
+
+
+def test_tc_draws_match_integer_path(native):
+    n = 300
+    seeds = W.random_seeds(n, 301)
+    a, b = pair(native, seeds)
+    ref = StreamSet.from_seeds(seeds, 2048)
+    for kind, count in [(S.KIND_F64, 1000), (S.KIND_U24, 37), (S.KIND_F64, 13), (S.KIND_U24, 24)]:
+        dt = torch.float64 if kind == S.KIND_F64 else torch.int32
+        oa = torch.zeros((n, count), dtype=dt, device="cuda")
+        ob = torch.zeros((n, count), dtype=dt, device="cuda")
+        (a.draw_f64 if kind == S.KIND_F64 else a.draw_u24)(oa, count)
+        (b.draw_f64 if kind == S.KIND_F64 else b.draw_u24)(ob, count)
+        assert torch.equal(oa, ob), (kind, count)
+        want = ref.draw(count, kind)
+        got = ob.cpu().numpy()
+        assert np.array_equal(got.view(np.uint64) if kind == S.KIND_F64 else got.view(np.uint32),
+                              want.view(np.uint64) if kind == S.KIND_F64 else want)
+    assert torch.equal(states(native, a, n), states(native, b, n))
+    # ragged counts and offsets
+    counts, offsets = W.ragged_counts(n, 100, seed=302)
+    oa = torch.zeros(int(counts.sum()) + 1, dtype=torch.float64, device="cuda")
+    ob = torch.zeros_like(oa)
+    c_d, o_d = torch.from_numpy(counts).cuda(), torch.from_numpy(offsets).cuda()
+    a.draw_f64(oa, 0, c_d, o_d)
+    b.draw_f64(ob, 0, c_d, o_d)
+    assert torch.equal(oa, ob)
+    # fused consumer
+    sa, sb = torch.zeros(n, dtype=torch.int64, device="cuda"), torch.zeros(n, dtype=torch.int64, device="cuda")
+    ha, hb = torch.zeros(256, dtype=torch.int64, device="cuda"), torch.zeros(256, dtype=torch.int64, device="cuda")
+    a.draw_f64_sum_hist(2000, sa, ha)
+    b.draw_f64_sum_hist(2000, sb, hb)
+    assert torch.equal(sa, sb) and torch.equal(ha, hb)
+    assert torch.equal(states(native, a, n), states(native, b, n))
+    b.sync()
+
+
+def test_tc_path_rules(native):
+    g = native.Generator(8, [24, 2048], torch.arange(1, 9, dtype=torch.int64, device="cuda"))
+    with pytest.raises(native.RlxppError) as e:
+        g.set_path(native.RLXPP_PATH_TENSOR)
+    assert e.value.status == native.RLXPP_ERR_UNSUPPORTED
+    with pytest.raises(native.RlxppError):
+        g.set_path(7)
+    assert native.rlxpp_get_path(g.handle) == native.RLXPP_PATH_IMAD
+
+
+def test_tc_full_size_workload(native):
+    """The 2^20-stream workload on the tensor path: sampled streams vs the oracle."""
+    n = 1 << 20
+    seeds = W.consecutive_seeds(n)
+    g = native.Generator(n, [2048], torch.from_numpy(seeds.view(np.int64)).cuda())
+    g.set_path(native.RLXPP_PATH_TENSOR)
+    out = torch.empty((n, 1024), dtype=torch.float64, device="cuda")
+    g.draw_f64(out, 1024)
+    sums = torch.zeros(n, dtype=torch.int64, device="cuda")
+    hist = torch.zeros(256, dtype=torch.int64, device="cuda")
+    g.draw_f64_sum_hist(4096, sums, hist)
+    g.sync()
+    rng = np.random.Generator(np.random.PCG64(303))
+    idx = np.unique(np.concatenate([rng.choice(n, 400, replace=False), [0, 127, 128, n - 1]]))
+    ref = StreamSet.from_seeds(seeds[idx], 2048)
+    want = ref.draw(1024, S.KIND_F64).view(np.uint64)
+    got = out.view(torch.int64)[torch.from_numpy(idx).cuda()].cpu().numpy().view(np.uint64)
+    assert np.array_equal(got, want)
+    wsums, _ = ref.sum_hist(4096)
+    assert np.array_equal(sums.cpu().numpy().view(np.uint64)[idx], wsums)
+    assert int(hist.sum()) == n * 4096
