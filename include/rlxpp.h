@@ -208,8 +208,10 @@ rlxpp_status rlxpp_set_state(rlxpp_gen* gen, const rlxpp_state* src, void* cuda_
 rlxpp_status rlxpp_sync(rlxpp_gen* gen, void* cuda_stream);
 
 /* ---- refill path -------------------------------------------------------------------
- * RLXPP_PATH_IMAD (default): the product on the integer pipe, one thread per stream.
- * RLXPP_PATH_TENSOR: the product A X mod m as an exact-integer fp16 matrix product on
+ * RLXPP_PATH_IMAD: the product on the integer pipe, one thread per stream (the default
+ * for handles with several luxury levels).
+ * RLXPP_PATH_TENSOR (the default for single-level handles): the product A X mod m as an
+ * exact-integer fp16 matrix product on
  * the tensor cores (tcgen05.mma, fp32 accumulation in tensor memory): with
  * R_j = A 2^(8j) mod m, A X = sum_j x_j R_j = sum_k S_k 2^(8k) (mod m) where x_j are
  * the 72 bytes of X and S_k = sum_j x_j byte_k(R_j) < 2^23, so a tile of 128 streams is

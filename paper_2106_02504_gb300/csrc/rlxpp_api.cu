@@ -275,6 +275,12 @@ rlxpp_status rlxpp_create(uint64_t n_streams, const uint32_t* levels, uint32_t n
   if (e == cudaSuccess) e = cudaMemsetAsync(g->meta, 0, sizeof(uint32_t) * nn, st);
   if (e != cudaSuccess) return bail(fail(RLXPP_ERR_CUDA, std::string("create: ") + cudaGetErrorString(e)));
   if (rlxpp_status s = setup_levels(g, st)) return bail(s);
+  if (n_levels == 1) {  // single-level handles refill on the tensor cores by default
+    e = cudaMalloc(&g->tc_matrix, tc_matrix_bytes());
+    if (e == cudaSuccess) e = launch_tc_matrix(g->lux, g->tc_matrix, st);
+    if (e != cudaSuccess) return bail(fail(RLXPP_ERR_CUDA, std::string("tensor setup: ") + cudaGetErrorString(e)));
+    g->path = RLXPP_PATH_TENSOR;
+  }
   if (n_streams > 0) {
     Staged ss, sl;
     if (rlxpp_status s = stage_in(seeds, sizeof(uint64_t) * n_streams, st, ss)) return bail(s);
@@ -410,11 +416,7 @@ rlxpp_status rlxpp_set_path(rlxpp_gen* g, uint32_t path) {
   if (path != RLXPP_PATH_IMAD && path != RLXPP_PATH_TENSOR) return fail(RLXPP_ERR_INVALID, "unknown path");
   if (path == RLXPP_PATH_TENSOR) {
     if (g->n_levels != 1) return fail(RLXPP_ERR_UNSUPPORTED, "the tensor path serves single-level handles");
-    if (!g->tc_matrix) {
-      RLX_CUDA(cudaMalloc(&g->tc_matrix, tc_matrix_bytes()));
-      RLX_CUDA(launch_tc_matrix(g->lux, g->tc_matrix, nullptr));
-      RLX_CUDA(cudaStreamSynchronize(nullptr));
-    }
+    if (!g->tc_matrix) return fail(RLXPP_ERR_CUDA, "tensor matrix missing");
   }
   RLX_CUDA(cudaDeviceSynchronize());  // no draw of the old path may still run
   g->path = path;

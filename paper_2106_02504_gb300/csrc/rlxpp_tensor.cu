@@ -156,10 +156,12 @@ __device__ __forceinline__ void columns_to_x(const uint32_t col[72], uint32_t X[
   for (int t = 0; t < kLimbs; ++t) {
     const uint32_t s0 = col[4 * t] & 0x7FFFFFu, s1 = col[4 * t + 1] & 0x7FFFFFu;
     const uint32_t s2 = col[4 * t + 2] & 0x7FFFFFu, s3 = col[4 * t + 3] & 0x7FFFFFu;
-    const uint32_t u = s0 + (s1 << 8);  // < 2^31
-    const uint32_t v = s2 + (s3 << 8);  // < 2^31
-    lo[t] = add_cc(u, v << 16);
-    hi[t] = addc(v >> 16, 0u);
+    uint32_t u, v;  // both below 2^31; the multiply-adds run on the FMA pipe
+    asm("mad.lo.u32 %0, %1, 256, %2;" : "=r"(u) : "r"(s1), "r"(s0));
+    asm("mad.lo.u32 %0, %1, 256, %2;" : "=r"(v) : "r"(s3), "r"(s2));
+    const uint64_t w = mad_wide(v, 65536u, (uint64_t)u);  // u + v 2^16 < 2^47
+    lo[t] = lo32(w);
+    hi[t] = hi32(w);
   }
   // value = sum_t lo_t 2^(32t) + hi_t 2^(32(t+1)): one carry chain, top limb T < 2^15
   X[0] = lo[0];
@@ -204,6 +206,38 @@ struct TcShared {
   uint32_t taddr;    // TMEM base
   int any;           // tile still refilling
 };
+constexpr int kSharedBytes = 64;               // TcShared, padded
+constexpr int kStageBytes = 96;                // one block of output per thread
+constexpr int kStageOffset = kTileBytes + kBBytes + kSharedBytes;
+
+// A full block of output (12 doubles or 24 numbers, 96 bytes) from this thread's
+// staging slot to global memory by one bulk copy (the TMA engine writes it), after the
+// slot's previous copy has been read out.  gdst must be 16-byte aligned.
+__device__ __forceinline__ void bulk_store96(void* gdst, uint4* slot, const uint4 v[6]) {
+  asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+#pragma unroll
+  for (int q = 0; q < 6; ++q) slot[q] = v[q];
+  fence_proxy_async_smem();
+  asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], 96;" ::"l"(gdst), "r"(smem_addr(slot))
+               : "memory");
+  asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+}
+__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+
+template <int Kind>
+__device__ __forceinline__ void block_values(const uint32_t D[kLimbs], uint4 v[6]) {
+  if constexpr (Kind == kDrawF64) {
+#pragma unroll
+    for (int q = 0; q < 6; ++q) {
+      const uint64_t a = f64_bits_from48(bits48(D, 2 * q)), b = f64_bits_from48(bits48(D, 2 * q + 1));
+      v[q] = make_uint4((uint32_t)a, (uint32_t)(a >> 32), (uint32_t)b, (uint32_t)(b >> 32));
+    }
+  } else {
+#pragma unroll
+    for (int q = 0; q < 6; ++q)
+      v[q] = make_uint4(word24(D, 4 * q), word24(D, 4 * q + 1), word24(D, 4 * q + 2), word24(D, 4 * q + 3));
+  }
+}
 
 // Setup per tile: the level's matrix into shared memory, the constant chunk 9 of every
 // row (bias 2048 at k = 72, zeros after it), the mbarrier and the TMEM columns.
@@ -274,6 +308,7 @@ __global__ void __launch_bounds__(kTcRows, 4) k_draw_tc(const DrawArgs a, const 
   __half* tile = reinterpret_cast<__half*>(smem);
   __half* bmat = reinterpret_cast<__half*>(smem + kTileBytes);
   TcShared* sh = reinterpret_cast<TcShared*>(smem + kTileBytes + kBBytes);
+  uint4* slot = reinterpret_cast<uint4*>(smem + kStageOffset + threadIdx.x * kStageBytes);
   __shared__ unsigned int hist_s[Kind == kDrawSumHist ? 4 * 256 : 1];
   const int tid = threadIdx.x;
   if (Kind == kDrawSumHist)
@@ -345,7 +380,18 @@ __global__ void __launch_bounds__(kTcRows, 4) k_draw_tc(const DrawArgs a, const 
       refilled = true;
       const int64_t rem = cnt - k;
       if (rem >= per_block) {
-        out.block(D, base + k);
+        if constexpr (Kind == kDrawSumHist) {
+          out.block(D, base + k);
+        } else {
+          void* dst = out.out + base + k;
+          if ((reinterpret_cast<uintptr_t>(dst) & 15) == 0) {
+            uint4 v[6];
+            block_values<Kind>(D, v);
+            bulk_store96(dst, slot, v);
+          } else {
+            out.block(D, base + k);
+          }
+        }
         k += per_block;
         pos = kWords;
       } else {
@@ -356,6 +402,7 @@ __global__ void __launch_bounds__(kTcRows, 4) k_draw_tc(const DrawArgs a, const 
       mine = k < cnt;
     }
   }
+  if (Kind != kDrawSumHist) bulk_wait_all();  // this thread's output copies are done
   if (!ok) {
     if (tid == 0) atomicCAS(s.status, 0, (int)RLXPP_ERR_TIMEOUT);
   } else if (live) {
@@ -440,9 +487,11 @@ __global__ void k_tc_matrix(const uint32_t* __restrict__ lux, __half* __restrict
   }
 }
 
-// Dynamic shared memory per CTA: the two operand tiles and the barrier (33.3 KB) rounded
-// up so that at most 4 CTAs share an SM, whose 512 TMEM columns then always suffice.
+// Dynamic shared memory per CTA: the two operand tiles, the barrier and the output
+// staging slots (45.6 KB) rounded up so that at most 4 CTAs share an SM, whose 512 TMEM
+// columns then always suffice.
 constexpr size_t kTcSmem = 48 * 1024;
+static_assert(kStageOffset + kTcRows * kStageBytes <= (int)kTcSmem, "shared memory layout");
 
 template <int Kind>
 cudaError_t launch_tc_kind(const DrawArgs& a, const __half* bimg, cudaStream_t st) {

@@ -50,9 +50,17 @@ def f64_bits(t):
 N = 300  # three blocks of 128 threads and a ragged tail
 
 
-def make(native, seeds, levels=(2048,), level_of=None):
+@pytest.fixture(params=["tensor", "imad"])
+def path(request):
+    return request.param
+
+
+def make(native, seeds, levels=(2048,), level_of=None, path=None):
     lo = None if level_of is None else torch.from_numpy(np.asarray(level_of, dtype=np.uint8)).cuda()
-    return native.Generator(len(seeds), list(levels), dev_u64(seeds), lo)
+    g = native.Generator(len(seeds), list(levels), dev_u64(seeds), lo)
+    if path is not None and len(levels) == 1:
+        g.set_path(native.RLXPP_PATH_IMAD if path == "imad" else native.RLXPP_PATH_TENSOR)
+    return g
 
 
 def test_seed_states(native):
@@ -68,9 +76,9 @@ def test_seed_states(native):
 
 
 @pytest.mark.parametrize("p,count", [(2048, 1000), (24, 1001), (223, 12), (389, 1)])
-def test_draw_f64_uniform(native, p, count):
+def test_draw_f64_uniform(native, p, count, path):
     seeds = W.random_seeds(N, 31 + p)
-    g = make(native, seeds, levels=(p,))
+    g = make(native, seeds, levels=(p,), path=path)
     out = torch.zeros((N, count), dtype=torch.float64, device="cuda")
     g.draw_f64(out, count)
     ref = StreamSet.from_seeds(seeds, p)
@@ -80,9 +88,9 @@ def test_draw_f64_uniform(native, p, count):
 
 
 @pytest.mark.parametrize("p,count", [(2048, 1000), (24, 24), (389, 23)])
-def test_draw_u24_uniform(native, p, count):
+def test_draw_u24_uniform(native, p, count, path):
     seeds = W.random_seeds(N, 41 + p)
-    g = make(native, seeds, levels=(p,))
+    g = make(native, seeds, levels=(p,), path=path)
     out = torch.zeros((N, count), dtype=torch.int32, device="cuda")
     g.draw_u24(out, count)
     ref = StreamSet.from_seeds(seeds, p)
@@ -90,10 +98,10 @@ def test_draw_u24_uniform(native, p, count):
     assert_states(native, g, ref)
 
 
-def test_mixed_types_odd_positions(native):
+def test_mixed_types_odd_positions(native, path):
     """u24 draws leave odd read positions; doubles then skip a lone leftover word."""
     seeds = W.consecutive_seeds(N, first=77)
-    g = make(native, seeds, levels=(223,))
+    g = make(native, seeds, levels=(223,), path=path)
     ref = StreamSet.from_seeds(seeds, 223)
     for kind, count in [(S.KIND_U24, 5), (S.KIND_F64, 7), (S.KIND_U24, 23), (S.KIND_F64, 30),
                         (S.KIND_U24, 1), (S.KIND_F64, 11), (S.KIND_F64, 0), (S.KIND_U24, 48)]:
@@ -113,11 +121,11 @@ def test_mixed_types_odd_positions(native):
 
 
 @pytest.mark.parametrize("kind", [S.KIND_U24, S.KIND_F64])
-def test_ragged_counts_offsets(native, kind):
+def test_ragged_counts_offsets(native, kind, path):
     seeds = W.random_seeds(N, 51)
     counts, offsets = W.ragged_counts(N, 200, seed=52)
     total = int(counts.sum())
-    g = make(native, seeds, levels=(2048,))
+    g = make(native, seeds, levels=(2048,), path=path)
     dt = torch.int32 if kind == S.KIND_U24 else torch.float64
     out = torch.full((total + 1,), -1, dtype=dt, device="cuda")
     c_d = torch.from_numpy(counts).cuda()
@@ -138,9 +146,9 @@ def test_ragged_counts_offsets(native, kind):
     assert_states(native, g, ref)
 
 
-def test_sum_hist(native):
+def test_sum_hist(native, path):
     seeds = W.consecutive_seeds(N, first=1000)
-    g = make(native, seeds, levels=(2048,))
+    g = make(native, seeds, levels=(2048,), path=path)
     sums = torch.zeros(N, dtype=torch.int64, device="cuda")
     hist = torch.zeros(256, dtype=torch.int64, device="cuda")
     g.draw_f64_sum_hist(4096, sums, hist)
@@ -312,11 +320,11 @@ def test_empty_and_zero(native):
         native.rlxpp_create(1, [0], np.array([1], dtype=np.uint64))
 
 
-def test_single_stream_workload(native):
+def test_single_stream_workload(native, path):
     """Seed 1, p = 2048: 2^20 doubles, and 2^20 integers from a fresh seed-1 state."""
     n = 1 << 20
     for kind in (S.KIND_F64, S.KIND_U24):
-        g = make(native, np.array([1], dtype=np.uint64))
+        g = make(native, np.array([1], dtype=np.uint64), path=path)
         dt = torch.float64 if kind == S.KIND_F64 else torch.int32
         out = torch.zeros((1, n), dtype=dt, device="cuda")
         (g.draw_f64 if kind == S.KIND_F64 else g.draw_u24)(out, n)
@@ -330,9 +338,9 @@ def test_single_stream_workload(native):
         assert_states(native, g, ref)
 
 
-def test_p24_ten_thousand_advances(native):
+def test_p24_ten_thousand_advances(native, path):
     """10,000 refills at p = 24 on one stream, each block equal to 24 recurrence steps."""
-    g = make(native, np.array([1], dtype=np.uint64), levels=(24,))
+    g = make(native, np.array([1], dtype=np.uint64), levels=(24,), path=path)
     n = 24 * 10_001
     out = torch.zeros((1, n), dtype=torch.int32, device="cuda")
     g.draw_u24(out, n)

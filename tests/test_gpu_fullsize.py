@@ -1,4 +1,5 @@
-"""The 2^20-stream workload at full size, in the launch configuration bench.py times
+"""The 2^20-stream workload at full size on the integer-pipe path (the tensor path has its
+own full-size test), in the launch configuration bench.py times
 (rlxpp_seed, rlxpp_draw_f64 of 1024 doubles per stream into an 8 GiB device buffer,
 rlxpp_draw_f64_sum_hist of 4096 doubles per stream), checked bit-exactly against the
 oracle on sampled streams (every output of each sampled stream, and its final state)
@@ -37,6 +38,7 @@ def sample_idx(seed, k=1500):
 def test_hbm_workload_full_size(native):
     seeds = W.consecutive_seeds(N)
     g = native.Generator(N, [P], torch.from_numpy(seeds.view(np.int64)).cuda())
+    g.set_path(native.RLXPP_PATH_IMAD)
     g.seed(torch.from_numpy(seeds.view(np.int64)).cuda())
     out = torch.empty((N, 1024), dtype=torch.float64, device="cuda")
     g.draw_f64(out, 1024)
@@ -65,6 +67,7 @@ def test_hbm_workload_full_size(native):
 def test_fused_workload_full_size(native):
     seeds = W.consecutive_seeds(N)
     g = native.Generator(N, [P], torch.from_numpy(seeds.view(np.int64)).cuda())
+    g.set_path(native.RLXPP_PATH_IMAD)
     sums = torch.zeros(N, dtype=torch.int64, device="cuda")
     hist = torch.zeros(256, dtype=torch.int64, device="cuda")
     g.draw_f64_sum_hist(4096, sums, hist)

@@ -49,8 +49,11 @@ def test_tc_product(native, p):
 def pair(native, seeds, levels=(2048,)):
     d = torch.from_numpy(np.asarray(seeds, np.uint64).view(np.int64)).cuda()
     a = native.Generator(len(seeds), list(levels), d)
+    a.set_path(native.RLXPP_PATH_IMAD)
     b = native.Generator(len(seeds), list(levels), d)
     b.set_path(native.RLXPP_PATH_TENSOR)
+    assert native.rlxpp_get_path(a.handle) == native.RLXPP_PATH_IMAD
+    assert native.rlxpp_get_path(b.handle) == native.RLXPP_PATH_TENSOR
     return a, b
 
 
@@ -96,6 +99,8 @@ def test_tc_draws_match_integer_path(native):
 
 
 def test_tc_path_rules(native):
+    one = native.Generator(8, [2048], torch.arange(1, 9, dtype=torch.int64, device="cuda"))
+    assert native.rlxpp_get_path(one.handle) == native.RLXPP_PATH_TENSOR   # single level: tensor default
     g = native.Generator(8, [24, 2048], torch.arange(1, 9, dtype=torch.int64, device="cuda"))
     with pytest.raises(native.RlxppError) as e:
         g.set_path(native.RLXPP_PATH_TENSOR)
