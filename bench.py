@@ -45,7 +45,8 @@ IMAD_PER_SM_CLK = 64
 SM_MAX_MHZ = 2070.0
 ALU_PER_SM_CLK = 64
 TC_FLOP_PER_ADVANCE = 2 * 80 * 80      # padded 128 x 80 x 80 fp16 product per 128 streams
-ALU_INSTR_PER_ADVANCE_TC = 299         # integer-pipe instructions per refill of k_draw_tc (ncu, fused kernel)
+ALU_INSTR_PER_ADVANCE_TC = 333         # integer-pipe instructions per refill of k_draw_tc<sum/hist> (ncu)
+TC_FUSED_DRAM_BYTES_PER_STREAM = 76.2  # its DRAM traffic per stream and launch (ncu, 2^18 streams)
 CPU_SAMPLE_STREAMS = 16384
 
 
@@ -290,7 +291,10 @@ def run_native(args, rank, world, local_rank):
                     "peak": SMS * ALU_PER_SM_CLK * SM_MAX_MHZ * 1e6 / 1e12,
                     "unit": f"Top/s (integer-pipe instructions of the epilogue, {ALU_INSTR_PER_ADVANCE_TC} per advance)",
                     "frac": achieved / (SMS * ALU_PER_SM_CLK * SM_MAX_MHZ * 1e6 / 1e12),
-                    "peak_source": "derived: 152 SMs x 64 ALU lanes/clk x 2070 MHz", "traffic": None,
+                    "peak_source": "derived: 152 SMs x 64 ALU lanes/clk x 2070 MHz",
+                    "traffic": TC_FUSED_DRAM_BYTES_PER_STREAM * n if dom == "draw_f64_sum_hist" else None,
+                    "traffic_source": "ncu dram__bytes_read+write of k_draw_tc<sum/hist> on 2^18 streams, "
+                                      "scaled by streams (profiles/k_draw_tc_262144_streams_full.md)",
                     "tensor_pipe": {"achieved_tflops": adv * TC_FLOP_PER_ADVANCE / (per_kernel[dom] * 1e-3) / 1e12,
                                     "peak_tflops": f16_peak, "peak_source": "MEASURED_PEAKS bf16_tflops (burst)"}}
     for name in paths:
