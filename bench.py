@@ -188,9 +188,9 @@ def run_native(args, rank, world, local_rank):
     dist = None
     if world > 1:
         import torch.distributed as dist
+    from paper_2106_02504_gb300 import workloads as W
     n = args.streams
-    first_seed = 1 + rank * n
-    seeds_h = np.arange(first_seed, first_seed + n, dtype=np.uint64)
+    seeds_h = W.rank_seeds(rank, world, n)
     seeds = torch.from_numpy(seeds_h.view(np.int64)).to(dev)
     g = nat.Generator(n, [LUXURY], seeds)
     out = torch.empty((n, HBM_COUNT), dtype=torch.float64, device=dev)

@@ -76,3 +76,12 @@ def serving_trace(n_requests, rate_hz, n_resident, lo=10**2, hi=10**7, seed=5):
     counts = log_uniform_counts(n_requests, lo, hi, seed + 1000)
     is_f64 = rng.integers(0, 2, size=n_requests).astype(bool)
     return arrival, stream, counts, is_f64
+
+
+def rank_seeds(rank, world, n_per_rank):
+    """Seeds of one rank when the stream workload is sharded over `world` GPUs (weak
+    scaling): rank r owns seeds 1 + r n .. (r + 1) n, so the ranks together run the
+    single-GPU workload's streams for world x n streams, without overlap."""
+    if not 0 <= rank < world:
+        raise ValueError("rank out of range")
+    return consecutive_seeds(n_per_rank, first=1 + rank * n_per_rank)
