@@ -18,7 +18,8 @@ Everything here is the plain definition, written with Python integers:
 * the conversion from the LCG state back to 24 RANLUX numbers and the carry (Sec. 2.3):
   the digits of X/m in base 2^24, i.e. D = floor(2^576 X / m), with the carry fixed by
   the inverse map X = D - floor(D / 2^336) + c;
-* 48-bit doubles in [0, 1) (Sec. 2.3) and 24-bit integers (Sec. 2.4, ``IntRndm``);
+* 48-bit doubles in [0, 1) (Sec. 2.3), 24-bit integers (Sec. 2.4, ``IntRndm``) and
+  24-bit single-precision floats w 2^-24 (RANLUX's own output format);
 * seeding and skipping by exponentiation (Sec. 2.4) as Python ``pow``.
 
 Readings where the paper is silent (each also listed in the design doc):
@@ -130,6 +131,12 @@ def f64_bits(x):
     return struct.unpack("<Q", struct.pack("<d", x))[0]
 
 
+def f32_bits_from24(w):
+    """One 24-bit number -> the binary32 bit pattern of w 2^-24 in [0, 1) (exact: w has
+    at most 24 significant bits)."""
+    return struct.unpack("<I", struct.pack("<f", float(w) * 2.0 ** -24))[0]
+
+
 # --- Sec. 2.4: seeding and skipping -------------------------------------------------
 def seed_lcg(seed, p):
     """LCG state of seed s: the state 1 skipped by 2^96 s luxury advances."""
@@ -181,6 +188,24 @@ class Stream:
 
     def draw_f64(self, n):
         return [f64_from_bits48(v) for v in self.draw_bits48(n)]
+
+    def draw_f32_bits(self, n):
+        """Single-precision draws: one number each, w 2^-24 (the 24-bit RANLUX output)."""
+        return [f32_bits_from24(w) for w in self.draw_u24(n)]
+
+    def skip_values(self, n, per_value_words):
+        """Move as if n values taking per_value_words numbers each had been drawn."""
+        pos, need = self.pos, per_value_words
+        room = (WORDS - pos) // need if pos + need <= WORDS else 0
+        if n <= room:
+            self.pos = pos + n * need
+            return
+        rest = n - room
+        per = WORDS // need
+        blocks = -(-rest // per)
+        X = pow(self.A, blocks, M) * self.X % M
+        self.D, self.c = to_ranlux(X)
+        self.pos = (rest - (blocks - 1) * per) * need
 
     def skip(self, n):
         """Apply n luxury advances without producing output; the position is kept."""

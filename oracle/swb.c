@@ -110,6 +110,24 @@ int64_t swb_draw_f64(uint32_t w[SWB_R], uint32_t *carry, int32_t *pos, int32_t p
     return blocks;
 }
 
+/* n single-precision floats w 2^-24 in [0, 1), one number each (exact). */
+int64_t swb_draw_f32(uint32_t w[SWB_R], uint32_t *carry, int32_t *pos, int32_t p,
+                     int64_t n, float *out)
+{
+    int64_t blocks = 0;
+    const float scale = 1.0f / 16777216.0f; /* 2^-24 */
+    for (int64_t k = 0; k < n; ++k) {
+        if (*pos + 1 > SWB_R) {
+            swb_block(w, carry, p);
+            *pos = 0;
+            ++blocks;
+        }
+        out[k] = (float)w[*pos] * scale;
+        *pos += 1;
+    }
+    return blocks;
+}
+
 /* Fused consumer: exact sum of n 48-bit integers and a 256-bin histogram of their top
  * 8 bits (hist is accumulated, not cleared). */
 int64_t swb_sum_hist48(uint32_t w[SWB_R], uint32_t *carry, int32_t *pos, int32_t p,
@@ -135,7 +153,7 @@ int64_t swb_sum_hist48(uint32_t w[SWB_R], uint32_t *carry, int32_t *pos, int32_t
 /* Many streams, each described by its own window/borrow/position, one after another.
  * w: n_streams x 24 words, carry/pos: n_streams each; draws `count` values per stream;
  * out: n_streams x count values, stream-major.  kind: 0 = u24 (uint32 out),
- * 1 = f64 (double out), 2 = bits48 (uint64 out). */
+ * 1 = f64 (double out), 2 = bits48 (uint64 out), 3 = f32 (float out). */
 void swb_draw_many(int64_t n_streams, uint32_t *w, uint32_t *carry, int32_t *pos,
                    int32_t p, int64_t count, int32_t kind, void *out)
 {
@@ -145,6 +163,8 @@ void swb_draw_many(int64_t n_streams, uint32_t *w, uint32_t *carry, int32_t *pos
             swb_draw_u24(wi, carry + i, pos + i, p, count, (uint32_t *)out + i * count);
         else if (kind == 1)
             swb_draw_f64(wi, carry + i, pos + i, p, count, (double *)out + i * count);
+        else if (kind == 3)
+            swb_draw_f32(wi, carry + i, pos + i, p, count, (float *)out + i * count);
         else
             swb_draw_bits48(wi, carry + i, pos + i, p, count, (uint64_t *)out + i * count);
     }

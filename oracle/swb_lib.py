@@ -22,7 +22,7 @@ _OUT_DIR = os.path.join(_HERE, "_build")
 _LIB_PATH = os.path.join(_OUT_DIR, "libswb_oracle.so")
 _lib = None
 
-KIND_U24, KIND_F64, KIND_BITS48 = 0, 1, 2
+KIND_U24, KIND_F64, KIND_BITS48, KIND_F32 = 0, 1, 2, 3
 
 
 def build(force=False):
@@ -75,12 +75,13 @@ def _ranges(n, parts):
 def draw_many(words, carry, pos, p, count, kind, threads=None):
     """Draw ``count`` values from each stream.  ``words``: (n, 24) uint32 windows,
     ``carry``: (n,) uint32, ``pos``: (n,) int32 — all updated in place.  Returns an
-    (n, count) array of uint32 (u24), float64 (f64) or uint64 (48-bit integers)."""
+    (n, count) array of uint32 (u24), float64 (f64), uint64 (48-bit integers) or
+    float32 (f32)."""
     L = lib()
     n = words.shape[0]
     assert words.dtype == np.uint32 and words.shape == (n, 24) and words.flags.c_contiguous
     assert carry.dtype == np.uint32 and pos.dtype == np.int32
-    dtype = {KIND_U24: np.uint32, KIND_F64: np.float64, KIND_BITS48: np.uint64}[kind]
+    dtype = {KIND_U24: np.uint32, KIND_F64: np.float64, KIND_BITS48: np.uint64, KIND_F32: np.float32}[kind]
     out = np.zeros((n, count), dtype=dtype)
     if n == 0:
         return out

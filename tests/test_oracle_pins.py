@@ -336,3 +336,44 @@ def test_golden_seed_vectors():
             st = R.Stream(p, seed=s)
             cache[key] = st.draw_u24(30) if kind == "u24" else [R.f64_bits(x) for x in st.draw_f64(15)]
         assert cache[key][k] == v, (p, s, kind, k)
+
+
+# --- single-precision draws and skipping by values -------------------------------------
+def test_f32_draws_are_the_u24_words_scaled():
+    s = R.Stream(389, seed=12)
+    t = R.Stream(389, seed=12)
+    f = s.draw_f32_bits(100)
+    u = t.draw_u24(100)
+    import struct
+    for fb, w in zip(f, u):
+        x = struct.unpack("<f", struct.pack("<I", fb))[0]
+        assert x * 2 ** 24 == w and 0.0 <= x < 1.0
+    assert R.f32_bits_from24(0) == 0
+    assert R.f32_bits_from24(1) == 0x33800000            # 2^-24
+    assert R.f32_bits_from24(2 ** 23) == 0x3F000000      # 0.5
+    assert R.f32_bits_from24(2 ** 24 - 1) == 0x3F7FFFFF  # 1 - 2^-24
+
+
+def test_c_f32_draws_match_python():
+    streams = [R.Stream(24, seed=s) for s in range(1, 5)]
+    words = np.array([st.words() for st in streams], dtype=np.uint32)
+    carry = np.array([st.c for st in streams], dtype=np.uint32)
+    pos = np.zeros(4, dtype=np.int32)
+    got = S.draw_many(words, carry, pos, 24, 50, S.KIND_F32, threads=2)
+    for k, st in enumerate(streams):
+        assert list(got[k].view(np.uint32)) == st.draw_f32_bits(50)
+
+
+@pytest.mark.parametrize("need", [1, 2])
+def test_skip_values_equals_drawing(need):
+    rng = random.Random(31 + need)
+    for _ in range(40):
+        s = R.Stream(223, seed=rng.randrange(1, 100))
+        t = R.Stream(223, X=s.X)
+        s.draw_u24(rng.randrange(0, 30))
+        t.pos = s.pos
+        t.D, t.c = s.D, s.c
+        n = rng.randrange(0, 200)
+        (s.draw_bits48 if need == 2 else s.draw_u24)(n)
+        t.skip_values(n, need)
+        assert (t.D, t.c, t.pos) == (s.D, s.c, s.pos)
