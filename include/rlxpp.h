@@ -111,6 +111,20 @@ rlxpp_status rlxpp_draw_u24(rlxpp_gen* gen, const int64_t* counts, const int64_t
 rlxpp_status rlxpp_draw_f64(rlxpp_gen* gen, const int64_t* counts, const int64_t* offsets,
                             int64_t count_each, double* out, void* cuda_stream);
 
+/* Draw single-precision floats in [0, 1): one RANLUX number w each, w 2^-24 (exact in
+ * binary32; the 24-bit output RANLUX itself delivers, Sec. 1); float out, same layout
+ * rules as rlxpp_draw_u24. */
+rlxpp_status rlxpp_draw_f32(rlxpp_gen* gen, const int64_t* counts, const int64_t* offsets,
+                            int64_t count_each, float* out, void* cuda_stream);
+
+/* Skip random numbers without generating them (Sec. 2.4), counted in values of one
+ * kind: stream i moves exactly as if it had drawn n_values[i] values of `kind`
+ * (RLXPP_KIND_U24, RLXPP_KIND_F64 or RLXPP_KIND_F32) and discarded them: the rest of
+ * its current block, then whole blocks by X <- A^blocks X over the power table.
+ * n_values: n_streams uint64, host or device. */
+rlxpp_status rlxpp_skip_values(rlxpp_gen* gen, const uint64_t* n_values, uint32_t kind,
+                               void* cuda_stream);
+
 /* Fused consumer (the GPU benchmark of Sec. 4.2 sums every number a thread draws):
  * every stream draws count_each doubles without storing them.  sums (NULL or
  * n_streams uint64, device) receives, per stream, the exact sum of the 48-bit
@@ -133,6 +147,7 @@ rlxpp_status rlxpp_draw_f64_sum_hist(rlxpp_gen* gen, int64_t count_each, uint64_
  * handle's tuner (rlxpp_autotune_requests) or by defaults. */
 #define RLXPP_KIND_U24 0u
 #define RLXPP_KIND_F64 1u
+#define RLXPP_KIND_F32 2u /* rlxpp_skip_values only; requests take u24 and f64 */
 #define RLXPP_REQ_ADVANCE 1u /* flag: move each stream to the end of its request (at most
                                 one request per stream); otherwise states are unchanged */
 
@@ -294,6 +309,12 @@ rlxpp_status rlxpp_test_f64_from48(const uint64_t* v, uint64_t* out, uint64_t n,
  * arrays of 9 uint64 limbs per item); synchronous. */
 rlxpp_status rlxpp_test_tc_mulmod(uint32_t p, const uint64_t* x, uint64_t* out, uint64_t n,
                                   void* cuda_stream);
+
+/* Failure-path test: runs one tensor-path tile whose MMA is never issued, so its
+ * bounded mbarrier wait (about 2^22 polls) must give up; returns RLXPP_ERR_TIMEOUT
+ * when the kernel reported the timeout and left the context usable.  scratch: 9
+ * uint64 of device memory (not written). */
+rlxpp_status rlxpp_test_tc_timeout(uint64_t* scratch, void* cuda_stream);
 
 /* Luxury multiplier A = a^p mod m as 9 uint64 limbs written to host memory out9,
  * computed on the device (Sec. 1: RANLUX as an LCG with a large multiplier). */

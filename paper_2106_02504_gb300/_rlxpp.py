@@ -33,7 +33,7 @@ class RlxppTuning(ctypes.Structure):
     _fields_ = [("chunk_blocks", ctypes.c_uint32), ("blocks_per_sm", ctypes.c_uint32)]
 
 
-RLXPP_KIND_U24, RLXPP_KIND_F64 = 0, 1
+RLXPP_KIND_U24, RLXPP_KIND_F64, RLXPP_KIND_F32 = 0, 1, 2
 RLXPP_PATH_IMAD, RLXPP_PATH_TENSOR = 0, 1
 RLXPP_REQ_ADVANCE = 1
 
@@ -68,6 +68,8 @@ def _load():
         "rlxpp_skip": [_vp, _vp, _vp],
         "rlxpp_draw_u24": [_vp, _vp, _vp, _i64, _vp, _vp],
         "rlxpp_draw_f64": [_vp, _vp, _vp, _i64, _vp, _vp],
+        "rlxpp_draw_f32": [_vp, _vp, _vp, _i64, _vp, _vp],
+        "rlxpp_skip_values": [_vp, _vp, _u32, _vp],
         "rlxpp_draw_f64_sum_hist": [_vp, _i64, _vp, _vp, _vp],
         "rlxpp_get_state": [_vp, _vp, _vp],
         "rlxpp_set_state": [_vp, _vp, _vp],
@@ -86,6 +88,7 @@ def _load():
         "rlxpp_autotune_requests": [_vp, _vp, _u64, _vp, _vp, _vp, _vp],
         "rlxpp_set_path": [_vp, _u32],
         "rlxpp_test_tc_mulmod": [_u32, _vp, _vp, _u64, _vp],
+        "rlxpp_test_tc_timeout": [_vp, _vp],
     }
     for name, args in sigs.items():
         fn = getattr(L, name)
@@ -170,6 +173,14 @@ def rlxpp_draw_u24(gen, out, count_each=0, counts=None, offsets=None, stream=Non
 
 def rlxpp_draw_f64(gen, out, count_each=0, counts=None, offsets=None, stream=None):
     _check(_lib.rlxpp_draw_f64(gen, _ptr(counts), _ptr(offsets), count_each, _ptr(out), _stream(stream)))
+
+
+def rlxpp_draw_f32(gen, out, count_each=0, counts=None, offsets=None, stream=None):
+    _check(_lib.rlxpp_draw_f32(gen, _ptr(counts), _ptr(offsets), count_each, _ptr(out), _stream(stream)))
+
+
+def rlxpp_skip_values(gen, n_values, kind, stream=None):
+    _check(_lib.rlxpp_skip_values(gen, _ptr(n_values), kind, _stream(stream)))
 
 
 def rlxpp_draw_f64_sum_hist(gen, count_each, sums, hist, stream=None):
@@ -301,6 +312,10 @@ def rlxpp_test_tc_mulmod(p, x, out, n, stream=None):
     _check(_lib.rlxpp_test_tc_mulmod(p, _ptr(x), _ptr(out), n, _stream(stream)))
 
 
+def rlxpp_test_tc_timeout(scratch, stream=None):
+    _check(_lib.rlxpp_test_tc_timeout(_ptr(scratch), _stream(stream)))
+
+
 def rlxpp_luxury_multiplier(p):
     """A = a^p mod m as a Python int (computed on the device)."""
     out = (ctypes.c_uint64 * 9)()
@@ -333,6 +348,12 @@ class Generator:
 
     def draw_requests(self, reqs, out_u24=None, out_f64=None, flags=0, stream=None):
         rlxpp_draw_requests(self.handle, reqs, out_u24, out_f64, flags, stream)
+
+    def draw_f32(self, out, count_each=0, counts=None, offsets=None, stream=None):
+        rlxpp_draw_f32(self.handle, out, count_each, counts, offsets, stream)
+
+    def skip_values(self, n_values, kind, stream=None):
+        rlxpp_skip_values(self.handle, n_values, kind, stream)
 
     def draw_f64_sum_hist(self, count_each, sums, hist, stream=None):
         rlxpp_draw_f64_sum_hist(self.handle, count_each, sums, hist, stream)

@@ -338,6 +338,26 @@ rlxpp_status rlxpp_draw_f64(rlxpp_gen* g, const int64_t* counts, const int64_t* 
                      as_stream(cuda_stream));
 }
 
+rlxpp_status rlxpp_draw_f32(rlxpp_gen* g, const int64_t* counts, const int64_t* offsets,
+                            int64_t count_each, float* out, void* cuda_stream) {
+  return draw_common(g, kDrawF32, counts, offsets, count_each, out, sizeof(float), as_stream(cuda_stream));
+}
+
+rlxpp_status rlxpp_skip_values(rlxpp_gen* g, const uint64_t* n_values, uint32_t kind, void* cuda_stream) {
+  if (rlxpp_status s = check_gen(g)) return s;
+  if (kind != RLXPP_KIND_U24 && kind != RLXPP_KIND_F64 && kind != RLXPP_KIND_F32)
+    return fail(RLXPP_ERR_INVALID, "unknown value kind");
+  if (g->n == 0) return RLXPP_OK;
+  if (!n_values) return fail(RLXPP_ERR_INVALID, "null counts");
+  cudaStream_t st = as_stream(cuda_stream);
+  Staged sn;
+  if (rlxpp_status s = stage_in(n_values, sizeof(uint64_t) * g->n, st, sn)) return s;
+  cudaError_t e = launch_skip_values(g->view(), static_cast<const uint64_t*>(sn.dev),
+                                     kind == RLXPP_KIND_F64 ? 2u : 1u, st);
+  if (e != cudaSuccess) return fail(RLXPP_ERR_CUDA, std::string("skip values: ") + cudaGetErrorString(e));
+  return RLXPP_OK;
+}
+
 rlxpp_status rlxpp_draw_f64_sum_hist(rlxpp_gen* g, int64_t count_each, uint64_t* sums,
                                      uint64_t* hist, void* cuda_stream) {
   if (rlxpp_status s = check_gen(g)) return s;
@@ -470,7 +490,20 @@ rlxpp_status rlxpp_test_f64_from48(const uint64_t* v, uint64_t* out, uint64_t n,
   return run_test(kTestF64, v, nullptr, out, nullptr, n, cuda_stream);
 }
 
+static rlxpp_status tc_test(uint32_t p, const uint64_t* x, uint64_t* out, uint64_t n, void* cuda_stream,
+                            bool issue);
+
 rlxpp_status rlxpp_test_tc_mulmod(uint32_t p, const uint64_t* x, uint64_t* out, uint64_t n, void* cuda_stream) {
+  return tc_test(p, x, out, n, cuda_stream, true);
+}
+
+rlxpp_status rlxpp_test_tc_timeout(uint64_t* scratch, void* cuda_stream) {
+  if (!scratch) return fail(RLXPP_ERR_INVALID, "null scratch");
+  return tc_test(1, scratch, scratch, 1, cuda_stream, false);
+}
+
+static rlxpp_status tc_test(uint32_t p, const uint64_t* x, uint64_t* out, uint64_t n, void* cuda_stream,
+                            bool issue) {
   if (p == 0) return fail(RLXPP_ERR_INVALID, "need p >= 1");
   if (n == 0) return RLXPP_OK;
   if (!x || !out) return fail(RLXPP_ERR_INVALID, "null test buffer");
@@ -485,7 +518,7 @@ rlxpp_status rlxpp_test_tc_mulmod(uint32_t p, const uint64_t* x, uint64_t* out, 
   if (e == cudaSuccess) e = cudaMemsetAsync(status, 0, sizeof(int), st);
   if (e == cudaSuccess) e = launch_level_setup(p, lux, table, st);
   if (e == cudaSuccess) e = launch_tc_matrix(lux, mat, st);
-  if (e == cudaSuccess) e = launch_tc_mulmod(mat, x, out, n, status, st);
+  if (e == cudaSuccess) e = launch_tc_mulmod(mat, x, out, n, status, st, issue);
   int h = 0;
   if (e == cudaSuccess) e = cudaMemcpyAsync(&h, status, sizeof(int), cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
@@ -494,7 +527,7 @@ rlxpp_status rlxpp_test_tc_mulmod(uint32_t p, const uint64_t* x, uint64_t* out, 
   cudaFree(mat);
   cudaFree(status);
   if (e != cudaSuccess) return fail(RLXPP_ERR_CUDA, std::string("tensor test: ") + cudaGetErrorString(e));
-  if (h) return fail((rlxpp_status)h, "tensor test: a bounded wait gave up");
+  if (h) return fail((rlxpp_status)h, "tensor test: a bounded device wait gave up");
   return RLXPP_OK;
 }
 

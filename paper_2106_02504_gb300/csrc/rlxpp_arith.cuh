@@ -385,4 +385,12 @@ __device__ __forceinline__ uint64_t f64_bits_from48(uint64_t v) {
   return v ? bits : 0ull;
 }
 
+// 24-bit number w -> the binary32 w 2^-24 in [0, 1) (exact), by integer operations:
+// the leading one goes to bit 23 and the exponent field makes the value read w 2^-24.
+__device__ __forceinline__ uint32_t f32_bits_from24(uint32_t w) {
+  const uint32_t lz = __clz(w);  // 8..32
+  const uint32_t bits = (w << ((lz - 8u) & 31u)) + ((133u - lz) << 23);
+  return w ? bits : 0u;
+}
+
 }  // namespace rlxpp

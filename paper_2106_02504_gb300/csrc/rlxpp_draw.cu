@@ -74,6 +74,7 @@ __global__ void __launch_bounds__(kDrawBlock, Uniform ? RLXPP_DRAW_MIN_BLOCKS : 
     Consumer<Kind> out;
     if constexpr (Kind == kDrawU24) out.out = static_cast<uint32_t*>(a.out);
     if constexpr (Kind == kDrawF64) out.out = static_cast<uint64_t*>(a.out);
+    if constexpr (Kind == kDrawF32) out.out = static_cast<uint32_t*>(a.out);
     if constexpr (Kind == kDrawSumHist) {
       out.sum = 0;
       out.hist = hist_s + (threadIdx.x / 32) * 256;
@@ -117,6 +118,7 @@ cudaError_t launch_draw(int kind, const DrawArgs& a, cudaStream_t st) {
     case kDrawU24: return launch_kind<kDrawU24>(a, st);
     case kDrawF64: return launch_kind<kDrawF64>(a, st);
     case kDrawSumHist: return launch_kind<kDrawSumHist>(a, st);
+    case kDrawF32: return launch_kind<kDrawF32>(a, st);
   }
   return cudaErrorInvalidValue;
 }

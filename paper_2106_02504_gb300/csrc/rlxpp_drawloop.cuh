@@ -87,6 +87,33 @@ struct Consumer<kDrawU24> {
 };
 
 template <>
+struct Consumer<kDrawF32> {
+  uint32_t* out;
+  __device__ __forceinline__ void value_at_word(const uint32_t D[kLimbs], int w, int64_t idx) {
+    out[idx] = f32_bits_from24(word24(D, w));
+  }
+  __device__ __forceinline__ void block(const uint32_t D[kLimbs], int64_t idx) {
+    uint32_t* o = out + idx;
+    uint32_t w[kWords];
+#pragma unroll
+    for (int j = 0; j < kWords; ++j) w[j] = f32_bits_from24(word24(D, j));
+    if ((reinterpret_cast<uintptr_t>(o) & 15) == 0) {
+#pragma unroll
+      for (int j = 0; j < kWords; j += 4)
+        *reinterpret_cast<uint4*>(o + j) = make_uint4(w[j], w[j + 1], w[j + 2], w[j + 3]);
+    } else {
+#pragma unroll
+      for (int j = 0; j < kWords; ++j) o[j] = w[j];
+    }
+  }
+  __device__ __forceinline__ void partial(const uint32_t D[kLimbs], int64_t idx, int64_t n) {
+#pragma unroll
+    for (int j = 0; j < kWords; ++j)
+      if (j < n) out[idx + j] = f32_bits_from24(word24(D, j));
+  }
+};
+
+template <>
 struct Consumer<kDrawF64> {
   uint64_t* out;
   __device__ __forceinline__ void value_at_word(const uint32_t D[kLimbs], int w, int64_t idx) {
@@ -132,7 +159,7 @@ struct Consumer<kDrawSumHist> {
 template <int Kind, class AFn, class ASFn>
 __device__ __forceinline__ bool draw_stream(Consumer<Kind>& out, uint32_t D[kLimbs], uint32_t& c, uint32_t& pos,
                                             AFn A, ASFn AS, uint32_t ca, int64_t cnt, int64_t base) {
-  constexpr int need = Kind == kDrawU24 ? 1 : 2;  // RANLUX numbers per value
+  constexpr int need = (Kind == kDrawU24 || Kind == kDrawF32) ? 1 : 2;  // RANLUX numbers per value
   constexpr int per_block = kWords / need;
   int64_t k = 0;
   // head: the unread part of the current block

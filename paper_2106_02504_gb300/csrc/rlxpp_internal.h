@@ -44,7 +44,7 @@ struct StateView {
   int* status;       // sticky device status (rlxpp_status value, 0 = ok)
 };
 
-enum DrawKind { kDrawU24 = 0, kDrawF64 = 1, kDrawSumHist = 2 };
+enum DrawKind { kDrawU24 = 0, kDrawF64 = 1, kDrawSumHist = 2, kDrawF32 = 3 };
 
 struct DrawArgs {
   StateView s;
@@ -67,6 +67,8 @@ cudaError_t launch_level_setup(uint32_t p, uint32_t* lux_out18, uint32_t* table_
 cudaError_t launch_seed(const StateView& s, const uint64_t* seeds, const uint8_t* level_of_stream,
                         uint32_t n_levels, bool keep_levels, cudaStream_t st);
 cudaError_t launch_skip(const StateView& s, const uint64_t* n128, cudaStream_t st);
+// move each stream as if n[i] values of `need` numbers each had been drawn
+cudaError_t launch_skip_values(const StateView& s, const uint64_t* n, uint32_t need, cudaStream_t st);
 cudaError_t launch_draw(int kind, const DrawArgs& a, cudaStream_t st);
 cudaError_t launch_export(const StateView& s, const uint32_t* level_p, rlxpp_state* dst,
                           cudaStream_t st);
@@ -77,7 +79,7 @@ size_t tc_matrix_bytes();
 cudaError_t launch_tc_matrix(const uint32_t* lux18, void* bimg, cudaStream_t st);
 cudaError_t launch_draw_tc(int kind, const DrawArgs& a, const void* bimg, cudaStream_t st);
 cudaError_t launch_tc_mulmod(const void* bimg, const uint64_t* x, uint64_t* out, uint64_t n, int* status,
-                             cudaStream_t st);
+                             cudaStream_t st, bool issue = true);
 cudaError_t launch_test(int which, const uint64_t* x, const uint64_t* y, uint64_t* out,
                         uint32_t* carry, uint64_t n, cudaStream_t st);
 

@@ -119,6 +119,32 @@ __global__ void k_skip(StateView s, const uint64_t* __restrict__ n128) {
   s.meta[i] = meta_pack(meta_pos(meta), carry_of(X, D), lvl);
 }
 
+// Position arithmetic of a draw of n values (need numbers each) without producing
+// them: the rest of the current block, then whole blocks; X <- A^blocks X.
+__global__ void k_skip_values(StateView s, const uint64_t* __restrict__ nvals, uint32_t need) {
+  const uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= s.n) return;
+  const uint64_t n = nvals[i];
+  const uint32_t meta = s.meta[i];
+  const uint32_t pos = meta_pos(meta), lvl = meta_level(meta);
+  const uint64_t room = pos + need <= (uint32_t)kWords ? (kWords - pos) / need : 0;
+  if (n <= room) {
+    s.meta[i] = meta_pack(pos + (uint32_t)(n * need), meta_carry(meta), lvl);
+    return;
+  }
+  const uint64_t rest = n - room, per = kWords / need;
+  const uint64_t blocks = (rest - 1) / per + 1;
+  const uint32_t new_pos = (uint32_t)((rest - (blocks - 1) * per) * need);
+  uint32_t D[kLimbs], X[kLimbs];
+  load_state_D(s, i, D);
+  to_lcg(D, meta_carry(meta), X);
+  bool have = true;
+  apply_digits(s.table + (size_t)lvl * kTableLimbs, 0, blocks, X, have);
+  to_ranlux(X, D);
+  store_state_D(s, i, D);
+  s.meta[i] = meta_pack(new_pos, carry_of(X, D), lvl);
+}
+
 __global__ void k_export(StateView s, const uint32_t* __restrict__ level_p, rlxpp_state* dst) {
   const uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= s.n) return;
@@ -253,6 +279,12 @@ cudaError_t launch_seed(const StateView& s, const uint64_t* seeds, const uint8_t
 cudaError_t launch_skip(const StateView& s, const uint64_t* n128, cudaStream_t st) {
   if (s.n == 0) return cudaSuccess;
   k_skip<<<grid_for(s.n, 128), 128, 0, st>>>(s, n128);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_skip_values(const StateView& s, const uint64_t* n, uint32_t need, cudaStream_t st) {
+  if (s.n == 0) return cudaSuccess;
+  k_skip_values<<<grid_for(s.n, 128), 128, 0, st>>>(s, n, need);
   return cudaGetLastError();
 }
 

@@ -232,6 +232,11 @@ __device__ __forceinline__ void block_values(const uint32_t D[kLimbs], uint4 v[6
       const uint64_t a = f64_bits_from48(bits48(D, 2 * q)), b = f64_bits_from48(bits48(D, 2 * q + 1));
       v[q] = make_uint4((uint32_t)a, (uint32_t)(a >> 32), (uint32_t)b, (uint32_t)(b >> 32));
     }
+  } else if constexpr (Kind == kDrawF32) {
+#pragma unroll
+    for (int q = 0; q < 6; ++q)
+      v[q] = make_uint4(f32_bits_from24(word24(D, 4 * q)), f32_bits_from24(word24(D, 4 * q + 1)),
+                        f32_bits_from24(word24(D, 4 * q + 2)), f32_bits_from24(word24(D, 4 * q + 3)));
   } else {
 #pragma unroll
     for (int q = 0; q < 6; ++q)
@@ -264,15 +269,16 @@ __device__ __forceinline__ void tc_setup(__half* tile, __half* bmat, const __hal
 }
 
 // One refill of the whole tile: rows already written; returns false on a wait timeout.
+// issue = false leaves the barrier without an arrival (used to test the timeout path).
 __device__ __forceinline__ bool tc_refill(__half* tile, __half* bmat, TcShared* sh, uint32_t& phase,
-                                          uint32_t col[72]) {
+                                          uint32_t col[72], bool issue = true) {
   const int tid = threadIdx.x;
   fence_proxy_async_smem();  // this thread's row writes -> visible to the tensor core
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
   const uint32_t taddr = sh->taddr;
-  if (tid == 0) {
+  if (tid == 0 && issue) {
     const uint32_t a0 = smem_addr(tile), b0 = smem_addr(bmat);
 #pragma unroll
     for (int s = 0; s < kTcK / 16; ++s)  // K = 16 per instruction: two core matrices
@@ -340,11 +346,12 @@ __global__ void __launch_bounds__(kTcRows, 4) k_draw_tc(const DrawArgs a, const 
   Consumer<Kind> out;
   if constexpr (Kind == kDrawU24) out.out = static_cast<uint32_t*>(a.out);
   if constexpr (Kind == kDrawF64) out.out = static_cast<uint64_t*>(a.out);
+  if constexpr (Kind == kDrawF32) out.out = static_cast<uint32_t*>(a.out);
   if constexpr (Kind == kDrawSumHist) {
     out.sum = 0;
     out.hist = hist_s + (tid / 32) * 256;
   }
-  constexpr int need = Kind == kDrawU24 ? 1 : 2;
+  constexpr int need = (Kind == kDrawU24 || Kind == kDrawF32) ? 1 : 2;
   constexpr int per_block = kWords / need;
   int64_t k = 0;
   if (live && cnt > 0 && pos + need <= (uint32_t)kWords) {  // head of the current block
@@ -428,9 +435,11 @@ __global__ void __launch_bounds__(kTcRows, 4) k_draw_tc(const DrawArgs a, const 
   }
 }
 
-// One tensor-path product per item: out = A x mod m (x < m), for testing.
+// One tensor-path product per item: out = A x mod m (x < m), for testing.  With
+// issue == 0 no MMA is issued, so the barrier never completes and the bounded wait
+// must give up and report RLXPP_ERR_TIMEOUT.
 __global__ void __launch_bounds__(kTcRows, 4) k_tc_mulmod(const __half* __restrict__ bimg, const uint64_t* x,
-                                                          uint64_t* out, uint64_t n, int* status) {
+                                                          uint64_t* out, uint64_t n, int* status, int issue) {
   extern __shared__ __align__(1024) unsigned char smem[];
   __half* tile = reinterpret_cast<__half*>(smem);
   __half* bmat = reinterpret_cast<__half*>(smem + kTileBytes);
@@ -446,7 +455,7 @@ __global__ void __launch_bounds__(kTcRows, 4) k_tc_mulmod(const __half* __restri
   }
   write_x_row(tile, threadIdx.x, X);
   uint32_t col[72], phase = 0;
-  const bool ok = tc_refill(tile, bmat, sh, phase, col);
+  const bool ok = tc_refill(tile, bmat, sh, phase, col, issue != 0);
   if (ok) {
     columns_to_x(col, X);
     if (i < n)
@@ -455,7 +464,7 @@ __global__ void __launch_bounds__(kTcRows, 4) k_tc_mulmod(const __half* __restri
   } else if (threadIdx.x == 0) {
     atomicCAS(status, 0, (int)RLXPP_ERR_TIMEOUT);
   }
-  tc_teardown(sh, !ok, phase);
+  tc_teardown(sh, !ok && issue, phase);  // nothing is in flight when no MMA was issued
 }
 
 // The level's matrix in the shared-memory image layout: column j (K index) holds the
@@ -518,17 +527,18 @@ cudaError_t launch_draw_tc(int kind, const DrawArgs& a, const void* bimg, cudaSt
     case kDrawU24: return launch_tc_kind<kDrawU24>(a, b, st);
     case kDrawF64: return launch_tc_kind<kDrawF64>(a, b, st);
     case kDrawSumHist: return launch_tc_kind<kDrawSumHist>(a, b, st);
+    case kDrawF32: return launch_tc_kind<kDrawF32>(a, b, st);
   }
   return cudaErrorInvalidValue;
 }
 
 cudaError_t launch_tc_mulmod(const void* bimg, const uint64_t* x, uint64_t* out, uint64_t n, int* status,
-                             cudaStream_t st) {
+                             cudaStream_t st, bool issue) {
   if (n == 0) return cudaSuccess;
   cudaError_t e = cudaFuncSetAttribute(k_tc_mulmod, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTcSmem);
   if (e != cudaSuccess) return e;
   k_tc_mulmod<<<(unsigned)((n + kTcRows - 1) / kTcRows), kTcRows, kTcSmem, st>>>(static_cast<const __half*>(bimg),
-                                                                                 x, out, n, status);
+                                                                                 x, out, n, status, issue ? 1 : 0);
   return cudaGetLastError();
 }
 

@@ -350,3 +350,38 @@ def test_p24_ten_thousand_advances(native, path):
     for b in range(10_001):
         assert list(got[24 * b:24 * (b + 1)]) == w, b
         w, c = S.block(w, c, 24)
+
+
+@pytest.mark.parametrize("p,count", [(2048, 1000), (24, 25)])
+def test_draw_f32(native, p, count, path):
+    seeds = W.random_seeds(N, 111 + p)
+    g = make(native, seeds, levels=(p,), path=path)
+    g.draw_u24(torch.zeros((N, 3), dtype=torch.int32, device="cuda"), 3)   # odd positions
+    out = torch.zeros((N, count), dtype=torch.float32, device="cuda")
+    g.draw_f32(out, count)
+    ref = StreamSet.from_seeds(seeds, p)
+    ref.draw(3, S.KIND_U24)
+    want = ref.draw(count, S.KIND_F32)
+    assert np.array_equal(out.cpu().numpy().view(np.uint32), want.view(np.uint32))
+    assert_states(native, g, ref)
+
+
+@pytest.mark.parametrize("kind,need", [(0, 1), (1, 2), (2, 1)])
+def test_skip_values(native, kind, need):
+    p = 389
+    seeds = W.random_seeds(N, 121 + kind)
+    g = make(native, seeds, levels=(p,))
+    g.draw_u24(torch.zeros((N, 7), dtype=torch.int32, device="cuda"), 7)
+    rng = np.random.Generator(np.random.PCG64(122 + kind))
+    n = rng.integers(0, 5000, size=N).astype(np.uint64)
+    n[:6] = [0, 1, 16, 17, 18, 2 ** 40 + 3]
+    g.skip_values(torch.from_numpy(n.view(np.int64)).cuda(), kind)
+    got = states(native, g, N)
+    xs = seeded_X(seeds, p)
+    for i in range(N):
+        st = R.Stream(p, X=xs[int(seeds[i])])
+        st.draw_u24(7)
+        st.skip_values(int(n[i]), need)
+        D, c, pos = st.D, st.c, st.pos
+        assert from_limbs64(got[i, :9]) == D, i
+        assert int(got[i, 9]) == c | (pos << 32), i

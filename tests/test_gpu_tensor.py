@@ -131,3 +131,20 @@ def test_tc_full_size_workload(native):
     wsums, _ = ref.sum_hist(4096)
     assert np.array_equal(sums.cpu().numpy().view(np.uint64)[idx], wsums)
     assert int(hist.sum()) == n * 4096
+
+
+def test_bounded_wait_reports_timeout(native):
+    """A wait that nothing completes gives up, reports RLXPP_ERR_TIMEOUT, and the
+    context keeps working."""
+    import time
+    scratch = torch.zeros(9, dtype=torch.int64, device="cuda")
+    t0 = time.perf_counter()
+    with pytest.raises(native.RlxppError) as e:
+        native.rlxpp_test_tc_timeout(scratch)
+    assert e.value.status == native.RLXPP_ERR_TIMEOUT
+    assert time.perf_counter() - t0 < 60
+    x = torch.zeros((1, 9), dtype=torch.int64, device="cuda")
+    x[0, 0] = 5
+    out = torch.zeros((1, 9), dtype=torch.int64, device="cuda")
+    native.rlxpp_test_tc_mulmod(2048, x, out, 1)
+    assert from_limbs64(out.cpu().numpy().view(np.uint64)[0]) == R.luxury_multiplier(2048) * 5 % R.M
