@@ -368,7 +368,7 @@ def bench_single_stream(nat, dev):
             "serial": {"ms": ms_serial, "doubles_per_s": n / (ms_serial * 1e-3),
                        "ns_per_advance": ms_serial * 1e6 / adv},
             "split": {"ms": ms_split, "doubles_per_s": n / (ms_split * 1e-3), "chunks": items,
-                      "tuning": {"chunk_blocks": tuning[0], "blocks_per_sm": tuning[1]}}}
+                      "tuning": {"chunk_blocks": tuning[0], "blocks_per_sm": tuning[1], "path": tuning[2]}}}
 
 
 def bench_mixed_batch(nat, dev, args):
@@ -399,22 +399,31 @@ def bench_mixed_batch(nat, dev, args):
     refills = sum(advances_for(int(c), 0, 2 if f else 1)[0] for c, f in zip(counts, is_f64))
     st = torch.cuda.current_stream()
     t = time.perf_counter()
-    tuning = nat.rlxpp_autotune_requests(g.handle, reqs, out_u, out_f)
+    tuned = nat.rlxpp_autotune_requests(g.handle, reqs, out_u, out_f)  # picks the kernel too
     tune_s = time.perf_counter() - t
-    t = time.perf_counter()
-    plan = nat.rlxpp_plan_requests(g.handle, reqs, 0, tuning)
-    plan_s = time.perf_counter() - t
-    graph = torch.cuda.CUDAGraph()
-    side = torch.cuda.Stream()
-    side.wait_stream(st)
-    with torch.cuda.stream(side):
-        nat.rlxpp_run_plan(g.handle, plan, out_u, out_f, side.cuda_stream)
-    st.wait_stream(side)
-    with torch.cuda.graph(graph):
-        nat.rlxpp_run_plan(g.handle, plan, out_u, out_f)
-    ms_graph = _time_events(graph.replay, 3, st)
-    items = nat.rlxpp_plan_items(plan)
-    nat.rlxpp_destroy_plan(plan)
+    by_path = {}
+    for name, pid in (("tensor", nat.RLXPP_PATH_TENSOR), ("imad", nat.RLXPP_PATH_IMAD)):
+        tuning = (tuned[0], tuned[1], pid)
+        t = time.perf_counter()
+        plan = nat.rlxpp_plan_requests(g.handle, reqs, 0, tuning)
+        plan_s = time.perf_counter() - t
+        graph = torch.cuda.CUDAGraph()
+        side = torch.cuda.Stream()
+        side.wait_stream(st)
+        with torch.cuda.stream(side):
+            nat.rlxpp_run_plan(g.handle, plan, out_u, out_f, side.cuda_stream)
+        st.wait_stream(side)
+        with torch.cuda.graph(graph):
+            nat.rlxpp_run_plan(g.handle, plan, out_u, out_f)
+        ms = _time_events(graph.replay, 3, st)
+        by_path[name] = {"ms": ms, "values_per_s": int(counts.sum()) / (ms * 1e-3),
+                         "advances_per_s": refills / (ms * 1e-3), "chunks": nat.rlxpp_plan_items(plan),
+                         "tuning": {"chunk_blocks": tuning[0], "blocks_per_sm": tuning[1], "path": tuning[2]},
+                         "plan_s": plan_s, "tuner_choice": pid == tuned[2]}
+        nat.rlxpp_destroy_plan(plan)
+        del graph
+    best = min(by_path, key=lambda k: by_path[k]["ms"])
+    ms_graph = by_path[best]["ms"]
     # plain per-stream kernels: u24 streams, then f64 streams (the other kind draws 0)
     cu = torch.from_numpy(np.where(kind == 0, counts, 0)).to(dev)
     cf = torch.from_numpy(np.where(kind == 1, counts, 0)).to(dev)
@@ -428,10 +437,7 @@ def bench_mixed_batch(nat, dev, args):
     values = int(counts.sum())
     return {"streams": n, "values": values, "doubles": n_f, "u24": n_u, "advances": int(refills),
             "output_bytes": n_u * 4 + n_f * 8,
-            "batched_graph": {"ms": ms_graph, "values_per_s": values / (ms_graph * 1e-3),
-                              "advances_per_s": refills / (ms_graph * 1e-3), "chunks": items,
-                              "tuning": {"chunk_blocks": tuning[0], "blocks_per_sm": tuning[1]},
-                              "tune_s": tune_s, "plan_s": plan_s},
+            "batched_graph": dict(by_path[best], path=best, tune_s=tune_s), "batched_graph_by_path": by_path,
             "plain_per_stream": {"ms": ms_plain, "values_per_s": values / (ms_plain * 1e-3),
                                  "advances_per_s": refills / (ms_plain * 1e-3)},
             "speedup_vs_plain": ms_plain / ms_graph}

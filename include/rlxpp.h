@@ -162,7 +162,9 @@ typedef struct rlxpp_request {
 
 typedef struct rlxpp_tuning {
   uint32_t chunk_blocks;  /* L: refills per chunk, >= 2                                  */
-  uint32_t blocks_per_sm; /* persistent grid = blocks_per_sm x SMs blocks of 128 threads */
+  uint32_t blocks_per_sm; /* integer kernel: persistent grid = blocks_per_sm x SMs blocks */
+  uint32_t path;          /* RLXPP_PATH_IMAD or RLXPP_PATH_TENSOR (defined below): which
+                             product kernel runs the chunks                             */
 } rlxpp_tuning;
 
 typedef struct rlxpp_plan rlxpp_plan;
@@ -171,7 +173,8 @@ typedef struct rlxpp_plan rlxpp_plan;
  * pos <= 24, kind, count >= 0, skip + refills < 2^64, no stream twice with
  * RLXPP_REQ_ADVANCE), splits them into chunks and uploads the work list to device
  * memory owned by the plan.  tuning: NULL = the handle's tuned choice for requests of
- * this shape, else the defaults.  Synchronous; the plan belongs to `gen`. */
+ * this shape, else the defaults (the handle's path).  Synchronous; the plan belongs
+ * to `gen`. */
 rlxpp_status rlxpp_plan_requests(rlxpp_gen* gen, const rlxpp_request* reqs, uint64_t n_reqs,
                                  uint32_t flags, const rlxpp_tuning* tuning, rlxpp_plan** out);
 
@@ -196,7 +199,8 @@ rlxpp_status rlxpp_draw_requests(rlxpp_gen* gen, const rlxpp_request* reqs, uint
                                  uint32_t* out_u24, double* out_f64, uint32_t flags,
                                  void* cuda_stream);
 
-/* Tuner: times candidate (chunk length, grid) pairs on these requests (without
+/* Tuner: times candidate (product kernel, chunk length, grid) choices on these requests
+ * (the integer-pipe and the tensor-core kernel; without
  * RLXPP_REQ_ADVANCE, so the streams do not move; the outputs are overwritten) and
  * keeps the fastest for requests of the same shape (log2 buckets of the request count
  * and of the total refills).  The choice is kept in the handle and, when the
@@ -223,17 +227,17 @@ rlxpp_status rlxpp_set_state(rlxpp_gen* gen, const rlxpp_state* src, void* cuda_
 rlxpp_status rlxpp_sync(rlxpp_gen* gen, void* cuda_stream);
 
 /* ---- refill path -------------------------------------------------------------------
- * RLXPP_PATH_IMAD: the product on the integer pipe, one thread per stream (the default
- * for handles with several luxury levels).
- * RLXPP_PATH_TENSOR (the default for single-level handles): the product A X mod m as an
- * exact-integer fp16 matrix product on
+ * RLXPP_PATH_IMAD: the product on the integer pipe, one thread per stream.
+ * RLXPP_PATH_TENSOR (the default): the product A X mod m as an exact-integer fp16
+ * matrix product on
  * the tensor cores (tcgen05.mma, fp32 accumulation in tensor memory): with
  * R_j = A 2^(8j) mod m, A X = sum_j x_j R_j = sum_k S_k 2^(8k) (mod m) where x_j are
  * the 72 bytes of X and S_k = sum_j x_j byte_k(R_j) < 2^23, so a tile of 128 streams is
  * one 128 x 80 x 80 product per refill (Sec. 2.1-2.2 computed differently, same
- * result).  Only for handles with one luxury level (else RLXPP_ERR_UNSUPPORTED); used
- * by rlxpp_draw_u24/f64/f64_sum_hist, not by batched requests.  Synchronises the
- * device.  Both paths give bit-identical results. */
+ * result).  It serves the plain draws of single-level handles (a tile's streams share
+ * one multiplier; plain draws of multi-level handles use the integer kernel) and every
+ * batched request (chunks are grouped by level).  Synchronises the device.  Both paths
+ * give bit-identical results. */
 #define RLXPP_PATH_IMAD 0u
 #define RLXPP_PATH_TENSOR 1u
 rlxpp_status rlxpp_set_path(rlxpp_gen* gen, uint32_t path);

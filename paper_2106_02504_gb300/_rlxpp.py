@@ -30,7 +30,7 @@ assert STATE_BYTES == 88
 
 class RlxppTuning(ctypes.Structure):
     """struct rlxpp_tuning."""
-    _fields_ = [("chunk_blocks", ctypes.c_uint32), ("blocks_per_sm", ctypes.c_uint32)]
+    _fields_ = [("chunk_blocks", ctypes.c_uint32), ("blocks_per_sm", ctypes.c_uint32), ("path", ctypes.c_uint32)]
 
 
 RLXPP_KIND_U24, RLXPP_KIND_F64, RLXPP_KIND_F32 = 0, 1, 2
@@ -251,11 +251,15 @@ def _requests(reqs):
     return a, len(a)
 
 
-def _tuning(t):
+def _tuning(t, gen=None):
+    """(chunk_blocks, blocks_per_sm[, path]); the path defaults to the handle's."""
     if t is None:
         return None
     if isinstance(t, RlxppTuning):
         return ctypes.byref(t)
+    t = tuple(t)
+    if len(t) == 2:
+        t = t + (rlxpp_get_path(gen) if gen else RLXPP_PATH_TENSOR,)
     return ctypes.byref(RlxppTuning(*t))
 
 
@@ -263,7 +267,7 @@ def rlxpp_plan_requests(gen, reqs, flags=0, tuning=None):
     """Returns a plan handle (int).  reqs: numpy array of request_dtype() (host)."""
     a, n = _requests(reqs)
     h = _vp()
-    _check(_lib.rlxpp_plan_requests(gen, a.ctypes.data if n else None, n, flags, _tuning(tuning),
+    _check(_lib.rlxpp_plan_requests(gen, a.ctypes.data if n else None, n, flags, _tuning(tuning, gen),
                                     ctypes.byref(h)))
     return h.value
 
@@ -278,7 +282,7 @@ def rlxpp_plan_items(plan):
 
 def rlxpp_plan_tuning(plan):
     t = _lib.rlxpp_plan_tuning(plan)
-    return (t.chunk_blocks, t.blocks_per_sm)
+    return (t.chunk_blocks, t.blocks_per_sm, t.path)
 
 
 def rlxpp_destroy_plan(plan):
@@ -292,12 +296,12 @@ def rlxpp_draw_requests(gen, reqs, out_u24=None, out_f64=None, flags=0, stream=N
 
 
 def rlxpp_autotune_requests(gen, reqs, out_u24=None, out_f64=None, stream=None):
-    """Returns the chosen (chunk_blocks, blocks_per_sm)."""
+    """Returns the chosen (chunk_blocks, blocks_per_sm, path)."""
     a, n = _requests(reqs)
     t = RlxppTuning()
     _check(_lib.rlxpp_autotune_requests(gen, a.ctypes.data if n else None, n, _ptr(out_u24), _ptr(out_f64),
                                         _stream(stream), ctypes.byref(t)))
-    return (t.chunk_blocks, t.blocks_per_sm)
+    return (t.chunk_blocks, t.blocks_per_sm, t.path)
 
 
 def rlxpp_set_path(gen, path):

@@ -124,9 +124,10 @@ DrawArgs make_args(const rlxpp_gen* g) {
 
 constexpr size_t kChunkBytes = size_t(256) << 20;  // device staging per chunk of host output
 
-// The draw kernels of the handle's path: integer pipe, or tensor cores (single level).
+// The draw kernels of the handle's path: tensor cores when the handle has one luxury
+// level (a tile's streams share the multiplier matrix), else the integer pipe.
 cudaError_t launch_path(const rlxpp_gen* g, int kind, const DrawArgs& a, cudaStream_t st) {
-  if (g->path == RLXPP_PATH_TENSOR) return launch_draw_tc(kind, a, g->tc_matrix, st);
+  if (g->path == RLXPP_PATH_TENSOR && g->n_levels == 1) return launch_draw_tc(kind, a, g->tc_matrix, st);
   return launch_draw(kind, a, st);
 }
 
@@ -275,9 +276,10 @@ rlxpp_status rlxpp_create(uint64_t n_streams, const uint32_t* levels, uint32_t n
   if (e == cudaSuccess) e = cudaMemsetAsync(g->meta, 0, sizeof(uint32_t) * nn, st);
   if (e != cudaSuccess) return bail(fail(RLXPP_ERR_CUDA, std::string("create: ") + cudaGetErrorString(e)));
   if (rlxpp_status s = setup_levels(g, st)) return bail(s);
-  if (n_levels == 1) {  // single-level handles refill on the tensor cores by default
-    e = cudaMalloc(&g->tc_matrix, tc_matrix_bytes());
-    if (e == cudaSuccess) e = launch_tc_matrix(g->lux, g->tc_matrix, st);
+  {  // tensor-path matrices of every level; the tensor path is the default
+    e = cudaMalloc(&g->tc_matrix, tc_matrix_bytes() * n_levels);
+    for (uint32_t l = 0; e == cudaSuccess && l < n_levels; ++l)
+      e = launch_tc_matrix(g->lux + (size_t)l * 18, static_cast<char*>(g->tc_matrix) + tc_matrix_bytes() * l, st);
     if (e != cudaSuccess) return bail(fail(RLXPP_ERR_CUDA, std::string("tensor setup: ") + cudaGetErrorString(e)));
     g->path = RLXPP_PATH_TENSOR;
   }
@@ -434,10 +436,7 @@ rlxpp_status rlxpp_sync(rlxpp_gen* g, void* cuda_stream) {
 rlxpp_status rlxpp_set_path(rlxpp_gen* g, uint32_t path) {
   if (rlxpp_status s = check_gen(g)) return s;
   if (path != RLXPP_PATH_IMAD && path != RLXPP_PATH_TENSOR) return fail(RLXPP_ERR_INVALID, "unknown path");
-  if (path == RLXPP_PATH_TENSOR) {
-    if (g->n_levels != 1) return fail(RLXPP_ERR_UNSUPPORTED, "the tensor path serves single-level handles");
-    if (!g->tc_matrix) return fail(RLXPP_ERR_CUDA, "tensor matrix missing");
-  }
+  if (path == RLXPP_PATH_TENSOR && !g->tc_matrix) return fail(RLXPP_ERR_CUDA, "tensor matrix missing");
   RLX_CUDA(cudaDeviceSynchronize());  // no draw of the old path may still run
   g->path = path;
   return RLXPP_OK;

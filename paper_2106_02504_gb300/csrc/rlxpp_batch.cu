@@ -21,6 +21,7 @@
 #include <vector>
 
 #include "rlxpp_arith.cuh"
+#include "rlxpp_batch.h"
 #include "rlxpp_drawloop.cuh"
 #include "rlxpp_internal.h"
 #include "rlxpp_state.cuh"
@@ -34,25 +35,6 @@ namespace rlxpp {
 namespace {
 
 constexpr int kReqBlock = 128;
-
-struct Item {       // one chunk (32 bytes)
-  uint64_t jump;    // LCG advances from the request's start state to this chunk's block
-  int64_t count;    // values
-  uint64_t out;     // index of the first value in the output array of its kind
-  uint32_t req;     // request index
-  uint32_t info;    // bit 0: kind (1 = f64); bits 8..15: read position; bit 16: last chunk
-};
-
-struct BatchArgs {
-  const uint64_t* req_stream;  // [n_reqs]
-  uint64_t* snap_D;            // [9][n_reqs]
-  uint32_t* snap_meta;         // [n_reqs]
-  uint64_t n_reqs;
-  StateView s;                 // resident states (final states are written back here)
-  uint32_t* out_u24;
-  uint64_t* out_f64;
-  int advance;
-};
 
 // Copy the state of each request's stream (before any chunk runs).
 __global__ void k_snapshot(BatchArgs b) {
@@ -147,7 +129,7 @@ void append_cache_line(const rlxpp_gen* g, uint32_t sig, const rlxpp_tuning& t) 
   if (!path || !*path) return;
   std::lock_guard<std::mutex> lock(g_cache_mutex);
   std::ofstream f(path, std::ios::app);
-  if (f) f << device_key(g) << "|" << sig << "|" << t.chunk_blocks << "|" << t.blocks_per_sm << "\n";
+  if (f) f << device_key(g) << "|" << sig << "|" << t.chunk_blocks << "|" << t.blocks_per_sm << "|" << t.path << "\n";
 }
 
 // Refills a request needs after its start block.
@@ -171,12 +153,13 @@ void load_tune_cache(rlxpp_gen* g) {
   const std::string key = device_key(g);
   std::string line;
   while (std::getline(f, line)) {
-    // <device>/<sms>|<signature>|<chunk_blocks>|<blocks_per_sm>
+    // <device>/<sms>|<signature>|<chunk_blocks>|<blocks_per_sm>|<path>
     const size_t a = line.find('|');
     if (a == std::string::npos || line.compare(0, a, key) != 0) continue;
-    unsigned sig = 0, L = 0, bps = 0;
-    if (std::sscanf(line.c_str() + a + 1, "%u|%u|%u", &sig, &L, &bps) == 3 && L >= 2 && bps >= 1 && bps <= 8)
-      g->tuned[sig] = rlxpp_tuning{L, bps};  // later lines win
+    unsigned sig = 0, L = 0, bps = 0, path = 0;
+    if (std::sscanf(line.c_str() + a + 1, "%u|%u|%u|%u", &sig, &L, &bps, &path) == 4 && L >= 2 && bps >= 1 &&
+        bps <= 8 && path <= 1)
+      g->tuned[sig] = rlxpp_tuning{L, bps, path};  // later lines win
   }
 }
 
@@ -255,11 +238,12 @@ rlxpp_status plan_impl(rlxpp_gen* g, const rlxpp_request* reqs, uint64_t n_reqs,
       uint64_t L = total_refills / std::max<uint64_t>(threads, 1);
       uint32_t p2 = 4;
       while (p2 < L && p2 < 256) p2 <<= 1;
-      t = rlxpp_tuning{p2, 4};
+      t = rlxpp_tuning{p2, 4, g->path};
     }
   }
-  if (t.chunk_blocks < 2 || t.blocks_per_sm < 1 || t.blocks_per_sm > 8)
-    return set_last_error(RLXPP_ERR_INVALID, "tuning needs chunk_blocks >= 2 and 1..8 blocks per SM");
+  if (t.chunk_blocks < 2 || t.blocks_per_sm < 1 || t.blocks_per_sm > 8 ||
+      (t.path != RLXPP_PATH_IMAD && t.path != RLXPP_PATH_TENSOR))
+    return set_last_error(RLXPP_ERR_INVALID, "tuning needs chunk_blocks >= 2, 1..8 blocks per SM and a path");
   const uint64_t L = t.chunk_blocks;
   // chunks
   std::vector<Item> items;
@@ -298,14 +282,22 @@ rlxpp_status plan_impl(rlxpp_gen* g, const rlxpp_request* reqs, uint64_t n_reqs,
     items.back().info |= 1u << 16;
   }
   if (n_reqs >= (uint64_t(1) << 32)) return set_last_error(RLXPP_ERR_INVALID, "too many requests");
-  // by luxury level (one launch each), then longest first; equal lengths grouped by kind
-  // and then by request
+  // by luxury level (one launch each), then most refills first (neighbours, which share
+  // a warp or a tensor tile, then take about as long), then by kind and request
   const uint8_t* lev = g->level_host.data();
   auto level_of = [&](const Item& a) { return lev[reqs[a.req].stream]; };
+  auto refills_of = [](const Item& a) {  // refills of a chunk: ceil((count - head) / per)
+    const uint32_t kind = a.info & 1u, pos = (a.info >> 8) & 0xFFu, need = kind ? 2 : 1;
+    const int64_t per = kWords / need;
+    const int64_t room = pos + need <= (uint32_t)kWords ? (kWords - pos) / need : 0;
+    const int64_t rest = a.count > room ? a.count - room : 0;
+    return (rest + per - 1) / per;
+  };
   std::sort(items.begin(), items.end(), [&](const Item& a, const Item& b) {
     const uint8_t la = level_of(a), lb = level_of(b);
     if (la != lb) return la < lb;
-    if (a.count != b.count) return a.count > b.count;
+    const int64_t ra = refills_of(a), rb = refills_of(b);
+    if (ra != rb) return ra > rb;
     if ((a.info & 1u) != (b.info & 1u)) return (a.info & 1u) > (b.info & 1u);
     return a.req < b.req;
   });
@@ -375,12 +367,19 @@ rlxpp_status run_impl(rlxpp_gen* g, const rlxpp_plan* p, uint32_t* out_u24, doub
   const unsigned grid = (unsigned)std::max(1, g->sms) * p->tuning.blocks_per_sm;
   uint32_t busy = 0;
   for (uint32_t l = 0; l < g->n_levels; ++l) busy += p->level_begin[l + 1] > p->level_begin[l];
+  const bool tensor = p->tuning.path == RLXPP_PATH_TENSOR && g->tc_matrix;
+  auto launch_level = [&](uint32_t l, uint64_t n, cudaStream_t s) {
+    const Item* it = p->items + p->level_begin[l];
+    if (tensor)
+      return launch_requests_tc(b, it, n, static_cast<const char*>(g->tc_matrix) + tc_matrix_bytes() * l, s);
+    k_requests<<<grid, kReqBlock, 0, s>>>(b, g->lux_host[l], it, n, p->counter + l);
+    return cudaGetLastError();
+  };
   if (busy <= 1) {
     for (uint32_t l = 0; e == cudaSuccess && l < g->n_levels; ++l) {
       const uint64_t n = p->level_begin[l + 1] - p->level_begin[l];
       if (n == 0) continue;
-      k_requests<<<grid, kReqBlock, 0, st>>>(b, g->lux_host[l], p->items + p->level_begin[l], n, p->counter + l);
-      e = cudaGetLastError();
+      e = launch_level(l, n, st);
     }
   } else {
     // one launch per level, concurrently on the handle's side streams (fork / join with
@@ -393,8 +392,7 @@ rlxpp_status run_impl(rlxpp_gen* g, const rlxpp_plan* p, uint32_t* out_u24, doub
       cudaStream_t ls = g->level_stream[l];
       e = cudaStreamWaitEvent(ls, fork, 0);
       if (e != cudaSuccess) break;
-      k_requests<<<grid, kReqBlock, 0, ls>>>(b, g->lux_host[l], p->items + p->level_begin[l], n, p->counter + l);
-      e = cudaGetLastError();
+      e = launch_level(l, n, ls);
       if (e == cudaSuccess) e = cudaEventRecord(g->level_event[l], ls);
       if (e == cudaSuccess) e = cudaStreamWaitEvent(st, g->level_event[l], 0);
     }
@@ -419,7 +417,7 @@ rlxpp_status rlxpp_run_plan(rlxpp_gen* gen, const rlxpp_plan* plan, uint32_t* ou
 
 uint64_t rlxpp_plan_items(const rlxpp_plan* plan) { return plan ? plan->n_items : 0; }
 
-rlxpp_tuning rlxpp_plan_tuning(const rlxpp_plan* plan) { return plan ? plan->tuning : rlxpp_tuning{0, 0}; }
+rlxpp_tuning rlxpp_plan_tuning(const rlxpp_plan* plan) { return plan ? plan->tuning : rlxpp_tuning{0, 0, 0}; }
 
 void rlxpp_destroy_plan(rlxpp_plan* plan) {
   if (plan) cudaSetDevice(plan->gen->device);
@@ -450,7 +448,7 @@ rlxpp_status rlxpp_autotune_requests(rlxpp_gen* gen, const rlxpp_request* reqs, 
   cudaEvent_t e0, e1;
   if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
     return set_last_error(RLXPP_ERR_CUDA, "cudaEventCreate failed");
-  rlxpp_tuning bestt{0, 0};
+  rlxpp_tuning bestt{0, 0, 0};
   float best_ms = 1e30f;
   rlxpp_status status = RLXPP_OK;
   // chunk lengths from the one giving ~64 chunks per resident thread (shorter ones only
@@ -458,14 +456,18 @@ rlxpp_status rlxpp_autotune_requests(rlxpp_gen* gen, const rlxpp_request* reqs, 
   const uint64_t threads = (uint64_t)std::max(1, gen->sms) * 4 * kReqBlock;
   uint32_t L0 = 4;
   while (L0 < 1024 && (uint64_t)L0 * threads * 64 < total) L0 <<= 1;
+  for (uint32_t path = 0; path < 2 && status == RLXPP_OK; ++path)
   for (uint32_t L = L0; L <= 1024 && status == RLXPP_OK; L <<= 1) {
+    if (path == RLXPP_PATH_TENSOR && !gen->tc_matrix) break;
     if (L > L0 && L / 2 >= std::max<uint64_t>(longest, 4)) break;  // longer chunks change nothing
-    rlxpp_tuning t{L, 4};
+    rlxpp_tuning t{L, 4, path};
     rlxpp_plan* p = nullptr;
     status = plan_impl(gen, reqs, n_reqs, 0, &t, &p);
     if (status != RLXPP_OK) break;
-    for (uint32_t bps = 2; bps <= 4 && status == RLXPP_OK; ++bps) {
-      p->tuning.blocks_per_sm = bps;  // the grid is chosen at run time
+    // the integer kernel's grid is chosen at run time; the tensor kernel has one tile per CTA
+    const uint32_t bps_hi = path == RLXPP_PATH_TENSOR ? 2 : 4;
+    for (uint32_t bps = 2; bps <= bps_hi && status == RLXPP_OK; ++bps) {
+      p->tuning.blocks_per_sm = bps;
       float ms = 1e30f;
       for (int rep = 0; rep < 3 && status == RLXPP_OK; ++rep) {  // first run warms up
         cudaEventRecord(e0, st);
@@ -478,7 +480,7 @@ rlxpp_status rlxpp_autotune_requests(rlxpp_gen* gen, const rlxpp_request* reqs, 
       }
       if (status == RLXPP_OK && ms < best_ms) {
         best_ms = ms;
-        bestt = rlxpp_tuning{L, bps};
+        bestt = rlxpp_tuning{L, bps, path};
       }
     }
     free_plan(p, nullptr, false);

@@ -25,6 +25,7 @@
 #include <cuda_fp16.h>
 
 #include "rlxpp_arith.cuh"
+#include "rlxpp_batch.h"
 #include "rlxpp_drawloop.cuh"
 #include "rlxpp_internal.h"
 #include "rlxpp_state.cuh"
@@ -435,6 +436,145 @@ __global__ void __launch_bounds__(kTcRows, 4) k_draw_tc(const DrawArgs a, const 
   }
 }
 
+// Emits the unread part of the current block for a value kind (f64 or u24).
+__device__ __forceinline__ void emit_head(bool f64, const BatchArgs& b, const uint32_t D[kLimbs], uint32_t& pos,
+                                          int64_t cnt, int64_t base, int64_t& k) {
+  const int need = f64 ? 2 : 1;
+  if (cnt <= 0 || pos + need > (uint32_t)kWords) return;
+  const int64_t room = (kWords - pos) / need;
+  const int64_t h = cnt < room ? cnt : room;
+#pragma unroll
+  for (int w = 0; w < kWords; ++w) {
+    const int d = w - (int)pos;
+    if (d < 0 || d % need != 0 || d / need >= h) continue;
+    if (f64) {
+      if (w + 1 < kWords) b.out_f64[base + d / 2] = f64_bits_from48(bits48_at_word(D, w));
+    } else {
+      b.out_u24[base + d] = word24(D, w);
+    }
+  }
+  k = h;
+  pos += (uint32_t)(h * need);
+}
+
+// Batched requests on the tensor cores.  One CTA = one tile of 128 consecutive chunks of
+// the (per level, longest-first) list: every thread jumps its chunk to its start block
+// (table products on the integer pipe), then the tile refills in lock step as in
+// k_draw_tc until every chunk is done.  Chunks of a tile have similar lengths, so little
+// work is lost to the longest one.
+__global__ void __launch_bounds__(kTcRows, 4) k_requests_tc(const BatchArgs b, const Item* __restrict__ items,
+                                                            uint64_t n_items, const __half* __restrict__ bimg) {
+  extern __shared__ __align__(1024) unsigned char smem[];
+  __half* tile = reinterpret_cast<__half*>(smem);
+  __half* bmat = reinterpret_cast<__half*>(smem + kTileBytes);
+  TcShared* sh = reinterpret_cast<TcShared*>(smem + kTileBytes + kBBytes);
+  uint4* slot = reinterpret_cast<uint4*>(smem + kStageOffset + threadIdx.x * kStageBytes);
+  const int tid = threadIdx.x;
+  tc_setup(tile, bmat, bimg, sh);
+  const uint64_t idx = (uint64_t)blockIdx.x * kTcRows + tid;
+  const bool live = idx < n_items;
+  Item it{};
+  if (live) it = items[idx];
+  uint32_t D[kLimbs];
+#pragma unroll
+  for (int q = 0; q < kLimbs; ++q) D[q] = 0;
+  uint32_t c = 0, lvl = 0;
+  if (live) {
+    const uint32_t meta = b.snap_meta[it.req];
+    lvl = meta_level(meta);
+    c = meta_carry(meta);
+#pragma unroll
+    for (int q = 0; q < 9; ++q) {
+      const uint64_t v = b.snap_D[(uint64_t)q * b.n_reqs + it.req];
+      D[2 * q] = (uint32_t)v;
+      D[2 * q + 1] = (uint32_t)(v >> 32);
+    }
+    if (it.jump) {  // X <- A^jump X
+      uint32_t X[kLimbs];
+      to_lcg(D, c, X);
+      bool have = true;
+      apply_digits(b.s.table + (size_t)lvl * kTableLimbs, 0, it.jump, X, have);
+      to_ranlux(X, D);
+      c = carry_of(X, D);
+    }
+  }
+  const bool f64 = (it.info & 1u) != 0;
+  const int64_t cnt = live ? it.count : 0, base = (int64_t)it.out;
+  uint32_t pos = live ? (it.info >> 8) & 0xFFu : (uint32_t)kWords;
+  int64_t k = 0;
+  emit_head(f64, b, D, pos, cnt, base, k);
+  bool mine = live && k < cnt, refilled = false;
+  uint32_t X[kLimbs];
+  to_lcg(D, c, X);
+  uint32_t phase = 0;
+  bool ok = true;
+  while (__syncthreads_or(mine)) {
+    write_x_row(tile, tid, X);
+    uint32_t col[72];
+    if (!tc_refill(tile, bmat, sh, phase, col)) {
+      ok = false;
+      break;
+    }
+    uint32_t Xn[kLimbs];
+    columns_to_x(col, Xn);
+    if (mine) {
+#pragma unroll
+      for (int q = 0; q < kLimbs; ++q) X[q] = Xn[q];
+      to_ranlux(X, D);
+      refilled = true;
+      const int64_t per = f64 ? kDoubles : kWords;
+      const int64_t rem = cnt - k;
+      if (rem >= per) {
+        void* dst = f64 ? (void*)(b.out_f64 + base + k) : (void*)(b.out_u24 + base + k);
+        uint4 v[6];
+        if (f64)
+          block_values<kDrawF64>(D, v);
+        else
+          block_values<kDrawU24>(D, v);
+        if ((reinterpret_cast<uintptr_t>(dst) & 15) == 0) {
+          bulk_store96(dst, slot, v);
+        } else {
+          uint32_t* o = static_cast<uint32_t*>(dst);
+#pragma unroll
+          for (int q = 0; q < 6; ++q) {
+            o[4 * q] = v[q].x;
+            o[4 * q + 1] = v[q].y;
+            o[4 * q + 2] = v[q].z;
+            o[4 * q + 3] = v[q].w;
+          }
+        }
+        k += per;
+        pos = kWords;
+      } else {
+        if (f64) {
+#pragma unroll
+          for (int j = 0; j < kDoubles; ++j)
+            if (j < rem) b.out_f64[base + k + j] = f64_bits_from48(bits48(D, j));
+          pos = (uint32_t)(rem * 2);
+        } else {
+#pragma unroll
+          for (int j = 0; j < kWords; ++j)
+            if (j < rem) b.out_u24[base + k + j] = word24(D, j);
+          pos = (uint32_t)rem;
+        }
+        k = cnt;
+      }
+      mine = k < cnt;
+    }
+  }
+  bulk_wait_all();
+  if (!ok) {
+    if (tid == 0) atomicCAS(b.s.status, 0, (int)RLXPP_ERR_TIMEOUT);
+  } else if (live && b.advance && ((it.info >> 16) & 1u)) {  // last chunk: final state
+    if (refilled) c = carry_of(X, D);
+    const uint64_t st = b.req_stream[it.req];
+#pragma unroll
+    for (int q = 0; q < 9; ++q) b.s.D[(uint64_t)q * b.s.stride + st] = ((uint64_t)D[2 * q + 1] << 32) | D[2 * q];
+    b.s.meta[st] = meta_pack(pos, c, lvl);
+  }
+  tc_teardown(sh, !ok, phase);
+}
+
 // One tensor-path product per item: out = A x mod m (x < m), for testing.  With
 // issue == 0 no MMA is issued, so the barrier never completes and the bounded wait
 // must give up and report RLXPP_ERR_TIMEOUT.
@@ -514,6 +654,16 @@ cudaError_t launch_tc_kind(const DrawArgs& a, const __half* bimg, cudaStream_t s
 }  // namespace
 
 size_t tc_matrix_bytes() { return kBBytes; }
+
+cudaError_t launch_requests_tc(const BatchArgs& b, const Item* items, uint64_t n, const void* bimg,
+                               cudaStream_t st) {
+  if (n == 0) return cudaSuccess;
+  cudaError_t e = cudaFuncSetAttribute(k_requests_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTcSmem);
+  if (e != cudaSuccess) return e;
+  k_requests_tc<<<(unsigned)((n + kTcRows - 1) / kTcRows), kTcRows, kTcSmem, st>>>(
+      b, items, n, static_cast<const __half*>(bimg));
+  return cudaGetLastError();
+}
 
 cudaError_t launch_tc_matrix(const uint32_t* lux18, void* bimg, cudaStream_t st) {
   k_tc_matrix<<<1, kTcK, 0, st>>>(lux18, static_cast<__half*>(bimg));

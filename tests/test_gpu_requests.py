@@ -16,6 +16,15 @@ pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
 
 
+@pytest.fixture(params=["tensor", "imad"])
+def path(request):
+    return request.param
+
+
+def set_path(native, g, path):
+    g.set_path(native.RLXPP_PATH_IMAD if path == "imad" else native.RLXPP_PATH_TENSOR)
+
+
 @pytest.fixture(scope="module")
 def native():
     if not torch.cuda.is_available():
@@ -92,13 +101,14 @@ def current_X(native, g, n):
     return xs, rec
 
 
-def test_mixed_requests(native):
+def test_mixed_requests(native, path):
     n = 200
     levels = [24, 223, 389, 2048]
     lvl = (np.arange(n) % 4).astype(np.uint8)
     seeds = W.random_seeds(n, 201)
     g = native.Generator(n, levels, torch.from_numpy(seeds.view(np.int64)).cuda(),
                          torch.from_numpy(lvl).cuda())
+    set_path(native, g, path)
     xs, _ = current_X(native, g, n)
     levels_of = [levels[int(lvl[i])] for i in range(n)]
     rng = np.random.Generator(np.random.PCG64(202))
@@ -111,17 +121,18 @@ def test_mixed_requests(native):
         count = int(rng.choice([0, 1, 2, 11, 12, 13, 24, 25, int(rng.integers(0, 3000))]))
         rows.append((st, skip, pos, kind, count))
     reqs, nu, nf = make_requests(rows)
-    for tuning in [(2, 2), (4, 4), (64, 3), None]:
+    for tuning in [(2, 2), (4, 4), (64, 3), (16, 2, 1 - native.rlxpp_get_path(g.handle)), None]:
         run_and_check(native, g, xs, levels_of, reqs, nu, nf, tuning=tuning)
     # streams did not move
     xs2, _ = current_X(native, g, n)
     assert xs2 == xs
 
 
-def test_advance_flag_and_graph(native):
+def test_advance_flag_and_graph(native, path):
     n = 130
     seeds = W.consecutive_seeds(n, first=300)
     g = native.Generator(n, [2048], torch.from_numpy(seeds.view(np.int64)).cuda())
+    set_path(native, g, path)
     xs, _ = current_X(native, g, n)
     rng = np.random.Generator(np.random.PCG64(203))
     rows = [(i, int(rng.integers(0, 1000)), int(rng.integers(0, 25)), int(rng.integers(0, 2)),
@@ -142,7 +153,7 @@ def test_advance_flag_and_graph(native):
     run_and_check(native, g, xs, [2048] * n, reqs, nu, nf, tuning=(16, 3), graph=True)
 
 
-def test_chunking_matches_plain_draw(native):
+def test_chunking_matches_plain_draw(native, path):
     """One long request split at several chunk lengths equals rlxpp_draw_f64."""
     seeds = np.array([42, 43], dtype=np.uint64)
     count = 100_003
@@ -150,6 +161,7 @@ def test_chunking_matches_plain_draw(native):
     plain = torch.zeros((2, count), dtype=torch.float64, device="cuda")
     ref.draw_f64(plain, count)
     g = native.Generator(2, [389], torch.from_numpy(seeds.view(np.int64)).cuda())
+    set_path(native, g, path)
     import paper_2106_02504_gb300._rlxpp as B
     reqs = np.zeros(2, dtype=B.request_dtype())
     reqs[0] = (0, 0, 0, 1, count, 0)
@@ -163,10 +175,11 @@ def test_chunking_matches_plain_draw(native):
         assert torch.equal(out.view(2, count), plain), L
 
 
-def test_single_stream_split(native):
+def test_single_stream_split(native, path):
     """Seed 1, p = 2048, 2^20 doubles drawn by many threads through jump-ahead."""
     n = 1 << 20
     g = native.Generator(1, [2048], torch.ones(1, dtype=torch.int64, device="cuda"))
+    set_path(native, g, path)
     import paper_2106_02504_gb300._rlxpp as B
     reqs = np.zeros(1, dtype=B.request_dtype())
     reqs[0] = (0, 0, 0, 1, n, 0)
@@ -184,10 +197,11 @@ def test_single_stream_split(native):
     assert np.array_equal(buf.cpu().numpy().view(np.uint64)[0], ref.state_records()[0])
 
 
-def test_autotune(native):
+def test_autotune(native, path):
     n = 512
     seeds = W.consecutive_seeds(n)
     g = native.Generator(n, [2048], torch.from_numpy(seeds.view(np.int64)).cuda())
+    set_path(native, g, path)
     xs, _ = current_X(native, g, n)
     counts = W.log_uniform_counts(n, 1, 20000, seed=204)
     rows = [(i, 0, 0, i % 2, int(counts[i])) for i in range(n)]
@@ -195,7 +209,7 @@ def test_autotune(native):
     out_u = torch.zeros(max(nu, 1), dtype=torch.int32, device="cuda")
     out_f = torch.zeros(max(nf, 1), dtype=torch.float64, device="cuda")
     best = native.rlxpp_autotune_requests(g.handle, reqs, out_u, out_f)
-    assert best[0] >= 2 and 1 <= best[1] <= 8
+    assert best[0] >= 2 and 1 <= best[1] <= 8 and best[2] in (0, 1)
     plan = native.rlxpp_plan_requests(g.handle, reqs)        # uses the tuned choice
     assert native.rlxpp_plan_tuning(plan) == best
     native.rlxpp_destroy_plan(plan)

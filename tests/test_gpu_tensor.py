@@ -102,9 +102,8 @@ def test_tc_path_rules(native):
     one = native.Generator(8, [2048], torch.arange(1, 9, dtype=torch.int64, device="cuda"))
     assert native.rlxpp_get_path(one.handle) == native.RLXPP_PATH_TENSOR   # single level: tensor default
     g = native.Generator(8, [24, 2048], torch.arange(1, 9, dtype=torch.int64, device="cuda"))
-    with pytest.raises(native.RlxppError) as e:
-        g.set_path(native.RLXPP_PATH_TENSOR)
-    assert e.value.status == native.RLXPP_ERR_UNSUPPORTED
+    assert native.rlxpp_get_path(g.handle) == native.RLXPP_PATH_TENSOR
+    g.set_path(native.RLXPP_PATH_IMAD)
     with pytest.raises(native.RlxppError):
         g.set_path(7)
     assert native.rlxpp_get_path(g.handle) == native.RLXPP_PATH_IMAD
