@@ -369,20 +369,32 @@ __device__ __forceinline__ uint64_t bits48(const uint32_t D[kLimbs], int j) {
 // reads v 2^-48: with lz leading zeros in the 64-bit v, the shift is s = lz - 11 and
 // the biased exponent 1038 - lz (the leading one itself adds 1 to the field when
 // (1026 - s) << 52 is added).  v = 0 maps to +0.0.
-__device__ __forceinline__ uint64_t f64_bits_from48(uint64_t v) {
-  const uint32_t hi = (uint32_t)(v >> 32), lo = (uint32_t)v;
-  if (hi != 0u) {  // 2^32 <= v < 2^48 (all but a 2^-16 share of the values)
-    const uint32_t lz = __clz(hi);  // 16..31, the leading zeros of v as a 64-bit word
-    const uint32_t s = lz - 11u;    // 5..20
-    const uint32_t mh = __funnelshift_l(lo, hi, s);
-    const uint32_t ml = lo << s;
-    return ((uint64_t)(mh + ((1037u - lz) << 20)) << 32) | ml;
-  }
+__device__ __forceinline__ uint64_t f64_bits_from48_small(uint64_t v) {  // v < 2^32
   const int lz = __clzll((long long)v);  // 32..64
   const int s = lz - 11;
   const uint64_t mant = v << (s & 63);
   const uint64_t bits = mant + ((uint64_t)(1026 - s) << 52);
   return v ? bits : 0ull;
+}
+__device__ __forceinline__ uint64_t f64_bits_from48_large(uint64_t v) {  // 2^32 <= v < 2^48
+  const uint32_t hi = (uint32_t)(v >> 32), lo = (uint32_t)v;
+  const uint32_t lz = __clz(hi);  // 16..31, the leading zeros of v as a 64-bit word
+  const uint32_t s = lz - 11u;    // 5..20
+  const uint32_t mh = __funnelshift_l(lo, hi, s);
+  const uint32_t ml = lo << s;
+  return ((uint64_t)(mh + ((1037u - lz) << 20)) << 32) | ml;
+}
+__device__ __forceinline__ uint64_t f64_bits_from48(uint64_t v) {
+  return (v >> 32) != 0u ? f64_bits_from48_large(v) : f64_bits_from48_small(v);
+}
+// The same value with the v < 2^32 case (a 2^-16 share of the values) in a call, so that
+// the common case carries no inline copy of it; for kernels with registers to spare.
+static __device__ __noinline__ uint64_t f64_bits_from48_small_call(uint64_t v) {
+  return f64_bits_from48_small(v);
+}
+__device__ __forceinline__ uint64_t f64_bits_from48_outlined(uint64_t v) {
+  if (__builtin_expect((v >> 32) == 0u, 0)) return f64_bits_from48_small_call(v);
+  return f64_bits_from48_large(v);
 }
 
 // 24-bit number w -> the binary32 w 2^-24 in [0, 1) (exact), by integer operations:

@@ -153,13 +153,17 @@ __device__ __forceinline__ void write_x_row(__half* tile, int row, const uint32_
 __device__ __forceinline__ void columns_to_x(const uint32_t col[72], uint32_t X[kLimbs]) {
   // limb t gathers S_4t + S_4t+1 2^8 + S_4t+2 2^16 + S_4t+3 2^24 (below 2^48) as lo + hi 2^32
   uint32_t lo[kLimbs], hi[kLimbs];
+  // With col = 0x4B000000 + S (B = the bias bits), u = S_4t + 2^8 S_4t+1 is
+  // (col_4t + 2^8 col_4t+1 - 257 B) mod 2^32 exactly, as u < 2^31: one multiply-add on
+  // the FMA pipe and one addition, instead of stripping the bias from each column.
+  constexpr uint32_t kBias257 = 0u - 257u * 0x4B000000u;
 #pragma unroll
   for (int t = 0; t < kLimbs; ++t) {
-    const uint32_t s0 = col[4 * t] & 0x7FFFFFu, s1 = col[4 * t + 1] & 0x7FFFFFu;
-    const uint32_t s2 = col[4 * t + 2] & 0x7FFFFFu, s3 = col[4 * t + 3] & 0x7FFFFFu;
-    uint32_t u, v;  // both below 2^31; the multiply-adds run on the FMA pipe
-    asm("mad.lo.u32 %0, %1, 256, %2;" : "=r"(u) : "r"(s1), "r"(s0));
-    asm("mad.lo.u32 %0, %1, 256, %2;" : "=r"(v) : "r"(s3), "r"(s2));
+    uint32_t u, v;  // both below 2^31
+    asm("mad.lo.u32 %0, %1, 256, %2;" : "=r"(u) : "r"(col[4 * t + 1]), "r"(col[4 * t]));
+    asm("mad.lo.u32 %0, %1, 256, %2;" : "=r"(v) : "r"(col[4 * t + 3]), "r"(col[4 * t + 2]));
+    u += kBias257;
+    v += kBias257;
     const uint64_t w = mad_wide(v, 65536u, (uint64_t)u);  // u + v 2^16 < 2^47
     lo[t] = lo32(w);
     hi[t] = hi32(w);
@@ -230,7 +234,7 @@ __device__ __forceinline__ void block_values(const uint32_t D[kLimbs], uint4 v[6
   if constexpr (Kind == kDrawF64) {
 #pragma unroll
     for (int q = 0; q < 6; ++q) {
-      const uint64_t a = f64_bits_from48(bits48(D, 2 * q)), b = f64_bits_from48(bits48(D, 2 * q + 1));
+      const uint64_t a = f64_bits_from48_outlined(bits48(D, 2 * q)), b = f64_bits_from48_outlined(bits48(D, 2 * q + 1));
       v[q] = make_uint4((uint32_t)a, (uint32_t)(a >> 32), (uint32_t)b, (uint32_t)(b >> 32));
     }
   } else if constexpr (Kind == kDrawF32) {
@@ -271,13 +275,10 @@ __device__ __forceinline__ void tc_setup(__half* tile, __half* bmat, const __hal
 
 // One refill of the whole tile: rows already written; returns false on a wait timeout.
 // issue = false leaves the barrier without an arrival (used to test the timeout path).
-__device__ __forceinline__ bool tc_refill(__half* tile, __half* bmat, TcShared* sh, uint32_t& phase,
-                                          uint32_t col[72], bool issue = true) {
+// The barrier that publishes the rows was already passed by the caller (tc_publish).
+__device__ __forceinline__ bool tc_refill_after_publish(__half* tile, __half* bmat, TcShared* sh,
+                                                        uint32_t& phase, uint32_t col[72], bool issue = true) {
   const int tid = threadIdx.x;
-  fence_proxy_async_smem();  // this thread's row writes -> visible to the tensor core
-  tc_fence_before();
-  __syncthreads();
-  tc_fence_after();
   const uint32_t taddr = sh->taddr;
   if (tid == 0 && issue) {
     const uint32_t a0 = smem_addr(tile), b0 = smem_addr(bmat);
@@ -300,6 +301,22 @@ __device__ __forceinline__ bool tc_refill(__half* tile, __half* bmat, TcShared* 
 
 // Release the TMEM columns.  After a timed-out wait (pending), first wait once more,
 // again with a limit, for the MMA that may still be writing them.
+// Publish this thread's row to the tensor core: the fences and the CTA barrier before
+// the MMA; returns whether any thread of the tile still refills.
+__device__ __forceinline__ bool tc_publish(bool mine) {
+  fence_proxy_async_smem();  // this thread's row writes -> visible to the tensor core
+  tc_fence_before();
+  const bool any = __syncthreads_or(mine) != 0;
+  tc_fence_after();
+  return any;
+}
+
+__device__ __forceinline__ bool tc_refill(__half* tile, __half* bmat, TcShared* sh, uint32_t& phase,
+                                          uint32_t col[72], bool issue = true) {
+  tc_publish(true);
+  return tc_refill_after_publish(tile, bmat, sh, phase, col, issue);
+}
+
 __device__ __forceinline__ void tc_teardown(TcShared* sh, bool pending, uint32_t phase) {
   if (pending) (void)mbar_wait_bounded(&sh->bar, phase);
   tc_fence_before();
@@ -372,10 +389,11 @@ __global__ void __launch_bounds__(kTcRows, 4) k_draw_tc(const DrawArgs a, const 
   to_lcg(D, c, X);
   uint32_t phase = 0;
   bool ok = true;
-  while (__syncthreads_or(mine)) {
+  while (true) {
     write_x_row(tile, tid, X);
+    if (!tc_publish(mine)) break;  // every stream of the tile is done
     uint32_t col[72];
-    if (!tc_refill(tile, bmat, sh, phase, col)) {
+    if (!tc_refill_after_publish(tile, bmat, sh, phase, col)) {
       ok = false;
       break;
     }
@@ -448,7 +466,7 @@ __device__ __forceinline__ void emit_head(bool f64, const BatchArgs& b, const ui
     const int d = w - (int)pos;
     if (d < 0 || d % need != 0 || d / need >= h) continue;
     if (f64) {
-      if (w + 1 < kWords) b.out_f64[base + d / 2] = f64_bits_from48(bits48_at_word(D, w));
+      if (w + 1 < kWords) b.out_f64[base + d / 2] = f64_bits_from48_outlined(bits48_at_word(D, w));
     } else {
       b.out_u24[base + d] = word24(D, w);
     }
@@ -508,10 +526,11 @@ __global__ void __launch_bounds__(kTcRows, 4) k_requests_tc(const BatchArgs b, c
   to_lcg(D, c, X);
   uint32_t phase = 0;
   bool ok = true;
-  while (__syncthreads_or(mine)) {
+  while (true) {
     write_x_row(tile, tid, X);
+    if (!tc_publish(mine)) break;  // every chunk of the tile is done
     uint32_t col[72];
-    if (!tc_refill(tile, bmat, sh, phase, col)) {
+    if (!tc_refill_after_publish(tile, bmat, sh, phase, col)) {
       ok = false;
       break;
     }
@@ -549,7 +568,7 @@ __global__ void __launch_bounds__(kTcRows, 4) k_requests_tc(const BatchArgs b, c
         if (f64) {
 #pragma unroll
           for (int j = 0; j < kDoubles; ++j)
-            if (j < rem) b.out_f64[base + k + j] = f64_bits_from48(bits48(D, j));
+            if (j < rem) b.out_f64[base + k + j] = f64_bits_from48_outlined(bits48(D, j));
           pos = (uint32_t)(rem * 2);
         } else {
 #pragma unroll
