@@ -5,10 +5,13 @@
 //   A X = sum_j x_j R_j = sum_k S_k 2^(8k) (mod m),   S_k = sum_j x_j byte_k(R_j),
 // so one refill of a tile of 128 streams is the product of a 128 x 72 byte matrix (the
 // streams' X) with the 72 x 72 byte matrix of the level.  Bytes are exact in fp16, each
-// product is below 2^16 and every partial sum below 72 * 255^2 < 2^23, so fp32
+// product is below 2^16 and every partial sum below 72 * 255^2 + 255 < 2^23, so fp32
 // accumulation is exact.  An extra K row (x_72 = 2048 against 4096) adds 2^23 to every
-// column: the fp32 bit pattern of 2^23 + S is then 0x4B000000 + S, which gives S with
-// one logical AND.  K = 80 and N = 80 after padding (five K = 16 instructions).
+// column, so that the fp32 bit pattern of column k is the integer 0x4B000000 + S_k + e_k.
+// A second one (x_73 = 1 against the bytes e_k of a constant E) cancels those bias
+// terms modulo m: the limb assembly below adds the bit patterns as they are, which
+// leaves the bias C = 0x4B004B000000 sum_t 2^(32t) in the sum, and E = -C mod m.
+// K = 80 and N = 80 after padding (five K = 16 instructions).
 //
 // One CTA owns one tile (128 threads, one stream per thread = one TMEM lane).  Per
 // refill: each thread writes its X as fp16 into the shared A tile, one thread issues
@@ -149,38 +152,36 @@ __device__ __forceinline__ void write_x_row(__half* tile, int row, const uint32_
   }
 }
 
-// Column sums S_0..S_71 (fp32 bits with the 2^23 bias) -> X = sum_k S_k 2^(8k) mod m.
+// Column bit patterns 0x4B000000 + S_k + e_k -> X = sum_k S_k 2^(8k) mod m.
 __device__ __forceinline__ void columns_to_x(const uint32_t col[72], uint32_t X[kLimbs]) {
-  // limb t gathers S_4t + S_4t+1 2^8 + S_4t+2 2^16 + S_4t+3 2^24 (below 2^48) as lo + hi 2^32
+  // Limb t gathers its four columns as w_t = u + 2^16 v (below 2^48, as lo + hi 2^32),
+  // u = col_4t + 2^8 col_4t+1 mod 2^32 = 0x4B000000 + (S + e)_4t + 2^8 (S + e)_4t+1
+  // exactly (2^8 0x4B000000 = 0 mod 2^32 and the rest stays below 2^32), v likewise:
+  // w_t = 0x4B004B000000 + sum_i (S + e)_4t+i 2^(8i), whose bias part E cancels mod m.
   uint32_t lo[kLimbs], hi[kLimbs];
-  // With col = 0x4B000000 + S (B = the bias bits), u = S_4t + 2^8 S_4t+1 is
-  // (col_4t + 2^8 col_4t+1 - 257 B) mod 2^32 exactly, as u < 2^31: one multiply-add on
-  // the FMA pipe and one addition, instead of stripping the bias from each column.
-  constexpr uint32_t kBias257 = 0u - 257u * 0x4B000000u;
 #pragma unroll
   for (int t = 0; t < kLimbs; ++t) {
-    uint32_t u, v;  // both below 2^31
+    uint32_t u, v;  // multiply-adds on the FMA pipe
     asm("mad.lo.u32 %0, %1, 256, %2;" : "=r"(u) : "r"(col[4 * t + 1]), "r"(col[4 * t]));
     asm("mad.lo.u32 %0, %1, 256, %2;" : "=r"(v) : "r"(col[4 * t + 3]), "r"(col[4 * t + 2]));
-    u += kBias257;
-    v += kBias257;
-    const uint64_t w = mad_wide(v, 65536u, (uint64_t)u);  // u + v 2^16 < 2^47
+    const uint64_t w = mad_wide(v, 65536u, (uint64_t)u);
     lo[t] = lo32(w);
     hi[t] = hi32(w);
   }
-  // value = sum_t lo_t 2^(32t) + hi_t 2^(32(t+1)): one carry chain, top limb T < 2^15
+  // value = sum_t lo_t 2^(32t) + hi_t 2^(32(t+1)): one carry chain, top limb T; the
+  // value is S + E + C with S < 2^590.2, E < 2^576 and C = 0x4B004B sum_t 2^(32t + 8),
+  // so 19200 <= T <= 37561
   X[0] = lo[0];
   X[1] = add_cc(lo[1], hi[0]);
 #pragma unroll
   for (int t = 2; t < kLimbs; ++t) X[t] = addc_cc(lo[t], hi[t - 1]);
   const uint32_t T = addc(hi[kLimbs - 1], 0u);
-  // fold: X + T (2^240 - 1).  T (2^240 - 1) = (T - 1) 2^240 + (2^240 - T) for T >= 1:
+  // fold: X + T (2^240 - 1).  T (2^240 - 1) = (T - 1) 2^240 + (2^240 - T) for 1 <= T < 2^16:
   // limb 0 = 2^32 - T, limbs 1..6 all ones, limb 7 = ((T - 1) << 16) | 0xFFFF.
-  const uint32_t nz = T ? 0xFFFFFFFFu : 0u;
   X[0] = add_cc(X[0], 0u - T);
 #pragma unroll
-  for (int k = 1; k < 7; ++k) X[k] = addc_cc(X[k], nz);
-  X[7] = addc_cc(X[7], ((T - 1u) << 16 | 0xFFFFu) & nz);
+  for (int k = 1; k < 7; ++k) X[k] = addc_cc(X[k], 0xFFFFFFFFu);
+  X[7] = addc_cc(X[7], (T - 1u) << 16 | 0xFFFFu);
 #pragma unroll
   for (int k = 8; k < kLimbs; ++k) X[k] = addc_cc(X[k], 0u);
   const uint32_t c = addc(0u, 0u);
@@ -259,8 +260,9 @@ __device__ __forceinline__ void tc_setup(__half* tile, __half* bmat, const __hal
   {
     __half* row9 = tile + tc_off(tid, 72);
     row9[0] = __float2half(2048.f);
+    row9[1] = __float2half(1.f);
 #pragma unroll
-    for (int k = 1; k < 8; ++k) row9[k] = __float2half(0.f);
+    for (int k = 2; k < 8; ++k) row9[k] = __float2half(0.f);
   }
   if (tid == 0) {
     mbar_init(&sh->bar, 1);
@@ -647,10 +649,30 @@ __global__ void k_tc_matrix(const uint32_t* __restrict__ lux, __half* __restrict
     mod_m(P, R);
 #pragma unroll 1
     for (int n = 0; n < kTcN; ++n) bytes[n] = n < 72 ? (uint8_t)(R[n >> 2] >> (8 * (n & 3))) : 0;
+  } else if (j == 73) {
+    // E = -C mod m, C = 0x4B004B000000 sum_{t<18} 2^(32t): limbs 0x4B000000, then
+    // 0x4B004B00 (limbs 1..17) and 0x4B00 (limb 18)
+    uint32_t P[2 * kLimbs];
+#pragma unroll 1
+    for (int q = 0; q < 2 * kLimbs; ++q) P[q] = q == 0 ? 0x4B000000u : (q < kLimbs ? 0x4B004B00u : 0u);
+    P[kLimbs] = 0x4B00u;
+    uint32_t R[kLimbs], E[kLimbs];
+    mod_m(P, R);
+    // E = m - R (R != 0 here; m = 2^576 - 2^240 + 1)
+    uint64_t borrow = 0;
+#pragma unroll 1
+    for (int q = 0; q < kLimbs; ++q) {
+      const uint32_t mq = q == 0 ? 1u : (q < 7 ? 0u : (q == 7 ? 0xFFFF0000u : 0xFFFFFFFFu));
+      const uint64_t d = (uint64_t)mq - R[q] - borrow;
+      E[q] = (uint32_t)d;
+      borrow = (d >> 63) & 1u;
+    }
+#pragma unroll 1
+    for (int n = 0; n < kTcN; ++n) bytes[n] = n < 72 ? (uint8_t)(E[n >> 2] >> (8 * (n & 3))) : 0;
   }
 #pragma unroll 1
   for (int n = 0; n < kTcN; ++n) {
-    float v = j < 72 ? (float)bytes[n] : (j == 72 ? 4096.f : 0.f);
+    const float v = (j < 72 || j == 73) ? (float)bytes[n] : (j == 72 ? 4096.f : 0.f);
     bimg[tc_off(n, j)] = __float2half(v);
   }
 }
