@@ -4,13 +4,16 @@
 // With X = sum_j x_j 2^(8j) (72 bytes) and R_j = A 2^(8j) mod m (72 bytes each),
 //   A X = sum_j x_j R_j = sum_k S_k 2^(8k) (mod m),   S_k = sum_j x_j byte_k(R_j),
 // so one refill of a tile of 128 streams is the product of a 128 x 72 byte matrix (the
-// streams' X) with the 72 x 72 byte matrix of the level.  Bytes are exact in fp16, each
-// product is below 2^16 and every partial sum below 72 * 255^2 + 255 < 2^23, so fp32
-// accumulation is exact.  An extra K row (x_72 = 2048 against 4096) adds 2^23 to every
-// column, so that the fp32 bit pattern of column k is the integer 0x4B000000 + S_k + e_k.
-// A second one (x_73 = 1 against the bytes e_k of a constant E) cancels those bias
-// terms modulo m: the limb assembly below adds the bit patterns as they are, which
-// leaves the bias C = 0x4B004B000000 sum_t 2^(32t) in the sum, and E = -C mod m.
+// streams' X) with the 72 x 72 byte matrix of the level.  A stream's byte b enters as
+// the fp16 subnormal b 2^-24 (its bit pattern is b itself, so writing the row is a byte
+// shuffle), the level's bytes as fp16 integers; each product is b r 2^-24 with
+// b r < 2^16, and every partial sum is a multiple of 2^-24 below
+// (72 * 255^2 + 255) 2^-24 < 1/2, so fp32 accumulation is exact.  An extra K row
+// (x_72 = 2048 against 2^-12) adds 1/2 to every column, so that the fp32 bit pattern of
+// column k is the integer 0x3F000000 + S_k + e_k.  A second one (x_73 = 1 against
+// e_k 2^-24, the bytes of a constant E) cancels those bias terms modulo m: the limb
+// assembly below adds the bit patterns as they are, which leaves the bias
+// C = 0x3F003F000000 sum_t 2^(32t) in the sum, and E = -C mod m.
 // K = 80 and N = 80 after padding (five K = 16 instructions).
 //
 // One CTA owns one tile (128 threads, one stream per thread = one TMEM lane).  Per
@@ -131,33 +134,24 @@ __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.
 
 // ---- per-thread pieces -------------------------------------------------------------
 // X (18 limbs) -> 72 fp16 values (one per byte) in this thread's row of the A tile
-// (chunks 0..8 of the row, 16 bytes each).  (0x6400 | b) is the fp16 1024 + b, exact.
+// (chunks 0..8 of the row, 16 bytes each).  The half with bit pattern b (< 2^10) is the
+// subnormal b 2^-24, exact: each pair of bytes is one byte shuffle with zeros.
 __device__ __forceinline__ void write_x_row(__half* tile, int row, const uint32_t X[kLimbs]) {
-  const __half2 k1024 = __floats2half2_rn(1024.f, 1024.f);
   uint4* base = reinterpret_cast<uint4*>(tile + tc_off(row, 0));
 #pragma unroll
   for (int c = 0; c < 9; ++c) {  // chunk c = bytes 8c .. 8c+7 = limbs 2c, 2c+1
-    uint32_t w[4];
-#pragma unroll
-    for (int h = 0; h < 2; ++h) {
-      const uint32_t L = X[2 * c + h];
-      const uint32_t lo = __byte_perm(L, 0x64646464u, 0x4140u);  // (1024+b0, 1024+b1)
-      const uint32_t hi = __byte_perm(L, 0x64646464u, 0x4342u);  // (1024+b2, 1024+b3)
-      __half2 a = __hsub2(*reinterpret_cast<const __half2*>(&lo), k1024);
-      __half2 b = __hsub2(*reinterpret_cast<const __half2*>(&hi), k1024);
-      w[2 * h] = *reinterpret_cast<uint32_t*>(&a);
-      w[2 * h + 1] = *reinterpret_cast<uint32_t*>(&b);
-    }
-    base[c * (kLBO / 16)] = make_uint4(w[0], w[1], w[2], w[3]);
+    const uint32_t L0 = X[2 * c], L1 = X[2 * c + 1];
+    base[c * (kLBO / 16)] = make_uint4(__byte_perm(L0, 0u, 0x4140u), __byte_perm(L0, 0u, 0x4342u),
+                                       __byte_perm(L1, 0u, 0x4140u), __byte_perm(L1, 0u, 0x4342u));
   }
 }
 
-// Column bit patterns 0x4B000000 + S_k + e_k -> X = sum_k S_k 2^(8k) mod m.
+// Column bit patterns 0x3F000000 + S_k + e_k -> X = sum_k S_k 2^(8k) mod m.
 __device__ __forceinline__ void columns_to_x(const uint32_t col[72], uint32_t X[kLimbs]) {
   // Limb t gathers its four columns as w_t = u + 2^16 v (below 2^48, as lo + hi 2^32),
-  // u = col_4t + 2^8 col_4t+1 mod 2^32 = 0x4B000000 + (S + e)_4t + 2^8 (S + e)_4t+1
-  // exactly (2^8 0x4B000000 = 0 mod 2^32 and the rest stays below 2^32), v likewise:
-  // w_t = 0x4B004B000000 + sum_i (S + e)_4t+i 2^(8i), whose bias part E cancels mod m.
+  // u = col_4t + 2^8 col_4t+1 mod 2^32 = 0x3F000000 + (S + e)_4t + 2^8 (S + e)_4t+1
+  // exactly (2^8 0x3F000000 = 0 mod 2^32 and the rest stays below 2^32), v likewise:
+  // w_t = 0x3F003F000000 + sum_i (S + e)_4t+i 2^(8i), whose bias part E cancels mod m.
   uint32_t lo[kLimbs], hi[kLimbs];
 #pragma unroll
   for (int t = 0; t < kLimbs; ++t) {
@@ -169,8 +163,8 @@ __device__ __forceinline__ void columns_to_x(const uint32_t col[72], uint32_t X[
     hi[t] = hi32(w);
   }
   // value = sum_t lo_t 2^(32t) + hi_t 2^(32(t+1)): one carry chain, top limb T; the
-  // value is S + E + C with S < 2^590.2, E < 2^576 and C = 0x4B004B sum_t 2^(32t + 8),
-  // so 19200 <= T <= 37561
+  // value is S + E + C with S < 2^590.2, E < 2^576 and C = 0x3F003F sum_t 2^(32t + 8),
+  // so 16128 <= T <= 34489
   X[0] = lo[0];
   X[1] = add_cc(lo[1], hi[0]);
 #pragma unroll
@@ -650,12 +644,12 @@ __global__ void k_tc_matrix(const uint32_t* __restrict__ lux, __half* __restrict
 #pragma unroll 1
     for (int n = 0; n < kTcN; ++n) bytes[n] = n < 72 ? (uint8_t)(R[n >> 2] >> (8 * (n & 3))) : 0;
   } else if (j == 73) {
-    // E = -C mod m, C = 0x4B004B000000 sum_{t<18} 2^(32t): limbs 0x4B000000, then
-    // 0x4B004B00 (limbs 1..17) and 0x4B00 (limb 18)
+    // E = -C mod m, C = 0x3F003F000000 sum_{t<18} 2^(32t): limbs 0x3F000000, then
+    // 0x3F003F00 (limbs 1..17) and 0x3F00 (limb 18)
     uint32_t P[2 * kLimbs];
 #pragma unroll 1
-    for (int q = 0; q < 2 * kLimbs; ++q) P[q] = q == 0 ? 0x4B000000u : (q < kLimbs ? 0x4B004B00u : 0u);
-    P[kLimbs] = 0x4B00u;
+    for (int q = 0; q < 2 * kLimbs; ++q) P[q] = q == 0 ? 0x3F000000u : (q < kLimbs ? 0x3F003F00u : 0u);
+    P[kLimbs] = 0x3F00u;
     uint32_t R[kLimbs], E[kLimbs];
     mod_m(P, R);
     // E = m - R (R != 0 here; m = 2^576 - 2^240 + 1)
@@ -672,7 +666,10 @@ __global__ void k_tc_matrix(const uint32_t* __restrict__ lux, __half* __restrict
   }
 #pragma unroll 1
   for (int n = 0; n < kTcN; ++n) {
-    const float v = (j < 72 || j == 73) ? (float)bytes[n] : (j == 72 ? 4096.f : 0.f);
+    // level bytes as integers; 2^-12 (x 2048 = 1/2) for the bias row; e_k 2^-24 (exact
+    // fp16 subnormals) for the correction row
+    const float v = j < 72 ? (float)bytes[n]
+                           : (j == 72 ? 0x1p-12f : (j == 73 ? (float)bytes[n] * 0x1p-24f : 0.f));
     bimg[tc_off(n, j)] = __float2half(v);
   }
 }
