@@ -269,7 +269,7 @@ __device__ __forceinline__ void mod_m(const uint32_t p[2 * kLimbs], uint32_t r[k
 //   T_lo + (q0 + 1)(2^240 - 1) >= 2^576,  T_lo = T mod 2^576,
 // using (q0 + 1) m = (q0 + 1) 2^576 - (q0 + 1)(2^240 - 1).
 // ---------------------------------------------------------------------------------
-__device__ __forceinline__ void to_ranlux(const uint32_t X[kLimbs], uint32_t D[kLimbs]) {
+__device__ __forceinline__ void to_ranlux_full(const uint32_t X[kLimbs], uint32_t D[kLimbs]) {
   // T = (X << 240) - X, 26 limbs
   uint32_t T[26];
   T[0] = sub_cc(0u, X[0]);
@@ -316,6 +316,34 @@ __device__ __forceinline__ void to_ranlux(const uint32_t X[kLimbs], uint32_t D[k
   D[0] = add_cc(X[0], T[18]);
 #pragma unroll
   for (int k = 1; k < 8; ++k) D[k] = addc_cc(X[k], T[18 + k]);
+#pragma unroll
+  for (int k = 8; k < kLimbs - 1; ++k) D[k] = addc_cc(X[k], 0u);
+  D[kLimbs - 1] = addc(X[kLimbs - 1], 0u);
+}
+
+// The same D with the long chain only where it decides anything.  T = X 2^240 - X has
+// T_lo = (S - X) mod 2^576 with S = (X << 240) mod 2^576, and q0 = (X >> 336) - [S < X].
+// The top three limbs of S - X, taken without the borrow from limb 14, settle both
+// [S < X] (their own borrow) and that q = q0 (T_lo is not all ones in limbs 15..17)
+// unless they are all zeros or all ones, about 2^-95 of the inputs; those go through
+// to_ranlux_full.
+__device__ __forceinline__ void to_ranlux(const uint32_t X[kLimbs], uint32_t D[kLimbs]) {
+  const uint32_t t15 = sub_cc(__funnelshift_l(X[7], X[8], 16), X[15]);
+  const uint32_t t16 = subc_cc(__funnelshift_l(X[8], X[9], 16), X[16]);
+  const uint32_t t17 = subc_cc(__funnelshift_l(X[9], X[10], 16), X[17]);
+  const uint32_t borrow = subc(0u, 0u) & 1u;
+  if (__builtin_expect((t15 & t16 & t17) == 0xFFFFFFFFu || (t15 | t16 | t17) == 0u, 0)) {
+    to_ranlux_full(X, D);
+    return;
+  }
+  uint32_t q[8];  // (X >> 336) - borrow, at least 0 (borrow = 1 needs X >= 2^336 here)
+  q[0] = sub_cc(__funnelshift_l(X[10], X[11], 16), borrow);
+#pragma unroll
+  for (int k = 1; k < 7; ++k) q[k] = subc_cc(__funnelshift_l(X[10 + k], X[11 + k], 16), 0u);
+  q[7] = subc(X[17] >> 16, 0u);
+  D[0] = add_cc(X[0], q[0]);
+#pragma unroll
+  for (int k = 1; k < 8; ++k) D[k] = addc_cc(X[k], q[k]);
 #pragma unroll
   for (int k = 8; k < kLimbs - 1; ++k) D[k] = addc_cc(X[k], 0u);
   D[kLimbs - 1] = addc(X[kLimbs - 1], 0u);

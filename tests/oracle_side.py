@@ -71,3 +71,27 @@ class StreamSet:
             rec[i, 9] = int(self.carry[i]) | (int(self.pos[i]) << 32)
             rec[i, 10] = self.p
         return rec
+
+
+def conversion_edge_states(rng, k=40):
+    """LCG states at the corners of the conversion D = floor(2^576 X / m) (Sec. 2.3):
+    X = ceil(q m / (2^240 - 1)) puts X (2^240 - 1) in [q m, q 2^576), where the quotient
+    by m exceeds the quotient by 2^576 by one; and states whose shifted copy
+    (X << 240) mod 2^576 agrees with X in bits 480..575, where comparing the top limbs
+    alone cannot decide the borrow."""
+    M = R.M
+    out = []
+    qs = [1, 2, 3, 2 ** 32, 2 ** 100 + 7, 2 ** 239, 2 ** 240 - 2] + [rng.randrange(1, 2 ** 240 - 1) for _ in range(k)]
+    for q in qs:
+        out.append(-(-q * M // (2 ** 240 - 1)))
+    top = ((1 << 96) - 1) << 480
+    for _ in range(k):
+        X = rng.randrange(1, M)
+        S = (X << 240) % 2 ** 576
+        X2 = (X & ~top) | (S & top)
+        if 0 < X2 < M:
+            out.append(X2)
+        X3 = (X2 - (1 << 480)) % M   # one below in limb 15: the top limbs of S - X all ones
+        if X3:
+            out.append(X3)
+    return [x for x in out if 0 < x < M]

@@ -9,7 +9,7 @@ import numpy as np
 import pytest
 
 from oracle import ranluxpp as R
-from tests.oracle_side import MASK64, from_limbs64, limbs64
+from tests.oracle_side import MASK64, conversion_edge_states, from_limbs64, limbs64
 
 pytestmark = pytest.mark.gpu
 
@@ -100,6 +100,7 @@ def test_mul_mod(native):
 def test_conversions(native):
     rng = random.Random(24)
     xs = [x for x in EDGE_X if 0 < x < M] + [rng.randrange(1, M) for _ in range(5000)]
+    xs += conversion_edge_states(rng)
     n = len(xs)
     d = torch.zeros((n, 9), dtype=torch.int64, device="cuda")
     carry = torch.zeros(n, dtype=torch.int32, device="cuda")

@@ -14,6 +14,7 @@ import pytest
 
 from oracle import ranluxpp as R
 from oracle import swb_lib as S
+from tests.oracle_side import conversion_edge_states
 
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
 
@@ -120,6 +121,8 @@ def test_conversion_round_trip_and_range():
     rng = random.Random(3)
     xs = [1, 2, 3, R.M - 1, R.M - 2, 2 ** 575, 2 ** 576 - 2 ** 240, 2 ** 336, 2 ** 336 - 1,
           2 ** 240, 2 ** 240 - 1] + [rng.randrange(1, R.M) for _ in range(2000)]
+    edges = conversion_edge_states(rng)
+    xs += edges
     for X in xs:
         D, c = R.to_ranlux(X)
         assert c in (0, 1)
@@ -127,6 +130,9 @@ def test_conversion_round_trip_and_range():
         assert R.to_lcg(D, c) == X
         # D / 2^576 approximates X / m from below within 2^-576
         assert D * R.M <= X * 2 ** 576 < (D + 1) * R.M
+    # the corner states include quotients by m one above the quotient by 2^576
+    over = [X for X in edges if R.to_ranlux(X)[0] != X + (X * (2 ** 240 - 1) >> 576)]
+    assert len(over) >= 7
 
 
 def test_conversion_inverts_recurrence_states():
