@@ -28,6 +28,9 @@
 //   (row / 8) * 1280 + (k / 8) * 128 + (row % 8) * 16 + (k % 8) * 2 bytes,
 // i.e. leading-dimension byte offset (between K-adjacent core matrices) 128 and stride
 // byte offset (between 8-row groups) 1280.
+#include <cstring>
+
+#include <cuda.h>  // CUtensorMap (the type only; the map is encoded on the host)
 #include <cuda_fp16.h>
 
 #include "rlxpp_arith.cuh"
@@ -204,9 +207,9 @@ __device__ __forceinline__ void columns_to_x(const uint32_t col[72], uint32_t X[
 struct TcShared {
   uint64_t bar;      // MMA completion
   uint32_t taddr;    // TMEM base
-  int any;           // tile still refilling
+  uint32_t pos0;     // read position of the tile's first stream at entry
 };
-constexpr int kSharedBytes = 64;               // TcShared, padded
+constexpr int kSharedBytes = 128;              // TcShared, padded (keeps the staging 128-byte aligned)
 constexpr int kStageBytes = 96;                // one block of output per thread
 constexpr int kStageOffset = kTileBytes + kBBytes + kSharedBytes;
 
@@ -223,6 +226,30 @@ __device__ __forceinline__ void bulk_store96(void* gdst, uint4* slot, const uint
   asm volatile("cp.async.bulk.commit_group;" ::: "memory");
 }
 __device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_read_all() {
+  asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+}
+
+// A tile-wide store of one block per stream: the staging area holds the 128 threads'
+// 96-byte blocks as a dense [128][96 B] box, which one TMA tensor store writes to rows
+// y .. y + 127 at column x of the output (rows past the stream count and columns past
+// the count per stream are clipped by the tensor map's extents).  One thread issues
+// it after the CTA barrier that follows the writes, and waits for the copy to have
+// read the staging area before the barrier that precedes the next writes.
+struct TileStore {
+  const CUtensorMap* map = nullptr;  // null: no tile-wide stores in this launch
+  uint32_t src = 0;                  // shared address of the staging box
+  int x = 0, y = 0;
+  bool pending = false;              // a written box waits to be stored (thread 0's view)
+};
+__device__ __forceinline__ void tile_store_issue(TileStore& t) {
+  asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%1, %2}], [%3];" ::"l"(
+                   reinterpret_cast<uint64_t>(t.map)),
+               "r"(t.x), "r"(t.y), "r"(t.src)
+               : "memory");
+  asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+  t.pending = false;
+}
 
 template <int Kind>
 __device__ __forceinline__ void block_values(const uint32_t D[kLimbs], uint4 v[6]) {
@@ -273,7 +300,8 @@ __device__ __forceinline__ void tc_setup(__half* tile, __half* bmat, const __hal
 // issue = false leaves the barrier without an arrival (used to test the timeout path).
 // The barrier that publishes the rows was already passed by the caller (tc_publish).
 __device__ __forceinline__ bool tc_refill_after_publish(__half* tile, __half* bmat, TcShared* sh,
-                                                        uint32_t& phase, uint32_t col[72], bool issue = true) {
+                                                        uint32_t& phase, uint32_t col[72], bool issue = true,
+                                                        TileStore* store = nullptr) {
   const int tid = threadIdx.x;
   const uint32_t taddr = sh->taddr;
   if (tid == 0 && issue) {
@@ -283,7 +311,10 @@ __device__ __forceinline__ bool tc_refill_after_publish(__half* tile, __half* bm
       tc_mma(taddr, smem_desc(a0 + s * 2 * kLBO), smem_desc(b0 + s * 2 * kLBO), s > 0 ? 1u : 0u);
     tc_commit(&sh->bar);
   }
+  // the previous refill's blocks, written before the publishing barrier
+  if (store && tid == 0 && store->pending) tile_store_issue(*store);
   const bool ok = mbar_wait_bounded(&sh->bar, phase);
+  if (store && tid == 0) bulk_wait_read_all();  // staging free again after the next barrier
   if (__syncthreads_and(ok) == 0) return false;  // phase stays: the teardown waits on it
   phase ^= 1u;
   tc_fence_after();
@@ -323,7 +354,12 @@ __device__ __forceinline__ void tc_teardown(TcShared* sh, bool pending, uint32_t
 
 // Draw kernel on the tensor path (single-level handles).  Same semantics as k_draw.
 template <int Kind>
-__global__ void __launch_bounds__(kTcRows, 4) k_draw_tc(const DrawArgs a, const __half* __restrict__ bimg) {
+// tmap (when use_tma): the output as a [n][count_each] tensor of 4- or 8-byte elements
+// with a [128][per block] box, for the tile-wide stores of tiles whose streams move in
+// step.
+__global__ void __launch_bounds__(kTcRows, 4)
+    k_draw_tc(const DrawArgs a, const __half* __restrict__ bimg, const __grid_constant__ CUtensorMap tmap,
+              int use_tma) {
   extern __shared__ __align__(1024) unsigned char smem[];
   __half* tile = reinterpret_cast<__half*>(smem);
   __half* bmat = reinterpret_cast<__half*>(smem + kTileBytes);
@@ -367,6 +403,7 @@ __global__ void __launch_bounds__(kTcRows, 4) k_draw_tc(const DrawArgs a, const 
   }
   constexpr int need = (Kind == kDrawU24 || Kind == kDrawF32) ? 1 : 2;
   constexpr int per_block = kWords / need;
+  const uint32_t pos_in = pos;
   int64_t k = 0;
   if (live && cnt > 0 && pos + need <= (uint32_t)kWords) {  // head of the current block
     const int64_t room = (kWords - pos) / need;
@@ -383,13 +420,29 @@ __global__ void __launch_bounds__(kTcRows, 4) k_draw_tc(const DrawArgs a, const 
   bool refilled = false;
   uint32_t X[kLimbs];
   to_lcg(D, c, X);
+  // Tile-wide stores when every live stream of the tile starts at the tile's first
+  // position (then, with one count for all, they stay in step) and the first column
+  // after the head is 16-byte aligned.  Thread 0 (always live) decides for the tile.
+  TileStore store;
+  bool tma = false;
+  if constexpr (Kind != kDrawSumHist) {
+    if (use_tma) {  // uniform over the grid
+      if (tid == 0) sh->pos0 = pos_in;
+      __syncthreads();
+      const bool same = !live || (pos_in == sh->pos0 && ((k * (int64_t)(need * 4)) & 15) == 0);
+      tma = __syncthreads_and(same) != 0;
+      store.map = &tmap;
+      store.src = smem_addr(smem + kStageOffset);
+      store.y = (int)(blockIdx.x * kTcRows);
+    }
+  }
   uint32_t phase = 0;
   bool ok = true;
   while (true) {
     write_x_row(tile, tid, X);
     if (!tc_publish(mine)) break;  // every stream of the tile is done
     uint32_t col[72];
-    if (!tc_refill_after_publish(tile, bmat, sh, phase, col)) {
+    if (!tc_refill_after_publish(tile, bmat, sh, phase, col, true, tma ? &store : nullptr)) {
       ok = false;
       break;
     }
@@ -401,7 +454,24 @@ __global__ void __launch_bounds__(kTcRows, 4) k_draw_tc(const DrawArgs a, const 
       to_ranlux(X, D);
       refilled = true;
       const int64_t rem = cnt - k;
-      if (rem >= per_block) {
+      if (tma) {
+        // the whole block into this thread's row of the staging box; past the count
+        // the box is clipped
+        uint4 v[6];
+        block_values<Kind>(D, v);
+#pragma unroll
+        for (int q = 0; q < 6; ++q) slot[q] = v[q];
+        fence_proxy_async_smem();
+        store.x = (int)k;
+        store.pending = true;
+        if (rem >= per_block) {
+          k += per_block;
+          pos = kWords;
+        } else {
+          k = cnt;
+          pos = (uint32_t)(rem * need);
+        }
+      } else if (rem >= per_block) {
         if constexpr (Kind == kDrawSumHist) {
           out.block(D, base + k);
         } else {
@@ -424,6 +494,7 @@ __global__ void __launch_bounds__(kTcRows, 4) k_draw_tc(const DrawArgs a, const 
       mine = k < cnt;
     }
   }
+  if (tma && tid == 0 && store.pending) tile_store_issue(store);  // the last blocks
   if (Kind != kDrawSumHist) bulk_wait_all();  // this thread's output copies are done
   if (!ok) {
     if (tid == 0) atomicCAS(s.status, 0, (int)RLXPP_ERR_TIMEOUT);
@@ -680,12 +751,57 @@ __global__ void k_tc_matrix(const uint32_t* __restrict__ lux, __half* __restrict
 constexpr size_t kTcSmem = 48 * 1024;
 static_assert(kStageOffset + kTcRows * kStageBytes <= (int)kTcSmem, "shared memory layout");
 
+// cuTensorMapEncodeTiled from the driver, looked up once (null if unavailable).
+using EncodeTiledFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                   const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+EncodeTiledFn encode_tiled_fn() {
+  static const EncodeTiledFn fn = [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess)
+      p = nullptr;
+    return reinterpret_cast<EncodeTiledFn>(p);
+  }();
+  return fn;
+}
+
+// The output of a draw with one count for every stream as a [n][count_each] tensor with a
+// [128][per block] box, when the TMA can address it: 16-byte aligned base and row
+// stride, and coordinates within 32 bits.  Returns false otherwise (the kernel then
+// writes each stream's blocks by itself).
+template <int Kind>
+bool encode_output_map(const DrawArgs& a, CUtensorMap* map) {
+  constexpr uint64_t esize = Kind == kDrawF64 ? 8 : 4;
+  constexpr uint32_t per_block = Kind == kDrawF64 ? kDoubles : kWords;
+  if (a.counts != nullptr || a.count_each <= 0 || a.s.n == 0) return false;
+  const uint64_t cols = (uint64_t)a.count_each, rows = a.s.n;
+  if (cols > 0x7FFFFFFFull || rows > 0x7FFFFFFFull) return false;
+  if ((reinterpret_cast<uintptr_t>(a.out) & 15) != 0 || ((cols * esize) & 15) != 0) return false;
+  if (cols * esize >= (1ull << 40)) return false;
+  const EncodeTiledFn enc = encode_tiled_fn();
+  if (!enc) return false;
+  const cuuint64_t dims[2] = {cols, rows};
+  const cuuint64_t strides[1] = {cols * esize};
+  const cuuint32_t box[2] = {per_block, (cuuint32_t)kTcRows};
+  const cuuint32_t estr[2] = {1, 1};
+  const CUresult r = enc(map, esize == 8 ? CU_TENSOR_MAP_DATA_TYPE_UINT64 : CU_TENSOR_MAP_DATA_TYPE_UINT32, 2, a.out,
+                         dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                         CU_TENSOR_MAP_L2_PROMOTION_NONE, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
 template <int Kind>
 cudaError_t launch_tc_kind(const DrawArgs& a, const __half* bimg, cudaStream_t st) {
   cudaError_t e = cudaFuncSetAttribute(k_draw_tc<Kind>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTcSmem);
   if (e != cudaSuccess) return e;
   const unsigned grid = (unsigned)((a.s.n + kTcRows - 1) / kTcRows);
-  k_draw_tc<Kind><<<grid, kTcRows, kTcSmem, st>>>(a, bimg);
+  CUtensorMap map;
+  std::memset(&map, 0, sizeof(map));
+  int use_tma = 0;
+  if constexpr (Kind != kDrawSumHist) use_tma = encode_output_map<Kind>(a, &map) ? 1 : 0;
+  k_draw_tc<Kind><<<grid, kTcRows, kTcSmem, st>>>(a, bimg, map, use_tma);
   return cudaGetLastError();
 }
 

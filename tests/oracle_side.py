@@ -56,6 +56,16 @@ class StreamSet:
     def draw(self, count, kind):
         return S.draw_many(self.words, self.carry, self.pos, self.p, count, kind)
 
+    def draw_ragged(self, counts, kind):
+        """counts[i] values from stream i (in place, one stream at a time); a list of arrays."""
+        out = []
+        for i in range(self.words.shape[0]):
+            one = StreamSet.__new__(StreamSet)
+            one.p = self.p
+            one.words, one.carry, one.pos = self.words[i:i + 1], self.carry[i:i + 1], self.pos[i:i + 1]
+            out.append(one.draw(int(counts[i]), kind)[0])
+        return out
+
     def sum_hist(self, count):
         return S.sum_hist_many(self.words, self.carry, self.pos, self.p, count)
 

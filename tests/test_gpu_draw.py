@@ -120,6 +120,47 @@ def test_mixed_types_odd_positions(native, path):
     assert_states(native, g, ref)
 
 
+def _draw(native, g, kind, count, n):
+    dt = {S.KIND_U24: torch.int32, S.KIND_F64: torch.float64, S.KIND_F32: torch.float32}[kind]
+    out = torch.full((n, max(count, 1)), -1, dtype=dt, device="cuda")
+    {S.KIND_U24: g.draw_u24, S.KIND_F64: g.draw_f64, S.KIND_F32: g.draw_f32}[kind](out, count)
+    a = out.cpu().numpy()[:, :count]
+    return a.view(np.uint64) if kind == S.KIND_F64 else a.view(np.uint32)
+
+
+def _want(ref, kind, count):
+    w = ref.draw(count, kind)
+    return w.view(np.uint64) if kind == S.KIND_F64 else w.view(np.uint32)
+
+
+def test_tile_stores_heads_and_tails(native, path):
+    """Uniform draws whose blocks go out as one store per tile when the tile's streams
+    move in step: fresh blocks, heads that keep the first column 16-byte aligned and
+    heads that do not, counts whose row length is or is not a multiple of 16 bytes,
+    ragged last blocks and a ragged last tile; then positions that differ within a
+    tile (a ragged draw first)."""
+    seeds = W.random_seeds(N, 91)
+    g = make(native, seeds, levels=(389,), path=path)
+    ref = StreamSet.from_seeds(seeds, 389)
+    steps = [(S.KIND_F64, 996), (S.KIND_U24, 4), (S.KIND_F64, 1000), (S.KIND_U24, 2), (S.KIND_F64, 998),
+             (S.KIND_F32, 100), (S.KIND_U24, 3), (S.KIND_F32, 1001), (S.KIND_F32, 96), (S.KIND_U24, 1),
+             (S.KIND_F64, 26), (S.KIND_U24, 500), (S.KIND_F64, 1002)]
+    for kind, count in steps:
+        assert np.array_equal(_draw(native, g, kind, count, N), _want(ref, kind, count)), (kind, count)
+    assert_states(native, g, ref)
+    # streams at different positions inside each tile, then uniform draws again
+    counts, offsets = W.ragged_counts(N, 30, seed=92)
+    out = torch.zeros(int(counts.sum()) + 1, dtype=torch.int32, device="cuda")
+    g.draw_u24(out, 0, torch.from_numpy(counts).cuda(), torch.from_numpy(offsets).cuda())
+    got = out.cpu().numpy().view(np.uint32)
+    for i, w in enumerate(ref.draw_ragged(counts, S.KIND_U24)):
+        assert np.array_equal(got[offsets[i]:offsets[i] + counts[i]], w), i
+    for kind, count in [(S.KIND_F64, 1000), (S.KIND_U24, 96), (S.KIND_F32, 48)]:
+        assert np.array_equal(_draw(native, g, kind, count, N), _want(ref, kind, count)), (kind, count)
+    assert_states(native, g, ref)
+    g.close()
+
+
 @pytest.mark.parametrize("kind", [S.KIND_U24, S.KIND_F64])
 def test_ragged_counts_offsets(native, kind, path):
     seeds = W.random_seeds(N, 51)
