@@ -45,7 +45,6 @@ namespace {
 constexpr int kTcRows = 128;                 // streams per tile = TMEM lanes = M
 constexpr int kTcK = 80;                     // 72 bytes + bias + padding
 constexpr int kTcN = 80;                     // 72 output columns + padding
-constexpr int kTcCols = 128;                 // TMEM columns allocated (power of two >= N)
 constexpr int kTileBytes = kTcRows * kTcK * 2;   // 20480
 constexpr int kBBytes = kTcN * kTcK * 2;         // 12800
 constexpr int kLBO = 128, kSBO = 1280;
@@ -206,12 +205,76 @@ __device__ __forceinline__ void columns_to_x(const uint32_t col[72], uint32_t X[
 
 struct TcShared {
   uint64_t bar;      // MMA completion
-  uint32_t taddr;    // TMEM base
+  uint32_t taddr;    // TMEM base (group 0's copy is the CTA's)
   uint32_t pos0;     // read position of the tile's first stream at entry
 };
 constexpr int kSharedBytes = 128;              // TcShared, padded (keeps the staging 128-byte aligned)
 constexpr int kStageBytes = 96;                // one block of output per thread
-constexpr int kStageOffset = kTileBytes + kBBytes + kSharedBytes;
+
+// Shared memory of a CTA of T tile-groups (128 threads and one tile each): the level's
+// matrix once, then per group its A tile, its TcShared and, for kernels that write
+// values, its [128][96 B] output staging box.  Groups start on 1 KB boundaries.
+constexpr int kBRegion = 13 * 1024;                          // kBBytes rounded up
+constexpr int kGroupStage = kTileBytes + kSharedBytes;       // 20608, a multiple of 128
+constexpr int kGroupBytesOut = 33 * 1024;                    // >= kGroupStage + 128 * 96
+constexpr int kGroupBytesNoOut = 21 * 1024;                  // >= kGroupStage
+static_assert(kBRegion >= kBBytes && kGroupBytesOut >= kGroupStage + kTcRows * kStageBytes &&
+                  kGroupBytesNoOut >= kGroupStage && kGroupStage % 128 == 0,
+              "shared memory layout");
+__host__ __device__ constexpr int tc_smem_bytes(int groups, bool staging) {
+  return kBRegion + groups * (staging ? kGroupBytesOut : kGroupBytesNoOut);
+}
+// TMEM: one allocation per CTA; group g's 80 accumulator columns start at column 96 g
+// (a multiple of the 32-column allocation unit), so five groups fit in 512 columns.
+constexpr int kGroupCols = 96;
+__host__ __device__ constexpr uint32_t tc_alloc_cols(int groups) { return groups == 1 ? 128u : 512u; }
+static_assert(4 * kGroupCols + kTcN <= 512, "five groups' accumulators in 512 TMEM columns");
+
+// This thread's tile-group: group index g (barrier g + 1), row t of the group's tile.
+// The group's lead thread (lane 0 of its warp g mod 4) issues its MMAs, so that the
+// groups' issuing warps sit on different SM sub-partitions; tile-wide stores are issued
+// by row 0, which is live whenever any row of the tile is.
+struct TcGroup {
+  int g, t, lead;
+  __half* tile;
+  TcShared* sh;
+  unsigned char* stage;  // the group's staging box (kernels that write values)
+};
+__device__ __forceinline__ TcGroup tc_group(unsigned char* smem, bool staging) {
+  TcGroup G;
+  G.g = threadIdx.x / kTcRows;
+  G.t = threadIdx.x % kTcRows;
+  G.lead = (G.g % 4) * 32;
+  unsigned char* base = smem + kBRegion + G.g * (staging ? kGroupBytesOut : kGroupBytesNoOut);
+  G.tile = reinterpret_cast<__half*>(base);
+  G.sh = reinterpret_cast<TcShared*>(base + kTileBytes);
+  G.stage = base + kGroupStage;
+  return G;
+}
+__device__ __forceinline__ __half* tc_bmat(unsigned char* smem) { return reinterpret_cast<__half*>(smem); }
+
+// Barriers of one group (128 threads, warp-uniform): named barrier g + 1.
+__device__ __forceinline__ void group_sync(const TcGroup& G) {
+  asm volatile("bar.sync %0, 128;" ::"r"(G.g + 1) : "memory");
+}
+__device__ __forceinline__ bool group_or(const TcGroup& G, bool p) {
+  uint32_t r;
+  asm volatile(
+      "{\n .reg .pred a, b;\n setp.ne.u32 a, %1, 0;\n bar.red.or.pred b, %2, 128, a;\n selp.u32 %0, 1, 0, b;\n}"
+      : "=r"(r)
+      : "r"((uint32_t)p), "r"(G.g + 1)
+      : "memory");
+  return r != 0;
+}
+__device__ __forceinline__ bool group_and(const TcGroup& G, bool p) {
+  uint32_t r;
+  asm volatile(
+      "{\n .reg .pred a, b;\n setp.ne.u32 a, %1, 0;\n bar.red.and.pred b, %2, 128, a;\n selp.u32 %0, 1, 0, b;\n}"
+      : "=r"(r)
+      : "r"((uint32_t)p), "r"(G.g + 1)
+      : "memory");
+  return r != 0;
+}
 
 // A full block of output (12 doubles or 24 numbers, 96 bytes) from this thread's
 // staging slot to global memory by one bulk copy (the TMA engine writes it), after the
@@ -271,54 +334,76 @@ __device__ __forceinline__ void block_values(const uint32_t D[kLimbs], uint4 v[6
   }
 }
 
-// Setup per tile: the level's matrix into shared memory, the constant chunk 9 of every
-// row (bias 2048 at k = 72, zeros after it), the mbarrier and the TMEM columns.
-__device__ __forceinline__ void tc_setup(__half* tile, __half* bmat, const __half* __restrict__ bimg, TcShared* sh) {
+// Group 0's TcShared: its taddr is the CTA's TMEM base.
+__device__ __forceinline__ TcShared* tc_sh0(unsigned char* smem) {
+  return reinterpret_cast<TcShared*>(smem + kBRegion + kTileBytes);
+}
+
+// Setup of a CTA of `groups` tile-groups: the level's matrix into shared memory, the
+// constant chunk 9 of every tile row (2048 and 1 at k = 72, 73, zeros after), one
+// mbarrier per group and the CTA's TMEM columns.  Ends with a CTA barrier.
+__device__ __forceinline__ void tc_setup(unsigned char* smem, const TcGroup& G, const __half* __restrict__ bimg,
+                                         int groups) {
   const int tid = threadIdx.x;
   const uint4* src = reinterpret_cast<const uint4*>(bimg);
-  uint4* dst = reinterpret_cast<uint4*>(bmat);
-  for (int i = tid; i < kBBytes / 16; i += kTcRows) dst[i] = src[i];
+  uint4* dst = reinterpret_cast<uint4*>(tc_bmat(smem));
+  for (int i = tid; i < kBBytes / 16; i += groups * kTcRows) dst[i] = src[i];
   {
-    __half* row9 = tile + tc_off(tid, 72);
+    __half* row9 = G.tile + tc_off(G.t, 72);
     row9[0] = __float2half(2048.f);
     row9[1] = __float2half(1.f);
 #pragma unroll
     for (int k = 2; k < 8; ++k) row9[k] = __float2half(0.f);
   }
-  if (tid == 0) {
-    mbar_init(&sh->bar, 1);
+  if (G.t == G.lead) {
+    mbar_init(&G.sh->bar, 1);
     fence_barrier_init();
   }
-  if (tid < 32) tmem_alloc(&sh->taddr, kTcCols);
+  if (tid < 32) tmem_alloc(&tc_sh0(smem)->taddr, tc_alloc_cols(groups));
   fence_proxy_async_smem();
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
 }
 
-// One refill of the whole tile: rows already written; returns false on a wait timeout.
-// issue = false leaves the barrier without an arrival (used to test the timeout path).
-// The barrier that publishes the rows was already passed by the caller (tc_publish).
-__device__ __forceinline__ bool tc_refill_after_publish(__half* tile, __half* bmat, TcShared* sh,
+// TMEM address of the group's accumulator (lane 0, its first column).
+__device__ __forceinline__ uint32_t tc_tmem(unsigned char* smem, const TcGroup& G) {
+  return tc_sh0(smem)->taddr + (uint32_t)(G.g * kGroupCols);
+}
+
+// Publish this thread's row to the tensor core: the fences and the group's barrier
+// before the MMA; returns whether any thread of the group's tile still refills.
+__device__ __forceinline__ bool tc_publish(const TcGroup& G, bool mine) {
+  fence_proxy_async_smem();  // this thread's row writes -> visible to the tensor core
+  tc_fence_before();
+  const bool any = group_or(G, mine);
+  tc_fence_after();
+  return any;
+}
+
+// One refill of the group's tile, its rows published (tc_publish); returns false on a
+// wait timeout.  issue = false leaves the barrier without an arrival (used to test the
+// timeout path).  With a store, the group's first thread also issues the pending
+// tile-wide store behind the MMA and waits for it to have read the staging box.
+__device__ __forceinline__ bool tc_refill_after_publish(const TcGroup& G, const __half* bmat, uint32_t taddr,
                                                         uint32_t& phase, uint32_t col[72], bool issue = true,
                                                         TileStore* store = nullptr) {
-  const int tid = threadIdx.x;
-  const uint32_t taddr = sh->taddr;
-  if (tid == 0 && issue) {
-    const uint32_t a0 = smem_addr(tile), b0 = smem_addr(bmat);
+  if (G.t == G.lead && issue) {
+    const uint32_t a0 = smem_addr(G.tile), b0 = smem_addr(bmat);
 #pragma unroll
     for (int s = 0; s < kTcK / 16; ++s)  // K = 16 per instruction: two core matrices
       tc_mma(taddr, smem_desc(a0 + s * 2 * kLBO), smem_desc(b0 + s * 2 * kLBO), s > 0 ? 1u : 0u);
-    tc_commit(&sh->bar);
+    tc_commit(&G.sh->bar);
   }
   // the previous refill's blocks, written before the publishing barrier
-  if (store && tid == 0 && store->pending) tile_store_issue(*store);
-  const bool ok = mbar_wait_bounded(&sh->bar, phase);
-  if (store && tid == 0) bulk_wait_read_all();  // staging free again after the next barrier
-  if (__syncthreads_and(ok) == 0) return false;  // phase stays: the teardown waits on it
+  if (store && G.t == 0 && store->pending) tile_store_issue(*store);
+  const bool ok = mbar_wait_bounded(&G.sh->bar, phase);
+  if (store && G.t == 0) bulk_wait_read_all();  // staging free again after the next barrier
+  if (!group_and(G, ok)) return false;           // phase stays: the teardown waits on it
   phase ^= 1u;
   tc_fence_after();
-  const uint32_t lane_addr = taddr + ((uint32_t)((tid / 32) * 32) << 16);
+  // warp (t / 32) of the group reads TMEM lanes 32 (t / 32) .. + 31, its rows
+  const uint32_t lane_addr = taddr + ((uint32_t)((G.t / 32) * 32) << 16);
 #pragma unroll
   for (int q = 0; q < 4; ++q) tmem_ld16(lane_addr + 16 * q, col + 16 * q);
   tmem_ld8(lane_addr + 64, col + 64);
@@ -326,53 +411,48 @@ __device__ __forceinline__ bool tc_refill_after_publish(__half* tile, __half* bm
   return true;
 }
 
-// Release the TMEM columns.  After a timed-out wait (pending), first wait once more,
-// again with a limit, for the MMA that may still be writing them.
-// Publish this thread's row to the tensor core: the fences and the CTA barrier before
-// the MMA; returns whether any thread of the tile still refills.
-__device__ __forceinline__ bool tc_publish(bool mine) {
-  fence_proxy_async_smem();  // this thread's row writes -> visible to the tensor core
-  tc_fence_before();
-  const bool any = __syncthreads_or(mine) != 0;
-  tc_fence_after();
-  return any;
-}
-
-__device__ __forceinline__ bool tc_refill(__half* tile, __half* bmat, TcShared* sh, uint32_t& phase,
+__device__ __forceinline__ bool tc_refill(const TcGroup& G, const __half* bmat, uint32_t taddr, uint32_t& phase,
                                           uint32_t col[72], bool issue = true) {
-  tc_publish(true);
-  return tc_refill_after_publish(tile, bmat, sh, phase, col, issue);
+  tc_publish(G, true);
+  return tc_refill_after_publish(G, bmat, taddr, phase, col, issue);
 }
 
-__device__ __forceinline__ void tc_teardown(TcShared* sh, bool pending, uint32_t phase) {
-  if (pending) (void)mbar_wait_bounded(&sh->bar, phase);
+// Release the CTA's TMEM columns.  After a timed-out wait (pending), first wait once
+// more, again with a limit, for the MMA that may still be writing them.  Every thread
+// of the CTA calls it.
+__device__ __forceinline__ void tc_teardown(unsigned char* smem, const TcGroup& G, bool pending, uint32_t phase,
+                                            int groups) {
+  if (pending) (void)mbar_wait_bounded(&G.sh->bar, phase);
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
-  if (threadIdx.x < 32) tmem_dealloc(sh->taddr, kTcCols);
+  if (threadIdx.x < 32) tmem_dealloc(tc_sh0(smem)->taddr, tc_alloc_cols(groups));
 }
 
 // Draw kernel on the tensor path (single-level handles).  Same semantics as k_draw.
-template <int Kind>
-// tmap (when use_tma): the output as a [n][count_each] tensor of 4- or 8-byte elements
-// with a [128][per block] box, for the tile-wide stores of tiles whose streams move in
-// step.
-__global__ void __launch_bounds__(kTcRows, 4)
+// A CTA holds T tile-groups (one SM's worth), each refilling its own tile of 128
+// streams independently of the others.  tmap (when use_tma): the output as a
+// [n][count_each] tensor of 4- or 8-byte elements with a [128][per block] box, for the
+// tile-wide stores of tiles whose streams move in step.
+template <int Kind, int T>
+__global__ void __launch_bounds__(kTcRows* T, T == 1 ? 4 : 1)
     k_draw_tc(const DrawArgs a, const __half* __restrict__ bimg, const __grid_constant__ CUtensorMap tmap,
               int use_tma) {
   extern __shared__ __align__(1024) unsigned char smem[];
-  __half* tile = reinterpret_cast<__half*>(smem);
-  __half* bmat = reinterpret_cast<__half*>(smem + kTileBytes);
-  TcShared* sh = reinterpret_cast<TcShared*>(smem + kTileBytes + kBBytes);
-  uint4* slot = reinterpret_cast<uint4*>(smem + kStageOffset + threadIdx.x * kStageBytes);
-  __shared__ unsigned int hist_s[Kind == kDrawSumHist ? 4 * 256 : 1];
+  constexpr bool kStaging = Kind != kDrawSumHist;
+  const TcGroup G = tc_group(smem, kStaging);
+  const __half* bmat = tc_bmat(smem);
+  uint4* slot = reinterpret_cast<uint4*>(G.stage + G.t * kStageBytes);
+  __shared__ unsigned int hist_s[Kind == kDrawSumHist ? 4 * T * 256 : 1];  // one histogram per warp
   const int tid = threadIdx.x;
   if (Kind == kDrawSumHist)
-    for (int t = tid; t < 4 * 256; t += kTcRows) hist_s[t] = 0;
-  tc_setup(tile, bmat, bimg, sh);
+    for (int t = tid; t < 4 * T * 256; t += kTcRows * T) hist_s[t] = 0;
+  tc_setup(smem, G, bimg, T);
+  const uint32_t taddr = tc_tmem(smem, G);
 
   const StateView& s = a.s;
-  const uint64_t i = (uint64_t)blockIdx.x * kTcRows + tid;
+  const uint64_t tile_idx = (uint64_t)blockIdx.x * T + G.g;
+  const uint64_t i = tile_idx * kTcRows + G.t;
   const bool live = i < s.n;
   int64_t cnt = 0, base = 0;
   uint32_t pos = kWords, c = 0, lvl = 0;
@@ -422,27 +502,28 @@ __global__ void __launch_bounds__(kTcRows, 4)
   to_lcg(D, c, X);
   // Tile-wide stores when every live stream of the tile starts at the tile's first
   // position (then, with one count for all, they stay in step) and the first column
-  // after the head is 16-byte aligned.  Thread 0 (always live) decides for the tile.
+  // after the head is 16-byte aligned.  The group's thread 0 decides for the tile (it
+  // is live whenever any thread of the group is).
   TileStore store;
   bool tma = false;
   if constexpr (Kind != kDrawSumHist) {
     if (use_tma) {  // uniform over the grid
-      if (tid == 0) sh->pos0 = pos_in;
-      __syncthreads();
-      const bool same = !live || (pos_in == sh->pos0 && ((k * (int64_t)(need * 4)) & 15) == 0);
-      tma = __syncthreads_and(same) != 0;
+      if (G.t == 0) G.sh->pos0 = pos_in;
+      group_sync(G);
+      const bool same = !live || (pos_in == G.sh->pos0 && ((k * (int64_t)(need * 4)) & 15) == 0);
+      tma = group_and(G, same);
       store.map = &tmap;
-      store.src = smem_addr(smem + kStageOffset);
-      store.y = (int)(blockIdx.x * kTcRows);
+      store.src = smem_addr(G.stage);
+      store.y = (int)(tile_idx * kTcRows);
     }
   }
   uint32_t phase = 0;
   bool ok = true;
   while (true) {
-    write_x_row(tile, tid, X);
-    if (!tc_publish(mine)) break;  // every stream of the tile is done
+    write_x_row(G.tile, G.t, X);
+    if (!tc_publish(G, mine)) break;  // every stream of the tile is done
     uint32_t col[72];
-    if (!tc_refill_after_publish(tile, bmat, sh, phase, col, true, tma ? &store : nullptr)) {
+    if (!tc_refill_after_publish(G, bmat, taddr, phase, col, true, tma ? &store : nullptr)) {
       ok = false;
       break;
     }
@@ -494,10 +575,10 @@ __global__ void __launch_bounds__(kTcRows, 4)
       mine = k < cnt;
     }
   }
-  if (tma && tid == 0 && store.pending) tile_store_issue(store);  // the last blocks
+  if (tma && G.t == 0 && store.pending) tile_store_issue(store);  // the last blocks
   if (Kind != kDrawSumHist) bulk_wait_all();  // this thread's output copies are done
   if (!ok) {
-    if (tid == 0) atomicCAS(s.status, 0, (int)RLXPP_ERR_TIMEOUT);
+    if (G.t == 0) atomicCAS(s.status, 0, (int)RLXPP_ERR_TIMEOUT);
   } else if (live) {
     if (refilled) {
       c = carry_of(X, D);
@@ -509,13 +590,12 @@ __global__ void __launch_bounds__(kTcRows, 4)
       if (sums) sums[i] = a.accumulate_sums ? sums[i] + out.sum : out.sum;
     }
   }
-  tc_teardown(sh, !ok, phase);
-  if (Kind == kDrawSumHist && ok) {
-    __syncthreads();
-    for (int t = tid; t < 256; t += kTcRows) {
+  tc_teardown(smem, G, !ok, phase, T);  // ends with a CTA barrier: the histograms are complete
+  if constexpr (Kind == kDrawSumHist) {
+    for (int t = tid; t < 256; t += kTcRows * T) {
       unsigned long long tot = 0;
 #pragma unroll
-      for (int w = 0; w < 4; ++w) tot += hist_s[w * 256 + t];
+      for (int w = 0; w < 4 * T; ++w) tot += hist_s[w * 256 + t];
       if (tot) atomicAdd(a.hist + t, tot);
     }
   }
@@ -550,12 +630,12 @@ __device__ __forceinline__ void emit_head(bool f64, const BatchArgs& b, const ui
 __global__ void __launch_bounds__(kTcRows, 4) k_requests_tc(const BatchArgs b, const Item* __restrict__ items,
                                                             uint64_t n_items, const __half* __restrict__ bimg) {
   extern __shared__ __align__(1024) unsigned char smem[];
-  __half* tile = reinterpret_cast<__half*>(smem);
-  __half* bmat = reinterpret_cast<__half*>(smem + kTileBytes);
-  TcShared* sh = reinterpret_cast<TcShared*>(smem + kTileBytes + kBBytes);
-  uint4* slot = reinterpret_cast<uint4*>(smem + kStageOffset + threadIdx.x * kStageBytes);
+  const TcGroup G = tc_group(smem, true);  // one group per CTA
+  const __half* bmat = tc_bmat(smem);
+  uint4* slot = reinterpret_cast<uint4*>(G.stage + G.t * kStageBytes);
   const int tid = threadIdx.x;
-  tc_setup(tile, bmat, bimg, sh);
+  tc_setup(smem, G, bimg, 1);
+  const uint32_t taddr = tc_tmem(smem, G);
   const uint64_t idx = (uint64_t)blockIdx.x * kTcRows + tid;
   const bool live = idx < n_items;
   Item it{};
@@ -594,10 +674,10 @@ __global__ void __launch_bounds__(kTcRows, 4) k_requests_tc(const BatchArgs b, c
   uint32_t phase = 0;
   bool ok = true;
   while (true) {
-    write_x_row(tile, tid, X);
-    if (!tc_publish(mine)) break;  // every chunk of the tile is done
+    write_x_row(G.tile, G.t, X);
+    if (!tc_publish(G, mine)) break;  // every chunk of the tile is done
     uint32_t col[72];
-    if (!tc_refill_after_publish(tile, bmat, sh, phase, col)) {
+    if (!tc_refill_after_publish(G, bmat, taddr, phase, col)) {
       ok = false;
       break;
     }
@@ -658,7 +738,7 @@ __global__ void __launch_bounds__(kTcRows, 4) k_requests_tc(const BatchArgs b, c
     for (int q = 0; q < 9; ++q) b.s.D[(uint64_t)q * b.s.stride + st] = ((uint64_t)D[2 * q + 1] << 32) | D[2 * q];
     b.s.meta[st] = meta_pack(pos, c, lvl);
   }
-  tc_teardown(sh, !ok, phase);
+  tc_teardown(smem, G, !ok, phase, 1);
 }
 
 // One tensor-path product per item: out = A x mod m (x < m), for testing.  With
@@ -667,10 +747,9 @@ __global__ void __launch_bounds__(kTcRows, 4) k_requests_tc(const BatchArgs b, c
 __global__ void __launch_bounds__(kTcRows, 4) k_tc_mulmod(const __half* __restrict__ bimg, const uint64_t* x,
                                                           uint64_t* out, uint64_t n, int* status, int issue) {
   extern __shared__ __align__(1024) unsigned char smem[];
-  __half* tile = reinterpret_cast<__half*>(smem);
-  __half* bmat = reinterpret_cast<__half*>(smem + kTileBytes);
-  TcShared* sh = reinterpret_cast<TcShared*>(smem + kTileBytes + kBBytes);
-  tc_setup(tile, bmat, bimg, sh);
+  const TcGroup G = tc_group(smem, false);  // one group per CTA
+  tc_setup(smem, G, bimg, 1);
+  const uint32_t taddr = tc_tmem(smem, G);
   const uint64_t i = (uint64_t)blockIdx.x * kTcRows + threadIdx.x;
   uint32_t X[kLimbs];
 #pragma unroll
@@ -679,9 +758,9 @@ __global__ void __launch_bounds__(kTcRows, 4) k_tc_mulmod(const __half* __restri
     X[2 * k] = (uint32_t)v;
     X[2 * k + 1] = (uint32_t)(v >> 32);
   }
-  write_x_row(tile, threadIdx.x, X);
+  write_x_row(G.tile, G.t, X);
   uint32_t col[72], phase = 0;
-  const bool ok = tc_refill(tile, bmat, sh, phase, col, issue != 0);
+  const bool ok = tc_refill(G, tc_bmat(smem), taddr, phase, col, issue != 0);
   if (ok) {
     columns_to_x(col, X);
     if (i < n)
@@ -690,7 +769,7 @@ __global__ void __launch_bounds__(kTcRows, 4) k_tc_mulmod(const __half* __restri
   } else if (threadIdx.x == 0) {
     atomicCAS(status, 0, (int)RLXPP_ERR_TIMEOUT);
   }
-  tc_teardown(sh, !ok && issue, phase);  // nothing is in flight when no MMA was issued
+  tc_teardown(smem, G, !ok && issue, phase, 1);  // nothing is in flight when no MMA was issued
 }
 
 // The level's matrix in the shared-memory image layout: column j (K index) holds the
@@ -748,8 +827,18 @@ __global__ void k_tc_matrix(const uint32_t* __restrict__ lux, __half* __restrict
 // Dynamic shared memory per CTA: the two operand tiles, the barrier and the output
 // staging slots (45.6 KB) rounded up so that at most 4 CTAs share an SM, whose 512 TMEM
 // columns then always suffice.
+// One-group CTAs (request and test kernels) take 46 KB, so that at most 4 share an SM,
+// whose 512 TMEM columns then always suffice; the draw kernels run kTcGroups groups
+// per CTA and one CTA per SM.
 constexpr size_t kTcSmem = 48 * 1024;
-static_assert(kStageOffset + kTcRows * kStageBytes <= (int)kTcSmem, "shared memory layout");
+static_assert(tc_smem_bytes(1, true) <= (int)kTcSmem, "shared memory layout");
+constexpr int kTcGroups = 5;
+static_assert(tc_smem_bytes(kTcGroups, true) <= 227 * 1024, "shared memory of a five-group CTA");
+// Tile-groups per CTA of each draw kernel.
+template <int Kind>
+constexpr int tc_groups() {
+  return Kind == kDrawSumHist ? 1 : kTcGroups;
+}
 
 // cuTensorMapEncodeTiled from the driver, looked up once (null if unavailable).
 using EncodeTiledFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
@@ -794,14 +883,18 @@ bool encode_output_map(const DrawArgs& a, CUtensorMap* map) {
 
 template <int Kind>
 cudaError_t launch_tc_kind(const DrawArgs& a, const __half* bimg, cudaStream_t st) {
-  cudaError_t e = cudaFuncSetAttribute(k_draw_tc<Kind>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTcSmem);
+  constexpr int T = tc_groups<Kind>();
+  // one-group CTAs keep 48 KB so that at most 4 share an SM (512 TMEM columns)
+  constexpr int smem_bytes = T == 1 ? (int)kTcSmem : tc_smem_bytes(T, Kind != kDrawSumHist);
+  cudaError_t e = cudaFuncSetAttribute(k_draw_tc<Kind, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes);
   if (e != cudaSuccess) return e;
-  const unsigned grid = (unsigned)((a.s.n + kTcRows - 1) / kTcRows);
+  const uint64_t tiles = (a.s.n + kTcRows - 1) / kTcRows;
+  const unsigned grid = (unsigned)((tiles + T - 1) / T);
   CUtensorMap map;
   std::memset(&map, 0, sizeof(map));
   int use_tma = 0;
   if constexpr (Kind != kDrawSumHist) use_tma = encode_output_map<Kind>(a, &map) ? 1 : 0;
-  k_draw_tc<Kind><<<grid, kTcRows, kTcSmem, st>>>(a, bimg, map, use_tma);
+  k_draw_tc<Kind, T><<<grid, kTcRows * T, smem_bytes, st>>>(a, bimg, map, use_tma);
   return cudaGetLastError();
 }
 
