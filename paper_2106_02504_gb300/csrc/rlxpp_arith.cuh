@@ -415,6 +415,50 @@ __device__ __forceinline__ uint64_t f64_bits_from48_large(uint64_t v) {  // 2^32
 __device__ __forceinline__ uint64_t f64_bits_from48(uint64_t v) {
   return (v >> 32) != 0u ? f64_bits_from48_large(v) : f64_bits_from48_small(v);
 }
+__device__ __forceinline__ uint32_t bfind_u32(uint32_t x) {  // position of the leading one
+  uint32_t p;
+  asm("bfind.u32 %0, %1;" : "=r"(p) : "r"(x));
+  return p;
+}
+
+// The 12 doubles of a block (Sec. 2.3 draw rule, integer construction as in
+// f64_bits_from48).  Value j is lo_j + hi_j 2^32 with hi_j < 2^16; when every hi_j is
+// nonzero (all but a 12 2^-16 share of the blocks, decided by one minimum) the leading
+// one of v_j is bit 32 + p_j, p_j = bfind(hi_j): the mantissa is v_j shifted left by
+// 20 - p_j and the exponent field (1006 + p_j) + 1 (the leading one adds the 1).
+__device__ __forceinline__ void block_f64(const uint32_t D[kLimbs], uint4 v[6]) {
+  uint32_t lo[kDoubles], hi[kDoubles];
+#pragma unroll
+  for (int q = 0; q < 6; ++q) {  // doubles 2q, 2q + 1 = limbs 3q .. 3q + 2
+    lo[2 * q] = D[3 * q];
+    hi[2 * q] = D[3 * q + 1] & 0xFFFFu;
+    lo[2 * q + 1] = __funnelshift_l(D[3 * q + 1], D[3 * q + 2], 16);
+    hi[2 * q + 1] = D[3 * q + 2] >> 16;
+  }
+  uint32_t mn = hi[0];
+#pragma unroll
+  for (int j = 1; j < kDoubles; ++j) mn = min(mn, hi[j]);
+  if (__builtin_expect(mn != 0u, 1)) {
+    uint32_t bh[kDoubles], bl[kDoubles];
+#pragma unroll
+    for (int j = 0; j < kDoubles; ++j) {
+      const uint32_t p = bfind_u32(hi[j]);  // 0..15
+      const uint32_t sh = 20u - p;          // 5..20
+      bl[j] = lo[j] << sh;
+      bh[j] = __funnelshift_l(lo[j], hi[j], sh) + ((1006u + p) << 20);
+    }
+#pragma unroll
+    for (int q = 0; q < 6; ++q) v[q] = make_uint4(bl[2 * q], bh[2 * q], bl[2 * q + 1], bh[2 * q + 1]);
+  } else {
+#pragma unroll
+    for (int q = 0; q < 6; ++q) {
+      const uint64_t a = f64_bits_from48(((uint64_t)hi[2 * q] << 32) | lo[2 * q]);
+      const uint64_t b = f64_bits_from48(((uint64_t)hi[2 * q + 1] << 32) | lo[2 * q + 1]);
+      v[q] = make_uint4((uint32_t)a, (uint32_t)(a >> 32), (uint32_t)b, (uint32_t)(b >> 32));
+    }
+  }
+}
+
 // The same value with the v < 2^32 case (a 2^-16 share of the values) in a call, so that
 // the common case carries no inline copy of it; for kernels with registers to spare.
 static __device__ __noinline__ uint64_t f64_bits_from48_small_call(uint64_t v) {

@@ -31,9 +31,14 @@ __device__ __forceinline__ void st_v8_u32(uint32_t* p, const uint32_t* v) {
 
 // A full block of 12 doubles to o[0..11]; 32-byte vector stores when aligned.
 __device__ __forceinline__ void store_block_f64(uint64_t* o, const uint32_t D[kLimbs]) {
+  uint4 v[6];
+  block_f64(D, v);
   uint64_t b[kDoubles];
 #pragma unroll
-  for (int j = 0; j < kDoubles; ++j) b[j] = f64_bits_from48(bits48(D, j));
+  for (int q = 0; q < 6; ++q) {
+    b[2 * q] = ((uint64_t)v[q].y << 32) | v[q].x;
+    b[2 * q + 1] = ((uint64_t)v[q].w << 32) | v[q].z;
+  }
   const uintptr_t addr = reinterpret_cast<uintptr_t>(o);
   if ((addr & 31) == 0) {
 #pragma unroll
