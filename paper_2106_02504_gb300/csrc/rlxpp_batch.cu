@@ -283,24 +283,50 @@ rlxpp_status plan_impl(rlxpp_gen* g, const rlxpp_request* reqs, uint64_t n_reqs,
   }
   if (n_reqs >= (uint64_t(1) << 32)) return set_last_error(RLXPP_ERR_INVALID, "too many requests");
   // by luxury level (one launch each), then most refills first (neighbours, which share
-  // a warp or a tensor tile, then take about as long), then by kind and request
+  // a warp or a tensor tile, then take about as long), then doubles before u24, then by
+  // request.  Items were made in request order, so a stable counting sort over
+  // (level, refills, kind) gives that order in O(n); sorting packed keys is the fallback
+  // when the refill range makes the bucket table large.
   const uint8_t* lev = g->level_host.data();
   auto level_of = [&](const Item& a) { return lev[reqs[a.req].stream]; };
-  auto refills_of = [](const Item& a) {  // refills of a chunk: ceil((count - head) / per)
+  auto refills_of = [](const Item& a) -> uint64_t {  // refills of a chunk: ceil((count - head) / per)
     const uint32_t kind = a.info & 1u, pos = (a.info >> 8) & 0xFFu, need = kind ? 2 : 1;
     const int64_t per = kWords / need;
     const int64_t room = pos + need <= (uint32_t)kWords ? (kWords - pos) / need : 0;
     const int64_t rest = a.count > room ? a.count - room : 0;
-    return (rest + per - 1) / per;
+    return (uint64_t)((rest + per - 1) / per);
   };
-  std::sort(items.begin(), items.end(), [&](const Item& a, const Item& b) {
-    const uint8_t la = level_of(a), lb = level_of(b);
-    if (la != lb) return la < lb;
-    const int64_t ra = refills_of(a), rb = refills_of(b);
-    if (ra != rb) return ra > rb;
-    if ((a.info & 1u) != (b.info & 1u)) return (a.info & 1u) > (b.info & 1u);
-    return a.req < b.req;
-  });
+  {
+    const size_t n_it = items.size();
+    std::vector<uint64_t> ref(n_it);
+    uint64_t rmax = 0;
+    for (size_t k = 0; k < n_it; ++k) {
+      ref[k] = refills_of(items[k]);
+      rmax = std::max(rmax, ref[k]);
+    }
+    const uint64_t n_buckets = (uint64_t)(g->n_levels + 1) * (rmax + 1) * 2;
+    std::vector<Item> sorted(n_it);
+    if (n_buckets <= std::max<uint64_t>(1u << 20, 4 * (uint64_t)n_it)) {
+      auto bucket = [&](size_t k) {
+        const Item& a = items[k];
+        return ((uint64_t)level_of(a) * (rmax + 1) + (rmax - ref[k])) * 2 + (1u - (a.info & 1u));
+      };
+      std::vector<uint64_t> start(n_buckets + 1, 0);
+      for (size_t k = 0; k < n_it; ++k) ++start[bucket(k) + 1];
+      for (uint64_t b = 0; b < n_buckets; ++b) start[b + 1] += start[b];
+      for (size_t k = 0; k < n_it; ++k) sorted[start[bucket(k)]++] = items[k];
+    } else {
+      std::vector<std::pair<uint64_t, uint64_t>> key(n_it);  // (level, refills desc, f64 first), index
+      for (size_t k = 0; k < n_it; ++k) {
+        const uint64_t r = std::min<uint64_t>(ref[k], (1ull << 54) - 1);
+        key[k] = {((uint64_t)level_of(items[k]) << 55) | ((((1ull << 54) - 1) - r) << 1) | (1u - (items[k].info & 1u)),
+                  k};
+      }
+      std::sort(key.begin(), key.end());
+      for (size_t k = 0; k < n_it; ++k) sorted[k] = items[key[k].second];
+    }
+    items.swap(sorted);
+  }
   rlxpp_plan* p = new rlxpp_plan();
   {
     uint64_t k = 0;

@@ -552,6 +552,8 @@ __global__ void __launch_bounds__(kTcRows* T, T == 1 ? 4 : 1)
         if constexpr (Kind == kDrawSumHist) {
           out.block(D, base + k);
         } else {
+          // streams out of step: a bulk copy of this thread's block from its staging
+          // slot (fewer registers than vector stores in this kernel)
           void* dst = out.out + base + k;
           if ((reinterpret_cast<uintptr_t>(dst) & 15) == 0) {
             uint4 v[6];
@@ -628,7 +630,6 @@ __global__ void __launch_bounds__(kTcRows, 4) k_requests_tc(const BatchArgs b, c
   extern __shared__ __align__(1024) unsigned char smem[];
   const TcGroup G = tc_group(smem, true);  // one group per CTA
   const __half* bmat = tc_bmat(smem);
-  uint4* slot = reinterpret_cast<uint4*>(G.stage + G.t * kStageBytes);
   const int tid = threadIdx.x;
   tc_setup(smem, G, bimg, 1);
   const uint32_t taddr = tc_tmem(smem, G);
@@ -687,24 +688,11 @@ __global__ void __launch_bounds__(kTcRows, 4) k_requests_tc(const BatchArgs b, c
       const int64_t per = f64 ? kDoubles : kWords;
       const int64_t rem = cnt - k;
       if (rem >= per) {
-        void* dst = f64 ? (void*)(b.out_f64 + base + k) : (void*)(b.out_u24 + base + k);
-        uint4 v[6];
+        // chunks write to unrelated places: direct vector stores (32 bytes when aligned)
         if (f64)
-          block_values<kDrawF64>(D, v);
+          store_block_f64(b.out_f64 + base + k, D);
         else
-          block_values<kDrawU24>(D, v);
-        if ((reinterpret_cast<uintptr_t>(dst) & 15) == 0) {
-          bulk_store96(dst, slot, v);
-        } else {
-          uint32_t* o = static_cast<uint32_t*>(dst);
-#pragma unroll
-          for (int q = 0; q < 6; ++q) {
-            o[4 * q] = v[q].x;
-            o[4 * q + 1] = v[q].y;
-            o[4 * q + 2] = v[q].z;
-            o[4 * q + 3] = v[q].w;
-          }
-        }
+          store_block_u24(b.out_u24 + base + k, D);
         k += per;
         pos = kWords;
       } else {
