@@ -45,6 +45,7 @@ IMAD_PER_SM_CLK = 64
 SM_MAX_MHZ = 2070.0
 ALU_PER_SM_CLK = 64
 TC_FLOP_PER_ADVANCE = 2 * 80 * 80      # padded 128 x 80 x 80 fp16 product per 128 streams
+TC_ALG_FLOP_PER_ADVANCE = 2 * 72 * 72  # the 5,184 byte products of the 72 x 72 folded matrix
 ALU_INSTR_PER_ADVANCE_TC = 244         # integer-pipe instructions per refill of k_draw_tc<sum/hist> (ncu)
 TC_FUSED_DRAM_BYTES_PER_STREAM = 76.2  # its DRAM traffic per stream and launch (ncu, 2^18 streams)
 CPU_SAMPLE_STREAMS = 16384
@@ -248,6 +249,9 @@ def run_native(args, rank, world, local_rank):
         return ms / args.steps, per_kernel, clocks
 
     launches_per_step = 3
+    # write-only HBM bandwidth on the same 8 GiB buffer (torch's fill kernel), next to
+    # the measured copy peak: the HBM kernel only writes
+    hbm_write_gbs = n * HBM_COUNT * 8 / (_time_events(lambda: out.zero_(), 3, stream) * 1e-3) / 1e9
     peaks = load_peaks()
     imad_peak = SMS * IMAD_PER_SM_CLK * SM_MAX_MHZ * 1e6  # IMAD ops/s, derived
     hbm_peak = peaks.get("hbm_gbs", 6800.0)
@@ -266,9 +270,12 @@ def run_native(args, rank, world, local_rank):
                 if name == "tensor":  # 128 x 80 x 80 fp16 MMA per 128-stream tile and refill
                     entry["tensor_tflops"] = adv * TC_FLOP_PER_ADVANCE / (kms * 1e-3) / 1e12
                     entry["tensor_frac"] = entry["tensor_tflops"] / f16_peak
+                    entry["tensor_alg_frac"] = adv * TC_ALG_FLOP_PER_ADVANCE / (kms * 1e-3) / 1e12 / f16_peak
             if kname == "draw_f64_hbm":
                 entry["hbm_gbs"] = n * HBM_COUNT * 8 / (kms * 1e-3) / 1e9
                 entry["hbm_frac"] = entry["hbm_gbs"] / hbm_peak
+                entry["hbm_write_peak_gbs"] = hbm_write_gbs
+                entry["hbm_write_frac"] = entry["hbm_gbs"] / hbm_write_gbs
             kern[kname] = entry
         paths[name] = {"ms_per_step": ms_step, "value": n * (HBM_COUNT + FUSED_COUNT) * world / (ms_step * 1e-3),
                        "kernels": kern, "per_kernel_ms": per_kernel, "clocks": clocks}
@@ -471,11 +478,13 @@ def bench_serving(args):
     n_res, rate = 100_000, 20_000
     n_req = int(rate * args.serve_seconds)
     arr, stream, counts, is_f64 = W.serving_trace(n_req, rate, n_res, seed=5)
-    srv = Server(n_res, pool_bytes=args.serve_pool_gib << 30, n_cuda_streams=4, max_batch=512)
+    srv = Server(n_res, pool_bytes=args.serve_pool_gib << 30, n_cuda_streams=args.serve_streams,
+                 max_batch=args.serve_max_batch)
     stats = srv.run_trace(arr, stream, counts, is_f64)
     srv.close()
     stats.update({"resident_streams": n_res, "arrival_rate_hz": rate, "trace_seconds": args.serve_seconds,
-                  "pool_bytes": args.serve_pool_gib << 30})
+                  "pool_bytes": args.serve_pool_gib << 30, "cuda_streams": args.serve_streams,
+                  "max_batch": args.serve_max_batch})
     return stats
 
 
@@ -532,7 +541,9 @@ def main():
     ap.add_argument("--only-main", action="store_true", help="skip the other workloads")
     ap.add_argument("--path", default="imad,tensor", help="refill paths to time; the faster one is reported")
     ap.add_argument("--batch-streams", type=int, default=65536)
-    ap.add_argument("--serve-seconds", type=float, default=5.0)
+    ap.add_argument("--serve-seconds", type=float, default=10.0)
+    ap.add_argument("--serve-streams", type=int, default=4)
+    ap.add_argument("--serve-max-batch", type=int, default=512)
     ap.add_argument("--serve-pool-gib", type=int, default=8)
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))

@@ -30,7 +30,8 @@
  *    refills first and a lone leftover number is skipped) and returns
  *    (w_k + 2^24 w_{k+1}) * 2^-48, exactly (Sec. 2.3: 48 bits per double).
  *  - Seeding (Sec. 2.4, exponentiation by squaring; the 2^96 spacing is the one in
- *    Sec. 2.5): seed s starts at the LCG state A^(2^96 s), read position 0.
+ *    Sec. 2.5): seed s, 1 <= s < 2^64, starts at the LCG state A^(2^96 s), read
+ *    position 0.
  */
 #ifndef RLXPP_H
 #define RLXPP_H
@@ -77,17 +78,21 @@ typedef struct rlxpp_state {
  *                     the device (Sec. 2.4).
  *  level_of_stream    NULL (every stream uses levels[0]) or n_streams bytes, each
  *                     < n_levels, host or device.
- *  seeds              n_streams uint64 seeds, host or device; stream i starts at
+ *  seeds              n_streams uint64 seeds >= 1, host or device; stream i starts at
  *                     A^(2^96 seeds[i]).
  *  out                receives the handle; *out is NULL on failure.
- * n_streams may be 0.  Fails with RLXPP_ERR_INVALID on a bad level or level index
- * (level indices are checked on the device and reported by rlxpp_sync()). */
+ * n_streams may be 0.  Fails with RLXPP_ERR_INVALID on a bad level, level index or
+ * seed: a zero in a host seed array fails the call; level indices and device seeds are
+ * checked on the device and reported by rlxpp_sync() (such a stream then holds the
+ * LCG state 1 at level 0). */
 rlxpp_status rlxpp_create(uint64_t n_streams, const uint32_t* levels, uint32_t n_levels,
                           const uint8_t* level_of_stream, const uint64_t* seeds,
                           void* cuda_stream, rlxpp_gen** out);
 
 /* Re-seed every stream in place (levels unchanged): stream i restarts at
- * A^(2^96 seeds[i]) with read position 0.  seeds: n_streams uint64, host or device. */
+ * A^(2^96 seeds[i]) with read position 0.  seeds: n_streams uint64 >= 1, host or
+ * device; a zero in a host array fails the call with RLXPP_ERR_INVALID, a zero in a
+ * device array leaves that stream unchanged and is reported by rlxpp_sync(). */
 rlxpp_status rlxpp_seed(rlxpp_gen* gen, const uint64_t* seeds, void* cuda_stream);
 
 /* Skip ahead (Sec. 2.4): stream i applies n_i LCG advances, X <- A^(n_i) X, without
@@ -269,7 +274,8 @@ void rlxpp_destroy(rlxpp_gen* gen);
  *  level_of_stream   NULL (all streams at levels[0]) or n_streams bytes, device memory;
  *                    a stream whose index is >= n_levels gets an all-zero record
  *                    (p = 0 marks it invalid).
- *  seeds             n_streams uint64, device memory.
+ *  seeds             n_streams uint64, device memory; a zero seed (seeds start at 1)
+ *                    also gets an all-zero record.
  *  out               n_streams records, device memory.
  * Host pointers are rejected (staging them would allocate).
  *

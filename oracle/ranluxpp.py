@@ -139,7 +139,10 @@ def f32_bits_from24(w):
 
 # --- Sec. 2.4: seeding and skipping -------------------------------------------------
 def seed_lcg(seed, p):
-    """LCG state of seed s: the state 1 skipped by 2^96 s luxury advances."""
+    """LCG state of seed s: the state 1 skipped by 2^96 s luxury advances.  Seeds are
+    1 .. 2^64 - 1; seed 0 would leave the state 1 itself and is rejected."""
+    if not 1 <= seed < 1 << 64:
+        raise ValueError("seed must be in [1, 2^64)")
     return pow(luxury_multiplier(p), seed << SEED_SHIFT, M)
 
 

@@ -40,6 +40,15 @@ bool on_device(const void* p) {
   return attr.type == cudaMemoryTypeDevice || attr.type == cudaMemoryTypeManaged;
 }
 
+// Seeds start at 1.  A host array is checked here (the call then fails at once); zeros
+// in a device array are reported by the seeding kernel (sticky RLXPP_ERR_INVALID).
+bool host_seeds_valid(const uint64_t* seeds, uint64_t n) {
+  if (on_device(seeds)) return true;
+  for (uint64_t i = 0; i < n; ++i)
+    if (seeds[i] == 0) return false;
+  return true;
+}
+
 // A device copy of a host input array, or the pointer itself if already on the device.
 // The copy completes before this returns, so the caller's host buffer may be reused.
 struct Staged {
@@ -237,6 +246,7 @@ rlxpp_status rlxpp_create(uint64_t n_streams, const uint32_t* levels, uint32_t n
     if (levels[l] == 0) return fail(RLXPP_ERR_INVALID, "luxury level must be >= 1");
   if (n_streams > 0 && !seeds) return fail(RLXPP_ERR_INVALID, "null seeds");
   if (n_streams > (uint64_t(1) << 40)) return fail(RLXPP_ERR_INVALID, "too many streams");
+  if (n_streams > 0 && !host_seeds_valid(seeds, n_streams)) return fail(RLXPP_ERR_INVALID, "seeds must be >= 1");
   cudaStream_t st = as_stream(cuda_stream);
   rlxpp_gen* g = new rlxpp_gen();
   auto bail = [&](rlxpp_status s) {
@@ -307,6 +317,7 @@ rlxpp_status rlxpp_seed(rlxpp_gen* g, const uint64_t* seeds, void* cuda_stream) 
   if (rlxpp_status s = check_gen(g)) return s;
   if (g->n == 0) return RLXPP_OK;
   if (!seeds) return fail(RLXPP_ERR_INVALID, "null seeds");
+  if (!host_seeds_valid(seeds, g->n)) return fail(RLXPP_ERR_INVALID, "seeds must be >= 1");
   cudaStream_t st = as_stream(cuda_stream);
   Staged ss;
   if (rlxpp_status s = stage_in(seeds, sizeof(uint64_t) * g->n, st, ss)) return s;

@@ -86,11 +86,16 @@ __global__ void k_seed(StateView s, const uint64_t* __restrict__ seeds,
     set_status(s.status, RLXPP_ERR_INVALID);
     lvl = 0;
   }
+  const uint64_t seed = seeds[i];
+  if (seed == 0) {  // seeds start at 1: report, and leave a re-seeded stream as it was
+    set_status(s.status, RLXPP_ERR_INVALID);
+    if (keep_levels) return;
+  }
   const uint32_t* T = s.table + (size_t)lvl * kTableLimbs;
   uint32_t X[kLimbs];
   bool have = false;
-  apply_digits(T, kSeedWindow0, seeds[i], X, have);
-  if (!have) {
+  apply_digits(T, kSeedWindow0, seed, X, have);
+  if (!have) {  // a new handle's stream with seed 0: the state 1, so that it is defined
 #pragma unroll
     for (int k = 0; k < kLimbs; ++k) X[k] = k == 0 ? 1u : 0u;
   }
@@ -341,7 +346,8 @@ __global__ void k_seed_records(const uint32_t* __restrict__ scratch, LevelList l
   if (i >= n) return;
   uint64_t* rec = reinterpret_cast<uint64_t*>(out + i);
   const uint32_t lvl = level_of ? level_of[i] : 0u;
-  if (lvl >= lv.n) {
+  const uint64_t seed = seeds[i];
+  if (lvl >= lv.n || seed == 0) {  // invalid level index or seed: an all-zero record
 #pragma unroll
     for (int k = 0; k < 11; ++k) rec[k] = 0;
     return;
@@ -349,11 +355,7 @@ __global__ void k_seed_records(const uint32_t* __restrict__ scratch, LevelList l
   const uint32_t* T = scratch + (size_t)lvl * kNoAllocLevelLimbs + 18;
   uint32_t X[kLimbs];
   bool have = false;
-  apply_digits(T, kSeedWindow0, seeds[i], X, have);
-  if (!have) {
-#pragma unroll
-    for (int k = 0; k < kLimbs; ++k) X[k] = k == 0 ? 1u : 0u;
-  }
+  apply_digits(T, kSeedWindow0, seed, X, have);
   uint32_t D[kLimbs];
   to_ranlux(X, D);
 #pragma unroll

@@ -9,7 +9,9 @@ after or beside any other request: the device starts it by jump-ahead
 (rlxpp_draw_requests with skip = start block).  A request is admitted when its output
 fits in a fixed device-memory arena, launched with whatever else is admitted as one
 batch on one of several CUDA streams while earlier batches still run, copied to a
-pinned host mirror of the arena, and completed when the batch's event has fired.
+pinned host mirror of the arena, and completed when its copy has finished: the small
+requests of a batch are copied first (adjacent blocks in one copy), then each large one
+by itself, smallest first, each group with its own event.
 """
 from __future__ import annotations
 
@@ -96,7 +98,7 @@ class Request:
 
 class Server:
     def __init__(self, n_resident, luxury=2048, seeds=None, pool_bytes=1 << 30, n_cuda_streams=4,
-                 max_batch=512, keep_results=False, copy_to_host=True):
+                 max_batch=512, keep_results=False, copy_to_host=True, small_bytes=1 << 20):
         import torch
         self.torch = torch
         if seeds is None:
@@ -112,8 +114,9 @@ class Server:
         self.free_streams = collections.deque(range(n_cuda_streams))
         self.waiting = collections.deque()     # arrived, not admitted (FIFO)
         self.admitted = collections.deque()    # admitted, not launched
-        self.inflight = collections.deque()    # (event, stream index, [requests])
+        self.inflight = collections.deque()    # (stream index, deque of (event, [requests]))
         self.max_batch = max_batch
+        self.small_bytes = small_bytes   # requests below this size share one copy group
         self.keep_results = keep_results
         self.finished = []
         self.t0 = time.perf_counter()
@@ -157,45 +160,66 @@ class Server:
             reqs["count"] = [r.count for r in batch]
             reqs["offset"] = [r.offset // (8 if r.kind == KIND_F64 else 4) for r in batch]
             base = self.dev.data_ptr()
+            groups = []   # (event, requests): each request completes with its group's event
             with torch.cuda.stream(st):
                 B.rlxpp_draw_requests(self.gen.handle, reqs, base, base, 0, st)
                 if self.host is not None:
-                    # one copy per run of adjacent arena blocks of this batch
-                    spans = sorted((r.offset, r.reserved) for r in batch if r.nbytes)
-                    k = 0
-                    while k < len(spans):
-                        a, ln = spans[k]
-                        while k + 1 < len(spans) and spans[k + 1][0] == a + ln:
-                            ln += spans[k + 1][1]
+                    # small requests first, one copy per run of adjacent arena blocks, so
+                    # that they do not wait behind the large copies of the same batch;
+                    # then each large request by itself, smallest first
+                    small = [r for r in batch if r.nbytes < self.small_bytes]
+                    large = sorted((r for r in batch if r.nbytes >= self.small_bytes), key=lambda r: r.nbytes)
+                    if small:
+                        spans = sorted((r.offset, r.reserved) for r in small if r.nbytes)
+                        k = 0
+                        while k < len(spans):
+                            a, ln = spans[k]
+                            while k + 1 < len(spans) and spans[k + 1][0] == a + ln:
+                                ln += spans[k + 1][1]
+                                k += 1
+                            self.host[a:a + ln].copy_(self.dev[a:a + ln], non_blocking=True)
                             k += 1
-                        self.host[a:a + ln].copy_(self.dev[a:a + ln], non_blocking=True)
-                        k += 1
-                ev = torch.cuda.Event()
-                ev.record(st)
+                        ev = torch.cuda.Event()
+                        ev.record(st)
+                        groups.append((ev, small))
+                    for r in large:
+                        self.host[r.offset:r.offset + r.nbytes].copy_(self.dev[r.offset:r.offset + r.nbytes],
+                                                                     non_blocking=True)
+                        ev = torch.cuda.Event()
+                        ev.record(st)
+                        groups.append((ev, [r]))
+                else:
+                    ev = torch.cuda.Event()
+                    ev.record(st)
+                    groups.append((ev, batch))
             t = self.now()
             for r in batch:
                 r.launch = t
-            self.inflight.append((ev, si, batch))
+            self.inflight.append((si, collections.deque(groups)))
 
     def _complete(self, wait_first=False):
-        """Retire every finished batch (any order); optionally wait for the oldest first."""
+        """Retire every request whose copy has finished (any order); a CUDA stream is
+        free again once its batch's last group is done.  Optionally wait for the
+        oldest batch's next group first."""
         if wait_first and self.inflight:
-            self.inflight[0][0].synchronize()
+            self.inflight[0][1][0][0].synchronize()
         keep = collections.deque()
         while self.inflight:
-            ev, si, batch = self.inflight.popleft()
-            if not ev.query():
-                keep.append((ev, si, batch))
-                continue
-            t = self.now()
-            for r in batch:
-                r.done = t
-                if self.keep_results and self.host is not None and r.nbytes:
-                    raw = self.host[r.offset:r.offset + r.nbytes].numpy()
-                    r.result = raw.view(np.uint64 if r.kind == KIND_F64 else np.uint32).copy()
-                self.arena.release(r.offset, r.reserved)
-                self.finished.append(r)
-            self.free_streams.append(si)
+            si, groups = self.inflight.popleft()
+            while groups and groups[0][0].query():  # a stream's groups finish in order
+                _, done = groups.popleft()
+                t = self.now()
+                for r in done:
+                    r.done = t
+                    if self.keep_results and self.host is not None and r.nbytes:
+                        raw = self.host[r.offset:r.offset + r.nbytes].numpy()
+                        r.result = raw.view(np.uint64 if r.kind == KIND_F64 else np.uint32).copy()
+                    self.arena.release(r.offset, r.reserved)
+                    self.finished.append(r)
+            if groups:
+                keep.append((si, groups))
+            else:
+                self.free_streams.append(si)
         self.inflight = keep
 
     def pump(self):

@@ -67,12 +67,33 @@ def test_seed_states(native):
     seeds = W.consecutive_seeds(N)
     g = make(native, seeds)
     assert_states(native, g, StreamSet.from_seeds(seeds, 2048))
-    # extreme seeds, including 0 and 2^64 - 1
-    seeds2 = np.array([0, 1, 2 ** 63, 2 ** 64 - 1, 2718, 123456789012345], dtype=np.uint64)
+    # extreme seeds: the smallest, 2^63 and the largest
+    seeds2 = np.array([1, 2, 2 ** 63, 2 ** 64 - 1, 2718, 123456789012345], dtype=np.uint64)
     g2 = make(native, seeds2, levels=(389,))
     assert_states(native, g2, StreamSet.from_seeds(seeds2, 389))
     g.close()
     g2.close()
+
+
+def test_zero_seed_rejected(native):
+    """Seeds start at 1: a zero in a host array fails the call at once; a zero in a
+    device array is reported by rlxpp_sync, a re-seeded stream with seed 0 keeps its
+    state and the other streams are seeded as usual."""
+    seeds = np.array([5, 0, 7], dtype=np.uint64)
+    with pytest.raises(native.RlxppError) as e:
+        native.Generator(3, [2048], torch.from_numpy(seeds.view(np.int64)))      # host seeds
+    assert e.value.status == native.RLXPP_ERR_INVALID
+    g = make(native, np.array([5, 6, 7], dtype=np.uint64))
+    with pytest.raises(native.RlxppError):
+        g.seed(torch.from_numpy(seeds.view(np.int64)))                             # host seeds
+    assert_states(native, g, StreamSet.from_seeds([5, 6, 7], 2048))               # nothing moved
+    g.seed(dev_u64(np.array([9, 0, 11], dtype=np.uint64)))                        # device seeds
+    with pytest.raises(native.RlxppError) as e:
+        g.sync()
+    assert e.value.status == native.RLXPP_ERR_INVALID
+    assert_states(native, g, StreamSet.from_seeds([9, 6, 11], 2048))             # stream 1 kept
+    g.sync()                                                                       # cleared
+    g.close()
 
 
 @pytest.mark.parametrize("p,count", [(2048, 1000), (24, 1001), (223, 12), (389, 1)])

@@ -221,6 +221,10 @@ def test_seed_spacing_is_2_96_advances():
     for _ in range(96):
         y = y * y % R.M
     assert R.seed_lcg(1, p) == y
+    # seeds start at 1 (seed 0 would be the unmoved state 1) and fit 64 bits
+    for bad in (0, -1, 2 ** 64):
+        with pytest.raises(ValueError):
+            R.seed_lcg(bad, p)
 
 
 def test_skip_keeps_position_and_matches_recurrence_blocks():

@@ -38,7 +38,7 @@ def test_noalloc_seeding_matches_allocating_path(native):
              ([24, 223, 389, 2048], 12, W.batch_mix(n, seed=13)[1])]
     for levels, seed, level_of in calls:   # two calls in a row share the scratch array
         seeds = W.random_seeds(n, seed)
-        seeds[:3] = [0, 1, 2 ** 64 - 1]
+        seeds[:3] = [1, 2, 2 ** 64 - 1]
         seeds_d = torch.from_numpy(seeds.view(np.int64)).cuda()
         level_of_d = None if level_of is None else torch.from_numpy(level_of).cuda()
         out = torch.full((n, 11), -1, dtype=torch.int64, device="cuda")
@@ -56,8 +56,10 @@ def test_noalloc_limits(native):
     assert e.value.status == native.RLXPP_ERR_INVALID
     with pytest.raises(native.RlxppError):
         native.rlxpp_seed_states_noalloc([2048], seeds.cpu(), 4, out)             # host seeds
-    # a level index beyond the list gives an all-zero (invalid, p = 0) record
+    # a level index beyond the list, or a zero seed, gives an all-zero (invalid, p = 0)
+    # record
     lvl = torch.tensor([0, 1, 0, 0], dtype=torch.uint8, device="cuda")
+    seeds[3] = 0
     native.rlxpp_seed_states_noalloc([2048], seeds, 4, out, lvl)
     torch.cuda.synchronize()
-    assert int(out[1].abs().sum()) == 0 and int(out[0, 10]) == 2048
+    assert int(out[1].abs().sum()) == 0 and int(out[3].abs().sum()) == 0 and int(out[0, 10]) == 2048
