@@ -326,6 +326,7 @@ def run_native(args, rank, world, local_rank):
             "single_stream": bench_single_stream(nat, dev),
             "mixed_batch": bench_mixed_batch(nat, dev, args),
             "skip": bench_skip(nat, dev),
+            "normal": bench_normal(nat, dev),
             "serving": bench_serving(args),
         }
     if rank == 0 and not args.no_cpu_baseline:
@@ -468,6 +469,28 @@ def bench_skip(nat, dev):
     g.close()
     return {"streams": n, "skip_ms": ms_skip, "skips_per_s": n / (ms_skip * 1e-3),
             "products_per_stream_max": 32, "draw48_ms": ms_draw}
+
+
+def bench_normal(nat, dev):
+    """Gaussian doubles (Box-Muller on pairs of the streams' doubles): 2^20 streams
+    (seeds i + 1, p = 2048), 1024 values each into an 8 GiB device buffer, both paths."""
+    import numpy as np
+    import torch
+    n, cnt = 1 << 20, 1024
+    seeds = torch.from_numpy(np.arange(1, n + 1, dtype=np.uint64).view(np.int64)).to(dev)
+    g = nat.Generator(n, [LUXURY], seeds)
+    out = torch.empty((n, cnt), dtype=torch.float64, device=dev)
+    st = torch.cuda.current_stream()
+    res = {"streams": n, "values_per_stream": cnt}
+    for name, pid in (("tensor", nat.RLXPP_PATH_TENSOR), ("imad", nat.RLXPP_PATH_IMAD)):
+        g.set_path(pid)
+        ms = _time_events(lambda: nat.rlxpp_draw_normal_f64(g.handle, out, cnt, None, None, st.cuda_stream), 3, st)
+        res[name] = {"ms": ms, "values_per_s": n * cnt / (ms * 1e-3)}
+    g.sync()
+    g.close()
+    del out
+    torch.cuda.empty_cache()
+    return res
 
 
 def bench_serving(args):

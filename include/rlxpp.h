@@ -122,6 +122,18 @@ rlxpp_status rlxpp_draw_f64(rlxpp_gen* gen, const int64_t* counts, const int64_t
 rlxpp_status rlxpp_draw_f32(rlxpp_gen* gen, const int64_t* counts, const int64_t* offsets,
                             int64_t count_each, float* out, void* cuda_stream);
 
+/* Draw standard Gaussian doubles (the distributions ROOT builds on Rndm, Sec. 2.4), by
+ * the Box-Muller transform (Box and Muller, Ann. Math. Statist. 29, 1958) on
+ * consecutive pairs (d_a, d_b) of the stream's doubles (the rlxpp_draw_f64 sequence):
+ * u1 = 1 - d_a in (0, 1], r = sqrt(-2 ln u1), then r cos(2 pi d_b) and r sin(2 pi d_b).
+ * n values take 2 ceil(n / 2) doubles (an odd count drops its last sine), so afterwards
+ * the stream stands where rlxpp_draw_f64 of 2 ceil(n / 2) values would leave it.  ln,
+ * sqrt, sin and cos are CUDA's double-precision functions: each value is within a few
+ * units in the last place of the exact transform of its pair.  double out, same layout
+ * rules as rlxpp_draw_u24 (count = normals per stream). */
+rlxpp_status rlxpp_draw_normal_f64(rlxpp_gen* gen, const int64_t* counts, const int64_t* offsets,
+                                   int64_t count_each, double* out, void* cuda_stream);
+
 /* Skip random numbers without generating them (Sec. 2.4), counted in values of one
  * kind: stream i moves exactly as if it had drawn n_values[i] values of `kind`
  * (RLXPP_KIND_U24, RLXPP_KIND_F64 or RLXPP_KIND_F32) and discarded them: the rest of

@@ -22,7 +22,7 @@ Everything here is the plain definition, written with Python integers:
   24-bit single-precision floats w 2^-24 (RANLUX's own output format);
 * seeding and skipping by exponentiation (Sec. 2.4) as Python ``pow``.
 
-Readings where the paper is silent (each also listed in the design doc):
+Readings where the paper is silent:
 
 * seed s gives the LCG state a_p^(2^96 s) (the state 1 skipped by 2^96 s luxury
   advances; Sec. 2.5 mentions skipping 2^96 seed states), converted to RANLUX numbers
@@ -30,13 +30,18 @@ Readings where the paper is silent (each also listed in the design doc):
 * one draw position counts 24-bit words 0..24; a u24 draw takes the next word, a double
   takes the next two words w_k + 2^24 w_{k+1} (k = pos) and needs both in the current
   block, otherwise the generator advances first (a lone leftover word is discarded);
-* skip(n) applies n luxury advances (A^n) to the LCG state and keeps the read position.
+* skip(n) applies n luxury advances (A^n) to the LCG state and keeps the read position;
+* seeds are 1 .. 2^64 - 1;
+* Gaussian values come from consecutive pairs of the stream's doubles by the
+  Box-Muller transform (Box and Muller, Ann. Math. Statist. 29, 1958), u1 = 1 - d_a so
+  that ln u1 is finite; n values take 2 ceil(n / 2) doubles.
 
 Parity pins for every function are in ``tests/test_oracle_pins.py`` (SWB brute force,
 closed forms, invariants and edge cases).
 """
 from __future__ import annotations
 
+import math
 import struct
 
 # --- Sec. 2.2: the modulus --------------------------------------------------------
@@ -126,6 +131,45 @@ def f64_from_bits48(v):
     return float(v) * 2.0 ** -48
 
 
+
+def cos_sin_2pi(d):
+    """(cos 2 pi d, sin 2 pi d) for a double d in [0, 1): 4d is exact, so it splits
+    exactly into q quarter turns (q = round(4d)) and a rest f in [-1/2, 1/2]; the angle
+    (pi / 2) f is at most pi / 4, where math.cos and math.sin are accurate to about an
+    ulp, and the quarter turns are exact sign and order changes."""
+    t = 4.0 * d
+    q = int(round(t))
+    f = t - q
+    th = (math.pi / 2.0) * f
+    c, s = math.cos(th), math.sin(th)
+    return [(c, s), (-s, c), (-c, -s), (s, -c)][q % 4]
+
+
+def box_muller(d_a, d_b):
+    """Box and Muller (1958): two standard Gaussian values from two doubles in [0, 1):
+    u1 = 1 - d_a in (0, 1] (exact for 48-bit doubles), r = sqrt(-2 ln u1), then
+    (r cos 2 pi d_b, r sin 2 pi d_b)."""
+    u1 = 1.0 - d_a
+    r = math.sqrt(-2.0 * math.log(u1))
+    c, s = cos_sin_2pi(d_b)
+    return r * c, r * s
+
+
+def box_muller_many(d_a, d_b):
+    """box_muller over numpy arrays of pairs (the same steps with numpy's log, sqrt, cos
+    and sin); returns the two arrays of values."""
+    import numpy as np
+    d_a = np.asarray(d_a, dtype=np.float64)
+    d_b = np.asarray(d_b, dtype=np.float64)
+    r = np.sqrt(-2.0 * np.log(1.0 - d_a))
+    t = 4.0 * d_b
+    q = np.rint(t)
+    th = (math.pi / 2.0) * (t - q)
+    c, s = np.cos(th), np.sin(th)
+    qi = q.astype(np.int64) % 4
+    return r * np.choose(qi, [c, -s, -c, s]), r * np.choose(qi, [s, c, -s, -c])
+
+
 def f64_bits(x):
     """IEEE-754 binary64 bit pattern of a Python float."""
     return struct.unpack("<Q", struct.pack("<d", x))[0]
@@ -191,6 +235,14 @@ class Stream:
 
     def draw_f64(self, n):
         return [f64_from_bits48(v) for v in self.draw_bits48(n)]
+
+    def draw_normal(self, n):
+        """n Gaussian values: Box-Muller on consecutive pairs of 2 ceil(n / 2) doubles."""
+        d = self.draw_f64(n + (n & 1))
+        out = []
+        for k in range(0, len(d), 2):
+            out.extend(box_muller(d[k], d[k + 1]))
+        return out[:n]
 
     def draw_f32_bits(self, n):
         """Single-precision draws: one number each, w 2^-24 (the 24-bit RANLUX output)."""

@@ -79,6 +79,13 @@ __global__ void __launch_bounds__(kDrawBlock, Uniform ? RLXPP_DRAW_MIN_BLOCKS : 
       out.sum = 0;
       out.hist = hist_s + (threadIdx.x / 32) * 256;
     }
+    if constexpr (Kind == kDrawNormal) {  // n normals take 2 ceil(n / 2) doubles
+      out.out = static_cast<double*>(a.out);
+      out.base = base;
+      out.end = base + cnt;
+      out.va = 0;
+      cnt += cnt & 1;
+    }
     if (draw_stream<Kind>(out, D, c, pos, A, AS, ca, cnt, base)) {
 #pragma unroll
       for (int q = 0; q < 9; ++q) s.D[(uint64_t)q * s.stride + i] = ((uint64_t)D[2 * q + 1] << 32) | D[2 * q];
@@ -119,6 +126,7 @@ cudaError_t launch_draw(int kind, const DrawArgs& a, cudaStream_t st) {
     case kDrawF64: return launch_kind<kDrawF64>(a, st);
     case kDrawSumHist: return launch_kind<kDrawSumHist>(a, st);
     case kDrawF32: return launch_kind<kDrawF32>(a, st);
+    case kDrawNormal: return launch_kind<kDrawNormal>(a, st);
   }
   return cudaErrorInvalidValue;
 }

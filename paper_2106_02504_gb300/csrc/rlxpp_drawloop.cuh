@@ -157,6 +157,45 @@ struct Consumer<kDrawSumHist> {
   }
 };
 
+// Gaussian doubles by the Box-Muller transform (Box and Muller, Ann. Math. Statist. 29,
+// 1958) on consecutive pairs (d_a, d_b) of the stream's doubles: u1 = 1 - d_a in (0, 1]
+// (exact: (2^48 - v_a) 2^-48), r = sqrt(-2 ln u1), z_a = r cos(2 pi d_b),
+// z_b = r sin(2 pi d_b).  The draw loop feeds it 2 ceil(n / 2) doubles, value j at
+// output index base + j; pairs start at even j; an index at or past `end` (the last
+// sine of an odd count) is not written.  log, sqrt and sincospi are CUDA's
+// double-precision functions.
+template <>
+struct Consumer<kDrawNormal> {
+  double* out;
+  int64_t base, end;
+  uint64_t va;  // first value of the current pair, as its 48-bit integer
+  __device__ __forceinline__ void take(uint64_t v, int64_t idx) {
+    if (((idx - base) & 1) == 0) {
+      va = v;
+      return;
+    }
+    const double u1 = va ? __longlong_as_double((long long)f64_bits_from48((1ull << 48) - va)) : 1.0;
+    const double u2 = __longlong_as_double((long long)f64_bits_from48(v));
+    const double r = sqrt(-2.0 * log(u1));
+    double sn, cs;
+    sincospi(2.0 * u2, &sn, &cs);
+    out[idx - 1] = r * cs;
+    if (idx < end) out[idx] = r * sn;
+  }
+  __device__ __forceinline__ void value_at_word(const uint32_t D[kLimbs], int w, int64_t idx) {
+    take(bits48_at_word(D, w), idx);
+  }
+  __device__ __forceinline__ void block(const uint32_t D[kLimbs], int64_t idx) {
+#pragma unroll
+    for (int j = 0; j < kDoubles; ++j) take(bits48(D, j), idx + j);
+  }
+  __device__ __forceinline__ void partial(const uint32_t D[kLimbs], int64_t idx, int64_t n) {
+#pragma unroll
+    for (int j = 0; j < kDoubles; ++j)
+      if (j < n) take(bits48(D, j), idx + j);
+  }
+};
+
 // Draws cnt values for one stream.  On entry D holds the RANLUX numbers of the current
 // block, c its borrow and pos the numbers already read; values go to out at indices
 // base, base + 1, ...  On return D, c and pos describe the stream after the draw.

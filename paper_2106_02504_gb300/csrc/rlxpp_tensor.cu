@@ -477,6 +477,13 @@ __global__ void __launch_bounds__(kTcRows* T, T == 1 ? 4 : 1)
     out.sum = 0;
     out.hist = hist_s + (tid / 32) * 256;
   }
+  if constexpr (Kind == kDrawNormal) {  // n normals take 2 ceil(n / 2) doubles
+    out.out = static_cast<double*>(a.out);
+    out.base = base;
+    out.end = base + cnt;
+    out.va = 0;
+    cnt += cnt & 1;
+  }
   constexpr int need = (Kind == kDrawU24 || Kind == kDrawF32) ? 1 : 2;
   constexpr int per_block = kWords / need;
   const uint32_t pos_in = pos;
@@ -549,7 +556,7 @@ __global__ void __launch_bounds__(kTcRows* T, T == 1 ? 4 : 1)
           pos = (uint32_t)(rem * need);
         }
       } else if (rem >= per_block) {
-        if constexpr (Kind == kDrawSumHist) {
+        if constexpr (Kind == kDrawSumHist || Kind == kDrawNormal) {
           out.block(D, base + k);
         } else {
           // streams out of step: a bulk copy of this thread's block from its staging
@@ -821,7 +828,7 @@ static_assert(tc_smem_bytes(kTcGroups, true) <= 227 * 1024, "shared memory of a 
 // Tile-groups per CTA of each draw kernel.
 template <int Kind>
 constexpr int tc_groups() {
-  return Kind == kDrawSumHist ? 1 : kTcGroups;
+  return (Kind == kDrawSumHist || Kind == kDrawNormal) ? 1 : kTcGroups;
 }
 
 // cuTensorMapEncodeTiled from the driver, looked up once (null if unavailable).
@@ -877,7 +884,7 @@ cudaError_t launch_tc_kind(const DrawArgs& a, const __half* bimg, cudaStream_t s
   CUtensorMap map;
   std::memset(&map, 0, sizeof(map));
   int use_tma = 0;
-  if constexpr (Kind != kDrawSumHist) use_tma = encode_output_map<Kind>(a, &map) ? 1 : 0;
+  if constexpr (Kind != kDrawSumHist && Kind != kDrawNormal) use_tma = encode_output_map<Kind>(a, &map) ? 1 : 0;
   k_draw_tc<Kind, T><<<grid, kTcRows * T, smem_bytes, st>>>(a, bimg, map, use_tma);
   return cudaGetLastError();
 }
@@ -909,6 +916,7 @@ cudaError_t launch_draw_tc(int kind, const DrawArgs& a, const void* bimg, cudaSt
     case kDrawF64: return launch_tc_kind<kDrawF64>(a, b, st);
     case kDrawSumHist: return launch_tc_kind<kDrawSumHist>(a, b, st);
     case kDrawF32: return launch_tc_kind<kDrawF32>(a, b, st);
+    case kDrawNormal: return launch_tc_kind<kDrawNormal>(a, b, st);
   }
   return cudaErrorInvalidValue;
 }

@@ -105,3 +105,19 @@ def conversion_edge_states(rng, k=40):
         if X3:
             out.append(X3)
     return [x for x in out if 0 < x < M]
+
+
+def normals_expected(doubles, n):
+    """Gaussian values the draw rule gives from each row's doubles (2 ceil(n / 2) of
+    them), with a per-value tolerance: (want, tol), both (rows, n) float64.  The
+    tolerance 2^-49 (r + 1) covers CUDA's stated error bounds of log (1 ulp), sqrt
+    (correctly rounded) and sincospi (2 ulp) on the device, the oracle's own rounding
+    (a few ulp of r and of the cosine and sine), and the products."""
+    d = np.asarray(doubles, dtype=np.float64)
+    da, db = d[:, 0::2], d[:, 1::2]
+    z0, z1 = R.box_muller_many(da, db)
+    want = np.empty_like(d)
+    want[:, 0::2], want[:, 1::2] = z0, z1
+    r = np.sqrt(-2.0 * np.log(1.0 - da))
+    tol = np.repeat(2.0 ** -49 * (r + 1.0), 2, axis=1)
+    return want[:, :n], tol[:, :n]

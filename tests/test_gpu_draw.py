@@ -10,7 +10,7 @@ import pytest
 from oracle import ranluxpp as R
 from oracle import swb_lib as S
 from paper_2106_02504_gb300 import workloads as W
-from tests.oracle_side import StreamSet, from_limbs64, seeded_X
+from tests.oracle_side import StreamSet, normals_expected, from_limbs64, seeded_X
 
 pytestmark = pytest.mark.gpu
 
@@ -178,6 +178,44 @@ def test_tile_stores_heads_and_tails(native, path):
         assert np.array_equal(got[offsets[i]:offsets[i] + counts[i]], w), i
     for kind, count in [(S.KIND_F64, 1000), (S.KIND_U24, 96), (S.KIND_F32, 48)]:
         assert np.array_equal(_draw(native, g, kind, count, N), _want(ref, kind, count)), (kind, count)
+    assert_states(native, g, ref)
+    g.close()
+
+
+def test_draw_normal(native, path):
+    """Gaussian values (Box-Muller on consecutive pairs of doubles) against the oracle
+    within the derived tolerance; odd counts, starts inside a block, ragged counts, a
+    host output buffer; the streams end where the f64 draw of 2 ceil(n / 2) values
+    leaves them."""
+    seeds = W.random_seeds(N, 93)
+    g = make(native, seeds, levels=(389,), path=path)
+    ref = StreamSet.from_seeds(seeds, 389)
+    for kind, count, host in [("n", 1000, False), (S.KIND_U24, 3, False), ("n", 1001, False), (S.KIND_F64, 5, False),
+                              ("n", 7, True), ("n", 1, False), ("n", 0, False)]:
+        if kind != "n":
+            _draw(native, g, kind, count, N)
+            ref.draw(count, kind)
+            continue
+        out = torch.full((N, max(count, 1)), 7.0, dtype=torch.float64, device="cpu" if host else "cuda")
+        g.draw_normal_f64(out, count)
+        got = out.cpu().numpy()[:, :count]
+        want, tol = normals_expected(ref.draw(count + (count & 1), S.KIND_F64), count)
+        assert np.all(np.abs(got - want) <= tol), (count, float(np.max(np.abs(got - want) - tol)))
+        if count == 0:
+            assert np.all(out.cpu().numpy() == 7.0)
+    assert_states(native, g, ref)
+    # ragged counts (odd and even) into one packed output
+    counts, offsets = W.ragged_counts(N, 41, seed=94)
+    out = torch.full((int(counts.sum()) + 1,), 7.0, dtype=torch.float64, device="cuda")
+    g.draw_normal_f64(out, 0, torch.from_numpy(counts).cuda(), torch.from_numpy(offsets).cuda())
+    got = out.cpu().numpy()
+    for i, d in enumerate(ref.draw_ragged(counts + (counts & 1), S.KIND_F64)):
+        c = int(counts[i])
+        if c == 0:
+            continue
+        want, tol = normals_expected(d.reshape(1, -1), c)
+        assert np.all(np.abs(got[offsets[i]:offsets[i] + c] - want[0]) <= tol[0]), i
+    assert got[-1] == 7.0
     assert_states(native, g, ref)
     g.close()
 

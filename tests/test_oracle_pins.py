@@ -387,3 +387,61 @@ def test_skip_values_equals_drawing(need):
         (s.draw_bits48 if need == 2 else s.draw_u24)(n)
         t.skip_values(n, need)
         assert (t.D, t.c, t.pos) == (s.D, s.c, s.pos)
+
+
+# --- Gaussian values (Box-Muller on pairs of doubles) ---------------------------------
+def test_box_muller_closed_forms():
+    import math
+    assert R.box_muller(0.0, 0.3) == (0.0, 0.0)                      # u1 = 1: r = 0
+    for k in (1, 2, 10, 48):
+        d_a = 1.0 - 2.0 ** -k                                         # u1 = 2^-k exactly
+        r = math.sqrt(2 * k * math.log(2.0))
+        assert R.box_muller(d_a, 0.0) == pytest.approx((r, 0.0), rel=1e-15, abs=0)
+        z = R.box_muller(d_a, 0.25)                                   # a quarter turn
+        assert z[0] == 0.0 and z[1] == pytest.approx(r, rel=1e-15)
+        z = R.box_muller(d_a, 0.5)
+        assert z[0] == pytest.approx(-r, rel=1e-15) and z[1] == 0.0
+        z = R.box_muller(d_a, 0.125)                                  # an eighth turn
+        assert z[0] == pytest.approx(r / math.sqrt(2), rel=1e-15) and z[1] == pytest.approx(z[0], rel=1e-15)
+    # the exact quarter-turn reduction against the plain formula
+    rng = random.Random(31)
+    for _ in range(10000):
+        d = rng.randrange(2 ** 48) / 2 ** 48
+        c, s = R.cos_sin_2pi(d)
+        assert abs(c - math.cos(2 * math.pi * d)) < 2e-15 and abs(s - math.sin(2 * math.pi * d)) < 2e-15
+
+
+def test_box_muller_invariants_and_vector_form():
+    import math
+    rng = random.Random(32)
+    da = np.array([rng.randrange(2 ** 48) / 2 ** 48 for _ in range(5000)] + [0.0, 1 - 2 ** -48])
+    db = np.array([rng.randrange(2 ** 48) / 2 ** 48 for _ in range(5002)])
+    z0v, z1v = R.box_muller_many(da, db)
+    for a, b, v0, v1 in zip(da, db, z0v, z1v):
+        z0, z1 = R.box_muller(a, b)
+        rr = -2.0 * math.log(1.0 - a)
+        assert z0 * z0 + z1 * z1 == pytest.approx(rr, rel=1e-13, abs=1e-300)   # radius
+        if rr > 1e-20:                                                          # angle
+            ang = math.atan2(z1, z0) % (2 * math.pi)
+            assert min(abs(ang - 2 * math.pi * b), 2 * math.pi - abs(ang - 2 * math.pi * b)) < 1e-12
+        r = math.sqrt(rr)
+        assert abs(v0 - z0) <= 2 ** -50 * (r + 1) and abs(v1 - z1) <= 2 ** -50 * (r + 1)
+
+
+def test_normal_draws_consume_pairs_and_look_gaussian():
+    import math
+    st, ref = R.Stream(2048, seed=21), R.Stream(2048, seed=21)
+    z = st.draw_normal(7)                                 # odd: 8 doubles taken, 7 values
+    d = ref.draw_f64(8)
+    assert z == [v for k in range(0, 8, 2) for v in R.box_muller(d[k], d[k + 1])][:7]
+    assert st.state() == ref.state()
+    # moments and the Kolmogorov-Smirnov distance to the normal distribution
+    n = 100000
+    s = R.Stream(389, seed=22)
+    x = np.array(s.draw_normal(n))
+    assert abs(x.mean()) < 5 / math.sqrt(n)
+    assert abs(x.var() - 1) < 5 * math.sqrt(2 / n)
+    xs = np.sort(x)
+    cdf = 0.5 * (1 + np.array([math.erf(v / math.sqrt(2)) for v in xs]))
+    ks = max(np.max(np.arange(1, n + 1) / n - cdf), np.max(cdf - np.arange(n) / n))
+    assert ks < 1.63 / math.sqrt(n)                        # 1 % critical value
