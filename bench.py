@@ -471,12 +471,12 @@ def bench_skip(nat, dev):
             "products_per_stream_max": 32, "draw48_ms": ms_draw}
 
 
-def bench_normal(nat, dev):
+def bench_normal(nat, dev, n=1 << 20):
     """Gaussian doubles (Box-Muller on pairs of the streams' doubles): 2^20 streams
     (seeds i + 1, p = 2048), 1024 values each into an 8 GiB device buffer, both paths."""
     import numpy as np
     import torch
-    n, cnt = 1 << 20, 1024
+    cnt = 1024
     seeds = torch.from_numpy(np.arange(1, n + 1, dtype=np.uint64).view(np.int64)).to(dev)
     g = nat.Generator(n, [LUXURY], seeds)
     out = torch.empty((n, cnt), dtype=torch.float64, device=dev)
@@ -562,6 +562,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--only-main", action="store_true", help="skip the other workloads")
+    ap.add_argument("--only-normal", action="store_true",
+                    help="run only the Gaussian workload on --streams streams (for profiling)")
     ap.add_argument("--path", default="imad,tensor", help="refill paths to time; the faster one is reported")
     ap.add_argument("--batch-streams", type=int, default=65536)
     ap.add_argument("--serve-seconds", type=float, default=10.0)
@@ -574,6 +576,13 @@ def main():
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
     if args.impl == "reference":
         return run_reference(args, rank, world)
+    if args.only_normal:
+        import torch
+        from paper_2106_02504_gb300 import build as _b
+        _b.build()
+        import paper_2106_02504_gb300._rlxpp as nat
+        print(json.dumps({"workload": "normal", **bench_normal(nat, torch.device("cuda", local_rank), args.streams)}))
+        return 0
     if world > 1:
         import torch
         import torch.distributed as dist

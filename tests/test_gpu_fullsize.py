@@ -80,3 +80,28 @@ def test_fused_workload_full_size(native):
     # the sampled streams' histogram is bounded by the full histogram bin by bin
     assert (hist.cpu().numpy().view(np.uint64) >= whist).all()
     g.close()
+
+
+@pytest.mark.parametrize("path", ["tensor", "imad"])
+def test_output_past_2_32_elements(native, path):
+    """More than 2^32 output elements in one call (2^20 streams x 4100 u24 = 4.3e9
+    values, 17.2 GB): element offsets, tile coordinates and the tensor map's extents
+    pass 32 bits; sampled streams, the last ones included, equal the oracle."""
+    n, cnt = N, 4100
+    assert n * cnt > 2 ** 32
+    seeds = W.consecutive_seeds(n)
+    g = native.Generator(n, [P], torch.from_numpy(seeds.view(np.int64)).cuda())
+    g.set_path(native.RLXPP_PATH_IMAD if path == "imad" else native.RLXPP_PATH_TENSOR)
+    out = torch.empty((n, cnt), dtype=torch.int32, device="cuda")
+    g.draw_u24(out, cnt)
+    torch.cuda.synchronize()
+    idx = np.array(sorted(set(sample_idx(3, k=200).tolist()) | {n - 129, n - 128, n - 3}))
+    ref = StreamSet.from_seeds(seeds[idx], P)
+    want = ref.draw(cnt, S.KIND_U24)
+    got = out[torch.from_numpy(idx).cuda()].cpu().numpy().view(np.uint32)
+    bad = np.nonzero((got != want).any(axis=1))[0]
+    assert bad.size == 0, f"streams {idx[bad[:5]]} differ"
+    # every value is a 24-bit number
+    assert int(out.max()) < 2 ** 24 and int(out.min()) >= 0
+    del out
+    g.close()
