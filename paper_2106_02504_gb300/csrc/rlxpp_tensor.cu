@@ -764,7 +764,8 @@ __global__ void __launch_bounds__(kTcRows, 4) k_tc_mulmod(const __half* __restri
 }
 
 // The level's matrix in the shared-memory image layout: column j (K index) holds the
-// bytes of R_j = A 2^(8j) mod m for j < 72, the bias 4096 for j = 72, zeros after.
+// bytes of R_j = A 2^(8j) mod m for j < 72, 2^-12 for j = 72 (against 2048: the 1/2
+// bias), the bytes of E as fp16 subnormals e_k 2^-24 for j = 73, zeros after.
 __global__ void k_tc_matrix(const uint32_t* __restrict__ lux, __half* __restrict__ bimg) {
   const int j = threadIdx.x;  // 0..79
   if (j >= kTcK) return;
@@ -815,12 +816,11 @@ __global__ void k_tc_matrix(const uint32_t* __restrict__ lux, __half* __restrict
   }
 }
 
-// Dynamic shared memory per CTA: the two operand tiles, the barrier and the output
-// staging slots (45.6 KB) rounded up so that at most 4 CTAs share an SM, whose 512 TMEM
-// columns then always suffice.
-// One-group CTAs (request and test kernels) take 46 KB, so that at most 4 share an SM,
-// whose 512 TMEM columns then always suffice; the draw kernels run kTcGroups groups
-// per CTA and one CTA per SM.
+// One-group CTAs (the request and test kernels, the fused and Gaussian draws) take
+// 48 KB of dynamic shared memory, so that at most 4 share an SM, whose 512 TMEM columns
+// then always suffice; the value-writing draws run kTcGroups groups per CTA and one CTA
+// per SM.  (Five groups per CTA made the fused draw slower: its per-warp shared-memory
+// histogram took about twice the bank-conflicted atomic wavefronts.)
 constexpr size_t kTcSmem = 48 * 1024;
 static_assert(tc_smem_bytes(1, true) <= (int)kTcSmem, "shared memory layout");
 constexpr int kTcGroups = 5;
