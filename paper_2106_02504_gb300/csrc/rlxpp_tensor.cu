@@ -606,6 +606,40 @@ __global__ void __launch_bounds__(kTcRows* T, T == 1 ? 4 : 1)
   }
 }
 
+// The full blocks of one warp (96 bytes per lane that has one; dst = 0 marks a lane
+// without) written cooperatively: each lane's block is already in its staging slot (the
+// warp's 32 slots are contiguous), and store i of lane l writes unit i 32 + l of the
+// warp's 3072 staged bytes to its block's destination, so one store instruction covers
+// 256 (or 128) consecutive bytes of one to three blocks instead of 32 scattered pieces.
+// 8-byte units when every destination is 8-byte aligned, else 4-byte units.  Every lane
+// of the warp calls it.
+__device__ __forceinline__ void warp_store_blocks(const unsigned char* wstage, uint64_t dst) {
+  const unsigned lane = threadIdx.x & 31u;
+  __syncwarp();  // the lanes' slots are written
+  if (__all_sync(0xFFFFFFFFu, (dst & 7u) == 0)) {
+    const uint64_t* src = reinterpret_cast<const uint64_t*>(wstage);
+#pragma unroll
+    for (int i = 0; i < 12; ++i) {
+      const unsigned u = i * 32u + lane;  // = 12 t + w: unit w of lane t's block
+      const unsigned t = u / 12u, w = u - 12u * t;
+      const uint64_t p = __shfl_sync(0xFFFFFFFFu, dst, (int)t);
+      const uint64_t val = src[u];
+      if (p) reinterpret_cast<uint64_t*>(p)[w] = val;
+    }
+  } else {
+    const uint32_t* src = reinterpret_cast<const uint32_t*>(wstage);
+#pragma unroll 4
+    for (int i = 0; i < 24; ++i) {
+      const unsigned u = i * 32u + lane;  // = 24 t + w
+      const unsigned t = u / 24u, w = u - 24u * t;
+      const uint64_t p = __shfl_sync(0xFFFFFFFFu, dst, (int)t);
+      const uint32_t val = src[u];
+      if (p) reinterpret_cast<uint32_t*>(p)[w] = val;
+    }
+  }
+  __syncwarp();  // the slots may be written again
+}
+
 // Emits the unread part of the current block for a value kind (f64 or u24).
 __device__ __forceinline__ void emit_head(bool f64, const BatchArgs& b, const uint32_t D[kLimbs], uint32_t& pos,
                                           int64_t cnt, int64_t base, int64_t& k) {
@@ -637,6 +671,8 @@ __global__ void __launch_bounds__(kTcRows, 4) k_requests_tc(const BatchArgs b, c
   extern __shared__ __align__(1024) unsigned char smem[];
   const TcGroup G = tc_group(smem, true);  // one group per CTA
   const __half* bmat = tc_bmat(smem);
+  uint4* slot = reinterpret_cast<uint4*>(G.stage + G.t * kStageBytes);
+  const unsigned char* wstage = G.stage + (G.t & ~31) * kStageBytes;  // this warp's 32 slots
   const int tid = threadIdx.x;
   tc_setup(smem, G, bimg, 1);
   const uint32_t taddr = tc_tmem(smem, G);
@@ -687,6 +723,7 @@ __global__ void __launch_bounds__(kTcRows, 4) k_requests_tc(const BatchArgs b, c
     }
     uint32_t Xn[kLimbs];
     columns_to_x(col, Xn);
+    uint64_t dst = 0;  // destination of this lane's full block, if it has one
     if (mine) {
 #pragma unroll
       for (int q = 0; q < kLimbs; ++q) X[q] = Xn[q];
@@ -695,11 +732,15 @@ __global__ void __launch_bounds__(kTcRows, 4) k_requests_tc(const BatchArgs b, c
       const int64_t per = f64 ? kDoubles : kWords;
       const int64_t rem = cnt - k;
       if (rem >= per) {
-        // chunks write to unrelated places: direct vector stores (32 bytes when aligned)
+        // chunks write to unrelated places: staged here, written by the whole warp below
+        uint4 v[6];
         if (f64)
-          store_block_f64(b.out_f64 + base + k, D);
+          block_values<kDrawF64>(D, v);
         else
-          store_block_u24(b.out_u24 + base + k, D);
+          block_values<kDrawU24>(D, v);
+#pragma unroll
+        for (int q = 0; q < 6; ++q) slot[q] = v[q];
+        dst = f64 ? reinterpret_cast<uint64_t>(b.out_f64 + base + k) : reinterpret_cast<uint64_t>(b.out_u24 + base + k);
         k += per;
         pos = kWords;
       } else {
@@ -718,6 +759,7 @@ __global__ void __launch_bounds__(kTcRows, 4) k_requests_tc(const BatchArgs b, c
       }
       mine = k < cnt;
     }
+    warp_store_blocks(wstage, dst);
   }
   bulk_wait_all();
   if (!ok) {
