@@ -425,12 +425,49 @@ __device__ __forceinline__ void tc_teardown(unsigned char* smem, const TcGroup& 
   if (threadIdx.x < 32) tmem_dealloc(tc_sh0(smem)->taddr, tc_alloc_cols(groups));
 }
 
+// The full blocks of one warp (96 bytes per lane that has one; dst = 0 marks a lane
+// without) written cooperatively: each lane's block is already in its staging slot (the
+// warp's 32 slots are contiguous), and store i of lane l writes unit i 32 + l of the
+// warp's 3072 staged bytes to its block's destination, so one store instruction covers
+// 256 (or 128) consecutive bytes of one to three blocks instead of 32 scattered pieces.
+// 8-byte units when every destination is 8-byte aligned, else 4-byte units.  Every lane
+// of the warp calls it.
+__device__ __forceinline__ void warp_store_blocks(const unsigned char* wstage, uint64_t dst) {
+  const unsigned lane = threadIdx.x & 31u;
+  __syncwarp();  // the lanes' slots are written
+  if (__all_sync(0xFFFFFFFFu, (dst & 7u) == 0)) {
+    const uint64_t* src = reinterpret_cast<const uint64_t*>(wstage);
+#pragma unroll
+    for (int i = 0; i < 12; ++i) {
+      const unsigned u = i * 32u + lane;  // = 12 t + w: unit w of lane t's block
+      const unsigned t = u / 12u, w = u - 12u * t;
+      const uint64_t p = __shfl_sync(0xFFFFFFFFu, dst, (int)t);
+      const uint64_t val = src[u];
+      if (p) reinterpret_cast<uint64_t*>(p)[w] = val;
+    }
+  } else {
+    const uint32_t* src = reinterpret_cast<const uint32_t*>(wstage);
+#pragma unroll 4
+    for (int i = 0; i < 24; ++i) {
+      const unsigned u = i * 32u + lane;  // = 24 t + w
+      const unsigned t = u / 24u, w = u - 24u * t;
+      const uint64_t p = __shfl_sync(0xFFFFFFFFu, dst, (int)t);
+      const uint32_t val = src[u];
+      if (p) reinterpret_cast<uint32_t*>(p)[w] = val;
+    }
+  }
+  __syncwarp();  // the slots may be written again
+}
+
 // Draw kernel on the tensor path (single-level handles).  Same semantics as k_draw.
 // A CTA holds T tile-groups (one SM's worth), each refilling its own tile of 128
 // streams independently of the others.  tmap (when use_tma): the output as a
 // [n][count_each] tensor of 4- or 8-byte elements with a [128][per block] box, for the
 // tile-wide stores of tiles whose streams move in step.
-template <int Kind, int T>
+// Coop: the launch has no tensor map (use_tma = 0) and every tile writes its blocks by
+// warp-cooperative stores; otherwise tiles out of step copy each lane's block by a bulk
+// copy (this form keeps the registers of the tile-store path free).
+template <int Kind, int T, bool Coop>
 __global__ void __launch_bounds__(kTcRows* T, T == 1 ? 4 : 1)
     k_draw_tc(const DrawArgs a, const __half* __restrict__ bimg, const __grid_constant__ CUtensorMap tmap,
               int use_tma) {
@@ -439,6 +476,7 @@ __global__ void __launch_bounds__(kTcRows* T, T == 1 ? 4 : 1)
   const TcGroup G = tc_group(smem, kStaging);
   const __half* bmat = tc_bmat(smem);
   uint4* slot = reinterpret_cast<uint4*>(G.stage + G.t * kStageBytes);
+  const unsigned char* wstage = G.stage + (G.t & ~31) * kStageBytes;  // this warp's 32 slots
   __shared__ unsigned int hist_s[Kind == kDrawSumHist ? 4 * T * 256 : 1];  // one histogram per warp
   const int tid = threadIdx.x;
   if (Kind == kDrawSumHist)
@@ -509,7 +547,7 @@ __global__ void __launch_bounds__(kTcRows* T, T == 1 ? 4 : 1)
   // is live whenever any thread of the group is).
   TileStore store;
   bool tma = false;
-  if constexpr (Kind != kDrawSumHist) {
+  if constexpr (Kind != kDrawSumHist && !Coop) {
     if (use_tma) {  // uniform over the grid
       if (G.t == 0) G.sh->pos0 = pos_in;
       group_sync(G);
@@ -532,6 +570,7 @@ __global__ void __launch_bounds__(kTcRows* T, T == 1 ? 4 : 1)
     }
     uint32_t Xn[kLimbs];
     columns_to_x(col, Xn);
+    uint64_t dst = 0;  // destination of this lane's full block (streams out of step)
     if (mine) {
 #pragma unroll
       for (int q = 0; q < kLimbs; ++q) X[q] = Xn[q];
@@ -558,14 +597,21 @@ __global__ void __launch_bounds__(kTcRows* T, T == 1 ? 4 : 1)
       } else if (rem >= per_block) {
         if constexpr (Kind == kDrawSumHist || Kind == kDrawNormal) {
           out.block(D, base + k);
+        } else if constexpr (Coop) {
+          // staged here, written by the whole warp below
+          uint4 v[6];
+          block_values<Kind>(D, v);
+#pragma unroll
+          for (int q = 0; q < 6; ++q) slot[q] = v[q];
+          dst = reinterpret_cast<uint64_t>(out.out + base + k);
         } else {
-          // streams out of step: a bulk copy of this thread's block from its staging
-          // slot (fewer registers than vector stores in this kernel)
-          void* dst = out.out + base + k;
-          if ((reinterpret_cast<uintptr_t>(dst) & 15) == 0) {
+          // streams out of step in a launch with tile-wide stores: a bulk copy of this
+          // lane's block from its staging slot
+          void* gdst = out.out + base + k;
+          if ((reinterpret_cast<uintptr_t>(gdst) & 15) == 0) {
             uint4 v[6];
             block_values<Kind>(D, v);
-            bulk_store96(dst, slot, v);
+            bulk_store96(gdst, slot, v);
           } else {
             out.block(D, base + k);
           }
@@ -579,6 +625,7 @@ __global__ void __launch_bounds__(kTcRows* T, T == 1 ? 4 : 1)
       }
       mine = k < cnt;
     }
+    if constexpr (Coop) warp_store_blocks(wstage, dst);
   }
   if (tma && G.t == 0 && store.pending) tile_store_issue(store);  // the last blocks
   if (Kind != kDrawSumHist) bulk_wait_all();  // this thread's output copies are done
@@ -604,40 +651,6 @@ __global__ void __launch_bounds__(kTcRows* T, T == 1 ? 4 : 1)
       if (tot) atomicAdd(a.hist + t, tot);
     }
   }
-}
-
-// The full blocks of one warp (96 bytes per lane that has one; dst = 0 marks a lane
-// without) written cooperatively: each lane's block is already in its staging slot (the
-// warp's 32 slots are contiguous), and store i of lane l writes unit i 32 + l of the
-// warp's 3072 staged bytes to its block's destination, so one store instruction covers
-// 256 (or 128) consecutive bytes of one to three blocks instead of 32 scattered pieces.
-// 8-byte units when every destination is 8-byte aligned, else 4-byte units.  Every lane
-// of the warp calls it.
-__device__ __forceinline__ void warp_store_blocks(const unsigned char* wstage, uint64_t dst) {
-  const unsigned lane = threadIdx.x & 31u;
-  __syncwarp();  // the lanes' slots are written
-  if (__all_sync(0xFFFFFFFFu, (dst & 7u) == 0)) {
-    const uint64_t* src = reinterpret_cast<const uint64_t*>(wstage);
-#pragma unroll
-    for (int i = 0; i < 12; ++i) {
-      const unsigned u = i * 32u + lane;  // = 12 t + w: unit w of lane t's block
-      const unsigned t = u / 12u, w = u - 12u * t;
-      const uint64_t p = __shfl_sync(0xFFFFFFFFu, dst, (int)t);
-      const uint64_t val = src[u];
-      if (p) reinterpret_cast<uint64_t*>(p)[w] = val;
-    }
-  } else {
-    const uint32_t* src = reinterpret_cast<const uint32_t*>(wstage);
-#pragma unroll 4
-    for (int i = 0; i < 24; ++i) {
-      const unsigned u = i * 32u + lane;  // = 24 t + w
-      const unsigned t = u / 24u, w = u - 24u * t;
-      const uint64_t p = __shfl_sync(0xFFFFFFFFu, dst, (int)t);
-      const uint32_t val = src[u];
-      if (p) reinterpret_cast<uint32_t*>(p)[w] = val;
-    }
-  }
-  __syncwarp();  // the slots may be written again
 }
 
 // Emits the unread part of the current block for a value kind (f64 or u24).
@@ -919,15 +932,17 @@ cudaError_t launch_tc_kind(const DrawArgs& a, const __half* bimg, cudaStream_t s
   constexpr int T = tc_groups<Kind>();
   // one-group CTAs keep 48 KB so that at most 4 share an SM (512 TMEM columns)
   constexpr int smem_bytes = T == 1 ? (int)kTcSmem : tc_smem_bytes(T, Kind != kDrawSumHist);
-  cudaError_t e = cudaFuncSetAttribute(k_draw_tc<Kind, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes);
-  if (e != cudaSuccess) return e;
+  constexpr bool kValues = Kind == kDrawU24 || Kind == kDrawF64 || Kind == kDrawF32;
   const uint64_t tiles = (a.s.n + kTcRows - 1) / kTcRows;
   const unsigned grid = (unsigned)((tiles + T - 1) / T);
   CUtensorMap map;
   std::memset(&map, 0, sizeof(map));
   int use_tma = 0;
-  if constexpr (Kind != kDrawSumHist && Kind != kDrawNormal) use_tma = encode_output_map<Kind>(a, &map) ? 1 : 0;
-  k_draw_tc<Kind, T><<<grid, kTcRows * T, smem_bytes, st>>>(a, bimg, map, use_tma);
+  if constexpr (kValues) use_tma = encode_output_map<Kind>(a, &map) ? 1 : 0;
+  auto kern = (kValues && !use_tma) ? k_draw_tc<Kind, T, kValues> : k_draw_tc<Kind, T, false>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes);
+  if (e != cudaSuccess) return e;
+  kern<<<grid, kTcRows * T, smem_bytes, st>>>(a, bimg, map, use_tma);
   return cudaGetLastError();
 }
 
