@@ -16,6 +16,7 @@ by itself, smallest first, each group with its own event.
 from __future__ import annotations
 
 import collections
+import gc
 import time
 from dataclasses import dataclass, field
 
@@ -241,23 +242,32 @@ class Server:
 
     # -- trace replay ---------------------------------------------------------------------
     def run_trace(self, arrival_s, stream, count, is_f64, duration=None):
-        """Release requests at their (wall-clock) arrival times; returns stats."""
+        """Release requests at their (wall-clock) arrival times; returns stats.  Python's
+        cyclic garbage collector is paused meanwhile: its full passes over the many live
+        request objects would stall the loop and every request in flight with it."""
         n = len(arrival_s)
         if duration is not None:
             n = int(np.searchsorted(arrival_s, duration))
-        self.t0 = time.perf_counter()
-        i = 0
-        while i < n or self.waiting or self.admitted or self.inflight:
-            t = self.now()
-            while i < n and arrival_s[i] <= t:
-                self.submit(i, stream[i], KIND_F64 if is_f64[i] else KIND_U24, count[i], arrival=float(arrival_s[i]))
-                i += 1
-            self.pump()
-            if i < n and not self.admitted and not self.waiting:
-                gap = arrival_s[i] - self.now()
-                if gap > 2e-4 and not self.inflight:
-                    time.sleep(min(gap, 1e-3))
-        self.torch.cuda.synchronize()
+        was_enabled = gc.isenabled()
+        gc.disable()
+        try:
+            self.t0 = time.perf_counter()
+            i = 0
+            while i < n or self.waiting or self.admitted or self.inflight:
+                t = self.now()
+                while i < n and arrival_s[i] <= t:
+                    self.submit(i, stream[i], KIND_F64 if is_f64[i] else KIND_U24, count[i],
+                                arrival=float(arrival_s[i]))
+                    i += 1
+                self.pump()
+                if i < n and not self.admitted and not self.waiting:
+                    gap = arrival_s[i] - self.now()
+                    if gap > 2e-4 and not self.inflight:
+                        time.sleep(min(gap, 1e-3))
+            self.torch.cuda.synchronize()
+        finally:
+            if was_enabled:
+                gc.enable()
         return self.stats()
 
     def stats(self):
