@@ -253,10 +253,15 @@ rlxpp_status rlxpp_sync(rlxpp_gen* gen, void* cuda_stream);
  * one 128 x 80 x 80 product per refill (Sec. 2.1-2.2 computed differently, same
  * result).  It serves the plain draws of single-level handles (a tile's streams share
  * one multiplier; plain draws of multi-level handles use the integer kernel) and every
- * batched request (chunks are grouped by level).  Synchronises the device.  Both paths
- * give bit-identical results. */
+ * batched request (chunks are grouped by level).
+ * RLXPP_PATH_WARP: the plain draws (u24, f32, f64, fused sum/histogram) with one warp
+ * per stream, lane l holding limb l, every multi-limb sum's carries resolved across the
+ * warp at once: for few streams, where the latency of one refill counts (a single
+ * stream read in order); Gaussian draws and batched requests of such a handle use the
+ * integer kernels.  All paths give bit-identical results.  Synchronises the device. */
 #define RLXPP_PATH_IMAD 0u
 #define RLXPP_PATH_TENSOR 1u
+#define RLXPP_PATH_WARP 2u
 rlxpp_status rlxpp_set_path(rlxpp_gen* gen, uint32_t path);
 uint32_t rlxpp_get_path(const rlxpp_gen* gen);
 

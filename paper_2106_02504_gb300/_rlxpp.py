@@ -34,7 +34,7 @@ class RlxppTuning(ctypes.Structure):
 
 
 RLXPP_KIND_U24, RLXPP_KIND_F64, RLXPP_KIND_F32 = 0, 1, 2
-RLXPP_PATH_IMAD, RLXPP_PATH_TENSOR = 0, 1
+RLXPP_PATH_IMAD, RLXPP_PATH_TENSOR, RLXPP_PATH_WARP = 0, 1, 2
 RLXPP_REQ_ADVANCE = 1
 
 
@@ -263,8 +263,9 @@ def _tuning(t, gen=None):
     if isinstance(t, RlxppTuning):
         return ctypes.byref(t)
     t = tuple(t)
-    if len(t) == 2:
-        t = t + (rlxpp_get_path(gen) if gen else RLXPP_PATH_TENSOR,)
+    if len(t) == 2:  # requests run on the integer or the tensor kernel
+        t = t + (RLXPP_PATH_TENSOR if (rlxpp_get_path(gen) if gen else RLXPP_PATH_TENSOR) == RLXPP_PATH_TENSOR
+                 else RLXPP_PATH_IMAD,)
     return ctypes.byref(RlxppTuning(*t))
 
 

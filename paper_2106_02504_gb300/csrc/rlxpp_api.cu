@@ -134,9 +134,11 @@ DrawArgs make_args(const rlxpp_gen* g) {
 constexpr size_t kChunkBytes = size_t(256) << 20;  // device staging per chunk of host output
 
 // The draw kernels of the handle's path: tensor cores when the handle has one luxury
-// level (a tile's streams share the multiplier matrix), else the integer pipe.
+// level (a tile's streams share the multiplier matrix), one warp per stream for the
+// kinds the warp kernel has, else the integer pipe.
 cudaError_t launch_path(const rlxpp_gen* g, int kind, const DrawArgs& a, cudaStream_t st) {
   if (g->path == RLXPP_PATH_TENSOR && g->n_levels == 1) return launch_draw_tc(kind, a, g->tc_matrix, st);
+  if (g->path == RLXPP_PATH_WARP && warp_draw_supported(kind)) return launch_draw_warp(kind, a, st);
   return launch_draw(kind, a, st);
 }
 
@@ -451,7 +453,8 @@ rlxpp_status rlxpp_sync(rlxpp_gen* g, void* cuda_stream) {
 
 rlxpp_status rlxpp_set_path(rlxpp_gen* g, uint32_t path) {
   if (rlxpp_status s = check_gen(g)) return s;
-  if (path != RLXPP_PATH_IMAD && path != RLXPP_PATH_TENSOR) return fail(RLXPP_ERR_INVALID, "unknown path");
+  if (path != RLXPP_PATH_IMAD && path != RLXPP_PATH_TENSOR && path != RLXPP_PATH_WARP)
+    return fail(RLXPP_ERR_INVALID, "unknown path");
   if (path == RLXPP_PATH_TENSOR && !g->tc_matrix) return fail(RLXPP_ERR_CUDA, "tensor matrix missing");
   RLX_CUDA(cudaDeviceSynchronize());  // no draw of the old path may still run
   g->path = path;

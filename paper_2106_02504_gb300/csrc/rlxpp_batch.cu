@@ -238,7 +238,7 @@ rlxpp_status plan_impl(rlxpp_gen* g, const rlxpp_request* reqs, uint64_t n_reqs,
       uint64_t L = total_refills / std::max<uint64_t>(threads, 1);
       uint32_t p2 = 4;
       while (p2 < L && p2 < 256) p2 <<= 1;
-      t = rlxpp_tuning{p2, 4, g->path};
+      t = rlxpp_tuning{p2, 4, g->path == RLXPP_PATH_TENSOR ? RLXPP_PATH_TENSOR : RLXPP_PATH_IMAD};
     }
   }
   if (t.chunk_blocks < 2 || t.blocks_per_sm < 1 || t.blocks_per_sm > 8 ||

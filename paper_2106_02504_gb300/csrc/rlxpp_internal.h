@@ -70,6 +70,9 @@ cudaError_t launch_skip(const StateView& s, const uint64_t* n128, cudaStream_t s
 // move each stream as if n[i] values of `need` numbers each had been drawn
 cudaError_t launch_skip_values(const StateView& s, const uint64_t* n, uint32_t need, cudaStream_t st);
 cudaError_t launch_draw(int kind, const DrawArgs& a, cudaStream_t st);
+// one warp per stream (RLXPP_PATH_WARP); warp_draw_supported: the kinds it has
+bool warp_draw_supported(int kind);
+cudaError_t launch_draw_warp(int kind, const DrawArgs& a, cudaStream_t st);
 cudaError_t launch_export(const StateView& s, const uint32_t* level_p, rlxpp_state* dst,
                           cudaStream_t st);
 cudaError_t launch_import(const StateView& s, const uint32_t* level_p, uint32_t n_levels,

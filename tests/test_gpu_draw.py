@@ -50,16 +50,20 @@ def f64_bits(t):
 N = 300  # three blocks of 128 threads and a ragged tail
 
 
-@pytest.fixture(params=["tensor", "imad"])
+@pytest.fixture(params=["tensor", "imad", "warp"])
 def path(request):
     return request.param
+
+
+def path_id(native, path):
+    return {"imad": native.RLXPP_PATH_IMAD, "tensor": native.RLXPP_PATH_TENSOR, "warp": native.RLXPP_PATH_WARP}[path]
 
 
 def make(native, seeds, levels=(2048,), level_of=None, path=None):
     lo = None if level_of is None else torch.from_numpy(np.asarray(level_of, dtype=np.uint8)).cuda()
     g = native.Generator(len(seeds), list(levels), dev_u64(seeds), lo)
-    if path is not None and len(levels) == 1:
-        g.set_path(native.RLXPP_PATH_IMAD if path == "imad" else native.RLXPP_PATH_TENSOR)
+    if path is not None and (len(levels) == 1 or path == "warp"):
+        g.set_path(path_id(native, path))
     return g
 
 
@@ -216,6 +220,17 @@ def test_draw_normal(native, path):
         want, tol = normals_expected(d.reshape(1, -1), c)
         assert np.all(np.abs(got[offsets[i]:offsets[i] + c] - want[0]) <= tol[0]), i
     assert got[-1] == 7.0
+    assert_states(native, g, ref)
+    g.close()
+
+
+def test_warp_path_single_stream(native):
+    """One stream read in order on the warp path (one warp per stream): 100,001 doubles,
+    then 50,001 u24 and 777 f32, every value and the final state against the oracle."""
+    g = make(native, np.array([1], dtype=np.uint64), path="warp")
+    ref = StreamSet.from_seeds([1], 2048)
+    for kind, count in [(S.KIND_F64, 100001), (S.KIND_U24, 50001), (S.KIND_F32, 777)]:
+        assert np.array_equal(_draw(native, g, kind, count, 1), _want(ref, kind, count)), kind
     assert_states(native, g, ref)
     g.close()
 
