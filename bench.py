@@ -362,8 +362,15 @@ def bench_single_stream(nat, dev):
     st = torch.cuda.current_stream()
     g = nat.Generator(1, [LUXURY], torch.ones(1, dtype=torch.int64, device=dev))
     out = torch.empty(n, dtype=torch.float64, device=dev)
-    ms_serial = _time_events(lambda: nat.rlxpp_draw_f64(g.handle, out, n, None, None, st.cuda_stream), 2, st)
     adv = advances_for(n, 0)[0]
+    serial = {}
+    for name, pid in (("warp", nat.RLXPP_PATH_WARP), ("tensor", nat.RLXPP_PATH_TENSOR), ("imad", nat.RLXPP_PATH_IMAD)):
+        g.set_path(pid)
+        ms = _time_events(lambda: nat.rlxpp_draw_f64(g.handle, out, n, None, None, st.cuda_stream), 2, st)
+        serial[name] = {"ms": ms, "ns_per_advance": ms * 1e6 / adv}
+    best = min(serial, key=lambda k: serial[k]["ms"])
+    ms_serial = serial[best]["ms"]
+    g.set_path(nat.RLXPP_PATH_TENSOR)
     req = np.zeros(1, dtype=nat.request_dtype())
     req[0] = (0, 0, 0, nat.RLXPP_KIND_F64, n, 0)
     tuning = nat.rlxpp_autotune_requests(g.handle, req, None, out)
@@ -374,7 +381,7 @@ def bench_single_stream(nat, dev):
     g.close()
     return {"doubles": n, "advances": adv,
             "serial": {"ms": ms_serial, "doubles_per_s": n / (ms_serial * 1e-3),
-                       "ns_per_advance": ms_serial * 1e6 / adv},
+                       "ns_per_advance": ms_serial * 1e6 / adv, "path": best, "by_path": serial},
             "split": {"ms": ms_split, "doubles_per_s": n / (ms_split * 1e-3), "chunks": items,
                       "tuning": {"chunk_blocks": tuning[0], "blocks_per_sm": tuning[1], "path": tuning[2]}}}
 
