@@ -320,7 +320,7 @@ def run_native(args, rank, world, local_rank):
         result["e2e"] = run_e2e(args, nat, g, seeds_h, n, world, dev, dist)
     g.close()
     del out
-    if not args.only_main:
+    if not args.only_main and world == 1:  # single-GPU workloads: reported at N = 1
         torch.cuda.empty_cache()
         result["other_workloads"] = {
             "single_stream": bench_single_stream(nat, dev),
@@ -329,7 +329,7 @@ def run_native(args, rank, world, local_rank):
             "normal": bench_normal(nat, dev),
             "serving": bench_serving(args),
         }
-    if rank == 0 and not args.no_cpu_baseline:
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
         dt, doubles, threads = cpu_oracle_sample(args.cpu_sample, 1)
         result["cpu_baseline"] = {
             "value": doubles / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
