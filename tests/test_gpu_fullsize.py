@@ -105,3 +105,97 @@ def test_output_past_2_32_elements(native, path):
     assert int(out.max()) < 2 ** 24 and int(out.min()) >= 0
     del out
     g.close()
+
+
+def test_config1_single_stream_serial_full_size(native):
+    """One stream (seed 1, p = 2048) read in order on the path bench.py times for it (one
+    warp per stream): 2^20 doubles, and separately 2^20 u24 from a fresh seed-1 state,
+    every value against the oracle."""
+    n = 1 << 20
+    for kind in (S.KIND_F64, S.KIND_U24):
+        g = native.Generator(1, [P], torch.ones(1, dtype=torch.int64, device="cuda"))
+        g.set_path(native.RLXPP_PATH_WARP)
+        dt = torch.float64 if kind == S.KIND_F64 else torch.int32
+        out = torch.empty(n, dtype=dt, device="cuda")
+        (g.draw_f64 if kind == S.KIND_F64 else g.draw_u24)(out, n)
+        torch.cuda.synchronize()
+        ref = StreamSet.from_seeds([1], P)
+        want = ref.draw(n, kind)[0]
+        got = out.cpu().numpy()
+        if kind == S.KIND_F64:
+            assert np.array_equal(got.view(np.uint64), want.view(np.uint64))
+        else:
+            assert np.array_equal(got.view(np.uint32), want)
+        st = torch.zeros((1, 11), dtype=torch.int64, device="cuda")
+        g.get_state(st)
+        assert np.array_equal(st.cpu().numpy().view(np.uint64), ref.state_records())
+        g.close()
+
+
+def test_config3_mixed_batch_full_size(native):
+    """The mixed batch at full size (65,536 streams, levels {24, 223, 389, 2048}, counts
+    log-uniform in [1, 10^6], u24/f64 50/50, seeds i + 1) as one planned run on the tensor
+    request kernel: sampled requests, the longest included, equal the oracle value by
+    value; the output totals and the untouched tail are checked whole."""
+    import paper_2106_02504_gb300._rlxpp as B
+    n = 65536
+    levels, lvl, counts, is_f64 = W.batch_mix(n, seed=3)
+    seeds = np.arange(1, n + 1, dtype=np.uint64)
+    g = native.Generator(n, levels, torch.from_numpy(seeds.view(np.int64)).cuda(), torch.from_numpy(lvl).cuda())
+    reqs = np.zeros(n, dtype=B.request_dtype())
+    reqs["stream"] = np.arange(n)
+    reqs["kind"] = is_f64.astype(np.uint32)
+    reqs["count"] = counts
+    off = np.zeros(n, dtype=np.int64)
+    for k in (0, 1):
+        sel = is_f64 == bool(k)
+        off[sel] = np.concatenate([[0], np.cumsum(counts[sel])[:-1]])
+    reqs["offset"] = off
+    nf, nu = int(counts[is_f64].sum()), int(counts[~is_f64].sum())
+    out_f = torch.full((nf + 1,), -1, dtype=torch.int64, device="cuda")
+    out_u = torch.full((nu + 1,), -1, dtype=torch.int32, device="cuda")
+    plan = native.rlxpp_plan_requests(g.handle, reqs, 0, (128, 4, native.RLXPP_PATH_TENSOR))
+    native.rlxpp_run_plan(g.handle, plan, out_u, out_f)
+    torch.cuda.synchronize()
+    native.rlxpp_destroy_plan(plan)
+    assert int(out_f[-1]) == -1 and int(out_u[-1]) == -1            # nothing past the outputs
+    assert int((out_u[:-1] < 0).sum()) == 0 and int((out_u[:-1] >= 2 ** 24).sum()) == 0
+    rng = np.random.Generator(np.random.PCG64(17))
+    sample = set(rng.choice(n, size=40, replace=False).tolist()) | set(np.argsort(counts)[-4:].tolist())
+    for i in sorted(sample):
+        ref = StreamSet.from_seeds([int(seeds[i])], levels[int(lvl[i])])
+        c, o = int(counts[i]), int(off[i])
+        if is_f64[i]:
+            want = ref.draw(c, S.KIND_F64)[0].view(np.uint64)
+            got = out_f[o:o + c].cpu().numpy().view(np.uint64)
+        else:
+            want = ref.draw(c, S.KIND_U24)[0]
+            got = out_u[o:o + c].cpu().numpy().view(np.uint32)
+        assert np.array_equal(got, want), (i, c)
+    g.close()
+
+
+def test_config4_skips_full_size(native):
+    """2^18 streams (seeds i + 1, p = 2048) skipped by uniform 128-bit distances, then 48
+    doubles each, as bench.py times it: sampled streams against pow(A, n, m)."""
+    from oracle import ranluxpp as R
+    from tests.oracle_side import seeded_X
+    n = 1 << 18
+    seeds = W.consecutive_seeds(n)
+    g = native.Generator(n, [P], torch.from_numpy(seeds.view(np.int64)).cuda())
+    dist = W.skip_distances(n, seed=4)
+    g.skip(torch.from_numpy(dist.view(np.int64)).cuda())
+    out = torch.empty((n, 48), dtype=torch.float64, device="cuda")
+    g.draw_f64(out, 48)
+    torch.cuda.synchronize()
+    rng = np.random.Generator(np.random.PCG64(18))
+    idx = np.array(sorted(set(rng.choice(n, size=300, replace=False).tolist()) | {0, n - 1}))
+    A = R.luxury_multiplier(P)
+    xs = seeded_X(seeds[idx], P)
+    got = out[torch.from_numpy(idx).cuda()].cpu().numpy().view(np.uint64)
+    for r, i in enumerate(idx):
+        d = int(dist[i, 0]) | (int(dist[i, 1]) << 64)
+        X = pow(A, d, R.M) * xs[int(seeds[i])] % R.M
+        want = StreamSet([X], P).draw(48, S.KIND_F64)[0].view(np.uint64)
+        assert np.array_equal(got[r], want), i
+    g.close()
