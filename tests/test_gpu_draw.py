@@ -358,17 +358,35 @@ def test_noncanonical_record_rejected(native):
         g.sync()
 
 
-def test_mixed_levels(native):
+def test_mixed_levels(native, path):
+    # per-stream multipliers: the integer kernel for the tensor path (its tiles share one
+    # level), the warp kernel's per-level loads for the warp path
     levels, lvl_idx, _, _ = W.batch_mix(N, seed=81)
     seeds = W.random_seeds(N, 82)
-    g = make(native, seeds, levels=levels, level_of=lvl_idx)
+    g = make(native, seeds, levels=levels, level_of=lvl_idx, path=path)
     out = torch.zeros((N, 40), dtype=torch.float64, device="cuda")
     g.draw_f64(out, 40)
     got = f64_bits(out)
+    refs = []
     for li, p in enumerate(levels):
         idx = np.nonzero(lvl_idx == li)[0]
         ref = StreamSet.from_seeds(seeds[idx], p)
         assert np.array_equal(got[idx], ref.draw(40, S.KIND_F64).view(np.uint64)), p
+        refs.append((idx, ref))
+    # the fused consumer, then u24, on the same handle
+    sums = torch.zeros(N, dtype=torch.int64, device="cuda")
+    hist = torch.zeros(256, dtype=torch.int64, device="cuda")
+    g.draw_f64_sum_hist(300, sums, hist)
+    out_u = torch.zeros((N, 30), dtype=torch.int32, device="cuda")
+    g.draw_u24(out_u, 30)
+    gs = sums.cpu().numpy().view(np.uint64)
+    gu = out_u.cpu().numpy().view(np.uint32)
+    for idx, ref in refs:
+        ws, _ = ref.sum_hist(300)
+        assert np.array_equal(gs[idx], ws)
+        assert np.array_equal(gu[idx], ref.draw(30, S.KIND_U24))
+    assert int(hist.sum()) == N * 300
+    g.close()
 
 
 def test_reseed(native):
