@@ -327,6 +327,7 @@ def run_native(args, rank, world, local_rank):
             "mixed_batch": bench_mixed_batch(nat, dev, args),
             "skip": bench_skip(nat, dev),
             "normal": bench_normal(nat, dev),
+            "exponential": bench_normal(nat, dev, exponential=True),
             "serving": bench_serving(args),
         }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -478,9 +479,10 @@ def bench_skip(nat, dev):
             "products_per_stream_max": 32, "draw48_ms": ms_draw}
 
 
-def bench_normal(nat, dev, n=1 << 20):
-    """Gaussian doubles (Box-Muller on pairs of the streams' doubles): 2^20 streams
-    (seeds i + 1, p = 2048), 1024 values each into an 8 GiB device buffer, both paths."""
+def bench_normal(nat, dev, n=1 << 20, exponential=False):
+    """Gaussian doubles (Box-Muller on pairs of the streams' doubles), or exponential
+    doubles (inversion, one double each): 2^20 streams (seeds i + 1, p = 2048), 1024
+    values each into an 8 GiB device buffer, both paths."""
     import numpy as np
     import torch
     cnt = 1024
@@ -491,7 +493,8 @@ def bench_normal(nat, dev, n=1 << 20):
     res = {"streams": n, "values_per_stream": cnt}
     for name, pid in (("tensor", nat.RLXPP_PATH_TENSOR), ("imad", nat.RLXPP_PATH_IMAD)):
         g.set_path(pid)
-        ms = _time_events(lambda: nat.rlxpp_draw_normal_f64(g.handle, out, cnt, None, None, st.cuda_stream), 3, st)
+        fn = nat.rlxpp_draw_exp_f64 if exponential else nat.rlxpp_draw_normal_f64
+        ms = _time_events(lambda: fn(g.handle, out, cnt, None, None, st.cuda_stream), 3, st)
         res[name] = {"ms": ms, "values_per_s": n * cnt / (ms * 1e-3)}
     g.sync()
     g.close()
@@ -570,7 +573,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--only-main", action="store_true", help="skip the other workloads")
     ap.add_argument("--only-normal", action="store_true",
-                    help="run only the Gaussian workload on --streams streams (for profiling)")
+                    help="run only the Gaussian and exponential workloads on --streams streams (for profiling)")
     ap.add_argument("--path", default="imad,tensor", help="refill paths to time; the faster one is reported")
     ap.add_argument("--batch-streams", type=int, default=65536)
     ap.add_argument("--serve-seconds", type=float, default=10.0)
@@ -588,7 +591,9 @@ def main():
         from paper_2106_02504_gb300 import build as _b
         _b.build()
         import paper_2106_02504_gb300._rlxpp as nat
-        print(json.dumps({"workload": "normal", **bench_normal(nat, torch.device("cuda", local_rank), args.streams)}))
+        dev = torch.device("cuda", local_rank)
+        print(json.dumps({"workload": "normal", **bench_normal(nat, dev, args.streams)}))
+        print(json.dumps({"workload": "exponential", **bench_normal(nat, dev, args.streams, exponential=True)}))
         return 0
     if world > 1:
         import torch

@@ -134,6 +134,15 @@ rlxpp_status rlxpp_draw_f32(rlxpp_gen* gen, const int64_t* counts, const int64_t
 rlxpp_status rlxpp_draw_normal_f64(rlxpp_gen* gen, const int64_t* counts, const int64_t* offsets,
                                    int64_t count_each, double* out, void* cuda_stream);
 
+/* Draw exponential doubles with rate 1 (another of the distributions ROOT builds on
+ * Rndm, Sec. 2.4) by inversion: x = -ln(1 - d) for each double d of the stream (the
+ * rlxpp_draw_f64 sequence; 1 - d in (0, 1], d = 0 gives +0).  ln is CUDA's
+ * double-precision log: each value is within a few units in the last place of the
+ * exact one.  double out, same layout rules as rlxpp_draw_u24; the stream moves as
+ * rlxpp_draw_f64 of the same count would move it. */
+rlxpp_status rlxpp_draw_exp_f64(rlxpp_gen* gen, const int64_t* counts, const int64_t* offsets,
+                                int64_t count_each, double* out, void* cuda_stream);
+
 /* Skip random numbers without generating them (Sec. 2.4), counted in values of one
  * kind: stream i moves exactly as if it had drawn n_values[i] values of `kind`
  * (RLXPP_KIND_U24, RLXPP_KIND_F64 or RLXPP_KIND_F32) and discarded them: the rest of

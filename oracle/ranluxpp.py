@@ -170,6 +170,13 @@ def box_muller_many(d_a, d_b):
     return r * np.choose(qi, [c, -s, -c, s]), r * np.choose(qi, [s, c, -s, -c])
 
 
+def exponential(d):
+    """Exponential value with rate 1 by inversion of its distribution function
+    F(x) = 1 - e^-x: x = -ln(1 - d) for a double d in [0, 1) (1 - d is exact for 48-bit
+    doubles; d = 0 gives 0)."""
+    return 0.0 - math.log(1.0 - d)
+
+
 def f64_bits(x):
     """IEEE-754 binary64 bit pattern of a Python float."""
     return struct.unpack("<Q", struct.pack("<d", x))[0]
@@ -243,6 +250,10 @@ class Stream:
         for k in range(0, len(d), 2):
             out.extend(box_muller(d[k], d[k + 1]))
         return out[:n]
+
+    def draw_exp(self, n):
+        """n exponential values, one double each."""
+        return [exponential(d) for d in self.draw_f64(n)]
 
     def draw_f32_bits(self, n):
         """Single-precision draws: one number each, w 2^-24 (the 24-bit RANLUX output)."""

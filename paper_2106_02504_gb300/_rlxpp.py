@@ -70,6 +70,7 @@ def _load():
         "rlxpp_draw_f64": [_vp, _vp, _vp, _i64, _vp, _vp],
         "rlxpp_draw_f32": [_vp, _vp, _vp, _i64, _vp, _vp],
         "rlxpp_draw_normal_f64": [_vp, _vp, _vp, _i64, _vp, _vp],
+        "rlxpp_draw_exp_f64": [_vp, _vp, _vp, _i64, _vp, _vp],
         "rlxpp_skip_values": [_vp, _vp, _u32, _vp],
         "rlxpp_draw_f64_sum_hist": [_vp, _i64, _vp, _vp, _vp],
         "rlxpp_get_state": [_vp, _vp, _vp],
@@ -182,6 +183,10 @@ def rlxpp_draw_f32(gen, out, count_each=0, counts=None, offsets=None, stream=Non
 
 def rlxpp_draw_normal_f64(gen, out, count_each=0, counts=None, offsets=None, stream=None):
     _check(_lib.rlxpp_draw_normal_f64(gen, _ptr(counts), _ptr(offsets), count_each, _ptr(out), _stream(stream)))
+
+
+def rlxpp_draw_exp_f64(gen, out, count_each=0, counts=None, offsets=None, stream=None):
+    _check(_lib.rlxpp_draw_exp_f64(gen, _ptr(counts), _ptr(offsets), count_each, _ptr(out), _stream(stream)))
 
 
 def rlxpp_skip_values(gen, n_values, kind, stream=None):
@@ -364,6 +369,9 @@ class Generator:
 
     def draw_normal_f64(self, out, count_each=0, counts=None, offsets=None, stream=None):
         rlxpp_draw_normal_f64(self.handle, out, count_each, counts, offsets, stream)
+
+    def draw_exp_f64(self, out, count_each=0, counts=None, offsets=None, stream=None):
+        rlxpp_draw_exp_f64(self.handle, out, count_each, counts, offsets, stream)
 
     def skip_values(self, n_values, kind, stream=None):
         rlxpp_skip_values(self.handle, n_values, kind, stream)

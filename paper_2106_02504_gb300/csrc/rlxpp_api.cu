@@ -363,6 +363,11 @@ rlxpp_status rlxpp_draw_normal_f64(rlxpp_gen* g, const int64_t* counts, const in
   return draw_common(g, kDrawNormal, counts, offsets, count_each, out, sizeof(double), as_stream(cuda_stream));
 }
 
+rlxpp_status rlxpp_draw_exp_f64(rlxpp_gen* g, const int64_t* counts, const int64_t* offsets,
+                            int64_t count_each, double* out, void* cuda_stream) {
+  return draw_common(g, kDrawExp, counts, offsets, count_each, out, sizeof(double), as_stream(cuda_stream));
+}
+
 rlxpp_status rlxpp_skip_values(rlxpp_gen* g, const uint64_t* n_values, uint32_t kind, void* cuda_stream) {
   if (rlxpp_status s = check_gen(g)) return s;
   if (kind != RLXPP_KIND_U24 && kind != RLXPP_KIND_F64 && kind != RLXPP_KIND_F32)

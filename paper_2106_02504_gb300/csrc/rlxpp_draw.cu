@@ -79,6 +79,7 @@ __global__ void __launch_bounds__(kDrawBlock, Uniform ? RLXPP_DRAW_MIN_BLOCKS : 
       out.sum = 0;
       out.hist = hist_s + (threadIdx.x / 32) * 256;
     }
+    if constexpr (Kind == kDrawExp) out.out = static_cast<double*>(a.out);
     if constexpr (Kind == kDrawNormal) {  // n normals take 2 ceil(n / 2) doubles
       out.out = static_cast<double*>(a.out);
       out.base = base;
@@ -127,6 +128,7 @@ cudaError_t launch_draw(int kind, const DrawArgs& a, cudaStream_t st) {
     case kDrawSumHist: return launch_kind<kDrawSumHist>(a, st);
     case kDrawF32: return launch_kind<kDrawF32>(a, st);
     case kDrawNormal: return launch_kind<kDrawNormal>(a, st);
+    case kDrawExp: return launch_kind<kDrawExp>(a, st);
   }
   return cudaErrorInvalidValue;
 }

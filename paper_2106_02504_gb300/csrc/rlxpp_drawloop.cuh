@@ -196,6 +196,30 @@ struct Consumer<kDrawNormal> {
   }
 };
 
+// Exponential doubles (rate 1) by inversion: x = -ln(1 - d) for each double d of the
+// stream (1 - d = (2^48 - v) 2^-48 exactly, in (0, 1]); written as 0 - ln(1 - d) so that
+// d = 0 gives +0.  ln is CUDA's double-precision log.
+__device__ __forceinline__ double exp_from48(uint64_t v) {
+  const double u1 = v ? __longlong_as_double((long long)f64_bits_from48((1ull << 48) - v)) : 1.0;
+  return 0.0 - log(u1);
+}
+template <>
+struct Consumer<kDrawExp> {
+  double* out;
+  __device__ __forceinline__ void value_at_word(const uint32_t D[kLimbs], int w, int64_t idx) {
+    out[idx] = exp_from48(bits48_at_word(D, w));
+  }
+  __device__ __forceinline__ void block(const uint32_t D[kLimbs], int64_t idx) {
+#pragma unroll
+    for (int j = 0; j < kDoubles; ++j) out[idx + j] = exp_from48(bits48(D, j));
+  }
+  __device__ __forceinline__ void partial(const uint32_t D[kLimbs], int64_t idx, int64_t n) {
+#pragma unroll
+    for (int j = 0; j < kDoubles; ++j)
+      if (j < n) out[idx + j] = exp_from48(bits48(D, j));
+  }
+};
+
 // Draws cnt values for one stream.  On entry D holds the RANLUX numbers of the current
 // block, c its borrow and pos the numbers already read; values go to out at indices
 // base, base + 1, ...  On return D, c and pos describe the stream after the draw.

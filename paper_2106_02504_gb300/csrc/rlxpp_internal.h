@@ -44,7 +44,7 @@ struct StateView {
   int* status;       // sticky device status (rlxpp_status value, 0 = ok)
 };
 
-enum DrawKind { kDrawU24 = 0, kDrawF64 = 1, kDrawSumHist = 2, kDrawF32 = 3, kDrawNormal = 4 };
+enum DrawKind { kDrawU24 = 0, kDrawF64 = 1, kDrawSumHist = 2, kDrawF32 = 3, kDrawNormal = 4, kDrawExp = 5 };
 
 struct DrawArgs {
   StateView s;

@@ -515,6 +515,7 @@ __global__ void __launch_bounds__(kTcRows* T, T == 1 ? 4 : 1)
     out.sum = 0;
     out.hist = hist_s + (tid / 32) * 256;
   }
+  if constexpr (Kind == kDrawExp) out.out = static_cast<double*>(a.out);
   if constexpr (Kind == kDrawNormal) {  // n normals take 2 ceil(n / 2) doubles
     out.out = static_cast<double*>(a.out);
     out.base = base;
@@ -595,7 +596,7 @@ __global__ void __launch_bounds__(kTcRows* T, T == 1 ? 4 : 1)
           pos = (uint32_t)(rem * need);
         }
       } else if (rem >= per_block) {
-        if constexpr (Kind == kDrawSumHist || Kind == kDrawNormal) {
+        if constexpr (Kind == kDrawSumHist || Kind == kDrawNormal || Kind == kDrawExp) {
           out.block(D, base + k);
         } else if constexpr (Coop) {
           // staged here, written by the whole warp below
@@ -883,7 +884,7 @@ static_assert(tc_smem_bytes(kTcGroups, true) <= 227 * 1024, "shared memory of a 
 // Tile-groups per CTA of each draw kernel.
 template <int Kind>
 constexpr int tc_groups() {
-  return (Kind == kDrawSumHist || Kind == kDrawNormal) ? 1 : kTcGroups;
+  return (Kind == kDrawSumHist || Kind == kDrawNormal || Kind == kDrawExp) ? 1 : kTcGroups;
 }
 
 // cuTensorMapEncodeTiled from the driver, looked up once (null if unavailable).
@@ -974,6 +975,7 @@ cudaError_t launch_draw_tc(int kind, const DrawArgs& a, const void* bimg, cudaSt
     case kDrawSumHist: return launch_tc_kind<kDrawSumHist>(a, b, st);
     case kDrawF32: return launch_tc_kind<kDrawF32>(a, b, st);
     case kDrawNormal: return launch_tc_kind<kDrawNormal>(a, b, st);
+    case kDrawExp: return launch_tc_kind<kDrawExp>(a, b, st);
   }
   return cudaErrorInvalidValue;
 }

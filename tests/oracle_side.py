@@ -121,3 +121,14 @@ def normals_expected(doubles, n):
     r = np.sqrt(-2.0 * np.log(1.0 - da))
     tol = np.repeat(2.0 ** -49 * (r + 1.0), 2, axis=1)
     return want[:, :n], tol[:, :n]
+
+
+def exponentials_expected(doubles):
+    """Exponential values x = -ln(1 - d) from each double, with a per-value tolerance:
+    (want, tol).  Each side's log is within about 1 ulp of x (CUDA's stated bound for the
+    device log; numpy's log is closer), an ulp of x is at most 2^-52 x, so the two differ
+    by at most 2^-51 x; the tolerance 2^-50 (x + 1) leaves a factor of two and an absolute
+    floor for x near 0."""
+    d = np.asarray(doubles, dtype=np.float64)
+    want = 0.0 - np.log(1.0 - d)
+    return want, 2.0 ** -50 * (want + 1.0)

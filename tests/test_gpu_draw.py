@@ -10,7 +10,7 @@ import pytest
 from oracle import ranluxpp as R
 from oracle import swb_lib as S
 from paper_2106_02504_gb300 import workloads as W
-from tests.oracle_side import StreamSet, normals_expected, from_limbs64, seeded_X
+from tests.oracle_side import StreamSet, normals_expected, exponentials_expected, from_limbs64, seeded_X
 
 pytestmark = pytest.mark.gpu
 
@@ -219,6 +219,41 @@ def test_draw_normal(native, path):
             continue
         want, tol = normals_expected(d.reshape(1, -1), c)
         assert np.all(np.abs(got[offsets[i]:offsets[i] + c] - want[0]) <= tol[0]), i
+    assert got[-1] == 7.0
+    assert_states(native, g, ref)
+    g.close()
+
+
+def test_draw_exp(native, path):
+    """Exponential values (inversion, one double each) against the oracle within the
+    derived tolerance; starts inside a block, ragged counts, a host output buffer; the
+    streams end where the f64 draw of the same count leaves them."""
+    seeds = W.random_seeds(N, 95)
+    g = make(native, seeds, levels=(223,), path=path)
+    ref = StreamSet.from_seeds(seeds, 223)
+    for kind, count, host in [("e", 1000, False), (S.KIND_U24, 3, False), ("e", 1001, False),
+                              ("e", 5, True), ("e", 1, False), ("e", 0, False)]:
+        if kind != "e":
+            _draw(native, g, kind, count, N)
+            ref.draw(count, kind)
+            continue
+        out = torch.full((N, max(count, 1)), 7.0, dtype=torch.float64, device="cpu" if host else "cuda")
+        g.draw_exp_f64(out, count)
+        got = out.cpu().numpy()[:, :count]
+        want, tol = exponentials_expected(ref.draw(count, S.KIND_F64))
+        assert np.all(np.abs(got - want) <= tol), (count, float(np.max(np.abs(got - want) - tol)))
+        assert np.all(got >= 0)
+        if count == 0:
+            assert np.all(out.cpu().numpy() == 7.0)
+    assert_states(native, g, ref)
+    counts, offsets = W.ragged_counts(N, 41, seed=96)
+    out = torch.full((int(counts.sum()) + 1,), 7.0, dtype=torch.float64, device="cuda")
+    g.draw_exp_f64(out, 0, torch.from_numpy(counts).cuda(), torch.from_numpy(offsets).cuda())
+    got = out.cpu().numpy()
+    for i, d in enumerate(ref.draw_ragged(counts, S.KIND_F64)):
+        c = int(counts[i])
+        want, tol = exponentials_expected(d)
+        assert np.all(np.abs(got[offsets[i]:offsets[i] + c] - want) <= tol), i
     assert got[-1] == 7.0
     assert_states(native, g, ref)
     g.close()

@@ -428,6 +428,35 @@ def test_box_muller_invariants_and_vector_form():
         assert abs(v0 - z0) <= 2 ** -50 * (r + 1) and abs(v1 - z1) <= 2 ** -50 * (r + 1)
 
 
+def test_exponential_closed_forms_and_distribution():
+    import math
+    assert R.exponential(0.0) == 0.0 and math.copysign(1, R.exponential(0.0)) == 1
+    for k in (1, 2, 10, 24, 48):
+        # 1 - d = 2^-k exactly, so x = k ln 2
+        assert R.exponential(1.0 - 2.0 ** -k) == pytest.approx(k * math.log(2.0), rel=1e-15)
+    assert R.exponential(0.5) == pytest.approx(math.log(2.0), rel=1e-15)
+    # small d: -ln(1 - d) = d + d^2 / 2 + ..., and the distribution function at x gives d back
+    for d in (2.0 ** -48, 2.0 ** -30, 3 * 2.0 ** -40):
+        assert R.exponential(d) == pytest.approx(d + d * d / 2, rel=1e-15)
+    rng = random.Random(33)
+    for _ in range(2000):
+        d = rng.randrange(2 ** 48) / 2 ** 48
+        assert -math.expm1(-R.exponential(d)) == pytest.approx(d, rel=1e-14, abs=2 ** -52)
+    st, ref = R.Stream(2048, seed=23), R.Stream(2048, seed=23)
+    x = st.draw_exp(5)
+    assert x == [R.exponential(d) for d in ref.draw_f64(5)] and st.state() == ref.state()
+    # moments (mean 1, variance 1) and the Kolmogorov-Smirnov distance to 1 - e^-x
+    n = 100000
+    x = np.array(R.Stream(389, seed=24).draw_exp(n))
+    assert x.min() >= 0
+    assert abs(x.mean() - 1) < 5 / math.sqrt(n)
+    assert abs(x.var() - 1) < 5 * math.sqrt(8 / n)        # the fourth central moment is 9
+    xs = np.sort(x)
+    cdf = -np.expm1(-xs)
+    ks = max(np.max(np.arange(1, n + 1) / n - cdf), np.max(cdf - np.arange(n) / n))
+    assert ks < 1.63 / math.sqrt(n)                        # 1 % critical value
+
+
 def test_normal_draws_consume_pairs_and_look_gaussian():
     import math
     st, ref = R.Stream(2048, seed=21), R.Stream(2048, seed=21)
