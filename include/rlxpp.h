@@ -328,7 +328,13 @@ rlxpp_status rlxpp_seed_states_noalloc(const uint32_t* levels, uint32_t n_levels
  *  rlxpp_test_mul_mod      x[9], y[9] -> out[9]  = x y mod m; x, y < 2^576
  *  rlxpp_test_to_ranlux    x[9] (< m) -> d[9] = floor(2^576 x / m), carry[1] (Sec. 2.3)
  *  rlxpp_test_to_lcg       d[9], carry[1] -> x[9] = d - floor(d / 2^336) + carry
- *  rlxpp_test_f64_from48   v[1] (< 2^48) -> out[1] = bit pattern of v 2^-48 */
+ *  rlxpp_test_f64_from48   v[1] (< 2^48) -> out[1] = bit pattern of v 2^-48
+ * The integer-pipe elementary functions under the distribution draws (Sec. 2.4); each
+ * output is a double's bit pattern, a quiet NaN for an input out of range:
+ *  rlxpp_test_neg_ln48       w[1] in [1, 2^48] -> out[1] = -ln(w 2^-48)
+ *  rlxpp_test_cos_sin_2pi48  v[1] (< 2^48)     -> out[2] = cos, sin of 2 pi v 2^-48
+ *  rlxpp_test_box_muller48   v[2] (< 2^48)     -> out[2] = r cos 2 pi d_b, r sin 2 pi d_b with
+ *                            r = sqrt(-2 ln(1 - d_a)), d = v 2^-48 */
 rlxpp_status rlxpp_test_multiply9x9(const uint64_t* x, const uint64_t* y, uint64_t* out,
                                     uint64_t n, void* cuda_stream);
 rlxpp_status rlxpp_test_mod_m(const uint64_t* in, uint64_t* out, uint64_t n, void* cuda_stream);
@@ -340,6 +346,11 @@ rlxpp_status rlxpp_test_to_lcg(const uint64_t* d, const uint32_t* carry, uint64_
                                uint64_t n, void* cuda_stream);
 rlxpp_status rlxpp_test_f64_from48(const uint64_t* v, uint64_t* out, uint64_t n,
                                    void* cuda_stream);
+rlxpp_status rlxpp_test_neg_ln48(const uint64_t* w, uint64_t* out, uint64_t n, void* cuda_stream);
+rlxpp_status rlxpp_test_cos_sin_2pi48(const uint64_t* v, uint64_t* out, uint64_t n,
+                                      void* cuda_stream);
+rlxpp_status rlxpp_test_box_muller48(const uint64_t* v, uint64_t* out, uint64_t n,
+                                     void* cuda_stream);
 
 /* One tensor-path product per item: out[9] = A x mod m for luxury p (x < m, device
  * arrays of 9 uint64 limbs per item); synchronous. */

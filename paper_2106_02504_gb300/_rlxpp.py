@@ -82,6 +82,9 @@ def _load():
         "rlxpp_test_to_ranlux": [_vp, _vp, _vp, _u64, _vp],
         "rlxpp_test_to_lcg": [_vp, _vp, _vp, _u64, _vp],
         "rlxpp_test_f64_from48": [_vp, _vp, _u64, _vp],
+        "rlxpp_test_neg_ln48": [_vp, _vp, _u64, _vp],
+        "rlxpp_test_cos_sin_2pi48": [_vp, _vp, _u64, _vp],
+        "rlxpp_test_box_muller48": [_vp, _vp, _u64, _vp],
         "rlxpp_luxury_multiplier": [_u32, _vp],
         "rlxpp_seed_states_noalloc": [_vp, _u32, _vp, _vp, _u64, _vp, _vp],
         "rlxpp_plan_requests": [_vp, _vp, _u64, _u32, _vp, ctypes.POINTER(_vp)],
@@ -243,6 +246,18 @@ def rlxpp_test_to_lcg(d, carry, x, n, stream=None):
 
 def rlxpp_test_f64_from48(v, out, n, stream=None):
     _check(_lib.rlxpp_test_f64_from48(_ptr(v), _ptr(out), n, _stream(stream)))
+
+
+def rlxpp_test_neg_ln48(w, out, n, stream=None):
+    _check(_lib.rlxpp_test_neg_ln48(_ptr(w), _ptr(out), n, _stream(stream)))
+
+
+def rlxpp_test_cos_sin_2pi48(v, out, n, stream=None):
+    _check(_lib.rlxpp_test_cos_sin_2pi48(_ptr(v), _ptr(out), n, _stream(stream)))
+
+
+def rlxpp_test_box_muller48(v, out, n, stream=None):
+    _check(_lib.rlxpp_test_box_muller48(_ptr(v), _ptr(out), n, _stream(stream)))
 
 
 def rlxpp_seed_states_noalloc(levels, seeds, n_streams, out, level_of_stream=None, stream=None):

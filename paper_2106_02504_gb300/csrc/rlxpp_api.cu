@@ -512,6 +512,15 @@ rlxpp_status rlxpp_test_to_lcg(const uint64_t* d, const uint32_t* carry, uint64_
 rlxpp_status rlxpp_test_f64_from48(const uint64_t* v, uint64_t* out, uint64_t n, void* cuda_stream) {
   return run_test(kTestF64, v, nullptr, out, nullptr, n, cuda_stream);
 }
+rlxpp_status rlxpp_test_neg_ln48(const uint64_t* w, uint64_t* out, uint64_t n, void* cuda_stream) {
+  return run_test(kTestNegLn48, w, nullptr, out, nullptr, n, cuda_stream);
+}
+rlxpp_status rlxpp_test_cos_sin_2pi48(const uint64_t* v, uint64_t* out, uint64_t n, void* cuda_stream) {
+  return run_test(kTestCosSin2Pi48, v, nullptr, out, nullptr, n, cuda_stream);
+}
+rlxpp_status rlxpp_test_box_muller48(const uint64_t* v, uint64_t* out, uint64_t n, void* cuda_stream) {
+  return run_test(kTestBoxMuller48, v, nullptr, out, nullptr, n, cuda_stream);
+}
 
 static rlxpp_status tc_test(uint32_t p, const uint64_t* x, uint64_t* out, uint64_t n, void* cuda_stream,
                             bool issue);

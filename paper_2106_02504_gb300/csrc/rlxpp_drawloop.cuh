@@ -4,6 +4,7 @@
 // reached, with the value written, stored or consumed by a Consumer.
 #pragma once
 #include "rlxpp_arith.cuh"
+#include "rlxpp_fixmath.cuh"
 #include "rlxpp_internal.h"
 
 namespace rlxpp {
@@ -162,8 +163,8 @@ struct Consumer<kDrawSumHist> {
 // (exact: (2^48 - v_a) 2^-48), r = sqrt(-2 ln u1), z_a = r cos(2 pi d_b),
 // z_b = r sin(2 pi d_b).  The draw loop feeds it 2 ceil(n / 2) doubles, value j at
 // output index base + j; pairs start at even j; an index at or past `end` (the last
-// sine of an odd count) is not written.  log, sqrt and sincospi are CUDA's
-// double-precision functions.
+// sine of an odd count) is not written.  ln, sqrt, cos and sin are the integer-pipe
+// routines of rlxpp_fixmath.cuh, applied to the 48-bit integers themselves.
 template <>
 struct Consumer<kDrawNormal> {
   double* out;
@@ -174,13 +175,10 @@ struct Consumer<kDrawNormal> {
       va = v;
       return;
     }
-    const double u1 = va ? __longlong_as_double((long long)f64_bits_from48((1ull << 48) - va)) : 1.0;
-    const double u2 = __longlong_as_double((long long)f64_bits_from48(v));
-    const double r = sqrt(-2.0 * log(u1));
-    double sn, cs;
-    sincospi(2.0 * u2, &sn, &cs);
-    out[idx - 1] = r * cs;
-    if (idx < end) out[idx] = r * sn;
+    double z0, z1;
+    fx_box_muller48(va, v, z0, z1);
+    out[idx - 1] = z0;
+    if (idx < end) out[idx] = z1;
   }
   __device__ __forceinline__ void value_at_word(const uint32_t D[kLimbs], int w, int64_t idx) {
     take(bits48_at_word(D, w), idx);
@@ -197,12 +195,9 @@ struct Consumer<kDrawNormal> {
 };
 
 // Exponential doubles (rate 1) by inversion: x = -ln(1 - d) for each double d of the
-// stream (1 - d = (2^48 - v) 2^-48 exactly, in (0, 1]); written as 0 - ln(1 - d) so that
-// d = 0 gives +0.  ln is CUDA's double-precision log.
-__device__ __forceinline__ double exp_from48(uint64_t v) {
-  const double u1 = v ? __longlong_as_double((long long)f64_bits_from48((1ull << 48) - v)) : 1.0;
-  return 0.0 - log(u1);
-}
+// stream (1 - d = (2^48 - v) 2^-48 exactly, in (0, 1]; d = 0 gives +0), with the
+// integer-pipe logarithm of rlxpp_fixmath.cuh.
+__device__ __forceinline__ double exp_from48(uint64_t v) { return fx_exponential48(v); }
 template <>
 struct Consumer<kDrawExp> {
   double* out;

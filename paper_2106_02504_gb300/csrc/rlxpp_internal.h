@@ -92,7 +92,10 @@ enum TestOp {
   kTestMulMod = 2,
   kTestToRanlux = 3,
   kTestToLcg = 4,
-  kTestF64 = 5
+  kTestF64 = 5,
+  kTestNegLn48 = 6,
+  kTestCosSin2Pi48 = 7,
+  kTestBoxMuller48 = 8
 };
 
 // Records msg as the calling thread's rlxpp_last_error() text and returns code.

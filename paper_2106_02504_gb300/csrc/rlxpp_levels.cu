@@ -7,6 +7,7 @@
 #include <mutex>
 
 #include "rlxpp_arith.cuh"
+#include "rlxpp_fixmath.cuh"
 #include "rlxpp_internal.h"
 #include "rlxpp_state.cuh"
 
@@ -222,6 +223,8 @@ __device__ __forceinline__ void store_u64_limbs(uint64_t* dst, int n64, const ui
   for (int k = 0; k < n64; ++k) dst[k] = ((uint64_t)v[2 * k + 1] << 32) | v[2 * k];
 }
 
+constexpr uint64_t kNaNBits = 0x7FF8000000000000ull;
+
 __global__ void k_test(int op, const uint64_t* __restrict__ x, const uint64_t* __restrict__ y,
                        uint64_t* __restrict__ out, uint32_t* __restrict__ carry, uint64_t n) {
   const uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -259,6 +262,29 @@ __global__ void k_test(int op, const uint64_t* __restrict__ x, const uint64_t* _
     case kTestF64:
       out[i] = f64_bits_from48(x[i]);
       break;
+    case kTestNegLn48: {  // w in [1, 2^48]; a NaN for anything else
+      const uint64_t w = x[i];
+      out[i] = (w >= 1 && w <= (1ull << 48))
+                   ? (uint64_t)__double_as_longlong(fx_to_double(fx_neg_ln48(w), -120, false))
+                   : kNaNBits;
+      break;
+    }
+    case kTestCosSin2Pi48: {  // v < 2^48
+      int64_t c = 0, s = 0;
+      if (x[i] < (1ull << 48)) fx_cos_sin_2pi48(x[i], c, s);
+      const bool ok = x[i] < (1ull << 48);
+      out[2 * i] = ok ? (uint64_t)__double_as_longlong(fx_scale_to_double(1ull << 60, -60, c)) : kNaNBits;
+      out[2 * i + 1] = ok ? (uint64_t)__double_as_longlong(fx_scale_to_double(1ull << 60, -60, s)) : kNaNBits;
+      break;
+    }
+    case kTestBoxMuller48: {  // va, vb < 2^48
+      double z0 = 0, z1 = 0;
+      const bool ok = x[2 * i] < (1ull << 48) && x[2 * i + 1] < (1ull << 48);
+      if (ok) fx_box_muller48(x[2 * i], x[2 * i + 1], z0, z1);
+      out[2 * i] = ok ? (uint64_t)__double_as_longlong(z0) : kNaNBits;
+      out[2 * i + 1] = ok ? (uint64_t)__double_as_longlong(z1) : kNaNBits;
+      break;
+    }
   }
 }
 
