@@ -4,11 +4,12 @@ rounded once to the stored fixed-point scale.
 
   * ln 2 at scale 2^-120 (128 bits) and 2 pi at scale 2^-61 (64 bits);
   * the logarithm's reduction table (table-driven logarithm, Tang, ACM TOMS 16(4),
-    1990): for the mantissa interval [i/256, (i+1)/256), i = 192..383, a 13-bit
-    reciprocal R_i = Rint_i / 4096 of the interval's centre (exactly 1 for the two
-    intervals touching 1) and ln R_i at scale 2^-120, rounded to a multiple of 2^13 so
-    that Rint_i fits in the low 13 bits of the same 128-bit word;
-  * sin and cos of 2 pi j / 256, j = 0..255, at scale 2^-62.
+    1990): for the mantissa interval (i/512, (i+1)/512], i = 384..767, the 16-bit
+    reciprocal R_i = Rint_i / 2^15 of the interval's upper end, rounded down (so that
+    m R_i <= 1 on the interval; exactly 1 for the interval ending at 1), and ln R_i at
+    scale 2^-120, rounded to a multiple of 2^16 so that Rint_i fits in the low 16 bits
+    of the same 128-bit word;
+  * sin and cos of 2 pi j / 256 for the first quadrant, j = 0..64, at scale 2^-63.
 
 Run it from anywhere: ``python gen_fixmath_tables.py`` rewrites the header beside it.
 """
@@ -63,18 +64,15 @@ def fixed(x, scale_bits):
 
 def ln_table():
     rows = []
-    for i in range(192, 384):
-        if i in (255, 256):
-            rint = 4096
-        else:
-            rint = int((Decimal(4096) * 256 / (Decimal(i) + Decimal("0.5"))).to_integral_value(
-                rounding=ROUND_HALF_EVEN))
-        # |r| = |m R - 1| over the interval stays within 2^-8 (the series' range)
-        for m in (Decimal(i) / 256, Decimal(i + 1) / 256):
-            assert abs(m * rint / 4096 - 1) <= Decimal(2) ** -8, (i, rint)
-        assert 0 < rint < 1 << 13
-        v = fixed((Decimal(rint) / 4096).ln(), 120)
-        v = (v + (1 << 12)) >> 13 << 13                # a multiple of 2^13
+    for i in range(384, 768):
+        rint = (1 << 15) * 512 // (i + 1)           # floor(2^15 / upper end)
+        # r = m R - 1 lies in [-2^-8.5, 0] over the interval (the series' range)
+        for m in (Decimal(i) / 512, Decimal(i + 1) / 512):
+            r = m * rint / (1 << 15) - 1
+            assert -Decimal(2) ** Decimal("-8.5") <= r <= 0, (i, rint)
+        assert 0 < rint < 1 << 16
+        v = fixed((Decimal(rint) / (1 << 15)).ln(), 120)
+        v = (v + (1 << 15)) >> 16 << 16                # a multiple of 2^16
         v &= (1 << 128) - 1                             # two's complement, 128 bits
         rows.append(((v & ((1 << 64) - 1)) | rint, v >> 64))
     return rows
@@ -82,9 +80,9 @@ def ln_table():
 
 def sincos_table():
     rows = []
-    for j in range(256):
+    for j in range(65):
         s, c = sin_cos(2 * PI * j / 256)
-        rows.append((fixed(s, 62), fixed(c, 62)))
+        rows.append((fixed(s, 63), fixed(c, 63)))
     return rows
 
 
@@ -98,17 +96,17 @@ def render():
            f"constexpr uint64_t kLn2Lo = 0x{ln2 & ((1 << 64) - 1):016x}ull;",
            f"constexpr uint64_t kLn2Hi = 0x{ln2 >> 64:016x}ull;",
            f"constexpr uint64_t kTwoPi61 = 0x{two_pi:016x}ull;", "",
-           "// Logarithm reduction, i = 192..383 (mantissa in [i/256, (i+1)/256)): x = low word",
-           "// with the reciprocal numerator Rint (R = Rint / 4096) in bits 0..12, y = high word;",
-           "// with those 13 bits cleared, (y:x) is ln R 2^120 in two's complement.",
-           "static __device__ const ulonglong2 kLnTab[192] = {"]
+           "// Logarithm reduction, i = 384..767 (mantissa in (i/512, (i+1)/512]): x = low word",
+           "// with the reciprocal numerator Rint (R = Rint / 2^15) in bits 0..15, y = high word;",
+           "// with those 16 bits cleared, (y:x) is ln R 2^120 in two's complement.",
+           "static __device__ const ulonglong2 kLnTab[384] = {"]
     for lo, hi in ln_table():
         out.append(f"    {{0x{lo:016x}ull, 0x{hi:016x}ull}},")
     out += ["};", "",
-            "// sin(2 pi j / 256) 2^62 and cos(2 pi j / 256) 2^62 (two's complement), j = 0..255.",
-            "static __device__ const longlong2 kSinCosTab[256] = {"]
+            "// sin(2 pi j / 256) 2^63 and cos(2 pi j / 256) 2^63, j = 0..64 (the first quadrant).",
+            "static __device__ const ulonglong2 kSinCosTab[65] = {"]
     for s, c in sincos_table():
-        out.append(f"    {{{s}ll, {c}ll}},")
+        out.append(f"    {{0x{s:016x}ull, 0x{c:016x}ull}},")
     out += ["};", "", "}  // namespace rlxpp", ""]
     return "\n".join(out)
 

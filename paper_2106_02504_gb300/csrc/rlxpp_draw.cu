@@ -22,7 +22,7 @@ namespace rlxpp {
 namespace {
 
 template <int Kind, bool Uniform>
-__global__ void __launch_bounds__(kDrawBlock, Uniform ? RLXPP_DRAW_MIN_BLOCKS : 4) k_draw(const DrawArgs a) {
+__global__ void __launch_bounds__(kDrawBlock, (Uniform && Kind != kDrawNormal && Kind != kDrawExp) ? RLXPP_DRAW_MIN_BLOCKS : 4) k_draw(const DrawArgs a) {
   constexpr int kWarps = kDrawBlock / 32;
   __shared__ unsigned int hist_s[Kind == kDrawSumHist ? kWarps * 256 : 1];
   if (Kind == kDrawSumHist) {

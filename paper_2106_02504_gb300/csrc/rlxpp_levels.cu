@@ -270,11 +270,10 @@ __global__ void k_test(int op, const uint64_t* __restrict__ x, const uint64_t* _
       break;
     }
     case kTestCosSin2Pi48: {  // v < 2^48
-      int64_t c = 0, s = 0;
-      if (x[i] < (1ull << 48)) fx_cos_sin_2pi48(x[i], c, s);
       const bool ok = x[i] < (1ull << 48);
-      out[2 * i] = ok ? (uint64_t)__double_as_longlong(fx_scale_to_double(1ull << 60, -60, c)) : kNaNBits;
-      out[2 * i + 1] = ok ? (uint64_t)__double_as_longlong(fx_scale_to_double(1ull << 60, -60, s)) : kNaNBits;
+      const FxCosSin cs = fx_cos_sin_2pi48(ok ? x[i] : 0);
+      out[2 * i] = ok ? (uint64_t)__double_as_longlong(fx_scale_to_double(1ull << 62, -62, cs.c, cs.nc)) : kNaNBits;
+      out[2 * i + 1] = ok ? (uint64_t)__double_as_longlong(fx_scale_to_double(1ull << 62, -62, cs.s, cs.ns)) : kNaNBits;
       break;
     }
     case kTestBoxMuller48: {  // va, vb < 2^48
