@@ -128,18 +128,20 @@ rlxpp_status rlxpp_draw_f32(rlxpp_gen* gen, const int64_t* counts, const int64_t
  * u1 = 1 - d_a in (0, 1], r = sqrt(-2 ln u1), then r cos(2 pi d_b) and r sin(2 pi d_b).
  * n values take 2 ceil(n / 2) doubles (an odd count drops its last sine), so afterwards
  * the stream stands where rlxpp_draw_f64 of 2 ceil(n / 2) values would leave it.  ln,
- * sqrt, sin and cos are CUDA's double-precision functions: each value is within a few
- * units in the last place of the exact transform of its pair.  double out, same layout
- * rules as rlxpp_draw_u24 (count = normals per stream). */
+ * sqrt, sin and cos are the library's own fixed-point routines on the 48-bit integers
+ * (table-driven log, Taylor series, Newton's iteration for 1/sqrt): each value is within
+ * half a unit in the last place plus 2^-56 r of the exact transform of its pair.
+ * double out, same layout rules as rlxpp_draw_u24 (count = normals per stream). */
 rlxpp_status rlxpp_draw_normal_f64(rlxpp_gen* gen, const int64_t* counts, const int64_t* offsets,
                                    int64_t count_each, double* out, void* cuda_stream);
 
 /* Draw exponential doubles with rate 1 (another of the distributions ROOT builds on
  * Rndm, Sec. 2.4) by inversion: x = -ln(1 - d) for each double d of the stream (the
- * rlxpp_draw_f64 sequence; 1 - d in (0, 1], d = 0 gives +0).  ln is CUDA's
- * double-precision log: each value is within a few units in the last place of the
- * exact one.  double out, same layout rules as rlxpp_draw_u24; the stream moves as
- * rlxpp_draw_f64 of the same count would move it. */
+ * rlxpp_draw_f64 sequence; 1 - d in (0, 1], d = 0 gives +0).  ln is the library's own
+ * fixed-point table-driven logarithm of the 48-bit integer 2^48 - v: each value is
+ * within half a unit in the last place plus 2^-60 x of the exact one.  double out, same
+ * layout rules as rlxpp_draw_u24; the stream moves as rlxpp_draw_f64 of the same count
+ * would move it. */
 rlxpp_status rlxpp_draw_exp_f64(rlxpp_gen* gen, const int64_t* counts, const int64_t* offsets,
                                 int64_t count_each, double* out, void* cuda_stream);
 
