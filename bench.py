@@ -172,7 +172,8 @@ def run_reference(args, rank, world):
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
                              "sample": f"first {n_sample} of the {args.streams} streams per step: seed + "
                                        f"{HBM_COUNT} f64 + {FUSED_COUNT} fused f64 each (C recurrence oracle, "
-                                       f"{threads} threads)"},
+                                       f"{threads} threads), {tot / args.steps:.1f} s wall and "
+                                       f"{tot / args.steps * threads:.0f} core-seconds per step"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -335,7 +336,8 @@ def run_native(args, rank, world, local_rank):
         result["cpu_baseline"] = {
             "value": doubles / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
             "sample": f"first {args.cpu_sample} of the {n} streams: seed + {HBM_COUNT} f64 + {FUSED_COUNT} "
-                      f"fused f64 each (C recurrence oracle, {threads} threads), {dt:.1f} s"}
+                      f"fused f64 each (C recurrence oracle, {threads} threads), {dt:.1f} s wall, "
+                      f"{dt * threads:.0f} core-seconds"}
     if rank == 0:
         print(json.dumps(result), flush=True)
     return 0
