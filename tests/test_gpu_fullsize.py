@@ -199,3 +199,36 @@ def test_config4_skips_full_size(native):
         want = StreamSet([X], P).draw(48, S.KIND_F64)[0].view(np.uint64)
         assert np.array_equal(got[r], want), i
     g.close()
+
+
+@pytest.mark.parametrize("kind", ["normal", "exponential"])
+def test_distributions_full_size(native, kind):
+    """Gaussian and exponential doubles as bench.py times them: 2^20 streams (seeds
+    1..2^20, p = 2048) x 1024 values on the tensor path into an 8 GiB buffer; sampled
+    streams against the oracle within the derived tolerances, and properties of every
+    value (finite; exponential values non-negative and at most 48 ln 2; Gaussian values
+    at most sqrt(96 ln 2) in magnitude, and sample moments near 0 and 1)."""
+    from tests.oracle_side import exponentials_expected, normals_expected
+    seeds = W.consecutive_seeds(N)
+    g = native.Generator(N, [P], torch.from_numpy(seeds.view(np.int64)).cuda())
+    g.set_path(native.RLXPP_PATH_TENSOR)
+    out = torch.empty((N, 1024), dtype=torch.float64, device="cuda")
+    (g.draw_normal_f64 if kind == "normal" else g.draw_exp_f64)(out, 1024)
+    torch.cuda.synchronize()
+    assert bool(torch.isfinite(out).all())
+    if kind == "normal":
+        assert float(out.abs().max()) <= np.sqrt(96 * np.log(2))
+        m, v = float(out.mean()), float(out.var())
+        assert abs(m) < 1e-3 and abs(v - 1) < 1e-3
+    else:
+        assert float(out.min()) >= 0 and float(out.max()) <= 48 * np.log(2)
+        assert abs(float(out.mean()) - 1) < 1e-3
+    idx = sample_idx(5, k=400)
+    got = out[torch.from_numpy(idx).cuda()].cpu().numpy()
+    ref = StreamSet.from_seeds(seeds[idx], P)
+    d = ref.draw(1024, S.KIND_F64)
+    want, tol = normals_expected(d, 1024) if kind == "normal" else exponentials_expected(d)
+    bad = np.nonzero((np.abs(got - want) > tol).any(axis=1))[0]
+    assert bad.size == 0, f"streams {idx[bad[:5]]} differ"
+    del out
+    g.close()
