@@ -23,7 +23,9 @@
  *  - The caller owns every buffer it passes; the library owns the generator state.
  *  - A handle is not thread-safe: calls on one handle must not overlap in time.
  *  - Every call returns RLXPP_OK or an error code; rlxpp_last_error() gives a message
- *    for the calling thread's last failure.
+ *    for the calling thread's last failure.  The environment variable RLXPP_LOG, read
+ *    once, turns on host logging to stderr: 1 logs every failure with its message, 2
+ *    also each create, destroy, draw, skip and seed call.
  *  - Draw order (a reading; the paper does not fix it): the 24 numbers of a block are
  *    delivered oldest first.  A u24 draw returns the next number; a double takes the
  *    next two numbers w_k, w_{k+1} (both from the current block; otherwise the stream
@@ -364,6 +366,13 @@ rlxpp_status rlxpp_test_tc_mulmod(uint32_t p, const uint64_t* x, uint64_t* out, 
  * when the kernel reported the timeout and left the context usable.  scratch: 9
  * uint64 of device memory (not written). */
 rlxpp_status rlxpp_test_tc_timeout(uint64_t* scratch, void* cuda_stream);
+
+/* Failure-path test: the library's device allocation number `after` from now (0 = the
+ * next one) reports out of memory without allocating, once; after < 0 switches this
+ * off.  Process-wide (one countdown shared by all threads and handles).  Calls that hit
+ * it return RLXPP_ERR_NOMEM and release what they had allocated; a handle whose call
+ * failed keeps its previous state. */
+rlxpp_status rlxpp_test_fail_alloc(int64_t after);
 
 /* Luxury multiplier A = a^p mod m as 9 uint64 limbs written to host memory out9,
  * computed on the device (Sec. 1: RANLUX as an LCG with a large multiplier). */

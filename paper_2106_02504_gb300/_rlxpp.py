@@ -83,6 +83,7 @@ def _load():
         "rlxpp_test_to_lcg": [_vp, _vp, _vp, _u64, _vp],
         "rlxpp_test_f64_from48": [_vp, _vp, _u64, _vp],
         "rlxpp_test_neg_ln48": [_vp, _vp, _u64, _vp],
+        "rlxpp_test_fail_alloc": [_i64],
         "rlxpp_test_cos_sin_2pi48": [_vp, _vp, _u64, _vp],
         "rlxpp_test_box_muller48": [_vp, _vp, _u64, _vp],
         "rlxpp_luxury_multiplier": [_u32, _vp],
@@ -246,6 +247,10 @@ def rlxpp_test_to_lcg(d, carry, x, n, stream=None):
 
 def rlxpp_test_f64_from48(v, out, n, stream=None):
     _check(_lib.rlxpp_test_f64_from48(_ptr(v), _ptr(out), n, _stream(stream)))
+
+
+def rlxpp_test_fail_alloc(after):
+    _check(_lib.rlxpp_test_fail_alloc(after))
 
 
 def rlxpp_test_neg_ln48(w, out, n, stream=None):

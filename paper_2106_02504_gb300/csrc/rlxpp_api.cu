@@ -1,6 +1,8 @@
 // Host side of the C ABI declared in include/rlxpp.h: argument checks, device memory
 // of the generator state, staging of host buffers, and the launches.
 #include <algorithm>
+#include <atomic>
+#include <cstdlib>
 #include <cstdio>
 #include <cstring>
 #include <string>
@@ -14,17 +16,61 @@ namespace {
 
 thread_local std::string g_last_error;
 
+// Host logging to stderr, chosen once by the environment variable RLXPP_LOG: 0 (or
+// unset) silent, 1 every failed call with its message, 2 also each create, destroy,
+// draw, skip and seed call with its main arguments.
+int log_level() {
+  static const int level = [] {
+    const char* v = std::getenv("RLXPP_LOG");
+    return v ? std::atoi(v) : 0;
+  }();
+  return level;
+}
+
 rlxpp_status fail(rlxpp_status code, const std::string& msg) {
   g_last_error = msg;
+  if (log_level() >= 1) std::fprintf(stderr, "rlxpp: error %d: %s\n", (int)code, msg.c_str());
   return code;
+}
+
+#define RLX_LOG_CALL(...)                          \
+  do {                                             \
+    if (log_level() >= 2) {                        \
+      std::fprintf(stderr, "rlxpp: " __VA_ARGS__); \
+      std::fputc('\n', stderr);                    \
+    }                                              \
+  } while (0)
+
+std::atomic<int64_t> g_fail_alloc{-1};  // rlxpp_test_fail_alloc's countdown (-1: off)
+
+cudaError_t dev_malloc(void** p, size_t bytes) {
+  if (injected_alloc_failure()) return cudaErrorMemoryAllocation;
+  return cudaMalloc(p, bytes);
+}
+template <class T>
+cudaError_t dev_malloc(T** p, size_t bytes) {
+  return dev_malloc(reinterpret_cast<void**>(p), bytes);
+}
+
+cudaError_t dev_malloc_async(void** p, size_t bytes, cudaStream_t st) {
+  if (injected_alloc_failure()) return cudaErrorMemoryAllocation;
+  return cudaMallocAsync(p, bytes, st);
+}
+template <class T>
+cudaError_t dev_malloc_async(T** p, size_t bytes, cudaStream_t st) {
+  return dev_malloc_async(reinterpret_cast<void**>(p), bytes, st);
+}
+
+// The status of a failed CUDA call: out of device memory is RLXPP_ERR_NOMEM.
+rlxpp_status cuda_status(cudaError_t e) {
+  return e == cudaErrorMemoryAllocation ? RLXPP_ERR_NOMEM : RLXPP_ERR_CUDA;
 }
 
 #define RLX_CUDA(expr)                                                                  \
   do {                                                                                  \
     cudaError_t e_ = (expr);                                                            \
     if (e_ != cudaSuccess) {                                                            \
-      return fail(e_ == cudaErrorMemoryAllocation ? RLXPP_ERR_NOMEM : RLXPP_ERR_CUDA,   \
-                  std::string(#expr) + ": " + cudaGetErrorString(e_));                  \
+      return fail(cuda_status(e_), std::string(#expr) + ": " + cudaGetErrorString(e_)); \
     }                                                                                   \
   } while (0)
 
@@ -66,7 +112,7 @@ rlxpp_status stage_in(const void* src, size_t bytes, cudaStream_t st, Staged& ou
     out.dev = const_cast<void*>(src);
     return RLXPP_OK;
   }
-  RLX_CUDA(cudaMallocAsync(&out.dev, bytes, st));
+  RLX_CUDA(dev_malloc_async(&out.dev, bytes, st));
   out.owned = true;
   RLX_CUDA(cudaMemcpyAsync(out.dev, src, bytes, cudaMemcpyHostToDevice, st));
   RLX_CUDA(cudaStreamSynchronize(st));
@@ -83,7 +129,7 @@ rlxpp_status setup_levels(rlxpp_gen* g, cudaStream_t st) {
   for (uint32_t l = 0; l < g->n_levels; ++l) {
     cudaError_t e = launch_level_setup(g->levels[l], g->lux + (size_t)l * 18,
                                        g->table + (size_t)l * kTableLimbs, st);
-    if (e != cudaSuccess) return fail(RLXPP_ERR_CUDA, std::string("level setup: ") + cudaGetErrorString(e));
+    if (e != cudaSuccess) return fail(cuda_status(e), std::string("level setup: ") + cudaGetErrorString(e));
   }
   std::vector<uint32_t> limbs(18 * g->n_levels);
   RLX_CUDA(cudaMemcpyAsync(limbs.data(), g->lux, sizeof(uint32_t) * limbs.size(), cudaMemcpyDeviceToHost, st));
@@ -146,6 +192,8 @@ cudaError_t launch_path(const rlxpp_gen* g, int kind, const DrawArgs& a, cudaStr
 // copied back on a second stream while the next chunk computes.
 rlxpp_status draw_common(rlxpp_gen* g, int kind, const int64_t* counts, const int64_t* offsets,
                          int64_t count_each, void* out, size_t elem, cudaStream_t st) {
+  RLX_LOG_CALL("draw kind %d gen %p count_each %lld per-stream counts %s out %p", kind, (void*)g,
+               (long long)count_each, counts ? "yes" : "no", out);
   if (rlxpp_status s = check_gen(g)) return s;
   if (g->n == 0) return RLXPP_OK;
   if (!counts && count_each < 0) return fail(RLXPP_ERR_INVALID, "count_each must be >= 0");
@@ -164,7 +212,7 @@ rlxpp_status draw_common(rlxpp_gen* g, int kind, const int64_t* counts, const in
   if (on_device(out)) {
     a.out = out;
     cudaError_t e = launch_path(g, kind, a, st);
-    if (e != cudaSuccess) return fail(RLXPP_ERR_CUDA, std::string("draw: ") + cudaGetErrorString(e));
+    if (e != cudaSuccess) return fail(cuda_status(e), std::string("draw: ") + cudaGetErrorString(e));
     return RLXPP_OK;
   }
   if (counts) {
@@ -180,7 +228,7 @@ rlxpp_status draw_common(rlxpp_gen* g, int kind, const int64_t* counts, const in
     }
     if (total == 0) return RLXPP_OK;
     void* dev = nullptr;
-    RLX_CUDA(cudaMallocAsync(&dev, (size_t)total * elem, st));
+    RLX_CUDA(dev_malloc_async(&dev, (size_t)total * elem, st));
     // keep untouched elements of the caller's buffer: start from its contents
     cudaError_t e = cudaMemcpyAsync(dev, out, (size_t)total * elem, cudaMemcpyHostToDevice, st);
     a.out = dev;
@@ -188,22 +236,29 @@ rlxpp_status draw_common(rlxpp_gen* g, int kind, const int64_t* counts, const in
     if (e == cudaSuccess) e = cudaMemcpyAsync(out, dev, (size_t)total * elem, cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     cudaFreeAsync(dev, st);
-    if (e != cudaSuccess) return fail(RLXPP_ERR_CUDA, std::string("draw to host: ") + cudaGetErrorString(e));
+    if (e != cudaSuccess) return fail(cuda_status(e), std::string("draw to host: ") + cudaGetErrorString(e));
     return RLXPP_OK;
   }
   if (count_each == 0) return RLXPP_OK;
-  // uniform counts: chunks of whole streams, double-buffered
+  // uniform counts: chunks of whole streams, double-buffered (one buffer when a second
+  // cannot be had)
   const size_t per_stream = (size_t)count_each * elem;
   uint64_t chunk = std::max<uint64_t>(1, kChunkBytes / per_stream);
   chunk = std::min<uint64_t>(chunk, g->n);
   void* buf[2] = {nullptr, nullptr};
-  RLX_CUDA(cudaMallocAsync(&buf[0], chunk * per_stream, st));
-  cudaError_t e = cudaMallocAsync(&buf[1], chunk * per_stream, st);
+  RLX_CUDA(dev_malloc_async(&buf[0], chunk * per_stream, st));
+  cudaError_t e = dev_malloc_async(&buf[1], chunk * per_stream, st);
+  if (e == cudaErrorMemoryAllocation) {
+    cudaGetLastError();
+    buf[1] = nullptr;
+    e = cudaSuccess;
+  }
+  const int nbuf = buf[1] ? 2 : 1;
   int k = 0;
   for (uint64_t s0 = 0; e == cudaSuccess && s0 < g->n; s0 += chunk, ++k) {
     const uint64_t s1 = std::min<uint64_t>(g->n, s0 + chunk);
-    const int b = k & 1;
-    if (k >= 2) e = cudaStreamWaitEvent(st, g->ev[2 + b], 0);  // buffer b copied out
+    const int b = k % nbuf;
+    if (k >= nbuf) e = cudaStreamWaitEvent(st, g->ev[2 + b], 0);  // buffer b copied out
     if (e != cudaSuccess) break;
     DrawArgs c = a;
     c.s.D = g->D + s0;  // a view of streams s0..s1-1 (plane stride stays n)
@@ -221,15 +276,26 @@ rlxpp_status draw_common(rlxpp_gen* g, int kind, const int64_t* counts, const in
   cudaError_t e2 = cudaStreamSynchronize(g->copy_stream);
   if (e == cudaSuccess) e = e2;
   cudaStreamWaitEvent(st, g->ev[2], 0);
-  cudaStreamWaitEvent(st, g->ev[3], 0);
+  if (nbuf == 2) cudaStreamWaitEvent(st, g->ev[3], 0);
   cudaFreeAsync(buf[0], st);
   if (buf[1]) cudaFreeAsync(buf[1], st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-  if (e != cudaSuccess) return fail(RLXPP_ERR_CUDA, std::string("draw to host: ") + cudaGetErrorString(e));
+  if (e != cudaSuccess)
+    return fail(cuda_status(e), std::string("draw to host: ") + cudaGetErrorString(e));
   return RLXPP_OK;
 }
 
 }  // namespace
+
+// Failure injection for the tests (rlxpp_test_fail_alloc): the device allocation that
+// brings the countdown to zero reports cudaErrorMemoryAllocation without allocating.
+bool rlxpp::injected_alloc_failure() {
+  int64_t c = g_fail_alloc.load();
+  while (c >= 0) {
+    if (g_fail_alloc.compare_exchange_weak(c, c - 1)) return c == 0;
+  }
+  return false;
+}
 
 rlxpp_status rlxpp::set_last_error(rlxpp_status code, const char* msg) {
   return fail(code, msg);
@@ -240,6 +306,8 @@ extern "C" {
 rlxpp_status rlxpp_create(uint64_t n_streams, const uint32_t* levels, uint32_t n_levels,
                           const uint8_t* level_of_stream, const uint64_t* seeds,
                           void* cuda_stream, rlxpp_gen** out) {
+  RLX_LOG_CALL("create %llu streams, %u levels (first p %u)", (unsigned long long)n_streams, n_levels,
+               levels && n_levels ? levels[0] : 0u);
   if (!out) return fail(RLXPP_ERR_INVALID, "null output handle pointer");
   *out = nullptr;
   if (!levels || n_levels == 0 || n_levels > RLXPP_MAX_LEVELS)
@@ -263,12 +331,12 @@ rlxpp_status rlxpp_create(uint64_t n_streams, const uint32_t* levels, uint32_t n
   g->n_levels = n_levels;
   std::memcpy(g->levels, levels, sizeof(uint32_t) * n_levels);
   const size_t nn = std::max<uint64_t>(n_streams, 1);
-  cudaError_t e = cudaMalloc(&g->D, sizeof(uint64_t) * 9 * nn);
-  if (e == cudaSuccess) e = cudaMalloc(&g->meta, sizeof(uint32_t) * nn);
-  if (e == cudaSuccess) e = cudaMalloc(&g->lux, sizeof(uint32_t) * 18 * n_levels);
-  if (e == cudaSuccess) e = cudaMalloc(&g->table, sizeof(uint32_t) * kTableLimbs * n_levels);
-  if (e == cudaSuccess) e = cudaMalloc(&g->level_p, sizeof(uint32_t) * n_levels);
-  if (e == cudaSuccess) e = cudaMalloc(&g->status, sizeof(int));
+  cudaError_t e = dev_malloc(&g->D, sizeof(uint64_t) * 9 * nn);
+  if (e == cudaSuccess) e = dev_malloc(&g->meta, sizeof(uint32_t) * nn);
+  if (e == cudaSuccess) e = dev_malloc(&g->lux, sizeof(uint32_t) * 18 * n_levels);
+  if (e == cudaSuccess) e = dev_malloc(&g->table, sizeof(uint32_t) * kTableLimbs * n_levels);
+  if (e == cudaSuccess) e = dev_malloc(&g->level_p, sizeof(uint32_t) * n_levels);
+  if (e == cudaSuccess) e = dev_malloc(&g->status, sizeof(int));
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&g->copy_stream, cudaStreamNonBlocking);
   for (auto& ev : g->ev)
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
@@ -279,20 +347,19 @@ rlxpp_status rlxpp_create(uint64_t n_streams, const uint32_t* levels, uint32_t n
       e = cudaEventCreateWithFlags(&g->level_event[l], cudaEventDisableTiming);
   }
   if (e != cudaSuccess)
-    return bail(fail(e == cudaErrorMemoryAllocation ? RLXPP_ERR_NOMEM : RLXPP_ERR_CUDA,
-                     std::string("create: ") + cudaGetErrorString(e)));
+    return bail(fail(cuda_status(e), std::string("create: ") + cudaGetErrorString(e)));
   e = cudaMemsetAsync(g->status, 0, sizeof(int), st);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(g->level_p, g->levels, sizeof(uint32_t) * n_levels, cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess) e = cudaMemsetAsync(g->D, 0, sizeof(uint64_t) * 9 * nn, st);
   if (e == cudaSuccess) e = cudaMemsetAsync(g->meta, 0, sizeof(uint32_t) * nn, st);
-  if (e != cudaSuccess) return bail(fail(RLXPP_ERR_CUDA, std::string("create: ") + cudaGetErrorString(e)));
+  if (e != cudaSuccess) return bail(fail(cuda_status(e), std::string("create: ") + cudaGetErrorString(e)));
   if (rlxpp_status s = setup_levels(g, st)) return bail(s);
   {  // tensor-path matrices of every level; the tensor path is the default
-    e = cudaMalloc(&g->tc_matrix, tc_matrix_bytes() * n_levels);
+    e = dev_malloc(&g->tc_matrix, tc_matrix_bytes() * n_levels);
     for (uint32_t l = 0; e == cudaSuccess && l < n_levels; ++l)
       e = launch_tc_matrix(g->lux + (size_t)l * 18, static_cast<char*>(g->tc_matrix) + tc_matrix_bytes() * l, st);
-    if (e != cudaSuccess) return bail(fail(RLXPP_ERR_CUDA, std::string("tensor setup: ") + cudaGetErrorString(e)));
+    if (e != cudaSuccess) return bail(fail(cuda_status(e), std::string("tensor setup: ") + cudaGetErrorString(e)));
     g->path = RLXPP_PATH_TENSOR;
   }
   if (n_streams > 0) {
@@ -301,12 +368,12 @@ rlxpp_status rlxpp_create(uint64_t n_streams, const uint32_t* levels, uint32_t n
     if (rlxpp_status s = stage_in(level_of_stream, n_streams, st, sl)) return bail(s);
     e = launch_seed(g->view(), static_cast<const uint64_t*>(ss.dev), static_cast<const uint8_t*>(sl.dev),
                     n_levels, false, st);
-    if (e != cudaSuccess) return bail(fail(RLXPP_ERR_CUDA, std::string("seed: ") + cudaGetErrorString(e)));
+    if (e != cudaSuccess) return bail(fail(cuda_status(e), std::string("seed: ") + cudaGetErrorString(e)));
     g->level_host.assign(n_streams, 0);
     if (sl.dev) {  // host copy of the level indices (out-of-range ones were seeded at level 0)
       e = cudaMemcpyAsync(g->level_host.data(), sl.dev, n_streams, cudaMemcpyDeviceToHost, st);
       if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-      if (e != cudaSuccess) return bail(fail(RLXPP_ERR_CUDA, std::string("levels: ") + cudaGetErrorString(e)));
+      if (e != cudaSuccess) return bail(fail(cuda_status(e), std::string("levels: ") + cudaGetErrorString(e)));
       for (auto& l : g->level_host)
         if (l >= n_levels) l = 0;
     }
@@ -316,6 +383,7 @@ rlxpp_status rlxpp_create(uint64_t n_streams, const uint32_t* levels, uint32_t n
 }
 
 rlxpp_status rlxpp_seed(rlxpp_gen* g, const uint64_t* seeds, void* cuda_stream) {
+  RLX_LOG_CALL("seed gen %p", (void*)g);
   if (rlxpp_status s = check_gen(g)) return s;
   if (g->n == 0) return RLXPP_OK;
   if (!seeds) return fail(RLXPP_ERR_INVALID, "null seeds");
@@ -325,11 +393,12 @@ rlxpp_status rlxpp_seed(rlxpp_gen* g, const uint64_t* seeds, void* cuda_stream) 
   if (rlxpp_status s = stage_in(seeds, sizeof(uint64_t) * g->n, st, ss)) return s;
   cudaError_t e = launch_seed(g->view(), static_cast<const uint64_t*>(ss.dev), nullptr, g->n_levels,
                               true, st);
-  if (e != cudaSuccess) return fail(RLXPP_ERR_CUDA, std::string("seed: ") + cudaGetErrorString(e));
+  if (e != cudaSuccess) return fail(cuda_status(e), std::string("seed: ") + cudaGetErrorString(e));
   return RLXPP_OK;
 }
 
 rlxpp_status rlxpp_skip(rlxpp_gen* g, const uint64_t* n128, void* cuda_stream) {
+  RLX_LOG_CALL("skip gen %p", (void*)g);
   if (rlxpp_status s = check_gen(g)) return s;
   if (g->n == 0) return RLXPP_OK;
   if (!n128) return fail(RLXPP_ERR_INVALID, "null skip distances");
@@ -337,7 +406,7 @@ rlxpp_status rlxpp_skip(rlxpp_gen* g, const uint64_t* n128, void* cuda_stream) {
   Staged sn;
   if (rlxpp_status s = stage_in(n128, sizeof(uint64_t) * 2 * g->n, st, sn)) return s;
   cudaError_t e = launch_skip(g->view(), static_cast<const uint64_t*>(sn.dev), st);
-  if (e != cudaSuccess) return fail(RLXPP_ERR_CUDA, std::string("skip: ") + cudaGetErrorString(e));
+  if (e != cudaSuccess) return fail(cuda_status(e), std::string("skip: ") + cudaGetErrorString(e));
   return RLXPP_OK;
 }
 
@@ -379,7 +448,7 @@ rlxpp_status rlxpp_skip_values(rlxpp_gen* g, const uint64_t* n_values, uint32_t 
   if (rlxpp_status s = stage_in(n_values, sizeof(uint64_t) * g->n, st, sn)) return s;
   cudaError_t e = launch_skip_values(g->view(), static_cast<const uint64_t*>(sn.dev),
                                      kind == RLXPP_KIND_F64 ? 2u : 1u, st);
-  if (e != cudaSuccess) return fail(RLXPP_ERR_CUDA, std::string("skip values: ") + cudaGetErrorString(e));
+  if (e != cudaSuccess) return fail(cuda_status(e), std::string("skip values: ") + cudaGetErrorString(e));
   return RLXPP_OK;
 }
 
@@ -402,7 +471,7 @@ rlxpp_status rlxpp_draw_f64_sum_hist(rlxpp_gen* g, int64_t count_each, uint64_t*
     a.count_each = std::min(count_each - done, kMaxPerLaunch);
     a.accumulate_sums = done > 0;
     cudaError_t e = launch_path(g, kDrawSumHist, a, st);
-    if (e != cudaSuccess) return fail(RLXPP_ERR_CUDA, std::string("sum/hist: ") + cudaGetErrorString(e));
+    if (e != cudaSuccess) return fail(cuda_status(e), std::string("sum/hist: ") + cudaGetErrorString(e));
     done += a.count_each;
   } while (done < count_each);
   return RLXPP_OK;
@@ -416,16 +485,16 @@ rlxpp_status rlxpp_get_state(const rlxpp_gen* g, rlxpp_state* dst, void* cuda_st
   const size_t bytes = sizeof(rlxpp_state) * g->n;
   if (on_device(dst)) {
     cudaError_t e = launch_export(g->view(), g->level_p, dst, st);
-    if (e != cudaSuccess) return fail(RLXPP_ERR_CUDA, std::string("export: ") + cudaGetErrorString(e));
+    if (e != cudaSuccess) return fail(cuda_status(e), std::string("export: ") + cudaGetErrorString(e));
     return RLXPP_OK;
   }
   void* dev = nullptr;
-  RLX_CUDA(cudaMallocAsync(&dev, bytes, st));
+  RLX_CUDA(dev_malloc_async(&dev, bytes, st));
   cudaError_t e = launch_export(g->view(), g->level_p, static_cast<rlxpp_state*>(dev), st);
   if (e == cudaSuccess) e = cudaMemcpyAsync(dst, dev, bytes, cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   cudaFreeAsync(dev, st);
-  if (e != cudaSuccess) return fail(RLXPP_ERR_CUDA, std::string("export: ") + cudaGetErrorString(e));
+  if (e != cudaSuccess) return fail(cuda_status(e), std::string("export: ") + cudaGetErrorString(e));
   return RLXPP_OK;
 }
 
@@ -438,7 +507,7 @@ rlxpp_status rlxpp_set_state(rlxpp_gen* g, const rlxpp_state* src, void* cuda_st
   if (rlxpp_status s = stage_in(src, sizeof(rlxpp_state) * g->n, st, ss)) return s;
   cudaError_t e = launch_import(g->view(), g->level_p, g->n_levels,
                                 static_cast<const rlxpp_state*>(ss.dev), st);
-  if (e != cudaSuccess) return fail(RLXPP_ERR_CUDA, std::string("import: ") + cudaGetErrorString(e));
+  if (e != cudaSuccess) return fail(cuda_status(e), std::string("import: ") + cudaGetErrorString(e));
   g->level_host_stale = true;  // levels may have changed; the next request plan re-reads them
   return RLXPP_OK;
 }
@@ -472,7 +541,15 @@ uint64_t rlxpp_num_streams(const rlxpp_gen* g) { return g ? g->n : 0; }
 
 const char* rlxpp_last_error(void) { return g_last_error.c_str(); }
 
-void rlxpp_destroy(rlxpp_gen* g) { free_gen(g); }
+void rlxpp_destroy(rlxpp_gen* g) {
+  RLX_LOG_CALL("destroy gen %p", (void*)g);
+  free_gen(g);
+}
+
+rlxpp_status rlxpp_test_fail_alloc(int64_t after) {
+  g_fail_alloc.store(after < 0 ? -1 : after);
+  return RLXPP_OK;
+}
 
 // ---- unit-test entry points --------------------------------------------------------
 static rlxpp_status run_test(int op, const void* x, const void* y, void* out, void* carry,
@@ -482,7 +559,7 @@ static rlxpp_status run_test(int op, const void* x, const void* y, void* out, vo
   cudaError_t e = launch_test(op, static_cast<const uint64_t*>(x), static_cast<const uint64_t*>(y),
                               static_cast<uint64_t*>(out), static_cast<uint32_t*>(carry), n,
                               as_stream(cuda_stream));
-  if (e != cudaSuccess) return fail(RLXPP_ERR_CUDA, std::string("test kernel: ") + cudaGetErrorString(e));
+  if (e != cudaSuccess) return fail(cuda_status(e), std::string("test kernel: ") + cudaGetErrorString(e));
   return RLXPP_OK;
 }
 
@@ -543,10 +620,10 @@ static rlxpp_status tc_test(uint32_t p, const uint64_t* x, uint64_t* out, uint64
   uint32_t *lux = nullptr, *table = nullptr;
   void* mat = nullptr;
   int* status = nullptr;
-  cudaError_t e = cudaMalloc(&lux, sizeof(uint32_t) * 18);
-  if (e == cudaSuccess) e = cudaMalloc(&table, sizeof(uint32_t) * kTableLimbs);
-  if (e == cudaSuccess) e = cudaMalloc(&mat, tc_matrix_bytes());
-  if (e == cudaSuccess) e = cudaMalloc(&status, sizeof(int));
+  cudaError_t e = dev_malloc(&lux, sizeof(uint32_t) * 18);
+  if (e == cudaSuccess) e = dev_malloc(&table, sizeof(uint32_t) * kTableLimbs);
+  if (e == cudaSuccess) e = dev_malloc(&mat, tc_matrix_bytes());
+  if (e == cudaSuccess) e = dev_malloc(&status, sizeof(int));
   if (e == cudaSuccess) e = cudaMemsetAsync(status, 0, sizeof(int), st);
   if (e == cudaSuccess) e = launch_level_setup(p, lux, table, st);
   if (e == cudaSuccess) e = launch_tc_matrix(lux, mat, st);
@@ -558,7 +635,7 @@ static rlxpp_status tc_test(uint32_t p, const uint64_t* x, uint64_t* out, uint64
   cudaFree(table);
   cudaFree(mat);
   cudaFree(status);
-  if (e != cudaSuccess) return fail(RLXPP_ERR_CUDA, std::string("tensor test: ") + cudaGetErrorString(e));
+  if (e != cudaSuccess) return fail(cuda_status(e), std::string("tensor test: ") + cudaGetErrorString(e));
   if (h) return fail((rlxpp_status)h, "tensor test: a bounded device wait gave up");
   return RLXPP_OK;
 }
@@ -566,14 +643,14 @@ static rlxpp_status tc_test(uint32_t p, const uint64_t* x, uint64_t* out, uint64
 rlxpp_status rlxpp_luxury_multiplier(uint32_t p, uint64_t* out9) {
   if (p == 0 || !out9) return fail(RLXPP_ERR_INVALID, "need p >= 1 and an output");
   uint32_t *lux = nullptr, *table = nullptr;
-  RLX_CUDA(cudaMalloc(&lux, sizeof(uint32_t) * 18));
-  cudaError_t e = cudaMalloc(&table, sizeof(uint32_t) * kTableLimbs);
+  RLX_CUDA(dev_malloc(&lux, sizeof(uint32_t) * 18));
+  cudaError_t e = dev_malloc(&table, sizeof(uint32_t) * kTableLimbs);
   if (e == cudaSuccess) e = launch_level_setup(p, lux, table, nullptr);
   uint32_t h[18] = {};
   if (e == cudaSuccess) e = cudaMemcpy(h, lux, sizeof h, cudaMemcpyDeviceToHost);
   cudaFree(lux);
   cudaFree(table);
-  if (e != cudaSuccess) return fail(RLXPP_ERR_CUDA, std::string("luxury multiplier: ") + cudaGetErrorString(e));
+  if (e != cudaSuccess) return fail(cuda_status(e), std::string("luxury multiplier: ") + cudaGetErrorString(e));
   for (int k = 0; k < 9; ++k) out9[k] = ((uint64_t)h[2 * k + 1] << 32) | h[2 * k];
   return RLXPP_OK;
 }

@@ -345,6 +345,7 @@ rlxpp_status plan_impl(rlxpp_gen* g, const rlxpp_request* reqs, uint64_t n_reqs,
   p->has_f64 = has_f64;
   const size_t nr = std::max<uint64_t>(n_reqs, 1);
   auto alloc = [&](void** ptr, size_t bytes) {
+    if (injected_alloc_failure()) return cudaErrorMemoryAllocation;
     return stream_ordered ? cudaMallocAsync(ptr, bytes, st) : cudaMalloc(ptr, bytes);
   };
   auto upload = [&](void* dst, const void* src, size_t bytes) {

@@ -83,6 +83,10 @@ cudaError_t launch_tc_matrix(const uint32_t* lux18, void* bimg, cudaStream_t st)
 cudaError_t launch_draw_tc(int kind, const DrawArgs& a, const void* bimg, cudaStream_t st);
 cudaError_t launch_tc_mulmod(const void* bimg, const uint64_t* x, uint64_t* out, uint64_t n, int* status,
                              cudaStream_t st, bool issue = true);
+// True when rlxpp_test_fail_alloc asked for this device allocation to fail (the caller
+// then reports cudaErrorMemoryAllocation without allocating).
+bool injected_alloc_failure();
+
 cudaError_t launch_test(int which, const uint64_t* x, const uint64_t* y, uint64_t* out,
                         uint32_t* carry, uint64_t n, cudaStream_t st);
 

@@ -12,6 +12,12 @@ batch on one of several CUDA streams while earlier batches still run, copied to 
 pinned host mirror of the arena, and completed when its copy has finished: the small
 requests of a batch are copied first (adjacent blocks in one copy), then each large one
 by itself, smallest first, each group with its own event.
+
+Admission: with a bound on the bytes waiting for the arena (max_queued_bytes), a request
+that would exceed it, or one larger than the whole arena, is rejected at submission and
+takes no numbers from its stream (the next request of that stream gets the segment).
+Cancellation: a request not yet launched can be cancelled; its segment of the stream is
+then skipped, as if drawn and discarded.
 """
 from __future__ import annotations
 
@@ -94,12 +100,14 @@ class Request:
     reserved: int = 0
     launch: float = 0.0
     done: float = 0.0
+    status: str = "waiting"   # waiting, admitted, launched, done, rejected, cancelled
     result: np.ndarray | None = field(default=None, repr=False)
 
 
 class Server:
     def __init__(self, n_resident, luxury=2048, seeds=None, pool_bytes=1 << 30, n_cuda_streams=4,
-                 max_batch=512, keep_results=False, copy_to_host=True, small_bytes=1 << 20):
+                 max_batch=512, keep_results=False, copy_to_host=True, small_bytes=1 << 20,
+                 max_queued_bytes=None):
         import torch
         self.torch = torch
         if seeds is None:
@@ -120,6 +128,11 @@ class Server:
         self.small_bytes = small_bytes   # requests below this size share one copy group
         self.keep_results = keep_results
         self.finished = []
+        self.max_queued_bytes = max_queued_bytes
+        self.queued_bytes = 0      # bytes of the requests waiting for the arena
+        self.pending = {}          # rid -> request not yet launched
+        self.rejected = []
+        self.cancelled = []
         self.t0 = time.perf_counter()
 
     def now(self):
@@ -127,15 +140,38 @@ class Server:
 
     # -- request life cycle -----------------------------------------------------------
     def submit(self, rid, stream, kind, count, arrival=None):
+        """Queue a request; returns it with status "waiting", or "rejected" when it is
+        larger than the arena or would push the waiting bytes past max_queued_bytes."""
         r = Request(rid, int(stream), int(kind), int(count), self.now() if arrival is None else arrival)
+        r.nbytes = r.count * (8 if r.kind == KIND_F64 else 4)
+        if r.nbytes > self.arena.size or (self.max_queued_bytes is not None and
+                                          self.queued_bytes + r.nbytes > self.max_queued_bytes):
+            r.status = "rejected"
+            self.rejected.append(r)
+            return r
         b, p = self.cur_block[r.stream], self.cur_pos[r.stream]
         r.skip, r.pos = b, p
         self.cur_block[r.stream], self.cur_pos[r.stream] = advance_cursor(b, p, r.kind, r.count)
-        r.nbytes = r.count * (8 if r.kind == KIND_F64 else 4)
-        if r.nbytes > self.arena.size:
-            raise ValueError(f"request {rid} needs {r.nbytes} bytes, more than the whole arena")
+        self.queued_bytes += r.nbytes
+        self.pending[r.rid] = r
         self.waiting.append(r)
         return r
+
+    def cancel(self, rid):
+        """Cancel a request that has not been launched; returns False if it has (or is
+        unknown).  Its arena block, if any, is released at once."""
+        r = self.pending.pop(rid, None)
+        if r is None:
+            return False
+        if r.status == "waiting":
+            self.waiting.remove(r)
+            self.queued_bytes -= r.nbytes
+        else:
+            self.admitted.remove(r)
+            self.arena.release(r.offset, r.reserved)
+        r.status = "cancelled"
+        self.cancelled.append(r)
+        return True
 
     def _admit(self):
         while self.waiting:
@@ -145,6 +181,8 @@ class Server:
                 return
             r.offset, r.reserved = got
             self.waiting.popleft()
+            self.queued_bytes -= r.nbytes
+            r.status = "admitted"
             self.admitted.append(r)
 
     def _dispatch(self):
@@ -196,6 +234,8 @@ class Server:
             t = self.now()
             for r in batch:
                 r.launch = t
+                r.status = "launched"
+                self.pending.pop(r.rid, None)
             self.inflight.append((si, collections.deque(groups)))
 
     def _complete(self, wait_first=False):
@@ -212,6 +252,7 @@ class Server:
                 t = self.now()
                 for r in done:
                     r.done = t
+                    r.status = "done"
                     if self.keep_results and self.host is not None and r.nbytes:
                         raw = self.host[r.offset:r.offset + r.nbytes].numpy()
                         r.result = raw.view(np.uint64 if r.kind == KIND_F64 else np.uint32).copy()
@@ -278,7 +319,8 @@ class Server:
         last = max(r.done for r in self.finished)
         values = sum(r.count for r in self.finished)
         doubles = sum(r.count for r in self.finished if r.kind == KIND_F64)
-        return {"requests": len(self.finished), "values": values, "doubles": doubles,
+        return {"requests": len(self.finished), "rejected": len(self.rejected), "cancelled": len(self.cancelled),
+                "values": values, "doubles": doubles,
                 "seconds": last - first, "values_per_s": values / (last - first),
                 "doubles_per_s": doubles / (last - first),
                 "p50_ms": float(np.percentile(lat, 50) * 1e3), "p99_ms": float(np.percentile(lat, 99) * 1e3),

@@ -76,3 +76,29 @@ def test_argument_errors_need_no_gpu(lib_path):
         B.rlxpp_draw_f64(None, None, 1)          # null handle
     with pytest.raises(B.RlxppError):
         B.rlxpp_luxury_multiplier(0)
+
+
+@pytest.mark.parametrize("level", ["0", "1"])
+def test_log_level_reports_argument_errors(lib_path, level):
+    """RLXPP_LOG=1 writes each failure (here argument errors, which return before any CUDA
+    call) with its status to stderr; unset or 0 keeps the library silent."""
+    import subprocess
+    import sys
+    code = (
+        "import ctypes, sys\n"
+        f"L = ctypes.CDLL({lib_path!r})\n"
+        "L.rlxpp_create.argtypes = [ctypes.c_uint64, ctypes.c_void_p, ctypes.c_uint32, ctypes.c_void_p,\n"
+        "                           ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]\n"
+        "h = ctypes.c_void_p()\n"
+        "s = L.rlxpp_create(1, None, 0, None, None, None, ctypes.byref(h))\n"
+        "L.rlxpp_last_error.restype = ctypes.c_char_p\n"
+        "print(s, L.rlxpp_last_error().decode())\n")
+    env = dict(os.environ, RLXPP_LOG=level)
+    p = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, timeout=120)
+    assert p.returncode == 0, p.stderr
+    status, msg = p.stdout.split(" ", 1)
+    assert int(status) == 1 and "luxury levels" in msg           # RLXPP_ERR_INVALID
+    if level == "1":
+        assert "rlxpp: error 1: " in p.stderr and "luxury levels" in p.stderr
+    else:
+        assert "rlxpp:" not in p.stderr

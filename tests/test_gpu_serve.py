@@ -67,3 +67,79 @@ def test_serving_results_alone_and_in_mix(native):
             assert np.array_equal(r.result, want.view(np.uint64) if r.kind == 1 else want), (s, r.rid)
     srv.close()
     g.close()
+
+
+def _stream_reference(stream, requests):
+    """The oracle's values for one stream's requests in submission order, each drawn
+    whether or not it ran (a cancelled request's segment is skipped, not reused)."""
+    ref = StreamSet.from_seeds([stream + 1], 2048)
+    out = {}
+    for r in requests:
+        vals = ref.draw(r.count, S.KIND_F64 if r.kind == 1 else S.KIND_U24)[0]
+        out[r.rid] = vals.view(np.uint64) if r.kind == 1 else vals
+    return out
+
+
+def test_admission_rejects_without_taking_stream_numbers(native):
+    """A bound on the bytes waiting for the arena: requests past it, and one larger than
+    the whole arena, are rejected at submission; the accepted requests of each stream
+    still read its sequence without a gap."""
+    from paper_2106_02504_gb300.serve import Server
+    srv = Server(4, pool_bytes=1 << 16, n_cuda_streams=2, max_batch=4, keep_results=True,
+                 max_queued_bytes=40_000)
+    rng = np.random.Generator(np.random.PCG64(11))
+    subs = []
+    for rid in range(24):        # submitted before any pumping: the queue fills up
+        stream, kind, count = int(rng.integers(0, 4)), int(rng.integers(0, 2)), int(rng.integers(1, 2500))
+        subs.append(srv.submit(rid, stream, kind, count))
+    big = srv.submit(99, 0, 1, 10_000)       # 80,000 bytes: more than the arena
+    assert big.status == "rejected"
+    rejected = [r for r in subs if r.status == "rejected"]
+    accepted = [r for r in subs if r.status == "waiting"]
+    assert rejected and accepted and sum(r.nbytes for r in accepted) <= 40_000
+    srv.drain()
+    # after the queue drained, a request is accepted again
+    late = srv.submit(100, 1, 0, 500)
+    assert late.status == "waiting"
+    srv.drain()
+    stats = srv.stats()
+    assert stats["rejected"] == len(rejected) + 1 and stats["requests"] == len(accepted) + 1
+    done = accepted + [late]
+    assert all(r.status == "done" for r in done) and all(r.result is None for r in rejected)
+    for s in range(4):
+        mine = [r for r in done if r.stream == s]
+        want = _stream_reference(s, mine)
+        for r in mine:
+            assert np.array_equal(r.result, want[r.rid]), (s, r.rid)
+    srv.close()
+
+
+def test_cancel_before_launch(native):
+    """Requests cancelled while waiting for the arena or admitted but not launched are
+    dropped (their arena block released at once) and their segments skipped; a launched
+    request cannot be cancelled; the rest equal the oracle."""
+    from paper_2106_02504_gb300.serve import Server
+    srv = Server(2, pool_bytes=1 << 15, n_cuda_streams=1, max_batch=1, keep_results=True)
+    reqs = [srv.submit(rid, rid % 2, rid % 2, 600 + 50 * rid) for rid in range(8)]
+    assert srv.cancel(1)                        # waiting
+    srv.pump()                                  # admits what fits, launches one batch of one
+    launched = [r for r in reqs if r.status == "launched"]
+    admitted = [r for r in reqs if r.status == "admitted"]
+    assert len(launched) == 1 and admitted
+    assert not srv.cancel(launched[0].rid)
+    used = srv.arena.used
+    victim = admitted[-1]
+    assert srv.cancel(victim.rid) and srv.arena.used == used - victim.reserved
+    assert not srv.cancel(victim.rid) and not srv.cancel(12345)
+    srv.drain()
+    cancelled = {1, victim.rid}
+    assert {r.rid for r in srv.cancelled} == cancelled and srv.stats()["cancelled"] == 2
+    for s in range(2):
+        mine = [r for r in reqs if r.stream == s]
+        want = _stream_reference(s, mine)
+        for r in mine:
+            if r.rid in cancelled:
+                assert r.status == "cancelled" and r.result is None
+            else:
+                assert r.status == "done" and np.array_equal(r.result, want[r.rid]), r.rid
+    srv.close()
