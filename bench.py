@@ -535,11 +535,12 @@ def run_e2e(args, nat, g, seeds_h, n, world, dev, dist):
     sp = torch.cuda.current_stream().cuda_stream
 
     def step():
-        nat.rlxpp_seed(g.handle, seeds_pin, sp)                       # host seeds
-        nat.rlxpp_draw_f64(g.handle, out_pin, HBM_COUNT, None, None, sp)  # host output
-        nat.rlxpp_draw_f64_sum_hist(g.handle, FUSED_COUNT, sums, hist, sp)
+        nat.rlxpp_seed(g.handle, seeds_pin, sp)                              # host seeds
+        nat.rlxpp_draw_f64_host_async(g.handle, out_pin, HBM_COUNT, sp)       # host output
+        nat.rlxpp_draw_f64_sum_hist(g.handle, FUSED_COUNT, sums, hist, sp)   # under its copies
         sums_h.copy_(sums, non_blocking=True)
         hist_h.copy_(hist, non_blocking=True)
+        nat.rlxpp_host_wait(g.handle, sp)
         torch.cuda.current_stream().synchronize()
 
     steps = max(1, min(args.steps, 3))
@@ -559,8 +560,9 @@ def run_e2e(args, nat, g, seeds_h, n, world, dev, dist):
     doubles = n * (HBM_COUNT + FUSED_COUNT) * world * steps
     return {"value": doubles / dt, "unit": UNIT, "h2d_bytes_per_step": n * 8,
             "d2h_bytes_per_step": n * HBM_COUNT * 8 + n * 8 + 256 * 8, "steps": steps,
-            "how": "rlxpp_seed from pinned host seeds, rlxpp_draw_f64 into pinned host memory (library-staged, "
-                   "double-buffered), fused sum/hist with sums+hist read back; wall clock"}
+            "how": "rlxpp_seed from pinned host seeds, rlxpp_draw_f64_host_async into pinned host memory "
+                   "(library-staged, copied on the library's copy stream while the fused sum/hist draw runs), "
+                   "sums+hist read back, rlxpp_host_wait; wall clock"}
 
 
 def main():

@@ -118,6 +118,25 @@ rlxpp_status rlxpp_draw_u24(rlxpp_gen* gen, const int64_t* counts, const int64_t
 rlxpp_status rlxpp_draw_f64(rlxpp_gen* gen, const int64_t* counts, const int64_t* offsets,
                             int64_t count_each, double* out, void* cuda_stream);
 
+/* Asynchronous draws into page-locked host memory (the values of rlxpp_draw_u24 and
+ * rlxpp_draw_f64 with one count for all streams: row i of out holds stream i's
+ * count_each values).  The values are computed on cuda_stream into a device staging
+ * buffer that the handle owns and copied to out on the handle's internal copy stream;
+ * the call returns once the work is queued.  The streams advance in cuda_stream's
+ * order, so later calls on that stream (device draws, skips) run without waiting for
+ * the copies.  out is complete once a stream made to wait by rlxpp_host_wait has
+ * reached that point; until then out must stay allocated and untouched.  A later
+ * asynchronous draw reuses the staging buffer after the earlier copies (in stream
+ * order, no host wait).  RLXPP_ERR_INVALID when out is not page-locked host memory. */
+rlxpp_status rlxpp_draw_u24_host_async(rlxpp_gen* gen, int64_t count_each, uint32_t* out,
+                                       void* cuda_stream);
+rlxpp_status rlxpp_draw_f64_host_async(rlxpp_gen* gen, int64_t count_each, double* out,
+                                       void* cuda_stream);
+
+/* Makes cuda_stream wait (on the device, without blocking the host) until the copies of
+ * every asynchronous host draw issued so far on this handle have completed. */
+rlxpp_status rlxpp_host_wait(rlxpp_gen* gen, void* cuda_stream);
+
 /* Draw single-precision floats in [0, 1): one RANLUX number w each, w 2^-24 (exact in
  * binary32; the 24-bit output RANLUX itself delivers, Sec. 1); float out, same layout
  * rules as rlxpp_draw_u24. */

@@ -71,6 +71,9 @@ def _load():
         "rlxpp_draw_f32": [_vp, _vp, _vp, _i64, _vp, _vp],
         "rlxpp_draw_normal_f64": [_vp, _vp, _vp, _i64, _vp, _vp],
         "rlxpp_draw_exp_f64": [_vp, _vp, _vp, _i64, _vp, _vp],
+        "rlxpp_draw_u24_host_async": [_vp, _i64, _vp, _vp],
+        "rlxpp_draw_f64_host_async": [_vp, _i64, _vp, _vp],
+        "rlxpp_host_wait": [_vp, _vp],
         "rlxpp_skip_values": [_vp, _vp, _u32, _vp],
         "rlxpp_draw_f64_sum_hist": [_vp, _i64, _vp, _vp, _vp],
         "rlxpp_get_state": [_vp, _vp, _vp],
@@ -191,6 +194,18 @@ def rlxpp_draw_normal_f64(gen, out, count_each=0, counts=None, offsets=None, str
 
 def rlxpp_draw_exp_f64(gen, out, count_each=0, counts=None, offsets=None, stream=None):
     _check(_lib.rlxpp_draw_exp_f64(gen, _ptr(counts), _ptr(offsets), count_each, _ptr(out), _stream(stream)))
+
+
+def rlxpp_draw_u24_host_async(gen, out, count_each, stream=None):
+    _check(_lib.rlxpp_draw_u24_host_async(gen, count_each, _ptr(out), _stream(stream)))
+
+
+def rlxpp_draw_f64_host_async(gen, out, count_each, stream=None):
+    _check(_lib.rlxpp_draw_f64_host_async(gen, count_each, _ptr(out), _stream(stream)))
+
+
+def rlxpp_host_wait(gen, stream=None):
+    _check(_lib.rlxpp_host_wait(gen, _stream(stream)))
 
 
 def rlxpp_skip_values(gen, n_values, kind, stream=None):
@@ -392,6 +407,15 @@ class Generator:
 
     def draw_exp_f64(self, out, count_each=0, counts=None, offsets=None, stream=None):
         rlxpp_draw_exp_f64(self.handle, out, count_each, counts, offsets, stream)
+
+    def draw_u24_host_async(self, out, count_each, stream=None):
+        rlxpp_draw_u24_host_async(self.handle, out, count_each, stream)
+
+    def draw_f64_host_async(self, out, count_each, stream=None):
+        rlxpp_draw_f64_host_async(self.handle, out, count_each, stream)
+
+    def host_wait(self, stream=None):
+        rlxpp_host_wait(self.handle, stream)
 
     def skip_values(self, n_values, kind, stream=None):
         rlxpp_skip_values(self.handle, n_values, kind, stream)

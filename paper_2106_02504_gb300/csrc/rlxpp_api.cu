@@ -159,6 +159,9 @@ void free_gen(rlxpp_gen* g) {
   cudaFree(g->level_p);
   cudaFree(g->status);
   cudaFree(g->tc_matrix);
+  cudaFree(g->host_stage);
+  if (g->chunk_ready) cudaEventDestroy(g->chunk_ready);
+  if (g->host_done) cudaEventDestroy(g->host_done);
   for (auto& e : g->ev)
     if (e) cudaEventDestroy(e);
   for (auto& e : g->level_event)
@@ -285,6 +288,56 @@ rlxpp_status draw_common(rlxpp_gen* g, int kind, const int64_t* counts, const in
   return RLXPP_OK;
 }
 
+// Asynchronous draw of count_each values per stream into page-locked host memory:
+// chunks of whole streams are computed on st into the handle's staging buffer and each
+// is copied out on the copy stream behind an event; nothing waits on the host.
+rlxpp_status draw_host_async(rlxpp_gen* g, int kind, int64_t count_each, void* out, size_t elem,
+                             cudaStream_t st) {
+  RLX_LOG_CALL("draw to host (asynchronous) kind %d gen %p count_each %lld out %p", kind, (void*)g,
+               (long long)count_each, out);
+  if (rlxpp_status s = check_gen(g)) return s;
+  if (count_each < 0) return fail(RLXPP_ERR_INVALID, "count_each must be >= 0");
+  if (g->n == 0 || count_each == 0) return RLXPP_OK;
+  if (!out) return fail(RLXPP_ERR_INVALID, "null output");
+  cudaPointerAttributes attr;
+  if (cudaPointerGetAttributes(&attr, out) != cudaSuccess || attr.type != cudaMemoryTypeHost) {
+    cudaGetLastError();
+    return fail(RLXPP_ERR_INVALID, "asynchronous host draws need page-locked host memory");
+  }
+  const size_t per_stream = (size_t)count_each * elem;
+  const size_t total = per_stream * g->n;
+  // the staging buffer is free again once the previous asynchronous draw's copies are done
+  RLX_CUDA(cudaStreamWaitEvent(st, g->host_done, 0));
+  if (g->host_stage_bytes < total) {
+    cudaFree(g->host_stage);  // waits for the device, copies of the old buffer included
+    g->host_stage = nullptr;
+    g->host_stage_bytes = 0;
+    RLX_CUDA(dev_malloc(&g->host_stage, total));
+    g->host_stage_bytes = total;
+  }
+  DrawArgs a = make_args(g);
+  a.count_each = count_each;
+  const uint64_t chunk = std::min<uint64_t>(g->n, std::max<uint64_t>(1, kChunkBytes / per_stream));
+  cudaError_t e = cudaSuccess;
+  for (uint64_t s0 = 0; e == cudaSuccess && s0 < g->n; s0 += chunk) {
+    const uint64_t s1 = std::min<uint64_t>(g->n, s0 + chunk);
+    DrawArgs c = a;
+    c.s.D = g->D + s0;  // a view of streams s0..s1-1 (plane stride stays n)
+    c.s.meta = g->meta + s0;
+    c.s.n = s1 - s0;
+    c.out = static_cast<char*>(g->host_stage) + s0 * per_stream;
+    e = launch_path(g, kind, c, st);
+    if (e == cudaSuccess) e = cudaEventRecord(g->chunk_ready, st);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(g->copy_stream, g->chunk_ready, 0);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(static_cast<char*>(out) + s0 * per_stream, c.out, (s1 - s0) * per_stream,
+                          cudaMemcpyDeviceToHost, g->copy_stream);
+  }
+  if (e == cudaSuccess) e = cudaEventRecord(g->host_done, g->copy_stream);
+  if (e != cudaSuccess) return fail(cuda_status(e), std::string("draw to host (asynchronous): ") + cudaGetErrorString(e));
+  return RLXPP_OK;
+}
+
 }  // namespace
 
 // Failure injection for the tests (rlxpp_test_fail_alloc): the device allocation that
@@ -340,6 +393,8 @@ rlxpp_status rlxpp_create(uint64_t n_streams, const uint32_t* levels, uint32_t n
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&g->copy_stream, cudaStreamNonBlocking);
   for (auto& ev : g->ev)
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&g->chunk_ready, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&g->host_done, cudaEventDisableTiming);
   if (n_levels > 1) {  // concurrent per-level launches of the request kernel
     for (uint32_t l = 0; l < n_levels && e == cudaSuccess; ++l)
       e = cudaStreamCreateWithFlags(&g->level_stream[l], cudaStreamNonBlocking);
@@ -425,6 +480,20 @@ rlxpp_status rlxpp_draw_f64(rlxpp_gen* g, const int64_t* counts, const int64_t* 
 rlxpp_status rlxpp_draw_f32(rlxpp_gen* g, const int64_t* counts, const int64_t* offsets,
                             int64_t count_each, float* out, void* cuda_stream) {
   return draw_common(g, kDrawF32, counts, offsets, count_each, out, sizeof(float), as_stream(cuda_stream));
+}
+
+rlxpp_status rlxpp_draw_u24_host_async(rlxpp_gen* g, int64_t count_each, uint32_t* out, void* cuda_stream) {
+  return draw_host_async(g, kDrawU24, count_each, out, sizeof(uint32_t), as_stream(cuda_stream));
+}
+
+rlxpp_status rlxpp_draw_f64_host_async(rlxpp_gen* g, int64_t count_each, double* out, void* cuda_stream) {
+  return draw_host_async(g, kDrawF64, count_each, out, sizeof(double), as_stream(cuda_stream));
+}
+
+rlxpp_status rlxpp_host_wait(rlxpp_gen* g, void* cuda_stream) {
+  if (rlxpp_status s = check_gen(g)) return s;
+  RLX_CUDA(cudaStreamWaitEvent(as_stream(cuda_stream), g->host_done, 0));
+  return RLXPP_OK;
 }
 
 rlxpp_status rlxpp_draw_normal_f64(rlxpp_gen* g, const int64_t* counts, const int64_t* offsets,

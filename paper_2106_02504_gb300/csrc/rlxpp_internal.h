@@ -125,6 +125,10 @@ struct rlxpp_gen {
   int* status = nullptr;        // sticky device status
   cudaStream_t copy_stream = nullptr;  // device-to-host copies of chunked host output
   cudaEvent_t ev[4] = {};
+  void* host_stage = nullptr;          // device staging of the asynchronous host draws
+  size_t host_stage_bytes = 0;
+  cudaEvent_t chunk_ready = nullptr;   // a staged chunk is complete (compute stream)
+  cudaEvent_t host_done = nullptr;     // the last asynchronous host draw's copies are done
   int sms = 0;                         // multiprocessors of the device
   std::map<uint32_t, rlxpp_tuning> tuned;  // request-shape signature -> tuner choice
   std::vector<uint8_t> level_host;         // host copy of every stream's level index
