@@ -152,18 +152,22 @@ __device__ __forceinline__ uint32_t wmod_m(uint32_t L, uint32_t H) {
   const unsigned l = lane_id();
   const uint32_t H0 = l < 10 ? H : (l == 10 ? (H & 0xFFFFu) : 0u);
   const uint32_t H1 = wshr336(H);  // lanes 0..7
-  const uint32_t A1 = wshl240(H0), A2 = wshl240(H1);
+  // A2 = H1 2^240 = (H >> 96) with bits below 240 cleared: limb 7 = the top half of H's
+  // limb 10, limbs 8..14 = H's limbs 11..17 (one shuffle by three lanes)
+  const uint32_t H3 = wdown(H, 3);
+  const uint32_t A1 = wshl240(H0);
+  const uint32_t A2 = l == 7 ? (H3 & 0xFFFF0000u) : ((l >= 8 && l < 15) ? H3 : 0u);
   // V = L + A1 + A2 + 2m - H - H1 on 19 lanes (V < 2^579), the subtrahends as their
   // complements: -Y = ~Y + 1 - 2^608 within 19 lanes, so every lane's sum is
   // non-negative and the 2 2^608 that remain fall past lane 18 and are dropped.
   uint64_t v = (uint64_t)L + A1 + A2 + two_m_limb(l) + (uint32_t)~H + (uint32_t)~H1 + (l == 0 ? 2u : 0u);
   if (l >= 19) v = 0;
   uint32_t V = wsettle(v);
-  const uint32_t t = __shfl_sync(kFull, V, 18);  // 0..7
+  const uint32_t t = __shfl_sync(kFull, V, 18);  // 0..7, almost always nonzero
   if (l >= 18) V = 0;
-  if (t) {  // + t (2^240 - 1) = (t - 1) 2^240 + (2^240 - t): non-negative limbs
+  {  // + t (2^240 - 1) = (t - 1) 2^240 + (2^240 - t) for t >= 1 (non-negative limbs); 0 for t = 0
     const uint32_t f = l == 0 ? 0u - t : (l < 7 ? 0xFFFFFFFFu : (l == 7 ? (((t - 1u) << 16) | 0xFFFFu) : 0u));
-    V = wadd(V, f);
+    V = wadd(V, t ? f : 0u);
   }
   if (__shfl_sync(kFull, V, 18)) {  // another 2^576 (rare): + 2^240 - 1
     if (l == 18) V = 0;
@@ -186,6 +190,7 @@ __device__ __forceinline__ uint32_t wto_ranlux(uint32_t X, uint32_t* scratch) {
   const unsigned l = lane_id();
   uint32_t S = wshl240(X);  // every lane shuffles; lanes 18.. then drop their part
   if (l >= 18) S = 0u;
+  const uint32_t Q336 = wshr336(X);  // needed below; shuffled early, beside wsub's votes
   uint32_t b;
   const uint32_t T = wsub(S, X, &b);
   const bool top3 = (l >= 15 && l < 18) ? T == 0xFFFFFFFFu : true;
@@ -206,7 +211,7 @@ __device__ __forceinline__ uint32_t wto_ranlux(uint32_t X, uint32_t* scratch) {
     return D;
   }
   // D = X + (X >> 336) - b = X + (X >> 336) + b (2^576 - 1) mod 2^576 (D < 2^576)
-  uint64_t v = (uint64_t)X + wshr336(X) + (b ? 0xFFFFFFFFu : 0u);
+  uint64_t v = (uint64_t)X + Q336 + (b ? 0xFFFFFFFFu : 0u);
   if (l >= 18) v = 0;
   const uint32_t D = wsettle(v);
   return l < 18 ? D : 0u;
