@@ -352,6 +352,10 @@ rlxpp_status rlxpp_seed_states_noalloc(const uint32_t* levels, uint32_t n_levels
  *  rlxpp_test_to_ranlux    x[9] (< m) -> d[9] = floor(2^576 x / m), carry[1] (Sec. 2.3)
  *  rlxpp_test_to_lcg       d[9], carry[1] -> x[9] = d - floor(d / 2^336) + carry
  *  rlxpp_test_f64_from48   v[1] (< 2^48) -> out[1] = bit pattern of v 2^-48
+ * The same two steps as the warp-cooperative refill computes them (one warp per item,
+ * one 32-bit limb per lane), same layouts:
+ *  rlxpp_test_warp_mod_m     in[18] -> out[9] = in mod m, in [0, m)      (Sec. 2.2)
+ *  rlxpp_test_warp_to_ranlux x[9] (< m) -> d[9], carry[1]                 (Sec. 2.3)
  * The integer-pipe elementary functions under the distribution draws (Sec. 2.4); each
  * output is a double's bit pattern, a quiet NaN for an input out of range:
  *  rlxpp_test_neg_ln48       w[1] in [1, 2^48] -> out[1] = -ln(w 2^-48)
@@ -369,6 +373,9 @@ rlxpp_status rlxpp_test_to_lcg(const uint64_t* d, const uint32_t* carry, uint64_
                                uint64_t n, void* cuda_stream);
 rlxpp_status rlxpp_test_f64_from48(const uint64_t* v, uint64_t* out, uint64_t n,
                                    void* cuda_stream);
+rlxpp_status rlxpp_test_warp_mod_m(const uint64_t* in, uint64_t* out, uint64_t n, void* cuda_stream);
+rlxpp_status rlxpp_test_warp_to_ranlux(const uint64_t* x, uint64_t* d, uint32_t* carry, uint64_t n,
+                                       void* cuda_stream);
 rlxpp_status rlxpp_test_neg_ln48(const uint64_t* w, uint64_t* out, uint64_t n, void* cuda_stream);
 rlxpp_status rlxpp_test_cos_sin_2pi48(const uint64_t* v, uint64_t* out, uint64_t n,
                                       void* cuda_stream);

@@ -85,6 +85,8 @@ def _load():
         "rlxpp_test_to_ranlux": [_vp, _vp, _vp, _u64, _vp],
         "rlxpp_test_to_lcg": [_vp, _vp, _vp, _u64, _vp],
         "rlxpp_test_f64_from48": [_vp, _vp, _u64, _vp],
+        "rlxpp_test_warp_mod_m": [_vp, _vp, _u64, _vp],
+        "rlxpp_test_warp_to_ranlux": [_vp, _vp, _vp, _u64, _vp],
         "rlxpp_test_neg_ln48": [_vp, _vp, _u64, _vp],
         "rlxpp_test_fail_alloc": [_i64],
         "rlxpp_test_cos_sin_2pi48": [_vp, _vp, _u64, _vp],
@@ -262,6 +264,14 @@ def rlxpp_test_to_lcg(d, carry, x, n, stream=None):
 
 def rlxpp_test_f64_from48(v, out, n, stream=None):
     _check(_lib.rlxpp_test_f64_from48(_ptr(v), _ptr(out), n, _stream(stream)))
+
+
+def rlxpp_test_warp_mod_m(inp, out, n, stream=None):
+    _check(_lib.rlxpp_test_warp_mod_m(_ptr(inp), _ptr(out), n, _stream(stream)))
+
+
+def rlxpp_test_warp_to_ranlux(x, d, carry, n, stream=None):
+    _check(_lib.rlxpp_test_warp_to_ranlux(_ptr(x), _ptr(d), _ptr(carry), n, _stream(stream)))
 
 
 def rlxpp_test_fail_alloc(after):

@@ -658,6 +658,21 @@ rlxpp_status rlxpp_test_to_lcg(const uint64_t* d, const uint32_t* carry, uint64_
 rlxpp_status rlxpp_test_f64_from48(const uint64_t* v, uint64_t* out, uint64_t n, void* cuda_stream) {
   return run_test(kTestF64, v, nullptr, out, nullptr, n, cuda_stream);
 }
+static rlxpp_status warp_test(int op, const uint64_t* in, uint64_t* out, uint32_t* carry, uint64_t n,
+                              void* cuda_stream) {
+  if (n == 0) return RLXPP_OK;
+  if (!in || !out || (op == 1 && !carry)) return fail(RLXPP_ERR_INVALID, "null test buffer");
+  cudaError_t e = launch_warp_test(op, in, out, carry, n, as_stream(cuda_stream));
+  if (e != cudaSuccess) return fail(cuda_status(e), std::string("warp test kernel: ") + cudaGetErrorString(e));
+  return RLXPP_OK;
+}
+rlxpp_status rlxpp_test_warp_mod_m(const uint64_t* in, uint64_t* out, uint64_t n, void* cuda_stream) {
+  return warp_test(0, in, out, nullptr, n, cuda_stream);
+}
+rlxpp_status rlxpp_test_warp_to_ranlux(const uint64_t* x, uint64_t* d, uint32_t* carry, uint64_t n,
+                                       void* cuda_stream) {
+  return warp_test(1, x, d, carry, n, cuda_stream);
+}
 rlxpp_status rlxpp_test_neg_ln48(const uint64_t* w, uint64_t* out, uint64_t n, void* cuda_stream) {
   return run_test(kTestNegLn48, w, nullptr, out, nullptr, n, cuda_stream);
 }

@@ -87,6 +87,11 @@ cudaError_t launch_tc_mulmod(const void* bimg, const uint64_t* x, uint64_t* out,
 // then reports cudaErrorMemoryAllocation without allocating).
 bool injected_alloc_failure();
 
+// Warp-arithmetic unit tests (rlxpp_warp.cu): op 0 mod_m of 18-uint64 inputs, op 1 the
+// conversion to RANLUX numbers of 9-uint64 states (with carry).
+cudaError_t launch_warp_test(int op, const uint64_t* in, uint64_t* out, uint32_t* carry, uint64_t n,
+                             cudaStream_t st);
+
 cudaError_t launch_test(int which, const uint64_t* x, const uint64_t* y, uint64_t* out,
                         uint32_t* carry, uint64_t n, cudaStream_t st);
 

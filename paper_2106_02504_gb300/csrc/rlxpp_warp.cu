@@ -353,6 +353,37 @@ __global__ void __launch_bounds__(kWarpBlock) k_draw_warp(const DrawArgs a) {
   }
 }
 
+// Unit tests of the warp arithmetic, one warp per item.  op 0: in = 18 uint64 (1152 bits)
+// -> out = in mod m (9 uint64); op 1: in = X < m (9 uint64) -> out = D (9 uint64) and
+// carry[i].
+__global__ void __launch_bounds__(kWarpBlock) k_test_warp(int op, const uint64_t* __restrict__ in,
+                                                          uint64_t* __restrict__ out, uint32_t* __restrict__ carry,
+                                                          uint64_t n) {
+  __shared__ uint32_t scratch_s[kWarpsPerBlock][36];
+  const unsigned l = lane_id();
+  const int warp = threadIdx.x / 32;
+  const uint64_t i = (uint64_t)blockIdx.x * kWarpsPerBlock + warp;
+  if (i >= n) return;  // the whole warp
+  auto limb = [](const uint64_t* p, unsigned k) {
+    return (k & 1) ? (uint32_t)(p[k / 2] >> 32) : (uint32_t)p[k / 2];
+  };
+  uint32_t r;
+  if (op == 0) {
+    const uint64_t* p = in + 18 * i;
+    const uint32_t L = l < 18 ? limb(p, l) : 0u;
+    const uint32_t H = l < 18 ? limb(p, 18 + l) : 0u;
+    r = wmod_m(L, H);
+  } else {
+    const uint64_t* p = in + 9 * i;
+    const uint32_t X = l < 18 ? limb(p, l) : 0u;
+    r = wto_ranlux(X, scratch_s[warp]);
+    const uint32_t c = wcarry(X, r);
+    if (l == 0) carry[i] = c;
+  }
+  const uint32_t hi = __shfl_down_sync(kFull, r, 1);
+  if (l < 18 && (l & 1) == 0) out[9 * i + l / 2] = ((uint64_t)hi << 32) | r;
+}
+
 template <int Kind>
 cudaError_t launch_warp_kind(const DrawArgs& a, cudaStream_t st) {
   const unsigned grid = (unsigned)((a.s.n + kWarpsPerBlock - 1) / kWarpsPerBlock);
@@ -364,6 +395,13 @@ cudaError_t launch_warp_kind(const DrawArgs& a, cudaStream_t st) {
 }
 
 }  // namespace
+
+cudaError_t launch_warp_test(int op, const uint64_t* in, uint64_t* out, uint32_t* carry, uint64_t n,
+                             cudaStream_t st) {
+  if (n == 0) return cudaSuccess;
+  k_test_warp<<<(unsigned)((n + kWarpsPerBlock - 1) / kWarpsPerBlock), kWarpBlock, 0, st>>>(op, in, out, carry, n);
+  return cudaGetLastError();
+}
 
 bool warp_draw_supported(int kind) {
   return kind == kDrawU24 || kind == kDrawF64 || kind == kDrawF32 || kind == kDrawSumHist;

@@ -73,12 +73,15 @@ def _mod_m_inputs():
     return [x for x in v if 0 <= x < 2 ** 1152]
 
 
-def test_mod_m(native):
+@pytest.mark.parametrize("form", ["thread", "warp"])
+def test_mod_m(native, form):
+    """mod_m on crafted inputs (values near m and 2m, reductions that land in [m, 2^576),
+    special high halves) and random ones, in the per-thread and the warp-cooperative form."""
     vals = _mod_m_inputs()
     n = len(vals)
     inp = to_dev([limbs64(v, 18) for v in vals])
     out = torch.zeros((n, 9), dtype=torch.int64, device="cuda")
-    native.rlxpp_test_mod_m(inp, out, n)
+    (native.rlxpp_test_mod_m if form == "thread" else native.rlxpp_test_warp_mod_m)(inp, out, n)
     got = from_dev(out)
     for k in range(n):
         assert from_limbs64(got[k]) == R.mod_m(vals[k]), hex(vals[k])
@@ -97,14 +100,19 @@ def test_mul_mod(native):
         assert from_limbs64(got[k]) == xs[k] * ys[k] % M, k
 
 
-def test_conversions(native):
+@pytest.mark.parametrize("form", ["thread", "warp"])
+def test_conversions(native, form):
+    """The conversion to RANLUX numbers (and back) on edge and random states, the
+    corners where the quotient's borrow cannot be decided from the top limbs included,
+    in the per-thread and the warp-cooperative form."""
     rng = random.Random(24)
     xs = [x for x in EDGE_X if 0 < x < M] + [rng.randrange(1, M) for _ in range(5000)]
     xs += conversion_edge_states(rng)
     n = len(xs)
     d = torch.zeros((n, 9), dtype=torch.int64, device="cuda")
     carry = torch.zeros(n, dtype=torch.int32, device="cuda")
-    native.rlxpp_test_to_ranlux(to_dev([limbs64(v, 9) for v in xs]), d, carry, n)
+    (native.rlxpp_test_to_ranlux if form == "thread" else native.rlxpp_test_warp_to_ranlux)(
+        to_dev([limbs64(v, 9) for v in xs]), d, carry, n)
     gd, gc = from_dev(d), carry.cpu().numpy()
     for k in range(n):
         D, c = R.to_ranlux(xs[k])
