@@ -22,21 +22,6 @@ def native():
     return P.native
 
 
-def test_cursor_arithmetic_matches_oracle_rule():
-    from paper_2106_02504_gb300.serve import advance_cursor
-    from oracle import ranluxpp as R
-    st = R.Stream(24, seed=3)
-    block, pos = 0, 0
-    rng = np.random.Generator(np.random.PCG64(9))
-    for _ in range(200):
-        kind, count = int(rng.integers(0, 2)), int(rng.integers(0, 40))
-        (st.draw_f64 if kind == 1 else st.draw_u24)(count)
-        block, pos = advance_cursor(block, pos, kind, count)
-        assert pos == st.pos
-        # the stream's LCG state sits `block` advances after the seeded state
-        assert pow(R.luxury_multiplier(24), block, R.M) * R.seed_lcg(3, 24) % R.M == st.X
-
-
 def test_serving_results_alone_and_in_mix(native):
     from paper_2106_02504_gb300.serve import Server
     n_res = 300
