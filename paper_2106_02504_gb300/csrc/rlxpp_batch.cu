@@ -233,9 +233,14 @@ rlxpp_status plan_impl(rlxpp_gen* g, const rlxpp_request* reqs, uint64_t n_reqs,
     auto it = g->tuned.find(shape_signature(n_reqs, total_refills));
     if (it != g->tuned.end()) {
       t = it->second;
-    } else {  // default: enough chunks to fill the GPU, at most 256 refills each
+    } else {
+      // default: enough chunks to fill the GPU, at most 256 refills each, and long enough
+      // that building the chunks here (about 18 ns each) costs no more than a chunk's
+      // serial refills on the device (about 1.2 us each): L >= sqrt(refills / 64)
       const uint64_t threads = (uint64_t)std::max(1, g->sms) * 4 * kReqBlock;
       uint64_t L = total_refills / std::max<uint64_t>(threads, 1);
+      const uint64_t L_host = (uint64_t)std::sqrt((double)total_refills / 64.0);
+      if (L_host > L) L = L_host;
       uint32_t p2 = 4;
       while (p2 < L && p2 < 256) p2 <<= 1;
       t = rlxpp_tuning{p2, 4, g->path == RLXPP_PATH_TENSOR ? RLXPP_PATH_TENSOR : RLXPP_PATH_IMAD};

@@ -539,7 +539,6 @@ __global__ void __launch_bounds__(kTcRows* T, T == 1 ? 4 : 1)
     pos += (uint32_t)(h * need);
   }
   bool mine = live && k < cnt;
-  bool refilled = false;
   uint32_t X[kLimbs];
   to_lcg(D, c, X);
   // Tile-wide stores when every live stream of the tile starts at the tile's first
@@ -561,22 +560,24 @@ __global__ void __launch_bounds__(kTcRows* T, T == 1 ? 4 : 1)
   }
   uint32_t phase = 0;
   bool ok = true;
+  bool stored = false;  // this stream's final state is written
+  // A stream's state lives in its operand row between refills: each new X is written
+  // there as soon as it is formed (the product that read the tile is complete), and the
+  // final (D, carry) is stored when the stream's last block is drawn, so neither X nor
+  // D stays live across the wait for the next product.
+  write_x_row(G.tile, G.t, X);
   while (true) {
-    write_x_row(G.tile, G.t, X);
     if (!tc_publish(G, mine)) break;  // every stream of the tile is done
     uint32_t col[72];
     if (!tc_refill_after_publish(G, bmat, taddr, phase, col, true, tma ? &store : nullptr)) {
       ok = false;
       break;
     }
-    uint32_t Xn[kLimbs];
-    columns_to_x(col, Xn);
     uint64_t dst = 0;  // destination of this lane's full block (streams out of step)
     if (mine) {
-#pragma unroll
-      for (int q = 0; q < kLimbs; ++q) X[q] = Xn[q];
+      columns_to_x(col, X);
+      write_x_row(G.tile, G.t, X);  // the next product's operand
       to_ranlux(X, D);
-      refilled = true;
       const int64_t rem = cnt - k;
       if (tma) {
         // the whole block into this thread's row of the staging box; past the count
@@ -625,19 +626,22 @@ __global__ void __launch_bounds__(kTcRows* T, T == 1 ? 4 : 1)
         pos = (uint32_t)(rem * need);
       }
       mine = k < cnt;
+      if (!mine) {
+        c = carry_of(X, D);
+        store_state_D(s, i, D);
+        stored = true;
+      }
     }
     if constexpr (Coop) warp_store_blocks(wstage, dst);
   }
   if (tma && G.t == 0 && store.pending) tile_store_issue(store);  // the last blocks
   if (Kind != kDrawSumHist) bulk_wait_all();  // this thread's output copies are done
+  // after a timed-out wait, streams that finished keep their new state (D with its
+  // position and carry), the others their old one
+  if (live && (ok || stored)) s.meta[i] = meta_pack(pos, c, lvl);
   if (!ok) {
     if (G.t == 0) atomicCAS(s.status, 0, (int)RLXPP_ERR_TIMEOUT);
   } else if (live) {
-    if (refilled) {
-      c = carry_of(X, D);
-      store_state_D(s, i, D);
-    }
-    s.meta[i] = meta_pack(pos, c, lvl);
     if constexpr (Kind == kDrawSumHist) {
       uint64_t* sums = static_cast<uint64_t*>(a.out);
       if (sums) sums[i] = a.accumulate_sums ? sums[i] + out.sum : out.sum;
