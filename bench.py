@@ -505,6 +505,18 @@ def bench_normal(nat, dev, n=1 << 20, exponential=False):
     return res
 
 
+def _host_cpu_times():
+    """Seconds of CPU time of the whole machine from /proc/stat: busy (user, nice,
+    system, irq, softirq) and steal; None where it is not available."""
+    try:
+        with open("/proc/stat") as f:
+            v = [int(x) for x in f.readline().split()[1:]]
+        hz = os.sysconf("SC_CLK_TCK")
+        return {"busy": (v[0] + v[1] + v[2] + v[5] + v[6]) / hz, "steal": (v[7] if len(v) > 7 else 0) / hz}
+    except (OSError, ValueError, IndexError):
+        return None
+
+
 def bench_serving(args):
     """10^5 resident streams, Poisson arrivals at 2 10^4 requests/s, counts log-uniform in
     [10^2, 10^7], u24/f64 50/50, outputs copied to pinned host memory."""
@@ -515,8 +527,16 @@ def bench_serving(args):
     arr, stream, counts, is_f64 = W.serving_trace(n_req, rate, n_res, seed=5)
     srv = Server(n_res, pool_bytes=args.serve_pool_gib << 30, n_cuda_streams=args.serve_streams,
                  max_batch=args.serve_max_batch)
+    host0, cpu0, t0 = _host_cpu_times(), time.process_time(), time.perf_counter()
     stats = srv.run_trace(arr, stream, counts, is_f64)
+    host1, cpu1, t1 = _host_cpu_times(), time.process_time(), time.perf_counter()
     srv.close()
+    # the loop is one host thread: CPU taken from this machine by others (steal) shows
+    # up as latency
+    if host0 and host1:
+        stats["host"] = {"steal_s": round(host1["steal"] - host0["steal"], 3),
+                         "busy_s": round(host1["busy"] - host0["busy"], 3), "cores": os.cpu_count(),
+                         "loop_cpu_share": round((cpu1 - cpu0) / (t1 - t0), 3)}
     stats.update({"resident_streams": n_res, "arrival_rate_hz": rate, "trace_seconds": args.serve_seconds,
                   "pool_bytes": args.serve_pool_gib << 30, "cuda_streams": args.serve_streams,
                   "max_batch": args.serve_max_batch})
