@@ -64,3 +64,26 @@ def test_async_host_draws(native, path):
     torch.cuda.synchronize()
     assert np.array_equal(nxt.cpu().numpy().view(np.uint64)[idx], ref.draw(10, S.KIND_F64).view(np.uint64))
     g.close()
+
+
+def test_async_host_draw_edge_cases(native):
+    """Zero counts and an empty generator return at once without touching the output;
+    waiting with nothing in flight is a no-op; the streams do not move."""
+    g = native.Generator(5, [2048], torch.arange(1, 6, dtype=torch.int64, device="cuda"))
+    ref = StreamSet.from_seeds(np.arange(1, 6, dtype=np.uint64), 2048)
+    g.host_wait()                                     # nothing issued yet
+    host = torch.full((5, 3), 7.0, dtype=torch.float64).pin_memory()
+    g.draw_f64_host_async(host, 0)
+    g.host_wait()
+    torch.cuda.synchronize()
+    assert bool((host == 7.0).all())
+    out = torch.empty((5, 4), dtype=torch.float64, device="cuda")
+    g.draw_f64(out, 4)
+    torch.cuda.synchronize()
+    assert np.array_equal(out.cpu().numpy().view(np.uint64), ref.draw(4, S.KIND_F64).view(np.uint64))
+    g.close()
+    e = native.Generator(0, [2048], None)
+    e.draw_u24_host_async(torch.empty((0, 8), dtype=torch.int32).pin_memory(), 8)
+    e.host_wait()
+    torch.cuda.synchronize()
+    e.close()
