@@ -519,24 +519,37 @@ def _host_cpu_times():
 
 def bench_serving(args):
     """10^5 resident streams, Poisson arrivals at 2 10^4 requests/s, counts log-uniform in
-    [10^2, 10^7], u24/f64 50/50, outputs copied to pinned host memory."""
+    [10^2, 10^7], u24/f64 50/50, outputs copied to pinned host memory; the library's
+    native serving loop replays the trace (rlxpp_server_run_trace)."""
+    import numpy as np
+
     from paper_2106_02504_gb300 import workloads as W
-    from paper_2106_02504_gb300.serve import Server
+    from paper_2106_02504_gb300.serve import NativeServer
     n_res, rate = 100_000, 20_000
     n_req = int(rate * args.serve_seconds)
     arr, stream, counts, is_f64 = W.serving_trace(n_req, rate, n_res, seed=5)
-    srv = Server(n_res, pool_bytes=args.serve_pool_gib << 30, n_cuda_streams=args.serve_streams,
-                 max_batch=args.serve_max_batch)
+    srv = NativeServer(n_res, pool_bytes=args.serve_pool_gib << 30, n_cuda_streams=args.serve_streams,
+                       max_batch=args.serve_max_batch)
     host0, cpu0, t0 = _host_cpu_times(), time.process_time(), time.perf_counter()
-    stats = srv.run_trace(arr, stream, counts, is_f64)
+    lat = srv.run_trace(arr, stream, counts, is_f64)
     host1, cpu1, t1 = _host_cpu_times(), time.process_time(), time.perf_counter()
+    loop = srv.stats()
     srv.close()
+    ok = lat >= 0
+    f64 = np.asarray(is_f64, dtype=bool)
+    secs = float((arr[ok] + lat[ok]).max() - arr[ok].min())
+    values, doubles = int(counts[ok].sum()), int(counts[ok & f64].sum())
+    stats = {"loop": "native (rlxpp_server_run_trace)", "requests": int(ok.sum()), "rejected": int((~ok).sum()),
+             "values": values, "doubles": doubles, "seconds": secs, "values_per_s": values / secs,
+             "doubles_per_s": doubles / secs, "p50_ms": float(np.percentile(lat[ok], 50) * 1e3),
+             "p99_ms": float(np.percentile(lat[ok], 99) * 1e3), "max_ms": float(lat[ok].max() * 1e3)}
     # the loop is one host thread: CPU taken from this machine by others (steal) shows
     # up as latency
     if host0 and host1:
         stats["host"] = {"steal_s": round(host1["steal"] - host0["steal"], 3),
                          "busy_s": round(host1["busy"] - host0["busy"], 3), "cores": os.cpu_count(),
                          "loop_cpu_share": round((cpu1 - cpu0) / (t1 - t0), 3)}
+    stats["launch"] = {"max_host_ms": loop["max_launch_us"] / 1e3, "slow_launches": loop["slow_launches"]}
     stats.update({"resident_streams": n_res, "arrival_rate_hz": rate, "trace_seconds": args.serve_seconds,
                   "pool_bytes": args.serve_pool_gib << 30, "cuda_streams": args.serve_streams,
                   "max_batch": args.serve_max_batch})

@@ -393,6 +393,63 @@ rlxpp_status rlxpp_test_tc_mulmod(uint32_t p, const uint64_t* x, uint64_t* out, 
  * uint64 of device memory (not written). */
 rlxpp_status rlxpp_test_tc_timeout(uint64_t* scratch, void* cuda_stream);
 
+/* ---- serving loop (host side, native) -------------------------------------------
+ * A continuous-batching request loop over the streams of one generator.  Each
+ * submitted request (count u24 or f64 values from one stream) is given the next
+ * segment of its stream at once (start block and read position by the draw rule), so
+ * requests run independently by jump-ahead; it is admitted when its output fits a
+ * device arena of pool_bytes (first fit in 256-byte granules), launched with what else
+ * is admitted (up to max_batch) as one rlxpp_draw_requests batch on one of
+ * n_cuda_streams streams while earlier batches run, copied (RLXPP_SERVER_COPY_TO_HOST)
+ * to a page-locked mirror of the arena, the batch's requests below small_bytes first,
+ * and completed when its copy has finished.  With max_queued_bytes > 0 a request that
+ * would push the bytes waiting for the arena past it, or one larger than the arena,
+ * is rejected (accepted = 0) and takes no numbers from its stream.  A request not yet
+ * launched can be cancelled; its segment of the stream is then skipped.  Times are
+ * seconds from the server's creation (or from the start of rlxpp_server_run_trace).
+ * The generator must outlive the server; a server is not thread-safe. */
+typedef struct rlxpp_server rlxpp_server;
+#define RLXPP_SERVER_COPY_TO_HOST 1u /* copy each result to the page-locked mirror       */
+#define RLXPP_SERVER_KEEP_RESULTS 2u /* keep a copy of each result for rlxpp_server_result */
+typedef struct rlxpp_served {        /* one completed request                          */
+  uint64_t rid, stream, skip;        /* id; stream; start block (advances from the state) */
+  uint32_t pos, kind;                /* read position in the start block; RLXPP_KIND_*  */
+  int64_t count;                     /* values                                          */
+  uint64_t offset, nbytes;           /* byte offset in the arena; bytes of output       */
+  double arrival, launch, done;      /* seconds                                         */
+} rlxpp_served;                      /* 80 bytes */
+typedef struct rlxpp_server_state {
+  uint64_t waiting, admitted, inflight_groups, arena_used, queued_bytes, done, rejected, cancelled;
+  uint64_t max_launch_us;  /* longest host time of one batch launch, microseconds      */
+  uint64_t slow_launches;  /* batch launches that took 1 ms or more on the host         */
+} rlxpp_server_state;
+rlxpp_status rlxpp_server_create(rlxpp_gen* gen, uint64_t pool_bytes, uint32_t n_cuda_streams,
+                                 uint32_t max_batch, uint64_t small_bytes, uint64_t max_queued_bytes,
+                                 uint32_t flags, rlxpp_server** out);
+void rlxpp_server_destroy(rlxpp_server* server);
+/* arrival < 0: now.  The id must not belong to a request that is pending or not yet
+ * taken by rlxpp_server_take_done. */
+rlxpp_status rlxpp_server_submit(rlxpp_server* server, uint64_t rid, uint64_t stream, uint32_t kind,
+                                 int64_t count, double arrival, int* accepted);
+rlxpp_status rlxpp_server_cancel(rlxpp_server* server, uint64_t rid, int* cancelled);
+/* One round: retire finished copies, admit, launch (wait_for_one: first wait on the
+ * host for the oldest batch's next copy group).  rlxpp_server_drain runs rounds until
+ * nothing is waiting, admitted or in flight. */
+rlxpp_status rlxpp_server_pump(rlxpp_server* server, int wait_for_one);
+rlxpp_status rlxpp_server_drain(rlxpp_server* server);
+rlxpp_status rlxpp_server_stats(const rlxpp_server* server, rlxpp_server_state* out);
+/* Up to max completed requests in completion order (each once) into out; *n = count. */
+rlxpp_status rlxpp_server_take_done(rlxpp_server* server, rlxpp_served* out, uint64_t max, uint64_t* n);
+/* The kept result of a completed request (RLXPP_SERVER_KEEP_RESULTS): nbytes must be its
+ * size; the copy is released. */
+rlxpp_status rlxpp_server_result(rlxpp_server* server, uint64_t rid, void* dst, uint64_t nbytes);
+/* Replays a trace on an idle server: request i (id i) of count[i] values (f64 if
+ * is_f64[i], else u24) from stream[i] is submitted once arrival[i] seconds have passed;
+ * latency[i] receives its completion minus its arrival in seconds, -1 if rejected. */
+rlxpp_status rlxpp_server_run_trace(rlxpp_server* server, uint64_t n, const double* arrival,
+                                    const uint64_t* stream, const int64_t* count, const uint8_t* is_f64,
+                                    double* latency);
+
 /* Failure-path test: the library's device allocation number `after` from now (0 = the
  * next one) reports out of memory without allocating, once; after < 0 switches this
  * off.  Process-wide (one countdown shared by all threads and handles).  Calls that hit

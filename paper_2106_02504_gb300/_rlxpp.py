@@ -44,6 +44,16 @@ def request_dtype():
     return np.dtype([("stream", "<u8"), ("skip", "<u8"), ("pos", "<u4"), ("kind", "<u4"),
                      ("count", "<i8"), ("offset", "<u8")])
 
+def served_dtype():
+    """numpy dtype laid out like struct rlxpp_served (80 bytes)."""
+    import numpy as np
+    return np.dtype([("rid", "<u8"), ("stream", "<u8"), ("skip", "<u8"), ("pos", "<u4"), ("kind", "<u4"),
+                     ("count", "<i8"), ("offset", "<u8"), ("nbytes", "<u8"), ("arrival", "<f8"),
+                     ("launch", "<f8"), ("done", "<f8")])
+
+
+RLXPP_SERVER_COPY_TO_HOST, RLXPP_SERVER_KEEP_RESULTS = 1, 2
+
 RLXPP_OK, RLXPP_ERR_INVALID, RLXPP_ERR_NOMEM, RLXPP_ERR_CUDA, RLXPP_ERR_TIMEOUT, \
     RLXPP_ERR_UNSUPPORTED = range(6)
 RLXPP_MAX_LEVELS = 16
@@ -100,6 +110,15 @@ def _load():
         "rlxpp_set_path": [_vp, _u32],
         "rlxpp_test_tc_mulmod": [_u32, _vp, _vp, _u64, _vp],
         "rlxpp_test_tc_timeout": [_vp, _vp],
+        "rlxpp_server_create": [_vp, _u64, _u32, _u32, _u64, _u64, _u32, ctypes.POINTER(_vp)],
+        "rlxpp_server_submit": [_vp, _u64, _u64, _u32, _i64, ctypes.c_double, ctypes.POINTER(ctypes.c_int)],
+        "rlxpp_server_cancel": [_vp, _u64, ctypes.POINTER(ctypes.c_int)],
+        "rlxpp_server_pump": [_vp, ctypes.c_int],
+        "rlxpp_server_drain": [_vp],
+        "rlxpp_server_stats": [_vp, _vp],
+        "rlxpp_server_take_done": [_vp, _vp, _u64, ctypes.POINTER(_u64)],
+        "rlxpp_server_result": [_vp, _u64, _vp, _u64],
+        "rlxpp_server_run_trace": [_vp, _u64, _vp, _vp, _vp, _vp, _vp],
     }
     for name, args in sigs.items():
         fn = getattr(L, name)
@@ -119,6 +138,8 @@ def _load():
     L.rlxpp_get_path.restype = _u32
     L.rlxpp_destroy_plan.argtypes = [_vp]
     L.rlxpp_destroy_plan.restype = None
+    L.rlxpp_server_destroy.argtypes = [_vp]
+    L.rlxpp_server_destroy.restype = None
     return L
 
 
@@ -272,6 +293,74 @@ def rlxpp_test_warp_mod_m(inp, out, n, stream=None):
 
 def rlxpp_test_warp_to_ranlux(x, d, carry, n, stream=None):
     _check(_lib.rlxpp_test_warp_to_ranlux(_ptr(x), _ptr(d), _ptr(carry), n, _stream(stream)))
+
+
+def rlxpp_server_create(gen, pool_bytes, n_cuda_streams=4, max_batch=512, small_bytes=1 << 20,
+                        max_queued_bytes=0, flags=RLXPP_SERVER_COPY_TO_HOST):
+    h = _vp()
+    _check(_lib.rlxpp_server_create(gen, pool_bytes, n_cuda_streams, max_batch, small_bytes, max_queued_bytes,
+                                    flags, ctypes.byref(h)))
+    return h.value
+
+
+def rlxpp_server_destroy(server):
+    _lib.rlxpp_server_destroy(server)
+
+
+def rlxpp_server_submit(server, rid, stream, kind, count, arrival=-1.0):
+    ok = ctypes.c_int()
+    _check(_lib.rlxpp_server_submit(server, rid, stream, kind, count, arrival, ctypes.byref(ok)))
+    return bool(ok.value)
+
+
+def rlxpp_server_cancel(server, rid):
+    ok = ctypes.c_int()
+    _check(_lib.rlxpp_server_cancel(server, rid, ctypes.byref(ok)))
+    return bool(ok.value)
+
+
+def rlxpp_server_pump(server, wait_for_one=False):
+    _check(_lib.rlxpp_server_pump(server, int(bool(wait_for_one))))
+
+
+def rlxpp_server_drain(server):
+    _check(_lib.rlxpp_server_drain(server))
+
+
+def rlxpp_server_stats(server):
+    """dict of the counters of struct rlxpp_server_state."""
+    v = (_u64 * 10)()
+    _check(_lib.rlxpp_server_stats(server, ctypes.addressof(v)))
+    keys = ("waiting", "admitted", "inflight_groups", "arena_used", "queued_bytes", "done", "rejected", "cancelled",
+            "max_launch_us", "slow_launches")
+    return dict(zip(keys, list(v)))
+
+
+def rlxpp_server_take_done(server, max_records=1 << 16):
+    import numpy as np
+    out = np.zeros(max_records, dtype=served_dtype())
+    n = _u64()
+    _check(_lib.rlxpp_server_take_done(server, out.ctypes.data, max_records, ctypes.byref(n)))
+    return out[:n.value]
+
+
+def rlxpp_server_result(server, rid, out):
+    """Copies the kept result of request rid into the numpy array out (its size in bytes)."""
+    _check(_lib.rlxpp_server_result(server, rid, out.ctypes.data if out.nbytes else None, out.nbytes))
+
+
+def rlxpp_server_run_trace(server, arrival, stream, count, is_f64):
+    """Latencies in seconds (float64 array; -1 for rejected requests)."""
+    import numpy as np
+    arrival = np.ascontiguousarray(arrival, dtype=np.float64)
+    stream = np.ascontiguousarray(stream, dtype=np.uint64)
+    count = np.ascontiguousarray(count, dtype=np.int64)
+    is_f64 = np.ascontiguousarray(is_f64, dtype=np.uint8)
+    n = len(arrival)
+    lat = np.zeros(n, dtype=np.float64)
+    _check(_lib.rlxpp_server_run_trace(server, n, arrival.ctypes.data, stream.ctypes.data, count.ctypes.data,
+                                       is_f64.ctypes.data, lat.ctypes.data))
+    return lat
 
 
 def rlxpp_test_fail_alloc(after):

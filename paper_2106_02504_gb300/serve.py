@@ -325,3 +325,58 @@ class Server:
                 "doubles_per_s": doubles / (last - first),
                 "p50_ms": float(np.percentile(lat, 50) * 1e3), "p99_ms": float(np.percentile(lat, 99) * 1e3),
                 "max_ms": float(lat.max() * 1e3)}
+
+
+class NativeServer:
+    """The same serving loop with the host side in the library (rlxpp_server_*): no
+    Python runs per request.  Results and records as for Server: take_done() returns the
+    completed requests (numpy records of struct rlxpp_served), result(rec) a kept result
+    (keep_results=True), run_trace() the latency of every request of a trace."""
+
+    def __init__(self, n_resident, luxury=2048, seeds=None, pool_bytes=1 << 30, n_cuda_streams=4,
+                 max_batch=512, keep_results=False, copy_to_host=True, small_bytes=1 << 20,
+                 max_queued_bytes=None):
+        import torch
+        if seeds is None:
+            seeds = np.arange(1, n_resident + 1, dtype=np.uint64)
+        self.gen = B.Generator(n_resident, [luxury], torch.from_numpy(np.asarray(seeds, np.uint64).view(np.int64)).cuda())
+        flags = (B.RLXPP_SERVER_COPY_TO_HOST if copy_to_host else 0) | (B.RLXPP_SERVER_KEEP_RESULTS if keep_results else 0)
+        self.handle = B.rlxpp_server_create(self.gen.handle, pool_bytes, n_cuda_streams, max_batch, small_bytes,
+                                            max_queued_bytes or 0, flags)
+
+    def submit(self, rid, stream, kind, count, arrival=-1.0):
+        """True if accepted (False: rejected by the admission bound)."""
+        return B.rlxpp_server_submit(self.handle, rid, stream, kind, count, arrival)
+
+    def cancel(self, rid):
+        return B.rlxpp_server_cancel(self.handle, rid)
+
+    def pump(self, wait=False):
+        B.rlxpp_server_pump(self.handle, wait)
+
+    def drain(self):
+        B.rlxpp_server_drain(self.handle)
+
+    def stats(self):
+        return B.rlxpp_server_stats(self.handle)
+
+    def take_done(self):
+        return B.rlxpp_server_take_done(self.handle)
+
+    def result(self, rec):
+        out = np.zeros(int(rec["count"]), dtype=np.uint64 if rec["kind"] == KIND_F64 else np.uint32)
+        B.rlxpp_server_result(self.handle, int(rec["rid"]), out)
+        return out
+
+    def run_trace(self, arrival_s, stream, count, is_f64):
+        return B.rlxpp_server_run_trace(self.handle, arrival_s, stream, count, is_f64)
+
+    def close(self):
+        self.torch_sync()
+        B.rlxpp_server_destroy(self.handle)
+        self.gen.close()
+
+    @staticmethod
+    def torch_sync():
+        import torch
+        torch.cuda.synchronize()

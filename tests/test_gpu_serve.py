@@ -128,3 +128,94 @@ def test_cancel_before_launch(native):
             else:
                 assert r.status == "done" and np.array_equal(r.result, want[r.rid]), r.rid
     srv.close()
+
+
+def _segments(stream, kind, count):
+    """(skip, pos) of each request by the cursor rule, in submission order."""
+    from paper_2106_02504_gb300.serve import advance_cursor
+    cur = {}
+    out = []
+    for s, k, c in zip(stream, kind, count):
+        b, p = cur.get(int(s), (0, 0))
+        out.append((b, p))
+        cur[int(s)] = advance_cursor(b, p, int(k), int(c))
+    return out
+
+
+def test_native_serving_trace_matches_oracle(native):
+    """The library's serving loop on a Poisson trace through a small arena (requests
+    wait for memory), three CUDA streams and small batches: every kept result equals the
+    oracle's values for its stream segment, and each stream read in request order is the
+    oracle's sequence."""
+    from paper_2106_02504_gb300.serve import NativeServer
+    n_res = 300
+    arr, stream, counts, is_f64 = W.serving_trace(400, rate_hz=4000, n_resident=n_res, lo=100, hi=20000, seed=7)
+    srv = NativeServer(n_res, pool_bytes=1 << 20, n_cuda_streams=3, max_batch=16, keep_results=True)
+    lat = srv.run_trace(arr, stream, counts, is_f64)
+    assert np.all(lat > 0) and srv.stats()["done"] == 400
+    kinds = is_f64.astype(int)
+    by_stream = {}
+    for i, (s, k, c) in enumerate(zip(stream, kinds, counts)):
+        rec = np.zeros(1, dtype=native.served_dtype())[0]
+        rec["rid"], rec["kind"], rec["count"] = i, k, c
+        by_stream.setdefault(int(s), []).append((k, int(c), srv.result(rec)))
+    for s, items in by_stream.items():
+        ref = StreamSet.from_seeds([s + 1], 2048)
+        for k, c, got in items:
+            want = ref.draw(c, S.KIND_F64 if k else S.KIND_U24)[0]
+            assert np.array_equal(got, want.view(np.uint64) if k else want), s
+    srv.close()
+
+
+def test_native_admission_and_cancel(native):
+    """Admission bound: rejected requests take no stream numbers; cancellation while
+    waiting or admitted skips the segment and frees the arena block; a launched request
+    cannot be cancelled; the served results equal the oracle."""
+    from paper_2106_02504_gb300.serve import NativeServer
+    srv = NativeServer(4, pool_bytes=1 << 16, n_cuda_streams=2, max_batch=4, keep_results=True,
+                       max_queued_bytes=40_000)
+    rng = np.random.Generator(np.random.PCG64(11))
+    subs = []
+    for rid in range(24):
+        s, k, c = int(rng.integers(0, 4)), int(rng.integers(0, 2)), int(rng.integers(1, 2500))
+        subs.append((rid, s, k, c, srv.submit(rid, s, k, c)))
+    assert not srv.submit(99, 0, 1, 10_000)                  # larger than the arena
+    accepted = [x for x in subs if x[4]]
+    assert accepted and len(accepted) < len(subs)
+    assert srv.stats()["rejected"] == len(subs) - len(accepted) + 1
+    srv.drain()
+    recs = {int(r["rid"]): r for r in srv.take_done()}
+    assert set(recs) == {x[0] for x in accepted}
+    for s in range(4):
+        ref = StreamSet.from_seeds([s + 1], 2048)
+        for rid, s2, k, c, _ in accepted:
+            if s2 != s:
+                continue
+            want = ref.draw(c, S.KIND_F64 if k else S.KIND_U24)[0]
+            assert np.array_equal(srv.result(recs[rid]), want.view(np.uint64) if k else want), rid
+    srv.close()
+
+    srv = NativeServer(2, pool_bytes=1 << 15, n_cuda_streams=1, max_batch=1, keep_results=True)
+    reqs = [(rid, rid % 2, rid % 2, 600 + 50 * rid) for rid in range(8)]
+    for rid, s, k, c in reqs:
+        assert srv.submit(rid, s, k, c)
+    assert srv.cancel(1)                                      # waiting
+    srv.pump()                                                # admits what fits, launches request 0
+    st = srv.stats()
+    assert st["admitted"] >= 1 and st["inflight_groups"] >= 1
+    assert not srv.cancel(0)                                  # launched
+    used = st["arena_used"]
+    assert srv.cancel(2) and srv.stats()["arena_used"] < used  # admitted: its block is freed
+    assert not srv.cancel(2) and not srv.cancel(12345)
+    srv.drain()
+    recs = {int(r["rid"]): r for r in srv.take_done()}
+    assert set(recs) == {0, 3, 4, 5, 6, 7} and srv.stats()["cancelled"] == 2
+    for s in range(2):
+        ref = StreamSet.from_seeds([s + 1], 2048)
+        for rid, s2, k, c in reqs:
+            if s2 != s:
+                continue
+            want = ref.draw(c, S.KIND_F64 if k else S.KIND_U24)[0]   # cancelled segments skipped
+            if rid in recs:
+                assert np.array_equal(srv.result(recs[rid]), want.view(np.uint64) if k else want), rid
+    srv.close()
