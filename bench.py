@@ -576,6 +576,20 @@ def run_e2e(args, nat, g, seeds_h, n, world, dev, dist):
         nat.rlxpp_host_wait(g.handle, sp)
         torch.cuda.current_stream().synchronize()
 
+    # the device-to-host link in this run: 1 GiB from device memory into the pinned
+    # output, median of three copies (the e2e leg moves 8.6 GB per step through it)
+    probe = torch.empty(1 << 27, dtype=torch.float64, device=dev)
+    probe.fill_(1.0)
+    link = []
+    for _ in range(3):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        out_pin.view(-1)[: 1 << 27].copy_(probe, non_blocking=True)
+        e1.record()
+        torch.cuda.synchronize()
+        link.append((8 << 27) / (e0.elapsed_time(e1) * 1e-3) / 1e9)
+    del probe
+    link_gbs = sorted(link)[1]
     steps = max(1, min(args.steps, 3))
     step()
     if dist is not None:
@@ -591,8 +605,10 @@ def run_e2e(args, nat, g, seeds_h, n, world, dev, dist):
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         dt = float(t.item())
     doubles = n * (HBM_COUNT + FUSED_COUNT) * world * steps
+    d2h = n * HBM_COUNT * 8 + n * 8 + 256 * 8
     return {"value": doubles / dt, "unit": UNIT, "h2d_bytes_per_step": n * 8,
-            "d2h_bytes_per_step": n * HBM_COUNT * 8 + n * 8 + 256 * 8, "steps": steps,
+            "d2h_bytes_per_step": d2h, "steps": steps, "d2h_link_gbs": round(link_gbs, 1),
+            "link_frac": round(d2h * steps / dt / 1e9 / link_gbs, 3),
             "how": "rlxpp_seed from pinned host seeds, rlxpp_draw_f64_host_async into pinned host memory "
                    "(library-staged, copied on the library's copy stream while the fused sum/hist draw runs), "
                    "sums+hist read back, rlxpp_host_wait; wall clock"}
