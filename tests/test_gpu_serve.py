@@ -155,10 +155,21 @@ def test_native_serving_trace_matches_oracle(native):
     assert np.all(lat > 0) and srv.stats()["done"] == 400
     kinds = is_f64.astype(int)
     by_stream = {}
-    for i, (s, k, c) in enumerate(zip(stream, kinds, counts)):
+    seeds = np.arange(1, n_res + 1, dtype=np.uint64)
+    g = native.Generator(n_res, [2048], torch.from_numpy(seeds.view(np.int64)).cuda())
+    for i, ((s, k, c), (skip, pos)) in enumerate(zip(zip(stream, kinds, counts), _segments(stream, kinds, counts))):
         rec = np.zeros(1, dtype=native.served_dtype())[0]
         rec["rid"], rec["kind"], rec["count"] = i, k, c
-        by_stream.setdefault(int(s), []).append((k, int(c), srv.result(rec)))
+        got = srv.result(rec)
+        # the same request alone
+        req = np.zeros(1, dtype=native.request_dtype())
+        req[0] = (s, skip, pos, k, c, 0)
+        out = torch.zeros(max(int(c), 1), dtype=torch.float64 if k else torch.int32, device="cuda")
+        native.rlxpp_draw_requests(g.handle, req, None if k else out, out if k else None)
+        alone = out.cpu().numpy().view(np.uint64 if k else np.uint32)[:c]
+        assert np.array_equal(alone, got), i
+        by_stream.setdefault(int(s), []).append((k, int(c), got))
+    g.close()
     for s, items in by_stream.items():
         ref = StreamSet.from_seeds([s + 1], 2048)
         for k, c, got in items:
