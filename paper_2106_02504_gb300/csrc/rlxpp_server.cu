@@ -320,7 +320,7 @@ rlxpp_status rlxpp_server_create(rlxpp_gen* gen, uint64_t pool_bytes, uint32_t n
   auto* s = new rlxpp_server();
   s->gen = gen;
   s->n_streams = n;
-  s->arena.reset(new Arena(pool_bytes));
+  s->arena.reset(new Arena(pool_bytes / kGranule * kGranule));  // whole granules
   s->max_batch = max_batch;
   s->small_bytes = small_bytes;
   s->max_queued = max_queued_bytes;
@@ -355,7 +355,8 @@ rlxpp_status rlxpp_server_submit(rlxpp_server* s, uint64_t rid, uint64_t stream,
     return set_last_error(RLXPP_ERR_INVALID, "bad request");
   if (s->live.count(rid)) return set_last_error(RLXPP_ERR_INVALID, "request id in use");
   const uint64_t nbytes = (uint64_t)count * (kind == RLXPP_KIND_F64 ? 8 : 4);
-  if (nbytes > s->arena->size() || (s->max_queued && s->queued + nbytes > s->max_queued)) {
+  const uint64_t held = (std::max<uint64_t>(nbytes, 1) + kGranule - 1) / kGranule * kGranule;
+  if (held > s->arena->size() || (s->max_queued && s->queued + nbytes > s->max_queued)) {
     ++s->n_rejected;  // takes no numbers from the stream
     return RLXPP_OK;
   }

@@ -118,7 +118,7 @@ class Server:
         self.cur_pos = [0] * n_resident
         self.dev = torch.empty(pool_bytes, dtype=torch.uint8, device="cuda")
         self.host = torch.empty(pool_bytes, dtype=torch.uint8).pin_memory() if copy_to_host else None
-        self.arena = Arena(pool_bytes)
+        self.arena = Arena(pool_bytes // _ALIGN * _ALIGN)  # whole granules
         self.streams = [torch.cuda.Stream() for _ in range(n_cuda_streams)]
         self.free_streams = collections.deque(range(n_cuda_streams))
         self.waiting = collections.deque()     # arrived, not admitted (FIFO)
@@ -144,7 +144,8 @@ class Server:
         larger than the arena or would push the waiting bytes past max_queued_bytes."""
         r = Request(rid, int(stream), int(kind), int(count), self.now() if arrival is None else arrival)
         r.nbytes = r.count * (8 if r.kind == KIND_F64 else 4)
-        if r.nbytes > self.arena.size or (self.max_queued_bytes is not None and
+        held = -(-max(r.nbytes, 1) // _ALIGN) * _ALIGN     # what the arena would reserve
+        if held > self.arena.size or (self.max_queued_bytes is not None and
                                           self.queued_bytes + r.nbytes > self.max_queued_bytes):
             r.status = "rejected"
             self.rejected.append(r)

@@ -62,3 +62,13 @@ def test_arena_first_fit_and_coalescing():
     for off, n in list(live.items()):
         a.release(off, n)
     assert a.free == [(0, size)] and a.used == 0
+
+
+def test_arena_rounds_pool_and_requests_to_granules():
+    """A pool that is not a whole number of 256-byte granules is used down to the last
+    whole one, so a request that fits the pool only before rounding is refused instead
+    of waiting forever."""
+    a = Arena(1000 // 256 * 256)
+    assert a.alloc(768) == (0, 768) and a.alloc(1) is None
+    a.release(0, 768)
+    assert a.alloc(769) is None and a.free == [(0, 768)]
