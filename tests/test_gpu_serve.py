@@ -206,6 +206,14 @@ def test_native_admission_and_cancel(native):
             assert np.array_equal(srv.result(recs[rid]), want.view(np.uint64) if k else want), rid
     srv.close()
 
+    # a pool of 1000 bytes holds three 256-byte granules: 960 bytes (1024 once rounded)
+    # are refused at once rather than waiting forever
+    srv = NativeServer(2, pool_bytes=1000, n_cuda_streams=1, max_batch=1)
+    assert not srv.submit(0, 0, 0, 240) and srv.submit(1, 0, 0, 192)
+    srv.drain()
+    assert [int(r["rid"]) for r in srv.take_done()] == [1]
+    srv.close()
+
     srv = NativeServer(2, pool_bytes=1 << 15, n_cuda_streams=1, max_batch=1, keep_results=True)
     reqs = [(rid, rid % 2, rid % 2, 600 + 50 * rid) for rid in range(8)]
     for rid, s, k, c in reqs:
