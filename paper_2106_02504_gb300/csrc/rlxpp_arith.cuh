@@ -181,22 +181,27 @@ __device__ __forceinline__ void mod_m(const uint32_t p[2 * kLimbs], uint32_t r[k
 #pragma unroll
   for (int k = 0; k < 7; ++k) H1[k] = shr_pair(H[10 + k], H[11 + k], 16);
   H1[7] = H[17] >> 16;
-  // S = H0 + H1, H0 = H mod 2^336 (limbs 0..9 and the low 16 bits of limb 10)
-  uint32_t S[11];
-  S[0] = add_cc(H[0], H1[0]);
-#pragma unroll
-  for (int k = 1; k < 8; ++k) S[k] = addc_cc(H[k], H1[k]);
-  S[8] = addc_cc(H[8], 0u);
-  S[9] = addc_cc(H[9], 0u);
-  S[10] = addc(H[10] & 0xFFFFu, 0u);
-  // V = H + H1 (19 limbs, top limb 0 or 1)
+  // V = H + H1 (19 limbs, top limb 0 or 1) and S = H0 + H1, H0 = H mod 2^336 (limbs
+  // 0..9 and the low 16 bits of limb 10), agree in limbs 0..9, whose sum is formed
+  // once.  H1 < 2^240, so a carry out of limb 7 needs limbs 0..7 of H within H1 of 2^256
+  // (about 2^-16 of the products): only then do the chains go on.
   uint32_t V[kLimbs + 1];
   V[0] = add_cc(H[0], H1[0]);
 #pragma unroll
   for (int k = 1; k < 8; ++k) V[k] = addc_cc(H[k], H1[k]);
+  const uint32_t c8 = addc(0u, 0u);
 #pragma unroll
-  for (int k = 8; k < kLimbs; ++k) V[k] = addc_cc(H[k], 0u);
-  V[kLimbs] = addc(0u, 0u);
+  for (int k = 8; k < kLimbs; ++k) V[k] = H[k];
+  V[kLimbs] = 0u;
+  uint32_t S10 = H[10] & 0xFFFFu;  // limb 10 of S
+  if (__builtin_expect(c8 != 0u, 0)) {
+    V[8] = add_cc(H[8], 1u);
+#pragma unroll
+    for (int k = 9; k < kLimbs; ++k) V[k] = addc_cc(H[k], 0u);
+    V[kLimbs] = addc(0u, 0u);
+    // the carry leaves limb 9 exactly when limbs 8 and 9 were all ones (both now zero)
+    S10 += (V[8] | V[9]) == 0u ? 1u : 0u;
+  }
   // W = 2m - V; 2m = 2^577 - 2^241 + 2: limb 0 = 2, limb 7 = 0xFFFE0000,
   // limbs 8..17 = 0xFFFFFFFF, limb 18 = 1, other limbs 0.
   uint32_t W[kLimbs + 1];
@@ -209,10 +214,11 @@ __device__ __forceinline__ void mod_m(const uint32_t p[2 * kLimbs], uint32_t r[k
   W[kLimbs] = subc(1u, V[kLimbs]);
   // U = L + (S << 240); 240 = 7 limbs + 16 bits, S << 240 covers limbs 7..18
   uint32_t Sh[12];
-  Sh[0] = S[0] << 16;
+  Sh[0] = V[0] << 16;
 #pragma unroll
-  for (int k = 1; k < 11; ++k) Sh[k] = __funnelshift_l(S[k - 1], S[k], 16);
-  Sh[11] = S[10] >> 16;
+  for (int k = 1; k < 10; ++k) Sh[k] = __funnelshift_l(V[k - 1], V[k], 16);
+  Sh[10] = __funnelshift_l(V[9], S10, 16);
+  Sh[11] = S10 >> 16;
   uint32_t R[kLimbs + 1];
   // R = L + W first (limbs 0..6 of the shifted S are zero), then add the shifted S.
   R[0] = add_cc(L[0], W[0]);
@@ -228,36 +234,43 @@ __device__ __forceinline__ void mod_m(const uint32_t p[2 * kLimbs], uint32_t r[k
   // for t >= 1; all zero for t = 0.
   const uint32_t t = R[kLimbs];
   const uint32_t nz = t ? 0xFFFFFFFFu : 0u;
-  uint32_t c;
   r[0] = add_cc(R[0], (0u - t));
 #pragma unroll
   for (int k = 1; k < 7; ++k) r[k] = addc_cc(R[k], nz);
   r[7] = addc_cc(R[7], ((t - 1u) << 16 | 0xFFFFu) & nz);
+  const uint32_t f8 = addc(0u, 0u);
 #pragma unroll
-  for (int k = 8; k < kLimbs; ++k) r[k] = addc_cc(R[k], 0u);
-  c = addc(0u, 0u);
-  // fold 2: c (2^240 - 1), c in {0, 1}; when c = 1 the value is below 2^243.  c = 1 needs
-  // the low part of R within t (2^240 - 1) of 2^576, so this branch is almost never taken.
-  if (c) {
-    r[0] = add_cc(r[0], 0xFFFFFFFFu);
+  for (int k = 8; k < kLimbs; ++k) r[k] = R[k];
+  // t (2^240 - 1) < 2^243, so a carry out of limb 7 is rare (at most about 2^-13), and
+  // only then does the chain go on.  fold 2: a carry c out of limb 17 adds c (2^240 - 1);
+  // when c = 1 the value is below 2^243, so that addition stops at limb 7.
+  if (__builtin_expect(f8 != 0u, 0)) {
+    r[8] = add_cc(R[8], 1u);
 #pragma unroll
-    for (int k = 1; k < 7; ++k) r[k] = addc_cc(r[k], 0xFFFFFFFFu);
-    r[7] = addc(r[7], 0xFFFFu);
+    for (int k = 9; k < kLimbs; ++k) r[k] = addc_cc(R[k], 0u);
+    if (addc(0u, 0u)) {
+      r[0] = add_cc(r[0], 0xFFFFFFFFu);
+#pragma unroll
+      for (int k = 1; k < 7; ++k) r[k] = addc_cc(r[k], 0xFFFFFFFFu);
+      r[7] = addc(r[7], 0xFFFFu);
+    }
   }
   // final correction: r >= m  <=>  r + (2^240 - 1) >= 2^576; then r - m = that sum mod
-  // 2^576.  r >= m needs bits 240..575 of r all set, which is checked first.
-  uint32_t top = r[8] & r[9] & r[10] & r[11] & r[12] & r[13] & r[14] & r[15] & r[16] & r[17];
-  if (top == 0xFFFFFFFFu && r[7] >= 0xFFFF0000u) {
-    uint32_t e[kLimbs];
-    e[0] = add_cc(r[0], 0xFFFFFFFFu);
+  // 2^576.  r >= m needs bits 240..575 of r all set: the top limb is tested first.
+  if (__builtin_expect(r[17] == 0xFFFFFFFFu, 0)) {
+    const uint32_t top = r[8] & r[9] & r[10] & r[11] & r[12] & r[13] & r[14] & r[15] & r[16];
+    if (top == 0xFFFFFFFFu && r[7] >= 0xFFFF0000u) {
+      uint32_t e[kLimbs];
+      e[0] = add_cc(r[0], 0xFFFFFFFFu);
 #pragma unroll
-    for (int k = 1; k < 7; ++k) e[k] = addc_cc(r[k], 0xFFFFFFFFu);
-    e[7] = addc_cc(r[7], 0xFFFFu);
+      for (int k = 1; k < 7; ++k) e[k] = addc_cc(r[k], 0xFFFFFFFFu);
+      e[7] = addc_cc(r[7], 0xFFFFu);
 #pragma unroll
-    for (int k = 8; k < kLimbs; ++k) e[k] = addc_cc(r[k], 0u);
-    const uint32_t ge = addc(0u, 0u);
+      for (int k = 8; k < kLimbs; ++k) e[k] = addc_cc(r[k], 0u);
+      const uint32_t ge = addc(0u, 0u);
 #pragma unroll
-    for (int k = 0; k < kLimbs; ++k) r[k] = ge ? e[k] : r[k];
+      for (int k = 0; k < kLimbs; ++k) r[k] = ge ? e[k] : r[k];
+    }
   }
 }
 
@@ -344,9 +357,17 @@ __device__ __forceinline__ void to_ranlux(const uint32_t X[kLimbs], uint32_t D[k
   D[0] = add_cc(X[0], q[0]);
 #pragma unroll
   for (int k = 1; k < 8; ++k) D[k] = addc_cc(X[k], q[k]);
+  const uint32_t c8 = addc(0u, 0u);
 #pragma unroll
-  for (int k = 8; k < kLimbs - 1; ++k) D[k] = addc_cc(X[k], 0u);
-  D[kLimbs - 1] = addc(X[kLimbs - 1], 0u);
+  for (int k = 8; k < kLimbs; ++k) D[k] = X[k];
+  // q < 2^240, so a carry out of limb 7 needs limbs 0..7 of X within q of 2^256
+  // (about 2^-16 of the states): only then does the chain go on
+  if (__builtin_expect(c8 != 0u, 0)) {
+    D[8] = add_cc(X[8], 1u);
+#pragma unroll
+    for (int k = 9; k < kLimbs - 1; ++k) D[k] = addc_cc(X[k], 0u);
+    D[kLimbs - 1] = addc(X[kLimbs - 1], 0u);
+  }
 }
 
 // (D, c) -> X = D - floor(D / 2^336) + c, 336 = 24 (r - s) bits (inverse of to_ranlux).

@@ -178,28 +178,37 @@ __device__ __forceinline__ void columns_to_x(const uint32_t col[72], uint32_t X[
 #pragma unroll
   for (int k = 1; k < 7; ++k) X[k] = addc_cc(X[k], 0xFFFFFFFFu);
   X[7] = addc_cc(X[7], (T - 1u) << 16 | 0xFFFFu);
+  X[8] = addc_cc(X[8], 0u);
+  // a carry out of limb 8 needs that limb all ones before (rare): only then run the
+  // rest of the chain, and past limb 17 it is another 2^576 while the low part is
+  // below 2^256, so 2^240 - 1 is added again
+  if (__builtin_expect(addc(0u, 0u) != 0u, 0)) {
+    X[9] = add_cc(X[9], 1u);
 #pragma unroll
-  for (int k = 8; k < kLimbs; ++k) X[k] = addc_cc(X[k], 0u);
-  const uint32_t c = addc(0u, 0u);
-  if (c) {  // another 2^576: the low part is below 2^256, add 2^240 - 1 again (rare)
-    X[0] = add_cc(X[0], 0xFFFFFFFFu);
+    for (int k = 10; k < kLimbs; ++k) X[k] = addc_cc(X[k], 0u);
+    if (addc(0u, 0u)) {
+      X[0] = add_cc(X[0], 0xFFFFFFFFu);
 #pragma unroll
-    for (int k = 1; k < 7; ++k) X[k] = addc_cc(X[k], 0xFFFFFFFFu);
-    X[7] = addc(X[7], 0xFFFFu);
+      for (int k = 1; k < 7; ++k) X[k] = addc_cc(X[k], 0xFFFFFFFFu);
+      X[7] = addc(X[7], 0xFFFFu);
+    }
   }
-  // X >= m needs bits 240..575 all set (rare): then X - m = X + 2^240 - 1 mod 2^576
-  const uint32_t top = X[8] & X[9] & X[10] & X[11] & X[12] & X[13] & X[14] & X[15] & X[16] & X[17];
-  if (top == 0xFFFFFFFFu && X[7] >= 0xFFFF0000u) {
-    uint32_t e[kLimbs];
-    e[0] = add_cc(X[0], 0xFFFFFFFFu);
+  // X >= m needs bits 240..575 all set (rare, so the top limb is tested first): then
+  // X - m = X + 2^240 - 1 mod 2^576
+  if (__builtin_expect(X[17] == 0xFFFFFFFFu, 0)) {
+    const uint32_t top = X[8] & X[9] & X[10] & X[11] & X[12] & X[13] & X[14] & X[15] & X[16];
+    if (top == 0xFFFFFFFFu && X[7] >= 0xFFFF0000u) {
+      uint32_t e[kLimbs];
+      e[0] = add_cc(X[0], 0xFFFFFFFFu);
 #pragma unroll
-    for (int k = 1; k < 7; ++k) e[k] = addc_cc(X[k], 0xFFFFFFFFu);
-    e[7] = addc_cc(X[7], 0xFFFFu);
+      for (int k = 1; k < 7; ++k) e[k] = addc_cc(X[k], 0xFFFFFFFFu);
+      e[7] = addc_cc(X[7], 0xFFFFu);
 #pragma unroll
-    for (int k = 8; k < kLimbs; ++k) e[k] = addc_cc(X[k], 0u);
-    const uint32_t ge = addc(0u, 0u);
+      for (int k = 8; k < kLimbs; ++k) e[k] = addc_cc(X[k], 0u);
+      const uint32_t ge = addc(0u, 0u);
 #pragma unroll
-    for (int k = 0; k < kLimbs; ++k) X[k] = ge ? e[k] : X[k];
+      for (int k = 0; k < kLimbs; ++k) X[k] = ge ? e[k] : X[k];
+    }
   }
 }
 

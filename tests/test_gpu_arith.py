@@ -10,6 +10,7 @@ import pytest
 
 from oracle import ranluxpp as R
 from tests.oracle_side import MASK64, conversion_edge_states, from_limbs64, limbs64
+from tests.rare_paths import conversion_carry_states, mod_m_carry_inputs
 
 pytestmark = pytest.mark.gpu
 
@@ -70,6 +71,8 @@ def _mod_m_inputs():
             v.append((H << 576) + L if L < 2 ** 576 else (H << 576) + (L % 2 ** 576))
     v += [rng.randrange(2 ** 1152) for _ in range(4000)]
     v += [rng.randrange(M) * rng.randrange(M) for _ in range(4000)]
+    # carries past limbs 7, 8 and 17 in the reduction's chains (rare for random inputs)
+    v += mod_m_carry_inputs(random.Random(26))
     return [x for x in v if 0 <= x < 2 ** 1152]
 
 
@@ -108,6 +111,7 @@ def test_conversions(native, form):
     rng = random.Random(24)
     xs = [x for x in EDGE_X if 0 < x < M] + [rng.randrange(1, M) for _ in range(5000)]
     xs += conversion_edge_states(rng)
+    xs += conversion_carry_states(random.Random(27))  # X + q carries past limbs 7 and 8
     n = len(xs)
     d = torch.zeros((n, 9), dtype=torch.int64, device="cuda")
     carry = torch.zeros(n, dtype=torch.int32, device="cuda")

@@ -13,6 +13,7 @@ from oracle import ranluxpp as R
 from oracle import swb_lib as S
 from paper_2106_02504_gb300 import workloads as W
 from tests.oracle_side import StreamSet, from_limbs64, limbs64
+from tests.rare_paths import tc_above_m_inputs, tc_limb8_carry_inputs
 
 pytestmark = pytest.mark.gpu
 
@@ -35,13 +36,20 @@ def to_dev(rows):
 def test_tc_product(native, p):
     rng = random.Random(300 + p)
     M = R.M
+    A = R.luxury_multiplier(p)
     xs = [0, 1, 2, M - 1, M - 2, 2 ** 576 - 1, 2 ** 575, 2 ** 240 - 1, (2 ** 576 - 1) // 255 * 254] + \
         [rng.randrange(M) for _ in range(1000)]
+    # products below 2^240 - 1 (folded to r + m: the final correction), and operands
+    # whose fold carries out of limb 8 (found for the levels with dense R_j)
+    xs += tc_above_m_inputs(A)
+    if p in (389, 2048):
+        hits = tc_limb8_carry_inputs(A, random.Random(100 + p))
+        assert hits
+        xs += hits
     n = len(xs)
     out = torch.zeros((n, 9), dtype=torch.int64, device="cuda")
     native.rlxpp_test_tc_mulmod(p, to_dev([limbs64(x, 9) for x in xs]), out, n)
     got = out.cpu().numpy().view(np.uint64)
-    A = R.luxury_multiplier(p)
     for k in range(n):
         assert from_limbs64(got[k]) == A * xs[k] % M, (p, k)
 
