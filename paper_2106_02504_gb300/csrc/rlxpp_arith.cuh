@@ -345,18 +345,18 @@ __device__ __forceinline__ void to_ranlux(const uint32_t X[kLimbs], uint32_t D[k
   const uint32_t t16 = subc_cc(__funnelshift_l(X[8], X[9], 16), X[16]);
   const uint32_t t17 = subc_cc(__funnelshift_l(X[9], X[10], 16), X[17]);
   const uint32_t borrow = subc(0u, 0u) & 1u;
-  if (__builtin_expect((t15 & t16 & t17) == 0xFFFFFFFFu || (t15 | t16 | t17) == 0u, 0)) {
+  // q = (X >> 336) - borrow takes the borrow from its lowest limb alone unless that limb
+  // is zero (about 2^-32 of the states, also sent to to_ranlux_full), so D = X + q is a
+  // single chain over the shifted limbs of X
+  const uint32_t q0 = __funnelshift_l(X[10], X[11], 16);
+  if (__builtin_expect((t15 & t16 & t17) == 0xFFFFFFFFu || (t15 | t16 | t17) == 0u || q0 < borrow, 0)) {
     to_ranlux_full(X, D);
     return;
   }
-  uint32_t q[8];  // (X >> 336) - borrow, at least 0 (borrow = 1 needs X >= 2^336 here)
-  q[0] = sub_cc(__funnelshift_l(X[10], X[11], 16), borrow);
+  D[0] = add_cc(X[0], q0 - borrow);
 #pragma unroll
-  for (int k = 1; k < 7; ++k) q[k] = subc_cc(__funnelshift_l(X[10 + k], X[11 + k], 16), 0u);
-  q[7] = subc(X[17] >> 16, 0u);
-  D[0] = add_cc(X[0], q[0]);
-#pragma unroll
-  for (int k = 1; k < 8; ++k) D[k] = addc_cc(X[k], q[k]);
+  for (int k = 1; k < 7; ++k) D[k] = addc_cc(X[k], __funnelshift_l(X[10 + k], X[11 + k], 16));
+  D[7] = addc_cc(X[7], X[17] >> 16);
   const uint32_t c8 = addc(0u, 0u);
 #pragma unroll
   for (int k = 8; k < kLimbs; ++k) D[k] = X[k];

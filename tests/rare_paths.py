@@ -64,7 +64,8 @@ def mod_m_fold_carries(p):
 # ---- conversion X -> D = X + q, q = floor(X (2^240 - 1) / m) -----------------------
 def conversion_carry_states(rng: random.Random, k: int = 24):
     """States 0 < X < m whose limbs 0..7 (and 8, 9) are all ones, so that X + q carries
-    out of limb 7 (and further) whenever q >= 1."""
+    out of limb 7 (and further) whenever q >= 1, and states whose q takes its borrow
+    past its lowest limb."""
     out = []
     for _ in range(k):
         for low_bits in (256, 288, 320):
@@ -72,7 +73,17 @@ def conversion_carry_states(rng: random.Random, k: int = 24):
             X = (top << low_bits) | ((1 << low_bits) - 1)
             assert 0 < X < M
             out.append(X)
+        # the lowest limb of X >> 336 zero while [(X << 240) mod 2^576 < X] = 1: the
+        # borrow of q = (X >> 336) - [...] runs past that limb
+        top = rng.randrange(1 << 180, M >> 368)
+        out.append(top << 368 | rng.randrange(1 << 300))
     return out
+
+
+def conversion_borrow_runs(X):
+    """Whether q = (X >> 336) - [(X << 240) mod 2^576 < X] borrows past its lowest limb."""
+    b = 1 if ((X << 240) % B576) < X else 0
+    return ((X >> 336) & 0xFFFFFFFF) < b
 
 
 # ---- the tensor-core product: column sums of the bytes of X against R_j ------------

@@ -23,8 +23,9 @@ def test_conversion_states_carry():
     xs = RP.conversion_carry_states(random.Random(27))
     q = [x * (2 ** 240 - 1) // R.M for x in xs]
     assert all(0 < x < R.M for x in xs)
-    assert all((x % 2 ** 256) + qq >= 2 ** 256 for x, qq in zip(xs, q))
+    assert sum((x % 2 ** 256) + qq >= 2 ** 256 for x, qq in zip(xs, q)) >= 72
     assert sum((x % 2 ** 288) + qq >= 2 ** 288 for x, qq in zip(xs, q)) >= 24
+    assert sum(RP.conversion_borrow_runs(x) for x in xs) >= 24
 
 
 def test_tc_model_and_crafted_operands():
