@@ -19,6 +19,7 @@ collective on the data path).
 from __future__ import annotations
 
 import argparse
+import datetime
 import json
 import os
 import statistics
@@ -77,30 +78,48 @@ def load_peaks():
 
 
 class ClockSampler:
-    """nvidia-smi clocks and throttle reasons sampled every 200 ms in the background."""
-    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+    """nvidia-smi clocks and throttle reasons sampled every 20 ms in the background.  start()
+    returns once the first sample is written, so that sampling runs before the timed region
+    begins; begin()/end() mark that region, and the reported clock is the median of the
+    samples taken inside it (of all samples when the region is too short to hold one)."""
+    Q = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
          "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    PERIOD_MS = 20
 
     def __init__(self, gpu_index):
         self.gpu = str(gpu_index)
         self.proc = None
         self.path = None
+        self.t_begin = self.t_end = None
 
     def start(self):
         fd, self.path = tempfile.mkstemp(suffix=".csv")
         os.close(fd)
         try:
             self.proc = subprocess.Popen(
-                ["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits", "-lms", "200",
-                 "-i", self.gpu], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+                ["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits", "-lms",
+                 str(self.PERIOD_MS), "-i", self.gpu], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
         except OSError:
             self.proc = None
+            return
+        deadline = time.time() + 3.0
+        while time.time() < deadline and self.proc.poll() is None:
+            with open(self.path) as fh:
+                if fh.read().count("\n") >= 1:
+                    break
+            time.sleep(0.01)
+
+    def begin(self):
+        self.t_begin = datetime.datetime.now()
+
+    def end(self):
+        self.t_end = datetime.datetime.now()
 
     def stop(self):
         if self.proc is None:
             return None
-        time.sleep(0.25)
+        time.sleep(2.5 * self.PERIOD_MS / 1000)
         self.proc.terminate()
         try:
             self.proc.wait(timeout=5)
@@ -110,17 +129,27 @@ class ClockSampler:
         with open(self.path) as fh:
             for line in fh:
                 parts = [x.strip() for x in line.split(",")]
-                if len(parts) >= 9:
+                if len(parts) >= 10:
                     rows.append(parts)
         os.unlink(self.path)
         if not rows:
             return None
-        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
-        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+
+        def when(r):
+            try:
+                return datetime.datetime.strptime(r[0], "%Y/%m/%d %H:%M:%S.%f")
+            except ValueError:
+                return None
+
+        inside = [r for r in rows if self.t_begin and self.t_end and when(r) and self.t_begin <= when(r) <= self.t_end]
+        use = inside or rows
+        sm = [float(r[2]) for r in use if r[2].replace(".", "").isdigit()]
+        mx = [float(r[3]) for r in rows if r[3].replace(".", "").isdigit()]
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower() == "active"})
+        reasons = sorted({names[k] for r in use for k in range(4) if r[6 + k].lower() == "active"})
         return {"sm_mhz": statistics.median(sm) if sm else None,
-                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons, "samples": len(rows)}
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons, "samples": len(rows),
+                "samples_in_timed_region": len(inside), "period_ms": self.PERIOD_MS}
 
 
 def cpu_oracle_sample(n_sample, first_seed, threads=None):
@@ -229,11 +258,13 @@ def run_native(args, rank, world, local_rank):
         barrier()
         torch.cuda.synchronize()
         clk.start()
+        clk.begin()
         t0.record(stream)
         for k in range(args.steps):
             step(evs[k])
         t1.record(stream)
         torch.cuda.synchronize()
+        clk.end()
         barrier()
         clocks = clk.stop()
         g.sync(sp)
