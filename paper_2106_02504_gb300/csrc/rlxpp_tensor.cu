@@ -148,8 +148,9 @@ __device__ __forceinline__ void write_x_row(__half* tile, int row, const uint32_
   }
 }
 
-// Column bit patterns 0x3F000000 + S_k + e_k -> X = sum_k S_k 2^(8k) mod m.
-__device__ __forceinline__ void columns_to_x(const uint32_t col[72], uint32_t X[kLimbs]) {
+// Column bit patterns 0x3F000000 + S_k + e_k -> the assembled value X + T 2^576, which
+// is congruent to sum_k S_k 2^(8k) mod m.
+__device__ __forceinline__ void columns_assemble(const uint32_t col[72], uint32_t X[kLimbs], uint32_t& T) {
   // Limb t gathers its four columns as w_t = u + 2^16 v (below 2^48, as lo + hi 2^32),
   // u = col_4t + 2^8 col_4t+1 mod 2^32 = 0x3F000000 + (S + e)_4t + 2^8 (S + e)_4t+1
   // exactly (2^8 0x3F000000 = 0 mod 2^32 and the rest stays below 2^32), v likewise:
@@ -171,7 +172,12 @@ __device__ __forceinline__ void columns_to_x(const uint32_t col[72], uint32_t X[
   X[1] = add_cc(lo[1], hi[0]);
 #pragma unroll
   for (int t = 2; t < kLimbs; ++t) X[t] = addc_cc(lo[t], hi[t - 1]);
-  const uint32_t T = addc(hi[kLimbs - 1], 0u);
+  T = addc(hi[kLimbs - 1], 0u);
+}
+
+// The fold of the assembled value, X + T (2^240 - 1) with 16128 <= T <= 34489, and the
+// final correction into [0, m).
+__device__ __forceinline__ void fold_x(uint32_t X[kLimbs], uint32_t T) {
   // fold: X + T (2^240 - 1).  T (2^240 - 1) = (T - 1) 2^240 + (2^240 - T) for 1 <= T < 2^16:
   // limb 0 = 2^32 - T, limbs 1..6 all ones, limb 7 = ((T - 1) << 16) | 0xFFFF.
   X[0] = add_cc(X[0], 0u - T);
@@ -209,6 +215,57 @@ __device__ __forceinline__ void columns_to_x(const uint32_t col[72], uint32_t X[
 #pragma unroll
       for (int k = 0; k < kLimbs; ++k) X[k] = ge ? e[k] : X[k];
     }
+  }
+}
+
+
+// Column bit patterns 0x3F000000 + S_k + e_k -> X = sum_k S_k 2^(8k) mod m.
+__device__ __forceinline__ void columns_to_x(const uint32_t col[72], uint32_t X[kLimbs]) {
+  uint32_t T;
+  columns_assemble(col, X, T);
+  fold_x(X, T);
+}
+
+// The integer epilogue of one refill: X = sum_k S_k 2^(8k) mod m from the column bit
+// patterns, written to this thread's operand row (the next product's input), and
+// D = its 24 RANLUX numbers (Sec. 2.3).  The common case is computed without a branch:
+// the fold's carry stops in limb 8, the top limb is not all ones (so X < m) and the
+// conversion's quick test decides its quotient, with no carry out of limb 7 of X + q.
+// Any other case (about 2^-15 of the refills) is redone in one branch by the exact forms
+// (fold_x, to_ranlux), which rewrite the row and D.
+__device__ __forceinline__ void tc_epilogue(const uint32_t col[72], __half* tile, int row, uint32_t X[kLimbs],
+                                            uint32_t D[kLimbs]) {
+  uint32_t Xa[kLimbs], T;
+  columns_assemble(col, Xa, T);
+  X[0] = add_cc(Xa[0], 0u - T);
+#pragma unroll
+  for (int k = 1; k < 7; ++k) X[k] = addc_cc(Xa[k], 0xFFFFFFFFu);
+  X[7] = addc_cc(Xa[7], (T - 1u) << 16 | 0xFFFFu);
+  X[8] = addc_cc(Xa[8], 0u);
+  const uint32_t c9 = addc(0u, 0u);  // carry out of limb 8
+#pragma unroll
+  for (int k = 9; k < kLimbs; ++k) X[k] = Xa[k];
+  write_x_row(tile, row, X);
+  const uint32_t t15 = sub_cc(__funnelshift_l(X[7], X[8], 16), X[15]);
+  const uint32_t t16 = subc_cc(__funnelshift_l(X[8], X[9], 16), X[16]);
+  const uint32_t t17 = subc_cc(__funnelshift_l(X[9], X[10], 16), X[17]);
+  const uint32_t borrow = subc(0u, 0u) & 1u;
+  const uint32_t q0 = __funnelshift_l(X[10], X[11], 16);
+  D[0] = add_cc(X[0], q0 - borrow);
+#pragma unroll
+  for (int k = 1; k < 7; ++k) D[k] = addc_cc(X[k], __funnelshift_l(X[10 + k], X[11 + k], 16));
+  D[7] = addc_cc(X[7], X[17] >> 16);
+  const uint32_t c8 = addc(0u, 0u);  // carry out of limb 7 of X + q
+#pragma unroll
+  for (int k = 8; k < kLimbs; ++k) D[k] = X[k];
+  const bool rare = (c9 | c8) != 0u || X[17] == 0xFFFFFFFFu || (t15 & t16 & t17) == 0xFFFFFFFFu ||
+                    (t15 | t16 | t17) == 0u || q0 < borrow;
+  if (__builtin_expect(rare, 0)) {
+#pragma unroll
+    for (int k = 0; k < kLimbs; ++k) X[k] = Xa[k];
+    fold_x(X, T);
+    write_x_row(tile, row, X);
+    to_ranlux(X, D);
   }
 }
 
@@ -584,9 +641,7 @@ __global__ void __launch_bounds__(kTcRows* T, T == 1 ? 4 : 1)
     }
     uint64_t dst = 0;  // destination of this lane's full block (streams out of step)
     if (mine) {
-      columns_to_x(col, X);
-      write_x_row(G.tile, G.t, X);  // the next product's operand
-      to_ranlux(X, D);
+      tc_epilogue(col, G.tile, G.t, X, D);  // X also into the next product's operand row
       const int64_t rem = cnt - k;
       if (tma) {
         // the whole block into this thread's row of the staging box; past the count

@@ -13,7 +13,7 @@ from oracle import ranluxpp as R
 from oracle import swb_lib as S
 from paper_2106_02504_gb300 import workloads as W
 from tests.oracle_side import StreamSet, from_limbs64, limbs64
-from tests.rare_paths import tc_above_m_inputs, tc_limb8_carry_inputs
+from tests.rare_paths import conversion_carry_states, tc_above_m_inputs, tc_limb8_carry_inputs
 
 pytestmark = pytest.mark.gpu
 
@@ -52,6 +52,42 @@ def test_tc_product(native, p):
     got = out.cpu().numpy().view(np.uint64)
     for k in range(n):
         assert from_limbs64(got[k]) == A * xs[k] % M, (p, k)
+
+
+@pytest.mark.parametrize("p", [389, 2048])
+def test_tc_draw_rare_epilogue(native, p):
+    """States whose next refill in the tensor draw kernels takes the epilogue's rare branch:
+    products whose fold carries past limb 8, products below 2^240 - 1 (the final
+    correction), and products whose conversion carries past limb 7 or borrows past the
+    lowest limb of its quotient.  From an exhausted block every stream draws two blocks of
+    doubles (the tile-wide store kernel) and then the fused sum and histogram; values, sums
+    and final states against the oracle."""
+    A, M = R.luxury_multiplier(p), R.M
+    Ainv = pow(A, -1, M)
+    xs = tc_limb8_carry_inputs(A, random.Random(500 + p)) + tc_above_m_inputs(A)
+    xs += [Ainv * y % M for y in conversion_carry_states(random.Random(600 + p), k=8)]
+    xs = [x for x in xs if 0 < x < M]
+    n = len(xs)
+    ref = StreamSet(xs, p, [24] * n)
+    g = native.Generator(n, [p], torch.arange(1, n + 1, dtype=torch.int64, device="cuda"))
+    g.set_path(native.RLXPP_PATH_TENSOR)
+    g.set_state(ref.state_records().view(np.int64).copy())
+    out = torch.zeros((n, 24), dtype=torch.float64, device="cuda")
+    g.draw_f64(out, 24)
+    want = ref.draw(24, S.KIND_F64)
+    assert np.array_equal(out.cpu().numpy().view(np.uint64), want.view(np.uint64))
+    assert np.array_equal(states(native, g, n).numpy().view(np.uint64), ref.state_records())
+    # the fused consumer from the same states
+    ref = StreamSet(xs, p, [24] * n)
+    g.set_state(ref.state_records().view(np.int64).copy())
+    sums = torch.zeros(n, dtype=torch.int64, device="cuda")
+    hist = torch.zeros(256, dtype=torch.int64, device="cuda")
+    g.draw_f64_sum_hist(36, sums, hist)
+    wsums, whist = ref.sum_hist(36)
+    assert np.array_equal(sums.cpu().numpy().view(np.uint64), wsums)
+    assert np.array_equal(hist.cpu().numpy().view(np.uint64), whist)
+    assert np.array_equal(states(native, g, n).numpy().view(np.uint64), ref.state_records())
+    g.sync()
 
 
 def pair(native, seeds, levels=(2048,)):
