@@ -47,7 +47,7 @@ SM_MAX_MHZ = 2070.0
 ALU_PER_SM_CLK = 64
 TC_FLOP_PER_ADVANCE = 2 * 80 * 80      # padded 128 x 80 x 80 fp16 product per 128 streams
 TC_ALG_FLOP_PER_ADVANCE = 2 * 72 * 72  # the 5,184 byte products of the 72 x 72 folded matrix
-ALU_INSTR_PER_ADVANCE_TC = 199         # ALU-pipe instructions per refill of k_draw_tc<sum/hist> (ncu)
+ALU_INSTR_PER_ADVANCE_TC = 202         # ALU-pipe instructions per refill of k_draw_tc<sum/hist> (ncu)
 TC_FUSED_DRAM_BYTES_PER_STREAM = 76.2  # its DRAM traffic per stream and launch (ncu, 2^18 streams)
 CPU_SAMPLE_STREAMS = 16384
 
