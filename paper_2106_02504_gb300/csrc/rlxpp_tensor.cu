@@ -218,7 +218,6 @@ __device__ __forceinline__ void fold_x(uint32_t X[kLimbs], uint32_t T) {
   }
 }
 
-
 // Column bit patterns 0x3F000000 + S_k + e_k -> X = sum_k S_k 2^(8k) mod m.
 __device__ __forceinline__ void columns_to_x(const uint32_t col[72], uint32_t X[kLimbs]) {
   uint32_t T;
@@ -230,7 +229,8 @@ __device__ __forceinline__ void columns_to_x(const uint32_t col[72], uint32_t X[
 // patterns, written to this thread's operand row (the next product's input), and
 // D = its 24 RANLUX numbers (Sec. 2.3).  The common case is computed without a branch:
 // the fold's carry stops in limb 8, the top limb is not all ones (so X < m) and the
-// conversion's quick test decides its quotient, with no carry out of limb 7 of X + q.
+// conversion's quick test (that of to_ranlux) decides its quotient, with no carry out
+// of limb 7 of X + q.
 // Any other case (about 2^-15 of the refills) is redone in one branch by the exact forms
 // (fold_x, to_ranlux), which rewrite the row and D.
 __device__ __forceinline__ void tc_epilogue(const uint32_t col[72], __half* tile, int row, uint32_t X[kLimbs],
