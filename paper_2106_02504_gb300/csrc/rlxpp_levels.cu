@@ -78,32 +78,54 @@ __global__ void k_level_digits(uint32_t* __restrict__ table) {
   }
 }
 
+// Seeding: stream i gets A^(2^96 seed_i), by the windowed table (at most 16 products
+// for a 64-bit seed).  Each thread seeds kSeedRun consecutive streams; where a stream's
+// seed is the previous stream's plus one at the same level, its state is the previous
+// state times A^(2^96) (the table's window 24, digit 1): one product instead of one per
+// nonzero hex digit of the seed.
+constexpr int kSeedRun = 8;
 __global__ void k_seed(StateView s, const uint64_t* __restrict__ seeds,
                        const uint8_t* __restrict__ level_of, uint32_t n_levels, bool keep_levels) {
-  const uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= s.n) return;
-  uint32_t lvl = keep_levels ? meta_level(s.meta[i]) : level_of ? level_of[i] : 0u;
-  if (lvl >= n_levels) {
-    set_status(s.status, RLXPP_ERR_INVALID);
-    lvl = 0;
-  }
-  const uint64_t seed = seeds[i];
-  if (seed == 0) {  // seeds start at 1: report, and leave a re-seeded stream as it was
-    set_status(s.status, RLXPP_ERR_INVALID);
-    if (keep_levels) return;
-  }
-  const uint32_t* T = s.table + (size_t)lvl * kTableLimbs;
+  const uint64_t i0 = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) * kSeedRun;
   uint32_t X[kLimbs];
-  bool have = false;
-  apply_digits(T, kSeedWindow0, seed, X, have);
-  if (!have) {  // a new handle's stream with seed 0: the state 1, so that it is defined
+  uint64_t prev = 0;  // seed of the state in X, 0 when X holds none to continue from
+  uint32_t prev_lvl = 0;
+#pragma unroll 1
+  for (int j = 0; j < kSeedRun; ++j) {
+    const uint64_t i = i0 + j;
+    if (i >= s.n) return;
+    uint32_t lvl = keep_levels ? meta_level(s.meta[i]) : level_of ? level_of[i] : 0u;
+    if (lvl >= n_levels) {
+      set_status(s.status, RLXPP_ERR_INVALID);
+      lvl = 0;
+    }
+    const uint64_t seed = seeds[i];
+    const uint32_t* T = s.table + (size_t)lvl * kTableLimbs;
+    if (seed == 0) {  // seeds start at 1: report, and leave a re-seeded stream as it was
+      set_status(s.status, RLXPP_ERR_INVALID);
+      prev = 0;
+      if (keep_levels) continue;
+      // a new handle's stream with seed 0: the state 1, so that it is defined
 #pragma unroll
-    for (int k = 0; k < kLimbs; ++k) X[k] = k == 0 ? 1u : 0u;
+      for (int k = 0; k < kLimbs; ++k) X[k] = k == 0 ? 1u : 0u;
+    } else if (prev != 0 && seed == prev + 1 && lvl == prev_lvl) {
+      uint32_t Y[kLimbs], R[kLimbs];
+      load18(T + ((size_t)kSeedWindow0 * kDigits + 1) * kLimbs, Y);
+      mul_mod(X, Y, R);
+#pragma unroll
+      for (int k = 0; k < kLimbs; ++k) X[k] = R[k];
+      prev = seed;
+    } else {
+      bool have = false;
+      apply_digits(T, kSeedWindow0, seed, X, have);  // have: seed != 0
+      prev = seed;
+      prev_lvl = lvl;
+    }
+    uint32_t D[kLimbs];
+    to_ranlux(X, D);
+    store_state_D(s, i, D);
+    s.meta[i] = meta_pack(0u, carry_of(X, D), lvl);
   }
-  uint32_t D[kLimbs];
-  to_ranlux(X, D);
-  store_state_D(s, i, D);
-  s.meta[i] = meta_pack(0u, carry_of(X, D), lvl);
 }
 
 __global__ void k_skip(StateView s, const uint64_t* __restrict__ n128) {
@@ -302,7 +324,8 @@ cudaError_t launch_level_setup(uint32_t p, uint32_t* lux_out18, uint32_t* table_
 cudaError_t launch_seed(const StateView& s, const uint64_t* seeds, const uint8_t* level_of_stream,
                         uint32_t n_levels, bool keep_levels, cudaStream_t st) {
   if (s.n == 0) return cudaSuccess;
-  k_seed<<<grid_for(s.n, 128), 128, 0, st>>>(s, seeds, level_of_stream, n_levels, keep_levels);
+  k_seed<<<grid_for((s.n + kSeedRun - 1) / kSeedRun, 128), 128, 0, st>>>(s, seeds, level_of_stream, n_levels,
+                                                                          keep_levels);
   return cudaGetLastError();
 }
 

@@ -79,6 +79,37 @@ def test_seed_states(native):
     g2.close()
 
 
+def _seed_records(seeds, levels, level_of):
+    rec = np.zeros((len(seeds), 11), dtype=np.uint64)
+    for i, s in enumerate(seeds):
+        p = levels[level_of[i]]
+        D, c = R.to_ranlux(R.seed_lcg(int(s), p))
+        rec[i, :9] = [(D >> (64 * k)) & (2 ** 64 - 1) for k in range(9)]
+        rec[i, 9] = c
+        rec[i, 10] = p
+    return rec
+
+
+def test_seed_runs(native):
+    """Seeding continues a run of consecutive seeds at one level by one product per stream:
+    runs that cross the kernel's groups of 8 streams, broken runs, repeated and
+    descending seeds, the largest seeds, level changes inside a run and a ragged tail, on
+    a new handle and when re-seeding, against the oracle."""
+    seeds = list(range(1, 20)) + [100, 101, 103, 104, 2 ** 64 - 2, 2 ** 64 - 1, 1, 2, 7, 7, 8, 5, 4] + \
+        list(range(1000, 1037))
+    seeds = np.array(seeds, dtype=np.uint64)
+    n = len(seeds)
+    levels = (24, 2048)
+    level_of = [(i // 5) % 2 for i in range(n)]   # a level change every 5 streams
+    g = make(native, seeds, levels=levels, level_of=level_of)
+    assert np.array_equal(states(native, g, n), _seed_records(seeds, levels, level_of))
+    re = seeds + np.uint64(5)                       # re-seed: the same runs, shifted
+    re[re < 5] = 9                                  # (2^64 - 2 and 2^64 - 1 wrapped)
+    g.seed(dev_u64(re))
+    assert np.array_equal(states(native, g, n), _seed_records(re, levels, level_of))
+    g.sync()
+
+
 def test_zero_seed_rejected(native):
     """Seeds start at 1: a zero in a host array fails the call at once; a zero in a
     device array is reported by rlxpp_sync, a re-seeded stream with seed 0 keeps its
