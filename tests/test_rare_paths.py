@@ -38,3 +38,49 @@ def test_tc_model_and_crafted_operands():
     hits = RP.tc_limb8_carry_inputs(A, random.Random(2148))
     assert hits and all(RP.tc_fold_carries(x, A)[0] for x in hits)
     assert all(RP.tc_fold_carries(x, A)[1] for x in RP.tc_above_m_inputs(A))
+
+
+def _tc_epilogue_common_path(x, A):
+    """The tensor draw kernels' epilogue on its common path, restated on Python integers
+    limb by limb as the kernel computes it: the fold with its carry stopped at limb 8,
+    and the conversion's quick quotient with its carry stopped at limb 7.  Returns
+    (X, D, rare), rare being the kernel's test for redoing both exactly."""
+    v = RP.tc_assembled(x, A)
+    T, Xa = v >> 576, v % RP.B576
+    low = (Xa % RP.B288) + T * ((1 << 240) - 1)
+    c9 = low >> 288
+    X = (Xa >> 288 << 288) | (low % RP.B288)
+    limb = [(X >> (32 * k)) & 0xFFFFFFFF for k in range(18)]
+    S = (X << 240) % RP.B576
+    top = (S >> 480) - (X >> 480)              # limbs 15..17 of S - X, no borrow from below
+    borrow = 1 if top < 0 else 0
+    t = top % (1 << 96)
+    q0 = (X >> 336) & 0xFFFFFFFF
+    # q = (X >> 336) - borrow, the borrow taken from its lowest limb alone
+    s8 = (X % RP.B256) + (q0 - borrow) % (1 << 32) + ((X >> 368) << 32)
+    c8 = s8 >> 256
+    D = (X >> 256 << 256) | (s8 % RP.B256)
+    rare = (c9 or c8 or limb[17] == 0xFFFFFFFF or t == (1 << 96) - 1 or t == 0 or q0 < borrow)
+    return X, D, rare
+
+
+def test_tc_epilogue_common_path_is_exact():
+    """Wherever the kernel's test lets the common path stand, its X and D equal A x mod m
+    and floor(2^576 X / m); the crafted operands all take the rare branch."""
+    rng = random.Random(8)
+    for p in (24, 2048):
+        A = R.luxury_multiplier(p)
+        common = 0
+        for _ in range(4000):
+            x = rng.randrange(1, R.M)
+            X, D, rare = _tc_epilogue_common_path(x, A)
+            if not rare:
+                common += 1
+                assert X == A * x % R.M
+                assert D == R.to_ranlux(X)[0]
+        assert common >= 3990
+    A = R.luxury_multiplier(2048)
+    Ainv = pow(A, -1, R.M)
+    crafted = RP.tc_limb8_carry_inputs(A, random.Random(2548)) + RP.tc_above_m_inputs(A)[1:]
+    crafted += [Ainv * y % R.M for y in RP.conversion_carry_states(random.Random(2648), k=8)]
+    assert all(_tc_epilogue_common_path(x, A)[2] for x in crafted)
