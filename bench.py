@@ -47,9 +47,52 @@ SM_MAX_MHZ = 2070.0
 ALU_PER_SM_CLK = 64
 TC_FLOP_PER_ADVANCE = 2 * 80 * 80      # padded 128 x 80 x 80 fp16 product per 128 streams
 TC_ALG_FLOP_PER_ADVANCE = 2 * 72 * 72  # the 5,184 byte products of the 72 x 72 folded matrix
-ALU_INSTR_PER_ADVANCE_TC = 202         # ALU-pipe instructions per refill of k_draw_tc<sum/hist> (ncu)
-TC_FUSED_DRAM_BYTES_PER_STREAM = 76.2  # its DRAM traffic per stream and launch (ncu, 2^18 streams)
 CPU_SAMPLE_STREAMS = 16384
+# Figures of one ncu capture of the fused tensor kernel (k_draw_tc<sum/hist>): DRAM
+# bytes (read + write) per stream and launch, and ALU-pipe instructions per refill.
+# They describe the kernel as compiled from the sources whose digest is `src_sha`
+# (kernel_sources_sha); once those sources change, the figures are reported as null.
+TC_FUSED_CAPTURE = {"dram_bytes_per_stream": None, "alu_instr_per_refill": None, "streams": None,
+                    "src_sha": None}
+KERNEL_SOURCES = ("rlxpp_tensor.cu", "rlxpp_arith.cuh", "rlxpp_drawloop.cuh", "rlxpp_state.cuh",
+                  "rlxpp_internal.h", "rlxpp_batch.h", "rlxpp_fixmath.cuh", "rlxpp_fixmath_tables.h")
+
+
+def kernel_sources_sha():
+    """Digest of the sources the tensor draw kernels compile from (first 16 hex digits)."""
+    import hashlib
+    h = hashlib.sha256()
+    for name in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, "paper_2106_02504_gb300", "csrc", name), "rb") as fh:
+            h.update(name.encode() + b"\0" + fh.read())
+    return h.hexdigest()[:16]
+
+
+def tensor_roofline(kernel, advances, ms, peak_tflops, peak_source, n_streams):
+    """Roofline of a tensor-path draw kernel: the algorithmic 72 x 72 byte products per
+    advance (5,184 multiply-adds, 10,368 flop) over the kernel's CUDA-event time, against
+    the measured dense fp16/bf16 tensor peak.  The ALU-pipe view and the DRAM traffic
+    come from the recorded ncu capture while the kernel's sources are unchanged."""
+    achieved = advances * TC_ALG_FLOP_PER_ADVANCE / (ms * 1e-3) / 1e12
+    cap = TC_FUSED_CAPTURE
+    current = cap["src_sha"] is not None and cap["src_sha"] == kernel_sources_sha()
+    r = {"bound": "tensor", "kernel": kernel, "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
+         "frac": achieved / peak_tflops, "peak_source": peak_source,
+         "work": f"{advances} advances x {TC_ALG_FLOP_PER_ADVANCE} flop (5,184 byte products of A's folded "
+                 f"72 x 72 matrix with X's bytes per advance)",
+         "padded_mma_tflops": advances * TC_FLOP_PER_ADVANCE / (ms * 1e-3) / 1e12,
+         "traffic": cap["dram_bytes_per_stream"] * n_streams if current else None,
+         "traffic_source": ("ncu dram__bytes_read.sum + dram__bytes_write.sum of this kernel on "
+                            f"{cap['streams']} streams, scaled by streams; sources {cap['src_sha']}"
+                            if current else "null: no ncu capture of the kernel as currently built")}
+    if current and cap["alu_instr_per_refill"]:
+        alu = advances * cap["alu_instr_per_refill"] / (ms * 1e-3) / 1e12
+        peak_alu = SMS * ALU_PER_SM_CLK * SM_MAX_MHZ * 1e6 / 1e12
+        r["secondary_alu_pipe"] = {"what": "ALU-pipe instructions issued (ncu count per refill), not "
+                                           "algorithmic work", "instr_per_refill": cap["alu_instr_per_refill"],
+                                   "achieved_tops": alu, "peak_tops": peak_alu, "frac": alu / peak_alu,
+                                   "peak_source": "derived: 152 SMs x 64 ALU lanes/clk x 2070 MHz"}
+    return r
 
 
 def advances_for(count, pos_words, need=2):
@@ -171,6 +214,23 @@ def cpu_oracle_sample(n_sample, first_seed, threads=None):
     return dt, n_sample * (HBM_COUNT + FUSED_COUNT), threads
 
 
+def max_over_ranks(x, dist, device):
+    """The largest of the ranks' values of x (the slowest rank's time); x itself when
+    there is one rank.  A collective of the benchmark only, not of the data path."""
+    if dist is None:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_doubles_per_s(n_streams_per_rank, world, ms_per_step):
+    """Doubles of all ranks per step (each rank draws for its own streams) over the
+    slowest rank's time per step."""
+    return n_streams_per_rank * (HBM_COUNT + FUSED_COUNT) * world / (ms_per_step * 1e-3)
+
+
 def workload_config(n_streams, world):
     return {"workload": f"{n_streams} streams x {world} ranks, p={LUXURY}: seed (stream i = seed-1 state "
                         f"skipped by i*2^96 advances) + {HBM_COUNT} f64/stream to HBM + {FUSED_COUNT} "
@@ -268,11 +328,7 @@ def run_native(args, rank, world, local_rank):
         barrier()
         clocks = clk.stop()
         g.sync(sp)
-        ms = t0.elapsed_time(t1)
-        if dist is not None:
-            t = torch.tensor([ms], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ms = float(t.item())
+        ms = max_over_ranks(t0.elapsed_time(t1), dist, dev)
         per_kernel = {
             "seed": statistics.mean(e[0].elapsed_time(e[1]) for e in evs),
             "draw_f64_hbm": statistics.mean(e[1].elapsed_time(e[2]) for e in evs),
@@ -309,13 +365,12 @@ def run_native(args, rank, world, local_rank):
                 entry["hbm_write_peak_gbs"] = hbm_write_gbs
                 entry["hbm_write_frac"] = entry["hbm_gbs"] / hbm_write_gbs
             kern[kname] = entry
-        paths[name] = {"ms_per_step": ms_step, "value": n * (HBM_COUNT + FUSED_COUNT) * world / (ms_step * 1e-3),
+        paths[name] = {"ms_per_step": ms_step, "value": whole_job_doubles_per_s(n, world, ms_step),
                        "kernels": kern, "per_kernel_ms": per_kernel, "clocks": clocks}
     best = max(paths, key=lambda k: paths[k]["value"])
     ms_step, per_kernel, clocks = paths[best]["ms_per_step"], paths[best]["per_kernel_ms"], paths[best]["clocks"]
-    doubles_step = n * (HBM_COUNT + FUSED_COUNT) * world
     advances_step = n * ADV_PER_STREAM * world
-    value = doubles_step / (ms_step * 1e-3)
+    value = whole_job_doubles_per_s(n, world, ms_step)
     dom = max(per_kernel, key=per_kernel.get)
     adv = {"draw_f64_sum_hist": n * ADV_FUSED, "draw_f64_hbm": n * ADV_HBM}.get(dom, 0)
     if best == "imad":
@@ -325,17 +380,8 @@ def run_native(args, rank, world, local_rank):
                     "frac": achieved / (imad_peak / 1e12),
                     "peak_source": "derived: 152 SMs x 64 IMAD/clk x 2070 MHz", "traffic": None}
     else:
-        achieved = adv * ALU_INSTR_PER_ADVANCE_TC / (per_kernel[dom] * 1e-3) / 1e12
-        roofline = {"bound": "alu", "kernel": dom + " (k_draw_tc, tensor path)", "achieved": achieved,
-                    "peak": SMS * ALU_PER_SM_CLK * SM_MAX_MHZ * 1e6 / 1e12,
-                    "unit": f"Top/s (integer-pipe instructions of the epilogue, {ALU_INSTR_PER_ADVANCE_TC} per advance)",
-                    "frac": achieved / (SMS * ALU_PER_SM_CLK * SM_MAX_MHZ * 1e6 / 1e12),
-                    "peak_source": "derived: 152 SMs x 64 ALU lanes/clk x 2070 MHz",
-                    "traffic": TC_FUSED_DRAM_BYTES_PER_STREAM * n if dom == "draw_f64_sum_hist" else None,
-                    "traffic_source": "ncu dram__bytes_read+write of k_draw_tc<sum/hist> on 2^18 streams, "
-                                      "scaled by streams (profiles/k_draw_tc_262144_streams_full.md)",
-                    "tensor_pipe": {"achieved_tflops": adv * TC_FLOP_PER_ADVANCE / (per_kernel[dom] * 1e-3) / 1e12,
-                                    "peak_tflops": f16_peak, "peak_source": "MEASURED_PEAKS bf16_tflops (burst)"}}
+        roofline = tensor_roofline(dom + " (k_draw_tc, tensor path)", adv, per_kernel[dom], f16_peak,
+                                   "MEASURED_PEAKS bf16_tflops (burst; dense fp16 runs at the bf16 rate)", n)
     for name in paths:
         paths[name].pop("per_kernel_ms")
     result = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -630,11 +676,7 @@ def run_e2e(args, nat, g, seeds_h, n, world, dev, dist):
     for _ in range(steps):
         step()
     torch.cuda.synchronize()
-    dt = time.perf_counter() - t0
-    if dist is not None:
-        t = torch.tensor([dt], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        dt = float(t.item())
+    dt = max_over_ranks(time.perf_counter() - t0, dist, dev)
     doubles = n * (HBM_COUNT + FUSED_COUNT) * world * steps
     d2h = n * HBM_COUNT * 8 + n * 8 + 256 * 8
     return {"value": doubles / dt, "unit": UNIT, "h2d_bytes_per_step": n * 8,

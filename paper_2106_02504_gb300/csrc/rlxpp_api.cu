@@ -76,15 +76,27 @@ rlxpp_status cuda_status(cudaError_t e) {
 
 cudaStream_t as_stream(void* s) { return reinterpret_cast<cudaStream_t>(s); }
 
-// true when the device can dereference p directly (device or managed memory)
-bool on_device(const void* p) {
+// Where a pointer lives, seen from the current device: memory the current device can
+// dereference directly (its own device memory, or managed memory), host memory (also
+// unregistered), or device memory of another GPU, which the kernels must not be given
+// (without peer access the first load would fault).
+enum class Mem { kHost, kDevice, kOtherDevice };
+Mem mem_kind(const void* p) {
   cudaPointerAttributes attr;
   if (cudaPointerGetAttributes(&attr, p) != cudaSuccess) {
     cudaGetLastError();
-    return false;
+    return Mem::kHost;
   }
-  return attr.type == cudaMemoryTypeDevice || attr.type == cudaMemoryTypeManaged;
+  if (attr.type == cudaMemoryTypeManaged) return Mem::kDevice;
+  if (attr.type != cudaMemoryTypeDevice) return Mem::kHost;
+  int cur = -1;
+  if (cudaGetDevice(&cur) != cudaSuccess) {
+    cudaGetLastError();
+    return Mem::kOtherDevice;
+  }
+  return attr.device == cur ? Mem::kDevice : Mem::kOtherDevice;
 }
+bool on_device(const void* p) { return mem_kind(p) == Mem::kDevice; }
 
 // Seeds start at 1.  A host array is checked here (the call then fails at once); zeros
 // in a device array are reported by the seeding kernel (sticky RLXPP_ERR_INVALID).
@@ -108,6 +120,8 @@ struct Staged {
 
 rlxpp_status stage_in(const void* src, size_t bytes, cudaStream_t st, Staged& out) {
   out.st = st;
+  if (src != nullptr && mem_kind(src) == Mem::kOtherDevice)
+    return fail(RLXPP_ERR_INVALID, "an input array is device memory of another GPU");
   if (src == nullptr || bytes == 0 || on_device(src)) {
     out.dev = const_cast<void*>(src);
     return RLXPP_OK;
@@ -205,6 +219,7 @@ rlxpp_status draw_common(rlxpp_gen* g, int kind, const int64_t* counts, const in
     if (!counts && count_each == 0) return RLXPP_OK;
     return fail(RLXPP_ERR_INVALID, "null output");
   }
+  if (mem_kind(out) == Mem::kOtherDevice) return fail(RLXPP_ERR_INVALID, "output is device memory of another GPU");
   Staged sc, so;
   if (rlxpp_status s = stage_in(counts, sizeof(int64_t) * g->n, st, sc)) return s;
   if (rlxpp_status s = stage_in(offsets, sizeof(int64_t) * g->n, st, so)) return s;

@@ -413,7 +413,9 @@ __global__ void k_seed_records(const uint32_t* __restrict__ scratch, LevelList l
 }
 
 // Device address of g_noalloc_scratch, looked up once per device (with that device
-// current) the first time the entry point runs on it.
+// current) the first time the entry point runs on it.  The address stays valid for the
+// life of the device's primary context: a cudaDeviceReset between calls would leave it
+// dangling, so the entry point must not be used across a reset.
 constexpr int kMaxDevices = 64;
 std::mutex g_noalloc_mutex;
 uint32_t* g_noalloc_ptr[kMaxDevices] = {};
@@ -436,13 +438,21 @@ rlxpp_status noalloc_scratch(uint32_t** out) {
   return RLXPP_OK;
 }
 
+// Memory the current device can dereference: its own device memory or managed memory.
+// Device memory of another GPU is refused (without peer access a load from it faults).
 bool device_pointer(const void* p) {
   cudaPointerAttributes attr;
   if (cudaPointerGetAttributes(&attr, p) != cudaSuccess) {
     cudaGetLastError();
     return false;
   }
-  return attr.type == cudaMemoryTypeDevice || attr.type == cudaMemoryTypeManaged;
+  if (attr.type == cudaMemoryTypeManaged) return true;
+  int cur = -1;
+  if (attr.type != cudaMemoryTypeDevice || cudaGetDevice(&cur) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return attr.device == cur;
 }
 
 }  // namespace
@@ -469,7 +479,8 @@ extern "C" rlxpp_status rlxpp_seed_states_noalloc(const uint32_t* levels, uint32
   if (!seeds || !out) return set_last_error(RLXPP_ERR_INVALID, "null seeds or output");
   if (!device_pointer(seeds) || !device_pointer(out) ||
       (level_of_stream && !device_pointer(level_of_stream)))
-    return set_last_error(RLXPP_ERR_INVALID, "seeds, level indices and output must be device memory");
+    return set_last_error(RLXPP_ERR_INVALID,
+                          "seeds, level indices and output must be memory of the current device");
   uint32_t* scratch = nullptr;
   if (rlxpp_status s = noalloc_scratch(&scratch)) return s;
   cudaStream_t st = reinterpret_cast<cudaStream_t>(cuda_stream);

@@ -109,10 +109,14 @@ def conversion_edge_states(rng, k=40):
 
 def normals_expected(doubles, n):
     """Gaussian values the draw rule gives from each row's doubles (2 ceil(n / 2) of
-    them), with a per-value tolerance: (want, tol), both (rows, n) float64.  The
-    tolerance 2^-49 (r + 1) covers CUDA's stated error bounds of log (1 ulp), sqrt
-    (correctly rounded) and sincospi (2 ulp) on the device, the oracle's own rounding
-    (a few ulp of r and of the cosine and sine), and the products."""
+    them), with a per-value tolerance: (want, tol), both (rows, n) float64.  The device
+    computes ln, sqrt, cos and sin with its own fixed-point integer routines and rounds
+    each Gaussian value once: it lies within half an ulp plus 2^-56 r of the exact value
+    (ln to a relative 2^-61, the square root to a relative 2^-59, cos and sin to an
+    absolute 2^-59, all before the final rounding).  The oracle uses Python's double
+    log, sqrt, cos and sin after an exact quarter-turn reduction, so it is within a few
+    ulp of r.  With r <= sqrt(96 ln 2) < 8.2, an ulp of a value is at most 2^-52 r, so
+    the two sides differ by well under 2^-49 (r + 1), the tolerance used here."""
     d = np.asarray(doubles, dtype=np.float64)
     da, db = d[:, 0::2], d[:, 1::2]
     z0, z1 = R.box_muller_many(da, db)
@@ -132,3 +136,39 @@ def exponentials_expected(doubles):
     d = np.asarray(doubles, dtype=np.float64)
     want = 0.0 - np.log(1.0 - d)
     return want, 2.0 ** -50 * (want + 1.0)
+
+
+def records_from_windows(words, carry, pos, p):
+    """(n, 11) uint64 state records (struct rlxpp_state: the 24 numbers packed as 9
+    little-endian 64-bit limbs, carry | pos << 32, p) from oracle windows, vectorised:
+    every 8 numbers (192 bits) fill 3 limbs."""
+    w = np.asarray(words, dtype=np.uint64)
+    n = w.shape[0]
+    rec = np.zeros((n, 11), dtype=np.uint64)
+    for g in range(3):
+        x = [w[:, 8 * g + k] for k in range(8)]
+        rec[:, 3 * g] = x[0] | (x[1] << np.uint64(24)) | ((x[2] & np.uint64(0xFFFF)) << np.uint64(48))
+        rec[:, 3 * g + 1] = ((x[2] >> np.uint64(16)) | (x[3] << np.uint64(8)) | (x[4] << np.uint64(32))
+                             | ((x[5] & np.uint64(0xFF)) << np.uint64(56)))
+        rec[:, 3 * g + 2] = (x[5] >> np.uint64(8)) | (x[6] << np.uint64(16)) | (x[7] << np.uint64(40))
+    rec[:, 9] = np.asarray(carry, dtype=np.uint64) | (np.asarray(pos, dtype=np.uint64) << np.uint64(32))
+    rec[:, 10] = p
+    return rec
+
+
+def weighted_checksum(values):
+    """sum_j v_j (2 j + 1) mod 2^64 along the last axis (v as unsigned 64-bit bit
+    patterns).  The weights are odd, hence invertible mod 2^64, so any single changed
+    value changes the sum, and values out of order change it unless their differences
+    cancel by chance."""
+    v = np.asarray(values)
+    v = v.view(np.uint64) if v.dtype.itemsize == 8 else v.astype(np.uint64)
+    w = np.arange(1, 2 * v.shape[-1], 2, dtype=np.uint64)
+    return (v * w).sum(axis=-1, dtype=np.uint64)
+
+
+def skipped_states(job):
+    """For a process pool: X_i A^d_i mod m for (X_i, d_i) pairs at luxury p, by pow."""
+    p, pairs = job
+    A = R.luxury_multiplier(p)
+    return [pow(A, d, R.M) * X % R.M for X, d in pairs]

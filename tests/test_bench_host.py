@@ -71,3 +71,27 @@ def test_clock_samples_inside_the_timed_region():
     c.t_begin = c.t_end = t0 + datetime.timedelta(milliseconds=55)
     got = c.stop()
     assert got["samples_in_timed_region"] == 0 and got["sm_mhz"] == 1835
+
+
+def test_tensor_roofline_is_algorithmic_work_over_the_measured_peak():
+    """The tensor path's roofline counts the 5,184 byte products (10,368 flop) of every
+    advance over the kernel's time, against the measured tensor peak; the recorded ncu
+    figures (traffic, ALU-pipe view) appear only while the kernel sources are the ones
+    they were captured from."""
+    adv, ms, peak, n = (1 << 20) * 341, 5.79, 1914.4, 1 << 20
+    r = bench.tensor_roofline("fused", adv, ms, peak, "measured", n)
+    want = adv * 2 * 72 * 72 / (ms * 1e-3) / 1e12
+    assert r["bound"] == "tensor" and r["unit"] == "TFLOP/s"
+    assert abs(r["achieved"] - want) < 1e-9 * want and abs(r["frac"] - want / peak) < 1e-12
+    saved = dict(bench.TC_FUSED_CAPTURE)
+    try:
+        bench.TC_FUSED_CAPTURE.update(dram_bytes_per_stream=80.0, alu_instr_per_refill=150, streams=262144,
+                                      src_sha="0" * 16)
+        r = bench.tensor_roofline("fused", adv, ms, peak, "measured", n)
+        assert r["traffic"] is None and "secondary_alu_pipe" not in r      # sources changed since
+        bench.TC_FUSED_CAPTURE["src_sha"] = bench.kernel_sources_sha()
+        r = bench.tensor_roofline("fused", adv, ms, peak, "measured", n)
+        assert r["traffic"] == 80.0 * n and r["secondary_alu_pipe"]["instr_per_refill"] == 150
+    finally:
+        bench.TC_FUSED_CAPTURE.clear()
+        bench.TC_FUSED_CAPTURE.update(saved)
