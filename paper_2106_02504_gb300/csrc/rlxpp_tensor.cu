@@ -133,6 +133,31 @@ __device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t* v) {
                : "r"(taddr));
 }
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+// The product with the A operand in tensor memory (a_tmem: its first column, lane 0).
+__device__ __forceinline__ void tc_mma_ta(uint32_t d_tmem, uint32_t a_tmem, uint64_t b_desc, uint32_t accumulate) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n}" ::"r"(d_tmem),
+      "r"(a_tmem), "l"(b_desc), "r"(kIdesc), "r"(accumulate)
+      : "memory");
+}
+// whole warp: 32 (4) consecutive columns of this warp's 32 lanes from registers
+__device__ __forceinline__ void tmem_st32(uint32_t taddr, const uint32_t* v) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,"
+      "%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31,%32};" ::"r"(taddr),
+      "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7]), "r"(v[8]),
+      "r"(v[9]), "r"(v[10]), "r"(v[11]), "r"(v[12]), "r"(v[13]), "r"(v[14]), "r"(v[15]), "r"(v[16]),
+      "r"(v[17]), "r"(v[18]), "r"(v[19]), "r"(v[20]), "r"(v[21]), "r"(v[22]), "r"(v[23]), "r"(v[24]),
+      "r"(v[25]), "r"(v[26]), "r"(v[27]), "r"(v[28]), "r"(v[29]), "r"(v[30]), "r"(v[31])
+      : "memory");
+}
+__device__ __forceinline__ void tmem_st4(uint32_t taddr, const uint32_t* v) {
+  asm volatile("tcgen05.st.sync.aligned.32x32b.x4.b32 [%0], {%1,%2,%3,%4};" ::"r"(taddr), "r"(v[0]), "r"(v[1]),
+               "r"(v[2]), "r"(v[3])
+               : "memory");
+}
+__device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
 
 // ---- per-thread pieces -------------------------------------------------------------
 // X (18 limbs) -> 72 fp16 values (one per byte) in this thread's row of the A tile
@@ -722,6 +747,296 @@ __global__ void __launch_bounds__(kTcRows* T, T == 1 ? 4 : 1)
   }
 }
 
+// ---- the fused sum/histogram draw with the A operand in tensor memory ----------------
+// A one-tile CTA keeps its operand rows in TMEM next to the accumulator: 128 columns,
+// the fp32 accumulator at columns 0..79, row r of the A operand in lane r at columns
+// 80..119 (elements 2i and 2i + 1 of the row in the low and high halves of column
+// 80 + i).  Each thread writes its own X there with tcgen05.st (its warp owns its 32
+// lanes), so per refill the tensor core reads only the level's 12.8 KB matrix from
+// shared memory, and no operand row is written to shared memory at all.
+constexpr uint32_t kTmA = kTcN;    // first A column
+constexpr uint32_t kTmCols = 128;  // TMEM columns of such a CTA
+static_assert(kTmA + kTcK / 2 <= kTmCols, "A operand after the accumulator");
+
+// X (18 limbs) -> its 72 bytes as fp16 subnormals (the pairs of one 32-bit word per two
+// bytes, as write_x_row forms them) into this thread's lane of the A columns.  Every
+// thread of the warp calls it (tcgen05.st is warp-wide).
+__device__ __forceinline__ void write_x_tmem(uint32_t lane_taddr, const uint32_t X[kLimbs]) {
+  uint32_t w[36];
+#pragma unroll
+  for (int c = 0; c < kLimbs; ++c) {
+    w[2 * c] = __byte_perm(X[c], 0u, 0x4140u);
+    w[2 * c + 1] = __byte_perm(X[c], 0u, 0x4342u);
+  }
+  tmem_st32(lane_taddr + kTmA, w);
+  tmem_st4(lane_taddr + kTmA + 32, w + 32);
+}
+
+// One thread: the five K = 16 products (A from TMEM, the level's matrix from shared
+// memory) into the accumulator, committed to the CTA's mbarrier.
+__device__ __forceinline__ void tc_issue_tm(uint32_t taddr, uint32_t b0, uint64_t* bar) {
+#pragma unroll
+  for (int s = 0; s < kTcK / 16; ++s)
+    tc_mma_ta(taddr, taddr + kTmA + 8 * s, smem_desc(b0 + s * 2 * kLBO), s > 0 ? 1u : 0u);
+  tc_commit(bar);
+}
+
+// X = sum_k S_k 2^(8k) mod m from the column bit patterns: the fold in its common form
+// (no carry out of limb 8, top limb not all ones, so the result is below m) and, in one
+// branch for the other cases (about 2^-15 of the refills), the exact fold.
+__device__ __forceinline__ void tc_fold_common(const uint32_t col[72], uint32_t X[kLimbs]) {
+  uint32_t Xa[kLimbs], T;
+  columns_assemble(col, Xa, T);
+  X[0] = add_cc(Xa[0], 0u - T);
+#pragma unroll
+  for (int k = 1; k < 7; ++k) X[k] = addc_cc(Xa[k], 0xFFFFFFFFu);
+  X[7] = addc_cc(Xa[7], (T - 1u) << 16 | 0xFFFFu);
+  X[8] = addc_cc(Xa[8], 0u);
+  const uint32_t c9 = addc(0u, 0u);
+#pragma unroll
+  for (int k = 9; k < kLimbs; ++k) X[k] = Xa[k];
+  if (__builtin_expect(c9 != 0u || X[17] == 0xFFFFFFFFu, 0)) {
+#pragma unroll
+    for (int k = 0; k < kLimbs; ++k) X[k] = Xa[k];
+    fold_x(X, T);
+  }
+}
+
+// The consumer of the fused draw on this kernel.  A full block's twelve 48-bit values
+// v_2q = D_3q + 2^32 lo16(D_3q+1) and v_2q+1 = hi16(D_3q+1) + 2^16 D_3q+2 (32-bit limbs
+// D_i of the block) add up to
+//   S0 + 2^32 S1 + 2^16 S2 - (2^48 - 1) H,
+// where S0, S1, S2 sum the limbs 3q, 3q + 1, 3q + 2 and H sums hi16(D_3q+1); these are
+// kept as 64-bit multiply-adds (hi16 itself as a multiply-high by 2^16) and combined
+// once at the end, modulo 2^64, which is exact because the stream's total is below
+// 2^64.  Values of partial blocks are added as they are.  The histogram of the top 8
+// bits of every value is counted per lane: bin b of lane l is word 32 b + l of the
+// tile's table, so the increments of a warp fall in 32 different banks; a bin is one
+// byte permute, its address one multiply-add.  The multipliers 1, 2^16 and 128 are
+// run-time values (derived from a launch argument), so that the compiler keeps these
+// steps on the FMA pipe rather than turning them into shifts and adds on the ALU pipe,
+// which the conversion and the operand rows already load.
+struct FusedAcc {
+  uint64_t s0 = 0, s1 = 0, s2 = 0, h = 0, direct = 0;
+  uint32_t hist;                  // shared address of this lane's column of the table
+  uint32_t one, c65536, c128;     // 1, 2^16, 128
+  __device__ __forceinline__ void count(uint32_t bin) {
+    uint32_t addr;
+    asm("mad.lo.u32 %0, %1, %2, %3;" : "=r"(addr) : "r"(bin), "r"(c128), "r"(hist));
+    asm volatile("red.shared.add.u32 [%0], 1;" ::"r"(addr) : "memory");
+  }
+  __device__ __forceinline__ void take(uint64_t v) {
+    direct += v;
+    count((uint32_t)(v >> 40));
+  }
+  __device__ __forceinline__ void block(const uint32_t D[kLimbs]) {
+#pragma unroll
+    for (int q = 0; q < 6; ++q) {
+      const uint32_t a = D[3 * q], b = D[3 * q + 1], c = D[3 * q + 2];
+      s0 = mad_wide(a, one, s0);
+      s1 = mad_wide(b, one, s1);
+      s2 = mad_wide(c, one, s2);
+      uint32_t hb;
+      asm("mul.hi.u32 %0, %1, %2;" : "=r"(hb) : "r"(b), "r"(c65536));
+      h = mad_wide(hb, one, h);
+      count(__byte_perm(b, 0u, 0x4441u));  // bits 40..47 of v_2q: byte 1 of D_3q+1
+      count(__byte_perm(c, 0u, 0x4443u));  // bits 40..47 of v_2q+1: byte 3 of D_3q+2
+    }
+  }
+  __device__ __forceinline__ uint64_t total() const {
+    return direct + s0 + (s1 << 32) + (s2 << 16) - h * ((1ull << 48) - 1ull);
+  }
+};
+
+// Shared memory of the fused CTA besides its static histogram table: the level's matrix
+// and the TcShared word.  With the 32 KB table, a CTA takes 46 KB, so at most four share
+// an SM and their 4 x 128 TMEM columns always fit.
+constexpr int kFusedDynSmem = kBRegion + 1024;
+
+// Largest value of v over the CTA's threads (v >= 0), through one shared word.
+__device__ __forceinline__ int64_t cta_max(int64_t v, unsigned long long* word) {
+  if (threadIdx.x == 0) *word = 0ull;
+  __syncthreads();
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const int64_t u = __shfl_xor_sync(0xFFFFFFFFu, v, o);
+    v = u > v ? u : v;
+  }
+  if ((threadIdx.x & 31) == 0) atomicMax(word, (unsigned long long)v);
+  __syncthreads();
+  return (int64_t)*word;
+}
+
+struct FusedShared {
+  uint64_t bar;                 // product completion
+  uint32_t taddr;               // TMEM base
+  uint32_t abort;               // a wait for the product timed out
+  unsigned long long iters;     // refills of the tile (its streams' largest count)
+};
+
+// The fused draw (exact sum and 256-bin histogram of every stream's doubles, nothing
+// written per value) on one-tile CTAs with the A operand in TMEM.  Same semantics as
+// k_draw_tc<kDrawSumHist>.  The tile refills as many times as its longest stream needs
+// (one CTA-wide maximum at the start); each refill: wait for the product, read the
+// accumulator, form X and write it as the next operand row (every thread, so the
+// warp-wide TMEM accesses stay converged; rows of finished streams keep advancing),
+// one CTA barrier, then thread 0 issues the next product while every thread converts
+// its X to RANLUX numbers and consumes the block.  A wait that gives up (after about
+// 0.3 s) marks the tile aborted; after the next barrier every thread leaves the loop,
+// and the status reports RLXPP_ERR_TIMEOUT.  one = 1 (a launch argument).
+__global__ void __launch_bounds__(kTcRows, 4)
+    k_fused_tc(const DrawArgs a, const __half* __restrict__ bimg, uint32_t one) {
+  extern __shared__ __align__(1024) unsigned char smem[];
+  __shared__ __align__(16) unsigned int hist_s[256 * 32];
+  const int tid = threadIdx.x;
+  {
+    uint4* h4 = reinterpret_cast<uint4*>(hist_s);
+    for (int w = tid; w < 256 * 32 / 4; w += kTcRows) h4[w] = make_uint4(0u, 0u, 0u, 0u);
+  }
+  FusedShared* sh = reinterpret_cast<FusedShared*>(smem + kBRegion);
+  const __half* bmat = tc_bmat(smem);
+  {
+    const uint4* src = reinterpret_cast<const uint4*>(bimg);
+    uint4* dst = reinterpret_cast<uint4*>(tc_bmat(smem));
+    for (int w = tid; w < kBBytes / 16; w += kTcRows) dst[w] = src[w];
+  }
+  if (tid == 0) {
+    mbar_init(&sh->bar, 1);
+    fence_barrier_init();
+    sh->abort = 0;
+  }
+  if (tid < 32) tmem_alloc(&sh->taddr, kTmCols);
+  fence_proxy_async_smem();  // the level's matrix -> visible to the tensor core
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t taddr = sh->taddr;
+  const uint32_t lane_taddr = taddr + ((uint32_t)((tid / 32) * 32) << 16);
+  {
+    // constant columns of every row: 2048 at k = 72 (against 2^-12: the 1/2 bias), 1 at
+    // k = 73 (against the bytes of E), zeros to k = 79
+    const uint32_t cst[4] = {0x3C006800u, 0u, 0u, 0u};
+    tmem_st4(lane_taddr + kTmA + 36, cst);
+  }
+  const uint32_t b0 = smem_addr(bmat);
+
+  const StateView& s = a.s;
+  const uint64_t i = (uint64_t)blockIdx.x * kTcRows + tid;
+  const bool live = i < s.n;
+  int64_t cnt = 0;
+  uint32_t pos = kWords, c = 0, lvl = 0;
+  uint32_t D[kLimbs];
+#pragma unroll
+  for (int k = 0; k < kLimbs; ++k) D[k] = 0;
+  if (live) {
+    cnt = a.counts ? a.counts[i] : a.count_each;
+    const uint32_t meta = s.meta[i];
+    pos = meta_pos(meta);
+    c = meta_carry(meta);
+    lvl = meta_level(meta);
+    load_state_D(s, i, D);
+  }
+  FusedAcc acc;
+  acc.hist = smem_addr(hist_s) + 4u * (uint32_t)(tid & 31);
+  acc.one = one;
+  acc.c65536 = one << 16;
+  acc.c128 = one << 7;
+  int64_t rest = cnt;  // values still to draw
+  if (live && cnt > 0 && pos + 2 <= (uint32_t)kWords) {  // head of the current block
+    const int64_t room = (kWords - pos) / 2;
+    const int64_t hcount = cnt < room ? cnt : room;
+#pragma unroll
+    for (int w = 0; w + 2 <= kWords; ++w) {
+      const int d = w - (int)pos;
+      if (d >= 0 && d % 2 == 0 && d / 2 < hcount) acc.take(bits48_at_word(D, w));
+    }
+    rest -= hcount;
+    pos += (uint32_t)(hcount * 2);
+  }
+  // refills of this stream: full blocks, and a last partial one of `tail` values
+  int64_t left = live && rest > 0 ? (rest + kDoubles - 1) / kDoubles : 0;
+  const uint32_t tail = live ? (uint32_t)(rest % kDoubles) : 0u;
+  const int64_t iters = cta_max(left, &sh->iters);
+  uint32_t X[kLimbs];
+  to_lcg(D, c, X);
+  write_x_tmem(lane_taddr, X);
+  tmem_wait_st();
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (iters > 0 && tid == 0) tc_issue_tm(taddr, b0, &sh->bar);
+  uint32_t phase = 0;
+  bool ok = true, inflight = iters > 0, stored = false;
+  const bool refills = left > 0;
+  for (int64_t it = 0; it < iters; ++it) {
+    bool got = mbar_wait_bounded(&sh->bar, phase);
+    got = __all_sync(0xFFFFFFFFu, got);  // the warp stays converged for the TMEM accesses
+    if (got) {
+      inflight = false;
+      phase ^= 1u;
+      tc_fence_after();
+      uint32_t col[72];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) tmem_ld16(lane_taddr + 16 * q, col + 16 * q);
+      tmem_ld8(lane_taddr + 64, col + 64);
+      tmem_wait_ld();
+      tc_fold_common(col, X);
+      __syncwarp();  // reconverged after the rare fold, before the warp-wide store
+      write_x_tmem(lane_taddr, X);
+      tmem_wait_st();
+    } else {
+      sh->abort = 1u;
+    }
+    // every row written and the accumulator read out: the next product may start
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (sh->abort) {
+      ok = false;
+      break;
+    }
+    if (it + 1 < iters) {
+      if (tid == 0) tc_issue_tm(taddr, b0, &sh->bar);
+      inflight = true;
+    }
+    if (left > 0) {  // this stream's block, while the next product computes
+      to_ranlux(X, D);
+      if (left > 1 || tail == 0) {
+        acc.block(D);
+      } else {
+#pragma unroll
+        for (int j = 0; j < kDoubles; ++j)
+          if (j < (int)tail) acc.take(bits48(D, j));
+      }
+      if (--left == 0) {
+        c = carry_of(X, D);
+        store_state_D(s, i, D);
+        stored = true;
+      }
+    }
+  }
+  if (refills) pos = tail ? 2u * tail : (uint32_t)kWords;
+  if (live && (ok || stored)) s.meta[i] = meta_pack(pos, c, lvl);
+  if (!ok) {
+    if (tid == 0) atomicCAS(s.status, 0, (int)RLXPP_ERR_TIMEOUT);
+  } else if (live) {
+    uint64_t* sums = static_cast<uint64_t*>(a.out);
+    if (sums) sums[i] = a.accumulate_sums ? sums[i] + acc.total() : acc.total();
+  }
+  // release TMEM; a thread that gave up on a product first waits for it once more
+  if (inflight) (void)mbar_wait_bounded(&sh->bar, phase);
+  tc_fence_before();
+  __syncthreads();  // also: every histogram increment is done
+  tc_fence_after();
+  if (tid < 32) tmem_dealloc(taddr, kTmCols);
+  for (int b = tid; b < 256; b += kTcRows) {
+    unsigned long long tot = 0;
+#pragma unroll 8
+    for (int l = 0; l < 32; ++l) tot += hist_s[b * 32 + l];
+    if (tot) atomicAdd(a.hist + b, tot);
+  }
+}
+
 // Emits the unread part of the current block for a value kind (f64 or u24).
 __device__ __forceinline__ void emit_head(bool f64, const BatchArgs& b, const uint32_t D[kLimbs], uint32_t& pos,
                                           int64_t cnt, int64_t base, int64_t& k) {
@@ -1015,6 +1330,14 @@ cudaError_t launch_tc_kind(const DrawArgs& a, const __half* bimg, cudaStream_t s
   return cudaGetLastError();
 }
 
+cudaError_t launch_fused_tc(const DrawArgs& a, const __half* bimg, cudaStream_t st) {
+  cudaError_t e = cudaFuncSetAttribute(k_fused_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, kFusedDynSmem);
+  if (e != cudaSuccess) return e;
+  const unsigned grid = (unsigned)((a.s.n + kTcRows - 1) / kTcRows);
+  k_fused_tc<<<grid, kTcRows, kFusedDynSmem, st>>>(a, bimg, 1u);
+  return cudaGetLastError();
+}
+
 }  // namespace
 
 size_t tc_matrix_bytes() { return kBBytes; }
@@ -1040,7 +1363,7 @@ cudaError_t launch_draw_tc(int kind, const DrawArgs& a, const void* bimg, cudaSt
   switch (kind) {
     case kDrawU24: return launch_tc_kind<kDrawU24>(a, b, st);
     case kDrawF64: return launch_tc_kind<kDrawF64>(a, b, st);
-    case kDrawSumHist: return launch_tc_kind<kDrawSumHist>(a, b, st);
+    case kDrawSumHist: return launch_fused_tc(a, b, st);
     case kDrawF32: return launch_tc_kind<kDrawF32>(a, b, st);
     case kDrawNormal: return launch_tc_kind<kDrawNormal>(a, b, st);
     case kDrawExp: return launch_tc_kind<kDrawExp>(a, b, st);
