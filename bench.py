@@ -497,7 +497,7 @@ def bench_mixed_batch(nat, dev, args):
     tuned = nat.rlxpp_autotune_requests(g.handle, reqs, out_u, out_f)  # picks the kernel too
     tune_s = time.perf_counter() - t
     by_path = {}
-    for name, pid in (("tensor", nat.RLXPP_PATH_TENSOR), ("imad", nat.RLXPP_PATH_IMAD)):
+    for name, pid in (("tensor", nat.RLXPP_PATH_TENSOR), ("imad", nat.RLXPP_PATH_IMAD), ("warp", nat.RLXPP_PATH_WARP)):
         tuning = (tuned[0], tuned[1], pid)
         t = time.perf_counter()
         plan = nat.rlxpp_plan_requests(g.handle, reqs, 0, tuning)

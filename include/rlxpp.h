@@ -192,7 +192,8 @@ rlxpp_status rlxpp_draw_f64_sum_hist(rlxpp_gen* gen, int64_t count_each, uint64_
  * The library splits every request into chunks of at most L refills and starts each
  * chunk from its own block by jump-ahead (X <- A^b X over the power table, Sec. 2.4),
  * so a long request runs on many threads; chunks are ordered longest first and taken
- * from a device work queue by a persistent kernel.  L and the grid are chosen by the
+ * from a device work queue by one persistent kernel for all luxury levels together.
+ * L, the product kernel, the threads per stream and the grid are chosen by the
  * handle's tuner (rlxpp_autotune_requests) or by defaults. */
 #define RLXPP_KIND_U24 0u
 #define RLXPP_KIND_F64 1u
@@ -211,9 +212,13 @@ typedef struct rlxpp_request {
 
 typedef struct rlxpp_tuning {
   uint32_t chunk_blocks;  /* L: refills per chunk, >= 2                                  */
-  uint32_t blocks_per_sm; /* integer kernel: persistent grid = blocks_per_sm x SMs blocks */
-  uint32_t path;          /* RLXPP_PATH_IMAD or RLXPP_PATH_TENSOR (defined below): which
-                             product kernel runs the chunks                             */
+  uint32_t blocks_per_sm; /* persistent grid = blocks_per_sm x SMs blocks, 1..8        */
+  uint32_t path;          /* which kernel runs the chunks (paths defined below):
+                             RLXPP_PATH_IMAD: one thread per chunk, integer pipe;
+                             RLXPP_PATH_TENSOR: one thread per chunk, 128-chunk tiles
+                             on the tensor cores (4 CTAs per SM at most);
+                             RLXPP_PATH_WARP: 32 threads per chunk (one warp, one limb
+                             per lane), for few long chunks                             */
 } rlxpp_tuning;
 
 typedef struct rlxpp_plan rlxpp_plan;
@@ -229,9 +234,12 @@ rlxpp_status rlxpp_plan_requests(rlxpp_gen* gen, const rlxpp_request* reqs, uint
 
 /* Run a plan: out_u24 / out_f64 are device arrays large enough for every request's
  * offset + count of its kind (NULL allowed when no request has that kind).  Issues
- * only kernel launches and one memset on cuda_stream (no allocation, no host
- * synchronisation), so it can be captured in a CUDA graph and replayed; every run
- * recomputes the same values unless RLXPP_REQ_ADVANCE moved the streams. */
+ * one kernel launch on cuda_stream (two with RLXPP_REQ_ADVANCE: a snapshot of the
+ * requested streams' states first), no allocation and no host synchronisation, so it
+ * can be captured in a CUDA graph and replayed; every run recomputes the same values
+ * unless RLXPP_REQ_ADVANCE moved the streams.  The plan's work counters are reset by
+ * the kernel itself at its end, so runs of one plan must not overlap on the device
+ * (run them on one stream, or wait between them). */
 rlxpp_status rlxpp_run_plan(rlxpp_gen* gen, const rlxpp_plan* plan, uint32_t* out_u24,
                             double* out_f64, void* cuda_stream);
 
@@ -248,9 +256,10 @@ rlxpp_status rlxpp_draw_requests(rlxpp_gen* gen, const rlxpp_request* reqs, uint
                                  uint32_t* out_u24, double* out_f64, uint32_t flags,
                                  void* cuda_stream);
 
-/* Tuner: times candidate (product kernel, chunk length, grid) choices on these requests
- * (the integer-pipe and the tensor-core kernel; without
- * RLXPP_REQ_ADVANCE, so the streams do not move; the outputs are overwritten) and
+/* Tuner: times candidate (kernel, chunk length, grid) choices on these requests (the
+ * integer-pipe kernel with one thread or one warp per chunk, and the tensor-core
+ * kernel; without RLXPP_REQ_ADVANCE, so the streams do not move; the outputs are
+ * overwritten) and
  * keeps the fastest for requests of the same shape (log2 buckets of the request count
  * and of the total refills).  The choice is kept in the handle and, when the
  * environment variable RLXPP_TUNE_CACHE names a file, appended there and read back
@@ -284,13 +293,14 @@ rlxpp_status rlxpp_sync(rlxpp_gen* gen, void* cuda_stream);
  * the 72 bytes of X and S_k = sum_j x_j byte_k(R_j) < 2^23, so a tile of 128 streams is
  * one 128 x 80 x 80 product per refill (Sec. 2.1-2.2 computed differently, same
  * result).  It serves the plain draws of single-level handles (a tile's streams share
- * one multiplier; plain draws of multi-level handles use the integer kernel) and every
- * batched request (chunks are grouped by level).
+ * one multiplier; plain draws of multi-level handles use the integer kernel) and the
+ * batched requests of the handle (chunks are grouped by level into tiles).
  * RLXPP_PATH_WARP: the plain draws (u24, f32, f64, fused sum/histogram) with one warp
  * per stream, lane l holding limb l, every multi-limb sum's carries resolved across the
  * warp at once: for few streams, where the latency of one refill counts (a single
- * stream read in order); Gaussian draws and batched requests of such a handle use the
- * integer kernels.  All paths give bit-identical results.  Synchronises the device. */
+ * stream read in order); Gaussian and exponential draws of such a handle use the
+ * integer kernels, and its batched requests (without a tuning) one warp per chunk.  All
+ * paths give bit-identical results.  Synchronises the device. */
 #define RLXPP_PATH_IMAD 0u
 #define RLXPP_PATH_TENSOR 1u
 #define RLXPP_PATH_WARP 2u

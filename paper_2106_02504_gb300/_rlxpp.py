@@ -402,9 +402,8 @@ def _tuning(t, gen=None):
     if isinstance(t, RlxppTuning):
         return ctypes.byref(t)
     t = tuple(t)
-    if len(t) == 2:  # requests run on the integer or the tensor kernel
-        t = t + (RLXPP_PATH_TENSOR if (rlxpp_get_path(gen) if gen else RLXPP_PATH_TENSOR) == RLXPP_PATH_TENSOR
-                 else RLXPP_PATH_IMAD,)
+    if len(t) == 2:  # the handle's path picks the request kernel
+        t = t + (rlxpp_get_path(gen) if gen else RLXPP_PATH_TENSOR,)
     return ctypes.byref(RlxppTuning(*t))
 
 

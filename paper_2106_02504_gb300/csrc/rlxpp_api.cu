@@ -173,15 +173,12 @@ void free_gen(rlxpp_gen* g) {
   cudaFree(g->level_p);
   cudaFree(g->status);
   cudaFree(g->tc_matrix);
+  cudaFree(g->tc_matrix_d);
   cudaFree(g->host_stage);
   if (g->chunk_ready) cudaEventDestroy(g->chunk_ready);
   if (g->host_done) cudaEventDestroy(g->host_done);
   for (auto& e : g->ev)
     if (e) cudaEventDestroy(e);
-  for (auto& e : g->level_event)
-    if (e) cudaEventDestroy(e);
-  for (auto& s : g->level_stream)
-    if (s) cudaStreamDestroy(s);
   if (g->copy_stream) cudaStreamDestroy(g->copy_stream);
   delete g;
 }
@@ -200,7 +197,8 @@ constexpr size_t kChunkBytes = size_t(256) << 20;  // device staging per chunk o
 // level (a tile's streams share the multiplier matrix), one warp per stream for the
 // kinds the warp kernel has, else the integer pipe.
 cudaError_t launch_path(const rlxpp_gen* g, int kind, const DrawArgs& a, cudaStream_t st) {
-  if (g->path == RLXPP_PATH_TENSOR && g->n_levels == 1) return launch_draw_tc(kind, a, g->tc_matrix, st);
+  if (g->path == RLXPP_PATH_TENSOR && g->n_levels == 1)
+    return launch_draw_tc(kind, a, g->tc_matrix, g->tc_matrix_d, st);
   if (g->path == RLXPP_PATH_WARP && warp_draw_supported(kind)) return launch_draw_warp(kind, a, st);
   return launch_draw(kind, a, st);
 }
@@ -410,12 +408,6 @@ rlxpp_status rlxpp_create(uint64_t n_streams, const uint32_t* levels, uint32_t n
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&g->chunk_ready, cudaEventDisableTiming);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&g->host_done, cudaEventDisableTiming);
-  if (n_levels > 1) {  // concurrent per-level launches of the request kernel
-    for (uint32_t l = 0; l < n_levels && e == cudaSuccess; ++l)
-      e = cudaStreamCreateWithFlags(&g->level_stream[l], cudaStreamNonBlocking);
-    for (uint32_t l = 0; l <= n_levels && e == cudaSuccess; ++l)
-      e = cudaEventCreateWithFlags(&g->level_event[l], cudaEventDisableTiming);
-  }
   if (e != cudaSuccess)
     return bail(fail(cuda_status(e), std::string("create: ") + cudaGetErrorString(e)));
   e = cudaMemsetAsync(g->status, 0, sizeof(int), st);
@@ -427,8 +419,13 @@ rlxpp_status rlxpp_create(uint64_t n_streams, const uint32_t* levels, uint32_t n
   if (rlxpp_status s = setup_levels(g, st)) return bail(s);
   {  // tensor-path matrices of every level; the tensor path is the default
     e = dev_malloc(&g->tc_matrix, tc_matrix_bytes() * n_levels);
-    for (uint32_t l = 0; e == cudaSuccess && l < n_levels; ++l)
+    if (e == cudaSuccess) e = dev_malloc(&g->tc_matrix_d, tc_matrix_bytes() * n_levels);
+    for (uint32_t l = 0; e == cudaSuccess && l < n_levels; ++l) {
       e = launch_tc_matrix(g->lux + (size_t)l * 18, static_cast<char*>(g->tc_matrix) + tc_matrix_bytes() * l, st);
+      if (e == cudaSuccess)
+        e = launch_tc_matrix_d(g->lux + (size_t)l * 18, static_cast<char*>(g->tc_matrix_d) + tc_matrix_bytes() * l,
+                               st);
+    }
     if (e != cudaSuccess) return bail(fail(cuda_status(e), std::string("tensor setup: ") + cudaGetErrorString(e)));
     g->path = RLXPP_PATH_TENSOR;
   }

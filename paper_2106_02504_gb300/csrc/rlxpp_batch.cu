@@ -5,11 +5,13 @@
 // stream's sequence.  The host planner cuts it into chunks of at most L refills; chunk
 // j starts from block b_j of that stream, whose LCG state is A^(b_j) X (fixed-window
 // exponentiation over the power table, Sec. 2.4: one product per non-zero 4-bit digit
-// of b_j), so every chunk is independent.  Chunks are sorted longest first and taken
-// 32 at a time by the warps of a persistent kernel from a device counter; each thread
-// then runs the same refill loop as the plain draw kernels.  Reading the stream states
-// through a snapshot taken at the start of the run keeps chunks independent of the
-// write-back of the final states.
+// of b_j), so every chunk is independent.  Chunks are sorted by level and longest first
+// and taken from a device counter by one persistent kernel for every level: 32 at a
+// time by the warps of the integer kernel (each thread then runs the same refill loop as
+// the plain draw kernels), one at a time by the warps of the warp-cooperative kernel,
+// or 128 at a time (a tile of one level) by the CTAs of the tensor-core kernel.  When
+// the run writes final states back, the chunks read the stream states through a
+// snapshot taken at its start, which keeps them independent of the write-back.
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
@@ -46,17 +48,16 @@ __global__ void k_snapshot(BatchArgs b) {
   b.snap_meta[r] = b.s.meta[st];
 }
 
+// The multipliers of every level, as one kernel argument.
+struct LuxTable {
+  Lux L[RLXPP_MAX_LEVELS];
+};
+
 __device__ __forceinline__ void run_item(const BatchArgs& b, const Lux& L, const Item& it) {
   const uint32_t r = it.req;
-  const uint32_t meta = b.snap_meta[r];
+  uint32_t D[kLimbs], meta;
+  request_state(b, r, D, meta);
   const uint32_t lvl = meta_level(meta);
-  uint32_t D[kLimbs];
-#pragma unroll
-  for (int k = 0; k < 9; ++k) {
-    const uint64_t v = b.snap_D[(uint64_t)k * b.n_reqs + r];
-    D[2 * k] = (uint32_t)v;
-    D[2 * k + 1] = (uint32_t)(v >> 32);
-  }
   uint32_t c = meta_carry(meta);
   if (it.jump) {  // X <- A^jump X
     uint32_t X[kLimbs];
@@ -66,7 +67,6 @@ __device__ __forceinline__ void run_item(const BatchArgs& b, const Lux& L, const
     to_ranlux(X, D);
     c = carry_of(X, D);
   }
-  // every chunk of this launch belongs to one luxury level: A stays in the constant bank
   auto A = [&](int k) { return L.a[k]; };
   auto AS = [&](int k) { return L.as[k]; };
   uint32_t pos = (it.info >> 8) & 0xFFu;
@@ -87,19 +87,42 @@ __device__ __forceinline__ void run_item(const BatchArgs& b, const Lux& L, const
   }
 }
 
-// Persistent, one luxury level per launch (items[0..n_items) of that level): each warp
-// takes the next 32 chunks of the longest-first list from the level's counter.
-__global__ void __launch_bounds__(kReqBlock, RLXPP_REQ_MIN_BLOCKS) k_requests(BatchArgs b, const Lux L, const Item* __restrict__ items,
-                                                           uint64_t n_items, unsigned long long* counter) {
+// Persistent, every level in one launch: each warp takes the next 32 chunks of the
+// list from the counter.  With one level (Multi = false) its multiplier stays in the
+// kernel argument (the constant bank); with several, the levels' multipliers are copied
+// into shared memory and each chunk reads its own level's (lanes of one level read the
+// same words, and different levels' words fall in different banks).
+template <bool Multi>
+__global__ void __launch_bounds__(kReqBlock, RLXPP_REQ_MIN_BLOCKS)
+    k_requests(BatchArgs b, const LuxTable lt, uint32_t n_levels, const Item* __restrict__ items, uint64_t n_items,
+               WorkCounters* wc) {
+  __shared__ Lux lux_s[Multi ? RLXPP_MAX_LEVELS : 1];
+  if (Multi) {
+    const uint32_t* src = reinterpret_cast<const uint32_t*>(lt.L);
+    uint32_t* dst = reinterpret_cast<uint32_t*>(lux_s);
+    for (uint32_t w = threadIdx.x; w < n_levels * (uint32_t)(sizeof(Lux) / 4); w += blockDim.x) dst[w] = src[w];
+    __syncthreads();
+  }
   const int lane = threadIdx.x & 31;
   while (true) {
     unsigned long long base = 0;
-    if (lane == 0) base = atomicAdd(counter, 32ull);
+    if (lane == 0) base = atomicAdd(&wc->next, 32ull);
     base = __shfl_sync(0xFFFFFFFFu, base, 0);
     if (base >= n_items) break;
     const uint64_t idx = base + (uint64_t)lane;
-    if (idx < n_items) run_item(b, L, items[idx]);
+    if (idx < n_items) {
+      const Item it = items[idx];
+      if (Multi) {
+        uint32_t meta;
+        if (b.snap_D) meta = b.snap_meta[it.req];
+        else meta = b.s.meta[b.req_stream[it.req]];
+        run_item(b, lux_s[meta_level(meta)], it);
+      } else {
+        run_item(b, lt.L[0], it);
+      }
+    }
   }
+  finish_cta(wc);
 }
 
 uint32_t log2_floor(uint64_t v) {
@@ -158,7 +181,7 @@ void load_tune_cache(rlxpp_gen* g) {
     if (a == std::string::npos || line.compare(0, a, key) != 0) continue;
     unsigned sig = 0, L = 0, bps = 0, path = 0;
     if (std::sscanf(line.c_str() + a + 1, "%u|%u|%u|%u", &sig, &L, &bps, &path) == 4 && L >= 2 && bps >= 1 &&
-        bps <= 8 && path <= 1)
+        bps <= 8 && path <= RLXPP_PATH_WARP)
       g->tuned[sig] = rlxpp_tuning{L, bps, path};  // later lines win
   }
 }
@@ -178,14 +201,17 @@ struct rlxpp_plan {
   uint64_t* req_stream = nullptr;  // [n_reqs] stream of each request
   uint64_t* snap_D = nullptr;
   uint32_t* snap_meta = nullptr;
-  unsigned long long* counter = nullptr;
+  WorkCounters* wc = nullptr;      // the request kernel's counters (zero between runs)
+  TcTile* tiles = nullptr;         // tensor path: the tile table, longest first
+  uint64_t n_tiles = 0;
+  uint32_t levels_used = 0;        // levels with at least one item
 };
 
 namespace {
 
 void free_plan(rlxpp_plan* p, cudaStream_t st, bool async) {
   if (!p) return;
-  void* ptrs[] = {p->items, p->req_stream, p->snap_D, p->snap_meta, p->counter};
+  void* ptrs[] = {p->items, p->req_stream, p->snap_D, p->snap_meta, p->wc, p->tiles};
   for (void* q : ptrs)
     if (q) async ? cudaFreeAsync(q, st) : cudaFree(q);
   delete p;
@@ -243,11 +269,11 @@ rlxpp_status plan_impl(rlxpp_gen* g, const rlxpp_request* reqs, uint64_t n_reqs,
       if (L_host > L) L = L_host;
       uint32_t p2 = 4;
       while (p2 < L && p2 < 256) p2 <<= 1;
-      t = rlxpp_tuning{p2, 4, g->path == RLXPP_PATH_TENSOR ? RLXPP_PATH_TENSOR : RLXPP_PATH_IMAD};
+      t = rlxpp_tuning{p2, 4, g->path};  // the handle's path: its request kernel
     }
   }
   if (t.chunk_blocks < 2 || t.blocks_per_sm < 1 || t.blocks_per_sm > 8 ||
-      (t.path != RLXPP_PATH_IMAD && t.path != RLXPP_PATH_TENSOR))
+      (t.path != RLXPP_PATH_IMAD && t.path != RLXPP_PATH_TENSOR && t.path != RLXPP_PATH_WARP))
     return set_last_error(RLXPP_ERR_INVALID, "tuning needs chunk_blocks >= 2, 1..8 blocks per SM and a path");
   const uint64_t L = t.chunk_blocks;
   // chunks
@@ -341,6 +367,22 @@ rlxpp_status plan_impl(rlxpp_gen* g, const rlxpp_request* reqs, uint64_t n_reqs,
     }
     p->level_begin[g->n_levels] = items.size();
   }
+  // tensor path: tiles of up to 128 consecutive items of one level, ordered by their
+  // first (longest) item's refills, longest first across levels
+  std::vector<TcTile> tiles;
+  if (t.path == RLXPP_PATH_TENSOR) {
+    std::vector<std::pair<uint64_t, TcTile>> keyed;
+    for (uint32_t l = 0; l < g->n_levels; ++l)
+      for (uint64_t a = p->level_begin[l]; a < p->level_begin[l + 1]; a += 128) {
+        const uint64_t n = std::min<uint64_t>(128, p->level_begin[l + 1] - a);
+        keyed.push_back({refills_of(items[a]), TcTile{a, (uint32_t)n, l}});
+      }
+    std::stable_sort(keyed.begin(), keyed.end(), [](const auto& x, const auto& y) { return x.first > y.first; });
+    tiles.reserve(keyed.size());
+    for (const auto& k : keyed) tiles.push_back(k.second);
+  }
+  for (uint32_t l = 0; l < g->n_levels; ++l) p->levels_used += p->level_begin[l + 1] > p->level_begin[l];
+  p->n_tiles = tiles.size();
   p->gen = g;
   p->n_items = items.size();
   p->n_reqs = n_reqs;
@@ -360,13 +402,19 @@ rlxpp_status plan_impl(rlxpp_gen* g, const rlxpp_request* reqs, uint64_t n_reqs,
   };
   cudaError_t e = alloc((void**)&p->items, sizeof(Item) * std::max<size_t>(items.size(), 1));
   if (e == cudaSuccess) e = alloc((void**)&p->req_stream, sizeof(uint64_t) * nr);
-  if (e == cudaSuccess) e = alloc((void**)&p->snap_D, sizeof(uint64_t) * 9 * nr);
-  if (e == cudaSuccess) e = alloc((void**)&p->snap_meta, sizeof(uint32_t) * nr);
-  if (e == cudaSuccess) e = alloc((void**)&p->counter, sizeof(unsigned long long) * RLXPP_MAX_LEVELS);
+  if (flags & RLXPP_REQ_ADVANCE) {  // runs that write states back read a snapshot
+    if (e == cudaSuccess) e = alloc((void**)&p->snap_D, sizeof(uint64_t) * 9 * nr);
+    if (e == cudaSuccess) e = alloc((void**)&p->snap_meta, sizeof(uint32_t) * nr);
+  }
+  if (e == cudaSuccess) e = alloc((void**)&p->wc, sizeof(WorkCounters));
+  if (e == cudaSuccess)
+    e = stream_ordered ? cudaMemsetAsync(p->wc, 0, sizeof(WorkCounters), st) : cudaMemset(p->wc, 0, sizeof(WorkCounters));
+  if (e == cudaSuccess && !tiles.empty()) e = alloc((void**)&p->tiles, sizeof(TcTile) * tiles.size());
   std::vector<uint64_t> rs(nr, 0);
   for (uint64_t r = 0; r < n_reqs; ++r) rs[r] = reqs[r].stream;
   if (e == cudaSuccess && !items.empty()) e = upload(p->items, items.data(), sizeof(Item) * items.size());
   if (e == cudaSuccess) e = upload(p->req_stream, rs.data(), sizeof(uint64_t) * rs.size());
+  if (e == cudaSuccess && !tiles.empty()) e = upload(p->tiles, tiles.data(), sizeof(TcTile) * tiles.size());
   if (e != cudaSuccess) {
     free_plan(p, st, stream_ordered);
     return set_last_error(e == cudaErrorMemoryAllocation ? RLXPP_ERR_NOMEM : RLXPP_ERR_CUDA,
@@ -384,49 +432,37 @@ rlxpp_status run_impl(rlxpp_gen* g, const rlxpp_plan* p, uint32_t* out_u24, doub
   if (p->n_items == 0) return RLXPP_OK;
   BatchArgs b{};
   b.req_stream = p->req_stream;
-  b.snap_D = p->snap_D;
+  b.snap_D = p->snap_D;  // null unless the run writes states back
   b.snap_meta = p->snap_meta;
   b.n_reqs = p->n_reqs;
   b.s = g->view();
   b.out_u24 = out_u24;
   b.out_f64 = reinterpret_cast<uint64_t*>(out_f64);
   b.advance = (p->flags & RLXPP_REQ_ADVANCE) ? 1 : 0;
-  cudaError_t e = cudaMemsetAsync(p->counter, 0, sizeof(unsigned long long) * RLXPP_MAX_LEVELS, st);
-  if (e == cudaSuccess) {
+  cudaError_t e = cudaSuccess;
+  if (p->snap_D) {
     k_snapshot<<<(unsigned)((p->n_reqs + 255) / 256), 256, 0, st>>>(b);
     e = cudaGetLastError();
   }
+  // one launch over every level (the work counters reset themselves at its end)
   const unsigned grid = (unsigned)std::max(1, g->sms) * p->tuning.blocks_per_sm;
-  uint32_t busy = 0;
-  for (uint32_t l = 0; l < g->n_levels; ++l) busy += p->level_begin[l + 1] > p->level_begin[l];
-  const bool tensor = p->tuning.path == RLXPP_PATH_TENSOR && g->tc_matrix;
-  auto launch_level = [&](uint32_t l, uint64_t n, cudaStream_t s) {
-    const Item* it = p->items + p->level_begin[l];
-    if (tensor)
-      return launch_requests_tc(b, it, n, static_cast<const char*>(g->tc_matrix) + tc_matrix_bytes() * l, s);
-    k_requests<<<grid, kReqBlock, 0, s>>>(b, g->lux_host[l], it, n, p->counter + l);
-    return cudaGetLastError();
-  };
-  if (busy <= 1) {
-    for (uint32_t l = 0; e == cudaSuccess && l < g->n_levels; ++l) {
-      const uint64_t n = p->level_begin[l + 1] - p->level_begin[l];
-      if (n == 0) continue;
-      e = launch_level(l, n, st);
-    }
-  } else {
-    // one launch per level, concurrently on the handle's side streams (fork / join with
-    // events, which stream capture records as graph dependencies)
-    cudaEvent_t fork = g->level_event[g->n_levels];
-    e = cudaEventRecord(fork, st);
-    for (uint32_t l = 0; e == cudaSuccess && l < g->n_levels; ++l) {
-      const uint64_t n = p->level_begin[l + 1] - p->level_begin[l];
-      if (n == 0) continue;
-      cudaStream_t ls = g->level_stream[l];
-      e = cudaStreamWaitEvent(ls, fork, 0);
-      if (e != cudaSuccess) break;
-      e = launch_level(l, n, ls);
-      if (e == cudaSuccess) e = cudaEventRecord(g->level_event[l], ls);
-      if (e == cudaSuccess) e = cudaStreamWaitEvent(st, g->level_event[l], 0);
+  if (e == cudaSuccess) {
+    if (p->tuning.path == RLXPP_PATH_TENSOR && g->tc_matrix && p->tiles) {
+      e = launch_requests_tc(b, p->items, p->tiles, p->n_tiles, g->tc_matrix, p->wc, grid, st);
+    } else if (p->tuning.path == RLXPP_PATH_WARP) {
+      e = launch_requests_warp(b, p->items, p->n_items, p->wc, grid, st);
+    } else {
+      LuxTable lt{};
+      for (uint32_t l = 0; l < g->n_levels; ++l) lt.L[l] = g->lux_host[l];
+      if (p->levels_used > 1) {
+        k_requests<true><<<grid, kReqBlock, 0, st>>>(b, lt, g->n_levels, p->items, p->n_items, p->wc);
+      } else {
+        uint32_t l = 0;
+        while (l + 1 < g->n_levels && p->level_begin[l + 1] == p->level_begin[l]) ++l;  // the one level used
+        lt.L[0] = g->lux_host[l];
+        k_requests<false><<<grid, kReqBlock, 0, st>>>(b, lt, 1, p->items, p->n_items, p->wc);
+      }
+      e = cudaGetLastError();
     }
   }
   if (e != cudaSuccess) return set_last_error(RLXPP_ERR_CUDA, (std::string("run plan: ") + cudaGetErrorString(e)).c_str());
@@ -488,7 +524,9 @@ rlxpp_status rlxpp_autotune_requests(rlxpp_gen* gen, const rlxpp_request* reqs, 
   const uint64_t threads = (uint64_t)std::max(1, gen->sms) * 4 * kReqBlock;
   uint32_t L0 = 4;
   while (L0 < 1024 && (uint64_t)L0 * threads * 64 < total) L0 <<= 1;
-  for (uint32_t path = 0; path < 2 && status == RLXPP_OK; ++path)
+  // the product (integer pipe or tensor cores) and the threads per stream (one, or a
+  // warp of 32 on the integer pipe), the chunk length, and the persistent grid
+  for (uint32_t path = 0; path < 3 && status == RLXPP_OK; ++path)
   for (uint32_t L = L0; L <= 1024 && status == RLXPP_OK; L <<= 1) {
     if (path == RLXPP_PATH_TENSOR && !gen->tc_matrix) break;
     if (L > L0 && L / 2 >= std::max<uint64_t>(longest, 4)) break;  // longer chunks change nothing
@@ -496,9 +534,11 @@ rlxpp_status rlxpp_autotune_requests(rlxpp_gen* gen, const rlxpp_request* reqs, 
     rlxpp_plan* p = nullptr;
     status = plan_impl(gen, reqs, n_reqs, 0, &t, &p);
     if (status != RLXPP_OK) break;
-    // the integer kernel's grid is chosen at run time; the tensor kernel has one tile per CTA
-    const uint32_t bps_hi = path == RLXPP_PATH_TENSOR ? 2 : 4;
-    for (uint32_t bps = 2; bps <= bps_hi && status == RLXPP_OK; ++bps) {
+    // resident CTAs per SM: the tensor kernel's 48 KB of shared memory and 128 TMEM
+    // columns allow four, the others are bounded by registers
+    const uint32_t bps_lo = path == RLXPP_PATH_WARP ? 4 : 2;
+    const uint32_t bps_hi = path == RLXPP_PATH_WARP ? 8 : 4;
+    for (uint32_t bps = bps_lo; bps <= bps_hi && status == RLXPP_OK; bps += (path == RLXPP_PATH_WARP ? 2 : 1)) {
       p->tuning.blocks_per_sm = bps;
       float ms = 1e30f;
       for (int rep = 0; rep < 3 && status == RLXPP_OK; ++rep) {  // first run warms up

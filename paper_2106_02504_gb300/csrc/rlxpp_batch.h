@@ -17,7 +17,7 @@ struct Item {       // one chunk (32 bytes)
 
 struct BatchArgs {
   const uint64_t* req_stream;  // [n_reqs]
-  uint64_t* snap_D;            // [9][n_reqs]
+  uint64_t* snap_D;            // [9][n_reqs], or null: read the resident state directly
   uint32_t* snap_meta;         // [n_reqs]
   uint64_t n_reqs;
   StateView s;                 // resident states (final states are written back here)
@@ -26,8 +26,67 @@ struct BatchArgs {
   int advance;
 };
 
-// Tensor-core request kernel: items[0..n) of one luxury level whose matrix is bimg.
-cudaError_t launch_requests_tc(const BatchArgs& b, const Item* items, uint64_t n, const void* bimg,
-                               cudaStream_t st);
+// One tile of the tensor-core request kernel: up to 128 consecutive items of one luxury
+// level (items[first .. first + n)).
+struct TcTile {
+  uint64_t first;
+  uint32_t n;
+  uint32_t level;
+};
+
+// Work counters of a persistent request kernel: [0] the next item or tile to take,
+// [1] CTAs that have finished.  Zero before a launch; the last CTA to finish sets both
+// back to zero, so that the next launch (a replayed graph included) needs no reset.
+struct WorkCounters {
+  unsigned long long next, done;
+};
+
+#ifdef __CUDACC__
+// The state (24 numbers as 18 limbs, and the meta word) of request r's stream at the
+// start of the run: from the snapshot when the run writes states back (the final state
+// of a stream must not change what its other chunks read), else the resident state.
+__device__ __forceinline__ void request_state(const BatchArgs& b, uint32_t r, uint32_t D[18], uint32_t& meta) {
+  if (b.snap_D) {
+    meta = b.snap_meta[r];
+#pragma unroll
+    for (int q = 0; q < 9; ++q) {
+      const uint64_t v = b.snap_D[(uint64_t)q * b.n_reqs + r];
+      D[2 * q] = (uint32_t)v;
+      D[2 * q + 1] = (uint32_t)(v >> 32);
+    }
+  } else {
+    const uint64_t st = b.req_stream[r];
+    meta = b.s.meta[st];
+#pragma unroll
+    for (int q = 0; q < 9; ++q) {
+      const uint64_t v = b.s.D[(uint64_t)q * b.s.stride + st];
+      D[2 * q] = (uint32_t)v;
+      D[2 * q + 1] = (uint32_t)(v >> 32);
+    }
+  }
+}
+
+// End of a CTA of a persistent request kernel (after its last use of the counters):
+// the last one to finish resets them.
+__device__ __forceinline__ void finish_cta(WorkCounters* wc) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    if (atomicAdd(&wc->done, 1ull) == (unsigned long long)(gridDim.x - 1)) {
+      wc->next = 0ull;
+      wc->done = 0ull;
+    }
+  }
+}
+#endif
+
+// Tensor-core request kernel: persistent CTAs over the tile table, every level in one
+// launch; bimg holds the levels' matrices one after the other.
+cudaError_t launch_requests_tc(const BatchArgs& b, const Item* items, const TcTile* tiles, uint64_t n_tiles,
+                               const void* bimg, WorkCounters* wc, unsigned grid, cudaStream_t st);
+// Warp-cooperative request kernel (one warp per chunk; rlxpp_warp.cu): every level in one
+// launch, the level's multiplier read from the state view's table.
+cudaError_t launch_requests_warp(const BatchArgs& b, const Item* items, uint64_t n_items, WorkCounters* wc,
+                                 unsigned grid, cudaStream_t st);
 
 }  // namespace rlxpp

@@ -80,7 +80,9 @@ cudaError_t launch_import(const StateView& s, const uint32_t* level_p, uint32_t 
 // tensor-core refill (rlxpp_tensor.cu)
 size_t tc_matrix_bytes();
 cudaError_t launch_tc_matrix(const uint32_t* lux18, void* bimg, cudaStream_t st);
-cudaError_t launch_draw_tc(int kind, const DrawArgs& a, const void* bimg, cudaStream_t st);
+// the matrix for operand rows that hold (D, c) instead of X, with the block-sum columns
+cudaError_t launch_tc_matrix_d(const uint32_t* lux18, void* bimg, cudaStream_t st);
+cudaError_t launch_draw_tc(int kind, const DrawArgs& a, const void* bimg, const void* bimg_d, cudaStream_t st);
 cudaError_t launch_tc_mulmod(const void* bimg, const uint64_t* x, uint64_t* out, uint64_t n, int* status,
                              cudaStream_t st, bool issue = true);
 // True when rlxpp_test_fail_alloc asked for this device allocation to fail (the caller
@@ -137,11 +139,10 @@ struct rlxpp_gen {
   int sms = 0;                         // multiprocessors of the device
   std::map<uint32_t, rlxpp_tuning> tuned;  // request-shape signature -> tuner choice
   std::vector<uint8_t> level_host;         // host copy of every stream's level index
-  cudaStream_t level_stream[RLXPP_MAX_LEVELS] = {};  // side streams: one per luxury level
-  cudaEvent_t level_event[RLXPP_MAX_LEVELS + 1] = {};  // fork (last) and per-level joins
   bool level_host_stale = false;           // set_state may have changed levels
   uint32_t path = 0;                       // RLXPP_PATH_IMAD or RLXPP_PATH_TENSOR
-  void* tc_matrix = nullptr;               // [n_levels] tensor-path matrices (on first use)
+  void* tc_matrix = nullptr;               // [n_levels] tensor-path matrices
+  void* tc_matrix_d = nullptr;             // [n_levels] the same for (D, c) operand rows
   rlxpp::StateView view() const { return rlxpp::StateView{D, meta, n, n, lux, table, status}; }
 };
 

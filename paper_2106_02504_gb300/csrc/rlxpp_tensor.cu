@@ -426,15 +426,18 @@ __device__ __forceinline__ TcShared* tc_sh0(unsigned char* smem) {
   return reinterpret_cast<TcShared*>(smem + kBRegion + kTileBytes);
 }
 
-// Setup of a CTA of `groups` tile-groups: the level's matrix into shared memory, the
-// constant chunk 9 of every tile row (2048 and 1 at k = 72, 73, zeros after), one
-// mbarrier per group and the CTA's TMEM columns.  Ends with a CTA barrier.
+// Setup of a CTA of `groups` tile-groups: the level's matrix into shared memory (unless
+// bimg is null: the kernel loads it later), the constant chunk 9 of every tile row
+// (2048 and 1 at k = 72, 73, zeros after), one mbarrier per group and the CTA's TMEM
+// columns.  Ends with a CTA barrier.
 __device__ __forceinline__ void tc_setup(unsigned char* smem, const TcGroup& G, const __half* __restrict__ bimg,
                                          int groups) {
   const int tid = threadIdx.x;
-  const uint4* src = reinterpret_cast<const uint4*>(bimg);
-  uint4* dst = reinterpret_cast<uint4*>(tc_bmat(smem));
-  for (int i = tid; i < kBBytes / 16; i += groups * kTcRows) dst[i] = src[i];
+  if (bimg) {
+    const uint4* src = reinterpret_cast<const uint4*>(bimg);
+    uint4* dst = reinterpret_cast<uint4*>(tc_bmat(smem));
+    for (int i = tid; i < kBBytes / 16; i += groups * kTcRows) dst[i] = src[i];
+  }
   {
     __half* row9 = G.tile + tc_off(G.t, 72);
     row9[0] = __float2half(2048.f);
@@ -758,20 +761,6 @@ constexpr uint32_t kTmA = kTcN;    // first A column
 constexpr uint32_t kTmCols = 128;  // TMEM columns of such a CTA
 static_assert(kTmA + kTcK / 2 <= kTmCols, "A operand after the accumulator");
 
-// X (18 limbs) -> its 72 bytes as fp16 subnormals (the pairs of one 32-bit word per two
-// bytes, as write_x_row forms them) into this thread's lane of the A columns.  Every
-// thread of the warp calls it (tcgen05.st is warp-wide).
-__device__ __forceinline__ void write_x_tmem(uint32_t lane_taddr, const uint32_t X[kLimbs]) {
-  uint32_t w[36];
-#pragma unroll
-  for (int c = 0; c < kLimbs; ++c) {
-    w[2 * c] = __byte_perm(X[c], 0u, 0x4140u);
-    w[2 * c + 1] = __byte_perm(X[c], 0u, 0x4342u);
-  }
-  tmem_st32(lane_taddr + kTmA, w);
-  tmem_st4(lane_taddr + kTmA + 32, w + 32);
-}
-
 // One thread: the five K = 16 products (A from TMEM, the level's matrix from shared
 // memory) into the accumulator, committed to the CTA's mbarrier.
 __device__ __forceinline__ void tc_issue_tm(uint32_t taddr, uint32_t b0, uint64_t* bar) {
@@ -802,55 +791,57 @@ __device__ __forceinline__ void tc_fold_common(const uint32_t col[72], uint32_t 
   }
 }
 
-// The consumer of the fused draw on this kernel.  A full block's twelve 48-bit values
-// v_2q = D_3q + 2^32 lo16(D_3q+1) and v_2q+1 = hi16(D_3q+1) + 2^16 D_3q+2 (32-bit limbs
-// D_i of the block) add up to
-//   S0 + 2^32 S1 + 2^16 S2 - (2^48 - 1) H,
-// where S0, S1, S2 sum the limbs 3q, 3q + 1, 3q + 2 and H sums hi16(D_3q+1); these are
-// kept as 64-bit multiply-adds (hi16 itself as a multiply-high by 2^16) and combined
-// once at the end, modulo 2^64, which is exact because the stream's total is below
-// 2^64.  Values of partial blocks are added as they are.  The histogram of the top 8
-// bits of every value is counted per lane: bin b of lane l is word 32 b + l of the
-// tile's table, so the increments of a warp fall in 32 different banks; a bin is one
-// byte permute, its address one multiply-add.  The multipliers 1, 2^16 and 128 are
-// run-time values (derived from a launch argument), so that the compiler keeps these
-// steps on the FMA pipe rather than turning them into shifts and adds on the ALU pipe,
-// which the conversion and the operand rows already load.
+// The consumer of the fused draw on this kernel: an exact sum and a 256-bin histogram of
+// the top 8 bits of every 48-bit value.  The sums of full blocks come from the tensor
+// core: the product that refills a block also sums its bytes by position within a
+// 48-bit value (columns 72..77, see k_tc_matrix_d), so a block's values add up to
+// sum_r 2^(8r) P_r.  The six column bit patterns 0x3F000000 + P_r are accumulated as
+// 32-bit multiply-adds by a run-time 1 (FMA pipe) and flushed into the 64-bit total at
+// least every 2^20 blocks, while sum P_r < 2^32 is certain (P_r <= 12 * 255).  Values of
+// the head and of the stream's last block are added one by one.  The histogram is
+// counted per lane: bin b of lane l is word 32 b + l of the tile's table, so the
+// increments of a warp fall in 32 different banks; a bin is one byte permute, its
+// address one multiply-add by a run-time 128.
+constexpr int64_t kFusedFlush = 1 << 20;  // blocks between flushes of the column sums
+
 struct FusedAcc {
-  uint64_t s0 = 0, s1 = 0, s2 = 0, h = 0, direct = 0;
-  uint32_t hist;                  // shared address of this lane's column of the table
-  uint32_t one, c65536, c128;     // 1, 2^16, 128
+  uint64_t total = 0;          // flushed column sums and single values
+  uint32_t t[6] = {0, 0, 0, 0, 0, 0};
+  uint32_t hist;               // shared address of this lane's column of the table
+  uint32_t one, c128;          // 1 and 128, not known to the compiler
   __device__ __forceinline__ void count(uint32_t bin) {
     uint32_t addr;
     asm("mad.lo.u32 %0, %1, %2, %3;" : "=r"(addr) : "r"(bin), "r"(c128), "r"(hist));
     asm volatile("red.shared.add.u32 [%0], 1;" ::"r"(addr) : "memory");
   }
   __device__ __forceinline__ void take(uint64_t v) {
-    direct += v;
+    total += v;
     count((uint32_t)(v >> 40));
   }
-  __device__ __forceinline__ void block(const uint32_t D[kLimbs]) {
+  __device__ __forceinline__ void hist_block(const uint32_t D[kLimbs]) {
 #pragma unroll
     for (int q = 0; q < 6; ++q) {
-      const uint32_t a = D[3 * q], b = D[3 * q + 1], c = D[3 * q + 2];
-      s0 = mad_wide(a, one, s0);
-      s1 = mad_wide(b, one, s1);
-      s2 = mad_wide(c, one, s2);
-      uint32_t hb;
-      asm("mul.hi.u32 %0, %1, %2;" : "=r"(hb) : "r"(b), "r"(c65536));
-      h = mad_wide(hb, one, h);
-      count(__byte_perm(b, 0u, 0x4441u));  // bits 40..47 of v_2q: byte 1 of D_3q+1
-      count(__byte_perm(c, 0u, 0x4443u));  // bits 40..47 of v_2q+1: byte 3 of D_3q+2
+      count(__byte_perm(D[3 * q + 1], 0u, 0x4441u));  // bits 40..47 of v_2q: byte 1 of D_3q+1
+      count(__byte_perm(D[3 * q + 2], 0u, 0x4443u));  // bits 40..47 of v_2q+1: byte 3 of D_3q+2
     }
   }
-  __device__ __forceinline__ uint64_t total() const {
-    return direct + s0 + (s1 << 32) + (s2 << 16) - h * ((1ull << 48) - 1ull);
+  __device__ __forceinline__ void columns(const uint32_t s[6]) {
+#pragma unroll
+    for (int r = 0; r < 6; ++r) asm("mad.lo.u32 %0, %1, %2, %0;" : "+r"(t[r]) : "r"(s[r]), "r"(one));
+  }
+  // n blocks' column sums into the total (each column carried the 1/2 bias 0x3F000000)
+  __device__ __forceinline__ void flush(uint32_t n) {
+#pragma unroll
+    for (int r = 0; r < 6; ++r) {
+      total += (uint64_t)(t[r] - n * 0x3F000000u) << (8 * r);
+      t[r] = 0;
+    }
   }
 };
 
 // Shared memory of the fused CTA besides its static histogram table: the level's matrix
-// and the TcShared word.  With the 32 KB table, a CTA takes 46 KB, so at most four share
-// an SM and their 4 x 128 TMEM columns always fit.
+// and the FusedShared words.  With the 32 KB table, a CTA takes 46 KB, so at most four
+// share an SM and their 4 x 128 TMEM columns always fit.
 constexpr int kFusedDynSmem = kBRegion + 1024;
 
 // Largest value of v over the CTA's threads (v >= 0), through one shared word.
@@ -867,6 +858,26 @@ __device__ __forceinline__ int64_t cta_max(int64_t v, unsigned long long* word) 
   return (int64_t)*word;
 }
 
+// D (18 limbs) and its borrow c -> the operand row of k_tc_matrix_d: D's 72 bytes as
+// fp16 subnormals, then 2048 and 1 (the bias and correction rows), c, zeros.  Every
+// thread of the warp calls it (tcgen05.st is warp-wide).
+__device__ __forceinline__ void write_d_tmem(uint32_t lane_taddr, const uint32_t D[kLimbs], uint32_t c) {
+  uint32_t w[40];
+#pragma unroll
+  for (int k = 0; k < kLimbs; ++k) {
+    w[2 * k] = __byte_perm(D[k], 0u, 0x4140u);
+    w[2 * k + 1] = __byte_perm(D[k], 0u, 0x4342u);
+  }
+  w[36] = 0x3C006800u;
+  w[37] = c;
+  w[38] = 0u;
+  w[39] = 0u;
+  tmem_st32(lane_taddr + kTmA, w);
+  asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};" ::"r"(lane_taddr + kTmA + 32),
+               "r"(w[32]), "r"(w[33]), "r"(w[34]), "r"(w[35]), "r"(w[36]), "r"(w[37]), "r"(w[38]), "r"(w[39])
+               : "memory");
+}
+
 struct FusedShared {
   uint64_t bar;                 // product completion
   uint32_t taddr;               // TMEM base
@@ -876,16 +887,19 @@ struct FusedShared {
 
 // The fused draw (exact sum and 256-bin histogram of every stream's doubles, nothing
 // written per value) on one-tile CTAs with the A operand in TMEM.  Same semantics as
-// k_draw_tc<kDrawSumHist>.  The tile refills as many times as its longest stream needs
-// (one CTA-wide maximum at the start); each refill: wait for the product, read the
-// accumulator, form X and write it as the next operand row (every thread, so the
-// warp-wide TMEM accesses stay converged; rows of finished streams keep advancing),
-// one CTA barrier, then thread 0 issues the next product while every thread converts
-// its X to RANLUX numbers and consumes the block.  A wait that gives up (after about
-// 0.3 s) marks the tile aborted; after the next barrier every thread leaves the loop,
-// and the status reports RLXPP_ERR_TIMEOUT.  one = 1 (a launch argument).
+// k_draw_tc<kDrawSumHist>.  The operand rows hold each stream's RANLUX numbers D and
+// borrow c, and the level's matrix is k_tc_matrix_d's, so a product yields the next LCG
+// state X and the byte sums of the block it was given.  The tile refills as many times
+// as its longest stream needs (one CTA-wide maximum at the start); each refill: wait for
+// the product, read the accumulator, form X, convert it to D and c and write them as the
+// next operand row (every thread, so that the warp-wide TMEM accesses stay converged;
+// rows of finished streams keep advancing), one CTA barrier, then thread 0 issues the
+// next product while every thread counts its block into the histogram and adds the
+// previous block's column sums.  A wait that gives up (after about 0.3 s) marks the
+// tile aborted; after the next barrier every thread leaves the loop, and the status
+// reports RLXPP_ERR_TIMEOUT.  one = 1 (a launch argument).
 __global__ void __launch_bounds__(kTcRows, 4)
-    k_fused_tc(const DrawArgs a, const __half* __restrict__ bimg, uint32_t one) {
+    k_fused_tc(const DrawArgs a, const __half* __restrict__ bimg_d, uint32_t one) {
   extern __shared__ __align__(1024) unsigned char smem[];
   __shared__ __align__(16) unsigned int hist_s[256 * 32];
   const int tid = threadIdx.x;
@@ -896,7 +910,7 @@ __global__ void __launch_bounds__(kTcRows, 4)
   FusedShared* sh = reinterpret_cast<FusedShared*>(smem + kBRegion);
   const __half* bmat = tc_bmat(smem);
   {
-    const uint4* src = reinterpret_cast<const uint4*>(bimg);
+    const uint4* src = reinterpret_cast<const uint4*>(bimg_d);
     uint4* dst = reinterpret_cast<uint4*>(tc_bmat(smem));
     for (int w = tid; w < kBBytes / 16; w += kTcRows) dst[w] = src[w];
   }
@@ -912,12 +926,6 @@ __global__ void __launch_bounds__(kTcRows, 4)
   tc_fence_after();
   const uint32_t taddr = sh->taddr;
   const uint32_t lane_taddr = taddr + ((uint32_t)((tid / 32) * 32) << 16);
-  {
-    // constant columns of every row: 2048 at k = 72 (against 2^-12: the 1/2 bias), 1 at
-    // k = 73 (against the bytes of E), zeros to k = 79
-    const uint32_t cst[4] = {0x3C006800u, 0u, 0u, 0u};
-    tmem_st4(lane_taddr + kTmA + 36, cst);
-  }
   const uint32_t b0 = smem_addr(bmat);
 
   const StateView& s = a.s;
@@ -939,7 +947,6 @@ __global__ void __launch_bounds__(kTcRows, 4)
   FusedAcc acc;
   acc.hist = smem_addr(hist_s) + 4u * (uint32_t)(tid & 31);
   acc.one = one;
-  acc.c65536 = one << 16;
   acc.c128 = one << 7;
   int64_t rest = cnt;  // values still to draw
   if (live && cnt > 0 && pos + 2 <= (uint32_t)kWords) {  // head of the current block
@@ -954,74 +961,84 @@ __global__ void __launch_bounds__(kTcRows, 4)
     pos += (uint32_t)(hcount * 2);
   }
   // refills of this stream: full blocks, and a last partial one of `tail` values
-  int64_t left = live && rest > 0 ? (rest + kDoubles - 1) / kDoubles : 0;
+  const int64_t nref = live && rest > 0 ? (rest + kDoubles - 1) / kDoubles : 0;
   const uint32_t tail = live ? (uint32_t)(rest % kDoubles) : 0u;
+  int64_t left = nref;
   const int64_t iters = cta_max(left, &sh->iters);
-  uint32_t X[kLimbs];
-  to_lcg(D, c, X);
-  write_x_tmem(lane_taddr, X);
+  write_d_tmem(lane_taddr, D, c);
   tmem_wait_st();
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
   if (iters > 0 && tid == 0) tc_issue_tm(taddr, b0, &sh->bar);
-  uint32_t phase = 0;
+  uint32_t phase = 0, c_fin = c;
   bool ok = true, inflight = iters > 0, stored = false;
-  const bool refills = left > 0;
-  for (int64_t it = 0; it < iters; ++it) {
-    bool got = mbar_wait_bounded(&sh->bar, phase);
-    got = __all_sync(0xFFFFFFFFu, got);  // the warp stays converged for the TMEM accesses
-    if (got) {
-      inflight = false;
-      phase ^= 1u;
-      tc_fence_after();
-      uint32_t col[72];
+  int64_t it = 0;
+  while (ok && it < iters) {
+    const int64_t it_begin = it, it_end = iters - it > kFusedFlush ? it + kFusedFlush : iters;
+    for (; it < it_end; ++it) {
+      bool got = mbar_wait_bounded(&sh->bar, phase);
+      got = __all_sync(0xFFFFFFFFu, got);  // the warp stays converged for the TMEM accesses
+      uint32_t sums[6] = {0, 0, 0, 0, 0, 0};
+      if (got) {
+        inflight = false;
+        phase ^= 1u;
+        tc_fence_after();
+        uint32_t col[80];
 #pragma unroll
-      for (int q = 0; q < 4; ++q) tmem_ld16(lane_taddr + 16 * q, col + 16 * q);
-      tmem_ld8(lane_taddr + 64, col + 64);
-      tmem_wait_ld();
-      tc_fold_common(col, X);
-      __syncwarp();  // reconverged after the rare fold, before the warp-wide store
-      write_x_tmem(lane_taddr, X);
-      tmem_wait_st();
-    } else {
-      sh->abort = 1u;
-    }
-    // every row written and the accumulator read out: the next product may start
-    tc_fence_before();
-    __syncthreads();
-    tc_fence_after();
-    if (sh->abort) {
-      ok = false;
-      break;
-    }
-    if (it + 1 < iters) {
-      if (tid == 0) tc_issue_tm(taddr, b0, &sh->bar);
-      inflight = true;
-    }
-    if (left > 0) {  // this stream's block, while the next product computes
-      to_ranlux(X, D);
-      if (left > 1 || tail == 0) {
-        acc.block(D);
-      } else {
+        for (int q = 0; q < 5; ++q) tmem_ld16(lane_taddr + 16 * q, col + 16 * q);
+        tmem_wait_ld();
 #pragma unroll
-        for (int j = 0; j < kDoubles; ++j)
-          if (j < (int)tail) acc.take(bits48(D, j));
-      }
-      if (--left == 0) {
+        for (int r = 0; r < 6; ++r) sums[r] = col[72 + r];
+        uint32_t X[kLimbs];
+        tc_fold_common(col, X);
+        to_ranlux(X, D);
         c = carry_of(X, D);
-        store_state_D(s, i, D);
-        stored = true;
+        __syncwarp();  // reconverged after the rare branches, before the warp-wide store
+        write_d_tmem(lane_taddr, D, c);
+        tmem_wait_st();
+      } else {
+        sh->abort = 1u;
+      }
+      // every row written and the accumulator read out: the next product may start
+      tc_fence_before();
+      __syncthreads();
+      tc_fence_after();
+      if (sh->abort) {
+        ok = false;
+        break;
+      }
+      if (it + 1 < iters) {
+        if (tid == 0) tc_issue_tm(taddr, b0, &sh->bar);
+        inflight = true;
+      }
+      if (left > 0) {  // while the next product computes
+        if (it > 0) acc.columns(sums);  // the previous block of this stream, all of it drawn
+        if (left > 1) {
+          acc.hist_block(D);  // its sums arrive with the next product
+        } else {
+          const uint32_t nv = tail ? tail : (uint32_t)kDoubles;
+#pragma unroll
+          for (int j = 0; j < kDoubles; ++j)
+            if (j < (int)nv) acc.take(bits48(D, j));
+          store_state_D(s, i, D);
+          c_fin = c;
+          stored = true;
+        }
+        --left;
       }
     }
+    // this thread's column sums of iterations 1 .. nref - 1 within [it_begin, it_end)
+    const int64_t lo = it_begin > 1 ? it_begin : 1, hi = (it_end < nref ? it_end : nref) - 1;
+    acc.flush(hi >= lo ? (uint32_t)(hi - lo + 1) : 0u);
   }
-  if (refills) pos = tail ? 2u * tail : (uint32_t)kWords;
-  if (live && (ok || stored)) s.meta[i] = meta_pack(pos, c, lvl);
+  if (nref > 0) pos = tail ? 2u * tail : (uint32_t)kWords;
+  if (live && (ok || stored)) s.meta[i] = meta_pack(pos, c_fin, lvl);
   if (!ok) {
     if (tid == 0) atomicCAS(s.status, 0, (int)RLXPP_ERR_TIMEOUT);
   } else if (live) {
     uint64_t* sums = static_cast<uint64_t*>(a.out);
-    if (sums) sums[i] = a.accumulate_sums ? sums[i] + acc.total() : acc.total();
+    if (sums) sums[i] = a.accumulate_sums ? sums[i] + acc.total : acc.total;
   }
   // release TMEM; a thread that gave up on a product first waits for it once more
   if (inflight) (void)mbar_wait_bounded(&sh->bar, phase);
@@ -1058,117 +1075,133 @@ __device__ __forceinline__ void emit_head(bool f64, const BatchArgs& b, const ui
   pos += (uint32_t)(h * need);
 }
 
-// Batched requests on the tensor cores.  One CTA = one tile of 128 consecutive chunks of
-// the (per level, longest-first) list: every thread jumps its chunk to its start block
-// (table products on the integer pipe), then the tile refills in lock step as in
-// k_draw_tc until every chunk is done.  Chunks of a tile have similar lengths, so little
-// work is lost to the longest one.
-__global__ void __launch_bounds__(kTcRows, 4) k_requests_tc(const BatchArgs b, const Item* __restrict__ items,
-                                                            uint64_t n_items, const __half* __restrict__ bimg) {
+// Batched requests on the tensor cores, every luxury level in one launch.  Persistent
+// CTAs (one tile-group each) take tiles from the counter: a tile is up to 128
+// consecutive chunks of one level of the (per level, longest-first) list, and the tile
+// table itself is ordered longest first across levels.  A CTA loads the level's matrix
+// into shared memory when it changes from the previous tile's; then every thread jumps
+// its chunk to its start block (table products on the integer pipe) and the tile
+// refills in lock step as in k_draw_tc until every chunk is done.  Chunks of a tile have
+// similar lengths, so little work is lost to the longest one.
+__global__ void __launch_bounds__(kTcRows, 4)
+    k_requests_tc(const BatchArgs b, const Item* __restrict__ items, const TcTile* __restrict__ tiles,
+                  uint64_t n_tiles, const __half* __restrict__ bimg_all, WorkCounters* wc) {
   extern __shared__ __align__(1024) unsigned char smem[];
+  __shared__ unsigned long long tile_s;
   const TcGroup G = tc_group(smem, true);  // one group per CTA
   const __half* bmat = tc_bmat(smem);
   uint4* slot = reinterpret_cast<uint4*>(G.stage + G.t * kStageBytes);
   const unsigned char* wstage = G.stage + (G.t & ~31) * kStageBytes;  // this warp's 32 slots
   const int tid = threadIdx.x;
-  tc_setup(smem, G, bimg, 1);
+  tc_setup(smem, G, nullptr, 1);
   const uint32_t taddr = tc_tmem(smem, G);
-  const uint64_t idx = (uint64_t)blockIdx.x * kTcRows + tid;
-  const bool live = idx < n_items;
-  Item it{};
-  if (live) it = items[idx];
-  uint32_t D[kLimbs];
-#pragma unroll
-  for (int q = 0; q < kLimbs; ++q) D[q] = 0;
-  uint32_t c = 0, lvl = 0;
-  if (live) {
-    const uint32_t meta = b.snap_meta[it.req];
-    lvl = meta_level(meta);
-    c = meta_carry(meta);
-#pragma unroll
-    for (int q = 0; q < 9; ++q) {
-      const uint64_t v = b.snap_D[(uint64_t)q * b.n_reqs + it.req];
-      D[2 * q] = (uint32_t)v;
-      D[2 * q + 1] = (uint32_t)(v >> 32);
-    }
-    if (it.jump) {  // X <- A^jump X
-      uint32_t X[kLimbs];
-      to_lcg(D, c, X);
-      bool have = true;
-      apply_digits(b.s.table + (size_t)lvl * kTableLimbs, 0, it.jump, X, have);
-      to_ranlux(X, D);
-      c = carry_of(X, D);
-    }
-  }
-  const bool f64 = (it.info & 1u) != 0;
-  const int64_t cnt = live ? it.count : 0, base = (int64_t)it.out;
-  uint32_t pos = live ? (it.info >> 8) & 0xFFu : (uint32_t)kWords;
-  int64_t k = 0;
-  emit_head(f64, b, D, pos, cnt, base, k);
-  bool mine = live && k < cnt, refilled = false;
-  uint32_t X[kLimbs];
-  to_lcg(D, c, X);
   uint32_t phase = 0;
   bool ok = true;
-  while (true) {
-    write_x_row(G.tile, G.t, X);
-    if (!tc_publish(G, mine)) break;  // every chunk of the tile is done
-    uint32_t col[72];
-    if (!tc_refill_after_publish(G, bmat, taddr, phase, col)) {
-      ok = false;
-      break;
+  uint32_t loaded = 0xFFFFFFFFu;  // level whose matrix is in shared memory
+  while (ok) {
+    if (tid == 0) tile_s = atomicAdd(&wc->next, 1ull);
+    __syncthreads();
+    const unsigned long long t = tile_s;
+    __syncthreads();  // every thread has read the tile index
+    if (t >= n_tiles) break;
+    const TcTile tile = tiles[t];
+    if (tile.level != loaded) {  // the products of the previous tile are complete
+      const uint4* src = reinterpret_cast<const uint4*>(bimg_all + (size_t)tile.level * (kBBytes / 2));
+      uint4* dst = reinterpret_cast<uint4*>(tc_bmat(smem));
+      for (int w = tid; w < kBBytes / 16; w += kTcRows) dst[w] = src[w];
+      loaded = tile.level;  // made visible to the tensor core by the publishing fence
     }
-    uint32_t Xn[kLimbs];
-    columns_to_x(col, Xn);
-    uint64_t dst = 0;  // destination of this lane's full block, if it has one
-    if (mine) {
+    const bool live = (uint32_t)tid < tile.n;
+    Item it{};
+    if (live) it = items[tile.first + tid];
+    uint32_t D[kLimbs];
 #pragma unroll
-      for (int q = 0; q < kLimbs; ++q) X[q] = Xn[q];
-      to_ranlux(X, D);
-      refilled = true;
-      const int64_t per = f64 ? kDoubles : kWords;
-      const int64_t rem = cnt - k;
-      if (rem >= per) {
-        // chunks write to unrelated places: staged here, written by the whole warp below
-        uint4 v[6];
-        if (f64)
-          block_values<kDrawF64>(D, v);
-        else
-          block_values<kDrawU24>(D, v);
-#pragma unroll
-        for (int q = 0; q < 6; ++q) slot[q] = v[q];
-        dst = f64 ? reinterpret_cast<uint64_t>(b.out_f64 + base + k) : reinterpret_cast<uint64_t>(b.out_u24 + base + k);
-        k += per;
-        pos = kWords;
-      } else {
-        if (f64) {
-#pragma unroll
-          for (int j = 0; j < kDoubles; ++j)
-            if (j < rem) b.out_f64[base + k + j] = f64_bits_from48_outlined(bits48(D, j));
-          pos = (uint32_t)(rem * 2);
-        } else {
-#pragma unroll
-          for (int j = 0; j < kWords; ++j)
-            if (j < rem) b.out_u24[base + k + j] = word24(D, j);
-          pos = (uint32_t)rem;
-        }
-        k = cnt;
+    for (int q = 0; q < kLimbs; ++q) D[q] = 0;
+    uint32_t c = 0, lvl = 0;
+    if (live) {
+      uint32_t meta;
+      request_state(b, it.req, D, meta);
+      lvl = meta_level(meta);
+      c = meta_carry(meta);
+      if (it.jump) {  // X <- A^jump X
+        uint32_t X[kLimbs];
+        to_lcg(D, c, X);
+        bool have = true;
+        apply_digits(b.s.table + (size_t)lvl * kTableLimbs, 0, it.jump, X, have);
+        to_ranlux(X, D);
+        c = carry_of(X, D);
       }
-      mine = k < cnt;
     }
-    warp_store_blocks(wstage, dst);
+    const bool f64 = (it.info & 1u) != 0;
+    const int64_t cnt = live ? it.count : 0, base = (int64_t)it.out;
+    uint32_t pos = live ? (it.info >> 8) & 0xFFu : (uint32_t)kWords;
+    int64_t k = 0;
+    emit_head(f64, b, D, pos, cnt, base, k);
+    bool mine = live && k < cnt, refilled = false;
+    uint32_t X[kLimbs];
+    to_lcg(D, c, X);
+    while (true) {
+      write_x_row(G.tile, G.t, X);
+      if (!tc_publish(G, mine)) break;  // every chunk of the tile is done
+      uint32_t col[72];
+      if (!tc_refill_after_publish(G, bmat, taddr, phase, col)) {
+        ok = false;
+        break;
+      }
+      uint32_t Xn[kLimbs];
+      columns_to_x(col, Xn);
+      uint64_t dst = 0;  // destination of this lane's full block, if it has one
+      if (mine) {
+#pragma unroll
+        for (int q = 0; q < kLimbs; ++q) X[q] = Xn[q];
+        to_ranlux(X, D);
+        refilled = true;
+        const int64_t per = f64 ? kDoubles : kWords;
+        const int64_t rem = cnt - k;
+        if (rem >= per) {
+          // chunks write to unrelated places: staged here, written by the whole warp below
+          uint4 v[6];
+          if (f64)
+            block_values<kDrawF64>(D, v);
+          else
+            block_values<kDrawU24>(D, v);
+#pragma unroll
+          for (int q = 0; q < 6; ++q) slot[q] = v[q];
+          dst = f64 ? reinterpret_cast<uint64_t>(b.out_f64 + base + k)
+                    : reinterpret_cast<uint64_t>(b.out_u24 + base + k);
+          k += per;
+          pos = kWords;
+        } else {
+          if (f64) {
+#pragma unroll
+            for (int j = 0; j < kDoubles; ++j)
+              if (j < rem) b.out_f64[base + k + j] = f64_bits_from48_outlined(bits48(D, j));
+            pos = (uint32_t)(rem * 2);
+          } else {
+#pragma unroll
+            for (int j = 0; j < kWords; ++j)
+              if (j < rem) b.out_u24[base + k + j] = word24(D, j);
+            pos = (uint32_t)rem;
+          }
+          k = cnt;
+        }
+        mine = k < cnt;
+      }
+      warp_store_blocks(wstage, dst);
+    }
+    if (ok && live && b.advance && ((it.info >> 16) & 1u)) {  // last chunk: final state
+      if (refilled) c = carry_of(X, D);
+      const uint64_t st = b.req_stream[it.req];
+#pragma unroll
+      for (int q = 0; q < 9; ++q)
+        b.s.D[(uint64_t)q * b.s.stride + st] = ((uint64_t)D[2 * q + 1] << 32) | D[2 * q];
+      b.s.meta[st] = meta_pack(pos, c, lvl);
+    }
   }
   bulk_wait_all();
-  if (!ok) {
-    if (tid == 0) atomicCAS(b.s.status, 0, (int)RLXPP_ERR_TIMEOUT);
-  } else if (live && b.advance && ((it.info >> 16) & 1u)) {  // last chunk: final state
-    if (refilled) c = carry_of(X, D);
-    const uint64_t st = b.req_stream[it.req];
-#pragma unroll
-    for (int q = 0; q < 9; ++q) b.s.D[(uint64_t)q * b.s.stride + st] = ((uint64_t)D[2 * q + 1] << 32) | D[2 * q];
-    b.s.meta[st] = meta_pack(pos, c, lvl);
-  }
+  if (!ok && tid == 0) atomicCAS(b.s.status, 0, (int)RLXPP_ERR_TIMEOUT);
   tc_teardown(smem, G, !ok, phase, 1);
+  finish_cta(wc);
 }
 
 // One tensor-path product per item: out = A x mod m (x < m), for testing.  With
@@ -1255,6 +1288,91 @@ __global__ void k_tc_matrix(const uint32_t* __restrict__ lux, __half* __restrict
   }
 }
 
+// The level's matrix for products whose operand rows hold a stream's RANLUX numbers D
+// and borrow c instead of its LCG state (the fused draw).  X = D - floor(D / 2^336) + c
+// is linear in the 72 bytes d_j of D: byte j stands for 2^(8j), less 2^(8j - 336) for
+// j >= 42, so A X = sum_j d_j R'_j + c A (mod m) with R'_j = A 2^(8j) - A 2^(8(j-42)) =
+// R_j - R_(j-42) mod m for j >= 42 and R'_j = R_j below.  Column k < 72 of row j holds
+// byte k of R'_j; row 74 holds the bytes of A (against c); rows 72 and 73 are the bias
+// and correction rows of k_tc_matrix.  Columns 72..77 of row j < 72 hold 1 when j mod 6
+// equals the column's index r = k - 72, so that those columns sum the bytes of D by
+// their position within a 48-bit value: the 48-bit values of the block add up to
+// sum_r 2^(8r) P_r, P_r the sum in column 72 + r (below 12 * 255).
+__device__ __forceinline__ void lux_shift_mod(const uint32_t* __restrict__ lux, int j, uint32_t R[kLimbs]) {
+  uint32_t P[2 * kLimbs];
+#pragma unroll 1
+  for (int q = 0; q < 2 * kLimbs; ++q) P[q] = 0;
+  const int sh_limb = (8 * j) >> 5, sh_bit = (8 * j) & 31;
+#pragma unroll 1
+  for (int q = 0; q < kLimbs; ++q) {
+    const uint32_t a = lux[q];
+    P[q + sh_limb] |= a << sh_bit;
+    if (sh_bit) P[q + sh_limb + 1] |= a >> (32 - sh_bit);
+  }
+  mod_m(P, R);
+}
+
+__global__ void k_tc_matrix_d(const uint32_t* __restrict__ lux, __half* __restrict__ bimg) {
+  const int j = threadIdx.x;  // 0..79
+  if (j >= kTcK) return;
+  float v[kTcN];
+#pragma unroll 1
+  for (int n = 0; n < kTcN; ++n) v[n] = 0.f;
+  if (j < 72) {
+    uint32_t R[kLimbs];
+    lux_shift_mod(lux, j, R);
+    if (j >= 42) {  // R - R_(j-42) mod m (both in [0, m))
+      uint32_t S[kLimbs];
+      lux_shift_mod(lux, j - 42, S);
+      uint64_t borrow = 0;
+#pragma unroll 1
+      for (int q = 0; q < kLimbs; ++q) {
+        const uint64_t d = (uint64_t)R[q] - S[q] - borrow;
+        R[q] = (uint32_t)d;
+        borrow = (d >> 63) & 1u;
+      }
+      if (borrow) {  // + m = 2^576 - 2^240 + 1 (the wrap past 2^576 cancels the borrow)
+        uint64_t carry = 0;
+#pragma unroll 1
+        for (int q = 0; q < kLimbs; ++q) {
+          const uint32_t mq = q == 0 ? 1u : (q < 7 ? 0u : (q == 7 ? 0xFFFF0000u : 0xFFFFFFFFu));
+          const uint64_t t = (uint64_t)R[q] + mq + carry;
+          R[q] = (uint32_t)t;
+          carry = t >> 32;
+        }
+      }
+    }
+#pragma unroll 1
+    for (int n = 0; n < 72; ++n) v[n] = (float)((R[n >> 2] >> (8 * (n & 3))) & 0xFFu);
+    v[72 + j % 6] = 1.f;
+  } else if (j == 72) {  // against 2048: 1/2 in every column
+#pragma unroll 1
+    for (int n = 0; n < kTcN; ++n) v[n] = 0x1p-12f;
+  } else if (j == 73) {  // against 1: the bytes of E = -C mod m as subnormals
+    uint32_t P[2 * kLimbs];
+#pragma unroll 1
+    for (int q = 0; q < 2 * kLimbs; ++q) P[q] = q == 0 ? 0x3F000000u : (q < kLimbs ? 0x3F003F00u : 0u);
+    P[kLimbs] = 0x3F00u;
+    uint32_t R[kLimbs], E[kLimbs];
+    mod_m(P, R);
+    uint64_t borrow = 0;
+#pragma unroll 1
+    for (int q = 0; q < kLimbs; ++q) {
+      const uint32_t mq = q == 0 ? 1u : (q < 7 ? 0u : (q == 7 ? 0xFFFF0000u : 0xFFFFFFFFu));
+      const uint64_t d = (uint64_t)mq - R[q] - borrow;
+      E[q] = (uint32_t)d;
+      borrow = (d >> 63) & 1u;
+    }
+#pragma unroll 1
+    for (int n = 0; n < 72; ++n) v[n] = (float)((E[n >> 2] >> (8 * (n & 3))) & 0xFFu) * 0x1p-24f;
+  } else if (j == 74) {  // against the borrow c: the bytes of A
+#pragma unroll 1
+    for (int n = 0; n < 72; ++n) v[n] = (float)((lux[n >> 2] >> (8 * (n & 3))) & 0xFFu);
+  }
+#pragma unroll 1
+  for (int n = 0; n < kTcN; ++n) bimg[tc_off(n, j)] = __float2half(v[n]);
+}
+
 // One-group CTAs (the request and test kernels, the fused and Gaussian draws) take
 // 48 KB of dynamic shared memory, so that at most 4 share an SM, whose 512 TMEM columns
 // then always suffice; the value-writing draws run kTcGroups groups per CTA and one CTA
@@ -1330,11 +1448,11 @@ cudaError_t launch_tc_kind(const DrawArgs& a, const __half* bimg, cudaStream_t s
   return cudaGetLastError();
 }
 
-cudaError_t launch_fused_tc(const DrawArgs& a, const __half* bimg, cudaStream_t st) {
+cudaError_t launch_fused_tc(const DrawArgs& a, const __half* bimg_d, cudaStream_t st) {
   cudaError_t e = cudaFuncSetAttribute(k_fused_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, kFusedDynSmem);
   if (e != cudaSuccess) return e;
   const unsigned grid = (unsigned)((a.s.n + kTcRows - 1) / kTcRows);
-  k_fused_tc<<<grid, kTcRows, kFusedDynSmem, st>>>(a, bimg, 1u);
+  k_fused_tc<<<grid, kTcRows, kFusedDynSmem, st>>>(a, bimg_d, 1u);
   return cudaGetLastError();
 }
 
@@ -1342,13 +1460,13 @@ cudaError_t launch_fused_tc(const DrawArgs& a, const __half* bimg, cudaStream_t 
 
 size_t tc_matrix_bytes() { return kBBytes; }
 
-cudaError_t launch_requests_tc(const BatchArgs& b, const Item* items, uint64_t n, const void* bimg,
-                               cudaStream_t st) {
-  if (n == 0) return cudaSuccess;
+cudaError_t launch_requests_tc(const BatchArgs& b, const Item* items, const TcTile* tiles, uint64_t n_tiles,
+                               const void* bimg, WorkCounters* wc, unsigned grid, cudaStream_t st) {
+  if (n_tiles == 0) return cudaSuccess;
   cudaError_t e = cudaFuncSetAttribute(k_requests_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTcSmem);
   if (e != cudaSuccess) return e;
-  k_requests_tc<<<(unsigned)((n + kTcRows - 1) / kTcRows), kTcRows, kTcSmem, st>>>(
-      b, items, n, static_cast<const __half*>(bimg));
+  if (grid > n_tiles) grid = (unsigned)n_tiles;
+  k_requests_tc<<<grid, kTcRows, kTcSmem, st>>>(b, items, tiles, n_tiles, static_cast<const __half*>(bimg), wc);
   return cudaGetLastError();
 }
 
@@ -1357,13 +1475,18 @@ cudaError_t launch_tc_matrix(const uint32_t* lux18, void* bimg, cudaStream_t st)
   return cudaGetLastError();
 }
 
-cudaError_t launch_draw_tc(int kind, const DrawArgs& a, const void* bimg, cudaStream_t st) {
+cudaError_t launch_tc_matrix_d(const uint32_t* lux18, void* bimg, cudaStream_t st) {
+  k_tc_matrix_d<<<1, kTcK, 0, st>>>(lux18, static_cast<__half*>(bimg));
+  return cudaGetLastError();
+}
+
+cudaError_t launch_draw_tc(int kind, const DrawArgs& a, const void* bimg, const void* bimg_d, cudaStream_t st) {
   if (a.s.n == 0) return cudaSuccess;
   const __half* b = static_cast<const __half*>(bimg);
   switch (kind) {
     case kDrawU24: return launch_tc_kind<kDrawU24>(a, b, st);
     case kDrawF64: return launch_tc_kind<kDrawF64>(a, b, st);
-    case kDrawSumHist: return launch_fused_tc(a, b, st);
+    case kDrawSumHist: return launch_fused_tc(a, static_cast<const __half*>(bimg_d), st);
     case kDrawF32: return launch_tc_kind<kDrawF32>(a, b, st);
     case kDrawNormal: return launch_tc_kind<kDrawNormal>(a, b, st);
     case kDrawExp: return launch_tc_kind<kDrawExp>(a, b, st);

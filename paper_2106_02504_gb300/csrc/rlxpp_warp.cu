@@ -10,6 +10,7 @@
 // ((G << 1) + P) ^ P — a carry enters lane l exactly when some lane below generated one
 // and every lane in between propagates it.  Subtractions do the same with borrows.
 #include "rlxpp_arith.cuh"
+#include "rlxpp_batch.h"
 #include "rlxpp_drawloop.cuh"
 #include "rlxpp_internal.h"
 #include "rlxpp_state.cuh"
@@ -384,6 +385,109 @@ __global__ void __launch_bounds__(kWarpBlock) k_test_warp(int op, const uint64_t
   if (l < 18 && (l & 1) == 0) out[9 * i + l / 2] = ((uint64_t)hi << 32) | r;
 }
 
+// Batched requests with 32 threads per stream: persistent warps take one chunk at a
+// time from the counter (every level in one launch).  Lane 0 jumps the chunk to its
+// start block with the single-thread table products; the warp then refills and emits as
+// k_draw_warp does, one value per lane, with the multiplier of the chunk's level read
+// from the level table.  For few, long chunks, where the latency of one refill is what
+// counts.
+__global__ void __launch_bounds__(kWarpBlock)
+    k_requests_warp(const BatchArgs b, const Item* __restrict__ items, uint64_t n_items, WorkCounters* wc) {
+  __shared__ uint32_t scratch_s[kWarpsPerBlock][36];
+  const unsigned l = lane_id();
+  const int warp = threadIdx.x / 32;
+  uint32_t* scratch = scratch_s[warp];
+  while (true) {
+    unsigned long long idx = 0;
+    if (l == 0) idx = atomicAdd(&wc->next, 1ull);
+    idx = __shfl_sync(kFull, idx, 0);
+    if (idx >= n_items) break;
+    const Item it = items[idx];
+    if (l == 0) {  // the chunk's start state, on one thread
+      uint32_t Ds[kLimbs], meta;
+      request_state(b, it.req, Ds, meta);
+      uint32_t c0 = meta_carry(meta);
+      const uint32_t lv = meta_level(meta);
+      if (it.jump) {  // X <- A^jump X
+        uint32_t Xs[kLimbs];
+        to_lcg(Ds, c0, Xs);
+        bool have = true;
+        apply_digits(b.s.table + (size_t)lv * kTableLimbs, 0, it.jump, Xs, have);
+        to_ranlux(Xs, Ds);
+        c0 = carry_of(Xs, Ds);
+      }
+#pragma unroll
+      for (int k = 0; k < kLimbs; ++k) scratch[k] = Ds[k];
+      scratch[18] = c0;
+      scratch[19] = lv;
+    }
+    __syncwarp();
+    uint32_t D = l < 18 ? scratch[l] : 0u;
+    uint32_t c = scratch[18];
+    const uint32_t lvl = scratch[19];
+    __syncwarp();  // scratch is free again (the conversion's rare case uses it)
+    const uint32_t* luxl = b.s.lux + (size_t)lvl * kLimbs;
+    auto A = [&](int k) { return __ldg(luxl + k); };
+    const bool f64 = (it.info & 1u) != 0;
+    const int need = f64 ? 2 : 1;
+    const int per_block = kWords / need;
+    const int64_t cnt = it.count, base = (int64_t)it.out;
+    uint32_t pos = (it.info >> 8) & 0xFFu;
+    // value of lane j of a block read from word w0 on (every lane takes part in the
+    // shuffles; only lanes with a value store)
+    auto emit = [&](int w0, int64_t idx0, int64_t nvals) {
+      const int j = (int)l;
+      if (f64) {
+        const int w = w0 + 2 * j;
+        const uint64_t v = wbits48(D, w < kWords - 1 ? w : 0);
+        if (j < nvals && w + 2 <= kWords) b.out_f64[idx0 + j] = f64_bits_from48(v);
+      } else {
+        const int w = w0 + j;
+        const uint32_t v = wword24(D, w < kWords ? w : 0);
+        if (j < nvals && w < kWords) b.out_u24[idx0 + j] = v;
+      }
+    };
+    int64_t k = 0;
+    if (cnt > 0 && pos + need <= (uint32_t)kWords) {  // head of the start block
+      const int64_t room = (kWords - pos) / need;
+      const int64_t h = cnt < room ? cnt : room;
+      emit((int)pos, base, h);
+      k = h;
+      pos += (uint32_t)(h * need);
+    }
+    if (k < cnt) {
+      uint32_t X = wto_lcg(D, c);
+#pragma unroll 1
+      while (true) {
+        uint32_t L, H;
+        wmul(A, l < 18 ? X : 0u, L, H);
+        X = wmod_m(L, H);
+        D = wto_ranlux(X, scratch);
+        const int64_t rem = cnt - k;
+        if (rem >= per_block) {
+          emit(0, base + k, per_block);
+          k += per_block;
+          pos = kWords;
+          if (k == cnt) break;
+        } else {
+          emit(0, base + k, rem);
+          k = cnt;
+          pos = (uint32_t)(rem * need);
+          break;
+        }
+      }
+      c = wcarry(X, D);
+    }
+    if (b.advance && ((it.info >> 16) & 1u)) {  // last chunk of its request: final state
+      const uint64_t st = b.req_stream[it.req];
+      const uint32_t hiD = __shfl_down_sync(kFull, D, 1);
+      if (l < 18 && (l & 1) == 0) b.s.D[(uint64_t)(l / 2) * b.s.stride + st] = ((uint64_t)hiD << 32) | D;
+      if (l == 0) b.s.meta[st] = meta_pack(pos, c, lvl);
+    }
+  }
+  finish_cta(wc);
+}
+
 template <int Kind>
 cudaError_t launch_warp_kind(const DrawArgs& a, cudaStream_t st) {
   const unsigned grid = (unsigned)((a.s.n + kWarpsPerBlock - 1) / kWarpsPerBlock);
@@ -395,6 +499,15 @@ cudaError_t launch_warp_kind(const DrawArgs& a, cudaStream_t st) {
 }
 
 }  // namespace
+
+cudaError_t launch_requests_warp(const BatchArgs& b, const Item* items, uint64_t n_items, WorkCounters* wc,
+                                 unsigned grid, cudaStream_t st) {
+  if (n_items == 0) return cudaSuccess;
+  const uint64_t need = (n_items + kWarpsPerBlock - 1) / kWarpsPerBlock;
+  if (grid > need) grid = (unsigned)need;
+  k_requests_warp<<<grid, kWarpBlock, 0, st>>>(b, items, n_items, wc);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_warp_test(int op, const uint64_t* in, uint64_t* out, uint32_t* carry, uint64_t n,
                              cudaStream_t st) {

@@ -1,8 +1,10 @@
 """Batched requests (rlxpp_plan_requests / rlxpp_run_plan / rlxpp_draw_requests) against
 the oracle, bit-exact (GPU): uneven counts, mixed kinds and luxury levels, skips,
 arbitrary start positions, the same stream several times, chunking by jump-ahead at
-several chunk lengths, RLXPP_REQ_ADVANCE, CUDA-graph capture of a run, the tuner, and
-the single-stream workload (2^20 doubles from seed 1) split over many threads."""
+several chunk lengths, RLXPP_REQ_ADVANCE, CUDA-graph capture of a run (one kernel node
+for all luxury levels), the tuner, and the single-stream workload (2^20 doubles from
+seed 1) split over many threads; on the three request kernels (one thread per chunk on
+the integer pipe or on the tensor cores, one warp per chunk)."""
 import numpy as np
 import pytest
 
@@ -16,13 +18,17 @@ pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
 
 
-@pytest.fixture(params=["tensor", "imad"])
+@pytest.fixture(params=["tensor", "imad", "warp"])
 def path(request):
     return request.param
 
 
+def path_id(native, path):
+    return {"imad": native.RLXPP_PATH_IMAD, "tensor": native.RLXPP_PATH_TENSOR, "warp": native.RLXPP_PATH_WARP}[path]
+
+
 def set_path(native, g, path):
-    g.set_path(native.RLXPP_PATH_IMAD if path == "imad" else native.RLXPP_PATH_TENSOR)
+    g.set_path(path_id(native, path))
 
 
 @pytest.fixture(scope="module")
@@ -121,7 +127,7 @@ def test_mixed_requests(native, path):
         count = int(rng.choice([0, 1, 2, 11, 12, 13, 24, 25, int(rng.integers(0, 3000))]))
         rows.append((st, skip, pos, kind, count))
     reqs, nu, nf = make_requests(rows)
-    for tuning in [(2, 2), (4, 4), (64, 3), (16, 2, 1 - native.rlxpp_get_path(g.handle)), None]:
+    for tuning in [(2, 2), (4, 4), (64, 3), (16, 2, (native.rlxpp_get_path(g.handle) + 1) % 3), None]:
         run_and_check(native, g, xs, levels_of, reqs, nu, nf, tuning=tuning)
     # streams did not move
     xs2, _ = current_X(native, g, n)
@@ -209,11 +215,72 @@ def test_autotune(native, path):
     out_u = torch.zeros(max(nu, 1), dtype=torch.int32, device="cuda")
     out_f = torch.zeros(max(nf, 1), dtype=torch.float64, device="cuda")
     best = native.rlxpp_autotune_requests(g.handle, reqs, out_u, out_f)
-    assert best[0] >= 2 and 1 <= best[1] <= 8 and best[2] in (0, 1)
+    assert best[0] >= 2 and 1 <= best[1] <= 8 and best[2] in (0, 1, 2)
     plan = native.rlxpp_plan_requests(g.handle, reqs)        # uses the tuned choice
     assert native.rlxpp_plan_tuning(plan) == best
     native.rlxpp_destroy_plan(plan)
     run_and_check(native, g, xs, [2048] * n, reqs, nu, nf)
+
+
+def _captured_node_types(fn, stream):
+    """Node types of the CUDA graph that capturing fn() on `stream` records (driver API:
+    0 kernel, 1 memcpy, 2 memset, ...)."""
+    import ctypes
+    cu = ctypes.CDLL("libcuda.so.1")
+    begin = getattr(cu, "cuStreamBeginCapture_v2", None) or cu.cuStreamBeginCapture
+    graph = ctypes.c_void_p()
+    assert begin(ctypes.c_void_p(stream.cuda_stream), 2) == 0   # CU_STREAM_CAPTURE_MODE_RELAXED
+    try:
+        fn()
+    finally:
+        assert cu.cuStreamEndCapture(ctypes.c_void_p(stream.cuda_stream), ctypes.byref(graph)) == 0
+    try:
+        n = ctypes.c_size_t(0)
+        assert cu.cuGraphGetNodes(graph, None, ctypes.byref(n)) == 0
+        nodes = (ctypes.c_void_p * max(n.value, 1))()
+        assert cu.cuGraphGetNodes(graph, nodes, ctypes.byref(n)) == 0
+        types = []
+        for k in range(n.value):
+            t = ctypes.c_int(-1)
+            assert cu.cuGraphNodeGetType(ctypes.c_void_p(nodes[k]), ctypes.byref(t)) == 0
+            types.append(t.value)
+        return types
+    finally:
+        cu.cuGraphDestroy(graph)
+
+
+def test_one_kernel_node_for_all_levels(native, path):
+    """A run of a plan over four luxury levels, captured on a stream, is one kernel node
+    (no per-level launches and no memset: the work counters reset themselves), and two
+    runs after the capture give the oracle's values."""
+    n = 96
+    levels = [24, 223, 389, 2048]
+    lvl = (np.arange(n) % 4).astype(np.uint8)
+    seeds = W.consecutive_seeds(n, first=900)
+    g = native.Generator(n, levels, torch.from_numpy(seeds.view(np.int64)).cuda(), torch.from_numpy(lvl).cuda())
+    xs, _ = current_X(native, g, n)
+    rows = [(i, i * 3, i % 25, i % 2, 50 + 37 * i) for i in range(n)]
+    reqs, nu, nf = make_requests(rows)
+    out_u = torch.full((nu,), -1, dtype=torch.int32, device="cuda")
+    out_f = torch.full((nf,), -1, dtype=torch.int64, device="cuda")
+    plan = native.rlxpp_plan_requests(g.handle, reqs, 0, (4, 2, path_id(native, path)))
+    try:
+        s = torch.cuda.Stream()
+        torch.cuda.synchronize()
+        types = _captured_node_types(lambda: native.rlxpp_run_plan(g.handle, plan, out_u, out_f, s), s)
+        assert types == [0], types
+        for _ in range(2):
+            native.rlxpp_run_plan(g.handle, plan, out_u, out_f, s)
+        torch.cuda.synchronize()
+    finally:
+        native.rlxpp_destroy_plan(plan)
+    gu = out_u.cpu().numpy().view(np.uint32)
+    gf = out_f.cpu().numpy().view(np.uint64)
+    for r in reqs:
+        st, skip, pos, kind, count, off = (int(r[k]) for k in ("stream", "skip", "pos", "kind", "count", "offset"))
+        want, _ = expected(xs[st], levels[int(lvl[st])], skip, pos, kind, count)
+        got = gf[off:off + count] if kind == 1 else gu[off:off + count]
+        assert np.array_equal(got, want), (st, kind, count)
 
 
 def test_request_validation(native):
