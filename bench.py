@@ -627,6 +627,16 @@ def bench_serving(args):
                          "busy_s": round(host1["busy"] - host0["busy"], 3), "cores": os.cpu_count(),
                          "loop_cpu_share": round((cpu1 - cpu0) / (t1 - t0), 3)}
     stats["launch"] = {"max_host_ms": loop["max_launch_us"] / 1e3, "slow_launches": loop["slow_launches"]}
+    # where a batch's time went on the device (CUDA events on its stream): the request
+    # kernel, and the device-to-host copies after it
+    nb = max(loop["batches_timed"], 1)
+    stats["device"] = {"batches": loop["batches_timed"], "kernel_ms_mean": loop["kernel_us_sum"] / nb / 1e3,
+                       "kernel_ms_max": loop["kernel_us_max"] / 1e3, "copy_ms_mean": loop["copy_us_sum"] / nb / 1e3,
+                       "copy_ms_max": loop["copy_us_max"] / 1e3}
+    # a backlog that builds up over the trace shows as a higher tail in its second half
+    late = ok & (arr >= arr[ok].min() + 0.5 * (arr[ok].max() - arr[ok].min()))
+    if late.any():
+        stats["p99_second_half_ms"] = float(np.percentile(lat[late], 99) * 1e3)
     stats.update({"resident_streams": n_res, "arrival_rate_hz": rate, "trace_seconds": args.serve_seconds,
                   "pool_bytes": args.serve_pool_gib << 30, "cuda_streams": args.serve_streams,
                   "max_batch": args.serve_max_batch})

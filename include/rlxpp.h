@@ -434,6 +434,14 @@ typedef struct rlxpp_server_state {
   uint64_t waiting, admitted, inflight_groups, arena_used, queued_bytes, done, rejected, cancelled;
   uint64_t max_launch_us;  /* longest host time of one batch launch, microseconds      */
   uint64_t slow_launches;  /* batch launches that took 1 ms or more on the host         */
+  /* Device-side times of completed batches, from CUDA events recorded on the batch's
+   * stream: "kernel" = from the batch's first operation to the end of its request
+   * kernel, "copy" = from there to the end of its last device-to-host copy.  A latency
+   * excursion whose batches show long copy times was spent on the link; one with
+   * short device times was spent waiting on the host. */
+  uint64_t batches_timed;                 /* completed batches with device times       */
+  uint64_t kernel_us_sum, kernel_us_max;  /* microseconds                              */
+  uint64_t copy_us_sum, copy_us_max;      /* microseconds                              */
 } rlxpp_server_state;
 rlxpp_status rlxpp_server_create(rlxpp_gen* gen, uint64_t pool_bytes, uint32_t n_cuda_streams,
                                  uint32_t max_batch, uint64_t small_bytes, uint64_t max_queued_bytes,

@@ -329,10 +329,11 @@ def rlxpp_server_drain(server):
 
 def rlxpp_server_stats(server):
     """dict of the counters of struct rlxpp_server_state."""
-    v = (_u64 * 10)()
-    _check(_lib.rlxpp_server_stats(server, ctypes.addressof(v)))
     keys = ("waiting", "admitted", "inflight_groups", "arena_used", "queued_bytes", "done", "rejected", "cancelled",
-            "max_launch_us", "slow_launches")
+            "max_launch_us", "slow_launches", "batches_timed", "kernel_us_sum", "kernel_us_max", "copy_us_sum",
+            "copy_us_max")
+    v = (_u64 * len(keys))()
+    _check(_lib.rlxpp_server_stats(server, ctypes.addressof(v)))
     return dict(zip(keys, list(v)))
 
 

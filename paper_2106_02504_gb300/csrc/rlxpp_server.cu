@@ -88,6 +88,7 @@ struct Group {
 struct InFlight {
   int si;
   std::deque<Group> groups;
+  cudaEvent_t t[3];  // timing events: batch start, request kernel end, copies end
 };
 
 double now_s() {
@@ -122,6 +123,9 @@ struct rlxpp_server {
   uint64_t n_done = 0, n_rejected = 0, n_cancelled = 0;
   double max_launch_s = 0;   // longest host time of one batch launch (rlxpp_draw_requests)
   uint64_t slow_launches = 0;  // launches of 1 ms or more
+  std::vector<cudaEvent_t> timing_pool;  // events with timing, three per batch
+  uint64_t batches_timed = 0;
+  double kernel_s_sum = 0, kernel_s_max = 0, copy_s_sum = 0, copy_s_max = 0;
 };
 
 namespace {
@@ -158,6 +162,33 @@ rlxpp_status get_event(rlxpp_server* s, cudaEvent_t& ev) {
   return e == cudaSuccess ? RLXPP_OK : cuda_fail(e, "server event");
 }
 
+rlxpp_status get_timing_event(rlxpp_server* s, cudaEvent_t& ev) {
+  if (!s->timing_pool.empty()) {
+    ev = s->timing_pool.back();
+    s->timing_pool.pop_back();
+    return RLXPP_OK;
+  }
+  cudaError_t e = cudaEventCreate(&ev);
+  return e == cudaSuccess ? RLXPP_OK : cuda_fail(e, "server timing event");
+}
+
+// Device times of a completed batch (its last copy is done, so all three events have
+// completed); the events go back to the pool.
+void record_batch_times(rlxpp_server* s, InFlight& f) {
+  float k_ms = 0, c_ms = 0;
+  if (cudaEventElapsedTime(&k_ms, f.t[0], f.t[1]) == cudaSuccess &&
+      cudaEventElapsedTime(&c_ms, f.t[1], f.t[2]) == cudaSuccess) {
+    ++s->batches_timed;
+    s->kernel_s_sum += k_ms * 1e-3;
+    s->kernel_s_max = std::max(s->kernel_s_max, k_ms * 1e-3);
+    s->copy_s_sum += c_ms * 1e-3;
+    s->copy_s_max = std::max(s->copy_s_max, c_ms * 1e-3);
+  } else {
+    cudaGetLastError();
+  }
+  for (cudaEvent_t& ev : f.t) s->timing_pool.push_back(ev);
+}
+
 void admit(rlxpp_server* s) {
   while (!s->waiting.empty()) {
     Req* r = s->waiting.front();
@@ -186,6 +217,11 @@ rlxpp_status dispatch(rlxpp_server* s) {
       s->batch[k] = rlxpp_request{q.stream, q.skip, q.pos, q.kind, q.count,
                                   q.offset / (q.kind == RLXPP_KIND_F64 ? 8 : 4)};
     }
+    InFlight f{si, {}, {}};
+    for (cudaEvent_t& ev : f.t)
+      if (rlxpp_status es = get_timing_event(s, ev)) return es;
+    cudaError_t et = cudaEventRecord(f.t[0], st);
+    if (et != cudaSuccess) return cuda_fail(et, "server event record");
     const double l0 = now_s();
     if (rlxpp_status rs = rlxpp_draw_requests(s->gen, s->batch.data(), nb, reinterpret_cast<uint32_t*>(s->dev),
                                               reinterpret_cast<double*>(s->dev), 0, st))
@@ -193,7 +229,8 @@ rlxpp_status dispatch(rlxpp_server* s) {
     const double dl = now_s() - l0;
     s->max_launch_s = std::max(s->max_launch_s, dl);
     if (dl >= 1e-3) ++s->slow_launches;
-    InFlight f{si, {}};
+    et = cudaEventRecord(f.t[1], st);
+    if (et != cudaSuccess) return cuda_fail(et, "server event record");
     auto close_group = [&](std::vector<Req*>&& members) -> rlxpp_status {
       cudaEvent_t ev;
       if (rlxpp_status es = get_event(s, ev)) return es;
@@ -230,6 +267,8 @@ rlxpp_status dispatch(rlxpp_server* s) {
     } else {
       if (rlxpp_status gs = close_group(std::move(reqs))) return gs;
     }
+    et = cudaEventRecord(f.t[2], st);  // after every copy of the batch
+    if (et != cudaSuccess) return cuda_fail(et, "server event record");
     const double t = now_s() - s->t0;
     for (const Group& g : f.groups)
       for (Req* r : g.reqs) {
@@ -271,9 +310,12 @@ rlxpp_status complete(rlxpp_server* s, bool wait_first) {
       }
       s->event_pool.push_back(g.ev);
     }
-    if (f.groups.empty())
+    if (f.groups.empty()) {
+      // the batch's last group is done; its timing events follow within the stream
+      if (cudaEventSynchronize(f.t[2]) == cudaSuccess) record_batch_times(s, f);
+      else for (cudaEvent_t& ev : f.t) s->timing_pool.push_back(ev);
       s->free_streams.push_back(f.si);
-    else
+    } else
       keep.push_back(std::move(f));
   }
   s->inflight = std::move(keep);
@@ -295,6 +337,9 @@ void free_server(rlxpp_server* s) {
   for (auto& f : s->inflight)
     for (auto& g : f.groups) cudaEventDestroy(g.ev);
   for (auto ev : s->event_pool) cudaEventDestroy(ev);
+  for (auto& f : s->inflight)
+    for (auto ev : f.t) cudaEventDestroy(ev);
+  for (auto ev : s->timing_pool) cudaEventDestroy(ev);
   for (auto st : s->streams)
     if (st) cudaStreamDestroy(st);
   cudaFree(s->dev);
@@ -427,6 +472,11 @@ rlxpp_status rlxpp_server_stats(const rlxpp_server* s, rlxpp_server_state* out) 
   out->cancelled = s->n_cancelled;
   out->max_launch_us = (uint64_t)(s->max_launch_s * 1e6);
   out->slow_launches = s->slow_launches;
+  out->batches_timed = s->batches_timed;
+  out->kernel_us_sum = (uint64_t)(s->kernel_s_sum * 1e6);
+  out->kernel_us_max = (uint64_t)(s->kernel_s_max * 1e6);
+  out->copy_us_sum = (uint64_t)(s->copy_s_sum * 1e6);
+  out->copy_us_max = (uint64_t)(s->copy_s_max * 1e6);
   return RLXPP_OK;
 }
 

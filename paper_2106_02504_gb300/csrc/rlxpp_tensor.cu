@@ -72,7 +72,8 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
   return ok != 0;
 }
 __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
-  for (uint64_t i = 0; i < kWaitLimit; ++i) {
+  if (mbar_try_wait(bar, parity)) return true;  // the common case, outside the loop
+  for (uint32_t i = 0; i < (uint32_t)kWaitLimit; ++i) {
     if (mbar_try_wait(bar, parity)) return true;
     if (i > 64) __nanosleep(64);
   }
@@ -1054,6 +1055,222 @@ __global__ void __launch_bounds__(kTcRows, 4)
   }
 }
 
+// ---- value-writing draws with the A operand in tensor memory -------------------------
+// X (18 limbs) -> its 72 bytes as fp16 subnormals (each pair of bytes one byte permute
+// with zeros, as write_x_row forms them) into this thread's lane of the A columns.
+// Every thread of the warp calls it (tcgen05.st is warp-wide).
+__device__ __forceinline__ void write_x_tmem(uint32_t lane_taddr, const uint32_t X[kLimbs]) {
+  uint32_t w[36];
+#pragma unroll
+  for (int c = 0; c < kLimbs; ++c) {
+    w[2 * c] = __byte_perm(X[c], 0u, 0x4140u);
+    w[2 * c + 1] = __byte_perm(X[c], 0u, 0x4342u);
+  }
+  tmem_st32(lane_taddr + kTmA, w);
+  tmem_st4(lane_taddr + kTmA + 32, w + 32);
+}
+
+struct ValuesShared {
+  uint64_t bar;                 // product completion
+  uint32_t taddr;               // TMEM base
+  uint32_t abort;               // a wait for the product timed out
+  unsigned long long iters;     // refills of the tile
+  uint32_t pos0;                // read position of the tile's first stream at entry
+};
+// Shared memory: the level's matrix, the shared words, two [128][96 B] staging boxes;
+// 48 KB in all, so that at most four CTAs (4 x 128 TMEM columns) share an SM.
+constexpr int kValuesBox = kTcRows * kStageBytes;  // 12 KB
+constexpr int kValuesSmem = 48 * 1024;
+static_assert(kBRegion + 1024 + 2 * kValuesBox <= kValuesSmem, "value draw shared memory");
+
+// Value-writing draws (u24, f32, f64) with one count for every stream and the output as
+// a [n][count] tensor (tmap), on one-tile CTAs with the A operand in TMEM.  Same
+// semantics as k_draw_tc.  The refill loop is the fused draw's: wait for the product,
+// form X and write it as the next operand row (every thread), one CTA barrier, thread 0
+// issues the next product, then every thread converts X to RANLUX numbers and stages
+// its block.  When every live stream of the tile starts at the tile's first position
+// (then they move in step), the blocks of a refill leave as one TMA tensor store of the
+// [128][96 B] staging box, issued by thread 0 after the next barrier; two boxes
+// alternate, and thread 0 waits for a store to have read its box before the barrier
+// after which that box is written again.  Tiles out of step write each stream's values
+// from registers.
+template <int Kind>
+__global__ void __launch_bounds__(kTcRows, 4)
+    k_values_tc(const DrawArgs a, const __half* __restrict__ bimg, const __grid_constant__ CUtensorMap tmap) {
+  extern __shared__ __align__(1024) unsigned char smem[];
+  const int tid = threadIdx.x;
+  ValuesShared* sh = reinterpret_cast<ValuesShared*>(smem + kBRegion);
+  unsigned char* box0 = smem + kBRegion + 1024;
+  const __half* bmat = tc_bmat(smem);
+  {
+    const uint4* src = reinterpret_cast<const uint4*>(bimg);
+    uint4* dst = reinterpret_cast<uint4*>(tc_bmat(smem));
+    for (int w = tid; w < kBBytes / 16; w += kTcRows) dst[w] = src[w];
+  }
+  if (tid == 0) {
+    mbar_init(&sh->bar, 1);
+    fence_barrier_init();
+    sh->abort = 0;
+  }
+  if (tid < 32) tmem_alloc(&sh->taddr, kTmCols);
+  fence_proxy_async_smem();
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t taddr = sh->taddr;
+  const uint32_t lane_taddr = taddr + ((uint32_t)((tid / 32) * 32) << 16);
+  {
+    const uint32_t cst[4] = {0x3C006800u, 0u, 0u, 0u};  // 2048 and 1 at k = 72, 73
+    tmem_st4(lane_taddr + kTmA + 36, cst);
+  }
+  const uint32_t b0 = smem_addr(bmat);
+
+  constexpr int need = (Kind == kDrawU24 || Kind == kDrawF32) ? 1 : 2;
+  constexpr int per_block = kWords / need;
+  const StateView& s = a.s;
+  const uint64_t i = (uint64_t)blockIdx.x * kTcRows + tid;
+  const bool live = i < s.n;
+  const int64_t cnt = live ? a.count_each : 0, base = (int64_t)i * a.count_each;
+  uint32_t pos = kWords, c = 0, lvl = 0;
+  uint32_t D[kLimbs];
+#pragma unroll
+  for (int k = 0; k < kLimbs; ++k) D[k] = 0;
+  if (live) {
+    const uint32_t meta = s.meta[i];
+    pos = meta_pos(meta);
+    c = meta_carry(meta);
+    lvl = meta_level(meta);
+    load_state_D(s, i, D);
+  }
+  Consumer<Kind> out;
+  out.out = static_cast<decltype(out.out)>(a.out);
+  const uint32_t pos_in = pos;
+  int64_t k = 0;
+  if (live && cnt > 0 && pos + need <= (uint32_t)kWords) {  // head of the current block
+    const int64_t room = (kWords - pos) / need;
+    const int64_t h = cnt < room ? cnt : room;
+#pragma unroll
+    for (int w = 0; w + need <= kWords; ++w) {
+      const int d = w - (int)pos;
+      if (d >= 0 && d % need == 0 && d / need < h) out.value_at_word(D, w, base + d / need);
+    }
+    k = h;
+    pos += (uint32_t)(h * need);
+  }
+  // tile-wide stores when every live stream starts at the tile's first position (with
+  // one count for all they then stay in step) and the first column after the head is
+  // 16-byte aligned; thread 0 (live whenever any thread is) issues them
+  if (tid == 0) sh->pos0 = pos_in;
+  __syncthreads();
+  const bool tma =
+      __syncthreads_and(!live || (pos_in == sh->pos0 && ((k * (int64_t)(need * 4)) & 15) == 0)) != 0;
+  int64_t left = live && k < cnt ? (cnt - k + per_block - 1) / per_block : 0;
+  const int64_t iters = cta_max(left, &sh->iters);
+  const int y0 = (int)((uint64_t)blockIdx.x * kTcRows);
+  uint32_t X[kLimbs];
+  to_lcg(D, c, X);
+  write_x_tmem(lane_taddr, X);
+  tmem_wait_st();
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (iters > 0 && tid == 0) tc_issue_tm(taddr, b0, &sh->bar);
+  uint32_t phase = 0, c_fin = c;
+  bool ok = true, inflight = iters > 0, stored = false;
+  int box_x[2] = {0, 0};  // thread 0: first column of the block staged in each box
+  bool pending = false;   // thread 0: a staged box waits for its store
+  for (int64_t it = 0; it < iters; ++it) {
+    bool got = mbar_wait_bounded(&sh->bar, phase);
+    got = __all_sync(0xFFFFFFFFu, got);  // the warp stays converged for the TMEM accesses
+    if (got) {
+      inflight = false;
+      phase ^= 1u;
+      tc_fence_after();
+      uint32_t col[72];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) tmem_ld16(lane_taddr + 16 * q, col + 16 * q);
+      tmem_ld8(lane_taddr + 64, col + 64);
+      tmem_wait_ld();
+      tc_fold_common(col, X);
+      __syncwarp();  // reconverged after the rare fold, before the warp-wide store
+      write_x_tmem(lane_taddr, X);
+      tmem_wait_st();
+    } else {
+      sh->abort = 1u;
+    }
+    if (tma && tid == 0) bulk_wait_read_all();  // the last store has read its box
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (sh->abort) {
+      ok = false;
+      break;
+    }
+    if (it + 1 < iters) {
+      if (tid == 0) tc_issue_tm(taddr, b0, &sh->bar);
+      inflight = true;
+    }
+    if (tid == 0 && pending) {  // the blocks staged before this barrier
+      asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%1, %2}], [%3];" ::"l"(
+                       reinterpret_cast<uint64_t>(&tmap)),
+                   "r"(box_x[(it - 1) & 1]), "r"(y0), "r"(smem_addr(box0 + ((it - 1) & 1) * kValuesBox))
+                   : "memory");
+      asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+      pending = false;
+    }
+    if (left > 0) {  // this stream's block, while the next product computes
+      to_ranlux(X, D);
+      const int64_t rem = cnt - k;
+      if (tma) {  // the whole block into this thread's row of the box; past the count it is clipped
+        uint4 v[6];
+        block_values<Kind>(D, v);
+        uint4* row = reinterpret_cast<uint4*>(box0 + (it & 1) * kValuesBox + tid * kStageBytes);
+#pragma unroll
+        for (int q = 0; q < 6; ++q) row[q] = v[q];
+        fence_proxy_async_smem();
+        if (tid == 0) {
+          box_x[it & 1] = (int)k;
+          pending = true;
+        }
+      } else if (rem >= per_block) {
+        out.block(D, base + k);
+      } else {
+        out.partial(D, base + k, rem);
+      }
+      if (rem >= per_block) {
+        k += per_block;
+        pos = kWords;
+      } else {
+        k = cnt;
+        pos = (uint32_t)(rem * need);
+      }
+      if (--left == 0) {
+        c_fin = carry_of(X, D);
+        store_state_D(s, i, D);
+        stored = true;
+      }
+    }
+  }
+  if (ok && tma && iters > 0) {  // the last staged box
+    __syncthreads();
+    if (tid == 0 && pending) {
+      asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%1, %2}], [%3];" ::"l"(
+                       reinterpret_cast<uint64_t>(&tmap)),
+                   "r"(box_x[(iters - 1) & 1]), "r"(y0), "r"(smem_addr(box0 + ((iters - 1) & 1) * kValuesBox))
+                   : "memory");
+      asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+    }
+  }
+  if (tid == 0) bulk_wait_all();  // every store of this CTA is done
+  if (live && (ok || stored)) s.meta[i] = meta_pack(pos, c_fin, lvl);
+  if (!ok && tid == 0) atomicCAS(s.status, 0, (int)RLXPP_ERR_TIMEOUT);
+  if (inflight) (void)mbar_wait_bounded(&sh->bar, phase);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (tid < 32) tmem_dealloc(taddr, kTmCols);
+}
+
 // Emits the unread part of the current block for a value kind (f64 or u24).
 __device__ __forceinline__ void emit_head(bool f64, const BatchArgs& b, const uint32_t D[kLimbs], uint32_t& pos,
                                           int64_t cnt, int64_t base, int64_t& k) {
@@ -1441,6 +1658,15 @@ cudaError_t launch_tc_kind(const DrawArgs& a, const __half* bimg, cudaStream_t s
   std::memset(&map, 0, sizeof(map));
   int use_tma = 0;
   if constexpr (kValues) use_tma = encode_output_map<Kind>(a, &map) ? 1 : 0;
+  if constexpr (kValues) {
+    if (use_tma) {  // one count for all and a tensor map: one-tile CTAs, A operand in TMEM
+      cudaError_t e = cudaFuncSetAttribute(k_values_tc<Kind>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           kValuesSmem);
+      if (e != cudaSuccess) return e;
+      k_values_tc<Kind><<<(unsigned)tiles, kTcRows, kValuesSmem, st>>>(a, bimg, map);
+      return cudaGetLastError();
+    }
+  }
   auto kern = (kValues && !use_tma) ? k_draw_tc<Kind, T, kValues> : k_draw_tc<Kind, T, false>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes);
   if (e != cudaSuccess) return e;

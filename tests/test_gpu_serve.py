@@ -152,7 +152,12 @@ def test_native_serving_trace_matches_oracle(native):
     arr, stream, counts, is_f64 = W.serving_trace(400, rate_hz=4000, n_resident=n_res, lo=100, hi=20000, seed=7)
     srv = NativeServer(n_res, pool_bytes=1 << 20, n_cuda_streams=3, max_batch=16, keep_results=True)
     lat = srv.run_trace(arr, stream, counts, is_f64)
-    assert np.all(lat > 0) and srv.stats()["done"] == 400
+    st = srv.stats()
+    assert np.all(lat > 0) and st["done"] == 400
+    # every batch's device times were read: the request kernel and the copies took time,
+    # and no batch's device time exceeds the longest request latency
+    assert st["batches_timed"] >= 400 // 16 and st["kernel_us_sum"] > 0 and st["copy_us_sum"] > 0
+    assert st["kernel_us_max"] + st["copy_us_max"] <= 1e6 * float(lat.max()) + 1000
     kinds = is_f64.astype(int)
     by_stream = {}
     seeds = np.arange(1, n_res + 1, dtype=np.uint64)
