@@ -174,6 +174,10 @@ void free_gen(rlxpp_gen* g) {
   cudaFree(g->status);
   cudaFree(g->tc_matrix);
   cudaFree(g->tc_matrix_d);
+  for (auto& u : g->upload) {
+    if (u.ev) cudaEventDestroy(u.ev);
+    if (u.host) cudaFreeHost(u.host);
+  }
   cudaFree(g->host_stage);
   if (g->chunk_ready) cudaEventDestroy(g->chunk_ready);
   if (g->host_done) cudaEventDestroy(g->host_done);

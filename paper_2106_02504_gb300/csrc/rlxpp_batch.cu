@@ -217,6 +217,38 @@ void free_plan(rlxpp_plan* p, cudaStream_t st, bool async) {
   delete p;
 }
 
+// One of the handle's two page-locked upload buffers, at least `bytes` long.  The buffer
+// last used two uploads ago is reused once its copies are done (they were queued long
+// before, so this rarely waits); it grows by reallocation when too small.
+cudaError_t pinned_upload_buffer(rlxpp_gen* g, size_t bytes, void** out) {
+  rlxpp_gen::Upload& u = g->upload[g->upload_next];
+  if (u.ev) {
+    cudaError_t e = cudaEventSynchronize(u.ev);
+    if (e != cudaSuccess) return e;
+  } else {
+    cudaError_t e = cudaEventCreateWithFlags(&u.ev, cudaEventDisableTiming);
+    if (e != cudaSuccess) return e;
+  }
+  if (u.bytes < bytes) {
+    if (u.host) cudaFreeHost(u.host);
+    u.host = nullptr;
+    u.bytes = 0;
+    const size_t want = std::max<size_t>(bytes + bytes / 2, 1 << 16);
+    cudaError_t e = cudaMallocHost(&u.host, want);
+    if (e != cudaSuccess) return e;
+    u.bytes = want;
+  }
+  *out = u.host;
+  return cudaSuccess;
+}
+
+// The copies from the current upload buffer are queued on st: mark its reuse point.
+cudaError_t pinned_upload_done(rlxpp_gen* g, cudaStream_t st) {
+  rlxpp_gen::Upload& u = g->upload[g->upload_next];
+  g->upload_next ^= 1;
+  return cudaEventRecord(u.ev, st);
+}
+
 // stream_ordered: allocate and upload on `st` (cudaMallocAsync / cudaMemcpyAsync), so
 // that planning does not synchronise the device; otherwise plain cudaMalloc/cudaMemcpy.
 rlxpp_status plan_impl(rlxpp_gen* g, const rlxpp_request* reqs, uint64_t n_reqs, uint32_t flags,
@@ -412,9 +444,27 @@ rlxpp_status plan_impl(rlxpp_gen* g, const rlxpp_request* reqs, uint64_t n_reqs,
   if (e == cudaSuccess && !tiles.empty()) e = alloc((void**)&p->tiles, sizeof(TcTile) * tiles.size());
   std::vector<uint64_t> rs(nr, 0);
   for (uint64_t r = 0; r < n_reqs; ++r) rs[r] = reqs[r].stream;
-  if (e == cudaSuccess && !items.empty()) e = upload(p->items, items.data(), sizeof(Item) * items.size());
-  if (e == cudaSuccess) e = upload(p->req_stream, rs.data(), sizeof(uint64_t) * rs.size());
-  if (e == cudaSuccess && !tiles.empty()) e = upload(p->tiles, tiles.data(), sizeof(TcTile) * tiles.size());
+  const size_t b_items = sizeof(Item) * items.size(), b_rs = sizeof(uint64_t) * rs.size(),
+               b_tiles = sizeof(TcTile) * tiles.size();
+  void* pinned = nullptr;
+  if (e == cudaSuccess && stream_ordered) e = pinned_upload_buffer(g, b_items + b_rs + b_tiles, &pinned);
+  if (pinned) {
+    // stream-ordered uploads from page-locked memory never wait on the host for staging
+    // (a pageable source can, while the copy engines are busy)
+    unsigned char* h = static_cast<unsigned char*>(pinned);
+    if (b_items) std::memcpy(h, items.data(), b_items);
+    std::memcpy(h + b_items, rs.data(), b_rs);
+    if (b_tiles) std::memcpy(h + b_items + b_rs, tiles.data(), b_tiles);
+    if (e == cudaSuccess && b_items) e = cudaMemcpyAsync(p->items, h, b_items, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(p->req_stream, h + b_items, b_rs, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess && b_tiles)
+      e = cudaMemcpyAsync(p->tiles, h + b_items + b_rs, b_tiles, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = pinned_upload_done(g, st);
+  } else {
+    if (e == cudaSuccess && b_items) e = upload(p->items, items.data(), b_items);
+    if (e == cudaSuccess) e = upload(p->req_stream, rs.data(), b_rs);
+    if (e == cudaSuccess && b_tiles) e = upload(p->tiles, tiles.data(), b_tiles);
+  }
   if (e != cudaSuccess) {
     free_plan(p, st, stream_ordered);
     return set_last_error(e == cudaErrorMemoryAllocation ? RLXPP_ERR_NOMEM : RLXPP_ERR_CUDA,

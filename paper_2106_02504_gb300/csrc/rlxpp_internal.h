@@ -143,6 +143,13 @@ struct rlxpp_gen {
   uint32_t path = 0;                       // RLXPP_PATH_IMAD or RLXPP_PATH_TENSOR
   void* tc_matrix = nullptr;               // [n_levels] tensor-path matrices
   void* tc_matrix_d = nullptr;             // [n_levels] the same for (D, c) operand rows
+  struct Upload {                          // page-locked staging of request work lists
+    void* host = nullptr;
+    size_t bytes = 0;
+    cudaEvent_t ev = nullptr;              // its last copies are done
+  };
+  Upload upload[2];
+  int upload_next = 0;
   rlxpp::StateView view() const { return rlxpp::StateView{D, meta, n, n, lux, table, status}; }
 };
 

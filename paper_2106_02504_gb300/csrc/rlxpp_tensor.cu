@@ -1293,27 +1293,45 @@ __device__ __forceinline__ void emit_head(bool f64, const BatchArgs& b, const ui
 }
 
 // Batched requests on the tensor cores, every luxury level in one launch.  Persistent
-// CTAs (one tile-group each) take tiles from the counter: a tile is up to 128
-// consecutive chunks of one level of the (per level, longest-first) list, and the tile
-// table itself is ordered longest first across levels.  A CTA loads the level's matrix
-// into shared memory when it changes from the previous tile's; then every thread jumps
-// its chunk to its start block (table products on the integer pipe) and the tile
-// refills in lock step as in k_draw_tc until every chunk is done.  Chunks of a tile have
-// similar lengths, so little work is lost to the longest one.
+// one-tile CTAs take tiles from the counter: a tile is up to 128 consecutive chunks of
+// one level of the (per level, longest-first) list, and the tile table itself is
+// ordered longest first across levels.  A CTA loads the level's matrix into shared
+// memory when it changes from the previous tile's; then every thread jumps its chunk to
+// its start block (table products on the integer pipe) and the tile refills in lock step
+// with the fused draw's pipelined loop (operand rows in TMEM, one barrier per refill,
+// the next product issued before the blocks are converted and written) until its
+// longest chunk is done.  Chunks of a tile have similar lengths, so little work is lost
+// to the longest one.  Chunks write to unrelated places: each lane stages its full
+// block, and the warp writes its 32 staged blocks cooperatively.
 __global__ void __launch_bounds__(kTcRows, 4)
     k_requests_tc(const BatchArgs b, const Item* __restrict__ items, const TcTile* __restrict__ tiles,
                   uint64_t n_tiles, const __half* __restrict__ bimg_all, WorkCounters* wc) {
   extern __shared__ __align__(1024) unsigned char smem[];
   __shared__ unsigned long long tile_s;
-  const TcGroup G = tc_group(smem, true);  // one group per CTA
-  const __half* bmat = tc_bmat(smem);
-  uint4* slot = reinterpret_cast<uint4*>(G.stage + G.t * kStageBytes);
-  const unsigned char* wstage = G.stage + (G.t & ~31) * kStageBytes;  // this warp's 32 slots
   const int tid = threadIdx.x;
-  tc_setup(smem, G, nullptr, 1);
-  const uint32_t taddr = tc_tmem(smem, G);
+  ValuesShared* sh = reinterpret_cast<ValuesShared*>(smem + kBRegion);
+  unsigned char* stage = smem + kBRegion + 1024;
+  uint4* slot = reinterpret_cast<uint4*>(stage + tid * kStageBytes);
+  const unsigned char* wstage = stage + (tid & ~31) * kStageBytes;  // this warp's 32 slots
+  const __half* bmat = tc_bmat(smem);
+  if (tid == 0) {
+    mbar_init(&sh->bar, 1);
+    fence_barrier_init();
+    sh->abort = 0;
+  }
+  if (tid < 32) tmem_alloc(&sh->taddr, kTmCols);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t taddr = sh->taddr;
+  const uint32_t lane_taddr = taddr + ((uint32_t)((tid / 32) * 32) << 16);
+  {
+    const uint32_t cst[4] = {0x3C006800u, 0u, 0u, 0u};  // 2048 and 1 at k = 72, 73
+    tmem_st4(lane_taddr + kTmA + 36, cst);
+  }
+  const uint32_t b0 = smem_addr(bmat);
   uint32_t phase = 0;
-  bool ok = true;
+  bool ok = true, inflight = false;
   uint32_t loaded = 0xFFFFFFFFu;  // level whose matrix is in shared memory
   while (ok) {
     if (tid == 0) tile_s = atomicAdd(&wc->next, 1ull);
@@ -1326,7 +1344,8 @@ __global__ void __launch_bounds__(kTcRows, 4)
       const uint4* src = reinterpret_cast<const uint4*>(bimg_all + (size_t)tile.level * (kBBytes / 2));
       uint4* dst = reinterpret_cast<uint4*>(tc_bmat(smem));
       for (int w = tid; w < kBBytes / 16; w += kTcRows) dst[w] = src[w];
-      loaded = tile.level;  // made visible to the tensor core by the publishing fence
+      fence_proxy_async_smem();  // -> visible to the tensor core after the next barrier
+      loaded = tile.level;
     }
     const bool live = (uint32_t)tid < tile.n;
     Item it{};
@@ -1351,32 +1370,62 @@ __global__ void __launch_bounds__(kTcRows, 4)
     }
     const bool f64 = (it.info & 1u) != 0;
     const int64_t cnt = live ? it.count : 0, base = (int64_t)it.out;
+    const int64_t per = f64 ? kDoubles : kWords;
     uint32_t pos = live ? (it.info >> 8) & 0xFFu : (uint32_t)kWords;
     int64_t k = 0;
     emit_head(f64, b, D, pos, cnt, base, k);
-    bool mine = live && k < cnt, refilled = false;
+    int64_t left = live && k < cnt ? (cnt - k + per - 1) / per : 0;
+    const bool refilled = left > 0;
+    const int64_t iters = cta_max(left, &sh->iters);
     uint32_t X[kLimbs];
     to_lcg(D, c, X);
-    while (true) {
-      write_x_row(G.tile, G.t, X);
-      if (!tc_publish(G, mine)) break;  // every chunk of the tile is done
-      uint32_t col[72];
-      if (!tc_refill_after_publish(G, bmat, taddr, phase, col)) {
+    write_x_tmem(lane_taddr, X);
+    tmem_wait_st();
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (iters > 0) {
+      if (tid == 0) tc_issue_tm(taddr, b0, &sh->bar);
+      inflight = true;
+    }
+    for (int64_t r = 0; r < iters; ++r) {
+      bool got = mbar_wait_bounded(&sh->bar, phase);
+      got = __all_sync(0xFFFFFFFFu, got);  // the warp stays converged for the TMEM accesses
+      uint32_t Xn[kLimbs];
+      if (got) {
+        inflight = false;
+        phase ^= 1u;
+        tc_fence_after();
+        uint32_t col[72];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) tmem_ld16(lane_taddr + 16 * q, col + 16 * q);
+        tmem_ld8(lane_taddr + 64, col + 64);
+        tmem_wait_ld();
+        tc_fold_common(col, Xn);
+        __syncwarp();  // reconverged after the rare fold, before the warp-wide store
+        write_x_tmem(lane_taddr, Xn);
+        tmem_wait_st();
+      } else {
+        sh->abort = 1u;
+      }
+      tc_fence_before();
+      __syncthreads();
+      tc_fence_after();
+      if (sh->abort) {
         ok = false;
         break;
       }
-      uint32_t Xn[kLimbs];
-      columns_to_x(col, Xn);
+      if (r + 1 < iters) {
+        if (tid == 0) tc_issue_tm(taddr, b0, &sh->bar);
+        inflight = true;
+      }
       uint64_t dst = 0;  // destination of this lane's full block, if it has one
-      if (mine) {
+      if (left > 0) {    // this chunk's block, while the next product computes
 #pragma unroll
         for (int q = 0; q < kLimbs; ++q) X[q] = Xn[q];
         to_ranlux(X, D);
-        refilled = true;
-        const int64_t per = f64 ? kDoubles : kWords;
         const int64_t rem = cnt - k;
         if (rem >= per) {
-          // chunks write to unrelated places: staged here, written by the whole warp below
           uint4 v[6];
           if (f64)
             block_values<kDrawF64>(D, v);
@@ -1402,7 +1451,7 @@ __global__ void __launch_bounds__(kTcRows, 4)
           }
           k = cnt;
         }
-        mine = k < cnt;
+        --left;
       }
       warp_store_blocks(wstage, dst);
     }
@@ -1415,9 +1464,12 @@ __global__ void __launch_bounds__(kTcRows, 4)
       b.s.meta[st] = meta_pack(pos, c, lvl);
     }
   }
-  bulk_wait_all();
   if (!ok && tid == 0) atomicCAS(b.s.status, 0, (int)RLXPP_ERR_TIMEOUT);
-  tc_teardown(smem, G, !ok, phase, 1);
+  if (inflight) (void)mbar_wait_bounded(&sh->bar, phase);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (tid < 32) tmem_dealloc(taddr, kTmCols);
   finish_cta(wc);
 }
 
