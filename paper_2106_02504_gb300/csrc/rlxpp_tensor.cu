@@ -964,8 +964,7 @@ __global__ void __launch_bounds__(kTcRows, 4)
   // refills of this stream: full blocks, and a last partial one of `tail` values
   const int64_t nref = live && rest > 0 ? (rest + kDoubles - 1) / kDoubles : 0;
   const uint32_t tail = live ? (uint32_t)(rest % kDoubles) : 0u;
-  int64_t left = nref;
-  const int64_t iters = cta_max(left, &sh->iters);
+  const int64_t iters = cta_max(nref, &sh->iters);
   write_d_tmem(lane_taddr, D, c);
   tmem_wait_st();
   tc_fence_before();
@@ -974,10 +973,17 @@ __global__ void __launch_bounds__(kTcRows, 4)
   if (iters > 0 && tid == 0) tc_issue_tm(taddr, b0, &sh->bar);
   uint32_t phase = 0, c_fin = c;
   bool ok = true, inflight = iters > 0, stored = false;
-  int64_t it = 0;
-  while (ok && it < iters) {
-    const int64_t it_begin = it, it_end = iters - it > kFusedFlush ? it + kFusedFlush : iters;
-    for (; it < it_end; ++it) {
+  // refills in chunks of at most kFusedFlush, counted in 32 bits within a chunk
+  for (int64_t it0 = 0; ok && it0 < iters;) {
+    const uint32_t n_in = (uint32_t)(iters - it0 > kFusedFlush ? kFusedFlush : iters - it0);
+    const bool more_after = it0 + n_in < iters;
+    // this stream's refills in the chunk, the one of its last block, and the first whose
+    // product carries a block of this stream already drawn whole (not its first block)
+    const int64_t rem_ref = nref - it0;
+    const uint32_t n_mine = rem_ref <= 0 ? 0u : (rem_ref >= (int64_t)n_in ? n_in : (uint32_t)rem_ref);
+    const uint32_t j_last = rem_ref >= 1 && rem_ref <= (int64_t)n_in ? (uint32_t)(rem_ref - 1) : 0xFFFFFFFFu;
+    const uint32_t j_sums = it0 == 0 ? 1u : 0u;
+    for (uint32_t j = 0; j < n_in; ++j) {
       bool got = mbar_wait_bounded(&sh->bar, phase);
       got = __all_sync(0xFFFFFFFFu, got);  // the warp stays converged for the TMEM accesses
       uint32_t sums[6] = {0, 0, 0, 0, 0, 0};
@@ -1009,29 +1015,27 @@ __global__ void __launch_bounds__(kTcRows, 4)
         ok = false;
         break;
       }
-      if (it + 1 < iters) {
+      if (j + 1 < n_in || more_after) {
         if (tid == 0) tc_issue_tm(taddr, b0, &sh->bar);
         inflight = true;
       }
-      if (left > 0) {  // while the next product computes
-        if (it > 0) acc.columns(sums);  // the previous block of this stream, all of it drawn
-        if (left > 1) {
+      if (j < n_mine) {  // while the next product computes
+        if (j >= j_sums) acc.columns(sums);  // the previous block of this stream, all of it drawn
+        if (j != j_last) {
           acc.hist_block(D);  // its sums arrive with the next product
         } else {
           const uint32_t nv = tail ? tail : (uint32_t)kDoubles;
 #pragma unroll
-          for (int j = 0; j < kDoubles; ++j)
-            if (j < (int)nv) acc.take(bits48(D, j));
+          for (int v = 0; v < kDoubles; ++v)
+            if (v < (int)nv) acc.take(bits48(D, v));
           store_state_D(s, i, D);
           c_fin = c;
           stored = true;
         }
-        --left;
       }
     }
-    // this thread's column sums of iterations 1 .. nref - 1 within [it_begin, it_end)
-    const int64_t lo = it_begin > 1 ? it_begin : 1, hi = (it_end < nref ? it_end : nref) - 1;
-    acc.flush(hi >= lo ? (uint32_t)(hi - lo + 1) : 0u);
+    acc.flush(n_mine > j_sums ? n_mine - j_sums : 0u);
+    it0 += n_in;
   }
   if (nref > 0) pos = tail ? 2u * tail : (uint32_t)kWords;
   if (live && (ok || stored)) s.meta[i] = meta_pack(pos, c_fin, lvl);

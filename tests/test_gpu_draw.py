@@ -346,6 +346,29 @@ def test_sum_hist(native, path):
     assert_states(native, g, ref)
 
 
+@pytest.mark.parametrize("p", [24, 223, 389, 2048])
+def test_sum_hist_levels_and_positions(native, p, path):
+    """The fused consumer at the four mixed-batch levels (the tensor path's matrix for
+    operand rows that hold the RANLUX numbers, with its block-sum columns, is built per
+    level) from streams left at every read position by a ragged u24 draw, with a count
+    that ends in a partial block; sums, histogram and final states against the oracle."""
+    seeds = W.random_seeds(N, 77 + p)
+    g = make(native, seeds, levels=(p,), path=path)
+    counts = (np.arange(N) * 7) % 29
+    offs = np.concatenate([[0], np.cumsum(counts)[:-1]]).astype(np.int64)
+    out = torch.zeros(int(counts.sum()) + 1, dtype=torch.int32, device="cuda")
+    g.draw_u24(out, 0, torch.from_numpy(counts.astype(np.int64)).cuda(), torch.from_numpy(offs).cuda())
+    sums = torch.zeros(N, dtype=torch.int64, device="cuda")
+    hist = torch.zeros(256, dtype=torch.int64, device="cuda")
+    g.draw_f64_sum_hist(1001, sums, hist)
+    ref = StreamSet.from_seeds(seeds, p)
+    ref.draw_ragged(counts, S.KIND_U24)
+    wsums, whist = ref.sum_hist(1001)
+    assert np.array_equal(sums.cpu().numpy().view(np.uint64), wsums)
+    assert np.array_equal(hist.cpu().numpy().view(np.uint64), whist)
+    assert_states(native, g, ref)
+
+
 def test_skip(native):
     seeds = W.consecutive_seeds(N)
     p = 2048
