@@ -166,6 +166,18 @@ rlxpp_status rlxpp_draw_normal_f64(rlxpp_gen* gen, const int64_t* counts, const 
 rlxpp_status rlxpp_draw_exp_f64(rlxpp_gen* gen, const int64_t* counts, const int64_t* offsets,
                                 int64_t count_each, double* out, void* cuda_stream);
 
+/* Draw raw LCG doubles, for comparison only (Sec. 2.3 names this form, Sibidanov's,
+ * only to replace it by the RANLUX numbers: its top bits lean towards 0 because the
+ * state is below m).  Each refill gives 11 values v_k 2^-52 with
+ * v_k = (X >> 52 k) mod 2^52, k = 0 .. 10, of the new LCG state X, low bits first (the
+ * top 4 bits of X are not used).  A stream's draw of n values starts with a refill
+ * (the unread part of its current block is skipped), takes ceil(n / 11) refills, drops
+ * the values of the last one past n and leaves the stream at the end of that block
+ * (read position 24); n = 0 leaves it unchanged.  Runs on the integer pipe on every
+ * path.  double out, same layout rules as rlxpp_draw_u24. */
+rlxpp_status rlxpp_draw_raw_f64(rlxpp_gen* gen, const int64_t* counts, const int64_t* offsets,
+                                int64_t count_each, double* out, void* cuda_stream);
+
 /* Skip random numbers without generating them (Sec. 2.4), counted in values of one
  * kind: stream i moves exactly as if it had drawn n_values[i] values of `kind`
  * (RLXPP_KIND_U24, RLXPP_KIND_F64 or RLXPP_KIND_F32) and discarded them: the rest of

@@ -34,7 +34,9 @@ Readings where the paper is silent:
 * seeds are 1 .. 2^64 - 1;
 * Gaussian values come from consecutive pairs of the stream's doubles by the
   Box-Muller transform (Box and Muller, Ann. Math. Statist. 29, 1958), u1 = 1 - d_a so
-  that ln u1 is finite; n values take 2 ceil(n / 2) doubles.
+  that ln u1 is finite; n values take 2 ceil(n / 2) doubles;
+* raw LCG doubles (for comparison only) take 11 x 52 bits of each new LCG state, low
+  bits first (Stream.draw_raw52).
 
 Parity pins for every function are in ``tests/test_oracle_pins.py`` (SWB brute force,
 closed forms, invariants and edge cases).
@@ -55,6 +57,9 @@ WORDS = LAG_R                   # 24 RANLUX numbers per block
 MASK24 = BASE - 1
 MASK48 = (1 << 48) - 1
 SEED_SHIFT = 96                 # seed s = 2^96 s luxury advances from the state 1
+RAW_BITS = 52                   # raw LCG doubles: 52 bits of the state each
+RAW_PER_REFILL = STATE_BITS // RAW_BITS   # 11 per refill
+MASK52 = (1 << RAW_BITS) - 1
 
 
 # --- Sec. 1 / Sec. 2: the subtract-with-borrow recurrence -------------------------
@@ -177,6 +182,11 @@ def exponential(d):
     return 0.0 - math.log(1.0 - d)
 
 
+def f64_from_bits52(v):
+    """52 raw LCG bits -> v 2^-52 in [0, 1), exact."""
+    return float(v) * 2.0 ** -52
+
+
 def f64_bits(x):
     """IEEE-754 binary64 bit pattern of a Python float."""
     return struct.unpack("<Q", struct.pack("<d", x))[0]
@@ -258,6 +268,25 @@ class Stream:
     def draw_f32_bits(self, n):
         """Single-precision draws: one number each, w 2^-24 (the 24-bit RANLUX output)."""
         return [f32_bits_from24(w) for w in self.draw_u24(n)]
+
+    def draw_raw52(self, n):
+        """Raw LCG doubles (Sec. 2.3 names this form, Sibidanov's, only to replace it by
+        the RANLUX numbers: its top bits are biased towards 0 because X < m; for
+        comparison only), as 52-bit integers v (the double is v 2^-52).  Each refill of
+        the LCG state gives 11 values, v_k = (X >> 52 k) mod 2^52 for k = 0 .. 10 of the
+        new state X, low bits first; the top 4 bits of X are not used.  A draw of n
+        values starts with a refill, takes ceil(n / 11) of them, discards the values of
+        the last one past n, and leaves the stream at the end of that block (read
+        position 24); n = 0 changes nothing."""
+        out = []
+        X = self.X
+        while len(out) < n:
+            X = advance(X, self.A)
+            out.extend((X >> (RAW_BITS * k)) & MASK52 for k in range(RAW_PER_REFILL))
+        if n:
+            self.D, self.c = to_ranlux(X)
+            self.pos = WORDS
+        return out[:n]
 
     def skip_values(self, n, per_value_words):
         """Move as if n values taking per_value_words numbers each had been drawn."""

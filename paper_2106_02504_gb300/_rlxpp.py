@@ -81,6 +81,7 @@ def _load():
         "rlxpp_draw_f32": [_vp, _vp, _vp, _i64, _vp, _vp],
         "rlxpp_draw_normal_f64": [_vp, _vp, _vp, _i64, _vp, _vp],
         "rlxpp_draw_exp_f64": [_vp, _vp, _vp, _i64, _vp, _vp],
+        "rlxpp_draw_raw_f64": [_vp, _vp, _vp, _i64, _vp, _vp],
         "rlxpp_draw_u24_host_async": [_vp, _i64, _vp, _vp],
         "rlxpp_draw_f64_host_async": [_vp, _i64, _vp, _vp],
         "rlxpp_host_wait": [_vp, _vp],
@@ -217,6 +218,10 @@ def rlxpp_draw_normal_f64(gen, out, count_each=0, counts=None, offsets=None, str
 
 def rlxpp_draw_exp_f64(gen, out, count_each=0, counts=None, offsets=None, stream=None):
     _check(_lib.rlxpp_draw_exp_f64(gen, _ptr(counts), _ptr(offsets), count_each, _ptr(out), _stream(stream)))
+
+
+def rlxpp_draw_raw_f64(gen, out, count_each=0, counts=None, offsets=None, stream=None):
+    _check(_lib.rlxpp_draw_raw_f64(gen, _ptr(counts), _ptr(offsets), count_each, _ptr(out), _stream(stream)))
 
 
 def rlxpp_draw_u24_host_async(gen, out, count_each, stream=None):
@@ -506,6 +511,9 @@ class Generator:
 
     def draw_exp_f64(self, out, count_each=0, counts=None, offsets=None, stream=None):
         rlxpp_draw_exp_f64(self.handle, out, count_each, counts, offsets, stream)
+
+    def draw_raw_f64(self, out, count_each=0, counts=None, offsets=None, stream=None):
+        rlxpp_draw_raw_f64(self.handle, out, count_each, counts, offsets, stream)
 
     def draw_u24_host_async(self, out, count_each, stream=None):
         rlxpp_draw_u24_host_async(self.handle, out, count_each, stream)

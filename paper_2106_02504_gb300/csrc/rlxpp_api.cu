@@ -201,6 +201,7 @@ constexpr size_t kChunkBytes = size_t(256) << 20;  // device staging per chunk o
 // level (a tile's streams share the multiplier matrix), one warp per stream for the
 // kinds the warp kernel has, else the integer pipe.
 cudaError_t launch_path(const rlxpp_gen* g, int kind, const DrawArgs& a, cudaStream_t st) {
+  if (kind == kDrawRaw52) return launch_draw(kind, a, st);  // integer pipe only
   if (g->path == RLXPP_PATH_TENSOR && g->n_levels == 1)
     return launch_draw_tc(kind, a, g->tc_matrix, g->tc_matrix_d, st);
   if (g->path == RLXPP_PATH_WARP && warp_draw_supported(kind)) return launch_draw_warp(kind, a, st);
@@ -520,6 +521,11 @@ rlxpp_status rlxpp_draw_normal_f64(rlxpp_gen* g, const int64_t* counts, const in
 rlxpp_status rlxpp_draw_exp_f64(rlxpp_gen* g, const int64_t* counts, const int64_t* offsets,
                             int64_t count_each, double* out, void* cuda_stream) {
   return draw_common(g, kDrawExp, counts, offsets, count_each, out, sizeof(double), as_stream(cuda_stream));
+}
+
+rlxpp_status rlxpp_draw_raw_f64(rlxpp_gen* g, const int64_t* counts, const int64_t* offsets,
+                                int64_t count_each, double* out, void* cuda_stream) {
+  return draw_common(g, kDrawRaw52, counts, offsets, count_each, out, sizeof(double), as_stream(cuda_stream));
 }
 
 rlxpp_status rlxpp_skip_values(rlxpp_gen* g, const uint64_t* n_values, uint32_t kind, void* cuda_stream) {

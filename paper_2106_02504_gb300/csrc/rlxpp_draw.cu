@@ -108,6 +108,85 @@ __global__ void __launch_bounds__(kDrawBlock, (Uniform && Kind != kDrawNormal &&
   }
 }
 
+// Raw LCG doubles (Sec. 2.3's biased form, for comparison): the 52 bits of the LCG state
+// X starting at bit 52 k (k <= 10, so the two limbs from bit 52 k's limb on exist), and
+// v 2^-52 as a double built with integer operations (exact: v < 2^52): the leading one
+// moves to bit 52, where it adds one to the exponent field 1033 - lz placed above it.
+__device__ __forceinline__ uint64_t bits52(const uint32_t X[kLimbs], int k) {
+  const int bit = 52 * k, limb = bit >> 5, off = bit & 31;
+  uint64_t v = ((uint64_t)X[limb] | ((uint64_t)X[limb + 1] << 32)) >> off;
+  if (off > 12 && limb + 2 < kLimbs) v |= (uint64_t)X[limb + 2] << (64 - off);
+  return v & ((1ull << 52) - 1);
+}
+__device__ __forceinline__ uint64_t f64_bits_from52(uint64_t v) {
+  if (v == 0) return 0;
+  const int lz = __clzll((long long)v);  // 12 .. 63
+  return (v << (lz - 11)) + ((uint64_t)(1033 - lz) << 52);
+}
+
+// Raw LCG doubles: each stream starts with a refill and emits 11 values of every new
+// LCG state until its count is reached; the stream is left at the end of its last
+// block (read position 24).
+template <bool Uniform>
+__global__ void __launch_bounds__(kDrawBlock, 4) k_draw_raw(const DrawArgs a) {
+  const StateView& s = a.s;
+  const uint64_t i = (uint64_t)blockIdx.x * kDrawBlock + threadIdx.x;
+  if (i >= s.n) return;
+  int64_t cnt, base;
+  if (a.counts) {
+    cnt = a.counts[i];
+    base = a.offsets[i];
+  } else {
+    cnt = a.count_each;
+    base = (int64_t)i * a.count_each;
+  }
+  if (cnt <= 0) return;
+  const uint32_t meta = s.meta[i];
+  uint32_t c = meta_carry(meta);
+  const uint32_t lvl = meta_level(meta);
+  uint32_t D[kLimbs];
+#pragma unroll
+  for (int k = 0; k < 9; ++k) {
+    const uint64_t v = s.D[(uint64_t)k * s.stride + i];
+    D[2 * k] = (uint32_t)v;
+    D[2 * k + 1] = (uint32_t)(v >> 32);
+  }
+  uint32_t Areg[kLimbs], ASreg[9], careg = 0;
+  if (!Uniform) {
+    const uint2* src = reinterpret_cast<const uint2*>(s.lux + (size_t)lvl * kLimbs);
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+      const uint2 t = __ldg(src + k);
+      Areg[2 * k] = t.x;
+      Areg[2 * k + 1] = t.y;
+    }
+    ASreg[0] = add_cc(Areg[0], Areg[9]);
+#pragma unroll
+    for (int k = 1; k < 9; ++k) ASreg[k] = addc_cc(Areg[k], Areg[9 + k]);
+    careg = addc(0u, 0u);
+  }
+  auto A = [&](int k) { return Uniform ? a.A.a[k] : Areg[k]; };
+  auto AS = [&](int k) { return Uniform ? a.A.as[k] : ASreg[k]; };
+  const uint32_t ca = Uniform ? a.A.ca : careg;
+  uint64_t* out = static_cast<uint64_t*>(a.out) + base;
+  uint32_t X[kLimbs];
+  to_lcg(D, c, X);
+#pragma unroll 1
+  for (int64_t k0 = 0; k0 < cnt; k0 += 11) {
+    uint32_t P[2 * kLimbs];
+    multiply9x9_split(A, AS, ca, X, P);
+    mod_m(P, X);
+#pragma unroll
+    for (int k = 0; k < 11; ++k)
+      if (k0 + k < cnt) out[k0 + k] = f64_bits_from52(bits52(X, k));
+  }
+  to_ranlux(X, D);
+  c = carry_of(X, D);
+#pragma unroll
+  for (int q = 0; q < 9; ++q) s.D[(uint64_t)q * s.stride + i] = ((uint64_t)D[2 * q + 1] << 32) | D[2 * q];
+  s.meta[i] = meta_pack((uint32_t)kWords, c, lvl);
+}
+
 template <int Kind>
 cudaError_t launch_kind(const DrawArgs& a, cudaStream_t st) {
   const unsigned grid = (unsigned)((a.s.n + kDrawBlock - 1) / kDrawBlock);
@@ -129,6 +208,14 @@ cudaError_t launch_draw(int kind, const DrawArgs& a, cudaStream_t st) {
     case kDrawF32: return launch_kind<kDrawF32>(a, st);
     case kDrawNormal: return launch_kind<kDrawNormal>(a, st);
     case kDrawExp: return launch_kind<kDrawExp>(a, st);
+    case kDrawRaw52: {
+      const unsigned grid = (unsigned)((a.s.n + kDrawBlock - 1) / kDrawBlock);
+      if (a.uniform)
+        k_draw_raw<true><<<grid, kDrawBlock, 0, st>>>(a);
+      else
+        k_draw_raw<false><<<grid, kDrawBlock, 0, st>>>(a);
+      return cudaGetLastError();
+    }
   }
   return cudaErrorInvalidValue;
 }

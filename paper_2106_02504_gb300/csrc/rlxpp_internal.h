@@ -44,7 +44,15 @@ struct StateView {
   int* status;       // sticky device status (rlxpp_status value, 0 = ok)
 };
 
-enum DrawKind { kDrawU24 = 0, kDrawF64 = 1, kDrawSumHist = 2, kDrawF32 = 3, kDrawNormal = 4, kDrawExp = 5 };
+enum DrawKind {
+  kDrawU24 = 0,
+  kDrawF64 = 1,
+  kDrawSumHist = 2,
+  kDrawF32 = 3,
+  kDrawNormal = 4,
+  kDrawExp = 5,
+  kDrawRaw52 = 6  // raw LCG doubles, 11 per refill (integer path only)
+};
 
 struct DrawArgs {
   StateView s;

@@ -1168,8 +1168,10 @@ __global__ void __launch_bounds__(kTcRows, 4)
   __syncthreads();
   const bool tma =
       __syncthreads_and(!live || (pos_in == sh->pos0 && ((k * (int64_t)(need * 4)) & 15) == 0)) != 0;
-  int64_t left = live && k < cnt ? (cnt - k + per_block - 1) / per_block : 0;
-  const int64_t iters = cta_max(left, &sh->iters);
+  // this stream's refills: full blocks, and a last one of `tail` values (0: full)
+  const int64_t nref = live && k < cnt ? (cnt - k + per_block - 1) / per_block : 0;
+  const uint32_t tail = (uint32_t)((cnt - k) % per_block);
+  const int64_t iters = cta_max(nref, &sh->iters);
   const int y0 = (int)((uint64_t)blockIdx.x * kTcRows);
   uint32_t X[kLimbs];
   to_lcg(D, c, X);
@@ -1183,77 +1185,87 @@ __global__ void __launch_bounds__(kTcRows, 4)
   bool ok = true, inflight = iters > 0, stored = false;
   int box_x[2] = {0, 0};  // thread 0: first column of the block staged in each box
   bool pending = false;   // thread 0: a staged box waits for its store
-  for (int64_t it = 0; it < iters; ++it) {
-    bool got = mbar_wait_bounded(&sh->bar, phase);
-    got = __all_sync(0xFFFFFFFFu, got);  // the warp stays converged for the TMEM accesses
-    if (got) {
-      inflight = false;
-      phase ^= 1u;
+  // refills in chunks of at most 2^20 (an even count, so a box's parity is the
+  // refill's), counted in 32 bits within a chunk
+  for (int64_t it0 = 0; ok && it0 < iters;) {
+    const uint32_t n_in = (uint32_t)(iters - it0 > kFusedFlush ? kFusedFlush : iters - it0);
+    const bool more_after = it0 + n_in < iters;
+    const int64_t rem_ref = nref - it0;
+    const uint32_t n_mine = rem_ref <= 0 ? 0u : (rem_ref >= (int64_t)n_in ? n_in : (uint32_t)rem_ref);
+    const uint32_t j_last = rem_ref >= 1 && rem_ref <= (int64_t)n_in ? (uint32_t)(rem_ref - 1) : 0xFFFFFFFFu;
+    const int64_t k_chunk = k + it0 * per_block;  // this stream's first value of the chunk
+    for (uint32_t j = 0; j < n_in; ++j) {
+      bool got = mbar_wait_bounded(&sh->bar, phase);
+      got = __all_sync(0xFFFFFFFFu, got);  // the warp stays converged for the TMEM accesses
+      if (got) {
+        inflight = false;
+        phase ^= 1u;
+        tc_fence_after();
+        uint32_t col[72];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) tmem_ld16(lane_taddr + 16 * q, col + 16 * q);
+        tmem_ld8(lane_taddr + 64, col + 64);
+        tmem_wait_ld();
+        tc_fold_common(col, X);
+        __syncwarp();  // reconverged after the rare fold, before the warp-wide store
+        write_x_tmem(lane_taddr, X);
+        tmem_wait_st();
+      } else {
+        sh->abort = 1u;
+      }
+      if (tma && tid == 0) bulk_wait_read_all();  // the last store has read its box
+      tc_fence_before();
+      __syncthreads();
       tc_fence_after();
-      uint32_t col[72];
+      if (sh->abort) {
+        ok = false;
+        break;
+      }
+      if (j + 1 < n_in || more_after) {
+        if (tid == 0) tc_issue_tm(taddr, b0, &sh->bar);
+        inflight = true;
+      }
+      if (tid == 0 && pending) {  // the blocks staged before this barrier
+        const uint32_t pb = (j + 1u) & 1u;
+        asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%1, %2}], [%3];" ::"l"(
+                         reinterpret_cast<uint64_t>(&tmap)),
+                     "r"(box_x[pb]), "r"(y0), "r"(smem_addr(box0 + pb * kValuesBox))
+                     : "memory");
+        asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+        pending = false;
+      }
+      if (j < n_mine) {  // this stream's block, while the next product computes
+        to_ranlux(X, D);
+        const int64_t kj = k_chunk + (int64_t)j * per_block;
+        const bool full = j != j_last || tail == 0;
+        if (tma) {  // the whole block into this thread's row of the box; past the count it is clipped
+          uint4 v[6];
+          block_values<Kind>(D, v);
+          uint4* row = reinterpret_cast<uint4*>(box0 + (j & 1u) * kValuesBox + tid * kStageBytes);
 #pragma unroll
-      for (int q = 0; q < 4; ++q) tmem_ld16(lane_taddr + 16 * q, col + 16 * q);
-      tmem_ld8(lane_taddr + 64, col + 64);
-      tmem_wait_ld();
-      tc_fold_common(col, X);
-      __syncwarp();  // reconverged after the rare fold, before the warp-wide store
-      write_x_tmem(lane_taddr, X);
-      tmem_wait_st();
-    } else {
-      sh->abort = 1u;
-    }
-    if (tma && tid == 0) bulk_wait_read_all();  // the last store has read its box
-    tc_fence_before();
-    __syncthreads();
-    tc_fence_after();
-    if (sh->abort) {
-      ok = false;
-      break;
-    }
-    if (it + 1 < iters) {
-      if (tid == 0) tc_issue_tm(taddr, b0, &sh->bar);
-      inflight = true;
-    }
-    if (tid == 0 && pending) {  // the blocks staged before this barrier
-      asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%1, %2}], [%3];" ::"l"(
-                       reinterpret_cast<uint64_t>(&tmap)),
-                   "r"(box_x[(it - 1) & 1]), "r"(y0), "r"(smem_addr(box0 + ((it - 1) & 1) * kValuesBox))
-                   : "memory");
-      asm volatile("cp.async.bulk.commit_group;" ::: "memory");
-      pending = false;
-    }
-    if (left > 0) {  // this stream's block, while the next product computes
-      to_ranlux(X, D);
-      const int64_t rem = cnt - k;
-      if (tma) {  // the whole block into this thread's row of the box; past the count it is clipped
-        uint4 v[6];
-        block_values<Kind>(D, v);
-        uint4* row = reinterpret_cast<uint4*>(box0 + (it & 1) * kValuesBox + tid * kStageBytes);
-#pragma unroll
-        for (int q = 0; q < 6; ++q) row[q] = v[q];
-        fence_proxy_async_smem();
-        if (tid == 0) {
-          box_x[it & 1] = (int)k;
-          pending = true;
+          for (int q = 0; q < 6; ++q) row[q] = v[q];
+          fence_proxy_async_smem();
+          if (tid == 0) {
+            box_x[j & 1u] = (int)kj;
+            pending = true;
+          }
+        } else if (full) {
+          out.block(D, base + kj);
+        } else {
+          out.partial(D, base + kj, tail);
         }
-      } else if (rem >= per_block) {
-        out.block(D, base + k);
-      } else {
-        out.partial(D, base + k, rem);
-      }
-      if (rem >= per_block) {
-        k += per_block;
-        pos = kWords;
-      } else {
-        k = cnt;
-        pos = (uint32_t)(rem * need);
-      }
-      if (--left == 0) {
-        c_fin = carry_of(X, D);
-        store_state_D(s, i, D);
-        stored = true;
+        if (j == j_last) {
+          c_fin = carry_of(X, D);
+          store_state_D(s, i, D);
+          stored = true;
+        }
       }
     }
+    it0 += n_in;
+  }
+  if (nref > 0) {
+    k = cnt;
+    pos = tail ? tail * need : (uint32_t)kWords;
   }
   if (ok && tma && iters > 0) {  // the last staged box
     __syncthreads();

@@ -607,3 +607,35 @@ def test_skip_values(native, kind, need):
         D, c, pos = st.D, st.c, st.pos
         assert from_limbs64(got[i, :9]) == D, i
         assert int(got[i, 9]) == c | (pos << 32), i
+
+
+def test_draw_raw_lcg_doubles(native, path):
+    """Raw LCG doubles (the comparison form of Sec. 2.3): per-stream counts with zeros,
+    counts that end inside a refill, streams left at odd read positions by a u24 draw,
+    two luxury levels; every value's bit pattern and every final state against the
+    oracle's Stream.draw_raw52."""
+    n = 150
+    seeds = W.random_seeds(n, 91)
+    levels = (223, 2048)
+    level_of = (np.arange(n) % 2).astype(np.uint8)
+    g = make(native, seeds, levels=levels, level_of=level_of, path=path)
+    pre = (np.arange(n) * 5) % 26                        # leaves positions 0 .. 24 and 25
+    po = np.concatenate([[0], np.cumsum(pre)[:-1]]).astype(np.int64)
+    tmp = torch.zeros(int(pre.sum()) + 1, dtype=torch.int32, device="cuda")
+    g.draw_u24(tmp, 0, torch.from_numpy(pre.astype(np.int64)).cuda(), torch.from_numpy(po).cuda())
+    counts = np.array([0 if i % 13 == 0 else (i * 37) % 300 + 1 for i in range(n)], dtype=np.int64)
+    offs = np.concatenate([[0], np.cumsum(counts)[:-1]]).astype(np.int64)
+    out = torch.full((int(counts.sum()) + 1,), -1, dtype=torch.int64, device="cuda")
+    g.draw_raw_f64(out, 0, torch.from_numpy(counts).cuda(), torch.from_numpy(offs).cuda())
+    got = out.cpu().numpy().view(np.uint64)
+    assert got[-1] == np.uint64(2 ** 64 - 1)              # nothing past the output
+    recs = states(native, g, n)
+    for i in range(n):
+        p = levels[int(level_of[i])]
+        s = R.Stream(p, seed=int(seeds[i]))
+        s.draw_u24(int(pre[i]))
+        vals = s.draw_raw52(int(counts[i]))
+        want = np.array([R.f64_bits(R.f64_from_bits52(v)) for v in vals], dtype=np.uint64)
+        assert np.array_equal(got[offs[i]:offs[i] + counts[i]], want), i
+        D, c, pos, _ = s.state()
+        assert list(recs[i, :9]) == D and int(recs[i, 9]) == c | (pos << 32), i

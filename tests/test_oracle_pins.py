@@ -474,3 +474,32 @@ def test_normal_draws_consume_pairs_and_look_gaussian():
     cdf = 0.5 * (1 + np.array([math.erf(v / math.sqrt(2)) for v in xs]))
     ks = max(np.max(np.arange(1, n + 1) / n - cdf), np.max(cdf - np.arange(n) / n))
     assert ks < 1.63 / math.sqrt(n)                        # 1 % critical value
+
+
+# --- raw LCG doubles (comparison mode) ----------------------------------------------------
+@pytest.mark.parametrize("p", [24, 389, 2048])
+def test_raw52_draws_are_the_bits_of_the_recurrence_states(p):
+    """The raw values of each refill reassemble the low 572 bits of the LCG state that the
+    recurrence reaches after p more steps (X = D - floor(D / 2^336) + c of its window),
+    low bits first, 11 per refill; the stream ends at the last refill's block, read
+    position 24; and the values are below 2^52."""
+    s = R.Stream(p, seed=9, pos=5)
+    w, c = s.words(), s.c
+    got = s.draw_raw52(11 * 3 + 4)      # four refills, the last one partly used
+    assert len(got) == 37 and all(0 <= v < 2 ** 52 for v in got)
+    for r in range(4):
+        w, c = S.block(w, c, p)         # the recurrence's next block (p steps)
+        X = R.pack_words(w) - (R.pack_words(w) >> 336) + c
+        vals = got[11 * r: 11 * r + 11]
+        assert sum(v << (52 * k) for k, v in enumerate(vals)) == X % 2 ** (52 * len(vals))
+    assert s.words() == w and s.c == c and s.pos == 24
+    # no values: no refill, nothing moves
+    t = R.Stream(p, seed=9, pos=5)
+    assert t.draw_raw52(0) == [] and t.pos == 5 and t.words() == R.Stream(p, seed=9).words()
+
+
+def test_raw52_double_conversion_closed_forms():
+    assert R.f64_from_bits52(0) == 0.0
+    assert R.f64_from_bits52(1) == 2.0 ** -52
+    assert R.f64_from_bits52(2 ** 51) == 0.5
+    assert R.f64_from_bits52(2 ** 52 - 1) == 1.0 - 2.0 ** -52
