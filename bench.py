@@ -52,8 +52,8 @@ CPU_SAMPLE_STREAMS = 16384
 # bytes (read + write) per stream and launch, and ALU-pipe instructions per refill.
 # They describe the kernel as compiled from the sources whose digest is `src_sha`
 # (kernel_sources_sha); once those sources change, the figures are reported as null.
-TC_FUSED_CAPTURE = {"dram_bytes_per_stream": None, "alu_instr_per_refill": None, "streams": None,
-                    "src_sha": None}
+TC_FUSED_CAPTURE = {"dram_bytes_per_stream": 76.2, "alu_instr_per_refill": 172, "streams": 262144,
+                    "src_sha": "42ab54e88fb33d36"}
 KERNEL_SOURCES = ("rlxpp_tensor.cu", "rlxpp_arith.cuh", "rlxpp_drawloop.cuh", "rlxpp_state.cuh",
                   "rlxpp_internal.h", "rlxpp_batch.h", "rlxpp_fixmath.cuh", "rlxpp_fixmath_tables.h")
 
@@ -710,6 +710,8 @@ def main():
     ap.add_argument("--only-main", action="store_true", help="skip the other workloads")
     ap.add_argument("--only-normal", action="store_true",
                     help="run only the Gaussian and exponential workloads on --streams streams (for profiling)")
+    ap.add_argument("--only-batch", action="store_true",
+                    help="run only the mixed batch on --batch-streams streams (for profiling)")
     ap.add_argument("--path", default="imad,tensor", help="refill paths to time; the faster one is reported")
     ap.add_argument("--batch-streams", type=int, default=65536)
     ap.add_argument("--serve-seconds", type=float, default=10.0)
@@ -722,6 +724,13 @@ def main():
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
     if args.impl == "reference":
         return run_reference(args, rank, world)
+    if args.only_batch:
+        import torch
+        from paper_2106_02504_gb300 import build as _b
+        _b.build()
+        import paper_2106_02504_gb300._rlxpp as nat
+        print(json.dumps({"workload": "mixed_batch", **bench_mixed_batch(nat, torch.device("cuda", local_rank), args)}))
+        return 0
     if args.only_normal:
         import torch
         from paper_2106_02504_gb300 import build as _b
