@@ -792,6 +792,49 @@ __device__ __forceinline__ void tc_fold_common(const uint32_t col[72], uint32_t 
   }
 }
 
+// The fused draw's epilogue: X = sum_k S_k 2^(8k) mod m from the column bit patterns, D its
+// 24 RANLUX numbers (Sec. 2.3) and c its borrow, computed without a branch in the common
+// case (the fold's carry stops in limb 8, the top limb is not all ones, the conversion's
+// quick test decides its quotient and X + q carries no further than limb 7); every other
+// case (about 2^-15 of the refills) is redone in one branch by the exact forms.  With no
+// branch before them, the byte permutes of D's upper limbs (equal to X's) can be
+// scheduled while the conversion's carry chain runs.
+__device__ __forceinline__ void tc_epilogue_d(const uint32_t col[72], uint32_t X[kLimbs], uint32_t D[kLimbs],
+                                              uint32_t& c) {
+  uint32_t Xa[kLimbs], T;
+  columns_assemble(col, Xa, T);
+  X[0] = add_cc(Xa[0], 0u - T);
+#pragma unroll
+  for (int k = 1; k < 7; ++k) X[k] = addc_cc(Xa[k], 0xFFFFFFFFu);
+  X[7] = addc_cc(Xa[7], (T - 1u) << 16 | 0xFFFFu);
+  X[8] = addc_cc(Xa[8], 0u);
+  const uint32_t c9 = addc(0u, 0u);  // carry out of limb 8
+#pragma unroll
+  for (int k = 9; k < kLimbs; ++k) X[k] = Xa[k];
+  const uint32_t t15 = sub_cc(__funnelshift_l(X[7], X[8], 16), X[15]);
+  const uint32_t t16 = subc_cc(__funnelshift_l(X[8], X[9], 16), X[16]);
+  const uint32_t t17 = subc_cc(__funnelshift_l(X[9], X[10], 16), X[17]);
+  const uint32_t borrow = subc(0u, 0u) & 1u;
+  const uint32_t q0 = __funnelshift_l(X[10], X[11], 16);
+  D[0] = add_cc(X[0], q0 - borrow);
+#pragma unroll
+  for (int k = 1; k < 7; ++k) D[k] = addc_cc(X[k], __funnelshift_l(X[10 + k], X[11 + k], 16));
+  D[7] = addc_cc(X[7], X[17] >> 16);
+  const uint32_t c8 = addc(0u, 0u);  // carry out of limb 7 of X + q
+#pragma unroll
+  for (int k = 8; k < kLimbs; ++k) D[k] = X[k];
+  c = carry_of(X, D);
+  const bool rare = (c9 | c8) != 0u || X[17] == 0xFFFFFFFFu || (t15 & t16 & t17) == 0xFFFFFFFFu ||
+                    (t15 | t16 | t17) == 0u || q0 < borrow;
+  if (__builtin_expect(rare, 0)) {
+#pragma unroll
+    for (int k = 0; k < kLimbs; ++k) X[k] = Xa[k];
+    fold_x(X, T);
+    to_ranlux(X, D);
+    c = carry_of(X, D);
+  }
+}
+
 // The consumer of the fused draw on this kernel: an exact sum and a 256-bin histogram of
 // the top 8 bits of every 48-bit value.  The sums of full blocks come from the tensor
 // core: the product that refills a block also sums its bytes by position within a
@@ -998,10 +1041,8 @@ __global__ void __launch_bounds__(kTcRows, 4)
 #pragma unroll
         for (int r = 0; r < 6; ++r) sums[r] = col[72 + r];
         uint32_t X[kLimbs];
-        tc_fold_common(col, X);
-        to_ranlux(X, D);
-        c = carry_of(X, D);
-        __syncwarp();  // reconverged after the rare branches, before the warp-wide store
+        tc_epilogue_d(col, X, D, c);
+        __syncwarp();  // reconverged after the rare branch, before the warp-wide store
         write_d_tmem(lane_taddr, D, c);
         tmem_wait_st();
       } else {
