@@ -133,6 +133,13 @@ __device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t* v) {
                : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7])
                : "r"(taddr));
 }
+// whole warp: 64 consecutive columns of this warp's 32 lanes into registers
+__device__ __forceinline__ void tmem_ld64(uint32_t taddr, uint32_t* v) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x64.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31,%32,%33,%34,%35,%36,%37,%38,%39,%40,%41,%42,%43,%44,%45,%46,%47,%48,%49,%50,%51,%52,%53,%54,%55,%56,%57,%58,%59,%60,%61,%62,%63}, [%64];"
+      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]), "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31]), "=r"(v[32]), "=r"(v[33]), "=r"(v[34]), "=r"(v[35]), "=r"(v[36]), "=r"(v[37]), "=r"(v[38]), "=r"(v[39]), "=r"(v[40]), "=r"(v[41]), "=r"(v[42]), "=r"(v[43]), "=r"(v[44]), "=r"(v[45]), "=r"(v[46]), "=r"(v[47]), "=r"(v[48]), "=r"(v[49]), "=r"(v[50]), "=r"(v[51]), "=r"(v[52]), "=r"(v[53]), "=r"(v[54]), "=r"(v[55]), "=r"(v[56]), "=r"(v[57]), "=r"(v[58]), "=r"(v[59]), "=r"(v[60]), "=r"(v[61]), "=r"(v[62]), "=r"(v[63])
+      : "r"(taddr));
+}
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 // The product with the A operand in tensor memory (a_tmem: its first column, lane 0).
 __device__ __forceinline__ void tc_mma_ta(uint32_t d_tmem, uint32_t a_tmem, uint64_t b_desc, uint32_t accumulate) {
@@ -1035,8 +1042,8 @@ __global__ void __launch_bounds__(kTcRows, 4)
         phase ^= 1u;
         tc_fence_after();
         uint32_t col[80];
-#pragma unroll
-        for (int q = 0; q < 5; ++q) tmem_ld16(lane_taddr + 16 * q, col + 16 * q);
+        tmem_ld64(lane_taddr, col);
+        tmem_ld16(lane_taddr + 64, col + 64);
         tmem_wait_ld();
 #pragma unroll
         for (int r = 0; r < 6; ++r) sums[r] = col[72 + r];
@@ -1243,8 +1250,7 @@ __global__ void __launch_bounds__(kTcRows, 4)
         phase ^= 1u;
         tc_fence_after();
         uint32_t col[72];
-#pragma unroll
-        for (int q = 0; q < 4; ++q) tmem_ld16(lane_taddr + 16 * q, col + 16 * q);
+        tmem_ld64(lane_taddr, col);
         tmem_ld8(lane_taddr + 64, col + 64);
         tmem_wait_ld();
         tc_fold_common(col, X);
@@ -1454,8 +1460,7 @@ __global__ void __launch_bounds__(kTcRows, 4)
         phase ^= 1u;
         tc_fence_after();
         uint32_t col[72];
-#pragma unroll
-        for (int q = 0; q < 4; ++q) tmem_ld16(lane_taddr + 16 * q, col + 16 * q);
+        tmem_ld64(lane_taddr, col);
         tmem_ld8(lane_taddr + 64, col + 64);
         tmem_wait_ld();
         tc_fold_common(col, Xn);
