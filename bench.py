@@ -463,7 +463,13 @@ def bench_single_stream(nat, dev):
             "serial": {"ms": ms_serial, "doubles_per_s": n / (ms_serial * 1e-3),
                        "ns_per_advance": ms_serial * 1e6 / adv, "path": best, "by_path": serial},
             "split": {"ms": ms_split, "doubles_per_s": n / (ms_split * 1e-3), "chunks": items,
-                      "tuning": {"chunk_blocks": tuning[0], "blocks_per_sm": tuning[1], "path": tuning[2]}}}
+                      "tuning": tuning_dict(tuning)}}
+
+
+def tuning_dict(t):
+    """A request tuning (chunk_blocks, blocks_per_sm, path, threads_per_block) for the
+    JSON line; threads per block 0 is the default, 128."""
+    return {"chunk_blocks": t[0], "blocks_per_sm": t[1], "path": t[2], "threads_per_block": t[3] or 128}
 
 
 def bench_mixed_batch(nat, dev, args):
@@ -498,7 +504,7 @@ def bench_mixed_batch(nat, dev, args):
     tune_s = time.perf_counter() - t
     by_path = {}
     for name, pid in (("tensor", nat.RLXPP_PATH_TENSOR), ("imad", nat.RLXPP_PATH_IMAD), ("warp", nat.RLXPP_PATH_WARP)):
-        tuning = (tuned[0], tuned[1], pid)
+        tuning = (tuned[0], tuned[1], pid, tuned[3] if pid == tuned[2] else 0)
         t = time.perf_counter()
         plan = nat.rlxpp_plan_requests(g.handle, reqs, 0, tuning)
         plan_s = time.perf_counter() - t
@@ -513,7 +519,7 @@ def bench_mixed_batch(nat, dev, args):
         ms = _time_events(graph.replay, 3, st)
         by_path[name] = {"ms": ms, "values_per_s": int(counts.sum()) / (ms * 1e-3),
                          "advances_per_s": refills / (ms * 1e-3), "chunks": nat.rlxpp_plan_items(plan),
-                         "tuning": {"chunk_blocks": tuning[0], "blocks_per_sm": tuning[1], "path": tuning[2]},
+                         "tuning": tuning_dict(tuning),
                          "plan_s": plan_s, "tuner_choice": pid == tuned[2]}
         nat.rlxpp_destroy_plan(plan)
         del graph

@@ -230,7 +230,13 @@ typedef struct rlxpp_tuning {
                              RLXPP_PATH_TENSOR: one thread per chunk, 128-chunk tiles
                              on the tensor cores (4 CTAs per SM at most);
                              RLXPP_PATH_WARP: 32 threads per chunk (one warp, one limb
-                             per lane), for few long chunks                             */
+                             per lane), for few long chunks.  The path also fixes the
+                             limb width of the product: 32-bit limbs on the integer
+                             pipe (IMAD, WARP), 8-bit limbs in the tensor product     */
+  uint32_t threads_per_block; /* block shape: threads per CTA, 0 = the path's default
+                             (128); IMAD and WARP take 64, 128 or 256, TENSOR only 128
+                             (one 128-row tile per CTA); blocks_per_sm x
+                             threads_per_block <= 2048                                  */
 } rlxpp_tuning;
 
 typedef struct rlxpp_plan rlxpp_plan;
@@ -268,11 +274,11 @@ rlxpp_status rlxpp_draw_requests(rlxpp_gen* gen, const rlxpp_request* reqs, uint
                                  uint32_t* out_u24, double* out_f64, uint32_t flags,
                                  void* cuda_stream);
 
-/* Tuner: times candidate (kernel, chunk length, grid) choices on these requests (the
- * integer-pipe kernel with one thread or one warp per chunk, and the tensor-core
- * kernel; without RLXPP_REQ_ADVANCE, so the streams do not move; the outputs are
- * overwritten) and
- * keeps the fastest for requests of the same shape (log2 buckets of the request count
+/* Tuner: times candidate (kernel, chunk length, block shape, grid) choices on these
+ * requests (the integer-pipe kernel with one thread or one warp per chunk, and the
+ * tensor-core kernel, i.e. threads per stream, limb width and product; 64, 128 or 256
+ * threads per CTA where the kernel allows it; without RLXPP_REQ_ADVANCE, so the
+ * streams do not move; the outputs are overwritten) and keeps the fastest for requests of the same shape (log2 buckets of the request count
  * and of the total refills).  The choice is kept in the handle and, when the
  * environment variable RLXPP_TUNE_CACHE names a file, appended there and read back
  * by later handles on the same device model.  best may be NULL. */

@@ -30,7 +30,8 @@ assert STATE_BYTES == 88
 
 class RlxppTuning(ctypes.Structure):
     """struct rlxpp_tuning."""
-    _fields_ = [("chunk_blocks", ctypes.c_uint32), ("blocks_per_sm", ctypes.c_uint32), ("path", ctypes.c_uint32)]
+    _fields_ = [("chunk_blocks", ctypes.c_uint32), ("blocks_per_sm", ctypes.c_uint32), ("path", ctypes.c_uint32),
+                ("threads_per_block", ctypes.c_uint32)]
 
 
 RLXPP_KIND_U24, RLXPP_KIND_F64, RLXPP_KIND_F32 = 0, 1, 2
@@ -402,7 +403,8 @@ def _requests(reqs):
 
 
 def _tuning(t, gen=None):
-    """(chunk_blocks, blocks_per_sm[, path]); the path defaults to the handle's."""
+    """(chunk_blocks, blocks_per_sm[, path[, threads_per_block]]); the path defaults to
+    the handle's, the threads per block to the path's default (0)."""
     if t is None:
         return None
     if isinstance(t, RlxppTuning):
@@ -410,7 +412,13 @@ def _tuning(t, gen=None):
     t = tuple(t)
     if len(t) == 2:  # the handle's path picks the request kernel
         t = t + (rlxpp_get_path(gen) if gen else RLXPP_PATH_TENSOR,)
+    if len(t) == 3:
+        t = t + (0,)
     return ctypes.byref(RlxppTuning(*t))
+
+
+def _tuple(t):
+    return (t.chunk_blocks, t.blocks_per_sm, t.path, t.threads_per_block)
 
 
 def rlxpp_plan_requests(gen, reqs, flags=0, tuning=None):
@@ -431,8 +439,7 @@ def rlxpp_plan_items(plan):
 
 
 def rlxpp_plan_tuning(plan):
-    t = _lib.rlxpp_plan_tuning(plan)
-    return (t.chunk_blocks, t.blocks_per_sm, t.path)
+    return _tuple(_lib.rlxpp_plan_tuning(plan))
 
 
 def rlxpp_destroy_plan(plan):
@@ -446,12 +453,12 @@ def rlxpp_draw_requests(gen, reqs, out_u24=None, out_f64=None, flags=0, stream=N
 
 
 def rlxpp_autotune_requests(gen, reqs, out_u24=None, out_f64=None, stream=None):
-    """Returns the chosen (chunk_blocks, blocks_per_sm, path)."""
+    """Returns the chosen (chunk_blocks, blocks_per_sm, path, threads_per_block)."""
     a, n = _requests(reqs)
     t = RlxppTuning()
     _check(_lib.rlxpp_autotune_requests(gen, a.ctypes.data if n else None, n, _ptr(out_u24), _ptr(out_f64),
                                         _stream(stream), ctypes.byref(t)))
-    return (t.chunk_blocks, t.blocks_per_sm, t.path)
+    return _tuple(t)
 
 
 def rlxpp_set_path(gen, path):

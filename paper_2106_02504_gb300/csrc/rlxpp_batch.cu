@@ -87,13 +87,21 @@ __device__ __forceinline__ void run_item(const BatchArgs& b, const Lux& L, const
   }
 }
 
+// Resident CTAs per SM that the register budget of a TPB-thread CTA allows for: the
+// same threads per SM as RLXPP_REQ_MIN_BLOCKS CTAs of kReqBlock (at least one).
+template <int TPB>
+constexpr int req_min_blocks() {
+  return (RLXPP_REQ_MIN_BLOCKS * kReqBlock) / TPB > 0 ? (RLXPP_REQ_MIN_BLOCKS * kReqBlock) / TPB : 1;
+}
+
 // Persistent, every level in one launch: each warp takes the next 32 chunks of the
 // list from the counter.  With one level (Multi = false) its multiplier stays in the
 // kernel argument (the constant bank); with several, the levels' multipliers are copied
 // into shared memory and each chunk reads its own level's (lanes of one level read the
-// same words, and different levels' words fall in different banks).
-template <bool Multi>
-__global__ void __launch_bounds__(kReqBlock, RLXPP_REQ_MIN_BLOCKS)
+// same words, and different levels' words fall in different banks).  TPB: threads per
+// CTA (the block shape the tuner picks).
+template <bool Multi, int TPB>
+__global__ void __launch_bounds__(TPB, req_min_blocks<TPB>())
     k_requests(BatchArgs b, const LuxTable lt, uint32_t n_levels, const Item* __restrict__ items, uint64_t n_items,
                WorkCounters* wc) {
   __shared__ Lux lux_s[Multi ? RLXPP_MAX_LEVELS : 1];
@@ -125,6 +133,23 @@ __global__ void __launch_bounds__(kReqBlock, RLXPP_REQ_MIN_BLOCKS)
   finish_cta(wc);
 }
 
+// Block shape of a tuning: 0 (the default, 128) or 64, 128, 256 threads per CTA on the
+// integer-pipe kernels, 128 only on the tensor kernel (one 128-row tile per CTA), and
+// no more than 2048 threads per SM.
+bool tuning_shape_ok(const rlxpp_tuning& t) {
+  const uint32_t tpb = tuning_tpb(t);
+  if (tpb != 64 && tpb != 128 && tpb != 256) return false;
+  if (t.path == RLXPP_PATH_TENSOR && tpb != 128) return false;
+  return t.blocks_per_sm * tpb <= 2048;
+}
+
+template <int TPB>
+void launch_requests_imad(const BatchArgs& b, const LuxTable& lt, uint32_t n_levels, bool multi, const Item* items,
+                          uint64_t n_items, WorkCounters* wc, unsigned grid, cudaStream_t st) {
+  if (multi) k_requests<true, TPB><<<grid, TPB, 0, st>>>(b, lt, n_levels, items, n_items, wc);
+  else k_requests<false, TPB><<<grid, TPB, 0, st>>>(b, lt, 1, items, n_items, wc);
+}
+
 uint32_t log2_floor(uint64_t v) {
   uint32_t r = 0;
   while (v > 1) {
@@ -152,7 +177,9 @@ void append_cache_line(const rlxpp_gen* g, uint32_t sig, const rlxpp_tuning& t) 
   if (!path || !*path) return;
   std::lock_guard<std::mutex> lock(g_cache_mutex);
   std::ofstream f(path, std::ios::app);
-  if (f) f << device_key(g) << "|" << sig << "|" << t.chunk_blocks << "|" << t.blocks_per_sm << "|" << t.path << "\n";
+  if (f)
+    f << device_key(g) << "|" << sig << "|" << t.chunk_blocks << "|" << t.blocks_per_sm << "|" << t.path << "|"
+      << t.threads_per_block << "\n";
 }
 
 // Refills a request needs after its start block.
@@ -176,13 +203,14 @@ void load_tune_cache(rlxpp_gen* g) {
   const std::string key = device_key(g);
   std::string line;
   while (std::getline(f, line)) {
-    // <device>/<sms>|<signature>|<chunk_blocks>|<blocks_per_sm>|<path>
+    // <device>/<sms>|<signature>|<chunk_blocks>|<blocks_per_sm>|<path>[|<threads_per_block>]
     const size_t a = line.find('|');
     if (a == std::string::npos || line.compare(0, a, key) != 0) continue;
-    unsigned sig = 0, L = 0, bps = 0, path = 0;
-    if (std::sscanf(line.c_str() + a + 1, "%u|%u|%u|%u", &sig, &L, &bps, &path) == 4 && L >= 2 && bps >= 1 &&
-        bps <= 8 && path <= RLXPP_PATH_WARP)
-      g->tuned[sig] = rlxpp_tuning{L, bps, path};  // later lines win
+    unsigned sig = 0, L = 0, bps = 0, path = 0, tpb = 0;
+    const int got = std::sscanf(line.c_str() + a + 1, "%u|%u|%u|%u|%u", &sig, &L, &bps, &path, &tpb);
+    const rlxpp_tuning t{L, bps, path, got == 5 ? tpb : 0u};
+    if (got >= 4 && L >= 2 && bps >= 1 && bps <= 8 && path <= RLXPP_PATH_WARP && tuning_shape_ok(t))
+      g->tuned[sig] = t;  // later lines win
   }
 }
 
@@ -301,12 +329,16 @@ rlxpp_status plan_impl(rlxpp_gen* g, const rlxpp_request* reqs, uint64_t n_reqs,
       if (L_host > L) L = L_host;
       uint32_t p2 = 4;
       while (p2 < L && p2 < 256) p2 <<= 1;
-      t = rlxpp_tuning{p2, 4, g->path};  // the handle's path: its request kernel
+      t = rlxpp_tuning{p2, 4, g->path, 0};  // the handle's path: its request kernel
     }
   }
   if (t.chunk_blocks < 2 || t.blocks_per_sm < 1 || t.blocks_per_sm > 8 ||
       (t.path != RLXPP_PATH_IMAD && t.path != RLXPP_PATH_TENSOR && t.path != RLXPP_PATH_WARP))
     return set_last_error(RLXPP_ERR_INVALID, "tuning needs chunk_blocks >= 2, 1..8 blocks per SM and a path");
+  if (!tuning_shape_ok(t))
+    return set_last_error(RLXPP_ERR_INVALID,
+                          "tuning needs 64, 128 or 256 threads per block (128 on the tensor path) and at most "
+                          "2048 threads per SM");
   const uint64_t L = t.chunk_blocks;
   // chunks
   std::vector<Item> items;
@@ -500,17 +532,22 @@ rlxpp_status run_impl(rlxpp_gen* g, const rlxpp_plan* p, uint32_t* out_u24, doub
     if (p->tuning.path == RLXPP_PATH_TENSOR && g->tc_matrix && p->tiles) {
       e = launch_requests_tc(b, p->items, p->tiles, p->n_tiles, g->tc_matrix, p->wc, grid, st);
     } else if (p->tuning.path == RLXPP_PATH_WARP) {
-      e = launch_requests_warp(b, p->items, p->n_items, p->wc, grid, st);
+      e = launch_requests_warp(b, p->items, p->n_items, p->wc, grid, tuning_tpb(p->tuning), st);
     } else {
       LuxTable lt{};
       for (uint32_t l = 0; l < g->n_levels; ++l) lt.L[l] = g->lux_host[l];
-      if (p->levels_used > 1) {
-        k_requests<true><<<grid, kReqBlock, 0, st>>>(b, lt, g->n_levels, p->items, p->n_items, p->wc);
-      } else {
+      uint32_t n_lv = g->n_levels;
+      const bool multi = p->levels_used > 1;
+      if (!multi) {
         uint32_t l = 0;
         while (l + 1 < g->n_levels && p->level_begin[l + 1] == p->level_begin[l]) ++l;  // the one level used
         lt.L[0] = g->lux_host[l];
-        k_requests<false><<<grid, kReqBlock, 0, st>>>(b, lt, 1, p->items, p->n_items, p->wc);
+        n_lv = 1;
+      }
+      switch (tuning_tpb(p->tuning)) {
+        case 64: launch_requests_imad<64>(b, lt, n_lv, multi, p->items, p->n_items, p->wc, grid, st); break;
+        case 256: launch_requests_imad<256>(b, lt, n_lv, multi, p->items, p->n_items, p->wc, grid, st); break;
+        default: launch_requests_imad<128>(b, lt, n_lv, multi, p->items, p->n_items, p->wc, grid, st); break;
       }
       e = cudaGetLastError();
     }
@@ -535,7 +572,7 @@ rlxpp_status rlxpp_run_plan(rlxpp_gen* gen, const rlxpp_plan* plan, uint32_t* ou
 
 uint64_t rlxpp_plan_items(const rlxpp_plan* plan) { return plan ? plan->n_items : 0; }
 
-rlxpp_tuning rlxpp_plan_tuning(const rlxpp_plan* plan) { return plan ? plan->tuning : rlxpp_tuning{0, 0, 0}; }
+rlxpp_tuning rlxpp_plan_tuning(const rlxpp_plan* plan) { return plan ? plan->tuning : rlxpp_tuning{0, 0, 0, 0}; }
 
 void rlxpp_destroy_plan(rlxpp_plan* plan) {
   if (plan) cudaSetDevice(plan->gen->device);
@@ -566,7 +603,7 @@ rlxpp_status rlxpp_autotune_requests(rlxpp_gen* gen, const rlxpp_request* reqs, 
   cudaEvent_t e0, e1;
   if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
     return set_last_error(RLXPP_ERR_CUDA, "cudaEventCreate failed");
-  rlxpp_tuning bestt{0, 0, 0};
+  rlxpp_tuning bestt{0, 0, 0, 0};
   float best_ms = 1e30f;
   rlxpp_status status = RLXPP_OK;
   // chunk lengths from the one giving ~64 chunks per resident thread (shorter ones only
@@ -580,15 +617,22 @@ rlxpp_status rlxpp_autotune_requests(rlxpp_gen* gen, const rlxpp_request* reqs, 
   for (uint32_t L = L0; L <= 1024 && status == RLXPP_OK; L <<= 1) {
     if (path == RLXPP_PATH_TENSOR && !gen->tc_matrix) break;
     if (L > L0 && L / 2 >= std::max<uint64_t>(longest, 4)) break;  // longer chunks change nothing
-    rlxpp_tuning t{L, 4, path};
+    rlxpp_tuning t{L, 4, path, 0};
     rlxpp_plan* p = nullptr;
     status = plan_impl(gen, reqs, n_reqs, 0, &t, &p);
     if (status != RLXPP_OK) break;
-    // resident CTAs per SM: the tensor kernel's 48 KB of shared memory and 128 TMEM
-    // columns allow four, the others are bounded by registers
-    const uint32_t bps_lo = path == RLXPP_PATH_WARP ? 4 : 2;
-    const uint32_t bps_hi = path == RLXPP_PATH_WARP ? 8 : 4;
-    for (uint32_t bps = bps_lo; bps <= bps_hi && status == RLXPP_OK; bps += (path == RLXPP_PATH_WARP ? 2 : 1)) {
+    // block shape and resident CTAs per SM: the tensor kernel's 48 KB of shared memory
+    // and 128 TMEM columns allow four 128-thread CTAs; the integer-pipe kernels are
+    // bounded by registers (up to 640 threads per SM with one thread per chunk, 512 with
+    // a warp per chunk)
+    static const uint32_t shapes[3][7][2] = {
+        {{64, 4}, {64, 8}, {128, 2}, {128, 3}, {128, 4}, {256, 1}, {256, 2}},  // IMAD
+        {{128, 2}, {128, 3}, {128, 4}, {0, 0}, {0, 0}, {0, 0}, {0, 0}},          // TENSOR
+        {{64, 4}, {64, 8}, {128, 2}, {128, 4}, {256, 1}, {256, 2}, {0, 0}},     // WARP
+    };
+    for (int k = 0; k < 7 && shapes[path][k][0] != 0 && status == RLXPP_OK; ++k) {
+      const uint32_t tpb = shapes[path][k][0], bps = shapes[path][k][1];
+      p->tuning.threads_per_block = tpb;
       p->tuning.blocks_per_sm = bps;
       float ms = 1e30f;
       for (int rep = 0; rep < 3 && status == RLXPP_OK; ++rep) {  // first run warms up
@@ -602,7 +646,7 @@ rlxpp_status rlxpp_autotune_requests(rlxpp_gen* gen, const rlxpp_request* reqs, 
       }
       if (status == RLXPP_OK && ms < best_ms) {
         best_ms = ms;
-        bestt = rlxpp_tuning{L, bps, path};
+        bestt = rlxpp_tuning{L, bps, path, tpb};
       }
     }
     free_plan(p, nullptr, false);

@@ -85,8 +85,12 @@ __device__ __forceinline__ void finish_cta(WorkCounters* wc) {
 cudaError_t launch_requests_tc(const BatchArgs& b, const Item* items, const TcTile* tiles, uint64_t n_tiles,
                                const void* bimg, WorkCounters* wc, unsigned grid, cudaStream_t st);
 // Warp-cooperative request kernel (one warp per chunk; rlxpp_warp.cu): every level in one
-// launch, the level's multiplier read from the state view's table.
+// launch, the level's multiplier read from the state view's table; tpb threads per CTA
+// (64, 128 or 256).
 cudaError_t launch_requests_warp(const BatchArgs& b, const Item* items, uint64_t n_items, WorkCounters* wc,
-                                 unsigned grid, cudaStream_t st);
+                                 unsigned grid, uint32_t tpb, cudaStream_t st);
+
+// Threads per CTA of a tuning (0: the default, 128).
+inline uint32_t tuning_tpb(const rlxpp_tuning& t) { return t.threads_per_block ? t.threads_per_block : 128u; }
 
 }  // namespace rlxpp

@@ -390,10 +390,11 @@ __global__ void __launch_bounds__(kWarpBlock) k_test_warp(int op, const uint64_t
 // start block with the single-thread table products; the warp then refills and emits as
 // k_draw_warp does, one value per lane, with the multiplier of the chunk's level read
 // from the level table.  For few, long chunks, where the latency of one refill is what
-// counts.
-__global__ void __launch_bounds__(kWarpBlock)
+// counts.  TPB: threads per CTA (the block shape the tuner picks).
+template <int TPB>
+__global__ void __launch_bounds__(TPB)
     k_requests_warp(const BatchArgs b, const Item* __restrict__ items, uint64_t n_items, WorkCounters* wc) {
-  __shared__ uint32_t scratch_s[kWarpsPerBlock][36];
+  __shared__ uint32_t scratch_s[TPB / 32][36];
   const unsigned l = lane_id();
   const int warp = threadIdx.x / 32;
   uint32_t* scratch = scratch_s[warp];
@@ -501,11 +502,15 @@ cudaError_t launch_warp_kind(const DrawArgs& a, cudaStream_t st) {
 }  // namespace
 
 cudaError_t launch_requests_warp(const BatchArgs& b, const Item* items, uint64_t n_items, WorkCounters* wc,
-                                 unsigned grid, cudaStream_t st) {
+                                 unsigned grid, uint32_t tpb, cudaStream_t st) {
   if (n_items == 0) return cudaSuccess;
-  const uint64_t need = (n_items + kWarpsPerBlock - 1) / kWarpsPerBlock;
+  if (tpb != 64 && tpb != 128 && tpb != 256) return cudaErrorInvalidValue;
+  const uint64_t warps = tpb / 32;
+  const uint64_t need = (n_items + warps - 1) / warps;
   if (grid > need) grid = (unsigned)need;
-  k_requests_warp<<<grid, kWarpBlock, 0, st>>>(b, items, n_items, wc);
+  if (tpb == 64) k_requests_warp<64><<<grid, 64, 0, st>>>(b, items, n_items, wc);
+  else if (tpb == 256) k_requests_warp<256><<<grid, 256, 0, st>>>(b, items, n_items, wc);
+  else k_requests_warp<128><<<grid, 128, 0, st>>>(b, items, n_items, wc);
   return cudaGetLastError();
 }
 

@@ -144,7 +144,7 @@ def test_config3_tuned_plan_every_request(native, batch_oracle, path):
     out_u = torch.full((nu + 1,), -1, dtype=torch.int32, device="cuda")
     tuned = native.rlxpp_autotune_requests(g.handle, reqs, out_u, out_f)
     pid = native.RLXPP_PATH_TENSOR if path == "tensor" else native.RLXPP_PATH_IMAD
-    plan = native.rlxpp_plan_requests(g.handle, reqs, 0, (tuned[0], tuned[1], pid))
+    plan = native.rlxpp_plan_requests(g.handle, reqs, 0, (tuned[0], tuned[1], pid, tuned[3] if pid == tuned[2] else 0))
     st = torch.cuda.current_stream()
     side = torch.cuda.Stream()
     side.wait_stream(st)

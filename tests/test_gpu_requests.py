@@ -134,6 +134,31 @@ def test_mixed_requests(native, path):
     assert xs2 == xs
 
 
+def test_block_shapes(native):
+    """Every block shape the tuner tries (64, 128, 256 threads per CTA on the integer
+    kernels, 128 on the tensor kernel) gives the oracle's values at mixed levels; shapes
+    outside them are refused when planning."""
+    n = 150
+    levels = [24, 389, 2048]
+    lvl = (np.arange(n) % 3).astype(np.uint8)
+    seeds = W.random_seeds(n, 211)
+    g = native.Generator(n, levels, torch.from_numpy(seeds.view(np.int64)).cuda(),
+                         torch.from_numpy(lvl).cuda())
+    xs, _ = current_X(native, g, n)
+    levels_of = [levels[int(lvl[i])] for i in range(n)]
+    rng = np.random.Generator(np.random.PCG64(212))
+    rows = [(i, int(rng.integers(0, 2 ** 20)), int(rng.integers(0, 25)), int(rng.integers(0, 2)),
+             int(rng.integers(0, 4000))) for i in range(n)]
+    reqs, nu, nf = make_requests(rows)
+    I, T, Wp = native.RLXPP_PATH_IMAD, native.RLXPP_PATH_TENSOR, native.RLXPP_PATH_WARP
+    for tuning in [(8, 4, I, 64), (8, 8, I, 64), (8, 1, I, 256), (8, 2, I, 256), (8, 3, T, 128),
+                   (8, 4, Wp, 64), (8, 2, Wp, 128), (8, 1, Wp, 256), (8, 2, Wp, 256)]:
+        run_and_check(native, g, xs, levels_of, reqs, nu, nf, tuning=tuning)
+    for bad in [(8, 2, T, 64), (8, 2, T, 256), (8, 2, I, 96), (8, 2, I, 512), (8, 8, I, 512)]:
+        with pytest.raises(native.RlxppError):
+            native.rlxpp_plan_requests(g.handle, reqs, 0, bad)
+
+
 def test_advance_flag_and_graph(native, path):
     n = 130
     seeds = W.consecutive_seeds(n, first=300)
@@ -215,11 +240,45 @@ def test_autotune(native, path):
     out_u = torch.zeros(max(nu, 1), dtype=torch.int32, device="cuda")
     out_f = torch.zeros(max(nf, 1), dtype=torch.float64, device="cuda")
     best = native.rlxpp_autotune_requests(g.handle, reqs, out_u, out_f)
-    assert best[0] >= 2 and 1 <= best[1] <= 8 and best[2] in (0, 1, 2)
+    assert best[0] >= 2 and 1 <= best[1] <= 8 and best[2] in (0, 1, 2) and best[3] in (64, 128, 256)
+    assert best[1] * best[3] <= 2048 and (best[2] != native.RLXPP_PATH_TENSOR or best[3] == 128)
     plan = native.rlxpp_plan_requests(g.handle, reqs)        # uses the tuned choice
     assert native.rlxpp_plan_tuning(plan) == best
     native.rlxpp_destroy_plan(plan)
     run_and_check(native, g, xs, [2048] * n, reqs, nu, nf)
+
+
+def test_tune_cache_file(native, tmp_path, monkeypatch):
+    """RLXPP_TUNE_CACHE: the tuner appends its choice (with the block shape) and a later
+    handle plans with it; a line without the block shape still reads (default shape)."""
+    cache = tmp_path / "tune.txt"
+    monkeypatch.setenv("RLXPP_TUNE_CACHE", str(cache))
+    n = 256
+    seeds = torch.from_numpy(W.consecutive_seeds(n).view(np.int64)).cuda()
+    rows = [(i, 0, 0, i % 2, 3000 + i) for i in range(n)]
+    reqs, nu, nf = make_requests(rows)
+    out_u = torch.zeros(max(nu, 1), dtype=torch.int32, device="cuda")
+    out_f = torch.zeros(max(nf, 1), dtype=torch.float64, device="cuda")
+    g = native.Generator(n, [2048], seeds)
+    best = native.rlxpp_autotune_requests(g.handle, reqs, out_u, out_f)
+    g.close()
+    line = cache.read_text().strip().splitlines()[-1].split("|")
+    assert len(line) == 6 and tuple(int(v) for v in line[2:]) == best
+    g2 = native.Generator(n, [2048], seeds)
+    plan = native.rlxpp_plan_requests(g2.handle, reqs)
+    assert native.rlxpp_plan_tuning(plan) == best
+    native.rlxpp_destroy_plan(plan)
+    g2.close()
+    # a line in the older five-field form, for the same shape, wins (later lines win)
+    with open(cache, "a") as f:
+        f.write("|".join(line[:2] + ["8", "3", str(native.RLXPP_PATH_IMAD)]) + "\n")
+    g3 = native.Generator(n, [2048], seeds)
+    xs, _ = current_X(native, g3, n)
+    plan = native.rlxpp_plan_requests(g3.handle, reqs)
+    assert native.rlxpp_plan_tuning(plan) == (8, 3, native.RLXPP_PATH_IMAD, 0)
+    native.rlxpp_destroy_plan(plan)
+    run_and_check(native, g3, xs, [2048] * n, reqs, nu, nf)
+    g3.close()
 
 
 def _captured_node_types(fn, stream):
