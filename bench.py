@@ -500,7 +500,11 @@ def bench_mixed_batch(nat, dev, args):
     refills = sum(advances_for(int(c), 0, 2 if f else 1)[0] for c, f in zip(counts, is_f64))
     st = torch.cuda.current_stream()
     t = time.perf_counter()
-    tuned = nat.rlxpp_autotune_requests(g.handle, reqs, out_u, out_f)  # picks the kernel too
+    if args.batch_tuning:  # a given tuning instead of the tuner's (to profile a known plan)
+        tuned = tuple(int(v) for v in args.batch_tuning.split(","))
+        assert len(tuned) == 4, "--batch-tuning needs chunk_blocks,blocks_per_sm,path,threads_per_block"
+    else:
+        tuned = nat.rlxpp_autotune_requests(g.handle, reqs, out_u, out_f)  # picks the kernel too
     tune_s = time.perf_counter() - t
     by_path = {}
     for name, pid in (("tensor", nat.RLXPP_PATH_TENSOR), ("imad", nat.RLXPP_PATH_IMAD), ("warp", nat.RLXPP_PATH_WARP)):
@@ -538,7 +542,8 @@ def bench_mixed_batch(nat, dev, args):
     values = int(counts.sum())
     return {"streams": n, "values": values, "doubles": n_f, "u24": n_u, "advances": int(refills),
             "output_bytes": n_u * 4 + n_f * 8,
-            "batched_graph": dict(by_path[best], path=best, tune_s=tune_s), "batched_graph_by_path": by_path,
+            "batched_graph": dict(by_path[best], path=best, tune_s=tune_s,
+                                   tuning_source="given" if args.batch_tuning else "tuner"), "batched_graph_by_path": by_path,
             "plain_per_stream": {"ms": ms_plain, "values_per_s": values / (ms_plain * 1e-3),
                                  "advances_per_s": refills / (ms_plain * 1e-3)},
             "speedup_vs_plain": ms_plain / ms_graph}
@@ -720,6 +725,9 @@ def main():
                     help="run only the mixed batch on --batch-streams streams (for profiling)")
     ap.add_argument("--path", default="imad,tensor", help="refill paths to time; the faster one is reported")
     ap.add_argument("--batch-streams", type=int, default=65536)
+    ap.add_argument("--batch-tuning", default="",
+                    help="chunk_blocks,blocks_per_sm,path,threads_per_block for the mixed batch instead of "
+                         "the tuner's choice (profiling)")
     ap.add_argument("--serve-seconds", type=float, default=10.0)
     ap.add_argument("--serve-streams", type=int, default=4)
     ap.add_argument("--serve-max-batch", type=int, default=512)
