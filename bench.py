@@ -48,12 +48,12 @@ ALU_PER_SM_CLK = 64
 TC_FLOP_PER_ADVANCE = 2 * 80 * 80      # padded 128 x 80 x 80 fp16 product per 128 streams
 TC_ALG_FLOP_PER_ADVANCE = 2 * 72 * 72  # the 5,184 byte products of the 72 x 72 folded matrix
 CPU_SAMPLE_STREAMS = 16384
-# Figures of one ncu capture of the fused tensor kernel (k_draw_tc<sum/hist>): DRAM
+# Figures of one ncu capture of the fused tensor kernel (k_fused_tc): DRAM
 # bytes (read + write) per stream and launch, and ALU-pipe instructions per refill.
 # They describe the kernel as compiled from the sources whose digest is `src_sha`
 # (kernel_sources_sha); once those sources change, the figures are reported as null.
-TC_FUSED_CAPTURE = {"dram_bytes_per_stream": 76.2, "alu_instr_per_refill": 172, "streams": 262144,
-                    "src_sha": "42ab54e88fb33d36"}
+TC_FUSED_CAPTURE = {"dram_bytes_per_stream": 76.2, "alu_instr_per_refill": 170, "streams": 262144,
+                    "src_sha": "078a879d83edd728"}
 KERNEL_SOURCES = ("rlxpp_tensor.cu", "rlxpp_arith.cuh", "rlxpp_drawloop.cuh", "rlxpp_state.cuh",
                   "rlxpp_internal.h", "rlxpp_batch.h", "rlxpp_fixmath.cuh", "rlxpp_fixmath_tables.h")
 
@@ -380,7 +380,8 @@ def run_native(args, rank, world, local_rank):
                     "frac": achieved / (imad_peak / 1e12),
                     "peak_source": "derived: 152 SMs x 64 IMAD/clk x 2070 MHz", "traffic": None}
     else:
-        roofline = tensor_roofline(dom + " (k_draw_tc, tensor path)", adv, per_kernel[dom], f16_peak,
+        tc_name = {"draw_f64_sum_hist": "k_fused_tc", "draw_f64_hbm": "k_values_tc<f64>"}.get(dom, "k_seed")
+        roofline = tensor_roofline(f"{dom} ({tc_name}, tensor path)", adv, per_kernel[dom], f16_peak,
                                    "MEASURED_PEAKS bf16_tflops (burst; dense fp16 runs at the bf16 rate)", n)
     for name in paths:
         paths[name].pop("per_kernel_ms")
