@@ -360,11 +360,12 @@ void rlxpp_destroy(rlxpp_gen* gen);
  * device, at every call, into one fixed array of the library (184,608 bytes, room for
  * RLXPP_NOALLOC_MAX_LEVELS levels) that every GPU loading the library holds until the
  * process exits.  The call allocates nothing (no cudaMalloc, cudaFree or allocating
- * library routine).  The first call on a device looks up the array's device address
- * with that device current (cudaGetSymbolAddress) and keeps it for later calls; make
- * that first call before any stream capture, and do not call the entry point again
- * after a cudaDeviceReset in the same process (the kept address would no longer be
- * the array's).  Device memory of another GPU is rejected with RLXPP_ERR_INVALID.  All calls share the array and it keeps the last call's contents:
+ * library routine).  Every call looks up the array's device address in the current
+ * device's context (cudaGetSymbolAddress, a host query), so a context reset between
+ * calls is harmless; the first lookup in a context may load the library's device
+ * code, which a stream capture does not allow, so make one call outside any capture
+ * first (after a cudaDeviceReset too).  Device memory of another GPU is rejected with
+ * RLXPP_ERR_INVALID.  All calls share the array and it keeps the last call's contents:
  * calls that overlap on the GPU (on different streams or from different threads) race
  * and must be serialised by the caller.  Each call costs the table set-up of its
  * levels (a few short kernels per level) plus one seeding kernel. */

@@ -4,7 +4,6 @@
 // Seeding and skipping follow Sec. 2.4: exponentiation by squaring, here with a
 // 4-bit fixed window whose powers A^(j 16^w) are tabulated once per luxury level, so
 // that a stream needs one modular product per non-zero exponent digit.
-#include <mutex>
 
 #include "rlxpp_arith.cuh"
 #include "rlxpp_fixmath.cuh"
@@ -412,29 +411,18 @@ __global__ void k_seed_records(const uint32_t* __restrict__ scratch, LevelList l
   rec[10] = lv.p[lvl];              // reserved 0
 }
 
-// Device address of g_noalloc_scratch, looked up once per device (with that device
-// current) the first time the entry point runs on it.  The address stays valid for the
-// life of the device's primary context: a cudaDeviceReset between calls would leave it
-// dangling, so the entry point must not be used across a reset.
-constexpr int kMaxDevices = 64;
-std::mutex g_noalloc_mutex;
-uint32_t* g_noalloc_ptr[kMaxDevices] = {};
-
+// Device address of g_noalloc_scratch in the current device's context, looked up on
+// every call (a host-side query, no stream work), so that a context torn down and
+// recreated between calls (cudaDeviceReset) never leaves a stale address behind.  The
+// first lookup in a context may load the module, which a stream capture does not allow:
+// hence the rule that the entry point runs once outside any capture first.
 rlxpp_status noalloc_scratch(uint32_t** out) {
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess) return set_last_error(RLXPP_ERR_CUDA, cudaGetErrorString(e));
-  if (dev < 0 || dev >= kMaxDevices) return set_last_error(RLXPP_ERR_UNSUPPORTED, "device ordinal >= 64");
-  std::lock_guard<std::mutex> lock(g_noalloc_mutex);
-  if (!g_noalloc_ptr[dev]) {
-    void* p = nullptr;
-    e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-    if (e != cudaSuccess || p == nullptr)
-      return set_last_error(RLXPP_ERR_CUDA, e != cudaSuccess ? cudaGetErrorString(e)
-                                                            : "no device address for the scratch array");
-    g_noalloc_ptr[dev] = static_cast<uint32_t*>(p);
-  }
-  *out = g_noalloc_ptr[dev];
+  void* p = nullptr;
+  const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+  if (e != cudaSuccess || p == nullptr)
+    return set_last_error(RLXPP_ERR_CUDA, e != cudaSuccess ? cudaGetErrorString(e)
+                                                          : "no device address for the scratch array");
+  *out = static_cast<uint32_t*>(p);
   return RLXPP_OK;
 }
 
