@@ -129,10 +129,11 @@ def normals_expected(doubles, n):
 
 def exponentials_expected(doubles):
     """Exponential values x = -ln(1 - d) from each double, with a per-value tolerance:
-    (want, tol).  Each side's log is within about 1 ulp of x (CUDA's stated bound for the
-    device log; numpy's log is closer), an ulp of x is at most 2^-52 x, so the two differ
-    by at most 2^-51 x; the tolerance 2^-50 (x + 1) leaves a factor of two and an absolute
-    floor for x near 0."""
+    (want, tol).  The device computes -ln with its own fixed-point integer routine
+    (relative error below 2^-61 before its one final rounding), so its value lies within
+    half an ulp plus 2^-60 x of the exact one; numpy's log is within about an ulp.  An ulp
+    of x is at most 2^-52 x, so the two differ by well under 2^-51 x; the tolerance
+    2^-50 (x + 1) leaves a factor of two and an absolute floor for x near 0."""
     d = np.asarray(doubles, dtype=np.float64)
     want = 0.0 - np.log(1.0 - d)
     return want, 2.0 ** -50 * (want + 1.0)
