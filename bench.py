@@ -689,14 +689,16 @@ def run_e2e(args, nat, g, seeds_h, n, world, dev, dist):
         link.append((8 << 27) / (e0.elapsed_time(e1) * 1e-3) / 1e9)
     del probe
     link_gbs = sorted(link)[1]
-    steps = max(1, min(args.steps, 3))
+    steps = max(1, min(args.steps, 5))
     step()
     if dist is not None:
         dist.barrier()
     torch.cuda.synchronize()
     t0 = time.perf_counter()
+    marks = [t0]
     for _ in range(steps):
         step()
+        marks.append(time.perf_counter())
     torch.cuda.synchronize()
     dt = max_over_ranks(time.perf_counter() - t0, dist, dev)
     doubles = n * (HBM_COUNT + FUSED_COUNT) * world * steps
@@ -704,6 +706,7 @@ def run_e2e(args, nat, g, seeds_h, n, world, dev, dist):
     return {"value": doubles / dt, "unit": UNIT, "h2d_bytes_per_step": n * 8,
             "d2h_bytes_per_step": d2h, "steps": steps, "d2h_link_gbs": round(link_gbs, 1),
             "link_frac": round(d2h * steps / dt / 1e9 / link_gbs, 3),
+            "step_ms": [round((b - a) * 1e3, 2) for a, b in zip(marks, marks[1:])],
             "how": "rlxpp_seed from pinned host seeds, rlxpp_draw_f64_host_async into pinned host memory "
                    "(library-staged, copied on the library's copy stream while the fused sum/hist draw runs), "
                    "sums+hist read back, rlxpp_host_wait; wall clock"}

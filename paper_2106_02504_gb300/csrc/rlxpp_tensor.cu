@@ -1137,10 +1137,11 @@ static_assert(kBRegion + 1024 + 2 * kValuesBox <= kValuesSmem, "value draw share
 
 // Value-writing draws (u24, f32, f64) with one count for every stream and the output as
 // a [n][count] tensor (tmap), on one-tile CTAs with the A operand in TMEM.  Same
-// semantics as k_draw_tc.  The refill loop is the fused draw's: wait for the product,
-// form X and write it as the next operand row (every thread), one CTA barrier, thread 0
-// issues the next product, then every thread converts X to RANLUX numbers and stages
-// its block.  When every live stream of the tile starts at the tile's first position
+// semantics as k_draw_tc.  The refill loop is the fused draw's, with the same operand
+// rows (the RANLUX numbers D and the borrow c) and level matrix (k_tc_matrix_d's): wait
+// for the product, form X, convert it to D and c and write them as the next operand row
+// (every thread), one CTA barrier, thread 0 issues the next product, then every thread
+// builds its block's values and stages them.  When every live stream of the tile starts at the tile's first position
 // (then they move in step), the blocks of a refill leave as one TMA tensor store of the
 // [128][96 B] staging box, issued by thread 0 after the next barrier; two boxes
 // alternate, and thread 0 waits for a store to have read its box before the barrier
@@ -1148,14 +1149,14 @@ static_assert(kBRegion + 1024 + 2 * kValuesBox <= kValuesSmem, "value draw share
 // from registers.
 template <int Kind>
 __global__ void __launch_bounds__(kTcRows, 4)
-    k_values_tc(const DrawArgs a, const __half* __restrict__ bimg, const __grid_constant__ CUtensorMap tmap) {
+    k_values_tc(const DrawArgs a, const __half* __restrict__ bimg_d, const __grid_constant__ CUtensorMap tmap) {
   extern __shared__ __align__(1024) unsigned char smem[];
   const int tid = threadIdx.x;
   ValuesShared* sh = reinterpret_cast<ValuesShared*>(smem + kBRegion);
   unsigned char* box0 = smem + kBRegion + 1024;
   const __half* bmat = tc_bmat(smem);
   {
-    const uint4* src = reinterpret_cast<const uint4*>(bimg);
+    const uint4* src = reinterpret_cast<const uint4*>(bimg_d);
     uint4* dst = reinterpret_cast<uint4*>(tc_bmat(smem));
     for (int w = tid; w < kBBytes / 16; w += kTcRows) dst[w] = src[w];
   }
@@ -1171,10 +1172,6 @@ __global__ void __launch_bounds__(kTcRows, 4)
   tc_fence_after();
   const uint32_t taddr = sh->taddr;
   const uint32_t lane_taddr = taddr + ((uint32_t)((tid / 32) * 32) << 16);
-  {
-    const uint32_t cst[4] = {0x3C006800u, 0u, 0u, 0u};  // 2048 and 1 at k = 72, 73
-    tmem_st4(lane_taddr + kTmA + 36, cst);
-  }
   const uint32_t b0 = smem_addr(bmat);
 
   constexpr int need = (Kind == kDrawU24 || Kind == kDrawF32) ? 1 : 2;
@@ -1221,9 +1218,7 @@ __global__ void __launch_bounds__(kTcRows, 4)
   const uint32_t tail = (uint32_t)((cnt - k) % per_block);
   const int64_t iters = cta_max(nref, &sh->iters);
   const int y0 = (int)((uint64_t)blockIdx.x * kTcRows);
-  uint32_t X[kLimbs];
-  to_lcg(D, c, X);
-  write_x_tmem(lane_taddr, X);
+  write_d_tmem(lane_taddr, D, c);
   tmem_wait_st();
   tc_fence_before();
   __syncthreads();
@@ -1253,9 +1248,10 @@ __global__ void __launch_bounds__(kTcRows, 4)
         tmem_ld64(lane_taddr, col);
         tmem_ld8(lane_taddr + 64, col + 64);
         tmem_wait_ld();
-        tc_fold_common(col, X);
-        __syncwarp();  // reconverged after the rare fold, before the warp-wide store
-        write_x_tmem(lane_taddr, X);
+        uint32_t X[kLimbs];
+        tc_epilogue_d(col, X, D, c);
+        __syncwarp();  // reconverged after the rare branch, before the warp-wide store
+        write_d_tmem(lane_taddr, D, c);
         tmem_wait_st();
       } else {
         sh->abort = 1u;
@@ -1282,7 +1278,6 @@ __global__ void __launch_bounds__(kTcRows, 4)
         pending = false;
       }
       if (j < n_mine) {  // this stream's block, while the next product computes
-        to_ranlux(X, D);
         const int64_t kj = k_chunk + (int64_t)j * per_block;
         const bool full = j != j_last || tail == 0;
         if (tma) {  // the whole block into this thread's row of the box; past the count it is clipped
@@ -1302,7 +1297,7 @@ __global__ void __launch_bounds__(kTcRows, 4)
           out.partial(D, base + kj, tail);
         }
         if (j == j_last) {
-          c_fin = carry_of(X, D);
+          c_fin = c;
           store_state_D(s, i, D);
           stored = true;
         }
@@ -1761,7 +1756,7 @@ bool encode_output_map(const DrawArgs& a, CUtensorMap* map) {
 }
 
 template <int Kind>
-cudaError_t launch_tc_kind(const DrawArgs& a, const __half* bimg, cudaStream_t st) {
+cudaError_t launch_tc_kind(const DrawArgs& a, const __half* bimg, const __half* bimg_d, cudaStream_t st) {
   constexpr int T = tc_groups<Kind>();
   // one-group CTAs keep 48 KB so that at most 4 share an SM (512 TMEM columns)
   constexpr int smem_bytes = T == 1 ? (int)kTcSmem : tc_smem_bytes(T, Kind != kDrawSumHist);
@@ -1777,7 +1772,7 @@ cudaError_t launch_tc_kind(const DrawArgs& a, const __half* bimg, cudaStream_t s
       cudaError_t e = cudaFuncSetAttribute(k_values_tc<Kind>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                            kValuesSmem);
       if (e != cudaSuccess) return e;
-      k_values_tc<Kind><<<(unsigned)tiles, kTcRows, kValuesSmem, st>>>(a, bimg, map);
+      k_values_tc<Kind><<<(unsigned)tiles, kTcRows, kValuesSmem, st>>>(a, bimg_d, map);
       return cudaGetLastError();
     }
   }
@@ -1823,13 +1818,14 @@ cudaError_t launch_tc_matrix_d(const uint32_t* lux18, void* bimg, cudaStream_t s
 cudaError_t launch_draw_tc(int kind, const DrawArgs& a, const void* bimg, const void* bimg_d, cudaStream_t st) {
   if (a.s.n == 0) return cudaSuccess;
   const __half* b = static_cast<const __half*>(bimg);
+  const __half* bd = static_cast<const __half*>(bimg_d);
   switch (kind) {
-    case kDrawU24: return launch_tc_kind<kDrawU24>(a, b, st);
-    case kDrawF64: return launch_tc_kind<kDrawF64>(a, b, st);
-    case kDrawSumHist: return launch_fused_tc(a, static_cast<const __half*>(bimg_d), st);
-    case kDrawF32: return launch_tc_kind<kDrawF32>(a, b, st);
-    case kDrawNormal: return launch_tc_kind<kDrawNormal>(a, b, st);
-    case kDrawExp: return launch_tc_kind<kDrawExp>(a, b, st);
+    case kDrawU24: return launch_tc_kind<kDrawU24>(a, b, bd, st);
+    case kDrawF64: return launch_tc_kind<kDrawF64>(a, b, bd, st);
+    case kDrawSumHist: return launch_fused_tc(a, bd, st);
+    case kDrawF32: return launch_tc_kind<kDrawF32>(a, b, bd, st);
+    case kDrawNormal: return launch_tc_kind<kDrawNormal>(a, b, bd, st);
+    case kDrawExp: return launch_tc_kind<kDrawExp>(a, b, bd, st);
   }
   return cudaErrorInvalidValue;
 }
