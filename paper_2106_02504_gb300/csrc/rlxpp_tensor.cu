@@ -1128,12 +1128,17 @@ struct ValuesShared {
   uint32_t abort;               // a wait for the product timed out
   unsigned long long iters;     // refills of the tile
   uint32_t pos0;                // read position of the tile's first stream at entry
+  int box_x[2];                 // first column of the block staged in each box
+  uint32_t box_pending[2];      // a staged box waits for its store
 };
 // Shared memory: the level's matrix, the shared words, two [128][96 B] staging boxes;
 // 48 KB in all, so that at most four CTAs (4 x 128 TMEM columns) share an SM.
 constexpr int kValuesBox = kTcRows * kStageBytes;  // 12 KB
 constexpr int kValuesSmem = 48 * 1024;
 static_assert(kBRegion + 1024 + 2 * kValuesBox <= kValuesSmem, "value draw shared memory");
+// The thread that issues the tile-wide stores: lane 0 of warp 1, so that warp 0, which
+// issues the products, does not also carry the stores' waits into every barrier.
+constexpr int kStoreTid = 32;
 
 // Value-writing draws (u24, f32, f64) with one count for every stream and the output as
 // a [n][count] tensor (tmap), on one-tile CTAs with the A operand in TMEM.  Same
@@ -1141,12 +1146,13 @@ static_assert(kBRegion + 1024 + 2 * kValuesBox <= kValuesSmem, "value draw share
 // rows (the RANLUX numbers D and the borrow c) and level matrix (k_tc_matrix_d's): wait
 // for the product, form X, convert it to D and c and write them as the next operand row
 // (every thread), one CTA barrier, thread 0 issues the next product, then every thread
-// builds its block's values and stages them.  When every live stream of the tile starts at the tile's first position
-// (then they move in step), the blocks of a refill leave as one TMA tensor store of the
-// [128][96 B] staging box, issued by thread 0 after the next barrier; two boxes
-// alternate, and thread 0 waits for a store to have read its box before the barrier
-// after which that box is written again.  Tiles out of step write each stream's values
-// from registers.
+// builds its block's values and stages them.  When every live stream of the tile starts
+// at the tile's first position (then they move in step), the blocks of a refill leave as
+// one TMA tensor store of the [128][96 B] staging box, issued by thread kStoreTid after
+// the next barrier (thread 0 records the box's column in shared memory: it is live
+// whenever any thread is); two boxes alternate, and thread kStoreTid waits for a store
+// to have read its box before the barrier after which that box is written again.  Tiles
+// out of step write each stream's values from registers.
 template <int Kind>
 __global__ void __launch_bounds__(kTcRows, 4)
     k_values_tc(const DrawArgs a, const __half* __restrict__ bimg_d, const __grid_constant__ CUtensorMap tmap) {
@@ -1164,6 +1170,7 @@ __global__ void __launch_bounds__(kTcRows, 4)
     mbar_init(&sh->bar, 1);
     fence_barrier_init();
     sh->abort = 0;
+    sh->box_pending[0] = sh->box_pending[1] = 0u;
   }
   if (tid < 32) tmem_alloc(&sh->taddr, kTmCols);
   fence_proxy_async_smem();
@@ -1226,10 +1233,11 @@ __global__ void __launch_bounds__(kTcRows, 4)
   if (iters > 0 && tid == 0) tc_issue_tm(taddr, b0, &sh->bar);
   uint32_t phase = 0, c_fin = c;
   bool ok = true, inflight = iters > 0, stored = false;
-  int box_x[2] = {0, 0};  // thread 0: first column of the block staged in each box
-  bool pending = false;   // thread 0: a staged box waits for its store
-  // refills in chunks of at most 2^20 (an even count, so a box's parity is the
-  // refill's), counted in 32 bits within a chunk
+  uint32_t box = 0;  // this refill's staging box (the refill's index mod 2)
+  volatile uint32_t* vpend = sh->box_pending;
+  volatile int* vbox_x = sh->box_x;
+  const bool store_thread = tid == kStoreTid;
+  // refills in chunks of at most 2^20, counted in 32 bits within a chunk
   for (int64_t it0 = 0; ok && it0 < iters;) {
     const uint32_t n_in = (uint32_t)(iters - it0 > kFusedFlush ? kFusedFlush : iters - it0);
     const bool more_after = it0 + n_in < iters;
@@ -1256,7 +1264,7 @@ __global__ void __launch_bounds__(kTcRows, 4)
       } else {
         sh->abort = 1u;
       }
-      if (tma && tid == 0) bulk_wait_read_all();  // the last store has read its box
+      if (tma && store_thread) bulk_wait_read_all();  // the last store has read its box
       tc_fence_before();
       __syncthreads();
       tc_fence_after();
@@ -1268,14 +1276,16 @@ __global__ void __launch_bounds__(kTcRows, 4)
         if (tid == 0) tc_issue_tm(taddr, b0, &sh->bar);
         inflight = true;
       }
-      if (tid == 0 && pending) {  // the blocks staged before this barrier
-        const uint32_t pb = (j + 1u) & 1u;
-        asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%1, %2}], [%3];" ::"l"(
-                         reinterpret_cast<uint64_t>(&tmap)),
-                     "r"(box_x[pb]), "r"(y0), "r"(smem_addr(box0 + pb * kValuesBox))
-                     : "memory");
-        asm volatile("cp.async.bulk.commit_group;" ::: "memory");
-        pending = false;
+      if (store_thread) {  // the box staged before this barrier
+        const uint32_t pb = box ^ 1u;
+        if (vpend[pb]) {
+          vpend[pb] = 0u;
+          asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%1, %2}], [%3];" ::"l"(
+                           reinterpret_cast<uint64_t>(&tmap)),
+                       "r"(vbox_x[pb]), "r"(y0), "r"(smem_addr(box0 + pb * kValuesBox))
+                       : "memory");
+          asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+        }
       }
       if (j < n_mine) {  // this stream's block, while the next product computes
         const int64_t kj = k_chunk + (int64_t)j * per_block;
@@ -1283,13 +1293,13 @@ __global__ void __launch_bounds__(kTcRows, 4)
         if (tma) {  // the whole block into this thread's row of the box; past the count it is clipped
           uint4 v[6];
           block_values<Kind>(D, v);
-          uint4* row = reinterpret_cast<uint4*>(box0 + (j & 1u) * kValuesBox + tid * kStageBytes);
+          uint4* rowp = reinterpret_cast<uint4*>(box0 + box * kValuesBox + tid * kStageBytes);
 #pragma unroll
-          for (int q = 0; q < 6; ++q) row[q] = v[q];
+          for (int q = 0; q < 6; ++q) rowp[q] = v[q];
           fence_proxy_async_smem();
           if (tid == 0) {
-            box_x[j & 1u] = (int)kj;
-            pending = true;
+            vbox_x[box] = (int)kj;
+            vpend[box] = 1u;
           }
         } else if (full) {
           out.block(D, base + kj);
@@ -1302,6 +1312,7 @@ __global__ void __launch_bounds__(kTcRows, 4)
           stored = true;
         }
       }
+      box ^= 1u;
     }
     it0 += n_in;
   }
@@ -1311,15 +1322,17 @@ __global__ void __launch_bounds__(kTcRows, 4)
   }
   if (ok && tma && iters > 0) {  // the last staged box
     __syncthreads();
-    if (tid == 0 && pending) {
+    const uint32_t pb = box ^ 1u;
+    if (store_thread && vpend[pb]) {
+      vpend[pb] = 0u;
       asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%1, %2}], [%3];" ::"l"(
                        reinterpret_cast<uint64_t>(&tmap)),
-                   "r"(box_x[(iters - 1) & 1]), "r"(y0), "r"(smem_addr(box0 + ((iters - 1) & 1) * kValuesBox))
+                   "r"(vbox_x[pb]), "r"(y0), "r"(smem_addr(box0 + pb * kValuesBox))
                    : "memory");
       asm volatile("cp.async.bulk.commit_group;" ::: "memory");
     }
   }
-  if (tid == 0) bulk_wait_all();  // every store of this CTA is done
+  if (store_thread) bulk_wait_all();  // every store of this CTA is done
   if (live && (ok || stored)) s.meta[i] = meta_pack(pos, c_fin, lvl);
   if (!ok && tid == 0) atomicCAS(s.status, 0, (int)RLXPP_ERR_TIMEOUT);
   if (inflight) (void)mbar_wait_bounded(&sh->bar, phase);
