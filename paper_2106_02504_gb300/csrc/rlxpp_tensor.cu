@@ -894,6 +894,7 @@ struct FusedAcc {
 // and the FusedShared words.  With the 32 KB table, a CTA takes 46 KB, so at most four
 // share an SM and their 4 x 128 TMEM columns always fit.
 constexpr int kFusedDynSmem = kBRegion + 1024;
+constexpr int kFusedThreads = kTcRows + 32;  // four compute warps (one tile) and the issuer warp
 
 // Largest value of v over the CTA's threads (v >= 0), through one shared word.
 __device__ __forceinline__ int64_t cta_max(int64_t v, unsigned long long* word) {
@@ -941,29 +942,34 @@ struct FusedShared {
 // k_draw_tc<kDrawSumHist>.  The operand rows hold each stream's RANLUX numbers D and
 // borrow c, and the level's matrix is k_tc_matrix_d's, so a product yields the next LCG
 // state X and the byte sums of the block it was given.  The tile refills as many times
-// as its longest stream needs (one CTA-wide maximum at the start); each refill: wait for
-// the product, read the accumulator, form X, convert it to D and c and write them as the
-// next operand row (every thread, so that the warp-wide TMEM accesses stay converged;
-// rows of finished streams keep advancing), one CTA barrier, then thread 0 issues the
-// next product while every thread counts its block into the histogram and adds the
-// previous block's column sums.  A wait that gives up (after about 0.3 s) marks the
-// tile aborted; after the next barrier every thread leaves the loop, and the status
-// reports RLXPP_ERR_TIMEOUT.  one = 1 (a launch argument).
-__global__ void __launch_bounds__(kTcRows, 4)
+// as its longest stream needs (one CTA-wide maximum at the start).  Four compute warps
+// (one stream a thread) and an issuer warp: each refill, a compute warp waits for the
+// product, reads its accumulator rows, forms X, converts it to D and c and writes them as
+// its next operand rows (every thread, so that the warp-wide TMEM accesses stay
+// converged; rows of finished streams keep advancing), arrives at barrier 1 without
+// waiting there, and counts its block into the histogram and adds the previous block's
+// column sums while the next product runs; the issuer warp waits at barrier 1 for the
+// four and issues the next product.  So no compute warp carries the issue or waits for
+// the others.  A wait that gives up (after about 0.3 s) sets the abort flag: that warp
+// arrives and leaves, the issuer warp issues nothing more, the other compute warps then
+// give up on the product that does not come, and each reports RLXPP_ERR_TIMEOUT.
+// one = 1 (a launch argument).
+__global__ void __launch_bounds__(kFusedThreads, 4)
     k_fused_tc(const DrawArgs a, const __half* __restrict__ bimg_d, uint32_t one) {
   extern __shared__ __align__(1024) unsigned char smem[];
   __shared__ __align__(16) unsigned int hist_s[256 * 32];
   const int tid = threadIdx.x;
+  const bool issuer_warp = tid >= kTcRows;  // warp 4: issues the products
   {
     uint4* h4 = reinterpret_cast<uint4*>(hist_s);
-    for (int w = tid; w < 256 * 32 / 4; w += kTcRows) h4[w] = make_uint4(0u, 0u, 0u, 0u);
+    for (int w = tid; w < 256 * 32 / 4; w += kFusedThreads) h4[w] = make_uint4(0u, 0u, 0u, 0u);
   }
   FusedShared* sh = reinterpret_cast<FusedShared*>(smem + kBRegion);
   const __half* bmat = tc_bmat(smem);
   {
     const uint4* src = reinterpret_cast<const uint4*>(bimg_d);
     uint4* dst = reinterpret_cast<uint4*>(tc_bmat(smem));
-    for (int w = tid; w < kBBytes / 16; w += kTcRows) dst[w] = src[w];
+    for (int w = tid; w < kBBytes / 16; w += kFusedThreads) dst[w] = src[w];
   }
   if (tid == 0) {
     mbar_init(&sh->bar, 1);
@@ -981,7 +987,7 @@ __global__ void __launch_bounds__(kTcRows, 4)
 
   const StateView& s = a.s;
   const uint64_t i = (uint64_t)blockIdx.x * kTcRows + tid;
-  const bool live = i < s.n;
+  const bool live = !issuer_warp && i < s.n;
   int64_t cnt = 0;
   uint32_t pos = kWords, c = 0, lvl = 0;
   uint32_t D[kLimbs];
@@ -1015,16 +1021,36 @@ __global__ void __launch_bounds__(kTcRows, 4)
   const int64_t nref = live && rest > 0 ? (rest + kDoubles - 1) / kDoubles : 0;
   const uint32_t tail = live ? (uint32_t)(rest % kDoubles) : 0u;
   const int64_t iters = cta_max(nref, &sh->iters);
-  write_d_tmem(lane_taddr, D, c);
-  tmem_wait_st();
+  if (!issuer_warp) {
+    write_d_tmem(lane_taddr, D, c);
+    tmem_wait_st();
+  }
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
-  if (iters > 0 && tid == 0) tc_issue_tm(taddr, b0, &sh->bar);
+  volatile uint32_t* vabort = &sh->abort;
   uint32_t phase = 0, c_fin = c;
-  bool ok = true, inflight = iters > 0, stored = false;
+  bool ok = true, stored = false;
+  if (issuer_warp) {
+    // one product now and one after each refill but the last, once all four compute
+    // warps have arrived at barrier 1 (their rows written, their accumulator rows read)
+    uint32_t issued = 0;
+    if (iters > 0) {
+      if (tid == kTcRows) tc_issue_tm(taddr, b0, &sh->bar);
+      issued = 1;
+      for (int64_t r = 0; r + 1 < iters; ++r) {
+        asm volatile("bar.sync 1, %0;" ::"n"(kFusedThreads) : "memory");
+        tc_fence_after();
+        if (*vabort) break;
+        if (tid == kTcRows) tc_issue_tm(taddr, b0, &sh->bar);
+        ++issued;
+      }
+    }
+    // the last product issued is complete before the tensor memory is released
+    if (issued) (void)mbar_wait_bounded(&sh->bar, (issued - 1u) & 1u);
+  }
   // refills in chunks of at most kFusedFlush, counted in 32 bits within a chunk
-  for (int64_t it0 = 0; ok && it0 < iters;) {
+  for (int64_t it0 = 0; !issuer_warp && ok && it0 < iters;) {
     const uint32_t n_in = (uint32_t)(iters - it0 > kFusedFlush ? kFusedFlush : iters - it0);
     const bool more_after = it0 + n_in < iters;
     // this stream's refills in the chunk, the one of its last block, and the first whose
@@ -1038,7 +1064,6 @@ __global__ void __launch_bounds__(kTcRows, 4)
       got = __all_sync(0xFFFFFFFFu, got);  // the warp stays converged for the TMEM accesses
       uint32_t sums[6] = {0, 0, 0, 0, 0, 0};
       if (got) {
-        inflight = false;
         phase ^= 1u;
         tc_fence_after();
         uint32_t col[80];
@@ -1053,19 +1078,17 @@ __global__ void __launch_bounds__(kTcRows, 4)
         write_d_tmem(lane_taddr, D, c);
         tmem_wait_st();
       } else {
-        sh->abort = 1u;
+        *vabort = 1u;
       }
-      // every row written and the accumulator read out: the next product may start
+      // this warp's rows are written and its accumulator rows read out: it arrives at
+      // barrier 1 (the issuer warp's, which issues the next product once all four have)
+      // and goes on at once; a warp that gave up arrives too and leaves, the others
+      // then give up on the product that is not issued
       tc_fence_before();
-      __syncthreads();
-      tc_fence_after();
-      if (sh->abort) {
+      if (j + 1 < n_in || more_after) asm volatile("bar.arrive 1, %0;" ::"n"(kFusedThreads) : "memory");
+      if (!got) {
         ok = false;
         break;
-      }
-      if (j + 1 < n_in || more_after) {
-        if (tid == 0) tc_issue_tm(taddr, b0, &sh->bar);
-        inflight = true;
       }
       if (j < n_mine) {  // while the next product computes
         if (j >= j_sums) acc.columns(sums);  // the previous block of this stream, all of it drawn
@@ -1087,19 +1110,18 @@ __global__ void __launch_bounds__(kTcRows, 4)
   }
   if (nref > 0) pos = tail ? 2u * tail : (uint32_t)kWords;
   if (live && (ok || stored)) s.meta[i] = meta_pack(pos, c_fin, lvl);
-  if (!ok) {
-    if (tid == 0) atomicCAS(s.status, 0, (int)RLXPP_ERR_TIMEOUT);
+  if (!ok) {  // compute warps leave the loop on their own, so each reports
+    if ((tid & 31) == 0) atomicCAS(s.status, 0, (int)RLXPP_ERR_TIMEOUT);
   } else if (live) {
     uint64_t* sums = static_cast<uint64_t*>(a.out);
     if (sums) sums[i] = a.accumulate_sums ? sums[i] + acc.total : acc.total;
   }
-  // release TMEM; a thread that gave up on a product first waits for it once more
-  if (inflight) (void)mbar_wait_bounded(&sh->bar, phase);
+  // release TMEM (the issuer warp has seen its last product complete)
   tc_fence_before();
   __syncthreads();  // also: every histogram increment is done
   tc_fence_after();
   if (tid < 32) tmem_dealloc(taddr, kTmCols);
-  for (int b = tid; b < 256; b += kTcRows) {
+  for (int b = tid; b < 256; b += kFusedThreads) {
     unsigned long long tot = 0;
 #pragma unroll 8
     for (int l = 0; l < 32; ++l) tot += hist_s[b * 32 + l];
@@ -1128,49 +1150,49 @@ struct ValuesShared {
   uint32_t abort;               // a wait for the product timed out
   unsigned long long iters;     // refills of the tile
   uint32_t pos0;                // read position of the tile's first stream at entry
-  int box_x[2];                 // first column of the block staged in each box
-  uint32_t box_pending[2];      // a staged box waits for its store
+  int box_x[3];                 // first column of the block staged in each box
+  uint32_t box_pending[3];      // a staged box waits for its store
 };
-// Shared memory: the level's matrix, the shared words, two [128][96 B] staging boxes;
-// 48 KB in all, so that at most four CTAs (4 x 128 TMEM columns) share an SM.
+// Shared memory: the level's matrix, the shared words, three [128][96 B] staging boxes;
+// 50 KB in all, so that at most four CTAs (4 x 128 TMEM columns) share an SM.
 constexpr int kValuesBox = kTcRows * kStageBytes;  // 12 KB
-constexpr int kValuesSmem = 48 * 1024;
-static_assert(kBRegion + 1024 + 2 * kValuesBox <= kValuesSmem, "value draw shared memory");
-// The thread that issues the tile-wide stores: lane 0 of warp 1, so that warp 0, which
-// issues the products, does not also carry the stores' waits into every barrier.
-constexpr int kStoreTid = 32;
+constexpr int kValuesBoxes = 3;
+constexpr int kValuesSmem = 50 * 1024;
+static_assert(kBRegion + 1024 + kValuesBoxes * kValuesBox <= kValuesSmem, "value draw shared memory");
+constexpr int kValuesThreads = kTcRows + 32;  // four compute warps (one tile) and the issuer warp
 
 // Value-writing draws (u24, f32, f64) with one count for every stream and the output as
 // a [n][count] tensor (tmap), on one-tile CTAs with the A operand in TMEM.  Same
 // semantics as k_draw_tc.  The refill loop is the fused draw's, with the same operand
-// rows (the RANLUX numbers D and the borrow c) and level matrix (k_tc_matrix_d's): wait
-// for the product, form X, convert it to D and c and write them as the next operand row
-// (every thread), one CTA barrier, thread 0 issues the next product, then every thread
-// builds its block's values and stages them.  When every live stream of the tile starts
-// at the tile's first position (then they move in step), the blocks of a refill leave as
-// one TMA tensor store of the [128][96 B] staging box, issued by thread kStoreTid after
-// the next barrier (thread 0 records the box's column in shared memory: it is live
-// whenever any thread is); two boxes alternate, and thread kStoreTid waits for a store
-// to have read its box before the barrier after which that box is written again.  Tiles
-// out of step write each stream's values from registers.
+// rows (the RANLUX numbers D and the borrow c), level matrix (k_tc_matrix_d's) and
+// issuer warp: the four compute warps wait for the product, form X, convert it to D and
+// c, write them as the next operand row (every thread), arrive at the issuer warp's
+// barrier and go on to build their block's values and stage them; the issuer warp issues
+// the next product once all four have arrived.  When every live stream of the tile
+// starts at the tile's first position (then they move in step), the blocks of a refill
+// leave as one TMA tensor store of the [128][96 B] staging box, issued by the issuer warp
+// at the arrival after the one that follows the staging (thread 0 records the box's
+// column in shared memory: it is live whenever any thread is); three boxes rotate.
+// Tiles out of step write each stream's values from registers.
 template <int Kind>
-__global__ void __launch_bounds__(kTcRows, 4)
+__global__ void __launch_bounds__(kValuesThreads, 4)
     k_values_tc(const DrawArgs a, const __half* __restrict__ bimg_d, const __grid_constant__ CUtensorMap tmap) {
   extern __shared__ __align__(1024) unsigned char smem[];
   const int tid = threadIdx.x;
+  const bool issuer_warp = tid >= kTcRows;  // warp 4: issues the products and the stores
   ValuesShared* sh = reinterpret_cast<ValuesShared*>(smem + kBRegion);
   unsigned char* box0 = smem + kBRegion + 1024;
   const __half* bmat = tc_bmat(smem);
   {
     const uint4* src = reinterpret_cast<const uint4*>(bimg_d);
     uint4* dst = reinterpret_cast<uint4*>(tc_bmat(smem));
-    for (int w = tid; w < kBBytes / 16; w += kTcRows) dst[w] = src[w];
+    for (int w = tid; w < kBBytes / 16; w += kValuesThreads) dst[w] = src[w];
   }
   if (tid == 0) {
     mbar_init(&sh->bar, 1);
     fence_barrier_init();
     sh->abort = 0;
-    sh->box_pending[0] = sh->box_pending[1] = 0u;
+    for (int b = 0; b < kValuesBoxes; ++b) sh->box_pending[b] = 0u;
   }
   if (tid < 32) tmem_alloc(&sh->taddr, kTmCols);
   fence_proxy_async_smem();
@@ -1185,7 +1207,7 @@ __global__ void __launch_bounds__(kTcRows, 4)
   constexpr int per_block = kWords / need;
   const StateView& s = a.s;
   const uint64_t i = (uint64_t)blockIdx.x * kTcRows + tid;
-  const bool live = i < s.n;
+  const bool live = !issuer_warp && i < s.n;
   const int64_t cnt = live ? a.count_each : 0, base = (int64_t)i * a.count_each;
   uint32_t pos = kWords, c = 0, lvl = 0;
   uint32_t D[kLimbs];
@@ -1215,7 +1237,7 @@ __global__ void __launch_bounds__(kTcRows, 4)
   }
   // tile-wide stores when every live stream starts at the tile's first position (with
   // one count for all they then stay in step) and the first column after the head is
-  // 16-byte aligned; thread 0 (live whenever any thread is) issues them
+  // 16-byte aligned; thread 0 (live whenever any thread is) records each staged box
   if (tid == 0) sh->pos0 = pos_in;
   __syncthreads();
   const bool tma =
@@ -1225,20 +1247,57 @@ __global__ void __launch_bounds__(kTcRows, 4)
   const uint32_t tail = (uint32_t)((cnt - k) % per_block);
   const int64_t iters = cta_max(nref, &sh->iters);
   const int y0 = (int)((uint64_t)blockIdx.x * kTcRows);
-  write_d_tmem(lane_taddr, D, c);
-  tmem_wait_st();
+  if (!issuer_warp) {
+    write_d_tmem(lane_taddr, D, c);
+    tmem_wait_st();
+  }
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
-  if (iters > 0 && tid == 0) tc_issue_tm(taddr, b0, &sh->bar);
-  uint32_t phase = 0, c_fin = c;
-  bool ok = true, inflight = iters > 0, stored = false;
-  uint32_t box = 0;  // this refill's staging box (the refill's index mod 2)
+  volatile uint32_t* vabort = &sh->abort;
   volatile uint32_t* vpend = sh->box_pending;
   volatile int* vbox_x = sh->box_x;
-  const bool store_thread = tid == kStoreTid;
+  uint32_t phase = 0, c_fin = c;
+  bool ok = true, stored = false;
+  if (issuer_warp) {
+    // One product now and one after each refill but the last, once the four compute
+    // warps have arrived at barrier 1 (their rows written, their accumulator rows read,
+    // and the block of the previous refill staged): then also the tile-wide store of
+    // that block's box.  Box b is written again two refills after its store is issued,
+    // after the product issued at the next arrival; that product waits until the store
+    // has read the box.
+    const bool lead = tid == kTcRows;
+    uint32_t issued = 0;
+    if (iters > 0) {
+      if (lead) tc_issue_tm(taddr, b0, &sh->bar);
+      issued = 1;
+      uint32_t box = 0;  // box staged in refill r (r mod 3)
+      for (int64_t r = 0; r + 1 < iters; ++r) {
+        asm volatile("bar.sync 1, %0;" ::"n"(kValuesThreads) : "memory");
+        tc_fence_after();
+        if (*vabort) break;
+        if (lead) {
+          if (tma) bulk_wait_read_all();  // the store issued at the last arrival has read its box
+          tc_issue_tm(taddr, b0, &sh->bar);
+          const uint32_t pb = box == 0 ? kValuesBoxes - 1 : box - 1;  // staged in refill r - 1
+          if (tma && vpend[pb]) {
+            vpend[pb] = 0u;
+            asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%1, %2}], [%3];" ::"l"(
+                             reinterpret_cast<uint64_t>(&tmap)),
+                         "r"(vbox_x[pb]), "r"(y0), "r"(smem_addr(box0 + pb * kValuesBox))
+                         : "memory");
+            asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+          }
+        }
+        ++issued;
+        box = box == kValuesBoxes - 1 ? 0u : box + 1u;
+      }
+    }
+    if (issued) (void)mbar_wait_bounded(&sh->bar, (issued - 1u) & 1u);
+  }
+  uint32_t box = 0;  // this refill's staging box (the refill's index mod 3)
   // refills in chunks of at most 2^20, counted in 32 bits within a chunk
-  for (int64_t it0 = 0; ok && it0 < iters;) {
+  for (int64_t it0 = 0; !issuer_warp && ok && it0 < iters;) {
     const uint32_t n_in = (uint32_t)(iters - it0 > kFusedFlush ? kFusedFlush : iters - it0);
     const bool more_after = it0 + n_in < iters;
     const int64_t rem_ref = nref - it0;
@@ -1249,7 +1308,6 @@ __global__ void __launch_bounds__(kTcRows, 4)
       bool got = mbar_wait_bounded(&sh->bar, phase);
       got = __all_sync(0xFFFFFFFFu, got);  // the warp stays converged for the TMEM accesses
       if (got) {
-        inflight = false;
         phase ^= 1u;
         tc_fence_after();
         uint32_t col[72];
@@ -1262,30 +1320,16 @@ __global__ void __launch_bounds__(kTcRows, 4)
         write_d_tmem(lane_taddr, D, c);
         tmem_wait_st();
       } else {
-        sh->abort = 1u;
+        *vabort = 1u;
       }
-      if (tma && store_thread) bulk_wait_read_all();  // the last store has read its box
+      // this warp's rows are written and its accumulator rows read out: it arrives at
+      // the issuer warp's barrier and goes on at once; a warp that gave up arrives too
+      // and leaves, the others then give up on the product that is not issued
       tc_fence_before();
-      __syncthreads();
-      tc_fence_after();
-      if (sh->abort) {
+      if (j + 1 < n_in || more_after) asm volatile("bar.arrive 1, %0;" ::"n"(kValuesThreads) : "memory");
+      if (!got) {
         ok = false;
         break;
-      }
-      if (j + 1 < n_in || more_after) {
-        if (tid == 0) tc_issue_tm(taddr, b0, &sh->bar);
-        inflight = true;
-      }
-      if (store_thread) {  // the box staged before this barrier
-        const uint32_t pb = box ^ 1u;
-        if (vpend[pb]) {
-          vpend[pb] = 0u;
-          asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%1, %2}], [%3];" ::"l"(
-                           reinterpret_cast<uint64_t>(&tmap)),
-                       "r"(vbox_x[pb]), "r"(y0), "r"(smem_addr(box0 + pb * kValuesBox))
-                       : "memory");
-          asm volatile("cp.async.bulk.commit_group;" ::: "memory");
-        }
       }
       if (j < n_mine) {  // this stream's block, while the next product computes
         const int64_t kj = k_chunk + (int64_t)j * per_block;
@@ -1312,7 +1356,7 @@ __global__ void __launch_bounds__(kTcRows, 4)
           stored = true;
         }
       }
-      box ^= 1u;
+      box = box == kValuesBoxes - 1 ? 0u : box + 1u;
     }
     it0 += n_in;
   }
@@ -1320,22 +1364,30 @@ __global__ void __launch_bounds__(kTcRows, 4)
     k = cnt;
     pos = tail ? tail * need : (uint32_t)kWords;
   }
-  if (ok && tma && iters > 0) {  // the last staged box
-    __syncthreads();
-    const uint32_t pb = box ^ 1u;
-    if (store_thread && vpend[pb]) {
-      vpend[pb] = 0u;
-      asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%1, %2}], [%3];" ::"l"(
-                       reinterpret_cast<uint64_t>(&tmap)),
-                   "r"(vbox_x[pb]), "r"(y0), "r"(smem_addr(box0 + pb * kValuesBox))
-                   : "memory");
-      asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+  if (live && (ok || stored)) s.meta[i] = meta_pack(pos, c_fin, lvl);
+  if (!ok && (tid & 31) == 0) atomicCAS(s.status, 0, (int)RLXPP_ERR_TIMEOUT);
+  // every block is staged: the boxes the loop did not store (those of the last two
+  // refills) leave now, and the CTA ends once every store is done
+  fence_proxy_async_smem();
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (tid == kTcRows && tma && !*vabort) {
+#pragma unroll 1
+    for (int64_t r = iters - 2; r < iters; ++r) {
+      if (r < 0) continue;
+      const uint32_t pb = (uint32_t)(r % kValuesBoxes);
+      if (vpend[pb]) {
+        vpend[pb] = 0u;
+        asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%1, %2}], [%3];" ::"l"(
+                         reinterpret_cast<uint64_t>(&tmap)),
+                     "r"(vbox_x[pb]), "r"(y0), "r"(smem_addr(box0 + pb * kValuesBox))
+                     : "memory");
+        asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+      }
     }
   }
-  if (store_thread) bulk_wait_all();  // every store of this CTA is done
-  if (live && (ok || stored)) s.meta[i] = meta_pack(pos, c_fin, lvl);
-  if (!ok && tid == 0) atomicCAS(s.status, 0, (int)RLXPP_ERR_TIMEOUT);
-  if (inflight) (void)mbar_wait_bounded(&sh->bar, phase);
+  if (tid == kTcRows) bulk_wait_all();
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
@@ -1785,7 +1837,7 @@ cudaError_t launch_tc_kind(const DrawArgs& a, const __half* bimg, const __half* 
       cudaError_t e = cudaFuncSetAttribute(k_values_tc<Kind>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                            kValuesSmem);
       if (e != cudaSuccess) return e;
-      k_values_tc<Kind><<<(unsigned)tiles, kTcRows, kValuesSmem, st>>>(a, bimg_d, map);
+      k_values_tc<Kind><<<(unsigned)tiles, kValuesThreads, kValuesSmem, st>>>(a, bimg_d, map);
       return cudaGetLastError();
     }
   }
@@ -1800,7 +1852,7 @@ cudaError_t launch_fused_tc(const DrawArgs& a, const __half* bimg_d, cudaStream_
   cudaError_t e = cudaFuncSetAttribute(k_fused_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, kFusedDynSmem);
   if (e != cudaSuccess) return e;
   const unsigned grid = (unsigned)((a.s.n + kTcRows - 1) / kTcRows);
-  k_fused_tc<<<grid, kTcRows, kFusedDynSmem, st>>>(a, bimg_d, 1u);
+  k_fused_tc<<<grid, kFusedThreads, kFusedDynSmem, st>>>(a, bimg_d, 1u);
   return cudaGetLastError();
 }
 
