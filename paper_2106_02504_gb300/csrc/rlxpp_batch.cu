@@ -530,7 +530,7 @@ rlxpp_status run_impl(rlxpp_gen* g, const rlxpp_plan* p, uint32_t* out_u24, doub
   const unsigned grid = (unsigned)std::max(1, g->sms) * p->tuning.blocks_per_sm;
   if (e == cudaSuccess) {
     if (p->tuning.path == RLXPP_PATH_TENSOR && g->tc_matrix && p->tiles) {
-      e = launch_requests_tc(b, p->items, p->tiles, p->n_tiles, g->tc_matrix, p->wc, grid, st);
+      e = launch_requests_tc(b, p->items, p->tiles, p->n_tiles, g->tc_matrix_d, p->wc, grid, st);
     } else if (p->tuning.path == RLXPP_PATH_WARP) {
       e = launch_requests_warp(b, p->items, p->n_items, p->wc, grid, tuning_tpb(p->tuning), st);
     } else {

@@ -778,27 +778,6 @@ __device__ __forceinline__ void tc_issue_tm(uint32_t taddr, uint32_t b0, uint64_
   tc_commit(bar);
 }
 
-// X = sum_k S_k 2^(8k) mod m from the column bit patterns: the fold in its common form
-// (no carry out of limb 8, top limb not all ones, so the result is below m) and, in one
-// branch for the other cases (about 2^-15 of the refills), the exact fold.
-__device__ __forceinline__ void tc_fold_common(const uint32_t col[72], uint32_t X[kLimbs]) {
-  uint32_t Xa[kLimbs], T;
-  columns_assemble(col, Xa, T);
-  X[0] = add_cc(Xa[0], 0u - T);
-#pragma unroll
-  for (int k = 1; k < 7; ++k) X[k] = addc_cc(Xa[k], 0xFFFFFFFFu);
-  X[7] = addc_cc(Xa[7], (T - 1u) << 16 | 0xFFFFu);
-  X[8] = addc_cc(Xa[8], 0u);
-  const uint32_t c9 = addc(0u, 0u);
-#pragma unroll
-  for (int k = 9; k < kLimbs; ++k) X[k] = Xa[k];
-  if (__builtin_expect(c9 != 0u || X[17] == 0xFFFFFFFFu, 0)) {
-#pragma unroll
-    for (int k = 0; k < kLimbs; ++k) X[k] = Xa[k];
-    fold_x(X, T);
-  }
-}
-
 // The fused draw's epilogue: X = sum_k S_k 2^(8k) mod m from the column bit patterns, D its
 // 24 RANLUX numbers (Sec. 2.3) and c its borrow, computed without a branch in the common
 // case (the fold's carry stops in limb 8, the top limb is not all ones, the conversion's
@@ -1130,20 +1109,6 @@ __global__ void __launch_bounds__(kFusedThreads, 4)
 }
 
 // ---- value-writing draws with the A operand in tensor memory -------------------------
-// X (18 limbs) -> its 72 bytes as fp16 subnormals (each pair of bytes one byte permute
-// with zeros, as write_x_row forms them) into this thread's lane of the A columns.
-// Every thread of the warp calls it (tcgen05.st is warp-wide).
-__device__ __forceinline__ void write_x_tmem(uint32_t lane_taddr, const uint32_t X[kLimbs]) {
-  uint32_t w[36];
-#pragma unroll
-  for (int c = 0; c < kLimbs; ++c) {
-    w[2 * c] = __byte_perm(X[c], 0u, 0x4140u);
-    w[2 * c + 1] = __byte_perm(X[c], 0u, 0x4342u);
-  }
-  tmem_st32(lane_taddr + kTmA, w);
-  tmem_st4(lane_taddr + kTmA + 32, w + 32);
-}
-
 struct ValuesShared {
   uint64_t bar;                 // product completion
   uint32_t taddr;               // TMEM base
@@ -1394,6 +1359,8 @@ __global__ void __launch_bounds__(kValuesThreads, 4)
   if (tid < 32) tmem_dealloc(taddr, kTmCols);
 }
 
+constexpr int kReqThreads = kTcRows + 32;  // four compute warps (one tile) and the issuer warp
+
 // Emits the unread part of the current block for a value kind (f64 or u24).
 __device__ __forceinline__ void emit_head(bool f64, const BatchArgs& b, const uint32_t D[kLimbs], uint32_t& pos,
                                           int64_t cnt, int64_t base, int64_t& k) {
@@ -1426,12 +1393,13 @@ __device__ __forceinline__ void emit_head(bool f64, const BatchArgs& b, const ui
 // longest chunk is done.  Chunks of a tile have similar lengths, so little work is lost
 // to the longest one.  Chunks write to unrelated places: each lane stages its full
 // block, and the warp writes its 32 staged blocks cooperatively.
-__global__ void __launch_bounds__(kTcRows, 4)
+__global__ void __launch_bounds__(kReqThreads, 4)
     k_requests_tc(const BatchArgs b, const Item* __restrict__ items, const TcTile* __restrict__ tiles,
                   uint64_t n_tiles, const __half* __restrict__ bimg_all, WorkCounters* wc) {
   extern __shared__ __align__(1024) unsigned char smem[];
   __shared__ unsigned long long tile_s;
   const int tid = threadIdx.x;
+  const bool issuer_warp = tid >= kTcRows;  // warp 4: issues the products
   ValuesShared* sh = reinterpret_cast<ValuesShared*>(smem + kBRegion);
   unsigned char* stage = smem + kBRegion + 1024;
   uint4* slot = reinterpret_cast<uint4*>(stage + tid * kStageBytes);
@@ -1448,13 +1416,10 @@ __global__ void __launch_bounds__(kTcRows, 4)
   tc_fence_after();
   const uint32_t taddr = sh->taddr;
   const uint32_t lane_taddr = taddr + ((uint32_t)((tid / 32) * 32) << 16);
-  {
-    const uint32_t cst[4] = {0x3C006800u, 0u, 0u, 0u};  // 2048 and 1 at k = 72, 73
-    tmem_st4(lane_taddr + kTmA + 36, cst);
-  }
   const uint32_t b0 = smem_addr(bmat);
-  uint32_t phase = 0;
-  bool ok = true, inflight = false;
+  volatile uint32_t* vabort = &sh->abort;
+  uint32_t phase = 0, issued = 0;  // issued: products issued (the issuer warp's count)
+  bool ok = true;
   uint32_t loaded = 0xFFFFFFFFu;  // level whose matrix is in shared memory
   while (ok) {
     if (tid == 0) tile_s = atomicAdd(&wc->next, 1ull);
@@ -1466,7 +1431,7 @@ __global__ void __launch_bounds__(kTcRows, 4)
     if (tile.level != loaded) {  // the products of the previous tile are complete
       const uint4* src = reinterpret_cast<const uint4*>(bimg_all + (size_t)tile.level * (kBBytes / 2));
       uint4* dst = reinterpret_cast<uint4*>(tc_bmat(smem));
-      for (int w = tid; w < kBBytes / 16; w += kTcRows) dst[w] = src[w];
+      for (int w = tid; w < kBBytes / 16; w += kReqThreads) dst[w] = src[w];
       fence_proxy_async_smem();  // -> visible to the tensor core after the next barrier
       loaded = tile.level;
     }
@@ -1498,54 +1463,66 @@ __global__ void __launch_bounds__(kTcRows, 4)
     int64_t k = 0;
     emit_head(f64, b, D, pos, cnt, base, k);
     int64_t left = live && k < cnt ? (cnt - k + per - 1) / per : 0;
-    const bool refilled = left > 0;
     const int64_t iters = cta_max(left, &sh->iters);
-    uint32_t X[kLimbs];
-    to_lcg(D, c, X);
-    write_x_tmem(lane_taddr, X);
-    tmem_wait_st();
+    // the stream's state after the request's last chunk (written when its last block is
+    // drawn, since the operand rows of a finished chunk keep advancing)
+    const bool final_state = live && b.advance && ((it.info >> 16) & 1u);
+    const uint64_t st = final_state ? b.req_stream[it.req] : 0;
+    if (final_state && left == 0) {
+#pragma unroll
+      for (int q = 0; q < 9; ++q)
+        b.s.D[(uint64_t)q * b.s.stride + st] = ((uint64_t)D[2 * q + 1] << 32) | D[2 * q];
+      b.s.meta[st] = meta_pack(pos, c, lvl);
+    }
+    if (!issuer_warp) {
+      write_d_tmem(lane_taddr, D, c);
+      tmem_wait_st();
+    }
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
-    if (iters > 0) {
-      if (tid == 0) tc_issue_tm(taddr, b0, &sh->bar);
-      inflight = true;
+    if (issuer_warp && iters > 0) {
+      // one product now and one after each refill but the last, once the four compute
+      // warps have arrived at barrier 1 (their rows written, their accumulator rows read)
+      if (tid == kTcRows) tc_issue_tm(taddr, b0, &sh->bar);
+      ++issued;
+      for (int64_t r = 0; r + 1 < iters; ++r) {
+        asm volatile("bar.sync 1, %0;" ::"n"(kReqThreads) : "memory");
+        tc_fence_after();
+        if (*vabort) break;
+        if (tid == kTcRows) tc_issue_tm(taddr, b0, &sh->bar);
+        ++issued;
+      }
     }
-    for (int64_t r = 0; r < iters; ++r) {
+    for (int64_t r = 0; !issuer_warp && r < iters; ++r) {
       bool got = mbar_wait_bounded(&sh->bar, phase);
       got = __all_sync(0xFFFFFFFFu, got);  // the warp stays converged for the TMEM accesses
-      uint32_t Xn[kLimbs];
       if (got) {
-        inflight = false;
         phase ^= 1u;
         tc_fence_after();
         uint32_t col[72];
         tmem_ld64(lane_taddr, col);
         tmem_ld8(lane_taddr + 64, col + 64);
         tmem_wait_ld();
-        tc_fold_common(col, Xn);
-        __syncwarp();  // reconverged after the rare fold, before the warp-wide store
-        write_x_tmem(lane_taddr, Xn);
+        uint32_t X[kLimbs];
+        tc_epilogue_d(col, X, D, c);
+        __syncwarp();  // reconverged after the rare branch, before the warp-wide store
+        write_d_tmem(lane_taddr, D, c);
         tmem_wait_st();
       } else {
-        sh->abort = 1u;
+        *vabort = 1u;
       }
+      // this warp's rows are written and its accumulator rows read out: it arrives at
+      // the issuer warp's barrier and goes on at once; a warp that gave up arrives too
+      // and leaves, the others then give up on the product that is not issued
       tc_fence_before();
-      __syncthreads();
-      tc_fence_after();
-      if (sh->abort) {
+      if (r + 1 < iters) asm volatile("bar.arrive 1, %0;" ::"n"(kReqThreads) : "memory");
+      if (!got) {
         ok = false;
         break;
       }
-      if (r + 1 < iters) {
-        if (tid == 0) tc_issue_tm(taddr, b0, &sh->bar);
-        inflight = true;
-      }
       uint64_t dst = 0;  // destination of this lane's full block, if it has one
       if (left > 0) {    // this chunk's block, while the next product computes
-#pragma unroll
-        for (int q = 0; q < kLimbs; ++q) X[q] = Xn[q];
-        to_ranlux(X, D);
         const int64_t rem = cnt - k;
         if (rem >= per) {
           uint4 v[6];
@@ -1573,21 +1550,23 @@ __global__ void __launch_bounds__(kTcRows, 4)
           }
           k = cnt;
         }
-        --left;
+        if (--left == 0 && final_state) {
+#pragma unroll
+          for (int q = 0; q < 9; ++q)
+            b.s.D[(uint64_t)q * b.s.stride + st] = ((uint64_t)D[2 * q + 1] << 32) | D[2 * q];
+          b.s.meta[st] = meta_pack(pos, c, lvl);
+        }
       }
       warp_store_blocks(wstage, dst);
     }
-    if (ok && live && b.advance && ((it.info >> 16) & 1u)) {  // last chunk: final state
-      if (refilled) c = carry_of(X, D);
-      const uint64_t st = b.req_stream[it.req];
-#pragma unroll
-      for (int q = 0; q < 9; ++q)
-        b.s.D[(uint64_t)q * b.s.stride + st] = ((uint64_t)D[2 * q + 1] << 32) | D[2 * q];
-      b.s.meta[st] = meta_pack(pos, c, lvl);
-    }
+    // every warp has left the tile's loop (on a timeout, after its own wait ran out):
+    // the CTA goes on to the next tile together, or stops together
+    if (issuer_warp && *vabort) ok = false;
+    ok = __syncthreads_and(ok) != 0;
   }
   if (!ok && tid == 0) atomicCAS(b.s.status, 0, (int)RLXPP_ERR_TIMEOUT);
-  if (inflight) (void)mbar_wait_bounded(&sh->bar, phase);
+  // the last product issued is complete before the tensor memory is released
+  if (issuer_warp && issued) (void)mbar_wait_bounded(&sh->bar, (issued - 1u) & 1u);
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
@@ -1866,7 +1845,7 @@ cudaError_t launch_requests_tc(const BatchArgs& b, const Item* items, const TcTi
   cudaError_t e = cudaFuncSetAttribute(k_requests_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTcSmem);
   if (e != cudaSuccess) return e;
   if (grid > n_tiles) grid = (unsigned)n_tiles;
-  k_requests_tc<<<grid, kTcRows, kTcSmem, st>>>(b, items, tiles, n_tiles, static_cast<const __half*>(bimg), wc);
+  k_requests_tc<<<grid, kReqThreads, kTcSmem, st>>>(b, items, tiles, n_tiles, static_cast<const __half*>(bimg), wc);
   return cudaGetLastError();
 }
 
