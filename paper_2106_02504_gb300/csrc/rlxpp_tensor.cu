@@ -160,11 +160,6 @@ __device__ __forceinline__ void tmem_st32(uint32_t taddr, const uint32_t* v) {
       "r"(v[25]), "r"(v[26]), "r"(v[27]), "r"(v[28]), "r"(v[29]), "r"(v[30]), "r"(v[31])
       : "memory");
 }
-__device__ __forceinline__ void tmem_st4(uint32_t taddr, const uint32_t* v) {
-  asm volatile("tcgen05.st.sync.aligned.32x32b.x4.b32 [%0], {%1,%2,%3,%4};" ::"r"(taddr), "r"(v[0]), "r"(v[1]),
-               "r"(v[2]), "r"(v[3])
-               : "memory");
-}
 __device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
 
 // ---- per-thread pieces -------------------------------------------------------------
@@ -261,19 +256,24 @@ __device__ __forceinline__ void columns_to_x(const uint32_t col[72], uint32_t X[
 // The integer epilogue of one refill: X = sum_k S_k 2^(8k) mod m from the column bit
 // patterns, written to this thread's operand row (the next product's input), and
 // D = its 24 RANLUX numbers (Sec. 2.3).  The common case is computed without a branch:
-// the fold's carry stops in limb 8, the top limb is not all ones (so X < m) and the
-// conversion's quick test (that of to_ranlux) decides its quotient, with no carry out
-// of limb 7 of X + q.
+// the fold's limb 0 does not borrow and its carry stops in limb 8, the top limb is not
+// all ones (so X < m) and the conversion's quick test (that of to_ranlux) decides its
+// quotient, with no carry out of limb 7 of X + q.
 // Any other case (about 2^-15 of the refills) is redone in one branch by the exact forms
 // (fold_x, to_ranlux), which rewrite the row and D.
 __device__ __forceinline__ void tc_epilogue(const uint32_t col[72], __half* tile, int row, uint32_t X[kLimbs],
                                             uint32_t D[kLimbs]) {
   uint32_t Xa[kLimbs], T;
   columns_assemble(col, Xa, T);
-  X[0] = add_cc(Xa[0], 0u - T);
+  // the fold X + T (2^240 - 1) = X + (T - 1) 2^240 + (2^32 - T) + sum_(0<k<7) 0xFFFFFFFF 2^(32k)
+  // + 0xFFFF 2^224 when limb 0 does not borrow (Xa_0 >= T, about all but 2^-17 of the
+  // refills): limbs 1..6 then come out unchanged and limb 7 gains T 2^16, so the chain
+  // is two limbs long
+  const bool b0 = Xa[0] < T;
+  X[0] = Xa[0] - T;
 #pragma unroll
-  for (int k = 1; k < 7; ++k) X[k] = addc_cc(Xa[k], 0xFFFFFFFFu);
-  X[7] = addc_cc(Xa[7], (T - 1u) << 16 | 0xFFFFu);
+  for (int k = 1; k < 7; ++k) X[k] = Xa[k];
+  X[7] = add_cc(Xa[7], T << 16);
   X[8] = addc_cc(Xa[8], 0u);
   const uint32_t c9 = addc(0u, 0u);  // carry out of limb 8
 #pragma unroll
@@ -291,7 +291,7 @@ __device__ __forceinline__ void tc_epilogue(const uint32_t col[72], __half* tile
   const uint32_t c8 = addc(0u, 0u);  // carry out of limb 7 of X + q
 #pragma unroll
   for (int k = 8; k < kLimbs; ++k) D[k] = X[k];
-  const bool rare = (c9 | c8) != 0u || X[17] == 0xFFFFFFFFu || (t15 & t16 & t17) == 0xFFFFFFFFu ||
+  const bool rare = b0 || (c9 | c8) != 0u || X[17] == 0xFFFFFFFFu || (t15 & t16 & t17) == 0xFFFFFFFFu ||
                     (t15 | t16 | t17) == 0u || q0 < borrow;
   if (__builtin_expect(rare, 0)) {
 #pragma unroll
@@ -780,7 +780,8 @@ __device__ __forceinline__ void tc_issue_tm(uint32_t taddr, uint32_t b0, uint64_
 
 // The fused draw's epilogue: X = sum_k S_k 2^(8k) mod m from the column bit patterns, D its
 // 24 RANLUX numbers (Sec. 2.3) and c its borrow, computed without a branch in the common
-// case (the fold's carry stops in limb 8, the top limb is not all ones, the conversion's
+// case (the fold's limb 0 does not borrow and its carry stops in limb 8, the top limb is
+// not all ones, the conversion's
 // quick test decides its quotient and X + q carries no further than limb 7); every other
 // case (about 2^-15 of the refills) is redone in one branch by the exact forms.  With no
 // branch before them, the byte permutes of D's upper limbs (equal to X's) can be
@@ -789,10 +790,15 @@ __device__ __forceinline__ void tc_epilogue_d(const uint32_t col[72], uint32_t X
                                               uint32_t& c) {
   uint32_t Xa[kLimbs], T;
   columns_assemble(col, Xa, T);
-  X[0] = add_cc(Xa[0], 0u - T);
+  // the fold X + T (2^240 - 1) = X + (T - 1) 2^240 + (2^32 - T) + sum_(0<k<7) 0xFFFFFFFF 2^(32k)
+  // + 0xFFFF 2^224 when limb 0 does not borrow (Xa_0 >= T, about all but 2^-17 of the
+  // refills): limbs 1..6 then come out unchanged and limb 7 gains T 2^16, so the chain
+  // is two limbs long
+  const bool b0 = Xa[0] < T;
+  X[0] = Xa[0] - T;
 #pragma unroll
-  for (int k = 1; k < 7; ++k) X[k] = addc_cc(Xa[k], 0xFFFFFFFFu);
-  X[7] = addc_cc(Xa[7], (T - 1u) << 16 | 0xFFFFu);
+  for (int k = 1; k < 7; ++k) X[k] = Xa[k];
+  X[7] = add_cc(Xa[7], T << 16);
   X[8] = addc_cc(Xa[8], 0u);
   const uint32_t c9 = addc(0u, 0u);  // carry out of limb 8
 #pragma unroll
@@ -810,7 +816,7 @@ __device__ __forceinline__ void tc_epilogue_d(const uint32_t col[72], uint32_t X
 #pragma unroll
   for (int k = 8; k < kLimbs; ++k) D[k] = X[k];
   c = carry_of(X, D);
-  const bool rare = (c9 | c8) != 0u || X[17] == 0xFFFFFFFFu || (t15 & t16 & t17) == 0xFFFFFFFFu ||
+  const bool rare = b0 || (c9 | c8) != 0u || X[17] == 0xFFFFFFFFu || (t15 & t16 & t17) == 0xFFFFFFFFu ||
                     (t15 | t16 | t17) == 0u || q0 < borrow;
   if (__builtin_expect(rare, 0)) {
 #pragma unroll

@@ -152,3 +152,125 @@ def tc_above_m_inputs(A, rs=(0, 1, 2, 5, 1 << 100, (1 << 239) + 7, (1 << 240) - 
     value can be r + m, which needs the final correction."""
     Ainv = pow(A, -1, M)
     return [Ainv * r % M for r in rs]
+
+
+# ---- the tensor-core product on operand rows that hold D and c ---------------------
+# The fused, value and request kernels feed the product the RANLUX numbers D (72 bytes)
+# and the borrow c of a state instead of X = D - floor(D / 2^336) + c.  Byte j of D
+# stands for 2^(8j), less 2^(8(j - 42)) for j >= 42, so row j of their matrix holds
+# R'_j = R_j - R_(j-42) mod m and a further row holds A against c.
+
+def _rows_d(A):
+    R = [A * pow(2, 8 * j, M) % M for j in range(72)]
+    return [(R[j] - R[j - 42]) % M if j >= 42 else R[j] for j in range(72)]
+
+
+def tc_assembled_d(D, c, A):
+    """The value the epilogue assembles before its fold when the operand row holds D and
+    c: sum_j d_j R'_j + c A plus the bias C and E = -C mod m.  Congruent to A X mod m."""
+    E = (-C_BIAS) % M
+    Rd = _rows_d(A)
+    return C_BIAS + E + c * A + sum(((D >> (8 * j)) & 0xFF) * Rd[j] for j in range(72))
+
+
+def tc_fold_cases_d(D, c, A):
+    """(limb 0 of the assembled value below its top limb T, carry out of limb 8 in the
+    fold, value >= m after the folds) for operand rows holding D and c."""
+    v = tc_assembled_d(D, c, A)
+    T, lo = v >> 576, v % B576
+    add = T * ((1 << 240) - 1)
+    past8 = (lo % B288) + add >= B288
+    f = lo + add
+    if f >= B576:
+        f = f - B576 + (1 << 240) - 1
+    return (lo & 0xFFFFFFFF) < T, past8, f >= M
+
+
+def _canonical_state(D, c):
+    """The LCG state X whose RANLUX form is (D, c), or None if (D, c) is not one."""
+    X = R.to_lcg(D, c)
+    if not 0 < X < M:
+        return None
+    return X if tuple(R.to_ranlux(X)) == (D, c) else None
+
+
+def tc_d_borrow_states(A, rng: random.Random, want: int = 4):
+    """States X whose RANLUX form (D, c) makes limb 0 of the assembled value smaller than
+    16128 (so below the top limb, which is at least that), so that the fold borrows out of
+    limb 0.  Limb 0 is sum_j d_j (R'_j mod 2^32) + c A + C + E mod 2^32; bytes 0..2 of D are
+    searched over all 2^24 values for each random rest (about 63 qualify)."""
+    import numpy as np
+    Rd = _rows_d(A)
+    E = (-C_BIAS) % M
+    r = [x & 0xFFFFFFFF for x in Rd[:3]]
+    grid = np.arange(1 << 24, dtype=np.uint64)
+    part = (((grid & np.uint64(0xFF)) * np.uint64(r[0]) + ((grid >> np.uint64(8)) & np.uint64(0xFF)) * np.uint64(r[1])
+             + (grid >> np.uint64(16)) * np.uint64(r[2])) & np.uint64(0xFFFFFFFF))
+    found = []
+    while len(found) < want:
+        rest = rng.randrange(B576) & ~((1 << 24) - 1)
+        c = rng.randrange(2)
+        base = (C_BIAS + E + c * A + sum(((rest >> (8 * j)) & 0xFF) * Rd[j] for j in range(3, 72))) & 0xFFFFFFFF
+        hits = np.nonzero(((part + np.uint64(base)) & np.uint64(0xFFFFFFFF)) < np.uint64(16128))[0]
+        for h in hits[:8]:
+            X = _canonical_state(rest | int(h), c)
+            if X is not None and tc_fold_cases_d(rest | int(h), c, A)[0]:
+                found.append(X)
+                break
+    return found
+
+
+def tc_d_limb8_carry_states(A, rng: random.Random, want: int = 3):
+    """States X whose RANLUX form (D, c) makes the fold carry out of limb 8, found as
+    tc_limb8_carry_inputs finds operands: meeting in the middle over the low six bytes of
+    D, for a random rest and borrow."""
+    Rd = _rows_d(A)
+    E = (-C_BIAS) % M
+    width = 16128 << 240
+    found = []
+    while len(found) < want:
+        base = rng.randrange(B576) & ~((1 << 48) - 1)
+        c = rng.randrange(2)
+        v0 = C_BIAS + E + c * A + sum(((base >> (8 * j)) & 0xFF) * Rd[j] for j in range(72))
+
+        def side(j0):
+            return [((a * Rd[j0] + b * Rd[j0 + 1] + cc * Rd[j0 + 2]) % B288, (a, b, cc))
+                    for a in range(256) for b in range(256) for cc in range(4)]
+
+        right = sorted(side(3))
+        keys = [t[0] for t in right]
+        for d_val, ta in side(0):
+            a_val = (v0 + d_val) % B288
+            lo = (B288 - width - a_val) % B288
+            hi = (B288 - a_val) % B288
+            spans = [(lo, hi)] if lo < hi else [(lo, B288), (0, hi)]
+            hit = None
+            for s, e in spans:
+                for idx in range(bisect.bisect_left(keys, s), bisect.bisect_left(keys, e)):
+                    tb = right[idx][1]
+                    D = base | ta[0] | ta[1] << 8 | ta[2] << 16 | tb[0] << 24 | tb[1] << 32 | tb[2] << 40
+                    if tc_fold_cases_d(D, c, A)[1]:
+                        X = _canonical_state(D, c)
+                        if X is not None:
+                            hit = X
+                            break
+                if hit is not None:
+                    break
+            if hit is not None:
+                found.append(hit)
+                break
+    return found
+
+
+def tc_d_above_m_states(A, rs=(0, 1, 2, 5, 1 << 100, (1 << 239) + 7, (1 << 240) - 3)):
+    """States X = A^-1 r mod m (product r below 2^240 - 1) whose operand rows (D, c) leave
+    the folded value at r + m, which needs the final correction."""
+    Ainv = pow(A, -1, M)
+    out = []
+    for r in rs:
+        X = Ainv * r % M
+        if 0 < X < M:
+            D, c = R.to_ranlux(X)
+            if tc_fold_cases_d(D, c, A)[2]:
+                out.append(X)
+    return out

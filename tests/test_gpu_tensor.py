@@ -13,7 +13,8 @@ from oracle import ranluxpp as R
 from oracle import swb_lib as S
 from paper_2106_02504_gb300 import workloads as W
 from tests.oracle_side import StreamSet, from_limbs64, limbs64
-from tests.rare_paths import conversion_carry_states, tc_above_m_inputs, tc_limb8_carry_inputs
+from tests.rare_paths import (conversion_carry_states, tc_above_m_inputs, tc_d_above_m_states,
+                               tc_d_borrow_states, tc_d_limb8_carry_states, tc_limb8_carry_inputs)
 
 pytestmark = pytest.mark.gpu
 
@@ -54,30 +55,28 @@ def test_tc_product(native, p):
         assert from_limbs64(got[k]) == A * xs[k] % M, (p, k)
 
 
-@pytest.mark.parametrize("p", [389, 2048])
-def test_tc_draw_rare_epilogue(native, p):
-    """States whose next refill in the tensor draw kernels takes the epilogue's rare branch:
-    products whose fold carries past limb 8, products below 2^240 - 1 (the final
-    correction), and products whose conversion carries past limb 7 or borrows past the
-    lowest limb of its quotient.  From an exhausted block every stream draws two blocks of
-    doubles (the tile-wide store kernel) and then the fused sum and histogram; values, sums
-    and final states against the oracle."""
-    A, M = R.luxury_multiplier(p), R.M
-    Ainv = pow(A, -1, M)
-    xs = tc_limb8_carry_inputs(A, random.Random(500 + p)) + tc_above_m_inputs(A)
-    xs += [Ainv * y % M for y in conversion_carry_states(random.Random(600 + p), k=8)]
-    xs = [x for x in xs if 0 < x < M]
+def _rare_epilogue_run(native, xs, p, per_stream):
+    """From an exhausted block, every stream draws two blocks of doubles (per-stream
+    counts: the kernel with operand rows holding X; one count for all: the tile-wide store
+    kernel, rows holding D and c) and then the fused sum and histogram (rows holding D and
+    c); values, sums and final states against the oracle."""
     n = len(xs)
     ref = StreamSet(xs, p, [24] * n)
     g = native.Generator(n, [p], torch.arange(1, n + 1, dtype=torch.int64, device="cuda"))
     g.set_path(native.RLXPP_PATH_TENSOR)
     g.set_state(ref.state_records().view(np.int64).copy())
-    out = torch.zeros((n, 24), dtype=torch.float64, device="cuda")
-    g.draw_f64(out, 24)
+    if per_stream:
+        out = torch.zeros(n * 24, dtype=torch.float64, device="cuda")
+        counts = torch.full((n,), 24, dtype=torch.int64, device="cuda")
+        offsets = torch.arange(0, 24 * n, 24, dtype=torch.int64, device="cuda")
+        g.draw_f64(out, 0, counts, offsets)
+        out = out.view(n, 24)
+    else:
+        out = torch.zeros((n, 24), dtype=torch.float64, device="cuda")
+        g.draw_f64(out, 24)
     want = ref.draw(24, S.KIND_F64)
     assert np.array_equal(out.cpu().numpy().view(np.uint64), want.view(np.uint64))
     assert np.array_equal(states(native, g, n).numpy().view(np.uint64), ref.state_records())
-    # the fused consumer from the same states
     ref = StreamSet(xs, p, [24] * n)
     g.set_state(ref.state_records().view(np.int64).copy())
     sums = torch.zeros(n, dtype=torch.int64, device="cuda")
@@ -88,6 +87,26 @@ def test_tc_draw_rare_epilogue(native, p):
     assert np.array_equal(hist.cpu().numpy().view(np.uint64), whist)
     assert np.array_equal(states(native, g, n).numpy().view(np.uint64), ref.state_records())
     g.sync()
+    g.close()
+
+
+@pytest.mark.parametrize("p", [389, 2048])
+def test_tc_draw_rare_epilogue(native, p):
+    """States whose next refill takes the tensor epilogue's rare branch, each kind of
+    state built for the form of operand row that meets it: for rows holding X, products
+    whose fold carries past limb 8 and products below 2^240 - 1 (the final correction);
+    for rows holding D and c, assembled values whose fold borrows out of limb 0 or carries
+    past limb 8, and products that need the final correction; for both, products whose
+    conversion carries past limb 7 or borrows past the lowest limb of its quotient
+    (tests/test_rare_paths.py checks on the CPU that each reaches its case)."""
+    A, M = R.luxury_multiplier(p), R.M
+    Ainv = pow(A, -1, M)
+    conv = [Ainv * y % M for y in conversion_carry_states(random.Random(600 + p), k=8)]
+    x_form = tc_limb8_carry_inputs(A, random.Random(500 + p)) + tc_above_m_inputs(A) + conv
+    d_form = (tc_d_borrow_states(A, random.Random(700 + p)) + tc_d_limb8_carry_states(A, random.Random(800 + p), want=2)
+              + tc_d_above_m_states(A) + conv)
+    _rare_epilogue_run(native, [x for x in x_form if 0 < x < M], p, per_stream=True)
+    _rare_epilogue_run(native, [x for x in d_form if 0 < x < M], p, per_stream=False)
 
 
 def pair(native, seeds, levels=(2048,)):

@@ -3,6 +3,8 @@ built for (checked on the CPU against the plain models of each step's intermedia
 value), so that the GPU parity tests that use them cover those branches."""
 import random
 
+import pytest
+
 from oracle import ranluxpp as R
 from tests import rare_paths as RP
 
@@ -40,17 +42,19 @@ def test_tc_model_and_crafted_operands():
     assert all(RP.tc_fold_carries(x, A)[1] for x in RP.tc_above_m_inputs(A))
 
 
-def _tc_epilogue_common_path(x, A):
+def _tc_epilogue_common_path(v):
     """The tensor draw kernels' epilogue on its common path, restated on Python integers
-    limb by limb as the kernel computes it: the fold with its carry stopped at limb 8,
-    and the conversion's quick quotient with its carry stopped at limb 7.  Returns
-    (X, D, rare), rare being the kernel's test for redoing both exactly."""
-    v = RP.tc_assembled(x, A)
+    limb by limb as the kernel computes it from the assembled value v: the fold with
+    limbs 1..6 taken unchanged (right when limb 0 does not borrow) and its carry stopped
+    at limb 8, and the conversion's quick quotient with its carry stopped at limb 7.
+    Returns (X, D, rare), rare being the kernel's test for redoing both exactly."""
     T, Xa = v >> 576, v % RP.B576
-    low = (Xa % RP.B288) + T * ((1 << 240) - 1)
-    c9 = low >> 288
-    X = (Xa >> 288 << 288) | (low % RP.B288)
-    limb = [(X >> (32 * k)) & 0xFFFFFFFF for k in range(18)]
+    a = [(Xa >> (32 * k)) & 0xFFFFFFFF for k in range(18)]
+    b0 = a[0] < T
+    s78 = a[7] + (a[8] << 32) + (T << 16)
+    c9 = s78 >> 64
+    limbs = [(a[0] - T) % (1 << 32)] + a[1:7] + [s78 & 0xFFFFFFFF, (s78 >> 32) & 0xFFFFFFFF] + a[9:]
+    X = sum(l << (32 * k) for k, l in enumerate(limbs))
     S = (X << 240) % RP.B576
     top = (S >> 480) - (X >> 480)              # limbs 15..17 of S - X, no borrow from below
     borrow = 1 if top < 0 else 0
@@ -60,20 +64,33 @@ def _tc_epilogue_common_path(x, A):
     s8 = (X % RP.B256) + (q0 - borrow) % (1 << 32) + ((X >> 368) << 32)
     c8 = s8 >> 256
     D = (X >> 256 << 256) | (s8 % RP.B256)
-    rare = (c9 or c8 or limb[17] == 0xFFFFFFFF or t == (1 << 96) - 1 or t == 0 or q0 < borrow)
+    rare = (b0 or c9 or c8 or limbs[17] == 0xFFFFFFFF or t == (1 << 96) - 1 or t == 0 or q0 < borrow)
     return X, D, rare
 
 
-def test_tc_epilogue_common_path_is_exact():
+def _assembled_x(x, A):
+    return RP.tc_assembled(x, A)
+
+
+def _assembled_d(x, A):
+    D, c = R.to_ranlux(x)
+    return RP.tc_assembled_d(D, c, A)
+
+
+@pytest.mark.parametrize("form", ["x", "d"])
+def test_tc_epilogue_common_path_is_exact(form):
     """Wherever the kernel's test lets the common path stand, its X and D equal A x mod m
-    and floor(2^576 X / m); the crafted operands all take the rare branch."""
-    rng = random.Random(8)
+    and floor(2^576 X / m), for operand rows holding X (the draw kernels with per-stream
+    counts) and holding D and c (the fused, value and request kernels); the crafted
+    operands all take the rare branch."""
+    assembled = _assembled_x if form == "x" else _assembled_d
+    rng = random.Random(8 if form == "x" else 9)
     for p in (24, 2048):
         A = R.luxury_multiplier(p)
         common = 0
         for _ in range(4000):
             x = rng.randrange(1, R.M)
-            X, D, rare = _tc_epilogue_common_path(x, A)
+            X, D, rare = _tc_epilogue_common_path(assembled(x, A))
             if not rare:
                 common += 1
                 assert X == A * x % R.M
@@ -81,6 +98,26 @@ def test_tc_epilogue_common_path_is_exact():
         assert common >= 3990
     A = R.luxury_multiplier(2048)
     Ainv = pow(A, -1, R.M)
-    crafted = RP.tc_limb8_carry_inputs(A, random.Random(2548)) + RP.tc_above_m_inputs(A)[1:]
+    if form == "x":
+        crafted = RP.tc_limb8_carry_inputs(A, random.Random(2548)) + RP.tc_above_m_inputs(A)[1:]
+    else:
+        crafted = (RP.tc_d_borrow_states(A, random.Random(2748)) + RP.tc_d_limb8_carry_states(A, random.Random(2848))
+                   + RP.tc_d_above_m_states(A))
     crafted += [Ainv * y % R.M for y in RP.conversion_carry_states(random.Random(2648), k=8)]
-    assert all(_tc_epilogue_common_path(x, A)[2] for x in crafted)
+    assert all(_tc_epilogue_common_path(assembled(x, A))[2] for x in crafted)
+
+
+def test_tc_d_crafted_states_reach_their_cases():
+    """The crafted states for operand rows holding D and c reach the case each is built
+    for: a borrow out of limb 0 of the fold, a carry out of limb 8, the final correction."""
+    for p in (389, 2048):
+        A = R.luxury_multiplier(p)
+        for want, states in ((0, RP.tc_d_borrow_states(A, random.Random(p))),
+                             (1, RP.tc_d_limb8_carry_states(A, random.Random(p + 1), want=2)),
+                             (2, RP.tc_d_above_m_states(A))):
+            assert states
+            for X in states:
+                assert 0 < X < R.M
+                D, c = R.to_ranlux(X)
+                assert R.to_lcg(D, c) == X
+                assert RP.tc_fold_cases_d(D, c, A)[want]
