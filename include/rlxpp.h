@@ -484,7 +484,8 @@ rlxpp_status rlxpp_server_take_done(rlxpp_server* server, rlxpp_served* out, uin
 rlxpp_status rlxpp_server_result(rlxpp_server* server, uint64_t rid, void* dst, uint64_t nbytes);
 /* Replays a trace on an idle server: request i (id i) of count[i] values (f64 if
  * is_f64[i], else u24) from stream[i] is submitted once arrival[i] seconds have passed;
- * latency[i] receives its completion minus its arrival in seconds, -1 if rejected. */
+ * latency[i] receives its completion minus its arrival in seconds, -1 if rejected.  The
+ * launch and device times of rlxpp_server_stats start again from zero at each call. */
 rlxpp_status rlxpp_server_run_trace(rlxpp_server* server, uint64_t n, const double* arrival,
                                     const uint64_t* stream, const int64_t* count, const uint8_t* is_f64,
                                     double* latency);

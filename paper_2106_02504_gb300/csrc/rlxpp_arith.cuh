@@ -444,7 +444,8 @@ __device__ __forceinline__ uint32_t bfind_u32(uint32_t x) {  // position of the 
 
 // The 12 doubles of a block (Sec. 2.3 draw rule, integer construction as in
 // f64_bits_from48).  Value j is lo_j + hi_j 2^32 with hi_j < 2^16; when every hi_j is
-// nonzero (all but a 12 2^-16 share of the blocks, decided by one minimum) the leading
+// nonzero (all but a 12 2^-16 share of the blocks, decided by one OR of the bfind
+// results, which are 0xFFFFFFFF for a zero hi_j) the leading
 // one of v_j is bit 32 + p_j, p_j = bfind(hi_j): the mantissa is v_j shifted left by
 // 20 - p_j and the exponent field (1006 + p_j) + 1 (the leading one adds the 1).
 __device__ __forceinline__ void block_f64(const uint32_t D[kLimbs], uint4 v[6]) {
@@ -456,14 +457,17 @@ __device__ __forceinline__ void block_f64(const uint32_t D[kLimbs], uint4 v[6]) 
     lo[2 * q + 1] = __funnelshift_l(D[3 * q + 1], D[3 * q + 2], 16);
     hi[2 * q + 1] = D[3 * q + 2] >> 16;
   }
-  uint32_t mn = hi[0];
+  uint32_t pos[kDoubles], any = 0;
 #pragma unroll
-  for (int j = 1; j < kDoubles; ++j) mn = min(mn, hi[j]);
-  if (__builtin_expect(mn != 0u, 1)) {
+  for (int j = 0; j < kDoubles; ++j) {
+    pos[j] = bfind_u32(hi[j]);
+    any |= pos[j];
+  }
+  if (__builtin_expect((int32_t)any >= 0, 1)) {
     uint32_t bh[kDoubles], bl[kDoubles];
 #pragma unroll
     for (int j = 0; j < kDoubles; ++j) {
-      const uint32_t p = bfind_u32(hi[j]);  // 0..15
+      const uint32_t p = pos[j];  // 0..15
       const uint32_t sh = 20u - p;          // 5..20
       bl[j] = lo[j] << sh;
       bh[j] = __funnelshift_l(lo[j], hi[j], sh) + ((1006u + p) << 20);

@@ -513,6 +513,12 @@ rlxpp_status rlxpp_server_run_trace(rlxpp_server* s, uint64_t n, const double* a
   if (busy(s) || !s->live.empty())
     return set_last_error(RLXPP_ERR_INVALID, "a trace needs an idle server with every result taken");
   for (uint64_t k = 0; k < n; ++k) latency[k] = -1.0;  // rejected requests stay at -1
+  // the launch and device times that rlxpp_server_stats reports cover this trace only
+  s->max_launch_s = 0.0;
+  s->slow_launches = 0;
+  s->batches_timed = 0;
+  s->kernel_s_sum = s->kernel_s_max = 0.0;
+  s->copy_s_sum = s->copy_s_max = 0.0;
   s->t0 = now_s();
   uint64_t i = 0;
   const uint64_t base_rid = 0;  // request i of the trace has id i
