@@ -174,6 +174,7 @@ void free_gen(rlxpp_gen* g) {
   cudaFree(g->status);
   cudaFree(g->tc_matrix);
   cudaFree(g->tc_matrix_d);
+  cudaFree(g->tc_matrix_d32);
   for (auto& u : g->upload) {
     if (u.ev) cudaEventDestroy(u.ev);
     if (u.host) cudaFreeHost(u.host);
@@ -425,11 +426,16 @@ rlxpp_status rlxpp_create(uint64_t n_streams, const uint32_t* levels, uint32_t n
   {  // tensor-path matrices of every level; the tensor path is the default
     e = dev_malloc(&g->tc_matrix, tc_matrix_bytes() * n_levels);
     if (e == cudaSuccess) e = dev_malloc(&g->tc_matrix_d, tc_matrix_bytes() * n_levels);
+    if (e == cudaSuccess) e = dev_malloc(&g->tc_matrix_d32, tc_matrix_bytes() * n_levels);
     for (uint32_t l = 0; e == cudaSuccess && l < n_levels; ++l) {
       e = launch_tc_matrix(g->lux + (size_t)l * 18, static_cast<char*>(g->tc_matrix) + tc_matrix_bytes() * l, st);
       if (e == cudaSuccess)
         e = launch_tc_matrix_d(g->lux + (size_t)l * 18, static_cast<char*>(g->tc_matrix_d) + tc_matrix_bytes() * l,
                                st);
+      // A^32 = power-table entry (window 1, digit 2): the multiplier of strided request chunks
+      if (e == cudaSuccess)
+        e = launch_tc_matrix_d(g->table + (size_t)l * kTableLimbs + (size_t)(1 * kDigits + 2) * 18,
+                               static_cast<char*>(g->tc_matrix_d32) + tc_matrix_bytes() * l, st);
     }
     if (e != cudaSuccess) return bail(fail(cuda_status(e), std::string("tensor setup: ") + cudaGetErrorString(e)));
     g->path = RLXPP_PATH_TENSOR;

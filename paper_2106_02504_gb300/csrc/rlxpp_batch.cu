@@ -343,6 +343,13 @@ rlxpp_status plan_impl(rlxpp_gen* g, const rlxpp_request* reqs, uint64_t n_reqs,
   // chunks
   std::vector<Item> items;
   items.reserve((size_t)(total_refills / L + n_reqs + 1));
+  // tensor path: a request with at least kStride L blocks after its start block draws
+  // them as strided chunks, warps of 32 lanes of L blocks each (blocks 1 + c 32 L + t +
+  // 32 j of warp c, lane t), kept apart from the sorted chunks; the head of its start
+  // block and the blocks past its last whole warp are plain chunks
+  const bool strided_ok = t.path == RLXPP_PATH_TENSOR;
+  std::vector<Item> sitems;                              // warps of 32 strided chunks
+  std::vector<std::pair<uint32_t, uint64_t>> swarps;     // (level, first strided chunk) per warp
   bool has_u24 = false, has_f64 = false;
   for (uint64_t r = 0; r < n_reqs; ++r) {
     const rlxpp_request& q = reqs[r];
@@ -357,6 +364,37 @@ rlxpp_status plan_impl(rlxpp_gen* g, const rlxpp_request* reqs, uint64_t n_reqs,
     if (count == 0) {
       if (flags & RLXPP_REQ_ADVANCE)  // no values, the state still moves by the skip
         items.push_back(Item{q.skip, 0, q.offset, (uint32_t)r, kind | (q.pos << 8) | (1u << 16)});
+      continue;
+    }
+    const uint64_t n_sw = strided_ok ? refills_left / (kStride * L) : 0;
+    if (n_sw > 0) {
+      const uint32_t lvl = g->level_host[q.stream];
+      const uint64_t nb = refills_left;                        // blocks 1 .. nb after the start block
+      const uint64_t last_vals = count - head - (nb - 1) * per;  // values of block nb, 1 .. per
+      if (head > 0) items.push_back(Item{q.skip, (int64_t)head, q.offset, (uint32_t)r, kind | (q.pos << 8)});
+      for (uint64_t c = 0; c < n_sw; ++c) {
+        swarps.push_back({lvl, sitems.size()});
+        for (uint32_t tl = 0; tl < kStride; ++tl) {
+          const uint64_t f = 1 + c * kStride * L + tl;           // first block of this lane
+          const bool has_last = f + kStride * (L - 1) == nb;     // the lane draws block nb
+          const uint64_t cnt = L * per - (has_last ? per - last_vals : 0);
+          sitems.push_back(Item{q.skip + f, (int64_t)cnt, q.offset + head + (f - 1) * per, (uint32_t)r,
+                                kind | kItemStrided | (has_last ? (1u << 16) : 0u)});
+        }
+      }
+      // blocks past the strided warps, from the last block they draw (refill first)
+      uint64_t block = q.skip + kStride * L * n_sw;
+      uint64_t emitted = std::min<uint64_t>(count, head + kStride * L * n_sw * per);
+      refills_left -= kStride * L * n_sw;
+      while (refills_left > 0) {
+        const uint64_t rj = std::min<uint64_t>(refills_left, L);
+        const uint64_t nj = std::min<uint64_t>(count - emitted, rj * per);
+        items.push_back(Item{block, (int64_t)nj, q.offset + emitted, (uint32_t)r, kind | ((uint32_t)kWords << 8)});
+        block += rj;
+        emitted += nj;
+        refills_left -= rj;
+        if (refills_left == 0) items.back().info |= 1u << 16;
+      }
       continue;
     }
     // chunk 0: the head of the start block and up to L - 1 refills
@@ -432,7 +470,8 @@ rlxpp_status plan_impl(rlxpp_gen* g, const rlxpp_request* reqs, uint64_t n_reqs,
     p->level_begin[g->n_levels] = items.size();
   }
   // tensor path: tiles of up to 128 consecutive items of one level, ordered by their
-  // first (longest) item's refills, longest first across levels
+  // first (longest) item's refills, longest first across levels; strided tiles (up to
+  // four warps of one level) after the sorted chunks in the item table
   std::vector<TcTile> tiles;
   if (t.path == RLXPP_PATH_TENSOR) {
     std::vector<std::pair<uint64_t, TcTile>> keyed;
@@ -441,6 +480,17 @@ rlxpp_status plan_impl(rlxpp_gen* g, const rlxpp_request* reqs, uint64_t n_reqs,
         const uint64_t n = std::min<uint64_t>(128, p->level_begin[l + 1] - a);
         keyed.push_back({refills_of(items[a]), TcTile{a, (uint32_t)n, l}});
       }
+    for (uint32_t l = 0; l < g->n_levels; ++l) {
+      uint32_t in_tile = 0;
+      for (const auto& w : swarps) {
+        if (w.first != l) continue;
+        if (in_tile == 0) keyed.push_back({refills_of(sitems[w.second]), TcTile{items.size(), 0, l | kTileStrided}});
+        items.insert(items.end(), sitems.begin() + (ptrdiff_t)w.second,
+                     sitems.begin() + (ptrdiff_t)(w.second + kStride));
+        keyed.back().second.n += kStride;
+        in_tile = in_tile + 1 == kTcTileWarps ? 0 : in_tile + 1;
+      }
+    }
     std::stable_sort(keyed.begin(), keyed.end(), [](const auto& x, const auto& y) { return x.first > y.first; });
     tiles.reserve(keyed.size());
     for (const auto& k : keyed) tiles.push_back(k.second);
@@ -530,7 +580,7 @@ rlxpp_status run_impl(rlxpp_gen* g, const rlxpp_plan* p, uint32_t* out_u24, doub
   const unsigned grid = (unsigned)std::max(1, g->sms) * p->tuning.blocks_per_sm;
   if (e == cudaSuccess) {
     if (p->tuning.path == RLXPP_PATH_TENSOR && g->tc_matrix && p->tiles) {
-      e = launch_requests_tc(b, p->items, p->tiles, p->n_tiles, g->tc_matrix_d, p->wc, grid, st);
+      e = launch_requests_tc(b, p->items, p->tiles, p->n_tiles, g->tc_matrix_d, g->tc_matrix_d32, p->wc, grid, st);
     } else if (p->tuning.path == RLXPP_PATH_WARP) {
       e = launch_requests_warp(b, p->items, p->n_items, p->wc, grid, tuning_tpb(p->tuning), st);
     } else {

@@ -12,8 +12,18 @@ struct Item {       // one chunk (32 bytes)
   int64_t count;    // values
   uint64_t out;     // index of the first value in the output array of its kind
   uint32_t req;     // request index
-  uint32_t info;    // bit 0: kind (1 = f64); bits 8..15: read position; bit 16: last chunk
+  uint32_t info;    // bit 0: kind (1 = f64); bits 8..15: read position; bit 16: last chunk;
+                    // bit 17: strided (its blocks are 32 apart, see kItemStrided)
 };
+// A strided chunk (tensor path) is one lane of a warp of 32 chunks of one request: lane t
+// draws blocks f + t, f + t + 32, f + t + 64, ... (one product by A^32 per refill), so the
+// warp's 32 blocks of a refill are consecutive in the output and leave as one contiguous
+// run.  Its first block is reached by its jump and drawn from read position 0; the j-th
+// block after it goes to out + 32 j per.
+constexpr uint32_t kItemStrided = 1u << 17;
+constexpr uint32_t kStride = 32;             // blocks between a strided chunk's blocks
+constexpr uint32_t kTileStrided = 1u << 31;  // TcTile::level flag: the tile's items are strided
+constexpr uint32_t kTcTileWarps = 4;         // warps of a tensor-path tile (128 rows)
 
 struct BatchArgs {
   const uint64_t* req_stream;  // [n_reqs]
@@ -27,7 +37,8 @@ struct BatchArgs {
 };
 
 // One tile of the tensor-core request kernel: up to 128 consecutive items of one luxury
-// level (items[first .. first + n)).
+// level (items[first .. first + n)); a strided tile (level | kTileStrided) holds up to four
+// warps of 32 strided chunks each and multiplies by the level's A^32.
 struct TcTile {
   uint64_t first;
   uint32_t n;
@@ -83,7 +94,8 @@ __device__ __forceinline__ void finish_cta(WorkCounters* wc) {
 // Tensor-core request kernel: persistent CTAs over the tile table, every level in one
 // launch; bimg holds the levels' matrices one after the other.
 cudaError_t launch_requests_tc(const BatchArgs& b, const Item* items, const TcTile* tiles, uint64_t n_tiles,
-                               const void* bimg, WorkCounters* wc, unsigned grid, cudaStream_t st);
+                               const void* bimg, const void* bimg32, WorkCounters* wc, unsigned grid,
+                               cudaStream_t st);
 // Warp-cooperative request kernel (one warp per chunk; rlxpp_warp.cu): every level in one
 // launch, the level's multiplier read from the state view's table; tpb threads per CTA
 // (64, 128 or 256).

@@ -151,6 +151,7 @@ struct rlxpp_gen {
   uint32_t path = 0;                       // RLXPP_PATH_IMAD or RLXPP_PATH_TENSOR
   void* tc_matrix = nullptr;               // [n_levels] tensor-path matrices
   void* tc_matrix_d = nullptr;             // [n_levels] the same for (D, c) operand rows
+  void* tc_matrix_d32 = nullptr;           // [n_levels] the same for the multiplier A^32 (strided chunks)
   struct Upload {                          // page-locked staging of request work lists
     void* host = nullptr;
     size_t bytes = 0;

@@ -561,6 +561,47 @@ __device__ __forceinline__ void warp_store_blocks(const unsigned char* wstage, u
   __syncwarp();  // the slots may be written again
 }
 
+// The full blocks of one warp of strided chunks (one request's blocks f .. f + 31 of a
+// refill): lanes 0 .. n - 1 have full blocks whose destinations run on consecutively
+// (lane l's is lane 0's plus 96 l bytes) and the others none, so the warp copies its
+// n * 96 staged bytes as one contiguous run, 16-, 8- or 4-byte units by the alignment of
+// its start.  Destinations that do not form such a run (not expected) go through
+// warp_store_blocks.  Every lane of the warp calls it.
+__device__ __forceinline__ void warp_store_run(const unsigned char* wstage, uint64_t dst) {
+  const unsigned lane = threadIdx.x & 31u;
+  const uint64_t d0 = __shfl_sync(0xFFFFFFFFu, dst, 0);
+  const unsigned nfull = __popc(__ballot_sync(0xFFFFFFFFu, dst != 0));
+  const bool in_run = dst == 0 ? lane >= nfull : (lane < nfull && dst == d0 + (uint64_t)kStageBytes * lane);
+  if (!__all_sync(0xFFFFFFFFu, in_run)) {
+    warp_store_blocks(wstage, dst);
+    return;
+  }
+  __syncwarp();  // the lanes' slots are written
+  if ((d0 & 15u) == 0) {
+    const uint4* src = reinterpret_cast<const uint4*>(wstage);
+    uint4* o = reinterpret_cast<uint4*>(d0);
+    const unsigned n = nfull * (kStageBytes / 16);
+#pragma unroll
+    for (int i = 0; i < 6; ++i)
+      if (i * 32u + lane < n) o[i * 32u + lane] = src[i * 32u + lane];
+  } else if ((d0 & 7u) == 0) {
+    const uint64_t* src = reinterpret_cast<const uint64_t*>(wstage);
+    uint64_t* o = reinterpret_cast<uint64_t*>(d0);
+    const unsigned n = nfull * (kStageBytes / 8);
+#pragma unroll
+    for (int i = 0; i < 12; ++i)
+      if (i * 32u + lane < n) o[i * 32u + lane] = src[i * 32u + lane];
+  } else {
+    const uint32_t* src = reinterpret_cast<const uint32_t*>(wstage);
+    uint32_t* o = reinterpret_cast<uint32_t*>(d0);
+    const unsigned n = nfull * (kStageBytes / 4);
+#pragma unroll
+    for (int i = 0; i < 24; ++i)
+      if (i * 32u + lane < n) o[i * 32u + lane] = src[i * 32u + lane];
+  }
+  __syncwarp();  // the slots may be written again
+}
+
 // Draw kernel on the tensor path (single-level handles).  Same semantics as k_draw.
 // A CTA holds T tile-groups (one SM's worth), each refilling its own tile of 128
 // streams independently of the others.  tmap (when use_tma): the output as a
@@ -1401,7 +1442,8 @@ __device__ __forceinline__ void emit_head(bool f64, const BatchArgs& b, const ui
 // block, and the warp writes its 32 staged blocks cooperatively.
 __global__ void __launch_bounds__(kReqThreads, 4)
     k_requests_tc(const BatchArgs b, const Item* __restrict__ items, const TcTile* __restrict__ tiles,
-                  uint64_t n_tiles, const __half* __restrict__ bimg_all, WorkCounters* wc) {
+                  uint64_t n_tiles, const __half* __restrict__ bimg_all, const __half* __restrict__ bimg32_all,
+                  WorkCounters* wc) {
   extern __shared__ __align__(1024) unsigned char smem[];
   __shared__ unsigned long long tile_s;
   const int tid = threadIdx.x;
@@ -1434,8 +1476,10 @@ __global__ void __launch_bounds__(kReqThreads, 4)
     __syncthreads();  // every thread has read the tile index
     if (t >= n_tiles) break;
     const TcTile tile = tiles[t];
+    const bool strided = (tile.level & kTileStrided) != 0;  // the tile's chunks step by A^32
     if (tile.level != loaded) {  // the products of the previous tile are complete
-      const uint4* src = reinterpret_cast<const uint4*>(bimg_all + (size_t)tile.level * (kBBytes / 2));
+      const uint4* src = reinterpret_cast<const uint4*>((strided ? bimg32_all : bimg_all) +
+                                                        (size_t)(tile.level & ~kTileStrided) * (kBBytes / 2));
       uint4* dst = reinterpret_cast<uint4*>(tc_bmat(smem));
       for (int w = tid; w < kBBytes / 16; w += kReqThreads) dst[w] = src[w];
       fence_proxy_async_smem();  // -> visible to the tensor core after the next barrier
@@ -1464,6 +1508,9 @@ __global__ void __launch_bounds__(kReqThreads, 4)
     }
     const bool f64 = (it.info & 1u) != 0;
     const int64_t cnt = live ? it.count : 0, base = (int64_t)it.out;
+    // a strided chunk's next block is kStride blocks on: the values drawn so far (k, whole
+    // blocks) stand for kStride as many places in the output
+    const int64_t ostep = strided ? (int64_t)kStride : 1;
     const int64_t per = f64 ? kDoubles : kWords;
     uint32_t pos = live ? (it.info >> 8) & 0xFFu : (uint32_t)kWords;
     int64_t k = 0;
@@ -1538,20 +1585,20 @@ __global__ void __launch_bounds__(kReqThreads, 4)
             block_values<kDrawU24>(D, v);
 #pragma unroll
           for (int q = 0; q < 6; ++q) slot[q] = v[q];
-          dst = f64 ? reinterpret_cast<uint64_t>(b.out_f64 + base + k)
-                    : reinterpret_cast<uint64_t>(b.out_u24 + base + k);
+          dst = f64 ? reinterpret_cast<uint64_t>(b.out_f64 + base + ostep * k)
+                    : reinterpret_cast<uint64_t>(b.out_u24 + base + ostep * k);
           k += per;
           pos = kWords;
         } else {
           if (f64) {
 #pragma unroll
             for (int j = 0; j < kDoubles; ++j)
-              if (j < rem) b.out_f64[base + k + j] = f64_bits_from48_outlined(bits48(D, j));
+              if (j < rem) b.out_f64[base + ostep * k + j] = f64_bits_from48_outlined(bits48(D, j));
             pos = (uint32_t)(rem * 2);
           } else {
 #pragma unroll
             for (int j = 0; j < kWords; ++j)
-              if (j < rem) b.out_u24[base + k + j] = word24(D, j);
+              if (j < rem) b.out_u24[base + ostep * k + j] = word24(D, j);
             pos = (uint32_t)rem;
           }
           k = cnt;
@@ -1563,7 +1610,10 @@ __global__ void __launch_bounds__(kReqThreads, 4)
           b.s.meta[st] = meta_pack(pos, c, lvl);
         }
       }
-      warp_store_blocks(wstage, dst);
+      if (strided)
+        warp_store_run(wstage, dst);
+      else
+        warp_store_blocks(wstage, dst);
     }
     // every warp has left the tile's loop (on a timeout, after its own wait ran out):
     // the CTA goes on to the next tile together, or stops together
@@ -1846,12 +1896,14 @@ cudaError_t launch_fused_tc(const DrawArgs& a, const __half* bimg_d, cudaStream_
 size_t tc_matrix_bytes() { return kBBytes; }
 
 cudaError_t launch_requests_tc(const BatchArgs& b, const Item* items, const TcTile* tiles, uint64_t n_tiles,
-                               const void* bimg, WorkCounters* wc, unsigned grid, cudaStream_t st) {
+                               const void* bimg, const void* bimg32, WorkCounters* wc, unsigned grid,
+                               cudaStream_t st) {
   if (n_tiles == 0) return cudaSuccess;
   cudaError_t e = cudaFuncSetAttribute(k_requests_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTcSmem);
   if (e != cudaSuccess) return e;
   if (grid > n_tiles) grid = (unsigned)n_tiles;
-  k_requests_tc<<<grid, kReqThreads, kTcSmem, st>>>(b, items, tiles, n_tiles, static_cast<const __half*>(bimg), wc);
+  k_requests_tc<<<grid, kReqThreads, kTcSmem, st>>>(b, items, tiles, n_tiles, static_cast<const __half*>(bimg),
+                                                    static_cast<const __half*>(bimg32), wc);
   return cudaGetLastError();
 }
 

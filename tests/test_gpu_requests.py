@@ -184,6 +184,43 @@ def test_advance_flag_and_graph(native, path):
     run_and_check(native, g, xs, [2048] * n, reqs, nu, nf, tuning=(16, 3), graph=True)
 
 
+def test_strided_chunks(native):
+    """Tensor path: requests of at least 32 L blocks after their start block go out as
+    warps of 32 strided chunks (lane t draws blocks f + t, f + t + 32, ... by products
+    with A^32).  Counts that end exactly at a warp's last block (the request's last block
+    then in lane 31), one block, a partial block and a warp past it; start positions that
+    leave a head or none; skips; u24 and f64 at odd and even output offsets (runs that
+    start 4-, 8- and 16-byte aligned); every value against the oracle and, with
+    RLXPP_REQ_ADVANCE, every final state."""
+    n = 48
+    levels = [24, 389, 2048]
+    lvl = (np.arange(n) % 3).astype(np.uint8)
+    seeds = W.random_seeds(n, 205)
+    g = native.Generator(n, levels, torch.from_numpy(seeds.view(np.int64)).cuda(),
+                         torch.from_numpy(lvl).cuda())
+    g.set_path(native.RLXPP_PATH_TENSOR)
+    levels_of = [levels[int(lvl[i])] for i in range(n)]
+    for L in (2, 3):
+        xs, _ = current_X(native, g, n)
+        rows = []
+        for i in range(n):
+            kind = i % 2
+            per = 12 if kind else 24
+            pos = [0, 24, 2, 7, 23][i % 5] & (~1 if kind else ~0)  # f64 heads start on even words
+            room = (24 - pos) // (2 if kind else 1)
+            nb = 32 * L * (1 + i % 3) + [0, 1, 0, 33, 32 * L - 1][(i // 3) % 5]
+            count = room + (nb - 1) * per + [per, per, per - 5, 1, per // 2][(i // 5) % 5]
+            rows.append((i, [0, 3, 1000][i % 3], pos, kind, count))
+        reqs, nu, nf = make_requests(rows)
+        _, finals = run_and_check(native, g, xs, levels_of, reqs, nu, nf, flags=native.RLXPP_REQ_ADVANCE,
+                                  tuning=(L, 2, native.RLXPP_PATH_TENSOR, 128))
+        buf = torch.zeros((n, 11), dtype=torch.int64, device="cuda")
+        g.get_state(buf)
+        rec = buf.cpu().numpy().view(np.uint64)
+        for st, want in finals.items():
+            assert np.array_equal(rec[st], want), (L, st)
+
+
 def test_chunking_matches_plain_draw(native, path):
     """One long request split at several chunk lengths equals rlxpp_draw_f64."""
     seeds = np.array([42, 43], dtype=np.uint64)
