@@ -190,8 +190,8 @@ def test_strided_chunks(native):
     with A^32).  Counts that end exactly at a warp's last block (the request's last block
     then in lane 31), one block, a partial block and a warp past it; start positions that
     leave a head or none; skips; u24 and f64 at odd and even output offsets (runs that
-    start 4-, 8- and 16-byte aligned); every value against the oracle and, with
-    RLXPP_REQ_ADVANCE, every final state."""
+    start 4-, 8- and 16-byte aligned); at L = 12 also remainders of hundreds of blocks;
+    every value against the oracle and, with RLXPP_REQ_ADVANCE, every final state."""
     n = 48
     levels = [24, 389, 2048]
     lvl = (np.arange(n) % 3).astype(np.uint8)
@@ -200,7 +200,7 @@ def test_strided_chunks(native):
                          torch.from_numpy(lvl).cuda())
     g.set_path(native.RLXPP_PATH_TENSOR)
     levels_of = [levels[int(lvl[i])] for i in range(n)]
-    for L in (2, 3):
+    for L in (2, 3, 12):
         xs, _ = current_X(native, g, n)
         rows = []
         for i in range(n):
@@ -208,7 +208,7 @@ def test_strided_chunks(native):
             per = 12 if kind else 24
             pos = [0, 24, 2, 7, 23][i % 5] & (~1 if kind else ~0)  # f64 heads start on even words
             room = (24 - pos) // (2 if kind else 1)
-            nb = 32 * L * (1 + i % 3) + [0, 1, 0, 33, 32 * L - 1][(i // 3) % 5]
+            nb = 32 * L * (1 + i % 3) + [0, 1, 256, 33, 32 * L - 1, 300][(i // 3) % 6]
             count = room + (nb - 1) * per + [per, per, per - 5, 1, per // 2][(i // 5) % 5]
             rows.append((i, [0, 3, 1000][i % 3], pos, kind, count))
         reqs, nu, nf = make_requests(rows)
