@@ -228,7 +228,11 @@ typedef struct rlxpp_tuning {
   uint32_t path;          /* which kernel runs the chunks (paths defined below):
                              RLXPP_PATH_IMAD: one thread per chunk, integer pipe;
                              RLXPP_PATH_TENSOR: one thread per chunk, 128-chunk tiles
-                             on the tensor cores (4 CTAs per SM at most);
+                             on the tensor cores (4 CTAs per SM at most); a request of
+                             at least 32 L blocks is cut into warps of 32 strided
+                             chunks (lane t of a warp draws every 32nd block from its
+                             own, by products with A^32), whose blocks leave as one
+                             contiguous run per warp and refill;
                              RLXPP_PATH_WARP: 32 threads per chunk (one warp, one limb
                              per lane), for few long chunks.  The path also fixes the
                              limb width of the product: 32-bit limbs on the integer
