@@ -1438,8 +1438,11 @@ __device__ __forceinline__ void emit_head(bool f64, const BatchArgs& b, const ui
 // with the fused draw's pipelined loop (operand rows in TMEM, one barrier per refill,
 // the next product issued before the blocks are converted and written) until its
 // longest chunk is done.  Chunks of a tile have similar lengths, so little work is lost
-// to the longest one.  Chunks write to unrelated places: each lane stages its full
-// block, and the warp writes its 32 staged blocks cooperatively.
+// to the longest one.  Plain chunks write to unrelated places: each lane stages its full
+// block, and the warp writes its 32 staged blocks cooperatively.  A strided tile (up to
+// four warps of 32 strided chunks, kItemStrided) multiplies by the level's A^32, so each
+// lane steps 32 blocks a refill and a warp's 32 blocks of one refill are consecutive in
+// the output: the warp writes them as one contiguous run (warp_store_run).
 __global__ void __launch_bounds__(kReqThreads, 4)
     k_requests_tc(const BatchArgs b, const Item* __restrict__ items, const TcTile* __restrict__ tiles,
                   uint64_t n_tiles, const __half* __restrict__ bimg_all, const __half* __restrict__ bimg32_all,
